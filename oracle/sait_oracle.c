@@ -1,0 +1,577 @@
+/*
+ * SAIT oracle: TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded FP64 CPU implementation of what the GPU path
+ * computes, written from the paper (Z. Lu, "A sparse approximate inverse for
+ * triangular matrices based on Jacobi iteration", arXiv 2106.12836) and from
+ * the textbook algorithms it relies on.  It shares no code, header, table or
+ * helper with the CUDA library; only tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load it.
+ *
+ * Compile with -O2 -ffp-contract=off: every fused multiply-add below is an
+ * explicit fma() call, every other product is rounded on its own.
+ *
+ * Status codes returned by every entry point:
+ *   0 ok, 1 invalid argument, 2 not triangular, 3 zero or non-finite pivot,
+ *   4 out of memory, 5 not converged, 6 breakdown.
+ *
+ * Drop rules (argument drop_kind of ora_sait):
+ *   0 none     keep every structural entry of T~M + I
+ *   1 abs      Algorithm 2 (SAIT_Thr): drop |v| < tau
+ *   2 rowrel   drop |v| < tau * max_j |v_ij| of the current row (diagonal included)
+ *   3 pattern  Algorithm 3 (SAIT_Pat): p undropped iterations fix the pattern S,
+ *              the remaining iterations drop every entry outside S
+ * The diagonal is never dropped (Section 3: the unit diagonal keeps M full rank).
+ *
+ * Parity pins: see tests/test_oracle_pins.py.  Every function here is pinned.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORA_OK 0
+#define ORA_INVALID 1
+#define ORA_NOT_TRIANGULAR 2
+#define ORA_ZERO_PIVOT 3
+#define ORA_OOM 4
+#define ORA_NOT_CONVERGED 5
+#define ORA_BREAKDOWN 6
+
+typedef struct {
+    int64_t n, nnz, cap;
+    int32_t *rp;
+    int32_t *ci;
+    double *va;
+} ora_mat;
+
+void ora_free(ora_mat *m)
+{
+    if (!m) return;
+    free(m->rp);
+    free(m->ci);
+    free(m->va);
+    m->rp = NULL; m->ci = NULL; m->va = NULL;
+    m->n = m->nnz = m->cap = 0;
+}
+
+static int mat_init(ora_mat *m, int64_t n, int64_t cap)
+{
+    m->n = n; m->nnz = 0; m->cap = cap > 16 ? cap : 16;
+    m->rp = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+    m->ci = (int32_t *)malloc((size_t)m->cap * sizeof(int32_t));
+    m->va = (double *)malloc((size_t)m->cap * sizeof(double));
+    if (!m->rp || !m->ci || !m->va) { ora_free(m); return ORA_OOM; }
+    m->rp[0] = 0;
+    return ORA_OK;
+}
+
+static int mat_push(ora_mat *m, int32_t c, double v)
+{
+    if (m->nnz == m->cap) {
+        int64_t cap = m->cap * 2;
+        int32_t *ci = (int32_t *)realloc(m->ci, (size_t)cap * sizeof(int32_t));
+        if (!ci) return ORA_OOM;
+        m->ci = ci;
+        double *va = (double *)realloc(m->va, (size_t)cap * sizeof(double));
+        if (!va) return ORA_OOM;
+        m->va = va;
+        m->cap = cap;
+    }
+    m->ci[m->nnz] = c;
+    m->va[m->nnz] = v;
+    m->nnz++;
+    return ORA_OK;
+}
+
+static int cmp_i32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sparse matrix-vector product y = A x, summed in stored order.            */
+/* ------------------------------------------------------------------------ */
+void ora_spmv(int64_t n, const int32_t *rp, const int32_t *ci, const double *va,
+              const double *x, double *y)
+{
+    for (int64_t i = 0; i < n; i++) {
+        double s = 0.0;
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++) s += va[e] * x[ci[e]];
+        y[i] = s;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forward (lower) / backward (upper) substitution T x = b.  The exact      */
+/* triangular solve the paper's SAIT apply replaces (Section 3.1).          */
+/* ------------------------------------------------------------------------ */
+int ora_trisolve(int64_t n, const int32_t *rp, const int32_t *ci, const double *va,
+                 int lower, const double *b, double *x)
+{
+    for (int64_t t = 0; t < n; t++) {
+        int64_t i = lower ? t : n - 1 - t;
+        double s = b[i], d = 0.0;
+        int have_d = 0;
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
+            int64_t j = ci[e];
+            if (j == i) { d = va[e]; have_d = 1; }
+            else if ((lower && j < i) || (!lower && j > i)) s -= va[e] * x[j];
+            else return ORA_NOT_TRIANGULAR;
+        }
+        if (!have_d || d == 0.0 || !isfinite(d)) return ORA_ZERO_PIVOT;
+        x[i] = s / d;
+    }
+    return ORA_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* ILU(0), IKJ variant (Saad, Iterative Methods for Sparse Linear Systems,   */
+/* 2nd ed., Algorithm 10.4).  Overwrites a (values of A in A's pattern)      */
+/* with L (strict lower part, unit diagonal implied) and U (upper part with  */
+/* the diagonal).  The paper takes level-0 ILU factors as the triangular    */
+/* inputs of SAIT (Section 4).  Columns must be sorted ascending.            */
+/* ------------------------------------------------------------------------ */
+int ora_ilu0(int64_t n, const int32_t *rp, const int32_t *ci, double *a)
+{
+    int64_t *pos = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int64_t *dpos = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    if (!pos || !dpos) { free(pos); free(dpos); return ORA_OOM; }
+    int st = ORA_OK;
+    for (int64_t i = 0; i < n; i++) {
+        pos[i] = -1;
+        dpos[i] = -1;
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
+            if (e > rp[i] && ci[e] <= ci[e - 1]) { st = ORA_INVALID; goto done; }
+            if (ci[e] == i) dpos[i] = e;
+        }
+        if (dpos[i] < 0) { st = ORA_ZERO_PIVOT; goto done; }
+    }
+    for (int64_t i = 0; i < n; i++) {
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++) pos[ci[e]] = e;
+        for (int32_t e = rp[i]; e < rp[i + 1] && ci[e] < i; e++) {
+            int64_t k = ci[e];
+            double ukk = a[dpos[k]];
+            if (ukk == 0.0 || !isfinite(ukk)) { st = ORA_ZERO_PIVOT; goto done; }
+            a[e] = a[e] / ukk;                       /* a_ik := a_ik / a_kk */
+            for (int32_t f = dpos[k] + 1; f < rp[k + 1]; f++) {
+                int64_t p = pos[ci[f]];              /* (i,j) in NZ(A), j > k */
+                if (p >= 0) a[p] = fma(-a[e], a[f], a[p]);   /* a_ij -= a_ik a_kj */
+            }
+        }
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++) pos[ci[e]] = -1;
+        if (a[dpos[i]] == 0.0 || !isfinite(a[dpos[i]])) { st = ORA_ZERO_PIVOT; goto done; }
+    }
+done:
+    free(pos);
+    free(dpos);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* SAIT (Algorithms 1-3).                                                   */
+/*                                                                          */
+/* With D = diag(T) and T~ = I - D^-1 T (strictly triangular, Section 2),    */
+/* the Horner / Qin Jiushao recursion (equation Recursive) is               */
+/*     M_0 D = I,   M_k D = T~ (M_{k-1} D) + I,                              */
+/* and after the loop M = (M D) D^-1.  m_terms is the number of series      */
+/* terms of M = sum_{i < m_terms} T~^i D^-1 (equation M_poly), i.e. the loop */
+/* runs m_terms - 1 times; the paper's SAIT_Thr(tau, m) is m_terms = m + 1 */
+/* and SAIT_Pat(p, m) is m_terms = p + m + 1.                               */
+/*                                                                          */
+/* Each product row is formed in a dense accumulator: for k over row i of   */
+/* T~ in ascending column order, for j over row k of the iterate,           */
+/*     acc_j = fma(T~_ik, (MD)_kj, acc_j),                                   */
+/* then the diagonal entry 1 is added, then the drop rule is applied to the */
+/* whole row (the thresholds act on the unit-diagonal iterate MD, as in     */
+/* step 3 of Algorithms 1-2, before the final scaling by D^-1).             */
+/* ------------------------------------------------------------------------ */
+int ora_sait(int64_t n, const int32_t *rp, const int32_t *ci, const double *va,
+             int m_terms, int drop_kind, double tau, int p, ora_mat *out)
+{
+    memset(out, 0, sizeof(*out));
+    if (n < 0 || m_terms < 1 || drop_kind < 0 || drop_kind > 3 || p < 0 ||
+        ((drop_kind == 1 || drop_kind == 2) && !(tau >= 0.0)))
+        return ORA_INVALID;
+    int st = ORA_OK;
+    int side = 0;   /* -1 lower, +1 upper, 0 diagonal only so far */
+    double *dinv = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    double *acc = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    int64_t *stamp = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int64_t *sstamp = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int32_t *list = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    ora_mat tt = {0}, M = {0}, S = {0};
+    if (!dinv || !acc || !stamp || !sstamp || !list) { st = ORA_OOM; goto done; }
+
+    /* Step 1: D^-1 and T~ = I - D^-1 T, whose off-diagonal entries are
+     * -(d_i^-1 T_ij) and whose diagonal is exactly zero. */
+    if ((st = mat_init(&tt, n, rp[n] > 0 ? rp[n] : 1)) != ORA_OK) goto done;
+    for (int64_t i = 0; i < n; i++) {
+        int have_d = 0;
+        double d = 0.0;
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
+            if (e > rp[i] && ci[e] <= ci[e - 1]) { st = ORA_INVALID; goto done; }
+            if (ci[e] == i) { have_d = 1; d = va[e]; continue; }
+            int s = ci[e] < i ? -1 : 1;
+            if (side == 0) side = s;
+            else if (side != s) { st = ORA_NOT_TRIANGULAR; goto done; }
+        }
+        if (!have_d || d == 0.0 || !isfinite(d)) { st = ORA_ZERO_PIVOT; goto done; }
+        dinv[i] = 1.0 / d;
+    }
+    for (int64_t i = 0; i < n; i++) {
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++)
+            if (ci[e] != i && (st = mat_push(&tt, ci[e], -(dinv[i] * va[e]))) != ORA_OK) goto done;
+        tt.rp[i + 1] = (int32_t)tt.nnz;
+    }
+
+    /* M D = I. */
+    if ((st = mat_init(&M, n, n)) != ORA_OK) goto done;
+    for (int64_t i = 0; i < n; i++) {
+        if ((st = mat_push(&M, (int32_t)i, 1.0)) != ORA_OK) goto done;
+        M.rp[i + 1] = (int32_t)(i + 1);
+    }
+    if (drop_kind == 3 && p == 0) {          /* S = pattern of M_1 = pattern(T^0) */
+        if ((st = mat_init(&S, n, n)) != ORA_OK) goto done;
+        for (int64_t i = 0; i < n; i++) { mat_push(&S, (int32_t)i, 1.0); S.rp[i + 1] = (int32_t)(i + 1); }
+    }
+
+    for (int64_t i = 0; i < n; i++) { stamp[i] = -1; sstamp[i] = -1; }
+    int64_t epoch = 0;
+    for (int it = 1; it < m_terms; it++) {
+        ora_mat Mn = {0};
+        if ((st = mat_init(&Mn, n, M.nnz + n)) != ORA_OK) goto done;
+        for (int64_t i = 0; i < n; i++) {
+            epoch++;
+            int64_t cnt = 0;
+            /* T~ (M D), row i, ascending k */
+            for (int32_t e = tt.rp[i]; e < tt.rp[i + 1]; e++) {
+                int64_t k = tt.ci[e];
+                double t = tt.va[e];
+                for (int32_t f = M.rp[k]; f < M.rp[k + 1]; f++) {
+                    int32_t j = M.ci[f];
+                    if (stamp[j] != epoch) { stamp[j] = epoch; acc[j] = 0.0; list[cnt++] = j; }
+                    acc[j] = fma(t, M.va[f], acc[j]);
+                }
+            }
+            /* + I */
+            if (stamp[i] != epoch) { stamp[i] = epoch; acc[i] = 0.0; list[cnt++] = (int32_t)i; }
+            acc[i] = acc[i] + 1.0;
+            qsort(list, (size_t)cnt, sizeof(int32_t), cmp_i32);
+
+            /* dropping rule on the whole new row */
+            int kind = drop_kind;
+            if (kind == 3 && it <= p) kind = 0;          /* pattern-building iterations */
+            double thr = tau;
+            if (kind == 2) {
+                double mx = 0.0;
+                for (int64_t q = 0; q < cnt; q++) { double a = fabs(acc[list[q]]); if (a > mx) mx = a; }
+                thr = tau * mx;
+            }
+            if (kind == 3)
+                for (int32_t f = S.rp[i]; f < S.rp[i + 1]; f++) sstamp[S.ci[f]] = epoch;
+            for (int64_t q = 0; q < cnt; q++) {
+                int32_t j = list[q];
+                double v = acc[j];
+                int keep = 1;
+                if (j != i) {
+                    if (kind == 1 || kind == 2) keep = !(fabs(v) < thr);
+                    else if (kind == 3) keep = (sstamp[j] == epoch);
+                }
+                if (keep && (st = mat_push(&Mn, j, v)) != ORA_OK) { ora_free(&Mn); goto done; }
+            }
+            Mn.rp[i + 1] = (int32_t)Mn.nnz;
+        }
+        ora_free(&M);
+        M = Mn;
+        if (drop_kind == 3 && it == p) {       /* keep the sparsity pattern S of M */
+            if ((st = mat_init(&S, n, M.nnz)) != ORA_OK) goto done;
+            for (int64_t i = 0; i < n; i++) {
+                for (int32_t f = M.rp[i]; f < M.rp[i + 1]; f++) mat_push(&S, M.ci[f], 1.0);
+                S.rp[i + 1] = (int32_t)S.nnz;
+            }
+        }
+    }
+
+    /* M = (M D) D^-1: column j scaled by d_j^-1 */
+    for (int64_t e = 0; e < M.nnz; e++) M.va[e] = M.va[e] * dinv[M.ci[e]];
+    *out = M;
+    M.rp = NULL; M.ci = NULL; M.va = NULL;
+done:
+    ora_free(&M);
+    ora_free(&tt);
+    ora_free(&S);
+    free(dinv); free(acc); free(stamp); free(sstamp); free(list);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Preconditioners for the Krylov solvers.                                   */
+/*   kind 0: none (z = r)                                                    */
+/*   kind 1: SAIT pair, z = M_U (M_L r)        (Section 3.1)                 */
+/*   kind 2: exact ILU, z = U^-1 (L^-1 r)      (substitution; Section 3.1)   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int kind;
+    int64_t n;
+    const int32_t *l_rp, *l_ci;
+    const double *l_va;
+    const int32_t *u_rp, *u_ci;
+    const double *u_va;
+} ora_prec;
+
+static int prec_apply(const ora_prec *P, const double *r, double *z, double *tmp)
+{
+    int64_t n = P->n;
+    if (P->kind == 0) { memcpy(z, r, (size_t)n * sizeof(double)); return ORA_OK; }
+    if (P->kind == 1) {
+        ora_spmv(n, P->l_rp, P->l_ci, P->l_va, r, tmp);
+        ora_spmv(n, P->u_rp, P->u_ci, P->u_va, tmp, z);
+        return ORA_OK;
+    }
+    if (P->kind == 2) {
+        int st = ora_trisolve(n, P->l_rp, P->l_ci, P->l_va, 1, r, tmp);
+        if (st) return st;
+        return ora_trisolve(n, P->u_rp, P->u_ci, P->u_va, 0, tmp, z);
+    }
+    return ORA_INVALID;
+}
+
+static double dot(int64_t n, const double *x, const double *y)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; i++) s += x[i] * y[i];
+    return s;
+}
+
+static double nrm2(int64_t n, const double *x) { return sqrt(dot(n, x, x)); }
+
+/* true residual r = b - A x, returns ||r|| */
+static double residual(int64_t n, const int32_t *rp, const int32_t *ci, const double *va,
+                       const double *b, const double *x, double *r)
+{
+    ora_spmv(n, rp, ci, va, x, r);
+    for (int64_t i = 0; i < n; i++) r[i] = b[i] - r[i];
+    return nrm2(n, r);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Restarted GMRES(m) with right preconditioning: Arnoldi by modified        */
+/* Gram-Schmidt, Givens rotations for the least-squares problem, x updated   */
+/* as x + P (V y) at the end of each cycle (Saad, Algorithms 6.9 and 9.5).   */
+/* Stops when ||b - A x|| / ||b|| <= tol (true residual, checked at the end  */
+/* of each cycle; the Givens estimate decides when a cycle ends).  *iters    */
+/* counts Arnoldi steps (matrix-vector products with A).                     */
+/* ------------------------------------------------------------------------ */
+int ora_gmres(int64_t n, const int32_t *rp, const int32_t *ci, const double *va,
+              const ora_prec *P, const double *b, double *x, int restart, double tol,
+              int maxit, int *iters, double *relres)
+{
+    if (restart < 1 || maxit < 0 || n < 0) return ORA_INVALID;
+    int m = restart;
+    double *V = (double *)malloc((size_t)(m + 1) * (size_t)n * sizeof(double) + 8);
+    double *H = (double *)calloc((size_t)(m + 1) * (size_t)m, sizeof(double));
+    double *cs = (double *)malloc((size_t)m * sizeof(double));
+    double *sn = (double *)malloc((size_t)m * sizeof(double));
+    double *g = (double *)malloc((size_t)(m + 1) * sizeof(double));
+    double *y = (double *)malloc((size_t)m * sizeof(double));
+    double *w = (double *)malloc((size_t)n * sizeof(double) + 8);
+    double *z = (double *)malloc((size_t)n * sizeof(double) + 8);
+    double *tmp = (double *)malloc((size_t)n * sizeof(double) + 8);
+    int st = ORA_NOT_CONVERGED;
+    *iters = 0;
+    *relres = 0.0;
+    if (!V || !H || !cs || !sn || !g || !y || !w || !z || !tmp) { st = ORA_OOM; goto done; }
+    double bnorm = nrm2(n, b);
+    if (bnorm == 0.0) { for (int64_t i = 0; i < n; i++) x[i] = 0.0; st = ORA_OK; goto done; }
+#define Hij(i, j) H[(size_t)(j) * (size_t)(m + 1) + (size_t)(i)]
+    for (;;) {
+        double beta = residual(n, rp, ci, va, b, x, w);
+        *relres = beta / bnorm;
+        if (*relres <= tol) { st = ORA_OK; break; }
+        if (*iters >= maxit) break;
+        for (int64_t i = 0; i < n; i++) V[i] = w[i] / beta;
+        g[0] = beta;
+        int jj = 0;
+        for (int j = 0; j < m; j++) {
+            double *vj = V + (size_t)j * n, *vn = V + (size_t)(j + 1) * n;
+            int ps = prec_apply(P, vj, z, tmp);
+            if (ps) { st = ps; goto done; }
+            ora_spmv(n, rp, ci, va, z, w);
+            (*iters)++;
+            for (int i = 0; i <= j; i++) {                       /* MGS */
+                double *vi = V + (size_t)i * n;
+                double h = dot(n, w, vi);
+                Hij(i, j) = h;
+                for (int64_t q = 0; q < n; q++) w[q] -= h * vi[q];
+            }
+            double hn = nrm2(n, w);
+            Hij(j + 1, j) = hn;
+            for (int i = 0; i < j; i++) {                        /* old rotations */
+                double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+                Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
+                Hij(i, j) = t;
+            }
+            double a = Hij(j, j), bb = Hij(j + 1, j);             /* new rotation */
+            if (bb == 0.0) { cs[j] = 1.0; sn[j] = 0.0; }
+            else { double t = hypot(a, bb); cs[j] = a / t; sn[j] = bb / t; }
+            Hij(j, j) = cs[j] * a + sn[j] * bb;
+            Hij(j + 1, j) = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            jj = j + 1;
+            if (hn != 0.0)
+                for (int64_t q = 0; q < n; q++) vn[q] = w[q] / hn;
+            if (fabs(g[j + 1]) <= tol * bnorm || hn == 0.0 || *iters >= maxit) break;
+        }
+        for (int i = jj - 1; i >= 0; i--) {                      /* H y = g */
+            double s = g[i];
+            for (int k = i + 1; k < jj; k++) s -= Hij(i, k) * y[k];
+            if (Hij(i, i) == 0.0) { st = ORA_BREAKDOWN; goto done; }
+            y[i] = s / Hij(i, i);
+        }
+        for (int64_t q = 0; q < n; q++) {
+            double s = 0.0;
+            for (int i = 0; i < jj; i++) s += y[i] * V[(size_t)i * n + q];
+            w[q] = s;
+        }
+        int ps = prec_apply(P, w, z, tmp);
+        if (ps) { st = ps; goto done; }
+        for (int64_t q = 0; q < n; q++) x[q] += z[q];
+    }
+#undef Hij
+done:
+    free(V); free(H); free(cs); free(sn); free(g); free(y); free(w); free(z); free(tmp);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* BiCGSTAB with right preconditioning (van der Vorst 1992; Saad,           */
+/* Algorithm 7.7 applied to A P u = b, x = P u).  *iters counts full        */
+/* iterations (two products with A each).  Convergence is tested on the     */
+/* recursive residuals s and r and confirmed on the true residual.          */
+/* ------------------------------------------------------------------------ */
+int ora_bicgstab(int64_t n, const int32_t *rp, const int32_t *ci, const double *va,
+                 const ora_prec *P, const double *b, double *x, double tol, int maxit,
+                 int *iters, double *relres)
+{
+    double *r = (double *)malloc((size_t)n * sizeof(double) + 8);
+    double *rh = (double *)malloc((size_t)n * sizeof(double) + 8);
+    double *p = (double *)calloc((size_t)n + 1, sizeof(double));
+    double *v = (double *)calloc((size_t)n + 1, sizeof(double));
+    double *ph = (double *)malloc((size_t)n * sizeof(double) + 8);
+    double *s = (double *)malloc((size_t)n * sizeof(double) + 8);
+    double *sh = (double *)malloc((size_t)n * sizeof(double) + 8);
+    double *t = (double *)malloc((size_t)n * sizeof(double) + 8);
+    double *tmp = (double *)malloc((size_t)n * sizeof(double) + 8);
+    int st = ORA_NOT_CONVERGED;
+    *iters = 0;
+    *relres = 0.0;
+    if (!r || !rh || !p || !v || !ph || !s || !sh || !t || !tmp) { st = ORA_OOM; goto done; }
+    double bnorm = nrm2(n, b);
+    if (bnorm == 0.0) { for (int64_t i = 0; i < n; i++) x[i] = 0.0; st = ORA_OK; goto done; }
+    double rn = residual(n, rp, ci, va, b, x, r);
+    *relres = rn / bnorm;
+    if (*relres <= tol) { st = ORA_OK; goto done; }
+    memcpy(rh, r, (size_t)n * sizeof(double));
+    double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+    while (*iters < maxit) {
+        double rho = dot(n, rh, r);
+        if (rho == 0.0 || omega == 0.0) { st = ORA_BREAKDOWN; break; }
+        double beta = (rho / rho_old) * (alpha / omega);
+        for (int64_t i = 0; i < n; i++) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+        int ps = prec_apply(P, p, ph, tmp);
+        if (ps) { st = ps; break; }
+        ora_spmv(n, rp, ci, va, ph, v);
+        double rv = dot(n, rh, v);
+        if (rv == 0.0) { st = ORA_BREAKDOWN; break; }
+        alpha = rho / rv;
+        for (int64_t i = 0; i < n; i++) s[i] = r[i] - alpha * v[i];
+        (*iters)++;
+        if (nrm2(n, s) / bnorm <= tol) {
+            for (int64_t i = 0; i < n; i++) x[i] += alpha * ph[i];
+            rn = residual(n, rp, ci, va, b, x, r);
+            *relres = rn / bnorm;
+            if (*relres <= tol) { st = ORA_OK; break; }
+            memcpy(rh, r, (size_t)n * sizeof(double));     /* restart the recurrence */
+            rho_old = alpha = omega = 1.0;
+            memset(p, 0, (size_t)n * sizeof(double));
+            memset(v, 0, (size_t)n * sizeof(double));
+            continue;
+        }
+        ps = prec_apply(P, s, sh, tmp);
+        if (ps) { st = ps; break; }
+        ora_spmv(n, rp, ci, va, sh, t);
+        double tt = dot(n, t, t);
+        omega = tt == 0.0 ? 0.0 : dot(n, t, s) / tt;
+        for (int64_t i = 0; i < n; i++) {
+            x[i] += alpha * ph[i] + omega * sh[i];
+            r[i] = s[i] - omega * t[i];
+        }
+        rho_old = rho;
+        if (nrm2(n, r) / bnorm <= tol) {
+            rn = residual(n, rp, ci, va, b, x, r);
+            *relres = rn / bnorm;
+            if (*relres <= tol) { st = ORA_OK; break; }
+            memcpy(rh, r, (size_t)n * sizeof(double));
+            rho_old = alpha = omega = 1.0;
+            memset(p, 0, (size_t)n * sizeof(double));
+            memset(v, 0, (size_t)n * sizeof(double));
+        }
+    }
+    if (st == ORA_NOT_CONVERGED) *relres = residual(n, rp, ci, va, b, x, r) / bnorm;
+done:
+    free(r); free(rh); free(p); free(v); free(ph); free(s); free(sh); free(t); free(tmp);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Preconditioned conjugate gradients (Saad, Algorithm 9.1), the paper's    */
+/* linear solver (Section 4).  The preconditioner is applied as given, even */
+/* when it is not symmetric (the SAIT pair M_U M_L is not).  Convergence is  */
+/* tested on the recursive residual ||r|| / ||b|| and the returned relres is */
+/* the true residual.                                                       */
+/* ------------------------------------------------------------------------ */
+int ora_pcg(int64_t n, const int32_t *rp, const int32_t *ci, const double *va,
+            const ora_prec *P, const double *b, double *x, double tol, int maxit,
+            int *iters, double *relres)
+{
+    double *r = (double *)malloc((size_t)n * sizeof(double) + 8);
+    double *z = (double *)malloc((size_t)n * sizeof(double) + 8);
+    double *p = (double *)malloc((size_t)n * sizeof(double) + 8);
+    double *q = (double *)malloc((size_t)n * sizeof(double) + 8);
+    double *tmp = (double *)malloc((size_t)n * sizeof(double) + 8);
+    int st = ORA_NOT_CONVERGED;
+    *iters = 0;
+    *relres = 0.0;
+    if (!r || !z || !p || !q || !tmp) { st = ORA_OOM; goto done; }
+    double bnorm = nrm2(n, b);
+    if (bnorm == 0.0) { for (int64_t i = 0; i < n; i++) x[i] = 0.0; st = ORA_OK; goto done; }
+    double rn = residual(n, rp, ci, va, b, x, r);
+    if (rn / bnorm <= tol) { *relres = rn / bnorm; st = ORA_OK; goto done; }
+    int ps = prec_apply(P, r, z, tmp);
+    if (ps) { st = ps; goto done; }
+    memcpy(p, z, (size_t)n * sizeof(double));
+    double rho = dot(n, r, z);
+    while (*iters < maxit) {
+        ora_spmv(n, rp, ci, va, p, q);
+        double pq = dot(n, p, q);
+        if (pq == 0.0) { st = ORA_BREAKDOWN; break; }
+        double alpha = rho / pq;
+        for (int64_t i = 0; i < n; i++) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
+        (*iters)++;
+        if (nrm2(n, r) / bnorm <= tol) { st = ORA_OK; break; }
+        ps = prec_apply(P, r, z, tmp);
+        if (ps) { st = ps; break; }
+        double rho_new = dot(n, r, z);
+        if (rho == 0.0) { st = ORA_BREAKDOWN; break; }
+        double beta = rho_new / rho;
+        for (int64_t i = 0; i < n; i++) p[i] = z[i] + beta * p[i];
+        rho = rho_new;
+    }
+    *relres = residual(n, rp, ci, va, b, x, r) / bnorm;
+done:
+    free(r); free(z); free(p); free(q); free(tmp);
+    return st;
+}
