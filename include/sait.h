@@ -1,0 +1,197 @@
+/*
+ * sait.h: C ABI of the GB300 SAIT library (libsait.so).
+ *
+ * SAIT (Z. Lu, "A sparse approximate inverse for triangular matrices based
+ * on Jacobi iteration", arXiv 2106.12836) replaces the two triangular
+ * substitutions of an ILU preconditioner, U (L x) = y, by two sparse
+ * matrix-vector products x = M_U (M_L y), where each M approximates T^-1 by
+ * the truncated Jacobi series
+ *
+ *     M = sum_{i < m_terms} T~^i D^-1,   D = diag(T),   T~ = I - D^-1 T
+ *
+ * (Section 2, equations M_poly and T_inverse), built by the Horner recursion
+ * M_k D = T~ (M_{k-1} D) + I (equation Recursive) with a dropping rule applied
+ * after every product (Algorithms 1-3).
+ *
+ * Conventions for every entry point:
+ *  - Matrices are square CSR with int32 row pointers and column indices,
+ *    columns ascending within each row, FP64 values.  A sait_csr holds
+ *    DEVICE pointers owned by the caller; the library reads them during the
+ *    call only.
+ *  - Vectors (double*) are DEVICE pointers of length n owned by the caller.
+ *  - Every call is ordered on the CUDA stream given to sait_ctx_create.  Calls
+ *    documented as "synchronizes" wait for that stream before returning;
+ *    sait_spmv, sait_apply and sait_prec_apply only enqueue work.
+ *  - Errors are returned as sait_status, never thrown and never fatal; the
+ *    arguments are validated before any kernel is launched.
+ *    sait_ctx_last_error gives a one-line description of the last failure.
+ *  - A context and everything created with it belong to one host thread at a
+ *    time.  sait_mat and sait_prec objects must be destroyed before their
+ *    context; a sait_prec does not own the matrices it refers to.
+ */
+#ifndef SAIT_H
+#define SAIT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SAIT_OK = 0,
+    SAIT_ERR_INVALID_ARG = 1,    /* bad pointer, size, option, or unsorted/out-of-range column */
+    SAIT_ERR_NOT_TRIANGULAR = 2, /* an entry lies on the wrong side of the diagonal */
+    SAIT_ERR_ZERO_PIVOT = 3,     /* missing, zero or non-finite diagonal entry */
+    SAIT_ERR_OOM = 4,            /* device allocation failed */
+    SAIT_ERR_CUDA = 5,           /* any other CUDA runtime error */
+    SAIT_ERR_NOT_CONVERGED = 6,  /* solver reached maxit; x holds the last iterate */
+    SAIT_ERR_BREAKDOWN = 7,      /* Krylov breakdown (zero inner product) */
+    SAIT_ERR_TIMEOUT = 8,        /* a bounded device-side wait ran out */
+    SAIT_ERR_NONFINITE = 9,      /* NaN or Inf met in a solver */
+    SAIT_ERR_UNSUPPORTED = 10    /* size beyond a documented limit (e.g. nnz >= 2^31) */
+} sait_status;
+
+/* Dropping rules applied to the unit-diagonal iterate M D after each product
+ * T~ (M D) + I.  The diagonal entry is never dropped (Section 3). */
+typedef enum {
+    SAIT_DROP_NONE = 0,    /* keep every structural entry (exact series) */
+    SAIT_DROP_ABS = 1,     /* Algorithm 2, SAIT_Thr: drop |v| < tau */
+    SAIT_DROP_ROWREL = 2,  /* drop |v| < tau * max_j |(M D)_ij| of the current row */
+    SAIT_DROP_PATTERN = 3  /* Algorithm 3, SAIT_Pat: the first p products are not dropped
+                              and fix the pattern S; later products drop entries outside S */
+} sait_drop_kind;
+
+typedef struct {
+    int32_t kind;   /* sait_drop_kind */
+    int32_t p;      /* SAIT_DROP_PATTERN: number of pattern-building products, 0 <= p */
+    double tau;     /* SAIT_DROP_ABS / SAIT_DROP_ROWREL: threshold, 0 <= tau < 1 */
+} sait_drop;
+
+/* Storage precision of a matrix's values for products (the FP64 values are
+ * always kept as well).  FP32 and BF16 products accumulate in FP32. */
+typedef enum { SAIT_F64 = 0, SAIT_F32 = 1, SAIT_BF16 = 2 } sait_dtype;
+
+typedef enum { SAIT_LOWER = 0, SAIT_UPPER = 1 } sait_uplo;
+
+typedef struct {
+    int64_t n;               /* rows = columns */
+    int64_t nnz;             /* row_ptr[n] */
+    const int32_t *row_ptr;  /* device, n + 1 entries, row_ptr[0] = 0 */
+    const int32_t *col;      /* device, nnz entries */
+    const double *val;       /* device, nnz entries */
+} sait_csr;
+
+typedef struct {
+    int32_t iters;      /* products with A: Arnoldi steps (GMRES) or 2 per iteration (BiCGSTAB) */
+    int32_t cycles;     /* GMRES restart cycles / BiCGSTAB recurrence restarts */
+    double rel_resid;   /* true ||b - A x||_2 / ||b||_2 at exit, computed in FP64 */
+} sait_info;
+
+typedef struct sait_ctx_s *sait_ctx;
+typedef struct sait_mat_s *sait_mat;
+typedef struct sait_prec_s *sait_prec;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context on the current CUDA device.  stream: a cudaStream_t, or
+ * NULL for the legacy default stream.  The context owns pinned host staging
+ * and the stream-ordered pool its temporaries come from. */
+sait_status sait_ctx_create(sait_ctx *ctx, void *stream);
+sait_status sait_ctx_destroy(sait_ctx ctx);
+/* Static description of a status code. */
+const char *sait_status_string(sait_status st);
+/* Description of the last failure on this context ("" if none).  The pointer
+ * stays valid until the next call on the context. */
+const char *sait_ctx_last_error(sait_ctx ctx);
+
+/* ---- matrices ---------------------------------------------------------- */
+
+/* Copy a caller CSR matrix into a library-owned matrix (FP64 storage).
+ * Validates row pointers and column order.  Synchronizes. */
+sait_status sait_mat_create_csr(sait_ctx ctx, const sait_csr *A, sait_mat *out);
+sait_status sait_mat_destroy(sait_mat M);
+/* Rows and stored entries of M. */
+sait_status sait_mat_info(sait_mat M, int64_t *n, int64_t *nnz);
+/* Copy M's CSR arrays (FP64 values) into caller device buffers of n + 1,
+ * nnz and nnz entries.  Any pointer may be NULL to skip it.  Enqueues only. */
+sait_status sait_mat_export_csr(sait_ctx ctx, sait_mat M, int32_t *row_ptr, int32_t *col,
+                                double *val);
+/* Select the precision products with M read (SAIT_F64, SAIT_F32 or SAIT_BF16);
+ * creates the reduced copy of the values on first use.  Synchronizes. */
+sait_status sait_mat_set_store(sait_ctx ctx, sait_mat M, sait_dtype store);
+
+/* ---- ILU(0) factors (Section 4: level-0 ILU factors are SAIT's input) ---- */
+
+/* Level-0 incomplete LU of A on A's pattern (Saad, Algorithm 10.4, IKJ order),
+ * computed on the GPU by level scheduling.  *L: unit lower triangular with
+ * its unit diagonal stored; *U: upper triangular with the pivots.  A needs
+ * every diagonal entry stored.  Returns SAIT_ERR_ZERO_PIVOT if a pivot is
+ * zero or non-finite.  Synchronizes. */
+sait_status sait_ilu0(sait_ctx ctx, const sait_csr *A, sait_mat *L, sait_mat *U);
+
+/* ---- SAIT build (Algorithms 1-3) ---------------------------------------- */
+
+/* Build M ~ T^-1 with m_terms series terms (m_terms >= 1; the loop of
+ * Algorithm 1 runs m_terms - 1 times, so the paper's SAIT_Thr(tau, m) is
+ * m_terms = m + 1 and SAIT_Pat(p, m) is m_terms = p + m + 1).  T must be
+ * triangular on side uplo with every diagonal entry stored, nonzero and
+ * finite.  Each product row is accumulated in ascending order of T~'s
+ * columns with FP64 fused multiply-adds; the dropping rule acts on M D before
+ * the final column scaling M = (M D) D^-1.  store selects the product
+ * precision (sait_mat_set_store).  Output limit: nnz(M) < 2^31.
+ * Synchronizes (the output size is data-dependent). */
+sait_status sait_build(sait_ctx ctx, sait_mat T, sait_uplo uplo, int32_t m_terms, sait_drop drop,
+                       sait_dtype store, sait_mat *M);
+
+/* ---- products ----------------------------------------------------------- */
+
+/* y = A x with A's selected storage precision (FP64 values accumulate in
+ * FP64, FP32/BF16 values in FP32).  x and y must not overlap.  Enqueues only. */
+sait_status sait_spmv(sait_ctx ctx, sait_mat A, const double *x, double *y);
+
+/* SAIT preconditioner apply z = M_U (M_L r) (Section 3.1).  The intermediate
+ * vector is FP64 when both matrices are stored in FP64, otherwise FP32.
+ * r and z must not overlap.  Enqueues only. */
+sait_status sait_apply(sait_ctx ctx, sait_mat ML, sait_mat MU, const double *r, double *z);
+
+/* ---- preconditioner objects for the solvers ----------------------------- */
+
+/* SAIT pair: applies z = M_U (M_L r). */
+sait_status sait_prec_create_sait(sait_ctx ctx, sait_mat ML, sait_mat MU, sait_prec *P);
+/* Exact ILU: z = U^-1 (L^-1 r) by level-scheduled substitution (the exact
+ * triangular solves SAIT replaces; the paper's comparison in Section 4).
+ * Computes the level sets on the GPU.  Synchronizes. */
+sait_status sait_prec_create_ilu(sait_ctx ctx, sait_mat L, sait_mat U, sait_prec *P);
+/* Number of level sets of the lower and upper factor (ILU preconditioner). */
+sait_status sait_prec_levels(sait_prec P, int32_t *levels_lower, int32_t *levels_upper);
+/* z = P r; enqueues only. */
+sait_status sait_prec_apply(sait_ctx ctx, sait_prec P, const double *r, double *z);
+sait_status sait_prec_destroy(sait_prec P);
+
+/* ---- solvers (Section 4 uses PCG/LOBPCG; GMRES and BiCGSTAB extend it to
+ * the nonsymmetric case) ------------------------------------------------ */
+
+/* Restarted GMRES(restart) with right preconditioning (Saad, Algorithm 9.5):
+ * Arnoldi with classical Gram-Schmidt and one reorthogonalisation, Givens
+ * rotations on the device, x <- x + P (V y) at the end of each cycle.
+ * P may be NULL (no preconditioner).  x: in, the initial guess; out, the
+ * solution.  Stops when the true relative residual ||b - A x|| / ||b|| <= tol
+ * (checked at the end of every cycle; the rotated residual estimate ends a
+ * cycle early).  maxit bounds the Arnoldi steps.  1 <= restart <= 512.
+ * The host reads a device status word every few steps.  Synchronizes;
+ * fills *info if info is not NULL. */
+sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const double *b, double *x,
+                       int32_t restart, double tol, int32_t maxit, sait_info *info);
+
+/* BiCGSTAB with right preconditioning (van der Vorst 1992; Saad,
+ * Algorithm 7.7 on A P u = b).  Same conventions as sait_gmres; maxit bounds
+ * the iterations (two products with A each). */
+sait_status sait_bicgstab(sait_ctx ctx, sait_mat A, sait_prec P, const double *b, double *x,
+                          double tol, int32_t maxit, sait_info *info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAIT_H */

@@ -1,0 +1,343 @@
+"""GB300 SAIT: sparse approximate inverses of triangular factors (arXiv 2106.12836).
+
+A thin ctypes binding over ``libsait.so`` whose functions carry the names of
+the C ABI in ``include/sait.h``.  It only marshals arguments: every step of
+the computation runs in the library's CUDA kernels.  Device buffers are torch
+tensors (int32 row pointers / columns, float64 values and vectors); the
+library runs on the stream of the context, by default torch's current stream.
+
+The library must have been built (``paper_2106_12836_gb300.build.build()``);
+importing this package on a machine where it is missing raises at once.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import build as _build
+
+__all__ = [
+    "SaitError", "Context", "Mat", "Prec", "Info", "DROP", "DTYPE",
+    "sait_ctx_create", "sait_ctx_destroy", "sait_status_string", "sait_ctx_last_error",
+    "sait_mat_create_csr", "sait_mat_destroy", "sait_mat_info", "sait_mat_export_csr",
+    "sait_mat_set_store", "sait_ilu0", "sait_build", "sait_spmv", "sait_apply",
+    "sait_prec_create_sait", "sait_prec_create_ilu", "sait_prec_levels", "sait_prec_apply",
+    "sait_prec_destroy", "sait_gmres", "sait_bicgstab", "lib_path", "EXPORTS",
+]
+
+DROP = {"none": 0, "abs": 1, "rowrel": 2, "pattern": 3}
+DTYPE = {"f64": 0, "f32": 1, "bf16": 2}
+LOWER, UPPER = 0, 1
+
+# Every entry point declared in include/sait.h.
+EXPORTS = [
+    "sait_ctx_create", "sait_ctx_destroy", "sait_status_string", "sait_ctx_last_error",
+    "sait_mat_create_csr", "sait_mat_destroy", "sait_mat_info", "sait_mat_export_csr",
+    "sait_mat_set_store", "sait_ilu0", "sait_build", "sait_spmv", "sait_apply",
+    "sait_prec_create_sait", "sait_prec_create_ilu", "sait_prec_levels", "sait_prec_apply",
+    "sait_prec_destroy", "sait_gmres", "sait_bicgstab",
+]
+
+
+class _Csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class _Drop(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("p", C.c_int32), ("tau", C.c_double)]
+
+
+class Info(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("cycles", C.c_int32), ("rel_resid", C.c_double)]
+
+    def as_dict(self):
+        return {"iters": self.iters, "cycles": self.cycles, "rel_resid": self.rel_resid}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise ImportError(f"libsait.so not built ({_build.LIB}); run "
+                              "paper_2106_12836_gb300.build.build() first")
+        lib = C.CDLL(_build.LIB)
+        vp, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        sigs = {
+            "sait_ctx_create": [C.POINTER(vp), vp],
+            "sait_ctx_destroy": [vp],
+            "sait_status_string": [C.c_int],
+            "sait_ctx_last_error": [vp],
+            "sait_mat_create_csr": [vp, C.POINTER(_Csr), C.POINTER(vp)],
+            "sait_mat_destroy": [vp],
+            "sait_mat_info": [vp, C.POINTER(i64), C.POINTER(i64)],
+            "sait_mat_export_csr": [vp, vp, vp, vp, vp],
+            "sait_mat_set_store": [vp, vp, C.c_int],
+            "sait_ilu0": [vp, C.POINTER(_Csr), C.POINTER(vp), C.POINTER(vp)],
+            "sait_build": [vp, vp, C.c_int, i32, _Drop, C.c_int, C.POINTER(vp)],
+            "sait_spmv": [vp, vp, vp, vp],
+            "sait_apply": [vp, vp, vp, vp, vp],
+            "sait_prec_create_sait": [vp, vp, vp, C.POINTER(vp)],
+            "sait_prec_create_ilu": [vp, vp, vp, C.POINTER(vp)],
+            "sait_prec_levels": [vp, C.POINTER(i32), C.POINTER(i32)],
+            "sait_prec_apply": [vp, vp, vp, vp],
+            "sait_prec_destroy": [vp],
+            "sait_gmres": [vp, vp, vp, vp, vp, i32, d, i32, C.POINTER(Info)],
+            "sait_bicgstab": [vp, vp, vp, vp, vp, d, i32, C.POINTER(Info)],
+        }
+        for name, args in sigs.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        lib.sait_status_string.restype = C.c_char_p
+        lib.sait_ctx_last_error.restype = C.c_char_p
+        _lib = lib
+    return _lib
+
+
+class SaitError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"[{status}] {msg}")
+        self.status = status
+
+
+def _check(ctx, st: int, what: str):
+    if st != 0:
+        detail = _L().sait_ctx_last_error(ctx.h if ctx is not None else None)
+        detail = detail.decode() if detail else ""
+        raise SaitError(st, f"{what}: {sait_status_string(st)}; {detail}")
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _vec(t: torch.Tensor, n: int, name: str) -> torch.Tensor:
+    if t.dtype != torch.float64 or t.numel() != n or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous float64 CUDA tensor of {n} entries")
+    return t
+
+
+class Context:
+    """Owns a sait_ctx bound to a CUDA stream (torch's current stream by default)."""
+
+    def __init__(self, stream: torch.cuda.Stream | None = None):
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.h = None
+        self.h = sait_ctx_create(self.stream.cuda_stream)
+
+    def close(self):
+        if self.h is not None:
+            sait_ctx_destroy(self)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Mat:
+    """A library-owned CSR matrix (sait_mat)."""
+
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+        self.n, self.nnz = sait_mat_info(self)
+
+    def export(self):
+        return sait_mat_export_csr(self.ctx, self)
+
+    def close(self):
+        if self.h is not None:
+            sait_mat_destroy(self)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Prec:
+    """A preconditioner object (sait_prec); keeps its matrices alive."""
+
+    def __init__(self, ctx: Context, h, mats):
+        self.ctx, self.h, self._mats = ctx, h, mats
+        self.n = mats[0].n
+
+    def close(self):
+        if self.h is not None:
+            sait_prec_destroy(self)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _csr(n: int, rp: torch.Tensor, ci: torch.Tensor, va: torch.Tensor) -> _Csr:
+    if rp.dtype != torch.int32 or ci.dtype != torch.int32 or va.dtype != torch.float64:
+        raise ValueError("CSR arrays must be int32 row_ptr, int32 col, float64 val")
+    if rp.numel() != n + 1 or ci.numel() != va.numel():
+        raise ValueError("CSR array sizes do not match")
+    return _Csr(n, va.numel(), _ptr(rp), _ptr(ci) if ci.numel() else None,
+                _ptr(va) if va.numel() else None)
+
+
+# ---- C ABI, one Python function per entry point -------------------------------
+def sait_status_string(st: int) -> str:
+    return _L().sait_status_string(st).decode()
+
+
+def sait_ctx_create(stream_handle: int):
+    h = C.c_void_p()
+    st = _L().sait_ctx_create(C.byref(h), C.c_void_p(stream_handle))
+    if st:
+        raise SaitError(st, "sait_ctx_create: " + sait_status_string(st))
+    return h
+
+
+def sait_ctx_destroy(ctx: Context):
+    _check(None, _L().sait_ctx_destroy(ctx.h), "sait_ctx_destroy")
+
+
+def sait_ctx_last_error(ctx: Context) -> str:
+    return _L().sait_ctx_last_error(ctx.h).decode()
+
+
+def sait_mat_create_csr(ctx: Context, n: int, rp, ci, va) -> Mat:
+    A = _csr(n, rp, ci, va)
+    h = C.c_void_p()
+    _check(ctx, _L().sait_mat_create_csr(ctx.h, C.byref(A), C.byref(h)), "sait_mat_create_csr")
+    return Mat(ctx, h)
+
+
+def sait_mat_destroy(M: Mat):
+    _check(None, _L().sait_mat_destroy(M.h), "sait_mat_destroy")
+
+
+def sait_mat_info(M: Mat):
+    n, nnz = C.c_int64(), C.c_int64()
+    _check(None, _L().sait_mat_info(M.h, C.byref(n), C.byref(nnz)), "sait_mat_info")
+    return int(n.value), int(nnz.value)
+
+
+def sait_mat_export_csr(ctx: Context, M: Mat):
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rp = torch.empty(M.n + 1, dtype=torch.int32, device=dev)
+    ci = torch.empty(max(M.nnz, 1), dtype=torch.int32, device=dev)
+    va = torch.empty(max(M.nnz, 1), dtype=torch.float64, device=dev)
+    _check(ctx, _L().sait_mat_export_csr(ctx.h, M.h, _ptr(rp), _ptr(ci), _ptr(va)),
+           "sait_mat_export_csr")
+    return rp, ci[:M.nnz], va[:M.nnz]
+
+
+def sait_mat_set_store(ctx: Context, M: Mat, store: str):
+    _check(ctx, _L().sait_mat_set_store(ctx.h, M.h, DTYPE[store]), "sait_mat_set_store")
+
+
+def sait_ilu0(ctx: Context, n: int, rp, ci, va):
+    A = _csr(n, rp, ci, va)
+    hl, hu = C.c_void_p(), C.c_void_p()
+    _check(ctx, _L().sait_ilu0(ctx.h, C.byref(A), C.byref(hl), C.byref(hu)), "sait_ilu0")
+    return Mat(ctx, hl), Mat(ctx, hu)
+
+
+def sait_build(ctx: Context, T: Mat, lower: bool, m_terms: int, drop: str = "rowrel",
+               tau: float = 0.0, p: int = 0, store: str = "f64") -> Mat:
+    h = C.c_void_p()
+    d = _Drop(DROP[drop], int(p), float(tau))
+    _check(ctx, _L().sait_build(ctx.h, T.h, LOWER if lower else UPPER, int(m_terms), d,
+                                DTYPE[store], C.byref(h)), "sait_build")
+    return Mat(ctx, h)
+
+
+def sait_spmv(ctx: Context, A: Mat, x: torch.Tensor, y: torch.Tensor | None = None):
+    _vec(x, A.n, "x")
+    y = torch.empty_like(x) if y is None else _vec(y, A.n, "y")
+    _check(ctx, _L().sait_spmv(ctx.h, A.h, _ptr(x), _ptr(y)), "sait_spmv")
+    return y
+
+
+def sait_apply(ctx: Context, ML: Mat, MU: Mat, r: torch.Tensor, z: torch.Tensor | None = None):
+    _vec(r, ML.n, "r")
+    z = torch.empty_like(r) if z is None else _vec(z, ML.n, "z")
+    _check(ctx, _L().sait_apply(ctx.h, ML.h, MU.h, _ptr(r), _ptr(z)), "sait_apply")
+    return z
+
+
+def sait_prec_create_sait(ctx: Context, ML: Mat, MU: Mat) -> Prec:
+    h = C.c_void_p()
+    _check(ctx, _L().sait_prec_create_sait(ctx.h, ML.h, MU.h, C.byref(h)), "sait_prec_create_sait")
+    return Prec(ctx, h, (ML, MU))
+
+
+def sait_prec_create_ilu(ctx: Context, L: Mat, U: Mat) -> Prec:
+    h = C.c_void_p()
+    _check(ctx, _L().sait_prec_create_ilu(ctx.h, L.h, U.h, C.byref(h)), "sait_prec_create_ilu")
+    return Prec(ctx, h, (L, U))
+
+
+def sait_prec_levels(P: Prec):
+    a, b = C.c_int32(), C.c_int32()
+    _check(None, _L().sait_prec_levels(P.h, C.byref(a), C.byref(b)), "sait_prec_levels")
+    return int(a.value), int(b.value)
+
+
+def sait_prec_apply(ctx: Context, P: Prec, r: torch.Tensor, z: torch.Tensor | None = None):
+    _vec(r, P.n, "r")
+    z = torch.empty_like(r) if z is None else _vec(z, P.n, "z")
+    _check(ctx, _L().sait_prec_apply(ctx.h, P.h, _ptr(r), _ptr(z)), "sait_prec_apply")
+    return z
+
+
+def sait_prec_destroy(P: Prec):
+    _check(None, _L().sait_prec_destroy(P.h), "sait_prec_destroy")
+
+
+def sait_gmres(ctx: Context, A: Mat, P: Prec | None, b: torch.Tensor, x: torch.Tensor | None = None,
+               restart: int = 30, tol: float = 1e-8, maxit: int = 10000, check: bool = True):
+    _vec(b, A.n, "b")
+    x = torch.zeros_like(b) if x is None else _vec(x, A.n, "x")
+    info = Info()
+    st = _L().sait_gmres(ctx.h, A.h, P.h if P is not None else None, _ptr(b), _ptr(x),
+                         int(restart), float(tol), int(maxit), C.byref(info))
+    if check:
+        _check(ctx, st, "sait_gmres")
+    return x, info, st
+
+
+def sait_bicgstab(ctx: Context, A: Mat, P: Prec | None, b: torch.Tensor,
+                  x: torch.Tensor | None = None, tol: float = 1e-8, maxit: int = 10000,
+                  check: bool = True):
+    _vec(b, A.n, "b")
+    x = torch.zeros_like(b) if x is None else _vec(x, A.n, "x")
+    info = Info()
+    st = _L().sait_bicgstab(ctx.h, A.h, P.h if P is not None else None, _ptr(b), _ptr(x),
+                            float(tol), int(maxit), C.byref(info))
+    if check:
+        _check(ctx, st, "sait_bicgstab")
+    return x, info, st

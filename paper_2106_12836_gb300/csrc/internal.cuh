@@ -1,0 +1,122 @@
+// Internal declarations shared by the translation units of libsait.so.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "sait.h"
+
+struct sait_ctx_s {
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 1;
+    std::string last_error;
+    int *d_word = nullptr;     // device scratch words (error flags, counters)
+    void *h_pinned = nullptr;  // pinned host staging (4 KB)
+};
+
+struct sait_mat_s {
+    int64_t n = 0, nnz = 0;
+    int32_t *rp = nullptr;
+    int32_t *ci = nullptr;
+    double *va = nullptr;           // FP64 values (always present)
+    float *va32 = nullptr;          // FP32 copy (on demand)
+    __nv_bfloat16 *va16 = nullptr;  // BF16 copy (on demand)
+    sait_dtype store = SAIT_F64;
+    int device = 0;
+    int lanes = 8;                  // lanes per row for CSR products
+};
+
+struct LevelSchedule {
+    int32_t nlev = 0;
+    int32_t *rows = nullptr;            // device: rows ordered by level
+    std::vector<int32_t> ptr;           // host: level l is rows[ptr[l] .. ptr[l+1])
+    int32_t max_width = 0;
+};
+
+struct sait_prec_s {
+    int kind = 0;  // 1 SAIT pair, 2 exact ILU
+    sait_mat lo = nullptr, up = nullptr;
+    LevelSchedule lev_lo, lev_up;
+    double *tmp = nullptr;      // n-vector scratch
+    int64_t n = 0;
+    int device = 0;
+    // CUDA graph of the level-scheduled substitution (input/output buffers fixed)
+    cudaGraphExec_t graph = nullptr;
+    double *gin = nullptr, *gout = nullptr;
+};
+
+// ---- error helpers ---------------------------------------------------------
+sait_status ctx_fail(sait_ctx ctx, sait_status st, const std::string &msg);
+sait_status ctx_cuda(sait_ctx ctx, cudaError_t e, const char *what, const char *file, int line);
+
+#define SAIT_CK(call)                                                         \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) return ctx_cuda(ctx, e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define SAIT_TRY(expr)                          \
+    do {                                        \
+        sait_status s_ = (expr);                \
+        if (s_ != SAIT_OK) return s_;           \
+    } while (0)
+
+// Stream-ordered device temporary, freed on scope exit (on the same stream).
+template <class T>
+struct DTemp {
+    T *p = nullptr;
+    cudaStream_t s = nullptr;
+    DTemp() = default;
+    DTemp(const DTemp &) = delete;
+    DTemp &operator=(const DTemp &) = delete;
+    ~DTemp() { release(); }
+    cudaError_t alloc(size_t count, cudaStream_t st) {
+        release();
+        s = st;
+        return cudaMallocAsync((void **)&p, (count ? count : 1) * sizeof(T), st);
+    }
+    void release() {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+    }
+    T *take() {
+        T *q = p;
+        p = nullptr;
+        return q;
+    }
+};
+
+static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ---- internal launchers (one translation unit each) -------------------------
+// scan.cu: out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.
+cudaError_t scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
+cudaError_t scan_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
+
+// spmv.cu
+int choose_lanes(int64_t n, int64_t nnz);
+// y = A x for the value storage of A; x/y element types given by flags.
+cudaError_t launch_spmv(const sait_mat_s *A, sait_dtype store, const void *x, bool x_f32, void *y,
+                        bool y_f32, const int *active, cudaStream_t s);
+cudaError_t cast_values(const double *src, float *d32, __nv_bfloat16 *d16, int64_t nnz,
+                        cudaStream_t s);
+
+// levels.cu
+sait_status build_levels(sait_ctx ctx, const int32_t *rp, const int32_t *ci, int64_t n, bool lower,
+                         LevelSchedule *out);
+void free_levels(LevelSchedule *L);
+cudaError_t launch_trisolve(const sait_mat_s *T, const LevelSchedule &lev, bool lower,
+                            const double *b, double *x, cudaStream_t s);
+sait_status ilu0_levels(sait_ctx ctx, const int32_t *rp, const int32_t *ci, double *lu, int64_t n,
+                        const LevelSchedule &lev);
+
+// mat helpers (api.cu)
+sait_status mat_alloc(sait_ctx ctx, int64_t n, int64_t nnz, sait_mat *out);
+sait_status mat_prepare_store(sait_ctx ctx, sait_mat M, sait_dtype store);
+sait_status prec_apply_impl(sait_ctx ctx, sait_prec P, const double *r, double *z,
+                            const int *active);

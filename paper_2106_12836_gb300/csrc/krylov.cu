@@ -1,0 +1,595 @@
+// Krylov solvers with a SAIT (or exact-ILU) preconditioner, all state on the
+// device.  The SAIT apply z = M_U (M_L r) is the preconditioning step of every
+// iteration (Section 3.1); the runtime model of the paper (equation runtime)
+// splits an iteration into that apply and the "other computation", which here
+// is one FP64 product with A and the orthogonalisation / vector updates.
+//
+// Every kernel of an iteration reads a device flag `active` and returns at
+// once when it is 0, so the host can enqueue several iterations ahead and
+// read the status word only every kPoll iterations.
+#include <algorithm>
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPoll = 8;       // iterations enqueued between status reads
+constexpr int kMaxRestart = 512;
+constexpr int kChunk = 64;     // vectors per pass of the multi-dot kernel
+
+struct Scal {        // device-resident solver scalars
+    int active;      // 1 while the current cycle / iteration runs
+    int jdone;       // GMRES: Arnoldi steps done in this cycle; BiCGSTAB: iterations done
+    int state;       // 0 running, 1 converged, 2 breakdown, 3 non-finite, 4 x updated (half step)
+    int pad;
+    double bnorm, beta, tolb, inv;
+    double rho, rho_old, alpha, omega, beta_b;
+    double r0, r1, r2, r3;    // reduction results
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double ws[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) ws[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kThreads / 32; w++) r += ws[w];
+    __syncthreads();
+    return r;  // valid in thread 0
+}
+
+// partial[b*3 + q] = sum over this block's rows of x_q * y_q, q < nd (nd <= 3)
+__global__ void __launch_bounds__(kThreads)
+k_dots(int64_t n, int nd, const double *__restrict__ x0, const double *__restrict__ y0,
+       const double *__restrict__ x1, const double *__restrict__ y1, const double *__restrict__ x2,
+       const double *__restrict__ y2, double *partial, const int *active) {
+    if (active && *active == 0) return;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        s0 = fma(x0[i], y0[i], s0);
+        if (nd > 1) s1 = fma(x1[i], y1[i], s1);
+        if (nd > 2) s2 = fma(x2[i], y2[i], s2);
+    }
+    double t0 = block_sum(s0);
+    double t1 = nd > 1 ? block_sum(s1) : 0.0;
+    double t2 = nd > 2 ? block_sum(s2) : 0.0;
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x * 3 + 0] = t0;
+        partial[blockIdx.x * 3 + 1] = t1;
+        partial[blockIdx.x * 3 + 2] = t2;
+    }
+}
+
+// out[q] = sum_b partial[b*stride + q]   (one block per q, fixed order)
+__global__ void __launch_bounds__(kThreads)
+k_reduce(const double *__restrict__ partial, int nb, int stride, double *out, const int *active) {
+    if (active && *active == 0) return;
+    const int q = blockIdx.x;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += kThreads) s += partial[(int64_t)b * stride + q];
+    s = block_sum(s);
+    if (threadIdx.x == 0) out[q] = s;
+}
+
+// Multi-dot h_q = V_q . w for q < nvec (nvec read from the device when
+// nvec_dev != null).  Warps split the vectors, lanes split the rows; each
+// block leaves partial[b*ldp + q].
+__global__ void __launch_bounds__(kThreads)
+k_mdot(int64_t n, const double *__restrict__ V, int64_t ldv, int nvec, const double *__restrict__ w,
+       double *partial, int ldp, const int *active) {
+    if (active && *active == 0) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c0 = 0; c0 < nvec; c0 += kChunk) {
+        double acc[kChunk / 8];
+#pragma unroll
+        for (int t = 0; t < kChunk / 8; t++) acc[t] = 0.0;
+        for (int64_t r = (int64_t)blockIdx.x * 32 + lane; r < n; r += (int64_t)gridDim.x * 32) {
+            const double wv = w[r];
+#pragma unroll
+            for (int t = 0; t < kChunk / 8; t++) {
+                const int q = c0 + warp + 8 * t;
+                if (q < nvec) acc[t] = fma(V[(int64_t)q * ldv + r], wv, acc[t]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kChunk / 8; t++) {
+            const int q = c0 + warp + 8 * t;
+            const double s = warp_sum(acc[t]);
+            if (lane == 0 && q < nvec) partial[(int64_t)blockIdx.x * ldp + q] = s;
+        }
+    }
+}
+
+// w -= V h (sub = true) or w = V h (sub = false); nvec from *nvec_dev if given.
+__global__ void __launch_bounds__(kThreads)
+k_gemv(int64_t n, const double *__restrict__ V, int64_t ldv, int nvec, const int *nvec_dev,
+       const double *__restrict__ h, double *w, int sub, const int *active) {
+    if (active && *active == 0) return;
+    __shared__ double hs[kMaxRestart + 1];
+    const int nv = nvec_dev ? *nvec_dev : nvec;
+    for (int q = threadIdx.x; q < nv; q += kThreads) hs[q] = h[q];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        double s = 0.0;
+        for (int q = 0; q < nv; q++) s = fma(V[(int64_t)q * ldv + i], hs[q], s);
+        w[i] = sub ? w[i] - s : s;
+    }
+}
+
+// r = b - A x, FP64, G lanes per row
+template <int G>
+__global__ void __launch_bounds__(kThreads)
+k_residual(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+           const double *__restrict__ va, const double *__restrict__ x, const double *__restrict__ b,
+           double *__restrict__ r) {
+    const int64_t row = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / G;
+    const int lane = threadIdx.x & (G - 1);
+    double s = 0.0;
+    if (row < n)
+        for (int k = rp[row] + lane; k < rp[row + 1]; k += G) s = fma(va[k], x[ci[k]], s);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (row < n && lane == 0) r[row] = b[row] - s;
+}
+
+// y = x * sc->inv
+__global__ void k_scale(int64_t n, const double *__restrict__ x, double *y, const Scal *sc, const int *active) {
+    if (active && *active == 0) return;
+    const double a = sc->inv;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+        y[i] = x[i] * a;
+}
+
+__global__ void k_axpy1(int64_t n, const double *__restrict__ x, double *y) {
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+        y[i] += x[i];
+}
+
+// ---- GMRES scalar kernels (one thread) -------------------------------------
+__global__ void k_gmres_start(Scal *sc, double *g, int m) {
+    const double beta = sqrt(sc->r0);
+    sc->beta = beta;
+    sc->inv = beta > 0.0 ? 1.0 / beta : 0.0;
+    sc->active = 1;
+    sc->jdone = 0;
+    sc->state = 0;
+    g[0] = beta;
+    for (int i = 1; i <= m; i++) g[i] = 0.0;
+}
+
+// add the CGS coefficients of one pass into column j of H
+__global__ void k_hadd(double *Hj, const double *h, int nv, int first, const int *active) {
+    if (*active == 0) return;
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) Hj[q] = first ? h[q] : Hj[q] + h[q];
+}
+
+__global__ void k_givens(int j, int m, int remaining, double *H, double *cs, double *sn, double *g, Scal *sc) {
+    if (sc->active == 0) return;
+    double *Hj = H + (int64_t)j * (m + 1);
+    const double hn = sqrt(sc->r0);
+    Hj[j + 1] = hn;
+    for (int i = 0; i < j; i++) {
+        const double t = cs[i] * Hj[i] + sn[i] * Hj[i + 1];
+        Hj[i + 1] = -sn[i] * Hj[i] + cs[i] * Hj[i + 1];
+        Hj[i] = t;
+    }
+    const double a = Hj[j], b = hn;
+    double c = 1.0, s = 0.0;
+    if (b != 0.0) {
+        const double t = hypot(a, b);
+        c = a / t;
+        s = b / t;
+    }
+    cs[j] = c;
+    sn[j] = s;
+    Hj[j] = c * a + s * b;
+    Hj[j + 1] = 0.0;
+    g[j + 1] = -s * g[j];
+    g[j] = c * g[j];
+    sc->jdone = j + 1;
+    sc->inv = hn != 0.0 ? 1.0 / hn : 0.0;
+    const double est = fabs(g[j + 1]);
+    if (!isfinite(est) || !isfinite(hn)) {
+        sc->state = 3;
+        sc->active = 0;
+    } else if (est <= sc->tolb || hn == 0.0 || j + 1 >= remaining || j + 1 >= m) {
+        sc->active = 0;
+    }
+}
+
+// back substitution H y = g on the first jdone rows
+__global__ void k_hsolve(const double *H, const double *g, double *y, int m, Scal *sc) {
+    const int jd = sc->jdone;
+    for (int i = jd - 1; i >= 0; i--) {
+        double s = g[i];
+        for (int k = i + 1; k < jd; k++) s -= H[(int64_t)k * (m + 1) + i] * y[k];
+        const double d = H[(int64_t)i * (m + 1) + i];
+        if (d == 0.0) { sc->state = 2; y[i] = 0.0; continue; }
+        y[i] = s / d;
+    }
+}
+
+// ---- BiCGSTAB kernels ---------------------------------------------------------
+__global__ void k_bicg_init(Scal *sc) {
+    sc->rho_old = sc->alpha = sc->omega = 1.0;
+    sc->active = 1;
+    sc->state = 0;
+}
+
+__global__ void k_bicg_beta(Scal *sc) {  // after rho = (rh, r) in r0
+    if (sc->active == 0) return;
+    const double rho = sc->r0;
+    sc->rho = rho;
+    if (rho == 0.0 || sc->omega == 0.0 || !isfinite(rho)) {
+        sc->state = !isfinite(rho) ? 3 : 2;
+        sc->active = 0;
+        return;
+    }
+    sc->beta_b = (rho / sc->rho_old) * (sc->alpha / sc->omega);
+}
+
+__global__ void k_bicg_p(int64_t n, const double *__restrict__ r, const double *__restrict__ v, double *p,
+                         const Scal *sc) {
+    if (sc->active == 0) return;
+    const double beta = sc->beta_b, omega = sc->omega;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+        p[i] = r[i] + beta * (p[i] - omega * v[i]);
+}
+
+__global__ void k_bicg_alpha(Scal *sc) {  // after (rh, v) in r0
+    if (sc->active == 0) return;
+    const double rv = sc->r0;
+    if (rv == 0.0 || !isfinite(rv)) {
+        sc->state = !isfinite(rv) ? 3 : 2;
+        sc->active = 0;
+        return;
+    }
+    sc->alpha = sc->rho / rv;
+}
+
+// s = r - alpha v
+__global__ void k_bicg_s(int64_t n, const double *__restrict__ r, const double *__restrict__ v, double *s,
+                         const Scal *sc) {
+    if (sc->active == 0) return;
+    const double alpha = sc->alpha;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+        s[i] = r[i] - alpha * v[i];
+}
+
+__global__ void k_bicg_check_s(Scal *sc) {  // after (s, s) in r0
+    if (sc->active == 0) return;
+    sc->jdone += 1;
+    const double sn = sqrt(sc->r0);
+    if (!isfinite(sn)) { sc->state = 3; sc->active = 0; return; }
+    if (sn <= sc->tolb) { sc->state = 4; sc->active = 0; }
+}
+
+// half step converged: x += alpha ph (runs once, when state == 4)
+__global__ void k_bicg_xhalf(int64_t n, double *x, const double *__restrict__ ph, Scal *sc) {
+    if (sc->state != 4) return;
+    const double alpha = sc->alpha;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+        x[i] += alpha * ph[i];
+}
+
+__global__ void k_bicg_xhalf_done(Scal *sc) {
+    if (sc->state == 4) sc->state = 1;
+}
+
+__global__ void k_bicg_omega(Scal *sc) {  // after (t,t) in r0, (t,s) in r1
+    if (sc->active == 0) return;
+    const double tt = sc->r0;
+    sc->omega = tt == 0.0 ? 0.0 : sc->r1 / tt;
+}
+
+// x += alpha ph + omega sh;  r = s - omega t
+__global__ void k_bicg_xr(int64_t n, double *x, double *r, const double *__restrict__ ph,
+                          const double *__restrict__ sh, const double *__restrict__ s,
+                          const double *__restrict__ t, const Scal *sc) {
+    if (sc->active == 0) return;
+    const double alpha = sc->alpha, omega = sc->omega;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        x[i] += alpha * ph[i] + omega * sh[i];
+        r[i] = s[i] - omega * t[i];
+    }
+}
+
+__global__ void k_bicg_check_r(Scal *sc, int remaining) {  // after (r, r) in r0
+    if (sc->active == 0) return;
+    sc->rho_old = sc->rho;
+    const double rn = sqrt(sc->r0);
+    if (!isfinite(rn)) { sc->state = 3; sc->active = 0; return; }
+    if (rn <= sc->tolb) { sc->state = 1; sc->active = 0; return; }
+    if (sc->jdone >= remaining) sc->active = 0;
+}
+
+// ---- host helpers ---------------------------------------------------------------
+struct Work {
+    int nb = 1;
+    double *partial = nullptr;
+};
+
+cudaError_t dots(sait_ctx ctx, const Work &W, int64_t n, int nd, const double *x0, const double *y0,
+                 const double *x1, const double *y1, const double *x2, const double *y2, double *out,
+                 const int *active) {
+    k_dots<<<W.nb, kThreads, 0, ctx->stream>>>(n, nd, x0, y0, x1, y1, x2, y2, W.partial, active);
+    k_reduce<<<nd, kThreads, 0, ctx->stream>>>(W.partial, W.nb, 3, out, active);
+    return cudaGetLastError();
+}
+
+cudaError_t residual(sait_ctx ctx, sait_mat A, const double *x, const double *b, double *r) {
+    const int G = A->lanes;
+    const unsigned grid = (unsigned)cdiv(A->n * G, kThreads);
+    cudaStream_t s = ctx->stream;
+    if (A->n == 0) return cudaSuccess;
+    switch (G) {
+        case 2: k_residual<2><<<grid, kThreads, 0, s>>>(A->n, A->rp, A->ci, A->va, x, b, r); break;
+        case 4: k_residual<4><<<grid, kThreads, 0, s>>>(A->n, A->rp, A->ci, A->va, x, b, r); break;
+        case 8: k_residual<8><<<grid, kThreads, 0, s>>>(A->n, A->rp, A->ci, A->va, x, b, r); break;
+        case 16: k_residual<16><<<grid, kThreads, 0, s>>>(A->n, A->rp, A->ci, A->va, x, b, r); break;
+        default: k_residual<32><<<grid, kThreads, 0, s>>>(A->n, A->rp, A->ci, A->va, x, b, r); break;
+    }
+    return cudaGetLastError();
+}
+
+sait_status read_scal(sait_ctx ctx, const Scal *d, Scal *h) {
+    SAIT_CK(cudaMemcpyAsync(ctx->h_pinned, d, sizeof(Scal), cudaMemcpyDeviceToHost, ctx->stream));
+    SAIT_CK(cudaStreamSynchronize(ctx->stream));
+    *h = *(const Scal *)ctx->h_pinned;
+    return SAIT_OK;
+}
+
+// preconditioned vector z = P v (copy when P is null); `active` gates the kernels
+sait_status precondition(sait_ctx ctx, sait_prec P, const double *v, double *z, int64_t n, const int *active) {
+    if (P) return prec_apply_impl(ctx, P, v, z, active);
+    SAIT_CK(cudaMemcpyAsync(z, v, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    return SAIT_OK;
+}
+
+sait_status check_solver_args(sait_ctx ctx, sait_mat A, sait_prec P, const double *b, double *x,
+                              double tol, int32_t maxit, const char *who) {
+    if (!A || (A->n > 0 && (!b || !x)) || !(tol >= 0.0) || maxit < 0)
+        return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, std::string(who) + ": bad argument");
+    if (P && P->n != A->n) return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, std::string(who) + ": size mismatch");
+    return SAIT_OK;
+}
+
+}  // namespace
+
+extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const double *b, double *x,
+                                  int32_t restart, double tol, int32_t maxit, sait_info *info) {
+    if (!ctx) return SAIT_ERR_INVALID_ARG;
+    SAIT_TRY(check_solver_args(ctx, A, P, b, x, tol, maxit, "sait_gmres"));
+    if (restart < 1 || restart > kMaxRestart)
+        return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_gmres: restart must lie in [1, 512]");
+    const int64_t n = A->n;
+    const int m = restart;
+    cudaStream_t s = ctx->stream;
+    sait_info inf{0, 0, 0.0};
+    if (info) *info = inf;
+    if (n == 0) return SAIT_OK;
+
+    Work W;
+    W.nb = (int)std::min<int64_t>(cdiv(n, kThreads), 2LL * ctx->num_sms);
+    const int ldp = m + 1;
+    DTemp<double> V, H, cs, sn, g, y, z, u, part;
+    DTemp<Scal> scd;
+    SAIT_CK(V.alloc((size_t)(m + 1) * n, s));
+    SAIT_CK(H.alloc((size_t)(m + 1) * m, s));
+    SAIT_CK(cs.alloc(m, s));
+    SAIT_CK(sn.alloc(m, s));
+    SAIT_CK(g.alloc(m + 1, s));
+    SAIT_CK(y.alloc(m + 1, s));
+    SAIT_CK(z.alloc(n, s));
+    SAIT_CK(u.alloc(n, s));
+    SAIT_CK(part.alloc((size_t)W.nb * std::max(ldp, 3), s));
+    SAIT_CK(scd.alloc(1, s));
+    SAIT_CK(cudaMemsetAsync(scd.p, 0, sizeof(Scal), s));
+    W.partial = part.p;
+    Scal *sc = scd.p;
+    const int *act = &sc->active;
+    double *r0 = &sc->r0;
+
+    // ||b||
+    SAIT_CK(dots(ctx, W, n, 1, b, b, nullptr, nullptr, nullptr, nullptr, r0, nullptr));
+    Scal hs;
+    SAIT_TRY(read_scal(ctx, sc, &hs));
+    const double bnorm = sqrt(hs.r0);
+    if (!std::isfinite(bnorm)) return ctx_fail(ctx, SAIT_ERR_NONFINITE, "sait_gmres: non-finite b");
+    if (bnorm == 0.0) {
+        SAIT_CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+        SAIT_CK(cudaStreamSynchronize(s));
+        return SAIT_OK;
+    }
+    const double tolb = tol * bnorm;
+    {
+        Scal init{};
+        init.bnorm = bnorm;
+        init.tolb = tolb;
+        SAIT_CK(cudaMemcpyAsync(&sc->bnorm, &init.bnorm, sizeof(double), cudaMemcpyHostToDevice, s));
+        SAIT_CK(cudaMemcpyAsync(&sc->tolb, &init.tolb, sizeof(double), cudaMemcpyHostToDevice, s));
+        SAIT_CK(cudaStreamSynchronize(s));
+    }
+    const unsigned egrid = (unsigned)std::min<int64_t>(cdiv(n, kThreads), 8LL * ctx->num_sms);
+    int iters = 0, cycles = 0;
+    sait_status result = SAIT_ERR_NOT_CONVERGED;
+    for (;;) {
+        // r = b - A x  -> V_0, beta = ||r||
+        SAIT_CK(residual(ctx, A, x, b, V.p));
+        SAIT_CK(dots(ctx, W, n, 1, V.p, V.p, nullptr, nullptr, nullptr, nullptr, r0, nullptr));
+        k_gmres_start<<<1, 1, 0, s>>>(sc, g.p, m);
+        SAIT_CK(cudaGetLastError());
+        SAIT_TRY(read_scal(ctx, sc, &hs));
+        inf.rel_resid = hs.beta / bnorm;
+        if (!std::isfinite(hs.beta)) { result = SAIT_ERR_NONFINITE; break; }
+        if (inf.rel_resid <= tol) { result = SAIT_OK; break; }
+        if (iters >= maxit) break;
+        k_scale<<<egrid, kThreads, 0, s>>>(n, V.p, V.p, sc, nullptr);
+        const int remaining = maxit - iters;
+        for (int j = 0; j < m; j++) {
+            double *vj = V.p + (size_t)j * n, *w = V.p + (size_t)(j + 1) * n;
+            SAIT_TRY(precondition(ctx, P, vj, z.p, n, act));
+            SAIT_CK(launch_spmv(A, SAIT_F64, z.p, false, w, false, act, s));
+            double *Hj = H.p + (size_t)j * (m + 1);
+            for (int pass = 0; pass < 2; pass++) {  // classical Gram-Schmidt, twice
+                k_mdot<<<W.nb, kThreads, 0, s>>>(n, V.p, n, j + 1, w, W.partial, ldp, act);
+                k_reduce<<<j + 1, kThreads, 0, s>>>(W.partial, W.nb, ldp, y.p, act);
+                k_hadd<<<1, 128, 0, s>>>(Hj, y.p, j + 1, pass == 0, act);
+                k_gemv<<<egrid, kThreads, 0, s>>>(n, V.p, n, j + 1, nullptr, y.p, w, 1, act);
+            }
+            SAIT_CK(dots(ctx, W, n, 1, w, w, nullptr, nullptr, nullptr, nullptr, r0, act));
+            k_givens<<<1, 1, 0, s>>>(j, m, remaining, H.p, cs.p, sn.p, g.p, sc);
+            k_scale<<<egrid, kThreads, 0, s>>>(n, w, w, sc, act);
+            SAIT_CK(cudaGetLastError());
+            if ((j + 1) % kPoll == 0 || j + 1 == m) {
+                SAIT_TRY(read_scal(ctx, sc, &hs));
+                if (!hs.active) break;
+            }
+        }
+        SAIT_TRY(read_scal(ctx, sc, &hs));
+        iters += hs.jdone;
+        cycles++;
+        if (hs.state == 3) { result = SAIT_ERR_NONFINITE; break; }
+        k_hsolve<<<1, 1, 0, s>>>(H.p, g.p, y.p, m, sc);
+        k_gemv<<<egrid, kThreads, 0, s>>>(n, V.p, n, 0, &sc->jdone, y.p, u.p, 0, nullptr);
+        SAIT_CK(cudaGetLastError());
+        SAIT_TRY(precondition(ctx, P, u.p, z.p, n, nullptr));
+        k_axpy1<<<egrid, kThreads, 0, s>>>(n, z.p, x);
+        SAIT_CK(cudaGetLastError());
+        SAIT_TRY(read_scal(ctx, sc, &hs));
+        if (hs.state == 2) { result = SAIT_ERR_BREAKDOWN; break; }
+    }
+    if (result == SAIT_ERR_NOT_CONVERGED || result == SAIT_ERR_BREAKDOWN) {
+        SAIT_CK(residual(ctx, A, x, b, z.p));
+        SAIT_CK(dots(ctx, W, n, 1, z.p, z.p, nullptr, nullptr, nullptr, nullptr, r0, nullptr));
+        SAIT_TRY(read_scal(ctx, sc, &hs));
+        inf.rel_resid = sqrt(hs.r0) / bnorm;
+    }
+    inf.iters = iters;
+    inf.cycles = cycles;
+    if (info) *info = inf;
+    SAIT_CK(cudaStreamSynchronize(s));
+    if (result != SAIT_OK) {
+        char buf[160];
+        snprintf(buf, sizeof(buf), "sait_gmres: %s after %d steps, relres %.3e", sait_status_string(result),
+                 iters, inf.rel_resid);
+        return ctx_fail(ctx, result, buf);
+    }
+    return SAIT_OK;
+}
+
+extern "C" sait_status sait_bicgstab(sait_ctx ctx, sait_mat A, sait_prec P, const double *b, double *x,
+                                     double tol, int32_t maxit, sait_info *info) {
+    if (!ctx) return SAIT_ERR_INVALID_ARG;
+    SAIT_TRY(check_solver_args(ctx, A, P, b, x, tol, maxit, "sait_bicgstab"));
+    const int64_t n = A->n;
+    cudaStream_t s = ctx->stream;
+    sait_info inf{0, 0, 0.0};
+    if (info) *info = inf;
+    if (n == 0) return SAIT_OK;
+    Work W;
+    W.nb = (int)std::min<int64_t>(cdiv(n, kThreads), 2LL * ctx->num_sms);
+    DTemp<double> r, rh, p, v, ph, sv, sh, t, part;
+    DTemp<Scal> scd;
+    for (DTemp<double> *d : {&r, &rh, &p, &v, &ph, &sv, &sh, &t}) SAIT_CK(d->alloc(n, s));
+    SAIT_CK(part.alloc((size_t)W.nb * 3, s));
+    SAIT_CK(scd.alloc(1, s));
+    SAIT_CK(cudaMemsetAsync(scd.p, 0, sizeof(Scal), s));
+    W.partial = part.p;
+    Scal *sc = scd.p;
+    const int *act = &sc->active;
+    double *r0 = &sc->r0;
+    const unsigned egrid = (unsigned)std::min<int64_t>(cdiv(n, kThreads), 8LL * ctx->num_sms);
+
+    SAIT_CK(dots(ctx, W, n, 1, b, b, nullptr, nullptr, nullptr, nullptr, r0, nullptr));
+    Scal hs;
+    SAIT_TRY(read_scal(ctx, sc, &hs));
+    const double bnorm = sqrt(hs.r0);
+    if (!std::isfinite(bnorm)) return ctx_fail(ctx, SAIT_ERR_NONFINITE, "sait_bicgstab: non-finite b");
+    if (bnorm == 0.0) {
+        SAIT_CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+        SAIT_CK(cudaStreamSynchronize(s));
+        return SAIT_OK;
+    }
+    {
+        double tb = tol * bnorm;
+        SAIT_CK(cudaMemcpyAsync(&sc->tolb, &tb, sizeof(double), cudaMemcpyHostToDevice, s));
+        SAIT_CK(cudaMemcpyAsync(&sc->bnorm, &bnorm, sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    int iters = 0, cycles = 0;
+    sait_status result = SAIT_ERR_NOT_CONVERGED;
+    for (;;) {
+        // (re)start: r = b - A x, rh = r
+        SAIT_CK(residual(ctx, A, x, b, r.p));
+        SAIT_CK(dots(ctx, W, n, 1, r.p, r.p, nullptr, nullptr, nullptr, nullptr, r0, nullptr));
+        SAIT_TRY(read_scal(ctx, sc, &hs));
+        inf.rel_resid = sqrt(hs.r0) / bnorm;
+        if (!std::isfinite(inf.rel_resid)) { result = SAIT_ERR_NONFINITE; break; }
+        if (inf.rel_resid <= tol) { result = SAIT_OK; break; }
+        if (iters >= maxit) break;
+        if (cycles > 0 && hs.state == 2) { result = SAIT_ERR_BREAKDOWN; break; }
+        SAIT_CK(cudaMemcpyAsync(rh.p, r.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        SAIT_CK(cudaMemsetAsync(p.p, 0, n * sizeof(double), s));
+        SAIT_CK(cudaMemsetAsync(v.p, 0, n * sizeof(double), s));
+        SAIT_CK(cudaMemsetAsync(&sc->jdone, 0, sizeof(int), s));
+        k_bicg_init<<<1, 1, 0, s>>>(sc);
+        const int remaining = maxit - iters;
+        for (int it = 0; it < remaining; it++) {
+            SAIT_CK(dots(ctx, W, n, 1, rh.p, r.p, nullptr, nullptr, nullptr, nullptr, r0, act));
+            k_bicg_beta<<<1, 1, 0, s>>>(sc);
+            k_bicg_p<<<egrid, kThreads, 0, s>>>(n, r.p, v.p, p.p, sc);
+            SAIT_TRY(precondition(ctx, P, p.p, ph.p, n, act));
+            SAIT_CK(launch_spmv(A, SAIT_F64, ph.p, false, v.p, false, act, s));
+            SAIT_CK(dots(ctx, W, n, 1, rh.p, v.p, nullptr, nullptr, nullptr, nullptr, r0, act));
+            k_bicg_alpha<<<1, 1, 0, s>>>(sc);
+            k_bicg_s<<<egrid, kThreads, 0, s>>>(n, r.p, v.p, sv.p, sc);
+            SAIT_CK(dots(ctx, W, n, 1, sv.p, sv.p, nullptr, nullptr, nullptr, nullptr, r0, act));
+            k_bicg_check_s<<<1, 1, 0, s>>>(sc);
+            k_bicg_xhalf<<<egrid, kThreads, 0, s>>>(n, x, ph.p, sc);
+            k_bicg_xhalf_done<<<1, 1, 0, s>>>(sc);
+            SAIT_TRY(precondition(ctx, P, sv.p, sh.p, n, act));
+            SAIT_CK(launch_spmv(A, SAIT_F64, sh.p, false, t.p, false, act, s));
+            SAIT_CK(dots(ctx, W, n, 2, t.p, t.p, t.p, sv.p, nullptr, nullptr, r0, act));
+            k_bicg_omega<<<1, 1, 0, s>>>(sc);
+            k_bicg_xr<<<egrid, kThreads, 0, s>>>(n, x, r.p, ph.p, sh.p, sv.p, t.p, sc);
+            SAIT_CK(dots(ctx, W, n, 1, r.p, r.p, nullptr, nullptr, nullptr, nullptr, r0, act));
+            k_bicg_check_r<<<1, 1, 0, s>>>(sc, remaining);
+            SAIT_CK(cudaGetLastError());
+            if ((it + 1) % kPoll == 0 || it + 1 == remaining) {
+                SAIT_TRY(read_scal(ctx, sc, &hs));
+                if (!hs.active) break;
+            }
+        }
+        SAIT_TRY(read_scal(ctx, sc, &hs));
+        iters += hs.jdone;
+        cycles++;
+        if (hs.state == 3) { result = SAIT_ERR_NONFINITE; break; }
+    }
+    if (result != SAIT_OK) {
+        SAIT_CK(residual(ctx, A, x, b, r.p));
+        SAIT_CK(dots(ctx, W, n, 1, r.p, r.p, nullptr, nullptr, nullptr, nullptr, r0, nullptr));
+        SAIT_TRY(read_scal(ctx, sc, &hs));
+        inf.rel_resid = sqrt(hs.r0) / bnorm;
+    }
+    inf.iters = iters;
+    inf.cycles = cycles;
+    if (info) *info = inf;
+    SAIT_CK(cudaStreamSynchronize(s));
+    if (result != SAIT_OK) {
+        char buf[160];
+        snprintf(buf, sizeof(buf), "sait_bicgstab: %s after %d iterations, relres %.3e",
+                 sait_status_string(result), iters, inf.rel_resid);
+        return ctx_fail(ctx, result, buf);
+    }
+    return SAIT_OK;
+}

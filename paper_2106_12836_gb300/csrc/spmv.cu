@@ -1,0 +1,107 @@
+// CSR sparse matrix-vector products y = A x.
+//
+// G consecutive lanes of a warp own one row and stride over its entries, so a
+// warp reads 32 consecutive (column, value) pairs per step when rows are at
+// least G long; partial sums are combined with warp shuffles.  The value type
+// is the matrix's storage precision: FP64 values accumulate in FP64, FP32 and
+// BF16 values in FP32 (the SAIT matrices approximate T^-1 anyway, so their
+// product precision can be reduced; Section 3.1).
+#include "internal.cuh"
+
+namespace {
+
+template <typename T> struct Acc;
+template <> struct Acc<double> { using type = double; };
+template <> struct Acc<float> { using type = float; };
+template <> struct Acc<__nv_bfloat16> { using type = float; };
+
+__device__ __forceinline__ double ld(const double *p) { return __ldg(p); }
+__device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+
+__device__ __forceinline__ double fmac(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmac(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <int G, typename TV, typename TX, typename TY>
+__global__ void __launch_bounds__(256)
+k_spmv_csr(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+           const TV *__restrict__ va, const TX *__restrict__ x, TY *__restrict__ y,
+           const int *__restrict__ active) {
+    using A = typename Acc<TV>::type;
+    if (active && *active == 0) return;  // uniform over the grid
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = gid / G;
+    const int lane = threadIdx.x & (G - 1);
+    A s = 0;
+    if (row < n) {
+        const int b = rp[row], e = rp[row + 1];
+        for (int k = b + lane; k < e; k += G) s = fmac(ld(va + k), (A)__ldg(x + ci[k]), s);
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (row < n && lane == 0) y[row] = (TY)s;
+}
+
+template <typename TV, typename TX, typename TY>
+cudaError_t launch_g(int G, int64_t n, const int32_t *rp, const int32_t *ci, const TV *va,
+                     const TX *x, TY *y, const int *active, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)cdiv(n * G, threads);
+    switch (G) {
+        case 2: k_spmv_csr<2><<<blocks, threads, 0, s>>>(n, rp, ci, va, x, y, active); break;
+        case 4: k_spmv_csr<4><<<blocks, threads, 0, s>>>(n, rp, ci, va, x, y, active); break;
+        case 8: k_spmv_csr<8><<<blocks, threads, 0, s>>>(n, rp, ci, va, x, y, active); break;
+        case 16: k_spmv_csr<16><<<blocks, threads, 0, s>>>(n, rp, ci, va, x, y, active); break;
+        default: k_spmv_csr<32><<<blocks, threads, 0, s>>>(n, rp, ci, va, x, y, active); break;
+    }
+    return cudaGetLastError();
+}
+
+template <typename TV>
+cudaError_t launch_xy(const sait_mat_s *A, const TV *va, const void *x, bool x_f32, void *y,
+                      bool y_f32, const int *active, cudaStream_t s) {
+    const int G = A->lanes;
+    if (x_f32) {
+        if (y_f32)
+            return launch_g(G, A->n, A->rp, A->ci, va, (const float *)x, (float *)y, active, s);
+        return launch_g(G, A->n, A->rp, A->ci, va, (const float *)x, (double *)y, active, s);
+    }
+    if (y_f32) return launch_g(G, A->n, A->rp, A->ci, va, (const double *)x, (float *)y, active, s);
+    return launch_g(G, A->n, A->rp, A->ci, va, (const double *)x, (double *)y, active, s);
+}
+
+__global__ void k_cast(const double *__restrict__ src, float *d32, __nv_bfloat16 *d16, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double v = src[i];
+        if (d32) d32[i] = (float)v;
+        if (d16) d16[i] = __double2bfloat16(v);
+    }
+}
+
+}  // namespace
+
+int choose_lanes(int64_t n, int64_t nnz) {
+    double avg = n > 0 ? (double)nnz / (double)n : 1.0;
+    int G = 2;
+    while (G < 32 && G * 2 <= avg) G *= 2;
+    return G;
+}
+
+cudaError_t launch_spmv(const sait_mat_s *A, sait_dtype store, const void *x, bool x_f32, void *y,
+                        bool y_f32, const int *active, cudaStream_t s) {
+    switch (store) {
+        case SAIT_F32: return launch_xy(A, A->va32, x, x_f32, y, y_f32, active, s);
+        case SAIT_BF16: return launch_xy(A, A->va16, x, x_f32, y, y_f32, active, s);
+        default: return launch_xy(A, A->va, x, x_f32, y, y_f32, active, s);
+    }
+}
+
+cudaError_t cast_values(const double *src, float *d32, __nv_bfloat16 *d16, int64_t nnz,
+                        cudaStream_t s) {
+    if (nnz == 0) return cudaSuccess;
+    unsigned blocks = (unsigned)std::min<int64_t>(cdiv(nnz, 256), 152 * 16);
+    k_cast<<<blocks, 256, 0, s>>>(src, d32, d16, nnz);
+    return cudaGetLastError();
+}

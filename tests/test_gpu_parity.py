@@ -1,0 +1,278 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bars (written out in each test):
+  * ILU(0) values and the SAIT structure: bit-exact (both sides run the same
+    fma chains); SAIT entries whose |(M D)_ij| lies within 1e-12 of the drop
+    threshold are excluded from the structure check.
+  * SAIT values: within 1e-12 relative.
+  * FP64 products: |y - y_ref| <= 1e-12 * (|M| |x|)_i (the usual bound for a
+    reordered sum); FP32 storage 1e-5 and BF16 storage 1e-2 of the same bound.
+  * Solvers: the GPU iterate's true residual, recomputed by the oracle, is
+    <= tol; iteration counts within 2 of the oracle's (CGS2 vs MGS).
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sg():
+    from paper_2106_12836_gb300 import build
+    build.build()
+    import paper_2106_12836_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(sg):
+    torch.cuda.set_device(0)
+    c = sg.Context()
+    yield c
+    torch.cuda.synchronize()
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def mat(sg, ctx, A):
+    return sg.sait_mat_create_csr(ctx, A.n, dev(A.rp), dev(A.ci), dev(A.va))
+
+
+def host_csr(M):
+    rp, ci, va = (t.cpu().numpy() for t in M.export())
+    return synth.CSR(M.n, rp, ci, va)
+
+
+def assert_sait_parity(G: synth.CSR, O: synth.CSR, T: synth.CSR, drop: str, tau: float):
+    """Structure bit-exact outside the threshold band, values within 1e-12."""
+    assert G.n == O.n
+    d = np.zeros(T.n)
+    rows_t = np.repeat(np.arange(T.n), np.diff(T.rp))
+    diag = T.ci == rows_t
+    d[rows_t[diag]] = T.va[diag]
+    if np.array_equal(G.rp, O.rp) and np.array_equal(G.ci, O.ci):
+        assert np.all(np.abs(G.va - O.va) <= 1e-12 * np.abs(O.va))
+        return
+    # structures differ: every differing entry must sit at the threshold
+    assert drop in ("abs", "rowrel"), "structure mismatch without a threshold rule"
+
+    def entries(M):
+        rows = np.repeat(np.arange(M.n), np.diff(M.rp))
+        return {(int(r), int(c)): v for r, c, v in zip(rows, M.ci, M.va)}
+
+    eg, eo = entries(G), entries(O)
+    rowmax = np.zeros(T.n)
+    for (r, c), v in eo.items():
+        rowmax[r] = max(rowmax[r], abs(v * d[c]))
+    for key in set(eg) ^ set(eo):
+        v = (eg.get(key, eo.get(key))) * d[key[1]]
+        thr = tau * (rowmax[key[0]] if drop == "rowrel" else 1.0)
+        assert abs(abs(v) - thr) <= 1e-12 * thr, ("structure differs away from the threshold", key)
+    for key in set(eg) & set(eo):
+        assert abs(eg[key] - eo[key]) <= 1e-12 * abs(eo[key])
+
+
+# ---- ILU(0) -------------------------------------------------------------------
+@pytest.mark.parametrize("make", [lambda: synth.poisson2d(37), lambda: synth.convdiff3d(17),
+                                  lambda: synth.varcoef3d(13, 1.0, 5), lambda: synth.aniso2d(50, 1e-3)])
+def test_ilu0_bit_exact(sg, ctx, oracle_lib, make):
+    A = make()
+    L, U = sg.sait_ilu0(ctx, A.n, dev(A.rp), dev(A.ci), dev(A.va))
+    Lo, Uo = oracle_lib.ilu0(A)
+    for G, O in ((host_csr(L), Lo), (host_csr(U), Uo)):
+        assert np.array_equal(G.rp, O.rp) and np.array_equal(G.ci, O.ci)
+        assert np.array_equal(G.va, O.va), np.abs(G.va - O.va).max()
+
+
+def test_ilu0_zero_pivot(sg, ctx):
+    A = synth.from_dense(np.array([[1.0, 2.0], [2.0, 4.0]]))   # U_11 = 4 - 2*2 = 0
+    with pytest.raises(sg.SaitError) as e:
+        sg.sait_ilu0(ctx, A.n, dev(A.rp), dev(A.ci), dev(A.va))
+    assert e.value.status == 3
+
+
+# ---- SAIT build -------------------------------------------------------------------
+CASES = [
+    ("rowrel", 1e-3, 0, 3), ("rowrel", 1e-3, 0, 6), ("abs", 0.05, 0, 11), ("abs", 0.01, 0, 5),
+    ("none", 0.0, 0, 4), ("pattern", 0.0, 2, 8), ("pattern", 0.0, 0, 4), ("pattern", 0.0, 3, 3),
+]
+
+
+@pytest.mark.parametrize("drop,tau,p,m", CASES)
+def test_sait_build_pde_factors(sg, ctx, oracle_lib, drop, tau, p, m):
+    A = synth.convdiff3d(19)
+    Lo, Uo = oracle_lib.ilu0(A)
+    for T, lower in ((Lo, True), (Uo, False)):
+        Tg = mat(sg, ctx, T)
+        M = sg.sait_build(ctx, Tg, lower, m, drop, tau, p)
+        O = oracle_lib.sait(T, m, drop, tau, p)
+        assert_sait_parity(host_csr(M), O, T, drop, tau)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+@pytest.mark.parametrize("lower", [True, False])
+@pytest.mark.parametrize("drop,tau,m", [("rowrel", 0.02, 4), ("abs", 0.05, 5), ("none", 0.0, 3)])
+def test_sait_build_random_ragged(sg, ctx, oracle_lib, seed, lower, drop, tau, m):
+    """Empty rows, long rows (the dense overflow kernel) and several tiles of rows."""
+    T = synth.random_triangular(900, lower, seed, max_row=24, empty_frac=0.15, long_frac=0.03,
+                                long_row=300)
+    M = sg.sait_build(ctx, mat(sg, ctx, T), lower, m, drop, tau)
+    O = oracle_lib.sait(T, m, drop, tau)
+    assert_sait_parity(host_csr(M), O, T, drop, tau)
+
+
+@pytest.mark.parametrize("lower", [True, False])
+def test_sait_exact_inverse_long_rows(sg, ctx, oracle_lib, lower):
+    """m_terms = n without dropping: the exact inverse, rows up to n long."""
+    n = 300
+    T = synth.random_triangular(n, lower, 7, max_row=6, long_frac=0.0)
+    M = sg.sait_build(ctx, mat(sg, ctx, T), lower, n, "none")
+    O = oracle_lib.sait(T, n, "none")
+    assert_sait_parity(host_csr(M), O, T, "none", 0.0)
+    Md = host_csr(M).to_dense()
+    assert np.abs(T.to_dense() @ Md - np.eye(n)).max() <= 1e-12
+
+
+def test_sait_degenerate_sizes(sg, ctx, oracle_lib):
+    for n in (1, 2):
+        T = synth.random_triangular(n, True, 3)
+        for m in (1, 2, 5):
+            M = sg.sait_build(ctx, mat(sg, ctx, T), True, m, "rowrel", 1e-3)
+            O = oracle_lib.sait(T, m, "rowrel", 1e-3)
+            assert_sait_parity(host_csr(M), O, T, "rowrel", 1e-3)
+    E = synth.CSR(0, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    M = sg.sait_build(ctx, mat(sg, ctx, E), True, 3, "abs", 0.1)
+    assert M.n == 0 and M.nnz == 0
+
+
+def test_sait_errors(sg, ctx):
+    T = synth.from_dense(np.array([[1.0, 2.0], [3.0, 4.0]]))
+    with pytest.raises(sg.SaitError) as e:
+        sg.sait_build(ctx, mat(sg, ctx, T), True, 3)
+    assert e.value.status == 2
+    Z = synth.from_dense(np.array([[1.0, 0.0], [3.0, 0.0]]))
+    with pytest.raises(sg.SaitError) as e:
+        sg.sait_build(ctx, mat(sg, ctx, Z), True, 3)
+    assert e.value.status == 3
+    T = synth.from_dense(np.tril(np.ones((3, 3))))
+    with pytest.raises(sg.SaitError) as e:
+        sg.sait_build(ctx, mat(sg, ctx, T), True, 0)
+    assert e.value.status == 1
+    with pytest.raises(sg.SaitError) as e:
+        sg.sait_build(ctx, mat(sg, ctx, T), True, 3, "abs", 1.5)
+    assert e.value.status == 1
+    bad = synth.CSR(2, np.array([0, 2, 3], np.int32), np.array([1, 0, 1], np.int32),
+                    np.ones(3))
+    with pytest.raises(sg.SaitError) as e:
+        mat(sg, ctx, bad)
+    assert e.value.status == 1
+
+
+# ---- products -------------------------------------------------------------------
+@pytest.mark.parametrize("store,tol", [("f64", 1e-12), ("f32", 1e-5), ("bf16", 1e-2)])
+def test_apply_parity(sg, ctx, oracle_lib, store, tol):
+    A = synth.convdiff3d(23)
+    Lo, Uo = oracle_lib.ilu0(A)
+    MLo, MUo = oracle_lib.sait(Lo, 4, "rowrel", 1e-3), oracle_lib.sait(Uo, 4, "rowrel", 1e-3)
+    ML = sg.sait_build(ctx, mat(sg, ctx, Lo), True, 4, "rowrel", 1e-3, store=store)
+    MU = sg.sait_build(ctx, mat(sg, ctx, Uo), False, 4, "rowrel", 1e-3, store=store)
+    r = synth.uniform(11, A.n)
+    z = sg.sait_apply(ctx, ML, MU, dev(r)).cpu().numpy()
+    zo = oracle_lib.apply(MLo, MUo, r)
+    absML = synth.CSR(MLo.n, MLo.rp, MLo.ci, np.abs(MLo.va))
+    absMU = synth.CSR(MUo.n, MUo.rp, MUo.ci, np.abs(MUo.va))
+    bound = oracle_lib.apply(absML, absMU, np.abs(r))
+    assert np.all(np.abs(z - zo) <= tol * bound)
+
+
+def test_spmv_parity_ragged(sg, ctx, oracle_lib):
+    T = synth.random_triangular(2000, True, 5, max_row=60, empty_frac=0.2, long_frac=0.02,
+                                long_row=1500)
+    x = synth.uniform(3, T.n)
+    y = sg.sait_spmv(ctx, mat(sg, ctx, T), dev(x)).cpu().numpy()
+    yo = oracle_lib.spmv(T, x)
+    bound = oracle_lib.spmv(synth.CSR(T.n, T.rp, T.ci, np.abs(T.va)), np.abs(x))
+    assert np.all(np.abs(y - yo) <= 1e-12 * bound)
+
+
+def test_exact_ilu_preconditioner(sg, ctx, oracle_lib):
+    A = synth.convdiff3d(21)
+    L, U = sg.sait_ilu0(ctx, A.n, dev(A.rp), dev(A.ci), dev(A.va))
+    Lo, Uo = oracle_lib.ilu0(A)
+    P = sg.sait_prec_create_ilu(ctx, L, U)
+    assert sg.sait_prec_levels(P) == (3 * 21 - 2, 3 * 21 - 2)
+    r = synth.uniform(4, A.n)
+    z = sg.sait_prec_apply(ctx, P, dev(r)).cpu().numpy()
+    zo = oracle_lib.trisolve(Uo, oracle_lib.trisolve(Lo, r, True), False)
+    assert np.abs(z - zo).max() <= 1e-12 * np.abs(zo).max()
+
+
+# ---- solvers -------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def c1(oracle_lib):
+    A = synth.poisson2d(64)
+    xt = synth.uniform(synth.SEED_BASE + 1, A.n)
+    b = oracle_lib.spmv(A, xt)
+    Lo, Uo = oracle_lib.ilu0(A)
+    return A, b, Lo, Uo
+
+
+@pytest.mark.parametrize("prec", ["sait", "ilu", "none"])
+def test_gmres_c1(sg, ctx, oracle_lib, c1, prec):
+    A, b, Lo, Uo = c1
+    Ag = mat(sg, ctx, A)
+    L, U = sg.sait_ilu0(ctx, A.n, dev(A.rp), dev(A.ci), dev(A.va))
+    if prec == "sait":
+        P = sg.sait_prec_create_sait(ctx, sg.sait_build(ctx, L, True, 3, "rowrel", 1e-3),
+                                     sg.sait_build(ctx, U, False, 3, "rowrel", 1e-3))
+        lo, up = oracle_lib.sait(Lo, 3, "rowrel", 1e-3), oracle_lib.sait(Uo, 3, "rowrel", 1e-3)
+    elif prec == "ilu":
+        P = sg.sait_prec_create_ilu(ctx, L, U)
+        lo, up = Lo, Uo
+    else:
+        P, lo, up = None, None, None
+    x, info, st = sg.sait_gmres(ctx, Ag, P, dev(b), restart=30, tol=1e-8, maxit=5000)
+    xo, ito, rro, sto = oracle_lib.gmres(A, b, prec, lo, up, restart=30, tol=1e-8, maxit=5000)
+    xg = x.cpu().numpy()
+    rel = np.linalg.norm(b - oracle_lib.spmv(A, xg)) / np.linalg.norm(b)
+    assert st == 0 and sto == 0
+    assert rel <= 1e-8 and abs(info.rel_resid - rel) <= 1e-3 * rel
+    assert abs(info.iters - ito) <= max(2, 0.02 * ito), (info.iters, ito)
+
+
+@pytest.mark.parametrize("prec", ["sait", "ilu"])
+def test_bicgstab_convdiff(sg, ctx, oracle_lib, prec):
+    A = synth.convdiff3d(20)
+    xt = synth.uniform(9, A.n)
+    b = oracle_lib.spmv(A, xt)
+    Lo, Uo = oracle_lib.ilu0(A)
+    L, U = sg.sait_ilu0(ctx, A.n, dev(A.rp), dev(A.ci), dev(A.va))
+    if prec == "sait":
+        P = sg.sait_prec_create_sait(ctx, sg.sait_build(ctx, L, True, 3, "rowrel", 1e-3),
+                                     sg.sait_build(ctx, U, False, 3, "rowrel", 1e-3))
+        lo, up = oracle_lib.sait(Lo, 3, "rowrel", 1e-3), oracle_lib.sait(Uo, 3, "rowrel", 1e-3)
+    else:
+        P = sg.sait_prec_create_ilu(ctx, L, U)
+        lo, up = Lo, Uo
+    x, info, st = sg.sait_bicgstab(ctx, mat(sg, ctx, A), P, dev(b), tol=1e-8, maxit=2000)
+    xo, ito, rro, sto = oracle_lib.bicgstab(A, b, prec, lo, up, tol=1e-8, maxit=2000)
+    rel = np.linalg.norm(b - oracle_lib.spmv(A, x.cpu().numpy())) / np.linalg.norm(b)
+    assert st == 0 and sto == 0 and rel <= 1e-8
+    assert abs(info.iters - ito) <= max(3, 0.1 * ito), (info.iters, ito)
+
+
+def test_gmres_nonconvergence_and_zero_rhs(sg, ctx, oracle_lib, c1):
+    A, b, _, _ = c1
+    Ag = mat(sg, ctx, A)
+    x, info, st = sg.sait_gmres(ctx, Ag, None, dev(b), restart=5, tol=1e-12, maxit=7, check=False)
+    assert st == 6 and info.iters == 7
+    rel = np.linalg.norm(b - oracle_lib.spmv(A, x.cpu().numpy())) / np.linalg.norm(b)
+    assert abs(info.rel_resid - rel) <= 1e-6 * rel
+    x, info, st = sg.sait_gmres(ctx, Ag, None, torch.zeros(A.n, dtype=torch.float64, device="cuda"))
+    assert st == 0 and float(x.abs().max()) == 0.0
