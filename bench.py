@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Time-to-1e-8 of SAIT-preconditioned GMRES and the SAIT-apply HBM bandwidth on one GB300.
+
+Workload (default): 7-point central-difference convection-diffusion on a 128^3
+grid (n = 2,097,152, nnz(A) = 14,581,760; convection (1, 0.5, 0.25) scaled to a
+cell Peclet number of 0.5), b = A x_true with x_true ~ U[-1, 1] (seeded).  One
+step is the whole hot path on the device: ILU(0) factors (GPU, level
+scheduled), the SAIT matrices of L and U (m = 3 series terms, row-relative drop
+1e-3), and GMRES(50) with z = M_U (M_L r) to a relative residual of 1e-8.
+
+Printed: one JSON line.  `value` is the time to a 1e-8 solution in ms (lower is
+better); `roofline` is the dominant kernel group of the step, `apply_roofline`
+the SAIT apply (two CSR products) measured live in the timed steps;
+`baseline_trisolve` is the same GMRES with the exact level-scheduled ILU
+substitutions; `cpu_baseline` is the FP64 oracle on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "time-to-1e-8 residual & SAIT-apply HBM GB/s (% peak) vs level-scheduled trisolve"
+TOL = 1e-8
+RESTART = 50
+DROP, TAU = "rowrel", 1e-3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--grid", type=int, default=128)
+    ap.add_argument("--m", type=int, default=3, help="series terms of SAIT")
+    ap.add_argument("--store", default="f64", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--no-extras", action="store_true", help="skip comparator and sweep runs")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def workload_name(a):
+    return (f"convdiff3d {a.grid}^3 (Pe 0.5): GPU ILU(0) + SAIT(m_terms={a.m}, {DROP} {TAU:g}, "
+            f"{a.store}) + GMRES({RESTART}) to {TOL:g}")
+
+
+# ---- clocks -------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k]
+                          and "Not" not in r[5 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+# ---- the step ----------------------------------------------------------------------
+class Problem:
+    def __init__(self, grid: int, device):
+        import torch
+        self.A = synth.convdiff3d(grid)
+        xt = synth.uniform(synth.SEED_BASE + 2, self.A.n)
+        self.b = self.A.to_scipy() @ xt
+        self.host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+                     for k, v in (("rp", self.A.rp), ("ci", self.A.ci), ("va", self.A.va), ("b", self.b))}
+        self.dev = {k: v.to(device) for k, v in self.host.items()}
+        self.h2d_bytes = sum(v.numel() * v.element_size() for v in self.host.values())
+        self.d2h_bytes = self.A.n * 8
+
+
+def sait_step(sg, ctx, P: Problem, d, m, store, solver="gmres"):
+    """One pass of the hot path on device-resident inputs d; returns (x, info, extra)."""
+    n = P.A.n
+    L, U = sg.sait_ilu0(ctx, n, d["rp"], d["ci"], d["va"])
+    ML = sg.sait_build(ctx, L, True, m, DROP, TAU, store=store)
+    MU = sg.sait_build(ctx, U, False, m, DROP, TAU, store=store)
+    Am = sg.sait_mat_create_csr(ctx, n, d["rp"], d["ci"], d["va"])
+    pre = sg.sait_prec_create_sait(ctx, ML, MU)
+    if solver == "gmres":
+        x, info, st = sg.sait_gmres(ctx, Am, pre, d["b"], restart=RESTART, tol=TOL, maxit=20000)
+    else:
+        x, info, st = sg.sait_bicgstab(ctx, Am, pre, d["b"], tol=TOL, maxit=20000)
+    # the objects are returned so that their teardown falls after the timed region
+    return x, info, {"nnz_ML": ML.nnz, "nnz_MU": MU.nnz, "nnz_L": L.nnz, "nnz_U": U.nnz}, \
+        (L, U, ML, MU, Am, pre)
+
+
+def trisolve_step(sg, ctx, P: Problem, d):
+    n = P.A.n
+    L, U = sg.sait_ilu0(ctx, n, d["rp"], d["ci"], d["va"])
+    Am = sg.sait_mat_create_csr(ctx, n, d["rp"], d["ci"], d["va"])
+    pre = sg.sait_prec_create_ilu(ctx, L, U)
+    x, info, st = sg.sait_gmres(ctx, Am, pre, d["b"], restart=RESTART, tol=TOL, maxit=20000)
+    return x, info, sg.sait_prec_levels(pre), (L, U, Am, pre)
+
+
+def apply_bytes(n, nnz_l, nnz_u, store):
+    sv = {"f64": 8, "f32": 4, "bf16": 2}[store]
+    vec = 32 * n if store == "f64" else 24 * n   # r in, w out+in, z out
+    return (nnz_l + nnz_u) * (sv + 4) + 2 * 4 * (n + 1) + vec
+
+
+def ortho_bytes(n, iters, restart):
+    """Algorithmic bytes of the CGS2 + norm + scale work of `iters` Arnoldi steps."""
+    total, left = 0, iters
+    while left > 0:
+        steps = min(left, restart)
+        for j in range(steps):
+            # two passes: read j+1 basis vectors + w (dots), read j+1 vectors + w, write w (update);
+            # then ||w|| (read w) and the scaling (read w, write v)
+            total += 2 * ((j + 1) * 8 * n + 8 * n + (j + 1) * 8 * n + 16 * n) + 8 * n + 16 * n
+        left -= steps
+    return total
+
+
+def spmv_a_bytes(A):
+    return A.nnz * 12 + 4 * (A.n + 1) + 16 * A.n
+
+
+def time_region(torch, ctx_stream, fn):
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(ctx_stream)
+    out = fn()
+    e.record(ctx_stream)
+    e.synchronize()
+    return s.elapsed_time(e), out
+
+
+# ---- CPU baseline: the oracle on a bounded sample ------------------------------------
+def oracle_sample(grid, m, gpu_iters=None):
+    """Full-size oracle ILU(0) + SAIT build, plus the first GMRES(50) cycle; the
+    solve time is scaled to the number of Arnoldi steps (the GPU's count when
+    given, else a log-linear estimate from the first cycle's residual drop)."""
+    import oracle
+    A = synth.convdiff3d(grid)
+    xt = synth.uniform(synth.SEED_BASE + 2, A.n)
+    b = A.to_scipy() @ xt
+    t0 = time.perf_counter()
+    L, U = oracle.ilu0(A)
+    ML = oracle.sait(L, m, DROP, TAU)
+    MU = oracle.sait(U, m, DROP, TAU)
+    t1 = time.perf_counter()
+    _, it, rr, st = oracle.gmres(A, b, "sait", ML, MU, restart=RESTART, tol=TOL, maxit=RESTART)
+    t2 = time.perf_counter()
+    if gpu_iters is None:
+        est = it if rr <= TOL else int(math.ceil(it * math.log(TOL) / math.log(max(rr, 1e-300))))
+        steps, how = est, "log-linear estimate from the first cycle's residual"
+    else:
+        steps, how = gpu_iters, "the GPU path's Arnoldi step count"
+    total_s = (t1 - t0) + (t2 - t1) * steps / max(it, 1)
+    sample = (f"oracle, 1 thread: full-size ILU(0) + SAIT build of L and U ({t1 - t0:.1f} s) and the "
+              f"first GMRES({RESTART}) cycle, {it} Arnoldi steps ({t2 - t1:.1f} s); solve time scaled "
+              f"to {steps} steps ({how})")
+    return total_s * 1e3, sample, t2 - t0
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # warm-up: page the oracle in on a small instance (untimed)
+    for _ in range(a.warmup):
+        oracle_sample(16, a.m)
+    vals, last = [], ""
+    for _ in range(a.steps):
+        v, sample, _ = oracle_sample(a.grid, a.m)
+        vals.append(v)
+        last = sample
+    v = statistics.mean(vals)
+    print(json.dumps({
+        "metric": METRIC, "impl": "reference", "value": v, "unit": "ms", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": v, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "parallelism": "replicas"},
+        "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": last},
+        "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---- our arm -----------------------------------------------------------------------
+def run_ours(a):
+    import torch
+    import paper_2106_12836_gb300 as sg
+    from paper_2106_12836_gb300 import build as sgb
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    sgb.build()
+    peak, peak_kind = peaks()
+
+    P = Problem(a.grid, device)
+    n = P.A.n
+    ctx = sg.Context()
+    stream = ctx.stream
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
+
+    def flush_l2():
+        flush.fill_(1)
+
+    for _ in range(max(a.warmup, 0)):
+        res = sait_step(sg, ctx, P, P.dev, a.m, a.store)
+        del res
+    torch.cuda.synchronize()
+
+    sg.sait_ctx_set_timing(ctx, True)
+    sg.sait_ctx_stats(ctx, reset=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    times, infos, extra = [], [], {}
+    for _ in range(a.steps):
+        flush_l2()
+        ms, (x, info, extra, keep) = time_region(torch, stream,
+                                                 lambda: sait_step(sg, ctx, P, P.dev, a.m, a.store))
+        del keep
+        times.append(ms)
+        infos.append(info.as_dict())
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    stats = sg.sait_ctx_stats(ctx, reset=True).as_dict()
+    sg.sait_ctx_set_timing(ctx, False)
+    ms_step = statistics.mean(times)
+    if dist:
+        t = torch.tensor([ms_step], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t)
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    # true residual of the last solution, checked in FP64 on the host
+    xr = x.cpu().numpy()
+    relres = float(np.linalg.norm(P.b - P.A.to_scipy() @ xr) / np.linalg.norm(P.b))
+
+    # ---- end to end through the C ABI from host (pinned) buffers
+    e2e_times = []
+    for _ in range(min(a.steps, 3)):
+        flush_l2()
+
+        def e2e():
+            d = {k: v.to(device, non_blocking=True) for k, v in P.host.items()}
+            xx, _, _, keep = sait_step(sg, ctx, P, d, a.m, a.store)
+            return xx.to("cpu", non_blocking=True), keep, d
+        ms, _ = time_region(torch, stream, e2e)
+        e2e_times.append(ms)
+
+    # ---- rooflines from the live timers of the timed steps
+    iters = infos[-1]["iters"]
+    groups = {g: stats[g]["ms"] for g in ("apply", "spmv", "ortho", "build", "ilu")}
+    ab = apply_bytes(n, extra["nnz_ML"], extra["nnz_MU"], a.store)
+    apply_ms = stats["apply"]["ms"] / max(stats["apply"]["calls"], 1)
+    ob = ortho_bytes(n, iters, RESTART) * a.steps
+    ortho_ms = stats["ortho"]["ms"]
+    sb = spmv_a_bytes(P.A)
+    spmv_ms = stats["spmv"]["ms"] / max(stats["spmv"]["calls"], 1)
+    rl = {
+        "apply": {"kernel": "k_spmv_csr x2 (M_L then M_U), one SAIT apply", "bound": "hbm",
+                  "achieved": ab / apply_ms / 1e6, "bytes": ab, "ms": apply_ms,
+                  "calls": stats["apply"]["calls"]},
+        "ortho": {"kernel": "GMRES CGS2 step (k_mdot, k_reduce, k_gemv x2, norm, Givens, scale)",
+                  "bound": "hbm", "achieved": ob / max(ortho_ms, 1e-9) / 1e6,
+                  "bytes": ob / max(stats["ortho"]["calls"], 1), "ms": ortho_ms / max(stats["ortho"]["calls"], 1),
+                  "calls": stats["ortho"]["calls"]},
+        "spmv": {"kernel": "k_spmv_csr (A, FP64)", "bound": "hbm", "achieved": sb / spmv_ms / 1e6,
+                 "bytes": sb, "ms": spmv_ms, "calls": stats["spmv"]["calls"]},
+    }
+    for r in rl.values():
+        r.update(peak=peak, unit="GB/s", frac=r["achieved"] / peak, peak_kind=peak_kind)
+    dom = max(("apply", "ortho", "spmv"), key=lambda g: groups[g])
+    traffic = {"apply": None, "ortho": None, "spmv": None}
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        with open(tfile) as f:
+            traffic.update(json.load(f).get(f"{a.grid}:{a.m}:{a.store}", {}))
+
+    def roof(g):
+        r = rl[g]
+        return {"bound": r["bound"], "achieved": round(r["achieved"], 1), "peak": peak, "unit": "GB/s",
+                "frac": round(r["frac"], 4), "traffic": traffic.get(g), "kernel": r["kernel"],
+                "algorithmic_bytes_per_launch": int(r["bytes"]), "avg_ms": round(r["ms"], 4),
+                "launches_timed": r["calls"], "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"}
+
+    out = {
+        "metric": METRIC, "value": round(ms_step, 3), "unit": "ms", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "n": n, "nnz_A": P.A.nnz, "m_terms": a.m, "drop": DROP,
+                   "tau": TAU, "store": a.store, "solver": f"gmres({RESTART})", "tol": TOL,
+                   "l2": "inputs larger than L2 (A 175 MB, SAIT pair 0.5 GB, basis 0.86 GB); L2 also "
+                         "flushed (512 MB write) before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "clocks": clk,
+        "e2e": {"value": round(statistics.mean(e2e_times), 3), "unit": "ms",
+                "h2d_bytes_per_step": P.h2d_bytes, "d2h_bytes_per_step": P.d2h_bytes},
+        "gpu_launches": stats["launches"],
+        "roofline": roof(dom),
+        "apply_roofline": roof("apply"),
+        "rooflines": {g: roof(g) for g in rl},
+        "breakdown_ms_per_step": {g: round(v / a.steps, 3) for g, v in groups.items()},
+        "solve": {"iters": iters, "cycles": infos[-1]["cycles"], "rel_resid": infos[-1]["rel_resid"],
+                  "rel_resid_host_check": relres, "step_ms": [round(t, 3) for t in times],
+                  **extra, "ratio_L": extra["nnz_ML"] / extra["nnz_L"],
+                  "ratio_U": extra["nnz_MU"] / extra["nnz_U"]},
+    }
+
+    if not a.no_extras:
+        # exact level-scheduled ILU substitution in the same GMRES (comparator)
+        flush_l2()
+        sg.sait_ctx_set_timing(ctx, True)
+        sg.sait_ctx_stats(ctx, reset=True)
+        ms_t, (xt_, info_t, levels, keep) = time_region(torch, stream, lambda: trisolve_step(sg, ctx, P, P.dev))
+        del keep
+        st_t = sg.sait_ctx_stats(ctx, reset=True).as_dict()
+        out["baseline_trisolve"] = {
+            "ms": round(ms_t, 3), "iters": info_t.iters, "rel_resid": info_t.rel_resid,
+            "levels": list(levels), "avg_trisolve_pair_ms": st_t["trisolve"]["ms"] / max(st_t["trisolve"]["calls"], 1),
+            "speedup_of_sait": round(ms_t / ms_step, 3)}
+        # BiCGSTAB with the same SAIT preconditioner
+        flush_l2()
+        ms_b, (_, info_b, _, keep) = time_region(
+            torch, stream, lambda: sait_step(sg, ctx, P, P.dev, a.m, a.store, "bicgstab"))
+        del keep
+        out["bicgstab"] = {"ms": round(ms_b, 3), "iters": info_b.iters, "rel_resid": info_b.rel_resid}
+        # m sweep (one run each)
+        sweep = []
+        for m in (2, 3, 4, 6):
+            flush_l2()
+            ms_m, (_, info_m, ex_m, keep) = time_region(torch, stream,
+                                                        lambda: sait_step(sg, ctx, P, P.dev, m, a.store))
+            del keep
+            st_m = sg.sait_ctx_stats(ctx, reset=True).as_dict()
+            sweep.append({"m_terms": m, "ms": round(ms_m, 3), "iters": info_m.iters,
+                          "nnz_ML": ex_m["nnz_ML"], "nnz_MU": ex_m["nnz_MU"],
+                          "build_ms": round(st_m["build"]["ms"], 3),
+                          "apply_ms": round(st_m["apply"]["ms"] / max(st_m["apply"]["calls"], 1), 4)})
+        out["m_sweep"] = sweep
+        sg.sait_ctx_set_timing(ctx, False)
+
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        v, sample, _ = oracle_sample(a.grid, a.m, gpu_iters=iters)
+        out["cpu_baseline"] = {"value": round(v, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+                               "sample": sample}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

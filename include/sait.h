@@ -83,10 +83,28 @@ typedef struct {
 } sait_csr;
 
 typedef struct {
-    int32_t iters;      /* products with A: Arnoldi steps (GMRES) or 2 per iteration (BiCGSTAB) */
+    int32_t iters;      /* Arnoldi steps (GMRES) or iterations, two products with A each (BiCGSTAB) */
     int32_t cycles;     /* GMRES restart cycles / BiCGSTAB recurrence restarts */
     double rel_resid;   /* true ||b - A x||_2 / ||b||_2 at exit, computed in FP64 */
 } sait_info;
+
+/* Groups of launches timed with CUDA events when timing is enabled. */
+typedef enum {
+    SAIT_TIMER_APPLY = 0,     /* SAIT preconditioner applies z = M_U (M_L r) (two products) */
+    SAIT_TIMER_SPMV = 1,      /* products with A inside the solvers and sait_spmv */
+    SAIT_TIMER_ORTHO = 2,     /* GMRES Gram-Schmidt + Givens step (per Arnoldi step) */
+    SAIT_TIMER_BUILD = 3,     /* whole sait_build calls */
+    SAIT_TIMER_ILU = 4,       /* whole sait_ilu0 calls */
+    SAIT_TIMER_TRISOLVE = 5,  /* exact-ILU preconditioner applies (two substitutions) */
+    SAIT_TIMER_COUNT = 6
+} sait_timer;
+
+typedef struct {
+    int64_t launches;                 /* kernel launches (graph kernel nodes included) */
+    double ms[SAIT_TIMER_COUNT];      /* event-timed milliseconds per group */
+    int64_t calls[SAIT_TIMER_COUNT];  /* calls that did work (counted on the device for
+                                         launches a solver may skip after convergence) */
+} sait_stats;
 
 typedef struct sait_ctx_s *sait_ctx;
 typedef struct sait_mat_s *sait_mat;
@@ -104,6 +122,14 @@ const char *sait_status_string(sait_status st);
 /* Description of the last failure on this context ("" if none).  The pointer
  * stays valid until the next call on the context. */
 const char *sait_ctx_last_error(sait_ctx ctx);
+
+/* Turn event timing of the launch groups of sait_timer on (1) or off (0).
+ * Timing adds two event records per timed call; it is off by default. */
+sait_status sait_ctx_set_timing(sait_ctx ctx, int enable);
+/* Read the launch count and timer totals accumulated since the last reset
+ * (launches made by this host thread).  reset = 1 clears them afterwards.
+ * Synchronizes. */
+sait_status sait_ctx_stats(sait_ctx ctx, sait_stats *out, int reset);
 
 /* ---- matrices ---------------------------------------------------------- */
 

@@ -24,7 +24,8 @@ __all__ = [
     "sait_mat_create_csr", "sait_mat_destroy", "sait_mat_info", "sait_mat_export_csr",
     "sait_mat_set_store", "sait_ilu0", "sait_build", "sait_spmv", "sait_apply",
     "sait_prec_create_sait", "sait_prec_create_ilu", "sait_prec_levels", "sait_prec_apply",
-    "sait_prec_destroy", "sait_gmres", "sait_bicgstab", "lib_path", "EXPORTS",
+    "sait_prec_destroy", "sait_gmres", "sait_bicgstab", "sait_ctx_set_timing", "sait_ctx_stats",
+    "Stats", "TIMERS", "lib_path", "EXPORTS",
 ]
 
 DROP = {"none": 0, "abs": 1, "rowrel": 2, "pattern": 3}
@@ -37,8 +38,9 @@ EXPORTS = [
     "sait_mat_create_csr", "sait_mat_destroy", "sait_mat_info", "sait_mat_export_csr",
     "sait_mat_set_store", "sait_ilu0", "sait_build", "sait_spmv", "sait_apply",
     "sait_prec_create_sait", "sait_prec_create_ilu", "sait_prec_levels", "sait_prec_apply",
-    "sait_prec_destroy", "sait_gmres", "sait_bicgstab",
+    "sait_prec_destroy", "sait_gmres", "sait_bicgstab", "sait_ctx_set_timing", "sait_ctx_stats",
 ]
+TIMERS = ["apply", "spmv", "ortho", "build", "ilu", "trisolve"]
 
 
 class _Csr(C.Structure):
@@ -48,6 +50,15 @@ class _Csr(C.Structure):
 
 class _Drop(C.Structure):
     _fields_ = [("kind", C.c_int32), ("p", C.c_int32), ("tau", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("ms", C.c_double * 6), ("calls", C.c_int64 * 6)]
+
+    def as_dict(self):
+        return {"launches": int(self.launches),
+                **{t: {"ms": float(self.ms[i]), "calls": int(self.calls[i])}
+                   for i, t in enumerate(TIMERS)}}
 
 
 class Info(C.Structure):
@@ -93,6 +104,8 @@ def _L():
             "sait_prec_destroy": [vp],
             "sait_gmres": [vp, vp, vp, vp, vp, i32, d, i32, C.POINTER(Info)],
             "sait_bicgstab": [vp, vp, vp, vp, vp, d, i32, C.POINTER(Info)],
+            "sait_ctx_set_timing": [vp, C.c_int],
+            "sait_ctx_stats": [vp, C.POINTER(Stats), C.c_int],
         }
         for name, args in sigs.items():
             f = getattr(lib, name)
@@ -222,6 +235,16 @@ def sait_ctx_create(stream_handle: int):
 
 def sait_ctx_destroy(ctx: Context):
     _check(None, _L().sait_ctx_destroy(ctx.h), "sait_ctx_destroy")
+
+
+def sait_ctx_set_timing(ctx: Context, enable: bool):
+    _check(ctx, _L().sait_ctx_set_timing(ctx.h, int(bool(enable))), "sait_ctx_set_timing")
+
+
+def sait_ctx_stats(ctx: Context, reset: bool = False) -> Stats:
+    st = Stats()
+    _check(ctx, _L().sait_ctx_stats(ctx.h, C.byref(st), int(bool(reset))), "sait_ctx_stats")
+    return st
 
 
 def sait_ctx_last_error(ctx: Context) -> str:

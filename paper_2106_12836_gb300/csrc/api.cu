@@ -16,6 +16,75 @@ sait_status ctx_cuda(sait_ctx ctx, cudaError_t e, const char *what, const char *
     return ctx_fail(ctx, e == cudaErrorMemoryAllocation ? SAIT_ERR_OOM : SAIT_ERR_CUDA, buf);
 }
 
+thread_local int64_t g_sait_launches = 0;
+
+// ---- timing ---------------------------------------------------------------------
+static cudaEvent_t get_event(sait_ctx ctx) {
+    if (!ctx->spare.empty()) {
+        cudaEvent_t e = ctx->spare.back();
+        ctx->spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+ScopedTimer::ScopedTimer(sait_ctx c, int g) : ctx(c), group(g) {
+    if (!ctx || !ctx->timing) return;
+    a = get_event(ctx);
+    if (a) cudaEventRecord(a, ctx->stream);
+}
+
+ScopedTimer::~ScopedTimer() {
+    if (!a) return;
+    cudaEvent_t b = get_event(ctx);
+    if (!b) { ctx->spare.push_back(a); return; }
+    cudaEventRecord(b, ctx->stream);
+    ctx->pending.push_back(TimerRec{group, a, b});
+    ctx->host_calls[group]++;
+}
+
+int *group_counter(sait_ctx ctx, int group) {
+    return ctx && ctx->timing ? ctx->d_word + kCounterBase + group : nullptr;
+}
+
+extern "C" sait_status sait_ctx_set_timing(sait_ctx ctx, int enable) {
+    if (!ctx) return SAIT_ERR_INVALID_ARG;
+    if (enable && !ctx->timing)
+        SAIT_CK(cudaMemsetAsync(ctx->d_word + kCounterBase, 0, SAIT_TIMER_COUNT * sizeof(int), ctx->stream));
+    ctx->timing = enable != 0;
+    return SAIT_OK;
+}
+
+extern "C" sait_status sait_ctx_stats(sait_ctx ctx, sait_stats *out, int reset) {
+    if (!ctx || !out) return SAIT_ERR_INVALID_ARG;
+    SAIT_CK(cudaStreamSynchronize(ctx->stream));
+    for (const TimerRec &r : ctx->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) ctx->ms[r.group] += ms;
+        ctx->spare.push_back(r.a);
+        ctx->spare.push_back(r.b);
+    }
+    ctx->pending.clear();
+    int dev_calls[SAIT_TIMER_COUNT];
+    SAIT_CK(cudaMemcpy(dev_calls, ctx->d_word + kCounterBase, sizeof(dev_calls), cudaMemcpyDeviceToHost));
+    out->launches = g_sait_launches - ctx->launch_base;
+    for (int g = 0; g < SAIT_TIMER_COUNT; g++) {
+        out->ms[g] = ctx->ms[g];
+        // groups whose kernels may be skipped after convergence are counted on the device
+        const bool device_counted = g == SAIT_TIMER_APPLY || g == SAIT_TIMER_SPMV || g == SAIT_TIMER_ORTHO;
+        out->calls[g] = device_counted ? dev_calls[g] : ctx->host_calls[g];
+    }
+    if (reset) {
+        for (int g = 0; g < SAIT_TIMER_COUNT; g++) { ctx->ms[g] = 0.0; ctx->host_calls[g] = 0; }
+        ctx->launch_base = g_sait_launches;
+        SAIT_CK(cudaMemsetAsync(ctx->d_word + kCounterBase, 0, SAIT_TIMER_COUNT * sizeof(int), ctx->stream));
+        SAIT_CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return SAIT_OK;
+}
+
 namespace {
 
 enum { V_ROWPTR = 1, V_RANGE = 2, V_UNSORTED = 4 };
@@ -54,6 +123,7 @@ extern "C" sait_status sait_ctx_create(sait_ctx *ctx, void *stream) {
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_word, 64 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_word, 0, 64 * sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_pinned, 4096);
     if (e == cudaSuccess) {
         // keep freed temporaries in the stream-ordered pool between calls
@@ -70,6 +140,7 @@ extern "C" sait_status sait_ctx_create(sait_ctx *ctx, void *stream) {
         delete c;
         return e == cudaErrorMemoryAllocation ? SAIT_ERR_OOM : SAIT_ERR_CUDA;
     }
+    c->launch_base = g_sait_launches;
     *ctx = c;
     return SAIT_OK;
 }
@@ -77,6 +148,8 @@ extern "C" sait_status sait_ctx_create(sait_ctx *ctx, void *stream) {
 extern "C" sait_status sait_ctx_destroy(sait_ctx ctx) {
     if (!ctx) return SAIT_ERR_INVALID_ARG;
     cudaStreamSynchronize(ctx->stream);
+    for (const TimerRec &r : ctx->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (cudaEvent_t e : ctx->spare) cudaEventDestroy(e);
     cudaFree(ctx->d_word);
     cudaFreeHost(ctx->h_pinned);
     delete ctx;
@@ -145,7 +218,7 @@ extern "C" sait_status sait_mat_create_csr(sait_ctx ctx, const sait_csr *A, sait
     cudaStream_t s = ctx->stream;
     int *h = (int *)ctx->h_pinned;
     SAIT_CK(cudaMemsetAsync(ctx->d_word, 0, sizeof(int), s));
-    k_validate<<<(unsigned)cdiv(A->n + 1, 256), 256, 0, s>>>(A->n, A->nnz, A->row_ptr, A->col, ctx->d_word);
+    launch_k(k_validate, (unsigned)cdiv(A->n + 1, 256), 256, 0, s, A->n, A->nnz, A->row_ptr, A->col, ctx->d_word);
     SAIT_CK(cudaGetLastError());
     SAIT_CK(cudaMemcpyAsync(h, ctx->d_word, sizeof(int), cudaMemcpyDeviceToHost, s));
     SAIT_CK(cudaStreamSynchronize(s));
@@ -210,14 +283,18 @@ extern "C" sait_status sait_mat_set_store(sait_ctx ctx, sait_mat M, sait_dtype s
 extern "C" sait_status sait_spmv(sait_ctx ctx, sait_mat A, const double *x, double *y) {
     if (!ctx) return SAIT_ERR_INVALID_ARG;
     if (!A || (A->n > 0 && (!x || !y))) return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_spmv: null argument");
-    SAIT_CK(launch_spmv(A, A->store, x, false, y, false, nullptr, ctx->stream));
+    ScopedTimer tm(ctx, SAIT_TIMER_SPMV);
+    SAIT_CK(launch_spmv(A, A->store, x, false, y, false, nullptr, ctx->stream,
+                        group_counter(ctx, SAIT_TIMER_SPMV)));
     return SAIT_OK;
 }
 
 static sait_status apply_pair(sait_ctx ctx, sait_mat ML, sait_mat MU, const double *r, double *z,
                               void *w, const int *active) {
     const bool f64 = ML->store == SAIT_F64 && MU->store == SAIT_F64;
-    SAIT_CK(launch_spmv(ML, ML->store, r, false, w, !f64, active, ctx->stream));
+    ScopedTimer tm(ctx, SAIT_TIMER_APPLY);
+    SAIT_CK(launch_spmv(ML, ML->store, r, false, w, !f64, active, ctx->stream,
+                        group_counter(ctx, SAIT_TIMER_APPLY)));
     SAIT_CK(launch_spmv(MU, MU->store, w, !f64, z, false, active, ctx->stream));
     return SAIT_OK;
 }
@@ -258,6 +335,7 @@ static sait_status capture_trisolve_graph(sait_ctx ctx, sait_prec p) {
     cudaStream_t cs;
     SAIT_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
+    const int64_t launches0 = g_sait_launches;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaError_t e1 = launch_trisolve(p->lo, p->lev_lo, true, p->gin, p->tmp, cs);
@@ -266,6 +344,8 @@ static sait_status capture_trisolve_graph(sait_ctx ctx, sait_prec p) {
         if (e == cudaSuccess && e1 != cudaSuccess) e = e1;
         if (e == cudaSuccess && e2 != cudaSuccess) e = e2;
     }
+    p->graph_kernels = g_sait_launches - launches0;  // captured, not executed
+    g_sait_launches = launches0;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&p->graph, g, 0);
     if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cs);
@@ -322,10 +402,12 @@ sait_status prec_apply_impl(sait_ctx ctx, sait_prec P, const double *r, double *
     if (P->kind == 1) return apply_pair(ctx, P->lo, P->up, r, z, P->tmp, active);
     if (P->kind == 2) {
         if (n == 0) return SAIT_OK;
-        k_copy_if<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(n, r, P->gin, active);
+        ScopedTimer tm(ctx, SAIT_TIMER_TRISOLVE);
+        launch_k(k_copy_if, (unsigned)cdiv(n, 256), 256, 0, s, n, r, P->gin, active);
         SAIT_CK(cudaGetLastError());
         SAIT_CK(cudaGraphLaunch(P->graph, s));
-        k_copy_if<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(n, P->gout, z, active);
+        g_sait_launches += P->graph_kernels;
+        launch_k(k_copy_if, (unsigned)cdiv(n, 256), 256, 0, s, n, P->gout, z, active);
         SAIT_CK(cudaGetLastError());
         return SAIT_OK;
     }

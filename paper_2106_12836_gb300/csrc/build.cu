@@ -462,6 +462,7 @@ extern "C" sait_status sait_build(sait_ctx ctx, sait_mat T, sait_uplo uplo, int3
         return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_build: bad storage type");
     const int64_t n = T->n, nnzT = T->nnz;
     cudaStream_t s = ctx->stream;
+    ScopedTimer tm(ctx, SAIT_TIMER_BUILD);
     int *h = (int *)ctx->h_pinned;
     int64_t *h64 = (int64_t *)ctx->h_pinned;
 
@@ -470,7 +471,7 @@ extern "C" sait_status sait_build(sait_ctx ctx, sait_mat T, sait_uplo uplo, int3
     SAIT_CK(dinv.alloc(n, s));
     SAIT_CK(cudaMemsetAsync(ctx->d_word, 0, sizeof(int), s));
     if (n > 0)
-        k_split_check<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(n, T->rp, T->ci, T->va,
+        launch_k(k_split_check, (unsigned)cdiv(n, 256), 256, 0, s, n, T->rp, T->ci, T->va,
                                                              uplo == SAIT_LOWER, dinv.p, ctx->d_word);
     SAIT_CK(cudaGetLastError());
     SAIT_CK(cudaMemcpyAsync(h, ctx->d_word, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -484,7 +485,7 @@ extern "C" sait_status sait_build(sait_ctx ctx, sait_mat T, sait_uplo uplo, int3
     sait_mat M = nullptr;
     if (m_terms == 1) {
         SAIT_TRY(mat_alloc(ctx, n, n, &M));
-        k_diag_inverse<<<(unsigned)cdiv(n + 1, 256), 256, 0, s>>>(n, dinv.p, M->rp, M->ci, M->va);
+        launch_k(k_diag_inverse, (unsigned)cdiv(n + 1, 256), 256, 0, s, n, dinv.p, M->rp, M->ci, M->va);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) { sait_mat_destroy(M); return ctx_cuda(ctx, e, "k_diag_inverse", __FILE__, __LINE__); }
     } else {
@@ -494,7 +495,7 @@ extern "C" sait_status sait_build(sait_ctx ctx, sait_mat T, sait_uplo uplo, int3
         SAIT_CK(tt_rp.alloc(n + 1, s));
         SAIT_CK(tt_ci.alloc(ntt, s));
         SAIT_CK(tt_va.alloc(ntt, s));
-        k_split_fill<<<(unsigned)cdiv(n + 1, 256), 256, 0, s>>>(n, T->rp, T->ci, T->va, dinv.p,
+        launch_k(k_split_fill, (unsigned)cdiv(n + 1, 256), 256, 0, s, n, T->rp, T->ci, T->va, dinv.p,
                                                                  tt_rp.p, tt_ci.p, tt_va.p);
         SAIT_CK(cudaGetLastError());
 
@@ -512,7 +513,7 @@ extern "C" sait_status sait_build(sait_ctx ctx, sait_mat T, sait_uplo uplo, int3
         SAIT_CK(owned.ci.alloc(n, s));
         SAIT_CK(owned.va.alloc(n, s));
         if (n > 0)
-            k_identity<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(n, owned.off.p, owned.cnt.p, owned.ci.p,
+            launch_k(k_identity, (unsigned)cdiv(n, 256), 256, 0, s, n, owned.off.p, owned.cnt.p, owned.ci.p,
                                                              owned.va.p);
         SAIT_CK(cudaGetLastError());
         View cur = view_of(owned);
@@ -531,7 +532,7 @@ extern "C" sait_status sait_build(sait_ctx ctx, sait_mat T, sait_uplo uplo, int3
             const int32_t *s_ci = masked && have_S ? S.ci.p : nullptr;
             SAIT_CK(cudaMemsetAsync(ctx->d_word, 0, sizeof(int), s));
             if (n > 0)
-                k_rowub<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(n, tt_rp.p, tt_ci.p, cur.cnt, masked,
+                launch_k(k_rowub, (unsigned)cdiv(n, 256), 256, 0, s, n, tt_rp.p, tt_ci.p, cur.cnt, masked,
                                                                 s_cnt, ub.p, ctx->d_word, ovf.p);
             SAIT_CK(cudaGetLastError());
             Iterate nx;
@@ -550,12 +551,12 @@ extern "C" sait_status sait_build(sait_ctx ctx, sait_mat T, sait_uplo uplo, int3
             if (n > 0) {
                 unsigned grid = (unsigned)std::min<int64_t>(cdiv(n, kWarps), (int64_t)ctx->num_sms * 4);
                 if (masked)
-                    k_spgemm_warp<true><<<grid, kWarps * 32, smem, s>>>(
+                    launch_k(k_spgemm_warp<true>, grid, kWarps * 32, smem, s, 
                         n, tt_rp.p, tt_ci.p, tt_va.p, cur.off, cur.cnt, cur.ci, cur.va, s_off, s_cnt,
                         s_ci, ub.p, nx.off.p, nx.cnt.p, nx.ci.p, nx.va.p, kind, tau, scale,
                         ctx->d_word + 1);
                 else
-                    k_spgemm_warp<false><<<grid, kWarps * 32, smem, s>>>(
+                    launch_k(k_spgemm_warp<false>, grid, kWarps * 32, smem, s, 
                         n, tt_rp.p, tt_ci.p, tt_va.p, cur.off, cur.cnt, cur.ci, cur.va, s_off, s_cnt,
                         s_ci, ub.p, nx.off.p, nx.cnt.p, nx.ci.p, nx.va.p, kind, tau, scale,
                         ctx->d_word + 1);
@@ -572,12 +573,12 @@ extern "C" sait_status sait_build(sait_ctx ctx, sait_mat T, sait_uplo uplo, int3
                 SAIT_CK(stp.alloc(nb * n, s));
                 SAIT_CK(cudaMemsetAsync(stp.p, 0xff, nb * n * sizeof(uint32_t), s));
                 if (masked)
-                    k_spgemm_dense<true><<<(unsigned)nb, kDenseThreads, 0, s>>>(
+                    launch_k(k_spgemm_dense<true>, (unsigned)nb, kDenseThreads, 0, s, 
                         novf, ovf.p, n, tt_rp.p, tt_ci.p, tt_va.p, cur.off, cur.cnt, cur.ci, cur.va,
                         s_off, s_cnt, s_ci, nx.off.p, nx.cnt.p, nx.ci.p, nx.va.p, kind, tau, scale,
                         acc.p, stp.p);
                 else
-                    k_spgemm_dense<false><<<(unsigned)nb, kDenseThreads, 0, s>>>(
+                    launch_k(k_spgemm_dense<false>, (unsigned)nb, kDenseThreads, 0, s, 
                         novf, ovf.p, n, tt_rp.p, tt_ci.p, tt_va.p, cur.off, cur.cnt, cur.ci, cur.va,
                         s_off, s_cnt, s_ci, nx.off.p, nx.cnt.p, nx.ci.p, nx.va.p, kind, tau, scale,
                         acc.p, stp.p);
@@ -604,7 +605,7 @@ extern "C" sait_status sait_build(sait_ctx ctx, sait_mat T, sait_uplo uplo, int3
         if (nnzM >= (int64_t)INT_MAX)
             return ctx_fail(ctx, SAIT_ERR_UNSUPPORTED, "sait_build: nnz(M) >= 2^31");
         SAIT_TRY(mat_alloc(ctx, n, nnzM, &M));
-        k_compact<<<(unsigned)cdiv((n + 1) * 32, 256), 256, 0, s>>>(n, fin.off, fin.cnt, fin.ci, fin.va,
+        launch_k(k_compact, (unsigned)cdiv((n + 1) * 32, 256), 256, 0, s, n, fin.off, fin.cnt, fin.ci, fin.va,
                                                                    rp64.p, M->rp, M->ci, M->va);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) { sait_mat_destroy(M); return ctx_cuda(ctx, e, "k_compact", __FILE__, __LINE__); }

@@ -10,6 +10,15 @@
 
 #include "sait.h"
 
+// d_word layout: [0..15] error flags and scratch, [16 + g] device-side call
+// counters of timer group g (incremented by kernels that did real work).
+constexpr int kCounterBase = 16;
+
+struct TimerRec {
+    int group;
+    cudaEvent_t a, b;
+};
+
 struct sait_ctx_s {
     cudaStream_t stream = nullptr;
     int device = 0;
@@ -17,7 +26,35 @@ struct sait_ctx_s {
     std::string last_error;
     int *d_word = nullptr;     // device scratch words (error flags, counters)
     void *h_pinned = nullptr;  // pinned host staging (4 KB)
+    bool timing = false;
+    std::vector<TimerRec> pending;
+    std::vector<cudaEvent_t> spare;
+    double ms[SAIT_TIMER_COUNT] = {};
+    int64_t host_calls[SAIT_TIMER_COUNT] = {};
+    int64_t launch_base = 0;
 };
+
+// Kernel launches made by this host thread (graph kernel nodes included).
+extern thread_local int64_t g_sait_launches;
+
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     Args... args) {
+    if (grid.x == 0 || grid.y == 0 || grid.z == 0) return;
+    kernel<<<grid, block, smem, s>>>(args...);
+    ++g_sait_launches;
+}
+
+// Event pair around a group of launches on the context stream (timing on only).
+struct ScopedTimer {
+    sait_ctx ctx;
+    int group;
+    cudaEvent_t a = nullptr;
+    ScopedTimer(sait_ctx c, int g);
+    ~ScopedTimer();
+};
+// device counter of a timer group, or null when timing is off
+int *group_counter(sait_ctx ctx, int group);
 
 struct sait_mat_s {
     int64_t n = 0, nnz = 0;
@@ -47,6 +84,7 @@ struct sait_prec_s {
     int device = 0;
     // CUDA graph of the level-scheduled substitution (input/output buffers fixed)
     cudaGraphExec_t graph = nullptr;
+    int64_t graph_kernels = 0;  // kernel nodes in the graph
     double *gin = nullptr, *gout = nullptr;
 };
 
@@ -102,7 +140,7 @@ cudaError_t scan_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s)
 int choose_lanes(int64_t n, int64_t nnz);
 // y = A x for the value storage of A; x/y element types given by flags.
 cudaError_t launch_spmv(const sait_mat_s *A, sait_dtype store, const void *x, bool x_f32, void *y,
-                        bool y_f32, const int *active, cudaStream_t s);
+                        bool y_f32, const int *active, cudaStream_t s, int *calls = nullptr);
 cudaError_t cast_values(const double *src, float *d32, __nv_bfloat16 *d16, int64_t nnz,
                         cudaStream_t s);
 

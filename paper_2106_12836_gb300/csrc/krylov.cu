@@ -173,8 +173,10 @@ __global__ void k_hadd(double *Hj, const double *h, int nv, int first, const int
     for (int q = threadIdx.x; q < nv; q += blockDim.x) Hj[q] = first ? h[q] : Hj[q] + h[q];
 }
 
-__global__ void k_givens(int j, int m, int remaining, double *H, double *cs, double *sn, double *g, Scal *sc) {
+__global__ void k_givens(int j, int m, int remaining, double *H, double *cs, double *sn, double *g, Scal *sc,
+                         int *calls) {
     if (sc->active == 0) return;
+    if (calls) atomicAdd(calls, 1);
     double *Hj = H + (int64_t)j * (m + 1);
     const double hn = sqrt(sc->r0);
     Hj[j + 1] = hn;
@@ -322,8 +324,8 @@ struct Work {
 cudaError_t dots(sait_ctx ctx, const Work &W, int64_t n, int nd, const double *x0, const double *y0,
                  const double *x1, const double *y1, const double *x2, const double *y2, double *out,
                  const int *active) {
-    k_dots<<<W.nb, kThreads, 0, ctx->stream>>>(n, nd, x0, y0, x1, y1, x2, y2, W.partial, active);
-    k_reduce<<<nd, kThreads, 0, ctx->stream>>>(W.partial, W.nb, 3, out, active);
+    launch_k(k_dots, W.nb, kThreads, 0, ctx->stream, n, nd, x0, y0, x1, y1, x2, y2, W.partial, active);
+    launch_k(k_reduce, nd, kThreads, 0, ctx->stream, W.partial, W.nb, 3, out, active);
     return cudaGetLastError();
 }
 
@@ -333,11 +335,11 @@ cudaError_t residual(sait_ctx ctx, sait_mat A, const double *x, const double *b,
     cudaStream_t s = ctx->stream;
     if (A->n == 0) return cudaSuccess;
     switch (G) {
-        case 2: k_residual<2><<<grid, kThreads, 0, s>>>(A->n, A->rp, A->ci, A->va, x, b, r); break;
-        case 4: k_residual<4><<<grid, kThreads, 0, s>>>(A->n, A->rp, A->ci, A->va, x, b, r); break;
-        case 8: k_residual<8><<<grid, kThreads, 0, s>>>(A->n, A->rp, A->ci, A->va, x, b, r); break;
-        case 16: k_residual<16><<<grid, kThreads, 0, s>>>(A->n, A->rp, A->ci, A->va, x, b, r); break;
-        default: k_residual<32><<<grid, kThreads, 0, s>>>(A->n, A->rp, A->ci, A->va, x, b, r); break;
+        case 2: launch_k(k_residual<2>, grid, kThreads, 0, s, A->n, A->rp, A->ci, A->va, x, b, r); break;
+        case 4: launch_k(k_residual<4>, grid, kThreads, 0, s, A->n, A->rp, A->ci, A->va, x, b, r); break;
+        case 8: launch_k(k_residual<8>, grid, kThreads, 0, s, A->n, A->rp, A->ci, A->va, x, b, r); break;
+        case 16: launch_k(k_residual<16>, grid, kThreads, 0, s, A->n, A->rp, A->ci, A->va, x, b, r); break;
+        default: launch_k(k_residual<32>, grid, kThreads, 0, s, A->n, A->rp, A->ci, A->va, x, b, r); break;
     }
     return cudaGetLastError();
 }
@@ -422,36 +424,47 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
     }
     const unsigned egrid = (unsigned)std::min<int64_t>(cdiv(n, kThreads), 8LL * ctx->num_sms);
     int iters = 0, cycles = 0;
+    // The level-scheduled substitution cannot skip its launches once the
+    // cycle has converged, so with an exact-ILU preconditioner poll every step.
+    const int poll = (P && P->kind == 2) ? 1 : kPoll;
     sait_status result = SAIT_ERR_NOT_CONVERGED;
     for (;;) {
         // r = b - A x  -> V_0, beta = ||r||
         SAIT_CK(residual(ctx, A, x, b, V.p));
         SAIT_CK(dots(ctx, W, n, 1, V.p, V.p, nullptr, nullptr, nullptr, nullptr, r0, nullptr));
-        k_gmres_start<<<1, 1, 0, s>>>(sc, g.p, m);
+        launch_k(k_gmres_start, 1, 1, 0, s, sc, g.p, m);
         SAIT_CK(cudaGetLastError());
         SAIT_TRY(read_scal(ctx, sc, &hs));
         inf.rel_resid = hs.beta / bnorm;
         if (!std::isfinite(hs.beta)) { result = SAIT_ERR_NONFINITE; break; }
         if (inf.rel_resid <= tol) { result = SAIT_OK; break; }
         if (iters >= maxit) break;
-        k_scale<<<egrid, kThreads, 0, s>>>(n, V.p, V.p, sc, nullptr);
+        launch_k(k_scale, egrid, kThreads, 0, s, n, V.p, V.p, sc, nullptr);
         const int remaining = maxit - iters;
         for (int j = 0; j < m; j++) {
             double *vj = V.p + (size_t)j * n, *w = V.p + (size_t)(j + 1) * n;
             SAIT_TRY(precondition(ctx, P, vj, z.p, n, act));
-            SAIT_CK(launch_spmv(A, SAIT_F64, z.p, false, w, false, act, s));
-            double *Hj = H.p + (size_t)j * (m + 1);
-            for (int pass = 0; pass < 2; pass++) {  // classical Gram-Schmidt, twice
-                k_mdot<<<W.nb, kThreads, 0, s>>>(n, V.p, n, j + 1, w, W.partial, ldp, act);
-                k_reduce<<<j + 1, kThreads, 0, s>>>(W.partial, W.nb, ldp, y.p, act);
-                k_hadd<<<1, 128, 0, s>>>(Hj, y.p, j + 1, pass == 0, act);
-                k_gemv<<<egrid, kThreads, 0, s>>>(n, V.p, n, j + 1, nullptr, y.p, w, 1, act);
+            {
+                ScopedTimer tm(ctx, SAIT_TIMER_SPMV);
+                SAIT_CK(launch_spmv(A, SAIT_F64, z.p, false, w, false, act, s,
+                                    group_counter(ctx, SAIT_TIMER_SPMV)));
             }
-            SAIT_CK(dots(ctx, W, n, 1, w, w, nullptr, nullptr, nullptr, nullptr, r0, act));
-            k_givens<<<1, 1, 0, s>>>(j, m, remaining, H.p, cs.p, sn.p, g.p, sc);
-            k_scale<<<egrid, kThreads, 0, s>>>(n, w, w, sc, act);
+            {
+                ScopedTimer tm(ctx, SAIT_TIMER_ORTHO);
+                double *Hj = H.p + (size_t)j * (m + 1);
+                for (int pass = 0; pass < 2; pass++) {  // classical Gram-Schmidt, twice
+                    launch_k(k_mdot, W.nb, kThreads, 0, s, n, V.p, n, j + 1, w, W.partial, ldp, act);
+                    launch_k(k_reduce, j + 1, kThreads, 0, s, W.partial, W.nb, ldp, y.p, act);
+                    launch_k(k_hadd, 1, 128, 0, s, Hj, y.p, j + 1, pass == 0, act);
+                    launch_k(k_gemv, egrid, kThreads, 0, s, n, V.p, n, j + 1, nullptr, y.p, w, 1, act);
+                }
+                SAIT_CK(dots(ctx, W, n, 1, w, w, nullptr, nullptr, nullptr, nullptr, r0, act));
+                launch_k(k_givens, 1, 1, 0, s, j, m, remaining, H.p, cs.p, sn.p, g.p, sc,
+                         group_counter(ctx, SAIT_TIMER_ORTHO));
+                launch_k(k_scale, egrid, kThreads, 0, s, n, w, w, sc, act);
+            }
             SAIT_CK(cudaGetLastError());
-            if ((j + 1) % kPoll == 0 || j + 1 == m) {
+            if ((j + 1) % poll == 0 || j + 1 == m) {
                 SAIT_TRY(read_scal(ctx, sc, &hs));
                 if (!hs.active) break;
             }
@@ -460,11 +473,11 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
         iters += hs.jdone;
         cycles++;
         if (hs.state == 3) { result = SAIT_ERR_NONFINITE; break; }
-        k_hsolve<<<1, 1, 0, s>>>(H.p, g.p, y.p, m, sc);
-        k_gemv<<<egrid, kThreads, 0, s>>>(n, V.p, n, 0, &sc->jdone, y.p, u.p, 0, nullptr);
+        launch_k(k_hsolve, 1, 1, 0, s, H.p, g.p, y.p, m, sc);
+        launch_k(k_gemv, egrid, kThreads, 0, s, n, V.p, n, 0, &sc->jdone, y.p, u.p, 0, nullptr);
         SAIT_CK(cudaGetLastError());
         SAIT_TRY(precondition(ctx, P, u.p, z.p, n, nullptr));
-        k_axpy1<<<egrid, kThreads, 0, s>>>(n, z.p, x);
+        launch_k(k_axpy1, egrid, kThreads, 0, s, n, z.p, x);
         SAIT_CK(cudaGetLastError());
         SAIT_TRY(read_scal(ctx, sc, &hs));
         if (hs.state == 2) { result = SAIT_ERR_BREAKDOWN; break; }
@@ -527,6 +540,7 @@ extern "C" sait_status sait_bicgstab(sait_ctx ctx, sait_mat A, sait_prec P, cons
         SAIT_CK(cudaMemcpyAsync(&sc->bnorm, &bnorm, sizeof(double), cudaMemcpyHostToDevice, s));
     }
     int iters = 0, cycles = 0;
+    const int poll = (P && P->kind == 2) ? 1 : kPoll;
     sait_status result = SAIT_ERR_NOT_CONVERGED;
     for (;;) {
         // (re)start: r = b - A x, rh = r
@@ -542,30 +556,38 @@ extern "C" sait_status sait_bicgstab(sait_ctx ctx, sait_mat A, sait_prec P, cons
         SAIT_CK(cudaMemsetAsync(p.p, 0, n * sizeof(double), s));
         SAIT_CK(cudaMemsetAsync(v.p, 0, n * sizeof(double), s));
         SAIT_CK(cudaMemsetAsync(&sc->jdone, 0, sizeof(int), s));
-        k_bicg_init<<<1, 1, 0, s>>>(sc);
+        launch_k(k_bicg_init, 1, 1, 0, s, sc);
         const int remaining = maxit - iters;
         for (int it = 0; it < remaining; it++) {
             SAIT_CK(dots(ctx, W, n, 1, rh.p, r.p, nullptr, nullptr, nullptr, nullptr, r0, act));
-            k_bicg_beta<<<1, 1, 0, s>>>(sc);
-            k_bicg_p<<<egrid, kThreads, 0, s>>>(n, r.p, v.p, p.p, sc);
+            launch_k(k_bicg_beta, 1, 1, 0, s, sc);
+            launch_k(k_bicg_p, egrid, kThreads, 0, s, n, r.p, v.p, p.p, sc);
             SAIT_TRY(precondition(ctx, P, p.p, ph.p, n, act));
-            SAIT_CK(launch_spmv(A, SAIT_F64, ph.p, false, v.p, false, act, s));
+            {
+                ScopedTimer tm(ctx, SAIT_TIMER_SPMV);
+                SAIT_CK(launch_spmv(A, SAIT_F64, ph.p, false, v.p, false, act, s,
+                                    group_counter(ctx, SAIT_TIMER_SPMV)));
+            }
             SAIT_CK(dots(ctx, W, n, 1, rh.p, v.p, nullptr, nullptr, nullptr, nullptr, r0, act));
-            k_bicg_alpha<<<1, 1, 0, s>>>(sc);
-            k_bicg_s<<<egrid, kThreads, 0, s>>>(n, r.p, v.p, sv.p, sc);
+            launch_k(k_bicg_alpha, 1, 1, 0, s, sc);
+            launch_k(k_bicg_s, egrid, kThreads, 0, s, n, r.p, v.p, sv.p, sc);
             SAIT_CK(dots(ctx, W, n, 1, sv.p, sv.p, nullptr, nullptr, nullptr, nullptr, r0, act));
-            k_bicg_check_s<<<1, 1, 0, s>>>(sc);
-            k_bicg_xhalf<<<egrid, kThreads, 0, s>>>(n, x, ph.p, sc);
-            k_bicg_xhalf_done<<<1, 1, 0, s>>>(sc);
+            launch_k(k_bicg_check_s, 1, 1, 0, s, sc);
+            launch_k(k_bicg_xhalf, egrid, kThreads, 0, s, n, x, ph.p, sc);
+            launch_k(k_bicg_xhalf_done, 1, 1, 0, s, sc);
             SAIT_TRY(precondition(ctx, P, sv.p, sh.p, n, act));
-            SAIT_CK(launch_spmv(A, SAIT_F64, sh.p, false, t.p, false, act, s));
+            {
+                ScopedTimer tm(ctx, SAIT_TIMER_SPMV);
+                SAIT_CK(launch_spmv(A, SAIT_F64, sh.p, false, t.p, false, act, s,
+                                    group_counter(ctx, SAIT_TIMER_SPMV)));
+            }
             SAIT_CK(dots(ctx, W, n, 2, t.p, t.p, t.p, sv.p, nullptr, nullptr, r0, act));
-            k_bicg_omega<<<1, 1, 0, s>>>(sc);
-            k_bicg_xr<<<egrid, kThreads, 0, s>>>(n, x, r.p, ph.p, sh.p, sv.p, t.p, sc);
+            launch_k(k_bicg_omega, 1, 1, 0, s, sc);
+            launch_k(k_bicg_xr, egrid, kThreads, 0, s, n, x, r.p, ph.p, sh.p, sv.p, t.p, sc);
             SAIT_CK(dots(ctx, W, n, 1, r.p, r.p, nullptr, nullptr, nullptr, nullptr, r0, act));
-            k_bicg_check_r<<<1, 1, 0, s>>>(sc, remaining);
+            launch_k(k_bicg_check_r, 1, 1, 0, s, sc, remaining);
             SAIT_CK(cudaGetLastError());
-            if ((it + 1) % kPoll == 0 || it + 1 == remaining) {
+            if ((it + 1) % poll == 0 || it + 1 == remaining) {
                 SAIT_TRY(read_scal(ctx, sc, &hs));
                 if (!hs.active) break;
             }

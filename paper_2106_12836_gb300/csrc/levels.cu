@@ -188,9 +188,9 @@ sait_status build_levels(sait_ctx ctx, const int32_t *rp, const int32_t *ci, int
     for (int64_t sweeps = 0;; sweeps += 8) {
         if (sweeps > n + 16) return ctx_fail(ctx, SAIT_ERR_CUDA, "level sweeps did not converge");
         for (int t = 0; t < 7; t++)
-            k_level_sweep<<<grid, 256, 0, s>>>(n, rp, ci, lower, lev.p, ctx->d_word + 8);
+            launch_k(k_level_sweep, grid, 256, 0, s, n, rp, ci, lower, lev.p, ctx->d_word + 8);
         SAIT_CK(cudaMemsetAsync(ctx->d_word + 8, 0, sizeof(int), s));
-        k_level_sweep<<<grid, 256, 0, s>>>(n, rp, ci, lower, lev.p, ctx->d_word + 8);
+        launch_k(k_level_sweep, grid, 256, 0, s, n, rp, ci, lower, lev.p, ctx->d_word + 8);
         SAIT_CK(cudaGetLastError());
         SAIT_CK(cudaMemcpyAsync(h, ctx->d_word + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
         SAIT_CK(cudaStreamSynchronize(s));
@@ -202,7 +202,7 @@ sait_status build_levels(sait_ctx ctx, const int32_t *rp, const int32_t *ci, int
     SAIT_CK(cudaMemsetAsync(hist.p, 0, n * sizeof(int32_t), s));
     SAIT_CK(cudaMemsetAsync(cursor.p, 0, n * sizeof(int32_t), s));
     SAIT_CK(cudaMemsetAsync(ctx->d_word + 9, 0, sizeof(int), s));
-    k_level_hist<<<grid, 256, 0, s>>>(n, lev.p, hist.p, ctx->d_word + 9);
+    launch_k(k_level_hist, grid, 256, 0, s, n, lev.p, hist.p, ctx->d_word + 9);
     SAIT_CK(cudaGetLastError());
     SAIT_CK(cudaMemcpyAsync(h + 1, ctx->d_word + 9, sizeof(int), cudaMemcpyDeviceToHost, s));
     SAIT_CK(cudaStreamSynchronize(s));
@@ -211,7 +211,7 @@ sait_status build_levels(sait_ctx ctx, const int32_t *rp, const int32_t *ci, int
     SAIT_CK(ptr.alloc(nlev + 1, s));
     SAIT_CK(scan_i32(hist.p, ptr.p, nlev, s));
     SAIT_CK(cudaMalloc((void **)&out->rows, n * sizeof(int32_t)));
-    k_level_scatter<<<grid, 256, 0, s>>>(n, lev.p, ptr.p, cursor.p, out->rows);
+    launch_k(k_level_scatter, grid, 256, 0, s, n, lev.p, ptr.p, cursor.p, out->rows);
     SAIT_CK(cudaGetLastError());
     std::vector<int64_t> hp(nlev + 1);
     SAIT_CK(cudaMemcpyAsync(hp.data(), ptr.p, (nlev + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -232,9 +232,9 @@ cudaError_t launch_trisolve(const sait_mat_s *T, const LevelSchedule &lev, bool 
         const int32_t *rows = lev.rows + lev.ptr[l];
         const unsigned grid = (unsigned)cdiv((int64_t)cnt * G, 256);
         switch (G) {
-            case 2: k_trisolve_level<2><<<grid, 256, 0, s>>>(rows, cnt, T->rp, T->ci, T->va, lower, b, x); break;
-            case 4: k_trisolve_level<4><<<grid, 256, 0, s>>>(rows, cnt, T->rp, T->ci, T->va, lower, b, x); break;
-            default: k_trisolve_level<8><<<grid, 256, 0, s>>>(rows, cnt, T->rp, T->ci, T->va, lower, b, x); break;
+            case 2: launch_k(k_trisolve_level<2>, grid, 256, 0, s, rows, cnt, T->rp, T->ci, T->va, lower, b, x); break;
+            case 4: launch_k(k_trisolve_level<4>, grid, 256, 0, s, rows, cnt, T->rp, T->ci, T->va, lower, b, x); break;
+            default: launch_k(k_trisolve_level<8>, grid, 256, 0, s, rows, cnt, T->rp, T->ci, T->va, lower, b, x); break;
         }
     }
     return cudaGetLastError();
@@ -244,6 +244,7 @@ extern "C" sait_status sait_ilu0(sait_ctx ctx, const sait_csr *A, sait_mat *L, s
     if (!ctx) return SAIT_ERR_INVALID_ARG;
     if (!A || !L || !U) return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_ilu0: null argument");
     *L = *U = nullptr;
+    ScopedTimer tm(ctx, SAIT_TIMER_ILU);
     sait_mat W = nullptr;  // validated working copy of A, overwritten with L\U
     SAIT_TRY(sait_mat_create_csr(ctx, A, &W));
     const int64_t n = W->n;
@@ -261,7 +262,7 @@ extern "C" sait_status sait_ilu0(sait_ctx ctx, const sait_csr *A, sait_mat *L, s
     cudaError_t e = dpos.alloc(n, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_word, 0, sizeof(int), s);
     if (e != cudaSuccess) { cuda_fail(e, "sait_ilu0 setup"); goto done; }
-    if (n > 0) k_diag_pos<<<grid, 256, 0, s>>>(n, W->rp, W->ci, dpos.p, ctx->d_word);
+    if (n > 0) launch_k(k_diag_pos, grid, 256, 0, s, n, W->rp, W->ci, dpos.p, ctx->d_word);
     e = cudaMemcpyAsync(h, ctx->d_word, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { cuda_fail(e, "sait_ilu0 diagonal"); goto done; }
@@ -270,7 +271,7 @@ extern "C" sait_status sait_ilu0(sait_ctx ctx, const sait_csr *A, sait_mat *L, s
     if (st != SAIT_OK) goto done;
     for (int l = 0; l < lev.nlev; l++) {
         const int cnt = lev.ptr[l + 1] - lev.ptr[l];
-        k_ilu0_level<<<(unsigned)cdiv((int64_t)cnt * 32, 256), 256, 0, s>>>(
+        launch_k(k_ilu0_level, (unsigned)cdiv((int64_t)cnt * 32, 256), 256, 0, s, 
             lev.rows + lev.ptr[l], cnt, W->rp, W->ci, dpos.p, W->va, ctx->d_word);
     }
     e = cudaGetLastError();
@@ -284,7 +285,7 @@ extern "C" sait_status sait_ilu0(sait_ctx ctx, const sait_csr *A, sait_mat *L, s
     if (e == cudaSuccess) e = lrp.alloc(n + 1, s);
     if (e == cudaSuccess) e = urp.alloc(n + 1, s);
     if (e != cudaSuccess) { cuda_fail(e, "sait_ilu0 split"); goto done; }
-    if (n > 0) k_lu_counts<<<grid, 256, 0, s>>>(n, W->rp, W->ci, lc.p, uc.p);
+    if (n > 0) launch_k(k_lu_counts, grid, 256, 0, s, n, W->rp, W->ci, lc.p, uc.p);
     e = scan_i32(lc.p, lrp.p, n, s);
     if (e == cudaSuccess) e = scan_i32(uc.p, urp.p, n, s);
     {
@@ -297,7 +298,7 @@ extern "C" sait_status sait_ilu0(sait_ctx ctx, const sait_csr *A, sait_mat *L, s
         if (st == SAIT_OK) st = mat_alloc(ctx, n, h64[1], &Um);
         if (st != SAIT_OK) goto done;
     }
-    k_lu_fill<<<(unsigned)cdiv(n + 1, 256), 256, 0, s>>>(n, W->rp, W->ci, W->va, lrp.p, urp.p, Lm->rp,
+    launch_k(k_lu_fill, (unsigned)cdiv(n + 1, 256), 256, 0, s, n, W->rp, W->ci, W->va, lrp.p, urp.p, Lm->rp,
                                                          Lm->ci, Lm->va, Um->rp, Um->ci, Um->va);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -90,9 +90,9 @@ cudaError_t scan_impl(const Tin *in, int64_t *out, int64_t n, cudaStream_t s) {
     int64_t *sums = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&sums, ntiles * sizeof(int64_t), s);
     if (e != cudaSuccess) return e;
-    k_scan_tiles<Tin><<<(unsigned)ntiles, kThreads, 0, s>>>(in, n, out, sums);
-    k_scan_sums<<<1, kThreads, 0, s>>>(sums, ntiles, out + n);
-    k_scan_add<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(out, n, sums);
+    launch_k(k_scan_tiles<Tin>, (unsigned)ntiles, kThreads, 0, s, in, n, out, sums);
+    launch_k(k_scan_sums, 1, kThreads, 0, s, sums, ntiles, out + n);
+    launch_k(k_scan_add, (unsigned)cdiv(n, 256), 256, 0, s, out, n, sums);
     e = cudaGetLastError();
     cudaFreeAsync(sums, s);
     return e;

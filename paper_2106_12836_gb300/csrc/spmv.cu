@@ -26,9 +26,10 @@ template <int G, typename TV, typename TX, typename TY>
 __global__ void __launch_bounds__(256)
 k_spmv_csr(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
            const TV *__restrict__ va, const TX *__restrict__ x, TY *__restrict__ y,
-           const int *__restrict__ active) {
+           const int *__restrict__ active, int *calls) {
     using A = typename Acc<TV>::type;
     if (active && *active == 0) return;  // uniform over the grid
+    if (calls && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(calls, 1);
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t row = gid / G;
     const int lane = threadIdx.x & (G - 1);
@@ -44,31 +45,32 @@ k_spmv_csr(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict_
 
 template <typename TV, typename TX, typename TY>
 cudaError_t launch_g(int G, int64_t n, const int32_t *rp, const int32_t *ci, const TV *va,
-                     const TX *x, TY *y, const int *active, cudaStream_t s) {
+                     const TX *x, TY *y, const int *active, cudaStream_t s, int *calls) {
     if (n == 0) return cudaSuccess;
     const int threads = 256;
     const unsigned blocks = (unsigned)cdiv(n * G, threads);
     switch (G) {
-        case 2: k_spmv_csr<2><<<blocks, threads, 0, s>>>(n, rp, ci, va, x, y, active); break;
-        case 4: k_spmv_csr<4><<<blocks, threads, 0, s>>>(n, rp, ci, va, x, y, active); break;
-        case 8: k_spmv_csr<8><<<blocks, threads, 0, s>>>(n, rp, ci, va, x, y, active); break;
-        case 16: k_spmv_csr<16><<<blocks, threads, 0, s>>>(n, rp, ci, va, x, y, active); break;
-        default: k_spmv_csr<32><<<blocks, threads, 0, s>>>(n, rp, ci, va, x, y, active); break;
+        case 2: launch_k(k_spmv_csr<2, TV, TX, TY>, blocks, threads, 0, s, n, rp, ci, va, x, y, active, calls); break;
+        case 4: launch_k(k_spmv_csr<4, TV, TX, TY>, blocks, threads, 0, s, n, rp, ci, va, x, y, active, calls); break;
+        case 8: launch_k(k_spmv_csr<8, TV, TX, TY>, blocks, threads, 0, s, n, rp, ci, va, x, y, active, calls); break;
+        case 16: launch_k(k_spmv_csr<16, TV, TX, TY>, blocks, threads, 0, s, n, rp, ci, va, x, y, active, calls); break;
+        default: launch_k(k_spmv_csr<32, TV, TX, TY>, blocks, threads, 0, s, n, rp, ci, va, x, y, active, calls); break;
     }
     return cudaGetLastError();
 }
 
 template <typename TV>
 cudaError_t launch_xy(const sait_mat_s *A, const TV *va, const void *x, bool x_f32, void *y,
-                      bool y_f32, const int *active, cudaStream_t s) {
+                      bool y_f32, const int *active, cudaStream_t s, int *calls) {
     const int G = A->lanes;
     if (x_f32) {
         if (y_f32)
-            return launch_g(G, A->n, A->rp, A->ci, va, (const float *)x, (float *)y, active, s);
-        return launch_g(G, A->n, A->rp, A->ci, va, (const float *)x, (double *)y, active, s);
+            return launch_g(G, A->n, A->rp, A->ci, va, (const float *)x, (float *)y, active, s, calls);
+        return launch_g(G, A->n, A->rp, A->ci, va, (const float *)x, (double *)y, active, s, calls);
     }
-    if (y_f32) return launch_g(G, A->n, A->rp, A->ci, va, (const double *)x, (float *)y, active, s);
-    return launch_g(G, A->n, A->rp, A->ci, va, (const double *)x, (double *)y, active, s);
+    if (y_f32)
+        return launch_g(G, A->n, A->rp, A->ci, va, (const double *)x, (float *)y, active, s, calls);
+    return launch_g(G, A->n, A->rp, A->ci, va, (const double *)x, (double *)y, active, s, calls);
 }
 
 __global__ void k_cast(const double *__restrict__ src, float *d32, __nv_bfloat16 *d16, int64_t n) {
@@ -90,11 +92,11 @@ int choose_lanes(int64_t n, int64_t nnz) {
 }
 
 cudaError_t launch_spmv(const sait_mat_s *A, sait_dtype store, const void *x, bool x_f32, void *y,
-                        bool y_f32, const int *active, cudaStream_t s) {
+                        bool y_f32, const int *active, cudaStream_t s, int *calls) {
     switch (store) {
-        case SAIT_F32: return launch_xy(A, A->va32, x, x_f32, y, y_f32, active, s);
-        case SAIT_BF16: return launch_xy(A, A->va16, x, x_f32, y, y_f32, active, s);
-        default: return launch_xy(A, A->va, x, x_f32, y, y_f32, active, s);
+        case SAIT_F32: return launch_xy(A, A->va32, x, x_f32, y, y_f32, active, s, calls);
+        case SAIT_BF16: return launch_xy(A, A->va16, x, x_f32, y, y_f32, active, s, calls);
+        default: return launch_xy(A, A->va, x, x_f32, y, y_f32, active, s, calls);
     }
 }
 
@@ -102,6 +104,6 @@ cudaError_t cast_values(const double *src, float *d32, __nv_bfloat16 *d16, int64
                         cudaStream_t s) {
     if (nnz == 0) return cudaSuccess;
     unsigned blocks = (unsigned)std::min<int64_t>(cdiv(nnz, 256), 152 * 16);
-    k_cast<<<blocks, 256, 0, s>>>(src, d32, d16, nnz);
+    launch_k(k_cast, blocks, 256, 0, s, src, d32, d16, nnz);
     return cudaGetLastError();
 }
