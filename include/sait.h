@@ -85,6 +85,8 @@ typedef struct {
 typedef struct {
     int32_t iters;      /* Arnoldi steps (GMRES) or iterations, two products with A each (BiCGSTAB) */
     int32_t cycles;     /* GMRES restart cycles / BiCGSTAB recurrence restarts */
+    int32_t reorth_steps; /* GMRES: Arnoldi steps that needed a second Gram-Schmidt pass */
+    int32_t pad;
     double rel_resid;   /* true ||b - A x||_2 / ||b||_2 at exit, computed in FP64 */
 } sait_info;
 

@@ -62,10 +62,12 @@ class Stats(C.Structure):
 
 
 class Info(C.Structure):
-    _fields_ = [("iters", C.c_int32), ("cycles", C.c_int32), ("rel_resid", C.c_double)]
+    _fields_ = [("iters", C.c_int32), ("cycles", C.c_int32), ("reorth_steps", C.c_int32),
+                ("pad", C.c_int32), ("rel_resid", C.c_double)]
 
     def as_dict(self):
-        return {"iters": self.iters, "cycles": self.cycles, "rel_resid": self.rel_resid}
+        return {"iters": self.iters, "cycles": self.cycles, "reorth_steps": self.reorth_steps,
+                "rel_resid": self.rel_resid}
 
 
 def lib_path() -> str:

@@ -197,6 +197,7 @@ sait_status mat_alloc(sait_ctx ctx, int64_t n, int64_t nnz, sait_mat *out) {
 }
 
 sait_status mat_prepare_store(sait_ctx ctx, sait_mat M, sait_dtype store) {
+    SAIT_TRY(mat_prepare_sell(ctx, M, store));
     if (store == SAIT_F32 && !M->va32) {
         SAIT_CK(cudaMalloc((void **)&M->va32, (M->nnz ? M->nnz : 1) * sizeof(float)));
         SAIT_CK(cast_values(M->va, M->va32, nullptr, M->nnz, ctx->stream));
@@ -237,6 +238,13 @@ extern "C" sait_status sait_mat_create_csr(sait_ctx ctx, const sait_csr *A, sait
         sait_mat_destroy(M);
         return ctx_cuda(ctx, e, "sait_mat_create_csr", __FILE__, __LINE__);
     }
+    sait_status st = mat_prepare_store(ctx, M, SAIT_F64);
+    if (st == SAIT_OK && cudaStreamSynchronize(s) != cudaSuccess)
+        st = ctx_cuda(ctx, cudaGetLastError(), "sait_mat_create_csr", __FILE__, __LINE__);
+    if (st != SAIT_OK) {
+        sait_mat_destroy(M);
+        return st;
+    }
     *out = M;
     return SAIT_OK;
 }
@@ -248,6 +256,11 @@ extern "C" sait_status sait_mat_destroy(sait_mat M) {
     if (M->va) cudaFree(M->va);
     if (M->va32) cudaFree(M->va32);
     if (M->va16) cudaFree(M->va16);
+    if (M->soff) cudaFree(M->soff);
+    if (M->sci) cudaFree(M->sci);
+    if (M->sva64) cudaFree(M->sva64);
+    if (M->sva32) cudaFree(M->sva32);
+    if (M->sva16) cudaFree(M->sva16);
     delete M;
     return SAIT_OK;
 }

@@ -66,6 +66,14 @@ struct sait_mat_s {
     sait_dtype store = SAIT_F64;
     int device = 0;
     int lanes = 8;                  // lanes per row for CSR products
+    // SELL-32 copy for products (built on demand; see sell.cu)
+    bool sell_rejected = false;     // padding above 20%: products stay on CSR
+    int64_t nslices = 0, sell_nnz = 0;
+    int64_t *soff = nullptr;
+    int32_t *sci = nullptr;
+    double *sva64 = nullptr;
+    float *sva32 = nullptr;
+    __nv_bfloat16 *sva16 = nullptr;
 };
 
 struct LevelSchedule {
@@ -143,6 +151,12 @@ cudaError_t launch_spmv(const sait_mat_s *A, sait_dtype store, const void *x, bo
                         bool y_f32, const int *active, cudaStream_t s, int *calls = nullptr);
 cudaError_t cast_values(const double *src, float *d32, __nv_bfloat16 *d16, int64_t nnz,
                         cudaStream_t s);
+
+// sell.cu
+sait_status mat_prepare_sell(sait_ctx ctx, sait_mat M, sait_dtype store);
+bool sell_ready(const sait_mat_s *A, sait_dtype store);
+cudaError_t launch_spmv_sell(const sait_mat_s *A, sait_dtype store, const void *x, bool x_f32, void *y,
+                             bool y_f32, const int *active, cudaStream_t s, int *calls);
 
 // levels.cu
 sait_status build_levels(sait_ctx ctx, const int32_t *rp, const int32_t *ci, int64_t n, bool lower,

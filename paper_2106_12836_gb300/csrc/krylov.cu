@@ -17,16 +17,17 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kPoll = 8;       // iterations enqueued between status reads
 constexpr int kMaxRestart = 512;
-constexpr int kChunk = 64;     // vectors per pass of the multi-dot kernel
 
 struct Scal {        // device-resident solver scalars
     int active;      // 1 while the current cycle / iteration runs
     int jdone;       // GMRES: Arnoldi steps done in this cycle; BiCGSTAB: iterations done
     int state;       // 0 running, 1 converged, 2 breakdown, 3 non-finite, 4 x updated (half step)
-    int pad;
+    int reorth;      // GMRES: 1 when the current step needs a second Gram-Schmidt pass
     double bnorm, beta, tolb, inv;
     double rho, rho_old, alpha, omega, beta_b;
     double r0, r1, r2, r3;    // reduction results
+    int nreorth;              // GMRES: steps that took a second Gram-Schmidt pass
+    int pad2;
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -81,33 +82,114 @@ k_reduce(const double *__restrict__ partial, int nb, int stride, double *out, co
     if (threadIdx.x == 0) out[q] = s;
 }
 
-// Multi-dot h_q = V_q . w for q < nvec (nvec read from the device when
-// nvec_dev != null).  Warps split the vectors, lanes split the rows; each
-// block leaves partial[b*ldp + q].
-__global__ void __launch_bounds__(kThreads)
-k_mdot(int64_t n, const double *__restrict__ V, int64_t ldv, int nvec, const double *__restrict__ w,
-       double *partial, int ldp, const int *active) {
-    if (active && *active == 0) return;
+// Classical Gram-Schmidt pass, dots: partial[b*ldp + q] = sum over block b's
+// rows of V_q . w for q < nvec, and partial[b*ldp + nvec] = w . w when
+// with_norm.  One thread per row with one register accumulator per vector of a
+// chunk (chunks of kCH; the last chunk is instantiated for its exact size so
+// no FP64 FMA slot is wasted -- FP64 throughput, not bandwidth, is the scarce
+// resource of these passes on GB300).  w is re-read from L2 for every chunk.
+constexpr int kCH = 16;
+
+template <int CH, bool NORM>
+__device__ __forceinline__ void dot_chunk(int64_t n, const double *__restrict__ V, int64_t ldv, int q0,
+                                          const double *__restrict__ w, double *partial, int ldp, int nvec,
+                                          double (*red)[kCH + 1]) {
+    constexpr int NA = CH + (NORM ? 1 : 0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int c0 = 0; c0 < nvec; c0 += kChunk) {
-        double acc[kChunk / 8];
+    double acc[NA > 0 ? NA : 1];
 #pragma unroll
-        for (int t = 0; t < kChunk / 8; t++) acc[t] = 0.0;
-        for (int64_t r = (int64_t)blockIdx.x * 32 + lane; r < n; r += (int64_t)gridDim.x * 32) {
-            const double wv = w[r];
+    for (int t = 0; t < NA; t++) acc[t] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        const double wi = w[i];
+        double vv[CH > 0 ? CH : 1];
 #pragma unroll
-            for (int t = 0; t < kChunk / 8; t++) {
-                const int q = c0 + warp + 8 * t;
-                if (q < nvec) acc[t] = fma(V[(int64_t)q * ldv + r], wv, acc[t]);
-            }
-        }
+        for (int t = 0; t < CH; t++) vv[t] = __ldg(V + (int64_t)(q0 + t) * ldv + i);
 #pragma unroll
-        for (int t = 0; t < kChunk / 8; t++) {
-            const int q = c0 + warp + 8 * t;
-            const double s = warp_sum(acc[t]);
-            if (lane == 0 && q < nvec) partial[(int64_t)blockIdx.x * ldp + q] = s;
-        }
+        for (int t = 0; t < CH; t++) acc[t] = fma(vv[t], wi, acc[t]);
+        if (NORM) acc[NA - 1] = fma(wi, wi, acc[NA - 1]);
     }
+#pragma unroll
+    for (int t = 0; t < NA; t++) {
+        const double v = warp_sum(acc[t]);
+        if (lane == 0) red[warp][t] = v;
+    }
+    __syncthreads();
+    if (NA > 0 && (int)threadIdx.x < NA) {
+        double sum = 0.0;
+        for (int w2 = 0; w2 < kThreads / 32; w2++) sum += red[w2][threadIdx.x];
+        const int q = (int)threadIdx.x < CH ? q0 + (int)threadIdx.x : nvec;
+        partial[(int64_t)blockIdx.x * ldp + q] = sum;
+    }
+    __syncthreads();
+}
+
+template <bool NORM>
+__device__ __forceinline__ void dot_tail(int rem, int64_t n, const double *V, int64_t ldv, int q0,
+                                         const double *w, double *partial, int ldp, int nvec,
+                                         double (*red)[kCH + 1]) {
+    switch (rem) {
+#define SAIT_TAIL(k) case k: dot_chunk<k, NORM>(n, V, ldv, q0, w, partial, ldp, nvec, red); break;
+        SAIT_TAIL(0) SAIT_TAIL(1) SAIT_TAIL(2) SAIT_TAIL(3) SAIT_TAIL(4) SAIT_TAIL(5) SAIT_TAIL(6)
+        SAIT_TAIL(7) SAIT_TAIL(8) SAIT_TAIL(9) SAIT_TAIL(10) SAIT_TAIL(11) SAIT_TAIL(12) SAIT_TAIL(13)
+        SAIT_TAIL(14) SAIT_TAIL(15)
+#undef SAIT_TAIL
+        default: break;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_cgs_dot(int64_t n, const double *__restrict__ V, int64_t ldv, int nvec, const double *__restrict__ w,
+          double *partial, int ldp, int with_norm, const int *gate) {
+    if (gate && *gate == 0) return;
+    __shared__ double red[kThreads / 32][kCH + 1];
+    int q0 = 0;
+    for (; nvec - q0 >= kCH; q0 += kCH) dot_chunk<kCH, false>(n, V, ldv, q0, w, partial, ldp, nvec, red);
+    if (with_norm) dot_tail<true>(nvec - q0, n, V, ldv, q0, w, partial, ldp, nvec, red);
+    else dot_tail<false>(nvec - q0, n, V, ldv, q0, w, partial, ldp, nvec, red);
+}
+
+// Classical Gram-Schmidt pass, update: w -= V h over q < nvec, and
+// partial[b] = ||w||^2 of the updated rows of block b.
+__global__ void __launch_bounds__(kThreads)
+k_cgs_update(int64_t n, const double *__restrict__ V, int64_t ldv, int nvec, const double *__restrict__ h,
+             double *w, double *partial, const int *gate) {
+    if (gate && *gate == 0) return;
+    __shared__ double hs[kMaxRestart + 1];
+    for (int q = threadIdx.x; q < nvec; q += kThreads) hs[q] = h[q];
+    __syncthreads();
+    double nrm = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;  // four chains: FP64 latency is long
+        int q = 0;
+        for (; q + 4 <= nvec; q += 4) {
+            const double v0 = __ldg(V + (int64_t)q * ldv + i), v1 = __ldg(V + (int64_t)(q + 1) * ldv + i);
+            const double v2 = __ldg(V + (int64_t)(q + 2) * ldv + i), v3 = __ldg(V + (int64_t)(q + 3) * ldv + i);
+            s0 = fma(v0, hs[q], s0);
+            s1 = fma(v1, hs[q + 1], s1);
+            s2 = fma(v2, hs[q + 2], s2);
+            s3 = fma(v3, hs[q + 3], s3);
+        }
+        for (; q < nvec; q++) s0 = fma(__ldg(V + (int64_t)q * ldv + i), hs[q], s0);
+        const double wi = w[i] - ((s0 + s1) + (s2 + s3));
+        w[i] = wi;
+        nrm = fma(wi, wi, nrm);
+    }
+    nrm = block_sum(nrm);
+    if (threadIdx.x == 0) partial[blockIdx.x] = nrm;
+}
+
+// After the first pass: store the coefficients in column j of H and decide
+// whether to reorthogonalise (Daniel, Gragg, Kaufman, Stewart 1976: a second
+// pass when the norm dropped below eta times its value before the pass).
+__global__ void k_cgs_decide(Scal *sc, double *Hj, const double *h, int nv, double eta2) {
+    if (sc->active == 0) {
+        sc->reorth = 0;
+        return;
+    }
+    for (int q = 0; q < nv; q++) Hj[q] = h[q];
+    const double before = h[nv], after = sc->r0;
+    sc->reorth = after < eta2 * before ? 1 : 0;
+    sc->nreorth += sc->reorth;
 }
 
 // w -= V h (sub = true) or w = V h (sub = false); nvec from *nvec_dev if given.
@@ -318,7 +400,8 @@ __global__ void k_bicg_check_r(Scal *sc, int remaining) {  // after (r, r) in r0
 // ---- host helpers ---------------------------------------------------------------
 struct Work {
     int nb = 1;
-    double *partial = nullptr;
+    double *partial = nullptr;   // nb x ldp
+    double *partial2 = nullptr;  // nb
 };
 
 cudaError_t dots(sait_ctx ctx, const Work &W, int64_t n, int nd, const double *x0, const double *y0,
@@ -377,27 +460,29 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
     const int64_t n = A->n;
     const int m = restart;
     cudaStream_t s = ctx->stream;
-    sait_info inf{0, 0, 0.0};
+    sait_info inf{0, 0, 0, 0, 0.0};
     if (info) *info = inf;
     if (n == 0) return SAIT_OK;
 
     Work W;
-    W.nb = (int)std::min<int64_t>(cdiv(n, kThreads), 2LL * ctx->num_sms);
-    const int ldp = m + 1;
-    DTemp<double> V, H, cs, sn, g, y, z, u, part;
+    W.nb = (int)std::min<int64_t>(cdiv(n, kThreads), 4LL * ctx->num_sms);
+    const int ldp = m + 2;
+    DTemp<double> V, H, cs, sn, g, y, z, u, part, part2;
     DTemp<Scal> scd;
     SAIT_CK(V.alloc((size_t)(m + 1) * n, s));
     SAIT_CK(H.alloc((size_t)(m + 1) * m, s));
     SAIT_CK(cs.alloc(m, s));
     SAIT_CK(sn.alloc(m, s));
     SAIT_CK(g.alloc(m + 1, s));
-    SAIT_CK(y.alloc(m + 1, s));
+    SAIT_CK(y.alloc(m + 2, s));
     SAIT_CK(z.alloc(n, s));
     SAIT_CK(u.alloc(n, s));
     SAIT_CK(part.alloc((size_t)W.nb * std::max(ldp, 3), s));
+    SAIT_CK(part2.alloc((size_t)W.nb, s));
     SAIT_CK(scd.alloc(1, s));
     SAIT_CK(cudaMemsetAsync(scd.p, 0, sizeof(Scal), s));
     W.partial = part.p;
+    W.partial2 = part2.p;
     Scal *sc = scd.p;
     const int *act = &sc->active;
     double *r0 = &sc->r0;
@@ -452,16 +537,27 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
             {
                 ScopedTimer tm(ctx, SAIT_TIMER_ORTHO);
                 double *Hj = H.p + (size_t)j * (m + 1);
-                for (int pass = 0; pass < 2; pass++) {  // classical Gram-Schmidt, twice
-                    launch_k(k_mdot, W.nb, kThreads, 0, s, n, V.p, n, j + 1, w, W.partial, ldp, act);
-                    launch_k(k_reduce, j + 1, kThreads, 0, s, W.partial, W.nb, ldp, y.p, act);
-                    launch_k(k_hadd, 1, 128, 0, s, Hj, y.p, j + 1, pass == 0, act);
-                    launch_k(k_gemv, egrid, kThreads, 0, s, n, V.p, n, j + 1, nullptr, y.p, w, 1, act);
-                }
-                SAIT_CK(dots(ctx, W, n, 1, w, w, nullptr, nullptr, nullptr, nullptr, r0, act));
+                const int nv = j + 1;
+                const int *ro = &sc->reorth;
+                // first pass: h = V^T w and ||w||^2, then w -= V h and ||w||^2
+                launch_k(k_cgs_dot, W.nb, kThreads, 0, s, n, (const double *)V.p, (int64_t)n, nv,
+                         (const double *)w, W.partial, ldp, 1, act);
+                launch_k(k_reduce, nv + 1, kThreads, 0, s, (const double *)W.partial, W.nb, ldp, y.p, act);
+                launch_k(k_cgs_update, W.nb, kThreads, 0, s, n, (const double *)V.p, (int64_t)n, nv,
+                         (const double *)y.p, w, W.partial2, act);
+                launch_k(k_reduce, 1, kThreads, 0, s, (const double *)W.partial2, W.nb, 1, r0, act);
+                launch_k(k_cgs_decide, 1, 1, 0, s, sc, Hj, (const double *)y.p, nv, 0.5);
+                // second pass only where the first lost too much of the norm
+                launch_k(k_cgs_dot, W.nb, kThreads, 0, s, n, (const double *)V.p, (int64_t)n, nv,
+                         (const double *)w, W.partial, ldp, 0, ro);
+                launch_k(k_reduce, nv, kThreads, 0, s, (const double *)W.partial, W.nb, ldp, y.p, ro);
+                launch_k(k_hadd, 1, 128, 0, s, Hj, (const double *)y.p, nv, 0, ro);
+                launch_k(k_cgs_update, W.nb, kThreads, 0, s, n, (const double *)V.p, (int64_t)n, nv,
+                         (const double *)y.p, w, W.partial2, ro);
+                launch_k(k_reduce, 1, kThreads, 0, s, (const double *)W.partial2, W.nb, 1, r0, ro);
                 launch_k(k_givens, 1, 1, 0, s, j, m, remaining, H.p, cs.p, sn.p, g.p, sc,
                          group_counter(ctx, SAIT_TIMER_ORTHO));
-                launch_k(k_scale, egrid, kThreads, 0, s, n, w, w, sc, act);
+                launch_k(k_scale, egrid, kThreads, 0, s, n, (const double *)w, w, (const Scal *)sc, act);
             }
             SAIT_CK(cudaGetLastError());
             if ((j + 1) % poll == 0 || j + 1 == m) {
@@ -490,6 +586,8 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
     }
     inf.iters = iters;
     inf.cycles = cycles;
+    SAIT_TRY(read_scal(ctx, sc, &hs));
+    inf.reorth_steps = hs.nreorth;
     if (info) *info = inf;
     SAIT_CK(cudaStreamSynchronize(s));
     if (result != SAIT_OK) {
@@ -507,7 +605,7 @@ extern "C" sait_status sait_bicgstab(sait_ctx ctx, sait_mat A, sait_prec P, cons
     SAIT_TRY(check_solver_args(ctx, A, P, b, x, tol, maxit, "sait_bicgstab"));
     const int64_t n = A->n;
     cudaStream_t s = ctx->stream;
-    sait_info inf{0, 0, 0.0};
+    sait_info inf{0, 0, 0, 0, 0.0};
     if (info) *info = inf;
     if (n == 0) return SAIT_OK;
     Work W;

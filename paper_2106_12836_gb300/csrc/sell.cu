@@ -1,0 +1,212 @@
+// Sliced ELLPACK (SELL-32) copies of CSR matrices and their products.
+//
+// Rows are cut into slices of 32 consecutive rows (no reordering); slice s
+// stores its entries column-major, padded to the longest row of the slice:
+// entry k of row 32 s + l sits at soff[s] + 32 k + l.  Padding has column -1
+// and value 0 and is skipped.  A warp owns one slice and lane l one row, so
+// every load of columns and values is a full 128-byte (int32 / FP32) or
+// 256-byte (FP64) coalesced line, and four column slots are loaded before
+// they are used to keep enough bytes in flight per warp.  For the PDE factors
+// of the SAIT path, whose rows of a slice have almost the same length, the
+// padding costs 0.2-1% of the entries.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace {
+
+// column slots loaded ahead per lane: enough bytes in flight per warp for
+// 8-byte values with 4, for 4- and 2-byte values with 8
+template <typename TV> struct Ahead { static constexpr int value = 8; };
+template <> struct Ahead<double> { static constexpr int value = 4; };
+
+template <typename T> struct Acc;
+template <> struct Acc<double> { using type = double; };
+template <> struct Acc<float> { using type = float; };
+template <> struct Acc<__nv_bfloat16> { using type = float; };
+
+__device__ __forceinline__ double cvt(double v) { return v; }
+__device__ __forceinline__ float cvt(float v) { return v; }
+__device__ __forceinline__ float cvt(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+__device__ __forceinline__ double fmac(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmac(float a, float b, float c) { return fmaf(a, b, c); }
+
+// streaming loads: columns and values are read once per product
+__device__ __forceinline__ int32_t lds(const int32_t *p) { return __ldcs(p); }
+__device__ __forceinline__ double lds(const double *p) { return __ldcs(p); }
+__device__ __forceinline__ float lds(const float *p) { return __ldcs(p); }
+__device__ __forceinline__ __nv_bfloat16 lds(const __nv_bfloat16 *p) {
+    unsigned short u = __ldcs(reinterpret_cast<const unsigned short *>(p));
+    return __ushort_as_bfloat16(u);
+}
+
+template <typename TV, typename TX, typename TY>
+__global__ void __launch_bounds__(256)
+k_spmv_sell(int64_t n, int64_t nslices, const int64_t *__restrict__ soff, const int32_t *__restrict__ ci,
+            const TV *__restrict__ va, const TX *__restrict__ x, TY *__restrict__ y,
+            const int *__restrict__ active, int *calls) {
+    using A = typename Acc<TV>::type;
+    constexpr int kU = Ahead<TV>::value;
+    if (active && *active == 0) return;
+    if (calls && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(calls, 1);
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (s >= nslices) return;
+    const int64_t b = soff[s];
+    const int len = (int)((soff[s + 1] - b) >> 5);
+    const int32_t *c = ci + b + lane;
+    const TV *v = va + b + lane;
+    A acc = 0;
+    int k = 0;
+    for (; k + kU <= len; k += kU) {
+        int32_t cc[kU];
+        A vv[kU], xx[kU];
+#pragma unroll
+        for (int u = 0; u < kU; u++) {
+            cc[u] = lds(c + 32 * u);
+            vv[u] = (A)cvt(lds(v + 32 * u));
+        }
+#pragma unroll
+        for (int u = 0; u < kU; u++) xx[u] = cc[u] >= 0 ? (A)__ldg(x + cc[u]) : (A)0;
+#pragma unroll
+        for (int u = 0; u < kU; u++) acc = fmac(vv[u], xx[u], acc);
+        c += 32 * kU;
+        v += 32 * kU;
+    }
+    for (; k < len; k++) {
+        const int32_t cc = lds(c);
+        const A vv = (A)cvt(lds(v));
+        if (cc >= 0) acc = fmac(vv, (A)__ldg(x + cc), acc);
+        c += 32;
+        v += 32;
+    }
+    const int64_t row = s * 32 + lane;
+    if (row < n) y[row] = (TY)acc;
+}
+
+// slice lengths (in column slots) and the padded-entry count per slice
+__global__ void k_sell_len(int64_t n, int64_t nslices, const int32_t *__restrict__ rp, int64_t *slots) {
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (s >= nslices) return;
+    const int64_t row = s * 32 + lane;
+    int len = row < n ? rp[row + 1] - rp[row] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+    if (lane == 0) slots[s] = 32LL * len;
+}
+
+__device__ __forceinline__ void put(double *p, double v) { *p = v; }
+__device__ __forceinline__ void put(float *p, double v) { *p = (float)v; }
+__device__ __forceinline__ void put(__nv_bfloat16 *p, double v) { *p = __double2bfloat16(v); }
+
+template <typename TV>
+__global__ void k_sell_fill(int64_t n, int64_t nslices, const int32_t *__restrict__ rp,
+                            const int32_t *__restrict__ ci, const double *__restrict__ va,
+                            const int64_t *__restrict__ soff, int32_t *sci, TV *sva, bool fill_cols) {
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (s >= nslices) return;
+    const int64_t row = s * 32 + lane;
+    const int64_t b = soff[s];
+    const int len = (int)((soff[s + 1] - b) >> 5);
+    const int rb = row < n ? rp[row] : 0, re = row < n ? rp[row + 1] : 0;
+    for (int k = 0; k < len; k++) {
+        const int64_t dst = b + 32LL * k + lane;
+        const bool in = rb + k < re;
+        if (fill_cols) sci[dst] = in ? ci[rb + k] : -1;
+        put(sva + dst, in ? va[rb + k] : 0.0);
+    }
+}
+
+template <typename TV, typename TX, typename TY>
+cudaError_t sell_launch(const sait_mat_s *A, const TV *va, const TX *x, TY *y, const int *active,
+                        cudaStream_t s, int *calls) {
+    const unsigned grid = (unsigned)cdiv(A->nslices * 32, 256);
+    launch_k(k_spmv_sell<TV, TX, TY>, grid, 256, 0, s, A->n, A->nslices, (const int64_t *)A->soff,
+             (const int32_t *)A->sci, va, x, y, active, calls);
+    return cudaGetLastError();
+}
+
+template <typename TV>
+cudaError_t sell_xy(const sait_mat_s *A, const TV *va, const void *x, bool x_f32, void *y, bool y_f32,
+                    const int *active, cudaStream_t s, int *calls) {
+    if (x_f32) {
+        if (y_f32) return sell_launch(A, va, (const float *)x, (float *)y, active, s, calls);
+        return sell_launch(A, va, (const float *)x, (double *)y, active, s, calls);
+    }
+    if (y_f32) return sell_launch(A, va, (const double *)x, (float *)y, active, s, calls);
+    return sell_launch(A, va, (const double *)x, (double *)y, active, s, calls);
+}
+
+}  // namespace
+
+// Build the SELL-32 structure of M (when its padding stays below 20%) and the
+// value array of the requested storage precision.
+sait_status mat_prepare_sell(sait_ctx ctx, sait_mat M, sait_dtype store) {
+    cudaStream_t s = ctx->stream;
+    const int64_t n = M->n;
+    if (n == 0 || M->sell_rejected) return SAIT_OK;
+    const int64_t nslices = cdiv(n, 32);
+    const unsigned grid = (unsigned)cdiv(nslices * 32, 256);
+    if (!M->soff) {
+        DTemp<int64_t> slots;
+        SAIT_CK(slots.alloc(nslices, s));
+        int64_t *soff = nullptr;
+        SAIT_CK(cudaMalloc((void **)&soff, (nslices + 1) * sizeof(int64_t)));
+        launch_k(k_sell_len, grid, 256, 0, s, n, nslices, (const int32_t *)M->rp, slots.p);
+        cudaError_t e = scan_i64(slots.p, soff, nslices, s);
+        int64_t total = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&total, soff + nslices, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cudaFree(soff);
+            return ctx_cuda(ctx, e, "mat_prepare_sell", __FILE__, __LINE__);
+        }
+        if ((double)total > 1.2 * (double)std::max<int64_t>(M->nnz, 1)) {
+            cudaFree(soff);
+            M->sell_rejected = true;  // too ragged: products stay on CSR
+            return SAIT_OK;
+        }
+        M->soff = soff;
+        M->nslices = nslices;
+        M->sell_nnz = total;
+        SAIT_CK(cudaMalloc((void **)&M->sci, std::max<int64_t>(total, 1) * sizeof(int32_t)));
+        SAIT_CK(cudaMalloc((void **)&M->sva64, std::max<int64_t>(total, 1) * sizeof(double)));
+        launch_k(k_sell_fill<double>, grid, 256, 0, s, n, nslices, (const int32_t *)M->rp,
+                 (const int32_t *)M->ci, (const double *)M->va, (const int64_t *)M->soff, M->sci, M->sva64,
+                 true);
+        SAIT_CK(cudaGetLastError());
+    }
+    const int64_t total = M->sell_nnz;
+    if (store == SAIT_F32 && !M->sva32) {
+        SAIT_CK(cudaMalloc((void **)&M->sva32, std::max<int64_t>(total, 1) * sizeof(float)));
+        launch_k(k_sell_fill<float>, grid, 256, 0, s, n, nslices, (const int32_t *)M->rp,
+                 (const int32_t *)M->ci, (const double *)M->va, (const int64_t *)M->soff, M->sci, M->sva32,
+                 false);
+        SAIT_CK(cudaGetLastError());
+    } else if (store == SAIT_BF16 && !M->sva16) {
+        SAIT_CK(cudaMalloc((void **)&M->sva16, std::max<int64_t>(total, 1) * sizeof(__nv_bfloat16)));
+        launch_k(k_sell_fill<__nv_bfloat16>, grid, 256, 0, s, n, nslices, (const int32_t *)M->rp,
+                 (const int32_t *)M->ci, (const double *)M->va, (const int64_t *)M->soff, M->sci, M->sva16,
+                 false);
+        SAIT_CK(cudaGetLastError());
+    }
+    return SAIT_OK;
+}
+
+bool sell_ready(const sait_mat_s *A, sait_dtype store) {
+    if (!A->soff) return false;
+    return store == SAIT_F64 ? A->sva64 != nullptr : store == SAIT_F32 ? A->sva32 != nullptr
+                                                                          : A->sva16 != nullptr;
+}
+
+cudaError_t launch_spmv_sell(const sait_mat_s *A, sait_dtype store, const void *x, bool x_f32, void *y,
+                             bool y_f32, const int *active, cudaStream_t s, int *calls) {
+    switch (store) {
+        case SAIT_F32: return sell_xy(A, A->sva32, x, x_f32, y, y_f32, active, s, calls);
+        case SAIT_BF16: return sell_xy(A, A->sva16, x, x_f32, y, y_f32, active, s, calls);
+        default: return sell_xy(A, A->sva64, x, x_f32, y, y_f32, active, s, calls);
+    }
+}
