@@ -209,8 +209,7 @@ sait_status mat_prepare_store(sait_ctx ctx, sait_mat M, sait_dtype store) {
     return SAIT_OK;
 }
 
-extern "C" sait_status sait_mat_create_csr(sait_ctx ctx, const sait_csr *A, sait_mat *out) {
-    if (!ctx) return SAIT_ERR_INVALID_ARG;
+sait_status mat_copy_csr(sait_ctx ctx, const sait_csr *A, sait_mat *out) {
     if (!A || !out) return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_mat_create_csr: null argument");
     *out = nullptr;
     if (A->n < 0 || A->nnz < 0 || A->nnz >= INT_MAX || A->n >= INT_MAX || !A->row_ptr ||
@@ -238,6 +237,15 @@ extern "C" sait_status sait_mat_create_csr(sait_ctx ctx, const sait_csr *A, sait
         sait_mat_destroy(M);
         return ctx_cuda(ctx, e, "sait_mat_create_csr", __FILE__, __LINE__);
     }
+    *out = M;
+    return SAIT_OK;
+}
+
+extern "C" sait_status sait_mat_create_csr(sait_ctx ctx, const sait_csr *A, sait_mat *out) {
+    if (!ctx) return SAIT_ERR_INVALID_ARG;
+    sait_mat M = nullptr;
+    SAIT_TRY(mat_copy_csr(ctx, A, &M));
+    cudaStream_t s = ctx->stream;
     sait_status st = mat_prepare_store(ctx, M, SAIT_F64);
     if (st == SAIT_OK && cudaStreamSynchronize(s) != cudaSuccess)
         st = ctx_cuda(ctx, cudaGetLastError(), "sait_mat_create_csr", __FILE__, __LINE__);

@@ -89,21 +89,38 @@ __global__ void k_identity(int64_t n, int64_t *off, int32_t *cnt, int32_t *ci, d
     va[i] = 1.0;
 }
 
+// Row bins by the symbolic bound u (products + 1): 0: u <= 8, 1: u <= 16,
+// 2: u <= 32 (register kernels, lanes hold one product each), 3: u <= kWarpMaxUb
+// (shared-memory hash), 4: longer rows (dense accumulator).  Masked iterations
+// of the pattern rule use the hash and dense kernels only.
+constexpr int kBins = 5;
+
 __global__ void k_rowub(int64_t n, const int32_t *__restrict__ tt_rp,
                         const int32_t *__restrict__ tt_ci, const int32_t *__restrict__ m_cnt,
                         int masked, const int32_t *__restrict__ s_cnt, int64_t *__restrict__ ub,
-                        int *ovf_count, int32_t *__restrict__ ovf_rows) {
+                        int *bin_count, int32_t *__restrict__ bin_rows) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int64_t u;
+    int bin;
     if (masked) {
         u = s_cnt ? s_cnt[i] : 1;
+        bin = u <= kWarpMaxUb ? 3 : 4;
     } else {
         u = 1;
         for (int e = tt_rp[i]; e < tt_rp[i + 1]; e++) u += m_cnt[tt_ci[e]];
+        bin = u <= 8 ? 0 : u <= 16 ? 1 : u <= 32 ? 2 : u <= kWarpMaxUb ? 3 : 4;
     }
     ub[i] = u;
-    if (u > kWarpMaxUb) ovf_rows[atomicAdd(ovf_count, 1)] = (int32_t)i;
+    // warp-aggregated append: one atomic per (warp, bin)
+    const unsigned act = __activemask();
+    const unsigned peers = __match_any_sync(act, bin);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(bin_count + bin, __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    bin_rows[(int64_t)bin * n + base + __popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
 }
 
 __device__ __forceinline__ int hslot(int32_t j, int logcap) {
@@ -143,7 +160,7 @@ __device__ __forceinline__ double warp_max(double v) {
 // One warp per output row (rows with bound <= kWarpMaxUb).
 template <bool MASKED>
 __global__ void __launch_bounds__(kWarps * 32)
-k_spgemm_warp(int64_t n, const int32_t *__restrict__ tt_rp, const int32_t *__restrict__ tt_ci,
+k_spgemm_warp(int nrows, const int32_t *__restrict__ rows, const int32_t *__restrict__ tt_rp, const int32_t *__restrict__ tt_ci,
               const double *__restrict__ tt_va, const int64_t *__restrict__ m_off,
               const int32_t *__restrict__ m_cnt, const int32_t *__restrict__ m_ci,
               const double *__restrict__ m_va, const int64_t *__restrict__ s_off,
@@ -160,10 +177,9 @@ k_spgemm_warp(int64_t n, const int32_t *__restrict__ tt_rp, const int32_t *__res
     const unsigned lt_mask = (1u << lane) - 1u;
     const bool thresholded = (kind == kDropAbs || kind == kDropRowRel);
 
-    for (int64_t i = (int64_t)blockIdx.x * kWarps + warp; i < n;
-         i += (int64_t)gridDim.x * kWarps) {
+    for (int r = blockIdx.x * kWarps + warp; r < nrows; r += gridDim.x * kWarps) {
+        const int32_t i = rows[r];
         const int64_t u = ub[i];
-        if (u > kWarpMaxUb) continue;
         int logcap = 5;
         while ((1 << logcap) < 2 * u) logcap++;
         const int cap = 1 << logcap;
@@ -262,6 +278,111 @@ k_spgemm_warp(int64_t n, const int32_t *__restrict__ tt_rp, const int32_t *__res
         if (lane == 0) o_cnt[i] = cnt;
         __syncwarp();
     }
+}
+
+// Register-resident product for short rows: a group of W lanes owns one
+// row, lane p holds the p-th product T~_ik (M D)_kj in the order (k ascending,
+// then j ascending), the lane after the last product holds the diagonal.  A
+// stable sort by column (ranks from shuffles) puts the products of one column
+// next to each other in ascending k; a segmented chain then forms
+// acc_j = fma(T~_ik, (MD)_kj, acc_j) in that order -- the oracle's chain.
+template <int W>
+__global__ void __launch_bounds__(256)
+k_spgemm_reg(int nrows, const int32_t *__restrict__ rows, const int32_t *__restrict__ tt_rp,
+             const int32_t *__restrict__ tt_ci, const double *__restrict__ tt_va,
+             const int64_t *__restrict__ m_off, const int32_t *__restrict__ m_cnt,
+             const int32_t *__restrict__ m_ci, const double *__restrict__ m_va,
+             const int64_t *__restrict__ o_off, int32_t *__restrict__ o_cnt, int32_t *__restrict__ o_ci,
+             double *__restrict__ o_va, int kind, double tau, const double *__restrict__ dinv_scale) {
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = gt / W;
+    if (g >= nrows) return;  // whole groups leave together
+    const int gl = threadIdx.x & (W - 1);
+    const int gbase = (threadIdx.x & 31) & ~(W - 1);
+    const unsigned gmask = W == 32 ? 0xffffffffu : (((1u << W) - 1u) << gbase);
+    const unsigned lt = (1u << gl) - 1u;
+    const int i = rows[g];
+    const int tb = tt_rp[i], nt = tt_rp[i + 1] - tb;
+    int kk = 0, cnt = 0;
+    int64_t off = 0;
+    double t = 0.0;
+    if (gl < nt) {
+        kk = tt_ci[tb + gl];
+        t = tt_va[tb + gl];
+        off = m_off[kk];
+        cnt = m_cnt[kk];
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < W; o <<= 1) {
+        const int v = __shfl_up_sync(gmask, incl, o, W);
+        if (gl >= o) incl += v;
+    }
+    const int start = incl - cnt;
+    const int pc = __shfl_sync(gmask, incl, W - 1, W);  // number of products (< W)
+    int my_e = 0;
+    for (int e2 = 0; e2 < nt; e2++) {
+        const int st = __shfl_sync(gmask, start, e2, W);
+        if (st <= gl) my_e = e2;
+    }
+    const double t_my = __shfl_sync(gmask, t, my_e, W);
+    const int64_t off_my = __shfl_sync(gmask, off, my_e, W);
+    const int start_my = __shfl_sync(gmask, start, my_e, W);
+    int key = INT_MAX;
+    double mv = 0.0;
+    if (gl < pc) {
+        key = m_ci[off_my + gl - start_my];
+        mv = m_va[off_my + gl - start_my];
+    } else if (gl == pc) {
+        key = i;  // + I
+    }
+    // stable ranks by column
+    int rank = 0;
+#pragma unroll
+    for (int q = 0; q < W; q++) {
+        const int kq = __shfl_sync(gmask, key, q, W);
+        rank += (kq < key) || (kq == key && q < gl);
+    }
+    int src = 0;
+#pragma unroll
+    for (int q = 0; q < W; q++) {
+        const int rq = __shfl_sync(gmask, rank, q, W);
+        if (rq == gl) src = q;
+    }
+    const int skey = __shfl_sync(gmask, key, src, W);
+    const double st_ = __shfl_sync(gmask, t_my, src, W);
+    const double sm = __shfl_sync(gmask, mv, src, W);
+    const bool sdiag = __shfl_sync(gmask, (int)(gl == pc), src, W) != 0;
+    const int prev_key = __shfl_up_sync(gmask, skey, 1, W);
+    const bool head = gl == 0 || prev_key != skey;
+    const unsigned heads = (__ballot_sync(gmask, head) >> gbase) & (W == 32 ? 0xffffffffu : ((1u << W) - 1u));
+    const int hpos = 31 - __clz(heads & (lt | (1u << gl)));
+    const int pos = gl - hpos;
+    double acc = 0.0;
+    if (sdiag) acc = 0.0 + 1.0;
+    else if (pos == 0 && skey != INT_MAX) acc = fma(st_, sm, 0.0);
+    for (int step = 1; step < nt; step++) {
+        const double prev = __shfl_up_sync(gmask, acc, 1, W);
+        if (pos == step && !sdiag) acc = fma(st_, sm, prev);
+    }
+    const int next_key = __shfl_down_sync(gmask, skey, 1, W);
+    const bool tail = skey != INT_MAX && (gl == W - 1 || next_key != skey);
+    double thr = tau;
+    if (kind == kDropRowRel) {
+        double mx = tail ? fabs(acc) : 0.0;
+#pragma unroll
+        for (int o = W / 2; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(gmask, mx, o, W));
+        thr = tau * mx;
+    }
+    bool keep = tail;
+    if (keep && (kind == kDropAbs || kind == kDropRowRel) && skey != i) keep = !(fabs(acc) < thr);
+    const unsigned km = (__ballot_sync(gmask, keep) >> gbase) & (W == 32 ? 0xffffffffu : ((1u << W) - 1u));
+    if (keep) {
+        const int64_t dst = o_off[i] + __popc(km & lt);
+        o_ci[dst] = skey;
+        o_va[dst] = dinv_scale ? acc * dinv_scale[skey] : acc;
+    }
+    if (gl == 0) o_cnt[i] = __popc(km);
 }
 
 // Exclusive scan of a 0/1 flag over a block of kDenseThreads threads.
@@ -464,7 +585,7 @@ extern "C" sait_status sait_build(sait_ctx ctx, sait_mat T, sait_uplo uplo, int3
     cudaStream_t s = ctx->stream;
     ScopedTimer tm(ctx, SAIT_TIMER_BUILD);
     int *h = (int *)ctx->h_pinned;
-    int64_t *h64 = (int64_t *)ctx->h_pinned;
+    int64_t *h64 = (int64_t *)((char *)ctx->h_pinned + 256);  // apart from the int words
 
     // ---- split and validate
     DTemp<double> dinv;
@@ -520,9 +641,12 @@ extern "C" sait_status sait_build(sait_ctx ctx, sait_mat T, sait_uplo uplo, int3
         const bool pattern = drop.kind == SAIT_DROP_PATTERN;
 
         DTemp<int64_t> ub;
-        DTemp<int32_t> ovf;
+        DTemp<int32_t> bins;  // kBins row lists of up to n rows each
         SAIT_CK(ub.alloc(n, s));
-        SAIT_CK(ovf.alloc(n, s));
+        SAIT_CK(bins.alloc((size_t)kBins * n, s));
+        int *bin_count = ctx->d_word + kWordBins;
+        int *hash_err = ctx->d_word + kWordBuildErr;
+        SAIT_CK(cudaMemsetAsync(hash_err, 0, sizeof(int), s));
         for (int it = 1; it < m_terms; it++) {
             const bool masked = pattern && it > drop.p;
             const int kind = pattern ? kDropNone : (int)drop.kind;
@@ -530,38 +654,56 @@ extern "C" sait_status sait_build(sait_ctx ctx, sait_mat T, sait_uplo uplo, int3
             const int32_t *s_cnt = masked && have_S ? S.cnt.p : nullptr;
             const int64_t *s_off = masked && have_S ? S.off.p : nullptr;
             const int32_t *s_ci = masked && have_S ? S.ci.p : nullptr;
-            SAIT_CK(cudaMemsetAsync(ctx->d_word, 0, sizeof(int), s));
+            SAIT_CK(cudaMemsetAsync(bin_count, 0, kBins * sizeof(int), s));
             if (n > 0)
-                launch_k(k_rowub, (unsigned)cdiv(n, 256), 256, 0, s, n, tt_rp.p, tt_ci.p, cur.cnt, masked,
-                                                                s_cnt, ub.p, ctx->d_word, ovf.p);
+                launch_k(k_rowub, (unsigned)cdiv(n, 256), 256, 0, s, n, (const int32_t *)tt_rp.p,
+                         (const int32_t *)tt_ci.p, cur.cnt, (int)masked, s_cnt, ub.p, bin_count, bins.p);
             SAIT_CK(cudaGetLastError());
             Iterate nx;
             SAIT_CK(nx.off.alloc(n + 1, s));
             SAIT_CK(scan_i64(ub.p, nx.off.p, n, s));
             SAIT_CK(cudaMemcpyAsync(h64, nx.off.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-            SAIT_CK(cudaMemcpyAsync(h + 2, ctx->d_word, sizeof(int), cudaMemcpyDeviceToHost, s));
+            SAIT_CK(cudaMemcpyAsync(h + 4, bin_count, kBins * sizeof(int), cudaMemcpyDeviceToHost, s));
             SAIT_CK(cudaStreamSynchronize(s));
             const int64_t total = h64[0];
-            const int novf = h[2];
+            int nbin[kBins];
+            for (int q = 0; q < kBins; q++) nbin[q] = h[4 + q];
             SAIT_CK(nx.cnt.alloc(n, s));
             SAIT_CK(nx.ci.alloc(total, s));
             SAIT_CK(nx.va.alloc(total, s));
             const double *scale = last ? dinv.p : nullptr;
             const double tau = drop.tau;
-            if (n > 0) {
-                unsigned grid = (unsigned)std::min<int64_t>(cdiv(n, kWarps), (int64_t)ctx->num_sms * 4);
+            const int32_t *rows0 = bins.p, *rows1 = bins.p + n, *rows2 = bins.p + 2 * n;
+            const int32_t *rows3 = bins.p + 3 * n, *rows4 = bins.p + 4 * n;
+            // short rows: register kernels (never masked)
+            launch_k(k_spgemm_reg<8>, (unsigned)cdiv((int64_t)nbin[0] * 8, 256), 256, 0, s, nbin[0], rows0,
+                     (const int32_t *)tt_rp.p, (const int32_t *)tt_ci.p, (const double *)tt_va.p, cur.off,
+                     cur.cnt, cur.ci, cur.va, (const int64_t *)nx.off.p, nx.cnt.p, nx.ci.p, nx.va.p, kind, tau,
+                     scale);
+            launch_k(k_spgemm_reg<16>, (unsigned)cdiv((int64_t)nbin[1] * 16, 256), 256, 0, s, nbin[1], rows1,
+                     (const int32_t *)tt_rp.p, (const int32_t *)tt_ci.p, (const double *)tt_va.p, cur.off,
+                     cur.cnt, cur.ci, cur.va, (const int64_t *)nx.off.p, nx.cnt.p, nx.ci.p, nx.va.p, kind, tau,
+                     scale);
+            launch_k(k_spgemm_reg<32>, (unsigned)cdiv((int64_t)nbin[2] * 32, 256), 256, 0, s, nbin[2], rows2,
+                     (const int32_t *)tt_rp.p, (const int32_t *)tt_ci.p, (const double *)tt_va.p, cur.off,
+                     cur.cnt, cur.ci, cur.va, (const int64_t *)nx.off.p, nx.cnt.p, nx.ci.p, nx.va.p, kind, tau,
+                     scale);
+            SAIT_CK(cudaGetLastError());
+            if (nbin[3] > 0) {
+                const unsigned grid = (unsigned)std::min<int64_t>(cdiv(nbin[3], kWarps), (int64_t)ctx->num_sms * 4);
                 if (masked)
-                    launch_k(k_spgemm_warp<true>, grid, kWarps * 32, smem, s, 
-                        n, tt_rp.p, tt_ci.p, tt_va.p, cur.off, cur.cnt, cur.ci, cur.va, s_off, s_cnt,
-                        s_ci, ub.p, nx.off.p, nx.cnt.p, nx.ci.p, nx.va.p, kind, tau, scale,
-                        ctx->d_word + 1);
+                    launch_k(k_spgemm_warp<true>, grid, kWarps * 32, smem, s, nbin[3], rows3,
+                             (const int32_t *)tt_rp.p, (const int32_t *)tt_ci.p, (const double *)tt_va.p, cur.off,
+                             cur.cnt, cur.ci, cur.va, s_off, s_cnt, s_ci, (const int64_t *)ub.p,
+                             (const int64_t *)nx.off.p, nx.cnt.p, nx.ci.p, nx.va.p, kind, tau, scale, hash_err);
                 else
-                    launch_k(k_spgemm_warp<false>, grid, kWarps * 32, smem, s, 
-                        n, tt_rp.p, tt_ci.p, tt_va.p, cur.off, cur.cnt, cur.ci, cur.va, s_off, s_cnt,
-                        s_ci, ub.p, nx.off.p, nx.cnt.p, nx.ci.p, nx.va.p, kind, tau, scale,
-                        ctx->d_word + 1);
+                    launch_k(k_spgemm_warp<false>, grid, kWarps * 32, smem, s, nbin[3], rows3,
+                             (const int32_t *)tt_rp.p, (const int32_t *)tt_ci.p, (const double *)tt_va.p, cur.off,
+                             cur.cnt, cur.ci, cur.va, s_off, s_cnt, s_ci, (const int64_t *)ub.p,
+                             (const int64_t *)nx.off.p, nx.cnt.p, nx.ci.p, nx.va.p, kind, tau, scale, hash_err);
                 SAIT_CK(cudaGetLastError());
             }
+            const int novf = nbin[4];
             if (novf > 0) {
                 // dense accumulators, bounded to about 2 GB of scratch
                 const int64_t per = n * (int64_t)(sizeof(double) + sizeof(uint32_t));
@@ -573,15 +715,15 @@ extern "C" sait_status sait_build(sait_ctx ctx, sait_mat T, sait_uplo uplo, int3
                 SAIT_CK(stp.alloc(nb * n, s));
                 SAIT_CK(cudaMemsetAsync(stp.p, 0xff, nb * n * sizeof(uint32_t), s));
                 if (masked)
-                    launch_k(k_spgemm_dense<true>, (unsigned)nb, kDenseThreads, 0, s, 
-                        novf, ovf.p, n, tt_rp.p, tt_ci.p, tt_va.p, cur.off, cur.cnt, cur.ci, cur.va,
-                        s_off, s_cnt, s_ci, nx.off.p, nx.cnt.p, nx.ci.p, nx.va.p, kind, tau, scale,
-                        acc.p, stp.p);
+                    launch_k(k_spgemm_dense<true>, (unsigned)nb, kDenseThreads, 0, s, novf, rows4, n,
+                             (const int32_t *)tt_rp.p, (const int32_t *)tt_ci.p, (const double *)tt_va.p, cur.off,
+                             cur.cnt, cur.ci, cur.va, s_off, s_cnt, s_ci, (const int64_t *)nx.off.p, nx.cnt.p,
+                             nx.ci.p, nx.va.p, kind, tau, scale, acc.p, stp.p);
                 else
-                    launch_k(k_spgemm_dense<false>, (unsigned)nb, kDenseThreads, 0, s, 
-                        novf, ovf.p, n, tt_rp.p, tt_ci.p, tt_va.p, cur.off, cur.cnt, cur.ci, cur.va,
-                        s_off, s_cnt, s_ci, nx.off.p, nx.cnt.p, nx.ci.p, nx.va.p, kind, tau, scale,
-                        acc.p, stp.p);
+                    launch_k(k_spgemm_dense<false>, (unsigned)nb, kDenseThreads, 0, s, novf, rows4, n,
+                             (const int32_t *)tt_rp.p, (const int32_t *)tt_ci.p, (const double *)tt_va.p, cur.off,
+                             cur.cnt, cur.ci, cur.va, s_off, s_cnt, s_ci, (const int64_t *)nx.off.p, nx.cnt.p,
+                             nx.ci.p, nx.va.p, kind, tau, scale, acc.p, stp.p);
                 SAIT_CK(cudaGetLastError());
             }
             move_iterate(owned, nx);   // frees the previous owned iterate (stream-ordered)
@@ -594,7 +736,7 @@ extern "C" sait_status sait_build(sait_ctx ctx, sait_mat T, sait_uplo uplo, int3
         }
         const View fin = cur;
         // compaction into CSR
-        SAIT_CK(cudaMemcpyAsync(h + 3, ctx->d_word + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SAIT_CK(cudaMemcpyAsync(h + 3, ctx->d_word + kWordBuildErr, sizeof(int), cudaMemcpyDeviceToHost, s));
         DTemp<int64_t> rp64;
         SAIT_CK(rp64.alloc(n + 1, s));
         SAIT_CK(scan_i32(fin.cnt, rp64.p, n, s));

@@ -10,8 +10,12 @@
 
 #include "sait.h"
 
-// d_word layout: [0..15] error flags and scratch, [16 + g] device-side call
-// counters of timer group g (incremented by kernels that did real work).
+// d_word layout: [0] per-call error flags, [1] ILU(0) row ticket, [2..6] SpGEMM
+// row-bin counters, [8..9] level analysis, [10] SpGEMM error flags, [16 + g]
+// device-side call counters of timer group g (incremented by kernels that did
+// real work).
+constexpr int kWordBins = 2;
+constexpr int kWordBuildErr = 10;
 constexpr int kCounterBase = 16;
 
 struct TimerRec {
@@ -164,10 +168,11 @@ sait_status build_levels(sait_ctx ctx, const int32_t *rp, const int32_t *ci, int
 void free_levels(LevelSchedule *L);
 cudaError_t launch_trisolve(const sait_mat_s *T, const LevelSchedule &lev, bool lower,
                             const double *b, double *x, cudaStream_t s);
-sait_status ilu0_levels(sait_ctx ctx, const int32_t *rp, const int32_t *ci, double *lu, int64_t n,
-                        const LevelSchedule &lev);
+sait_status frontier_schedule(sait_ctx ctx, const int32_t *rp, const int32_t *ci, int64_t n, bool lower,
+                              const int32_t *dpos, double *a, int *err_word, LevelSchedule *out);
 
 // mat helpers (api.cu)
+sait_status mat_copy_csr(sait_ctx ctx, const sait_csr *A, sait_mat *out);  // validated copy, CSR only
 sait_status mat_alloc(sait_ctx ctx, int64_t n, int64_t nnz, sait_mat *out);
 sait_status mat_prepare_store(sait_ctx ctx, sait_mat M, sait_dtype store);
 sait_status prec_apply_impl(sait_ctx ctx, sait_prec P, const double *r, double *z,

@@ -22,12 +22,10 @@ struct Scal {        // device-resident solver scalars
     int active;      // 1 while the current cycle / iteration runs
     int jdone;       // GMRES: Arnoldi steps done in this cycle; BiCGSTAB: iterations done
     int state;       // 0 running, 1 converged, 2 breakdown, 3 non-finite, 4 x updated (half step)
-    int reorth;      // GMRES: 1 when the current step needs a second Gram-Schmidt pass
+    int pad;
     double bnorm, beta, tolb, inv;
     double rho, rho_old, alpha, omega, beta_b;
     double r0, r1, r2, r3;    // reduction results
-    int nreorth;              // GMRES: steps that took a second Gram-Schmidt pass
-    int pad2;
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -82,35 +80,45 @@ k_reduce(const double *__restrict__ partial, int nb, int stride, double *out, co
     if (threadIdx.x == 0) out[q] = s;
 }
 
-// Classical Gram-Schmidt pass, dots: partial[b*ldp + q] = sum over block b's
-// rows of V_q . w for q < nvec, and partial[b*ldp + nvec] = w . w when
-// with_norm.  One thread per row with one register accumulator per vector of a
-// chunk (chunks of kCH; the last chunk is instantiated for its exact size so
-// no FP64 FMA slot is wasted -- FP64 throughput, not bandwidth, is the scarce
-// resource of these passes on GB300).  w is re-read from L2 for every chunk.
+// Classical Gram-Schmidt with two passes, split by precision.  On GB300 the
+// FP64 pipe (1.2 TFLOP/s measured) bounds these passes, not HBM, so:
+//   pass 1 dots   h1 = V^T w   FP32 products on an FP32 copy of the basis;
+//   pass 1 update w -= V h1    FP64 (this subtraction cancels);
+//   pass 2 dots   h2 = V^T w   FP64 (it measures what pass 1 left in span V);
+//   pass 2 update w -= V h2    FP32 products (h2 is ~1e-6 |w|, so the FP32
+//                              error of the correction is ~1e-13 |w|),
+// and H(:, j) = h1 + h2 in FP64.  Pass 2 removes the FP32 error of pass 1, so
+// the basis is orthogonal to FP64 level and the Arnoldi relation holds in FP64.
+//
+// Dots: partial[b*ldp + q] = sum over block b's rows of V_q . w (q < nvec),
+// partial[b*ldp + nvec] = w . w when NORM.  One thread per row, one register
+// accumulator per vector of a chunk; the last chunk is instantiated for its
+// exact size so no FMA slot is wasted.  w is re-read from L2 for each chunk.
 constexpr int kCH = 16;
 
-template <int CH, bool NORM>
-__device__ __forceinline__ void dot_chunk(int64_t n, const double *__restrict__ V, int64_t ldv, int q0,
+template <typename T, int CH, bool NORM>
+__device__ __forceinline__ void dot_chunk(int64_t n, const T *__restrict__ V, int64_t ldv, int q0,
                                           const double *__restrict__ w, double *partial, int ldp, int nvec,
                                           double (*red)[kCH + 1]) {
     constexpr int NA = CH + (NORM ? 1 : 0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double acc[NA > 0 ? NA : 1];
+    T acc[CH > 0 ? CH : 1];
+    double nacc = 0.0;
 #pragma unroll
-    for (int t = 0; t < NA; t++) acc[t] = 0.0;
+    for (int t = 0; t < (CH > 0 ? CH : 1); t++) acc[t] = (T)0;
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
-        const double wi = w[i];
-        double vv[CH > 0 ? CH : 1];
+        const double wd = w[i];
+        const T wi = (T)wd;
+        T vv[CH > 0 ? CH : 1];
 #pragma unroll
         for (int t = 0; t < CH; t++) vv[t] = __ldg(V + (int64_t)(q0 + t) * ldv + i);
 #pragma unroll
         for (int t = 0; t < CH; t++) acc[t] = fma(vv[t], wi, acc[t]);
-        if (NORM) acc[NA - 1] = fma(wi, wi, acc[NA - 1]);
+        if (NORM) nacc = fma(wd, wd, nacc);
     }
 #pragma unroll
     for (int t = 0; t < NA; t++) {
-        const double v = warp_sum(acc[t]);
+        const double v = warp_sum(t < CH ? (double)acc[t < CH ? t : 0] : nacc);
         if (lane == 0) red[warp][t] = v;
     }
     __syncthreads();
@@ -123,12 +131,11 @@ __device__ __forceinline__ void dot_chunk(int64_t n, const double *__restrict__ 
     __syncthreads();
 }
 
-template <bool NORM>
-__device__ __forceinline__ void dot_tail(int rem, int64_t n, const double *V, int64_t ldv, int q0,
-                                         const double *w, double *partial, int ldp, int nvec,
-                                         double (*red)[kCH + 1]) {
+template <typename T, bool NORM>
+__device__ __forceinline__ void dot_tail(int rem, int64_t n, const T *V, int64_t ldv, int q0, const double *w,
+                                         double *partial, int ldp, int nvec, double (*red)[kCH + 1]) {
     switch (rem) {
-#define SAIT_TAIL(k) case k: dot_chunk<k, NORM>(n, V, ldv, q0, w, partial, ldp, nvec, red); break;
+#define SAIT_TAIL(k) case k: dot_chunk<T, k, NORM>(n, V, ldv, q0, w, partial, ldp, nvec, red); break;
         SAIT_TAIL(0) SAIT_TAIL(1) SAIT_TAIL(2) SAIT_TAIL(3) SAIT_TAIL(4) SAIT_TAIL(5) SAIT_TAIL(6)
         SAIT_TAIL(7) SAIT_TAIL(8) SAIT_TAIL(9) SAIT_TAIL(10) SAIT_TAIL(11) SAIT_TAIL(12) SAIT_TAIL(13)
         SAIT_TAIL(14) SAIT_TAIL(15)
@@ -137,40 +144,42 @@ __device__ __forceinline__ void dot_tail(int rem, int64_t n, const double *V, in
     }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_cgs_dot(int64_t n, const double *__restrict__ V, int64_t ldv, int nvec, const double *__restrict__ w,
+k_cgs_dot(int64_t n, const T *__restrict__ V, int64_t ldv, int nvec, const double *__restrict__ w,
           double *partial, int ldp, int with_norm, const int *gate) {
     if (gate && *gate == 0) return;
     __shared__ double red[kThreads / 32][kCH + 1];
     int q0 = 0;
-    for (; nvec - q0 >= kCH; q0 += kCH) dot_chunk<kCH, false>(n, V, ldv, q0, w, partial, ldp, nvec, red);
-    if (with_norm) dot_tail<true>(nvec - q0, n, V, ldv, q0, w, partial, ldp, nvec, red);
-    else dot_tail<false>(nvec - q0, n, V, ldv, q0, w, partial, ldp, nvec, red);
+    for (; nvec - q0 >= kCH; q0 += kCH) dot_chunk<T, kCH, false>(n, V, ldv, q0, w, partial, ldp, nvec, red);
+    if (with_norm) dot_tail<T, true>(nvec - q0, n, V, ldv, q0, w, partial, ldp, nvec, red);
+    else dot_tail<T, false>(nvec - q0, n, V, ldv, q0, w, partial, ldp, nvec, red);
 }
 
-// Classical Gram-Schmidt pass, update: w -= V h over q < nvec, and
-// partial[b] = ||w||^2 of the updated rows of block b.
+// Update: w -= V h over q < nvec with products in T (V stored in T, h rounded
+// to T), and partial[b] = ||w||^2 (FP64) of the updated rows of block b.
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_cgs_update(int64_t n, const double *__restrict__ V, int64_t ldv, int nvec, const double *__restrict__ h,
+k_cgs_update(int64_t n, const T *__restrict__ V, int64_t ldv, int nvec, const double *__restrict__ h,
              double *w, double *partial, const int *gate) {
     if (gate && *gate == 0) return;
-    __shared__ double hs[kMaxRestart + 1];
-    for (int q = threadIdx.x; q < nvec; q += kThreads) hs[q] = h[q];
+    __shared__ T hs[kMaxRestart + 1];
+    for (int q = threadIdx.x; q < nvec; q += kThreads) hs[q] = (T)h[q];
     __syncthreads();
     double nrm = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;  // four chains: FP64 latency is long
+        T s0 = 0, s1 = 0, s2 = 0, s3 = 0;  // four chains: FP64 latency is long
         int q = 0;
         for (; q + 4 <= nvec; q += 4) {
-            const double v0 = __ldg(V + (int64_t)q * ldv + i), v1 = __ldg(V + (int64_t)(q + 1) * ldv + i);
-            const double v2 = __ldg(V + (int64_t)(q + 2) * ldv + i), v3 = __ldg(V + (int64_t)(q + 3) * ldv + i);
+            const T v0 = __ldg(V + (int64_t)q * ldv + i), v1 = __ldg(V + (int64_t)(q + 1) * ldv + i);
+            const T v2 = __ldg(V + (int64_t)(q + 2) * ldv + i), v3 = __ldg(V + (int64_t)(q + 3) * ldv + i);
             s0 = fma(v0, hs[q], s0);
             s1 = fma(v1, hs[q + 1], s1);
             s2 = fma(v2, hs[q + 2], s2);
             s3 = fma(v3, hs[q + 3], s3);
         }
         for (; q < nvec; q++) s0 = fma(__ldg(V + (int64_t)q * ldv + i), hs[q], s0);
-        const double wi = w[i] - ((s0 + s1) + (s2 + s3));
+        const double wi = w[i] - (double)((s0 + s1) + (s2 + s3));
         w[i] = wi;
         nrm = fma(wi, wi, nrm);
     }
@@ -178,18 +187,16 @@ k_cgs_update(int64_t n, const double *__restrict__ V, int64_t ldv, int nvec, con
     if (threadIdx.x == 0) partial[blockIdx.x] = nrm;
 }
 
-// After the first pass: store the coefficients in column j of H and decide
-// whether to reorthogonalise (Daniel, Gragg, Kaufman, Stewart 1976: a second
-// pass when the norm dropped below eta times its value before the pass).
-__global__ void k_cgs_decide(Scal *sc, double *Hj, const double *h, int nv, double eta2) {
-    if (sc->active == 0) {
-        sc->reorth = 0;
-        return;
+// v = w / ||w|| in FP64, plus its FP32 copy for the first Gram-Schmidt pass
+__global__ void k_scale2(int64_t n, const double *__restrict__ x, double *y, float *y32, const Scal *sc,
+                         const int *active) {
+    if (active && *active == 0) return;
+    const double a = sc->inv;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        const double v = x[i] * a;
+        y[i] = v;
+        y32[i] = (float)v;
     }
-    for (int q = 0; q < nv; q++) Hj[q] = h[q];
-    const double before = h[nv], after = sc->r0;
-    sc->reorth = after < eta2 * before ? 1 : 0;
-    sc->nreorth += sc->reorth;
 }
 
 // w -= V h (sub = true) or w = V h (sub = false); nvec from *nvec_dev if given.
@@ -222,14 +229,6 @@ k_residual(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict_
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (row < n && lane == 0) r[row] = b[row] - s;
-}
-
-// y = x * sc->inv
-__global__ void k_scale(int64_t n, const double *__restrict__ x, double *y, const Scal *sc, const int *active) {
-    if (active && *active == 0) return;
-    const double a = sc->inv;
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
-        y[i] = x[i] * a;
 }
 
 __global__ void k_axpy1(int64_t n, const double *__restrict__ x, double *y) {
@@ -468,8 +467,10 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
     W.nb = (int)std::min<int64_t>(cdiv(n, kThreads), 4LL * ctx->num_sms);
     const int ldp = m + 2;
     DTemp<double> V, H, cs, sn, g, y, z, u, part, part2;
+    DTemp<float> V32;  // FP32 copy of the basis for the first Gram-Schmidt pass
     DTemp<Scal> scd;
     SAIT_CK(V.alloc((size_t)(m + 1) * n, s));
+    SAIT_CK(V32.alloc((size_t)(m + 1) * n, s));
     SAIT_CK(H.alloc((size_t)(m + 1) * m, s));
     SAIT_CK(cs.alloc(m, s));
     SAIT_CK(sn.alloc(m, s));
@@ -524,7 +525,8 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
         if (!std::isfinite(hs.beta)) { result = SAIT_ERR_NONFINITE; break; }
         if (inf.rel_resid <= tol) { result = SAIT_OK; break; }
         if (iters >= maxit) break;
-        launch_k(k_scale, egrid, kThreads, 0, s, n, V.p, V.p, sc, nullptr);
+        launch_k(k_scale2, egrid, kThreads, 0, s, n, (const double *)V.p, V.p, V32.p, (const Scal *)sc,
+                 nullptr);
         const int remaining = maxit - iters;
         for (int j = 0; j < m; j++) {
             double *vj = V.p + (size_t)j * n, *w = V.p + (size_t)(j + 1) * n;
@@ -538,26 +540,25 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
                 ScopedTimer tm(ctx, SAIT_TIMER_ORTHO);
                 double *Hj = H.p + (size_t)j * (m + 1);
                 const int nv = j + 1;
-                const int *ro = &sc->reorth;
-                // first pass: h = V^T w and ||w||^2, then w -= V h and ||w||^2
-                launch_k(k_cgs_dot, W.nb, kThreads, 0, s, n, (const double *)V.p, (int64_t)n, nv,
-                         (const double *)w, W.partial, ldp, 1, act);
-                launch_k(k_reduce, nv + 1, kThreads, 0, s, (const double *)W.partial, W.nb, ldp, y.p, act);
-                launch_k(k_cgs_update, W.nb, kThreads, 0, s, n, (const double *)V.p, (int64_t)n, nv,
+                // pass 1: FP32 dots, FP64 update
+                launch_k(k_cgs_dot<float>, W.nb, kThreads, 0, s, n, (const float *)V32.p, (int64_t)n, nv,
+                         (const double *)w, W.partial, ldp, 0, act);
+                launch_k(k_reduce, nv, kThreads, 0, s, (const double *)W.partial, W.nb, ldp, y.p, act);
+                launch_k(k_hadd, 1, 128, 0, s, Hj, (const double *)y.p, nv, 1, act);
+                launch_k(k_cgs_update<double>, W.nb, kThreads, 0, s, n, (const double *)V.p, (int64_t)n, nv,
+                         (const double *)y.p, w, W.partial2, act);
+                // pass 2: FP64 dots, FP32 update, ||w||^2
+                launch_k(k_cgs_dot<double>, W.nb, kThreads, 0, s, n, (const double *)V.p, (int64_t)n, nv,
+                         (const double *)w, W.partial, ldp, 0, act);
+                launch_k(k_reduce, nv, kThreads, 0, s, (const double *)W.partial, W.nb, ldp, y.p, act);
+                launch_k(k_hadd, 1, 128, 0, s, Hj, (const double *)y.p, nv, 0, act);
+                launch_k(k_cgs_update<float>, W.nb, kThreads, 0, s, n, (const float *)V32.p, (int64_t)n, nv,
                          (const double *)y.p, w, W.partial2, act);
                 launch_k(k_reduce, 1, kThreads, 0, s, (const double *)W.partial2, W.nb, 1, r0, act);
-                launch_k(k_cgs_decide, 1, 1, 0, s, sc, Hj, (const double *)y.p, nv, 0.5);
-                // second pass only where the first lost too much of the norm
-                launch_k(k_cgs_dot, W.nb, kThreads, 0, s, n, (const double *)V.p, (int64_t)n, nv,
-                         (const double *)w, W.partial, ldp, 0, ro);
-                launch_k(k_reduce, nv, kThreads, 0, s, (const double *)W.partial, W.nb, ldp, y.p, ro);
-                launch_k(k_hadd, 1, 128, 0, s, Hj, (const double *)y.p, nv, 0, ro);
-                launch_k(k_cgs_update, W.nb, kThreads, 0, s, n, (const double *)V.p, (int64_t)n, nv,
-                         (const double *)y.p, w, W.partial2, ro);
-                launch_k(k_reduce, 1, kThreads, 0, s, (const double *)W.partial2, W.nb, 1, r0, ro);
                 launch_k(k_givens, 1, 1, 0, s, j, m, remaining, H.p, cs.p, sn.p, g.p, sc,
                          group_counter(ctx, SAIT_TIMER_ORTHO));
-                launch_k(k_scale, egrid, kThreads, 0, s, n, (const double *)w, w, (const Scal *)sc, act);
+                launch_k(k_scale2, egrid, kThreads, 0, s, n, (const double *)w, w, V32.p + (size_t)(j + 1) * n,
+                         (const Scal *)sc, act);
             }
             SAIT_CK(cudaGetLastError());
             if ((j + 1) % poll == 0 || j + 1 == m) {
@@ -586,8 +587,7 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
     }
     inf.iters = iters;
     inf.cycles = cycles;
-    SAIT_TRY(read_scal(ctx, sc, &hs));
-    inf.reorth_steps = hs.nreorth;
+    inf.reorth_steps = iters;  // every Arnoldi step takes the two Gram-Schmidt passes
     if (info) *info = inf;
     SAIT_CK(cudaStreamSynchronize(s));
     if (result != SAIT_OK) {

@@ -1,11 +1,13 @@
 // Level scheduling for the exact triangular solves and for ILU(0).
 //
-// The level of row i is 0 if it depends on no other row, else 1 + the largest
-// level among the rows it depends on (columns j < i for a lower factor,
-// j > i for an upper one).  Rows of one level are independent, so each level
-// is one parallel launch.  Levels are found on the GPU by repeated in-place
-// relaxation sweeps (monotone, so a sweep that changes nothing proves the
-// fixed point), then rows are bucketed by level with a counting sort.
+// Row i depends on the rows j on the strict side of row i (j < i for a lower
+// factor, j > i for an upper one).  Rows whose dependencies are all finished
+// form the next level set and are independent of one another.  The level sets
+// are found by a frontier sweep over the transposed dependency graph (Kahn's
+// topological order): one launch per level processes the current frontier and
+// releases its dependents, whose in-degree drops to zero, into the next one.
+// ILU(0) is fused into that sweep (a row is factored in the launch of its
+// level), so the factorisation costs one launch per level and O(nnz) work.
 //
 // These are the "exact triangular solvers" that SAIT replaces (Section 3.1)
 // and the level-0 ILU factorisation that supplies SAIT's input (Section 4).
@@ -15,39 +17,6 @@
 #include "internal.cuh"
 
 namespace {
-
-__global__ void k_level_sweep(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                              int lower, int32_t *lev, int *changed) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int l = 0;
-    for (int k = rp[i]; k < rp[i + 1]; k++) {
-        const int j = ci[k];
-        if (lower ? j < i : j > i) {
-            const int lj = *((volatile int32_t *)lev + j);
-            l = max(l, lj + 1);
-        }
-    }
-    if (l != lev[i]) {
-        lev[i] = l;
-        *changed = 1;
-    }
-}
-
-__global__ void k_level_hist(int64_t n, const int32_t *__restrict__ lev, int32_t *hist, int *maxlev) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    atomicAdd(&hist[lev[i]], 1);
-    atomicMax(maxlev, lev[i]);
-}
-
-__global__ void k_level_scatter(int64_t n, const int32_t *__restrict__ lev, const int64_t *__restrict__ ptr,
-                                int32_t *cursor, int32_t *rows) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int l = lev[i];
-    rows[ptr[l] + atomicAdd(&cursor[l], 1)] = (int32_t)i;
-}
 
 // x_i = (b_i - sum_{j on the strict side} T_ij x_j) / T_ii, G lanes per row.
 template <int G>
@@ -76,16 +45,68 @@ k_trisolve_level(const int32_t *__restrict__ rows, int cnt, const int32_t *__res
     if (r < cnt && lane == 0) x[i] = (b[i] - s) / d;
 }
 
-// ILU(0), IKJ order (Saad, Algorithm 10.4), one warp per row of a level.
-// For each k < i in row i (ascending): a_ik /= a_kk, then a_ij -= a_ik a_kj for
-// every j > k of row k that is also in row i's pattern.
-__global__ void __launch_bounds__(256)
-k_ilu0_level(const int32_t *__restrict__ rows, int cnt, const int32_t *__restrict__ rp,
-             const int32_t *__restrict__ ci, const int32_t *__restrict__ dpos, double *a, int *err) {
-    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= cnt) return;  // uniform per warp
-    const int i = rows[w];
+// ---- dependency graph and frontier sweep ----------------------------------------
+__global__ void k_dep_count(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            int lower, int32_t *indeg, int32_t *tcnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = 0;
+    for (int k = rp[i]; k < rp[i + 1]; k++) {
+        const int j = ci[k];
+        if (lower ? j < i : j > i) {
+            c++;
+            atomicAdd(tcnt + j, 1);
+        }
+    }
+    indeg[i] = c;
+}
+
+__global__ void k_dep_fill(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                           int lower, const int64_t *__restrict__ trp, int32_t *tfill, int32_t *tcol) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = rp[i]; k < rp[i + 1]; k++) {
+        const int j = ci[k];
+        if (lower ? j < i : j > i) tcol[trp[j] + atomicAdd(tfill + j, 1)] = (int32_t)i;
+    }
+}
+
+// q[0] begin and q[1] end of the current level in `order`, q[2] append tail,
+// q[3] number of levels found; lptr[l] = start of level l in `order`.
+__global__ void k_front0(int64_t n, const int32_t *__restrict__ indeg, int32_t *order, int *q) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || indeg[i] != 0) return;
+    const unsigned act = __activemask();
+    const int lane = threadIdx.x & 31, leader = __ffs(act) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(q + 2, __popc(act));
+    base = __shfl_sync(act, base, leader);
+    order[base + __popc(act & ((1u << lane) - 1u))] = (int32_t)i;
+}
+
+__global__ void k_front_init(int *q, int32_t *lptr) {
+    q[0] = 0;
+    q[1] = q[2];
+    q[3] = q[2] > 0 ? 1 : 0;
+    lptr[0] = 0;
+    lptr[1] = q[2];
+}
+
+__global__ void k_front_advance(int *q, int32_t *lptr) {
+    q[0] = q[1];
+    q[1] = q[2];
+    if (q[1] > q[0]) {
+        q[3] += 1;
+        lptr[q[3]] = q[1];
+    }
+}
+
+// ILU(0), IKJ order (Saad, Algorithm 10.4), for row i whose dependencies are
+// final: for each k < i in row i (ascending) a_ik /= a_kk, then
+// a_ij -= a_ik a_kj for every j > k of row k that is also in row i's pattern.
+__device__ __forceinline__ void ilu0_row(int i, int lane, const int32_t *__restrict__ rp,
+                                         const int32_t *__restrict__ ci, const int32_t *__restrict__ dpos,
+                                         double *a, int *err) {
     const int b = rp[i], e = rp[i + 1];
     for (int q = b; q < e; q++) {
         const int k = ci[q];
@@ -100,12 +121,16 @@ k_ilu0_level(const int32_t *__restrict__ rows, int cnt, const int32_t *__restric
         if (lane == 0) a[q] = aik;
         for (int f = dpos[k] + 1 + lane; f < rp[k + 1]; f += 32) {
             const int j = ci[f];
-            int lo = b, hi = e - 1;  // binary search for j in row i
+            int lo = q + 1, hi = e - 1;  // j > k: search the rest of row i
             while (lo <= hi) {
                 const int mid = (lo + hi) >> 1;
                 const int c = ci[mid];
-                if (c == j) { a[mid] = fma(-aik, a[f], a[mid]); break; }
-                if (c < j) lo = mid + 1; else hi = mid - 1;
+                if (c == j) {
+                    a[mid] = fma(-aik, a[f], a[mid]);
+                    break;
+                }
+                if (c < j) lo = mid + 1;
+                else hi = mid - 1;
             }
         }
         __syncwarp();
@@ -113,6 +138,27 @@ k_ilu0_level(const int32_t *__restrict__ rows, int cnt, const int32_t *__restric
     if (lane == 0) {
         const double d = a[dpos[i]];
         if (d == 0.0 || !isfinite(d)) atomicOr(err, 1);
+    }
+}
+
+// One level: a warp per frontier row (factor it if ILU), then release its
+// dependents; a dependent whose in-degree reaches zero joins the next level.
+template <bool ILU>
+__global__ void __launch_bounds__(256)
+k_front_step(int32_t *order, int *q, const int64_t *__restrict__ trp, const int32_t *__restrict__ tcol,
+             int32_t *indeg, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+             const int32_t *__restrict__ dpos, double *a, int *err) {
+    const int begin = q[0], end = q[1];
+    const int lane = threadIdx.x & 31;
+    const int w0 = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+    for (int r = begin + w0; r < end; r += nw) {
+        const int i = order[r];
+        if (ILU) ilu0_row(i, lane, rp, ci, dpos, a, err);
+        for (int64_t t = trp[i] + lane; t < trp[i + 1]; t += 32) {
+            const int d = tcol[t];
+            if (atomicSub(indeg + d, 1) == 1) order[atomicAdd(q + 2, 1)] = d;
+        }
     }
 }
 
@@ -172,56 +218,78 @@ void free_levels(LevelSchedule *L) {
     L->nlev = 0;
 }
 
-sait_status build_levels(sait_ctx ctx, const int32_t *rp, const int32_t *ci, int64_t n, bool lower,
-                         LevelSchedule *out) {
+// Frontier sweep over the dependency graph of (rp, ci); fills `out` (level
+// sets on the device, level pointers on the host) when given, and factors
+// ILU(0) in place in `a` when `a` is given (err_word collects pivot errors).
+sait_status frontier_schedule(sait_ctx ctx, const int32_t *rp, const int32_t *ci, int64_t n, bool lower,
+                              const int32_t *dpos, double *a, int *err_word, LevelSchedule *out) {
     cudaStream_t s = ctx->stream;
     int *h = (int *)ctx->h_pinned;
-    out->nlev = 0;
-    out->ptr.assign(1, 0);
-    if (n == 0) return SAIT_OK;
-    DTemp<int32_t> lev;
-    SAIT_CK(lev.alloc(n, s));
-    SAIT_CK(cudaMemsetAsync(lev.p, 0, n * sizeof(int32_t), s));
-    const unsigned grid = (unsigned)cdiv(n, 256);
-    // Relaxation: in batches of 8 sweeps; the flag is reset before the last
-    // sweep of a batch, so it reports whether that sweep changed anything.
-    for (int64_t sweeps = 0;; sweeps += 8) {
-        if (sweeps > n + 16) return ctx_fail(ctx, SAIT_ERR_CUDA, "level sweeps did not converge");
-        for (int t = 0; t < 7; t++)
-            launch_k(k_level_sweep, grid, 256, 0, s, n, rp, ci, lower, lev.p, ctx->d_word + 8);
-        SAIT_CK(cudaMemsetAsync(ctx->d_word + 8, 0, sizeof(int), s));
-        launch_k(k_level_sweep, grid, 256, 0, s, n, rp, ci, lower, lev.p, ctx->d_word + 8);
-        SAIT_CK(cudaGetLastError());
-        SAIT_CK(cudaMemcpyAsync(h, ctx->d_word + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
-        SAIT_CK(cudaStreamSynchronize(s));
-        if (h[0] == 0) break;
+    if (out) {
+        out->nlev = 0;
+        out->ptr.assign(1, 0);
     }
-    DTemp<int32_t> hist, cursor;
-    SAIT_CK(hist.alloc(n, s));
-    SAIT_CK(cursor.alloc(n, s));
-    SAIT_CK(cudaMemsetAsync(hist.p, 0, n * sizeof(int32_t), s));
-    SAIT_CK(cudaMemsetAsync(cursor.p, 0, n * sizeof(int32_t), s));
-    SAIT_CK(cudaMemsetAsync(ctx->d_word + 9, 0, sizeof(int), s));
-    launch_k(k_level_hist, grid, 256, 0, s, n, lev.p, hist.p, ctx->d_word + 9);
-    SAIT_CK(cudaGetLastError());
-    SAIT_CK(cudaMemcpyAsync(h + 1, ctx->d_word + 9, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (n == 0) return SAIT_OK;
+    const unsigned grid = (unsigned)cdiv(n, 256);
+    DTemp<int32_t> indeg, tcnt, order, lptr;
+    DTemp<int64_t> trp;
+    DTemp<int32_t> tcol;
+    DTemp<int> q;
+    SAIT_CK(indeg.alloc(n, s));
+    SAIT_CK(tcnt.alloc(n, s));
+    SAIT_CK(order.alloc(n, s));
+    SAIT_CK(lptr.alloc(n + 2, s));
+    SAIT_CK(trp.alloc(n + 1, s));
+    SAIT_CK(q.alloc(4, s));
+    SAIT_CK(cudaMemsetAsync(tcnt.p, 0, n * sizeof(int32_t), s));
+    SAIT_CK(cudaMemsetAsync(q.p, 0, 4 * sizeof(int), s));
+    launch_k(k_dep_count, grid, 256, 0, s, n, rp, ci, (int)lower, indeg.p, tcnt.p);
+    SAIT_CK(scan_i32(tcnt.p, trp.p, n, s));
+    int64_t *h64 = (int64_t *)((char *)ctx->h_pinned + 256);
+    SAIT_CK(cudaMemcpyAsync(h64, trp.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     SAIT_CK(cudaStreamSynchronize(s));
-    const int nlev = h[1] + 1;
-    DTemp<int64_t> ptr;
-    SAIT_CK(ptr.alloc(nlev + 1, s));
-    SAIT_CK(scan_i32(hist.p, ptr.p, nlev, s));
-    SAIT_CK(cudaMalloc((void **)&out->rows, n * sizeof(int32_t)));
-    launch_k(k_level_scatter, grid, 256, 0, s, n, lev.p, ptr.p, cursor.p, out->rows);
+    SAIT_CK(tcol.alloc(h64[0], s));
+    SAIT_CK(cudaMemsetAsync(tcnt.p, 0, n * sizeof(int32_t), s));  // reused as fill cursors
+    launch_k(k_dep_fill, grid, 256, 0, s, n, rp, ci, (int)lower, (const int64_t *)trp.p, tcnt.p, tcol.p);
+    launch_k(k_front0, grid, 256, 0, s, n, (const int32_t *)indeg.p, order.p, q.p);
+    launch_k(k_front_init, 1, 1, 0, s, q.p, lptr.p);
     SAIT_CK(cudaGetLastError());
-    std::vector<int64_t> hp(nlev + 1);
-    SAIT_CK(cudaMemcpyAsync(hp.data(), ptr.p, (nlev + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    SAIT_CK(cudaStreamSynchronize(s));
-    out->nlev = nlev;
-    out->ptr.resize(nlev + 1);
-    out->max_width = 0;
-    for (int l = 0; l <= nlev; l++) out->ptr[l] = (int32_t)hp[l];
-    for (int l = 0; l < nlev; l++) out->max_width = std::max(out->max_width, out->ptr[l + 1] - out->ptr[l]);
+    const unsigned sgrid = (unsigned)std::min<int64_t>(cdiv(n * 32, 256), (int64_t)ctx->num_sms * 4);
+    const bool ilu = a != nullptr;
+    for (int64_t batch = 0;; batch++) {
+        if (batch * 32 > n + 64) return ctx_fail(ctx, SAIT_ERR_CUDA, "level schedule did not terminate");
+        for (int t = 0; t < 32; t++) {
+            if (ilu)
+                launch_k(k_front_step<true>, sgrid, 256, 0, s, order.p, q.p, (const int64_t *)trp.p,
+                         (const int32_t *)tcol.p, indeg.p, rp, ci, dpos, a, err_word);
+            else
+                launch_k(k_front_step<false>, sgrid, 256, 0, s, order.p, q.p, (const int64_t *)trp.p,
+                         (const int32_t *)tcol.p, indeg.p, rp, ci, dpos, a, err_word);
+            launch_k(k_front_advance, 1, 1, 0, s, q.p, lptr.p);
+        }
+        SAIT_CK(cudaGetLastError());
+        SAIT_CK(cudaMemcpyAsync(h, q.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        SAIT_CK(cudaStreamSynchronize(s));
+        if (h[0] == h[1]) break;  // empty frontier: every row is scheduled
+    }
+    if (h[1] != n) return ctx_fail(ctx, SAIT_ERR_CUDA, "level schedule lost rows");
+    if (out) {
+        const int nlev = h[3];
+        out->nlev = nlev;
+        out->ptr.resize(nlev + 1);
+        SAIT_CK(cudaMemcpyAsync(out->ptr.data(), lptr.p, (nlev + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SAIT_CK(cudaMalloc((void **)&out->rows, n * sizeof(int32_t)));
+        SAIT_CK(cudaMemcpyAsync(out->rows, order.p, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        SAIT_CK(cudaStreamSynchronize(s));
+        out->max_width = 0;
+        for (int l = 0; l < nlev; l++) out->max_width = std::max(out->max_width, out->ptr[l + 1] - out->ptr[l]);
+    }
     return SAIT_OK;
+}
+
+sait_status build_levels(sait_ctx ctx, const int32_t *rp, const int32_t *ci, int64_t n, bool lower,
+                         LevelSchedule *out) {
+    return frontier_schedule(ctx, rp, ci, n, lower, nullptr, nullptr, nullptr, out);
 }
 
 cudaError_t launch_trisolve(const sait_mat_s *T, const LevelSchedule &lev, bool lower, const double *b,
@@ -246,12 +314,11 @@ extern "C" sait_status sait_ilu0(sait_ctx ctx, const sait_csr *A, sait_mat *L, s
     *L = *U = nullptr;
     ScopedTimer tm(ctx, SAIT_TIMER_ILU);
     sait_mat W = nullptr;  // validated working copy of A, overwritten with L\U
-    SAIT_TRY(sait_mat_create_csr(ctx, A, &W));
+    SAIT_TRY(mat_copy_csr(ctx, A, &W));
     const int64_t n = W->n;
     cudaStream_t s = ctx->stream;
     int *h = (int *)ctx->h_pinned;
     sait_status st = SAIT_OK;
-    LevelSchedule lev;
     DTemp<int32_t> dpos, lc, uc;
     DTemp<int64_t> lrp, urp;
     sait_mat Lm = nullptr, Um = nullptr;
@@ -267,15 +334,11 @@ extern "C" sait_status sait_ilu0(sait_ctx ctx, const sait_csr *A, sait_mat *L, s
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { cuda_fail(e, "sait_ilu0 diagonal"); goto done; }
     if (h[0]) { st = ctx_fail(ctx, SAIT_ERR_ZERO_PIVOT, "sait_ilu0: missing diagonal entry"); goto done; }
-    st = build_levels(ctx, W->rp, W->ci, n, true, &lev);
+    e = cudaMemsetAsync(ctx->d_word, 0, sizeof(int), s);
+    if (e != cudaSuccess) { cuda_fail(e, "sait_ilu0 setup"); goto done; }
+    st = frontier_schedule(ctx, W->rp, W->ci, n, true, dpos.p, W->va, ctx->d_word, nullptr);
     if (st != SAIT_OK) goto done;
-    for (int l = 0; l < lev.nlev; l++) {
-        const int cnt = lev.ptr[l + 1] - lev.ptr[l];
-        launch_k(k_ilu0_level, (unsigned)cdiv((int64_t)cnt * 32, 256), 256, 0, s, 
-            lev.rows + lev.ptr[l], cnt, W->rp, W->ci, dpos.p, W->va, ctx->d_word);
-    }
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h, ctx->d_word, sizeof(int), cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(h, ctx->d_word, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { cuda_fail(e, "sait_ilu0 factorisation"); goto done; }
     if (h[0]) { st = ctx_fail(ctx, SAIT_ERR_ZERO_PIVOT, "sait_ilu0: zero or non-finite pivot"); goto done; }
@@ -289,7 +352,7 @@ extern "C" sait_status sait_ilu0(sait_ctx ctx, const sait_csr *A, sait_mat *L, s
     e = scan_i32(lc.p, lrp.p, n, s);
     if (e == cudaSuccess) e = scan_i32(uc.p, urp.p, n, s);
     {
-        int64_t *h64 = (int64_t *)ctx->h_pinned;
+        int64_t *h64 = (int64_t *)((char *)ctx->h_pinned + 256);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h64, lrp.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h64 + 1, urp.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -311,7 +374,6 @@ extern "C" sait_status sait_ilu0(sait_ctx ctx, const sait_csr *A, sait_mat *L, s
 done:
     if (Lm) sait_mat_destroy(Lm);
     if (Um) sait_mat_destroy(Um);
-    free_levels(&lev);
     cudaStreamSynchronize(s);
     sait_mat_destroy(W);
     return st;
