@@ -183,6 +183,30 @@ sait_status sait_spmv(sait_ctx ctx, sait_mat A, const double *x, double *y);
  * r and z must not overlap.  Enqueues only. */
 sait_status sait_apply(sait_ctx ctx, sait_mat ML, sait_mat MU, const double *r, double *z);
 
+/* Largest n accepted by sait_apply_static. */
+#define SAIT_APPLY_STATIC_MAX_N 2097152
+
+/* z = M_U (M_L r) like sait_apply, but allocating nothing.  The paper has no
+ * counterpart: this is for callers that cannot let the library allocate
+ * device memory when the preconditioner is applied -- code running inside
+ * CUDA stream capture, loops whose latency budget forbids allocator calls, and
+ * frameworks that hand out all device memory through their own pools.  The
+ * caller still owns r and z (device, n doubles, not overlapping); the
+ * intermediate vector lives in a fixed 16 MiB array compiled into the
+ * library, present on every device that loads the library until the process
+ * exits.  Requirements and behaviour:
+ *  - n <= SAIT_APPLY_STATIC_MAX_N, else SAIT_ERR_UNSUPPORTED; ML and MU must
+ *    live on the current device (else SAIT_ERR_INVALID_ARG).
+ *  - Enqueues two products on `stream` (a cudaStream_t, NULL = legacy default
+ *    stream) and returns; no context is needed, and sait_ctx_last_error does
+ *    not see its failures.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call on a device shares the one array: calls whose work overlaps
+ *    on the GPU (different streams, no ordering between them) race and give
+ *    wrong results.  Calls ordered on one stream are safe. */
+sait_status sait_apply_static(sait_mat ML, sait_mat MU, const double *r, double *z, void *stream);
+
 /* ---- preconditioner objects for the solvers ----------------------------- */
 
 /* SAIT pair: applies z = M_U (M_L r). */

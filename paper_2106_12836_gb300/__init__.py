@@ -25,7 +25,7 @@ __all__ = [
     "sait_mat_set_store", "sait_ilu0", "sait_build", "sait_spmv", "sait_apply",
     "sait_prec_create_sait", "sait_prec_create_ilu", "sait_prec_levels", "sait_prec_apply",
     "sait_prec_destroy", "sait_gmres", "sait_bicgstab", "sait_ctx_set_timing", "sait_ctx_stats",
-    "Stats", "TIMERS", "lib_path", "EXPORTS",
+    "sait_apply_static", "APPLY_STATIC_MAX_N", "Stats", "TIMERS", "lib_path", "EXPORTS",
 ]
 
 DROP = {"none": 0, "abs": 1, "rowrel": 2, "pattern": 3}
@@ -39,7 +39,9 @@ EXPORTS = [
     "sait_mat_set_store", "sait_ilu0", "sait_build", "sait_spmv", "sait_apply",
     "sait_prec_create_sait", "sait_prec_create_ilu", "sait_prec_levels", "sait_prec_apply",
     "sait_prec_destroy", "sait_gmres", "sait_bicgstab", "sait_ctx_set_timing", "sait_ctx_stats",
+    "sait_apply_static",
 ]
+APPLY_STATIC_MAX_N = 2097152  # SAIT_APPLY_STATIC_MAX_N in include/sait.h
 TIMERS = ["apply", "spmv", "ortho", "build", "ilu", "trisolve"]
 
 
@@ -108,6 +110,7 @@ def _L():
             "sait_bicgstab": [vp, vp, vp, vp, vp, d, i32, C.POINTER(Info)],
             "sait_ctx_set_timing": [vp, C.c_int],
             "sait_ctx_stats": [vp, C.POINTER(Stats), C.c_int],
+            "sait_apply_static": [vp, vp, vp, vp, vp],
         }
         for name, args in sigs.items():
             f = getattr(lib, name)
@@ -312,6 +315,23 @@ def sait_apply(ctx: Context, ML: Mat, MU: Mat, r: torch.Tensor, z: torch.Tensor 
     z = torch.empty_like(r) if z is None else _vec(z, ML.n, "z")
     _check(ctx, _L().sait_apply(ctx.h, ML.h, MU.h, _ptr(r), _ptr(z)), "sait_apply")
     return z
+
+
+def sait_apply_static(ML: Mat, MU: Mat, r: torch.Tensor, z: torch.Tensor,
+                      stream: torch.cuda.Stream | None = None) -> int:
+    """z = M_U (M_L r) without any allocation by the library (see include/sait.h).
+
+    For callers that cannot allow device allocations at apply time (stream
+    capture, allocator-free loops, framework-owned memory): the intermediate
+    vector lives in a fixed array inside the library, shared by all calls on a
+    device, so calls that overlap on the GPU race.  n must not exceed
+    APPLY_STATIC_MAX_N.  Returns the status code (0 = ok) instead of raising,
+    since no context records a message.
+    """
+    _vec(r, ML.n, "r")
+    _vec(z, ML.n, "z")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(_L().sait_apply_static(ML.h, MU.h, _ptr(r), _ptr(z), C.c_void_p(s.cuda_stream)))
 
 
 def sait_prec_create_sait(ctx: Context, ML: Mat, MU: Mat) -> Prec:
