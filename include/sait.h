@@ -183,6 +183,30 @@ sait_status sait_spmv(sait_ctx ctx, sait_mat A, const double *x, double *y);
  * r and z must not overlap.  Enqueues only. */
 sait_status sait_apply(sait_ctx ctx, sait_mat ML, sait_mat MU, const double *r, double *z);
 
+/* Block products for many right-hand sides / block eigenvectors.  X, Y, R, Z
+ * are row-major n x k device blocks with leading dimensions ld >= k (entry
+ * (i, t) at X[i * ldx + t]).  Each entry of the matrix is read once per block
+ * whatever k is (Section 4.4 applies SAIT to a block of vectors this way).
+ * Enqueue only. */
+sait_status sait_spmm(sait_ctx ctx, sait_mat A, int32_t k, const double *X, int64_t ldx, double *Y,
+                      int64_t ldy);
+/* Z = M_U (M_L R) for a block of k vectors (intermediate block FP64 when both
+ * matrices are stored in FP64, else FP32).  Enqueue only. */
+sait_status sait_apply_multi(sait_ctx ctx, sait_mat ML, sait_mat MU, int32_t k, const double *R,
+                             int64_t ldr, double *Z, int64_t ldz);
+
+/* ---- adjoint support ------------------------------------------------------ */
+
+/* *out = M^T as a new matrix with the same storage precision (rows sorted).
+ * The transposed SAIT apply of the adjoint, (M_U M_L)^T = M_L^T M_U^T, is
+ * sait_prec_create_sait(ctx, MU^T, ML^T).  Synchronizes. */
+sait_status sait_mat_transpose(sait_ctx ctx, sait_mat M, sait_mat *out);
+/* out[e] = alpha * u[row(e)] * v[col(e)] for every stored entry e of A, in
+ * A's CSR order (nnz entries).  With alpha = -1, u = lambda (adjoint
+ * solution) and v = x this is dl/dA on A's pattern.  Enqueue only. */
+sait_status sait_outer_on_pattern(sait_ctx ctx, sait_mat A, double alpha, const double *u, const double *v,
+                                  double *out);
+
 /* Largest n accepted by sait_apply_static. */
 #define SAIT_APPLY_STATIC_MAX_N 2097152
 

@@ -25,7 +25,8 @@ __all__ = [
     "sait_mat_set_store", "sait_ilu0", "sait_build", "sait_spmv", "sait_apply",
     "sait_prec_create_sait", "sait_prec_create_ilu", "sait_prec_levels", "sait_prec_apply",
     "sait_prec_destroy", "sait_gmres", "sait_bicgstab", "sait_ctx_set_timing", "sait_ctx_stats",
-    "sait_apply_static", "APPLY_STATIC_MAX_N", "Stats", "TIMERS", "lib_path", "EXPORTS",
+    "sait_apply_static", "APPLY_STATIC_MAX_N", "sait_spmm", "sait_apply_multi", "sait_mat_transpose",
+    "sait_outer_on_pattern", "Stats", "TIMERS", "lib_path", "EXPORTS",
 ]
 
 DROP = {"none": 0, "abs": 1, "rowrel": 2, "pattern": 3}
@@ -39,7 +40,7 @@ EXPORTS = [
     "sait_mat_set_store", "sait_ilu0", "sait_build", "sait_spmv", "sait_apply",
     "sait_prec_create_sait", "sait_prec_create_ilu", "sait_prec_levels", "sait_prec_apply",
     "sait_prec_destroy", "sait_gmres", "sait_bicgstab", "sait_ctx_set_timing", "sait_ctx_stats",
-    "sait_apply_static",
+    "sait_apply_static", "sait_spmm", "sait_apply_multi", "sait_mat_transpose", "sait_outer_on_pattern",
 ]
 APPLY_STATIC_MAX_N = 2097152  # SAIT_APPLY_STATIC_MAX_N in include/sait.h
 TIMERS = ["apply", "spmv", "ortho", "build", "ilu", "trisolve"]
@@ -111,6 +112,10 @@ def _L():
             "sait_ctx_set_timing": [vp, C.c_int],
             "sait_ctx_stats": [vp, C.POINTER(Stats), C.c_int],
             "sait_apply_static": [vp, vp, vp, vp, vp],
+            "sait_spmm": [vp, vp, i32, vp, i64, vp, i64],
+            "sait_apply_multi": [vp, vp, vp, i32, vp, i64, vp, i64],
+            "sait_mat_transpose": [vp, vp, C.POINTER(vp)],
+            "sait_outer_on_pattern": [vp, vp, d, vp, vp, vp],
         }
         for name, args in sigs.items():
             f = getattr(lib, name)
@@ -141,6 +146,12 @@ def _ptr(t: torch.Tensor | None):
     if not t.is_cuda or not t.is_contiguous():
         raise ValueError("expected a contiguous CUDA tensor")
     return t.data_ptr()
+
+
+def _ptr_any(t: torch.Tensor):
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    return t.data_ptr() if t.numel() else None
 
 
 def _vec(t: torch.Tensor, n: int, name: str) -> torch.Tensor:
@@ -332,6 +343,47 @@ def sait_apply_static(ML: Mat, MU: Mat, r: torch.Tensor, z: torch.Tensor,
     _vec(z, ML.n, "z")
     s = stream if stream is not None else torch.cuda.current_stream()
     return int(_L().sait_apply_static(ML.h, MU.h, _ptr(r), _ptr(z), C.c_void_p(s.cuda_stream)))
+
+
+def _block(t: torch.Tensor, n: int, name: str) -> torch.Tensor:
+    if t.dtype != torch.float64 or not t.is_cuda or t.dim() != 2 or t.shape[0] != n or t.stride(1) != 1:
+        raise ValueError(f"{name}: expected a float64 CUDA block of {n} rows with unit column stride")
+    return t
+
+
+def sait_spmm(ctx: Context, A: Mat, X: torch.Tensor, Y: torch.Tensor | None = None) -> torch.Tensor:
+    """Y = A X for a row-major n x k block."""
+    _block(X, A.n, "X")
+    Y = torch.empty_like(X) if Y is None else _block(Y, A.n, "Y")
+    _check(ctx, _L().sait_spmm(ctx.h, A.h, X.shape[1], _ptr_any(X), X.stride(0), _ptr_any(Y), Y.stride(0)),
+           "sait_spmm")
+    return Y
+
+
+def sait_apply_multi(ctx: Context, ML: Mat, MU: Mat, R: torch.Tensor, Z: torch.Tensor | None = None):
+    """Z = M_U (M_L R) for a row-major n x k block."""
+    _block(R, ML.n, "R")
+    Z = torch.empty_like(R) if Z is None else _block(Z, ML.n, "Z")
+    _check(ctx, _L().sait_apply_multi(ctx.h, ML.h, MU.h, R.shape[1], _ptr_any(R), R.stride(0), _ptr_any(Z),
+                                      Z.stride(0)), "sait_apply_multi")
+    return Z
+
+
+def sait_mat_transpose(ctx: Context, M: Mat) -> Mat:
+    h = C.c_void_p()
+    _check(ctx, _L().sait_mat_transpose(ctx.h, M.h, C.byref(h)), "sait_mat_transpose")
+    return Mat(ctx, h)
+
+
+def sait_outer_on_pattern(ctx: Context, A: Mat, alpha: float, u: torch.Tensor, v: torch.Tensor,
+                          out: torch.Tensor | None = None) -> torch.Tensor:
+    """out[e] = alpha * u[row(e)] * v[col(e)] over A's stored entries (CSR order)."""
+    _vec(u, A.n, "u")
+    _vec(v, A.n, "v")
+    out = torch.empty(A.nnz, dtype=torch.float64, device=u.device) if out is None else out
+    _check(ctx, _L().sait_outer_on_pattern(ctx.h, A.h, float(alpha), _ptr(u), _ptr(v), _ptr_any(out)),
+           "sait_outer_on_pattern")
+    return out
 
 
 def sait_prec_create_sait(ctx: Context, ML: Mat, MU: Mat) -> Prec:

@@ -156,6 +156,12 @@ cudaError_t launch_spmv(const sait_mat_s *A, sait_dtype store, const void *x, bo
 cudaError_t cast_values(const double *src, float *d32, __nv_bfloat16 *d16, int64_t nnz,
                         cudaStream_t s);
 
+// spmm.cu
+cudaError_t launch_spmm(const sait_mat_s *A, sait_dtype store, int k, int64_t ldx, int64_t ldy, const void *X,
+                        bool x_f32, void *Y, bool y_f32, cudaStream_t s, int *calls);
+sait_status apply_multi_impl(sait_ctx ctx, sait_mat ML, sait_mat MU, int k, const double *R, int64_t ldr,
+                             double *Z, int64_t ldz, void *W);
+
 // sell.cu
 sait_status mat_prepare_sell(sait_ctx ctx, sait_mat M, sait_dtype store);
 bool sell_ready(const sait_mat_s *A, sait_dtype store);

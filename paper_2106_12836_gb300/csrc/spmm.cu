@@ -1,0 +1,144 @@
+// Multi-right-hand-side products Y = A X (X, Y row-major n x k with leading
+// dimension ld) and the SAIT block apply Z = M_U (M_L R).
+//
+// A group of G lanes owns one row; lane l handles columns l, l + G, ... of
+// the block.  The group loads G entries of the row at a time (one per lane)
+// and broadcasts each (column, value) pair with shuffles, so every entry of A
+// is read once per product whatever k is, and for each entry the group reads
+// the G consecutive values X[c, :] -- one coalesced line.  With the block of
+// k columns, the matrix traffic of one apply is shared by k vectors (the
+// block eigensolver and many-right-hand-side cases).
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace {
+
+template <typename T> struct Acc;
+template <> struct Acc<double> { using type = double; };
+template <> struct Acc<float> { using type = float; };
+template <> struct Acc<__nv_bfloat16> { using type = float; };
+
+__device__ __forceinline__ double cvt(double v) { return v; }
+__device__ __forceinline__ float cvt(float v) { return v; }
+__device__ __forceinline__ float cvt(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ double fmac(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmac(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <int G, int CPL, typename TV, typename TX, typename TY>
+__global__ void __launch_bounds__(256)
+k_spmm_csr(int64_t n, int k, int64_t ldx, int64_t ldy, const int32_t *__restrict__ rp,
+           const int32_t *__restrict__ ci, const TV *__restrict__ va, const TX *__restrict__ X,
+           TY *__restrict__ Y, int *calls) {
+    using A = typename Acc<TV>::type;
+    if (calls && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(calls, 1);
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int gl = threadIdx.x & (G - 1);
+    const int gbase = (threadIdx.x & 31) & ~(G - 1);
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << gbase);
+    if (row >= n) return;  // whole groups leave together
+    A acc[CPL];
+#pragma unroll
+    for (int t = 0; t < CPL; t++) acc[t] = 0;
+    const int b = rp[row], e = rp[row + 1];
+    for (int base = b; base < e; base += G) {
+        const int idx = base + gl;
+        const int c_l = idx < e ? __ldg(ci + idx) : 0;
+        const A v_l = idx < e ? (A)cvt(va[idx]) : (A)0;
+        const int cnt = min(G, e - base);
+        for (int u = 0; u < cnt; u++) {
+            const int c = __shfl_sync(gmask, c_l, u, G);
+            const A v = __shfl_sync(gmask, v_l, u, G);
+            const TX *xr = X + (int64_t)c * ldx;
+#pragma unroll
+            for (int t = 0; t < CPL; t++) {
+                const int col = gl + t * G;
+                if (col < k) acc[t] = fmac(v, (A)__ldg(xr + col), acc[t]);
+            }
+        }
+    }
+    TY *yr = Y + row * ldy;
+#pragma unroll
+    for (int t = 0; t < CPL; t++) {
+        const int col = gl + t * G;
+        if (col < k) yr[col] = (TY)acc[t];
+    }
+}
+
+template <int G, int CPL, typename TV, typename TX, typename TY>
+void launch_gc(const sait_mat_s *A, const TV *va, int k, int64_t ldx, int64_t ldy, const TX *X, TY *Y,
+               cudaStream_t s, int *calls) {
+    launch_k(k_spmm_csr<G, CPL, TV, TX, TY>, (unsigned)cdiv(A->n * G, 256), 256, 0, s, A->n, k, ldx, ldy,
+             (const int32_t *)A->rp, (const int32_t *)A->ci, va, X, Y, calls);
+}
+
+template <typename TV, typename TX, typename TY>
+void launch_shape(const sait_mat_s *A, const TV *va, int k, int64_t ldx, int64_t ldy, const TX *X, TY *Y,
+                  cudaStream_t s, int *calls) {
+    if (k <= 1) launch_gc<2, 1>(A, va, k, ldx, ldy, X, Y, s, calls);
+    else if (k <= 2) launch_gc<2, 1>(A, va, k, ldx, ldy, X, Y, s, calls);
+    else if (k <= 4) launch_gc<4, 1>(A, va, k, ldx, ldy, X, Y, s, calls);
+    else if (k <= 8) launch_gc<8, 1>(A, va, k, ldx, ldy, X, Y, s, calls);
+    else if (k <= 16) launch_gc<16, 1>(A, va, k, ldx, ldy, X, Y, s, calls);
+    else if (k <= 32) launch_gc<32, 1>(A, va, k, ldx, ldy, X, Y, s, calls);
+    else if (k <= 64) launch_gc<32, 2>(A, va, k, ldx, ldy, X, Y, s, calls);
+    else launch_gc<32, 4>(A, va, k, ldx, ldy, X, Y, s, calls);
+}
+
+template <typename TV>
+cudaError_t spmm_xy(const sait_mat_s *A, const TV *va, int k, int64_t ldx, int64_t ldy, const void *X,
+                    bool x_f32, void *Y, bool y_f32, cudaStream_t s, int *calls) {
+    if (x_f32) {
+        if (y_f32) launch_shape(A, va, k, ldx, ldy, (const float *)X, (float *)Y, s, calls);
+        else launch_shape(A, va, k, ldx, ldy, (const float *)X, (double *)Y, s, calls);
+    } else {
+        if (y_f32) launch_shape(A, va, k, ldx, ldy, (const double *)X, (float *)Y, s, calls);
+        else launch_shape(A, va, k, ldx, ldy, (const double *)X, (double *)Y, s, calls);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_spmm(const sait_mat_s *A, sait_dtype store, int k, int64_t ldx, int64_t ldy, const void *X,
+                        bool x_f32, void *Y, bool y_f32, cudaStream_t s, int *calls) {
+    if (A->n == 0 || k <= 0) return cudaSuccess;
+    switch (store) {
+        case SAIT_F32: return spmm_xy(A, (const float *)A->va32, k, ldx, ldy, X, x_f32, Y, y_f32, s, calls);
+        case SAIT_BF16:
+            return spmm_xy(A, (const __nv_bfloat16 *)A->va16, k, ldx, ldy, X, x_f32, Y, y_f32, s, calls);
+        default: return spmm_xy(A, (const double *)A->va, k, ldx, ldy, X, x_f32, Y, y_f32, s, calls);
+    }
+}
+
+extern "C" sait_status sait_spmm(sait_ctx ctx, sait_mat A, int32_t k, const double *X, int64_t ldx, double *Y,
+                                 int64_t ldy) {
+    if (!ctx) return SAIT_ERR_INVALID_ARG;
+    if (!A || k < 0 || ldx < k || ldy < k || (A->n > 0 && k > 0 && (!X || !Y)))
+        return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_spmm: bad argument");
+    ScopedTimer tm(ctx, SAIT_TIMER_SPMV);
+    SAIT_CK(launch_spmm(A, A->store, k, ldx, ldy, X, false, Y, false, ctx->stream,
+                        group_counter(ctx, SAIT_TIMER_SPMV)));
+    return SAIT_OK;
+}
+
+sait_status apply_multi_impl(sait_ctx ctx, sait_mat ML, sait_mat MU, int k, const double *R, int64_t ldr,
+                             double *Z, int64_t ldz, void *W) {
+    const bool f64 = ML->store == SAIT_F64 && MU->store == SAIT_F64;
+    ScopedTimer tm(ctx, SAIT_TIMER_APPLY);
+    SAIT_CK(launch_spmm(ML, ML->store, k, ldr, k, R, false, W, !f64, ctx->stream,
+                        group_counter(ctx, SAIT_TIMER_APPLY)));
+    SAIT_CK(launch_spmm(MU, MU->store, k, k, ldz, W, !f64, Z, false, ctx->stream, nullptr));
+    return SAIT_OK;
+}
+
+extern "C" sait_status sait_apply_multi(sait_ctx ctx, sait_mat ML, sait_mat MU, int32_t k, const double *R,
+                                        int64_t ldr, double *Z, int64_t ldz) {
+    if (!ctx) return SAIT_ERR_INVALID_ARG;
+    if (!ML || !MU || ML->n != MU->n || k < 0 || ldr < k || ldz < k || (ML->n > 0 && k > 0 && (!R || !Z)))
+        return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_apply_multi: bad argument");
+    if (ML->n == 0 || k == 0) return SAIT_OK;
+    DTemp<double> W;  // n x k intermediate (FP64, or FP32 in its first half)
+    SAIT_CK(W.alloc((size_t)ML->n * k, ctx->stream));
+    return apply_multi_impl(ctx, ML, MU, k, R, ldr, Z, ldz, W.p);
+}
