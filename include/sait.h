@@ -195,6 +195,37 @@ sait_status sait_spmm(sait_ctx ctx, sait_mat A, int32_t k, const double *X, int6
 sait_status sait_apply_multi(sait_ctx ctx, sait_mat ML, sait_mat MU, int32_t k, const double *R,
                              int64_t ldr, double *Z, int64_t ldz);
 
+/* ---- batched solves ---------------------------------------------------------- */
+
+typedef struct {
+    int32_t nsys;           /* systems (or right-hand sides) */
+    int32_t converged;      /* with true relative residual <= tol */
+    int32_t max_iters;      /* largest per-system iteration count */
+    int32_t graph_replays;  /* CUDA-graph replays of one iteration */
+    double max_rel_resid;   /* largest true ||b_s - A_s x_s|| / ||b_s|| */
+} sait_batch_info;
+
+/* BiCGSTAB on many independent systems at once.  A is block diagonal: system
+ * s owns rows and columns sys_ptr[s] .. sys_ptr[s+1] (device int64 array of
+ * nsys + 1 entries, sys_ptr[0] = 0, sys_ptr[nsys] = n) and has no entry
+ * outside its block.  P: a SAIT pair built from A's ILU(0) factors (block
+ * diagonal as well) or NULL.  Every system has its own scalars, stopping test
+ * (true relative residual <= tol) and iteration count (<= maxit); converged
+ * systems stop changing.  One iteration is captured in a CUDA graph and
+ * replayed.  rel_resid (device, nsys doubles) and iters (device, nsys ints)
+ * receive per-system results when not NULL.  Synchronizes. */
+sait_status sait_bicgstab_batched(sait_ctx ctx, sait_mat A, sait_prec P, int32_t nsys, const int64_t *sys_ptr,
+                                  const double *b, double *x, double tol, int32_t maxit, sait_batch_info *info,
+                                  double *rel_resid, int32_t *iters);
+/* BiCGSTAB for k right-hand sides of one matrix at once: B, X row-major n x k
+ * (contiguous), one set of scalars per column; the products are block
+ * products (sait_spmm / sait_apply_multi), so each matrix entry is read once
+ * per iteration for all k columns.  k in 1..32 or a divisor of 256.
+ * Same conventions as sait_bicgstab_batched. */
+sait_status sait_bicgstab_multi(sait_ctx ctx, sait_mat A, sait_prec P, int32_t k, const double *B, double *X,
+                                double tol, int32_t maxit, sait_batch_info *info, double *rel_resid,
+                                int32_t *iters);
+
 /* ---- adjoint support ------------------------------------------------------ */
 
 /* *out = M^T as a new matrix with the same storage precision (rows sorted).

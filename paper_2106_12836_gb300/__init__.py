@@ -26,7 +26,8 @@ __all__ = [
     "sait_prec_create_sait", "sait_prec_create_ilu", "sait_prec_levels", "sait_prec_apply",
     "sait_prec_destroy", "sait_gmres", "sait_bicgstab", "sait_ctx_set_timing", "sait_ctx_stats",
     "sait_apply_static", "APPLY_STATIC_MAX_N", "sait_spmm", "sait_apply_multi", "sait_mat_transpose",
-    "sait_outer_on_pattern", "Stats", "TIMERS", "lib_path", "EXPORTS",
+    "sait_outer_on_pattern", "sait_bicgstab_batched", "sait_bicgstab_multi", "BatchInfo", "Stats",
+    "TIMERS", "lib_path", "EXPORTS",
 ]
 
 DROP = {"none": 0, "abs": 1, "rowrel": 2, "pattern": 3}
@@ -41,6 +42,7 @@ EXPORTS = [
     "sait_prec_create_sait", "sait_prec_create_ilu", "sait_prec_levels", "sait_prec_apply",
     "sait_prec_destroy", "sait_gmres", "sait_bicgstab", "sait_ctx_set_timing", "sait_ctx_stats",
     "sait_apply_static", "sait_spmm", "sait_apply_multi", "sait_mat_transpose", "sait_outer_on_pattern",
+    "sait_bicgstab_batched", "sait_bicgstab_multi",
 ]
 APPLY_STATIC_MAX_N = 2097152  # SAIT_APPLY_STATIC_MAX_N in include/sait.h
 TIMERS = ["apply", "spmv", "ortho", "build", "ilu", "trisolve"]
@@ -62,6 +64,14 @@ class Stats(C.Structure):
         return {"launches": int(self.launches),
                 **{t: {"ms": float(self.ms[i]), "calls": int(self.calls[i])}
                    for i, t in enumerate(TIMERS)}}
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("nsys", C.c_int32), ("converged", C.c_int32), ("max_iters", C.c_int32),
+                ("graph_replays", C.c_int32), ("max_rel_resid", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Info(C.Structure):
@@ -116,6 +126,8 @@ def _L():
             "sait_apply_multi": [vp, vp, vp, i32, vp, i64, vp, i64],
             "sait_mat_transpose": [vp, vp, C.POINTER(vp)],
             "sait_outer_on_pattern": [vp, vp, d, vp, vp, vp],
+            "sait_bicgstab_batched": [vp, vp, vp, i32, vp, vp, vp, d, i32, C.POINTER(BatchInfo), vp, vp],
+            "sait_bicgstab_multi": [vp, vp, vp, i32, vp, vp, d, i32, C.POINTER(BatchInfo), vp, vp],
         }
         for name, args in sigs.items():
             f = getattr(lib, name)
@@ -438,3 +450,46 @@ def sait_bicgstab(ctx: Context, A: Mat, P: Prec | None, b: torch.Tensor,
     if check:
         _check(ctx, st, "sait_bicgstab")
     return x, info, st
+
+
+def sait_bicgstab_batched(ctx: Context, A: Mat, P: Prec | None, sys_ptr: torch.Tensor, b: torch.Tensor,
+                          x: torch.Tensor | None = None, tol: float = 1e-8, maxit: int = 10000,
+                          check: bool = True):
+    """BiCGSTAB on the independent diagonal blocks of A (rows sys_ptr[s]..sys_ptr[s+1]).
+
+    Returns (x, BatchInfo, status, per-system relative residuals, per-system iterations).
+    """
+    if sys_ptr.dtype != torch.int64 or not sys_ptr.is_cuda:
+        raise ValueError("sys_ptr: int64 CUDA tensor of nsys + 1 offsets")
+    nsys = sys_ptr.numel() - 1
+    _vec(b, A.n, "b")
+    x = torch.zeros_like(b) if x is None else _vec(x, A.n, "x")
+    rr = torch.empty(nsys, dtype=torch.float64, device=b.device)
+    its = torch.empty(nsys, dtype=torch.int32, device=b.device)
+    info = BatchInfo()
+    st = _L().sait_bicgstab_batched(ctx.h, A.h, P.h if P is not None else None, nsys, _ptr(sys_ptr), _ptr(b),
+                                    _ptr(x), float(tol), int(maxit), C.byref(info), _ptr(rr), _ptr(its))
+    if check:
+        _check(ctx, st, "sait_bicgstab_batched")
+    return x, info, st, rr, its
+
+
+def sait_bicgstab_multi(ctx: Context, A: Mat, P: Prec | None, B: torch.Tensor, X: torch.Tensor | None = None,
+                        tol: float = 1e-8, maxit: int = 10000, check: bool = True):
+    """BiCGSTAB for the k columns of the row-major n x k block B at once.
+
+    Returns (X, BatchInfo, status, per-column relative residuals, per-column iterations).
+    """
+    if B.dim() != 2 or not B.is_contiguous():
+        raise ValueError("B: contiguous row-major n x k block")
+    _block(B, A.n, "B")
+    k = B.shape[1]
+    X = torch.zeros_like(B) if X is None else _block(X, A.n, "X")
+    rr = torch.empty(k, dtype=torch.float64, device=B.device)
+    its = torch.empty(k, dtype=torch.int32, device=B.device)
+    info = BatchInfo()
+    st = _L().sait_bicgstab_multi(ctx.h, A.h, P.h if P is not None else None, k, _ptr_any(B), _ptr_any(X),
+                                  float(tol), int(maxit), C.byref(info), _ptr(rr), _ptr(its))
+    if check:
+        _check(ctx, st, "sait_bicgstab_multi")
+    return X, info, st, rr, its

@@ -141,7 +141,7 @@ struct DTemp {
     }
 };
 
-static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // ---- internal launchers (one translation unit each) -------------------------
 // scan.cu: out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.
