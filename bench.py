@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--grid", type=int, default=128)
     ap.add_argument("--m", type=int, default=3, help="series terms of SAIT")
-    ap.add_argument("--store", default="f64", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--store", default="f64", choices=["f64", "f32", "bf16", "f32x64", "bf16x64"])
     ap.add_argument("--no-extras", action="store_true", help="skip comparator and sweep runs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -148,9 +148,107 @@ def trisolve_step(sg, ctx, P: Problem, d):
     return x, info, sg.sait_prec_levels(pre), (L, U, Am, pre)
 
 
+def concat_block_diag(mats):
+    """Block-diagonal CSR of independent systems (numpy; input assembly only)."""
+    n = sum(m.n for m in mats)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    ci, va, r0, e0 = [], [], 0, 0
+    for m in mats:
+        rp[r0 + 1:r0 + m.n + 1] = m.rp[1:].astype(np.int64) + e0
+        ci.append(m.ci.astype(np.int64) + r0)
+        va.append(m.va)
+        r0 += m.n
+        e0 += m.nnz
+    return synth.CSR(n, rp.astype(np.int32), np.concatenate(ci).astype(np.int32), np.concatenate(va))
+
+
+def batched_workloads(sg, ctx, torch, device, stream):
+    """Many independent systems and many right-hand sides (one run each, FP32 and FP64 SAIT)."""
+    out = {}
+    sides, eps = synth.aniso2d_batch_params(512, synth.SEED_BASE + 4)
+    systems = [synth.aniso2d(int(s_), float(e_)) for s_, e_ in zip(sides, eps)]
+    A = concat_block_diag(systems)
+    ptr = np.concatenate([[0], np.cumsum([m.n for m in systems])]).astype(np.int64)
+    b = A.to_scipy() @ synth.uniform(synth.SEED_BASE + 5, A.n)
+    d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in
+         (("rp", A.rp), ("ci", A.ci), ("va", A.va), ("b", b), ("ptr", ptr))}
+
+    def solve_batch(store):
+        L, U = sg.sait_ilu0(ctx, A.n, d["rp"], d["ci"], d["va"])
+        P = sg.sait_prec_create_sait(ctx, sg.sait_build(ctx, L, True, 3, DROP, TAU, store=store),
+                                     sg.sait_build(ctx, U, False, 3, DROP, TAU, store=store))
+        Am = sg.sait_mat_create_csr(ctx, A.n, d["rp"], d["ci"], d["va"])
+        x, info, st, rr, its = sg.sait_bicgstab_batched(ctx, Am, P, d["ptr"], d["b"], tol=TOL, maxit=5000,
+                                                        check=False)
+        return info, (L, U, P, Am, x)
+
+    res = {}
+    for store in ("f32", "f32x64", "f64"):
+        solve_batch(store)                                   # warm-up (graph capture, pools)
+        ms, (info, keep) = time_region(torch, stream, lambda: solve_batch(store))
+        del keep
+        res[store] = {"ms": round(ms, 3), **info.as_dict()}
+    out["independent_systems"] = {"nsys": len(systems), "n": A.n, "nnz": A.nnz,
+                                  "sides": [int(sides.min()), int(sides.max())], "solver": "bicgstab",
+                                  "m_terms": 3, "tol": TOL, **res}
+    del d
+    torch.cuda.empty_cache()
+    # one 128^3 Poisson, 64 right-hand sides
+    A = synth.laplace3d(128)
+    k = 64
+    Xt = synth.uniform(synth.SEED_BASE + 6, (A.n, k))
+    B = np.ascontiguousarray(A.to_scipy() @ Xt)
+    del Xt
+    d = {kk: torch.from_numpy(np.ascontiguousarray(v)).to(device) for kk, v in
+         (("rp", A.rp), ("ci", A.ci), ("va", A.va), ("B", B))}
+    del B
+
+    def solve_multi(store):
+        L, U = sg.sait_ilu0(ctx, A.n, d["rp"], d["ci"], d["va"])
+        P = sg.sait_prec_create_sait(ctx, sg.sait_build(ctx, L, True, 3, DROP, TAU, store=store),
+                                     sg.sait_build(ctx, U, False, 3, DROP, TAU, store=store))
+        Am = sg.sait_mat_create_csr(ctx, A.n, d["rp"], d["ci"], d["va"])
+        X, info, st, rr, its = sg.sait_bicgstab_multi(ctx, Am, P, d["B"], tol=TOL, maxit=5000, check=False)
+        return info, (L, U, P, Am, X)
+
+    res = {}
+    for store in ("f32", "f32x64", "f64"):
+        solve_multi(store)
+        ms, (info, keep) = time_region(torch, stream, lambda: solve_multi(store))
+        del keep
+        res[store] = {"ms": round(ms, 3), **info.as_dict()}
+    out["many_rhs"] = {"n": A.n, "k": k, "solver": "bicgstab", "m_terms": 3, "tol": TOL, **res}
+    del d
+    torch.cuda.empty_cache()
+    return out
+
+
+def adjoint_workload(sg, ctx, torch, device, stream):
+    """Forward + backward of the differentiable solve on 64^3 log-normal diffusion."""
+    from paper_2106_12836_gb300.autograd import SolveOptions, sait_solve
+    A = synth.varcoef3d(64, 1.0, synth.SEED_BASE + 7)
+    d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in
+         (("rp", A.rp), ("ci", A.ci), ("va", A.va))}
+    b = torch.from_numpy(synth.uniform(synth.SEED_BASE + 8, A.n)).to(device)
+    xt = torch.from_numpy(synth.uniform(synth.SEED_BASE + 9, A.n)).to(device)
+    opts = SolveOptions(restart=50, tol=TOL, store="f32")
+
+    def run():
+        vals = d["va"].clone().requires_grad_(True)
+        bb = b.clone().requires_grad_(True)
+        x = sait_solve(vals, bb, d["rp"], d["ci"], ctx, opts)
+        loss = 0.5 * ((x - xt) ** 2).sum()
+        loss.backward()
+        return vals.grad
+
+    run()
+    ms, _ = time_region(torch, stream, run)
+    return {"n": A.n, "ms_forward_backward": round(ms, 3), "store": "f32", "restart": 50, "tol": TOL}
+
+
 def apply_bytes(n, nnz_l, nnz_u, store):
-    sv = {"f64": 8, "f32": 4, "bf16": 2}[store]
-    vec = 32 * n if store == "f64" else 24 * n   # r in, w out+in, z out
+    sv = {"f64": 8, "f32": 4, "bf16": 2, "f32x64": 4, "bf16x64": 2}[store]
+    vec = 32 * n if store in ("f64", "f32x64", "bf16x64") else 24 * n   # r in, w out+in, z out
     return (nnz_l + nnz_u) * (sv + 4) + 2 * 4 * (n + 1) + vec
 
 
@@ -396,6 +494,8 @@ def run_ours(a):
                           "apply_ms": round(st_m["apply"]["ms"] / max(st_m["apply"]["calls"], 1), 4)})
         out["m_sweep"] = sweep
         sg.sait_ctx_set_timing(ctx, False)
+        out["batched"] = batched_workloads(sg, ctx, torch, device, stream)
+        out["adjoint"] = adjoint_workload(sg, ctx, torch, device, stream)
 
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         v, sample, _ = oracle_sample(a.grid, a.m, gpu_iters=iters)

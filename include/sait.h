@@ -69,8 +69,22 @@ typedef struct {
 } sait_drop;
 
 /* Storage precision of a matrix's values for products (the FP64 values are
- * always kept as well).  FP32 and BF16 products accumulate in FP32. */
-typedef enum { SAIT_F64 = 0, SAIT_F32 = 1, SAIT_BF16 = 2 } sait_dtype;
+ * always kept as well) and the arithmetic of the products:
+ *   SAIT_F64       FP64 values, FP64 arithmetic;
+ *   SAIT_F32/BF16  FP32 / BF16 values, FP32 accumulation, and an FP32
+ *                  intermediate vector in the SAIT apply (fewest bytes; the
+ *                  rounding depends on the input, so the apply is not exactly
+ *                  linear -- restarted GMRES absorbs that, BiCGSTAB can stall);
+ *   SAIT_F32_X64/BF16_X64  FP32 / BF16 values, FP64 arithmetic and FP64
+ *                  intermediate (the rounded matrix applied exactly: a fixed
+ *                  linear preconditioner, with the byte savings of the storage). */
+typedef enum {
+    SAIT_F64 = 0,
+    SAIT_F32 = 1,
+    SAIT_BF16 = 2,
+    SAIT_F32_X64 = 3,
+    SAIT_BF16_X64 = 4
+} sait_dtype;
 
 typedef enum { SAIT_LOWER = 0, SAIT_UPPER = 1 } sait_uplo;
 
@@ -145,7 +159,7 @@ sait_status sait_mat_info(sait_mat M, int64_t *n, int64_t *nnz);
  * nnz and nnz entries.  Any pointer may be NULL to skip it.  Enqueues only. */
 sait_status sait_mat_export_csr(sait_ctx ctx, sait_mat M, int32_t *row_ptr, int32_t *col,
                                 double *val);
-/* Select the precision products with M read (SAIT_F64, SAIT_F32 or SAIT_BF16);
+/* Select the storage precision and arithmetic of M's products (sait_dtype);
  * creates the reduced copy of the values on first use.  Synchronizes. */
 sait_status sait_mat_set_store(sait_ctx ctx, sait_mat M, sait_dtype store);
 
@@ -174,13 +188,13 @@ sait_status sait_build(sait_ctx ctx, sait_mat T, sait_uplo uplo, int32_t m_terms
 
 /* ---- products ----------------------------------------------------------- */
 
-/* y = A x with A's selected storage precision (FP64 values accumulate in
- * FP64, FP32/BF16 values in FP32).  x and y must not overlap.  Enqueues only. */
+/* y = A x with A's selected storage precision and arithmetic (sait_dtype).
+ * x and y must not overlap.  Enqueues only. */
 sait_status sait_spmv(sait_ctx ctx, sait_mat A, const double *x, double *y);
 
 /* SAIT preconditioner apply z = M_U (M_L r) (Section 3.1).  The intermediate
- * vector is FP64 when both matrices are stored in FP64, otherwise FP32.
- * r and z must not overlap.  Enqueues only. */
+ * vector is FP64 when both matrices use FP64 arithmetic (SAIT_F64, *_X64),
+ * otherwise FP32.  r and z must not overlap.  Enqueues only. */
 sait_status sait_apply(sait_ctx ctx, sait_mat ML, sait_mat MU, const double *r, double *z);
 
 /* Block products for many right-hand sides / block eigenvectors.  X, Y, R, Z

@@ -31,7 +31,7 @@ __all__ = [
 ]
 
 DROP = {"none": 0, "abs": 1, "rowrel": 2, "pattern": 3}
-DTYPE = {"f64": 0, "f32": 1, "bf16": 2}
+DTYPE = {"f64": 0, "f32": 1, "bf16": 2, "f32x64": 3, "bf16x64": 4}
 LOWER, UPPER = 0, 1
 
 # Every entry point declared in include/sait.h.

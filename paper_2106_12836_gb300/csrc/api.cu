@@ -196,8 +196,9 @@ sait_status mat_alloc(sait_ctx ctx, int64_t n, int64_t nnz, sait_mat *out) {
     return SAIT_OK;
 }
 
-sait_status mat_prepare_store(sait_ctx ctx, sait_mat M, sait_dtype store) {
-    SAIT_TRY(mat_prepare_sell(ctx, M, store));
+sait_status mat_prepare_store(sait_ctx ctx, sait_mat M, sait_dtype store_mode) {
+    SAIT_TRY(mat_prepare_sell(ctx, M, store_mode));
+    const sait_dtype store = store_base(store_mode);
     if (store == SAIT_F32 && !M->va32) {
         SAIT_CK(cudaMalloc((void **)&M->va32, (M->nnz ? M->nnz : 1) * sizeof(float)));
         SAIT_CK(cast_values(M->va, M->va32, nullptr, M->nnz, ctx->stream));
@@ -205,7 +206,7 @@ sait_status mat_prepare_store(sait_ctx ctx, sait_mat M, sait_dtype store) {
         SAIT_CK(cudaMalloc((void **)&M->va16, (M->nnz ? M->nnz : 1) * sizeof(__nv_bfloat16)));
         SAIT_CK(cast_values(M->va, nullptr, M->va16, M->nnz, ctx->stream));
     }
-    M->store = store;
+    M->store = store_mode;
     return SAIT_OK;
 }
 
@@ -293,7 +294,7 @@ extern "C" sait_status sait_mat_export_csr(sait_ctx ctx, sait_mat M, int32_t *ro
 
 extern "C" sait_status sait_mat_set_store(sait_ctx ctx, sait_mat M, sait_dtype store) {
     if (!ctx) return SAIT_ERR_INVALID_ARG;
-    if (!M || store < SAIT_F64 || store > SAIT_BF16)
+    if (!M || !store_valid(store))
         return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_mat_set_store: bad argument");
     SAIT_TRY(mat_prepare_store(ctx, M, store));
     SAIT_CK(cudaStreamSynchronize(ctx->stream));
@@ -312,7 +313,7 @@ extern "C" sait_status sait_spmv(sait_ctx ctx, sait_mat A, const double *x, doub
 
 static sait_status apply_pair(sait_ctx ctx, sait_mat ML, sait_mat MU, const double *r, double *z,
                               void *w, const int *active) {
-    const bool f64 = ML->store == SAIT_F64 && MU->store == SAIT_F64;
+    const bool f64 = store_x64(ML->store) && store_x64(MU->store);
     ScopedTimer tm(ctx, SAIT_TIMER_APPLY);
     SAIT_CK(launch_spmv(ML, ML->store, r, false, w, !f64, active, ctx->stream,
                         group_counter(ctx, SAIT_TIMER_APPLY)));

@@ -54,7 +54,7 @@ extern "C" sait_status sait_apply_static(sait_mat ML, sait_mat MU, const double 
         return SAIT_ERR_CUDA;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    const bool f64 = ML->store == SAIT_F64 && MU->store == SAIT_F64;
+    const bool f64 = store_x64(ML->store) && store_x64(MU->store);
     cudaError_t e = launch_spmv(ML, ML->store, r, false, w, !f64, nullptr, s);
     if (e == cudaSuccess) e = launch_spmv(MU, MU->store, w, !f64, z, false, nullptr, s);
     if (e != cudaSuccess) {

@@ -27,8 +27,10 @@ constexpr int kPollB = 8;      // iterations replayed between status reads
 
 // per-system state (structure of arrays)
 struct BState {
-    double *rho, *rho_old, *alpha, *omega, *beta, *tolb, *bnorm, *red;  // red: nsys x 3 reduction results
-    int *active, *state, *iters;  // state: 0 run, 1 converged, 2 breakdown, 3 non-finite, 4 half step
+    double *rho, *rho_old, *alpha, *omega, *beta, *tolb, *bnorm, *rmin;  // rmin: smallest ||r|| so far
+    double *red;                                                          // nsys x 3 reduction results
+    int *active, *state, *iters;  // state: 0 run, 1 converged, 2 breakdown, 3 non-finite, 4 half step,
+                                  // 5 residual grew 1e4 x above its minimum: restart the recurrence
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -114,6 +116,7 @@ __global__ void k_b_start(int nsys, BState st, double tol) {  // red[.,0] = ||b|
     const double bn = sqrt(st.red[s * 3]), rn = sqrt(st.red[s * 3 + 1]);
     st.bnorm[s] = bn;
     st.tolb[s] = tol * bn;
+    st.rmin[s] = rn;
     st.rho_old[s] = st.alpha[s] = st.omega[s] = 1.0;
     st.iters[s] = 0;
     const bool done = bn == 0.0 || rn <= tol * bn;
@@ -174,7 +177,11 @@ __global__ void k_b_check_r(int nsys, BState st, int maxit) {
     const double rn = sqrt(st.red[s * 3]);
     if (!isfinite(rn)) { st.state[s] = 3; st.active[s] = 0; return; }
     if (rn <= st.tolb[s]) { st.state[s] = 1; st.active[s] = 0; return; }
-    if (st.iters[s] >= maxit) st.active[s] = 0;
+    if (st.iters[s] >= maxit) { st.active[s] = 0; return; }
+    // divergence guard: restart from the current iterate once the residual has
+    // grown four orders of magnitude above the best seen in this recurrence
+    if (rn > 1e4 * st.rmin[s]) { st.state[s] = 5; st.active[s] = 0; return; }
+    st.rmin[s] = fmin(st.rmin[s], rn);
 }
 
 __global__ void k_b_count(int nsys, const int *__restrict__ active, int *count) {
@@ -249,10 +256,11 @@ __global__ void k_b_relres(int nsys, const double *__restrict__ red, const doubl
 __global__ void k_b_restart(int nsys, BState st, const double *__restrict__ relres, double tol, int maxit) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsys) return;
-    if (st.state[s] == 1 && relres[s] > tol && st.iters[s] < maxit) {
+    if ((st.state[s] == 5 || (st.state[s] == 1 && relres[s] > tol)) && st.iters[s] < maxit) {
         st.state[s] = 0;
         st.active[s] = 1;
         st.rho_old[s] = st.alpha[s] = st.omega[s] = 1.0;
+        st.rmin[s] = relres[s] * st.bnorm[s];
     } else {
         st.active[s] = 0;
     }
@@ -359,7 +367,8 @@ BState make_state(Buffers &B, int nsys) {
     BState st;
     double *d = B.sc.p;
     st.rho = d; st.rho_old = d + nsys; st.alpha = d + 2 * nsys; st.omega = d + 3 * nsys;
-    st.beta = d + 4 * nsys; st.tolb = d + 5 * nsys; st.bnorm = d + 6 * nsys; st.red = B.red.p;
+    st.beta = d + 4 * nsys; st.tolb = d + 5 * nsys; st.bnorm = d + 6 * nsys; st.rmin = d + 7 * nsys;
+    st.red = B.red.p;
     st.active = B.si.p; st.state = B.si.p + nsys; st.iters = B.si.p + 2 * nsys;
     return st;
 }
@@ -552,7 +561,7 @@ extern "C" sait_status sait_bicgstab_batched(sait_ctx ctx, sait_mat A, sait_prec
         launch_k(k_b_count, gs, 256, 0, cs, (int)nsys, (const int *)st.active, ctx->d_word);
         SAIT_CK(cudaMemcpyAsync(h, ctx->d_word, sizeof(int), cudaMemcpyDeviceToHost, cs));
         SAIT_CK(cudaStreamSynchronize(cs));
-        if (h[0] == 0 || round >= 8) break;
+        if (h[0] == 0 || round >= 64) break;
         launch_k(k_bt_reset, gt, kT, 0, cs, TS, TB, TE, (const int *)st.active, (const double *)B.r.p, B.rh.p, B.p.p,
                  B.v.p);
     }
@@ -706,7 +715,7 @@ extern "C" sait_status sait_bicgstab_multi(sait_ctx ctx, sait_mat A, sait_prec P
         launch_k(k_b_count, gs, 256, 0, cs, (int)k, (const int *)st.active, ctx->d_word);
         SAIT_CK(cudaMemcpyAsync(h, ctx->d_word, sizeof(int), cudaMemcpyDeviceToHost, cs));
         SAIT_CK(cudaStreamSynchronize(cs));
-        if (h[0] == 0 || round >= 8) break;
+        if (h[0] == 0 || round >= 64) break;
         launch_k(k_mc_update<4>, ge, 256, 0, cs, n, (int)k, st, (const double *)Bf.r.p, (const double *)nullptr,
                  (const double *)Bf.v.p, (const double *)nullptr, Bf.rh.p, Bf.p.p);
     }

@@ -579,7 +579,7 @@ extern "C" sait_status sait_build(sait_ctx ctx, sait_mat T, sait_uplo uplo, int3
         return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_build: tau must lie in [0, 1)");
     if (drop.kind == SAIT_DROP_PATTERN && drop.p < 0)
         return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_build: p < 0");
-    if (store < SAIT_F64 || store > SAIT_BF16)
+    if (!store_valid(store))
         return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_build: bad storage type");
     const int64_t n = T->n, nnzT = T->nnz;
     cudaStream_t s = ctx->stream;

@@ -143,6 +143,34 @@ struct DTemp {
 
 __host__ __device__ static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Exact widening of stored FP32 / BF16 values to FP64 (a hardware
+// conversion; integer bit assembly measured slower on GB300).
+__device__ __forceinline__ double widen(float f) { return (double)f; }
+__device__ __forceinline__ double widen(__nv_bfloat16 b) {
+    return widen(__uint_as_float((uint32_t)__bfloat16_as_ushort(b) << 16));
+}
+__device__ __forceinline__ double widen(double v) { return v; }
+
+// value of storage type TV in accumulator type A
+template <typename A, typename TV> struct Load;
+template <typename TV> struct Load<double, TV> {
+    __device__ __forceinline__ static double get(TV v) { return widen(v); }
+};
+template <> struct Load<float, float> {
+    __device__ __forceinline__ static float get(float v) { return v; }
+};
+template <> struct Load<float, __nv_bfloat16> {
+    __device__ __forceinline__ static float get(__nv_bfloat16 v) { return __bfloat162float(v); }
+};
+
+// FP64 arithmetic in products with this storage (values converted exactly)
+static inline bool store_x64(sait_dtype s) { return s == SAIT_F64 || s == SAIT_F32_X64 || s == SAIT_BF16_X64; }
+// which value array a storage mode reads
+static inline sait_dtype store_base(sait_dtype s) {
+    return s == SAIT_F32_X64 ? SAIT_F32 : s == SAIT_BF16_X64 ? SAIT_BF16 : s;
+}
+static inline bool store_valid(int s) { return s >= SAIT_F64 && s <= SAIT_BF16_X64; }
+
 // ---- internal launchers (one translation unit each) -------------------------
 // scan.cu: out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.
 cudaError_t scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);

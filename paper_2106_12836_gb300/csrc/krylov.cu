@@ -303,10 +303,11 @@ __global__ void k_hsolve(const double *H, const double *g, double *y, int m, Sca
 }
 
 // ---- BiCGSTAB kernels ---------------------------------------------------------
-__global__ void k_bicg_init(Scal *sc) {
+__global__ void k_bicg_init(Scal *sc) {  // r0 holds ||r||^2 of the (re)start residual
     sc->rho_old = sc->alpha = sc->omega = 1.0;
     sc->active = 1;
     sc->state = 0;
+    sc->r3 = sqrt(sc->r0);  // smallest residual norm of this recurrence
 }
 
 __global__ void k_bicg_beta(Scal *sc) {  // after rho = (rh, r) in r0
@@ -393,7 +394,11 @@ __global__ void k_bicg_check_r(Scal *sc, int remaining) {  // after (r, r) in r0
     const double rn = sqrt(sc->r0);
     if (!isfinite(rn)) { sc->state = 3; sc->active = 0; return; }
     if (rn <= sc->tolb) { sc->state = 1; sc->active = 0; return; }
-    if (sc->jdone >= remaining) sc->active = 0;
+    if (sc->jdone >= remaining) { sc->active = 0; return; }
+    // divergence guard: restart the recurrence from the current iterate once
+    // the residual has grown four orders of magnitude above its minimum
+    if (rn > 1e4 * sc->r3) { sc->state = 5; sc->active = 0; return; }
+    sc->r3 = fmin(sc->r3, rn);
 }
 
 // ---- host helpers ---------------------------------------------------------------

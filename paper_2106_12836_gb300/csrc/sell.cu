@@ -20,14 +20,6 @@ namespace {
 template <typename TV> struct Ahead { static constexpr int value = 8; };
 template <> struct Ahead<double> { static constexpr int value = 4; };
 
-template <typename T> struct Acc;
-template <> struct Acc<double> { using type = double; };
-template <> struct Acc<float> { using type = float; };
-template <> struct Acc<__nv_bfloat16> { using type = float; };
-
-__device__ __forceinline__ double cvt(double v) { return v; }
-__device__ __forceinline__ float cvt(float v) { return v; }
-__device__ __forceinline__ float cvt(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 __device__ __forceinline__ double fmac(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmac(float a, float b, float c) { return fmaf(a, b, c); }
@@ -41,12 +33,11 @@ __device__ __forceinline__ __nv_bfloat16 lds(const __nv_bfloat16 *p) {
     return __ushort_as_bfloat16(u);
 }
 
-template <typename TV, typename TX, typename TY>
+template <typename TV, typename A, typename TX, typename TY>
 __global__ void __launch_bounds__(256)
 k_spmv_sell(int64_t n, int64_t nslices, const int64_t *__restrict__ soff, const int32_t *__restrict__ ci,
             const TV *__restrict__ va, const TX *__restrict__ x, TY *__restrict__ y,
             const int *__restrict__ active, int *calls) {
-    using A = typename Acc<TV>::type;
     constexpr int kU = Ahead<TV>::value;
     if (active && *active == 0) return;
     if (calls && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(calls, 1);
@@ -65,7 +56,7 @@ k_spmv_sell(int64_t n, int64_t nslices, const int64_t *__restrict__ soff, const 
 #pragma unroll
         for (int u = 0; u < kU; u++) {
             cc[u] = lds(c + 32 * u);
-            vv[u] = (A)cvt(lds(v + 32 * u));
+            vv[u] = Load<A, TV>::get(lds(v + 32 * u));
         }
 #pragma unroll
         for (int u = 0; u < kU; u++) xx[u] = cc[u] >= 0 ? (A)__ldg(x + cc[u]) : (A)0;
@@ -76,7 +67,7 @@ k_spmv_sell(int64_t n, int64_t nslices, const int64_t *__restrict__ soff, const 
     }
     for (; k < len; k++) {
         const int32_t cc = lds(c);
-        const A vv = (A)cvt(lds(v));
+        const A vv = Load<A, TV>::get(lds(v));
         if (cc >= 0) acc = fmac(vv, (A)__ldg(x + cc), acc);
         c += 32;
         v += 32;
@@ -120,24 +111,24 @@ __global__ void k_sell_fill(int64_t n, int64_t nslices, const int32_t *__restric
     }
 }
 
-template <typename TV, typename TX, typename TY>
+template <typename TV, typename TA, typename TX, typename TY>
 cudaError_t sell_launch(const sait_mat_s *A, const TV *va, const TX *x, TY *y, const int *active,
                         cudaStream_t s, int *calls) {
     const unsigned grid = (unsigned)cdiv(A->nslices * 32, 256);
-    launch_k(k_spmv_sell<TV, TX, TY>, grid, 256, 0, s, A->n, A->nslices, (const int64_t *)A->soff,
+    launch_k(k_spmv_sell<TV, TA, TX, TY>, grid, 256, 0, s, A->n, A->nslices, (const int64_t *)A->soff,
              (const int32_t *)A->sci, va, x, y, active, calls);
     return cudaGetLastError();
 }
 
-template <typename TV>
+template <typename TV, typename TA>
 cudaError_t sell_xy(const sait_mat_s *A, const TV *va, const void *x, bool x_f32, void *y, bool y_f32,
                     const int *active, cudaStream_t s, int *calls) {
     if (x_f32) {
-        if (y_f32) return sell_launch(A, va, (const float *)x, (float *)y, active, s, calls);
-        return sell_launch(A, va, (const float *)x, (double *)y, active, s, calls);
+        if (y_f32) return sell_launch<TV, TA>(A, va, (const float *)x, (float *)y, active, s, calls);
+        return sell_launch<TV, TA>(A, va, (const float *)x, (double *)y, active, s, calls);
     }
-    if (y_f32) return sell_launch(A, va, (const double *)x, (float *)y, active, s, calls);
-    return sell_launch(A, va, (const double *)x, (double *)y, active, s, calls);
+    if (y_f32) return sell_launch<TV, TA>(A, va, (const double *)x, (float *)y, active, s, calls);
+    return sell_launch<TV, TA>(A, va, (const double *)x, (double *)y, active, s, calls);
 }
 
 }  // namespace
@@ -180,6 +171,7 @@ sait_status mat_prepare_sell(sait_ctx ctx, sait_mat M, sait_dtype store) {
         SAIT_CK(cudaGetLastError());
     }
     const int64_t total = M->sell_nnz;
+    store = store_base(store);
     if (store == SAIT_F32 && !M->sva32) {
         SAIT_CK(cudaMalloc((void **)&M->sva32, std::max<int64_t>(total, 1) * sizeof(float)));
         launch_k(k_sell_fill<float>, grid, 256, 0, s, n, nslices, (const int32_t *)M->rp,
@@ -198,6 +190,7 @@ sait_status mat_prepare_sell(sait_ctx ctx, sait_mat M, sait_dtype store) {
 
 bool sell_ready(const sait_mat_s *A, sait_dtype store) {
     if (!A->soff) return false;
+    store = store_base(store);
     return store == SAIT_F64 ? A->sva64 != nullptr : store == SAIT_F32 ? A->sva32 != nullptr
                                                                           : A->sva16 != nullptr;
 }
@@ -205,8 +198,11 @@ bool sell_ready(const sait_mat_s *A, sait_dtype store) {
 cudaError_t launch_spmv_sell(const sait_mat_s *A, sait_dtype store, const void *x, bool x_f32, void *y,
                              bool y_f32, const int *active, cudaStream_t s, int *calls) {
     switch (store) {
-        case SAIT_F32: return sell_xy(A, A->sva32, x, x_f32, y, y_f32, active, s, calls);
-        case SAIT_BF16: return sell_xy(A, A->sva16, x, x_f32, y, y_f32, active, s, calls);
-        default: return sell_xy(A, A->sva64, x, x_f32, y, y_f32, active, s, calls);
+        case SAIT_F32: return sell_xy<float, float>(A, A->sva32, x, x_f32, y, y_f32, active, s, calls);
+        case SAIT_BF16: return sell_xy<__nv_bfloat16, float>(A, A->sva16, x, x_f32, y, y_f32, active, s, calls);
+        case SAIT_F32_X64: return sell_xy<float, double>(A, A->sva32, x, x_f32, y, y_f32, active, s, calls);
+        case SAIT_BF16_X64:
+            return sell_xy<__nv_bfloat16, double>(A, A->sva16, x, x_f32, y, y_f32, active, s, calls);
+        default: return sell_xy<double, double>(A, A->sva64, x, x_f32, y, y_f32, active, s, calls);
     }
 }

@@ -14,23 +14,14 @@
 
 namespace {
 
-template <typename T> struct Acc;
-template <> struct Acc<double> { using type = double; };
-template <> struct Acc<float> { using type = float; };
-template <> struct Acc<__nv_bfloat16> { using type = float; };
-
-__device__ __forceinline__ double cvt(double v) { return v; }
-__device__ __forceinline__ float cvt(float v) { return v; }
-__device__ __forceinline__ float cvt(__nv_bfloat16 v) { return __bfloat162float(v); }
 __device__ __forceinline__ double fmac(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmac(float a, float b, float c) { return fmaf(a, b, c); }
 
-template <int G, int CPL, typename TV, typename TX, typename TY>
+template <int G, int CPL, typename TV, typename A, typename TX, typename TY>
 __global__ void __launch_bounds__(256)
 k_spmm_csr(int64_t n, int k, int64_t ldx, int64_t ldy, const int32_t *__restrict__ rp,
            const int32_t *__restrict__ ci, const TV *__restrict__ va, const TX *__restrict__ X,
            TY *__restrict__ Y, int *calls) {
-    using A = typename Acc<TV>::type;
     if (calls && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(calls, 1);
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
     const int gl = threadIdx.x & (G - 1);
@@ -44,7 +35,7 @@ k_spmm_csr(int64_t n, int k, int64_t ldx, int64_t ldy, const int32_t *__restrict
     for (int base = b; base < e; base += G) {
         const int idx = base + gl;
         const int c_l = idx < e ? __ldg(ci + idx) : 0;
-        const A v_l = idx < e ? (A)cvt(va[idx]) : (A)0;
+        const A v_l = idx < e ? Load<A, TV>::get(va[idx]) : (A)0;
         const int cnt = min(G, e - base);
         for (int u = 0; u < cnt; u++) {
             const int c = __shfl_sync(gmask, c_l, u, G);
@@ -65,35 +56,35 @@ k_spmm_csr(int64_t n, int k, int64_t ldx, int64_t ldy, const int32_t *__restrict
     }
 }
 
-template <int G, int CPL, typename TV, typename TX, typename TY>
+template <int G, int CPL, typename TV, typename TA, typename TX, typename TY>
 void launch_gc(const sait_mat_s *A, const TV *va, int k, int64_t ldx, int64_t ldy, const TX *X, TY *Y,
                cudaStream_t s, int *calls) {
-    launch_k(k_spmm_csr<G, CPL, TV, TX, TY>, (unsigned)cdiv(A->n * G, 256), 256, 0, s, A->n, k, ldx, ldy,
+    launch_k(k_spmm_csr<G, CPL, TV, TA, TX, TY>, (unsigned)cdiv(A->n * G, 256), 256, 0, s, A->n, k, ldx, ldy,
              (const int32_t *)A->rp, (const int32_t *)A->ci, va, X, Y, calls);
 }
 
-template <typename TV, typename TX, typename TY>
+template <typename TV, typename TA, typename TX, typename TY>
 void launch_shape(const sait_mat_s *A, const TV *va, int k, int64_t ldx, int64_t ldy, const TX *X, TY *Y,
                   cudaStream_t s, int *calls) {
-    if (k <= 1) launch_gc<2, 1>(A, va, k, ldx, ldy, X, Y, s, calls);
-    else if (k <= 2) launch_gc<2, 1>(A, va, k, ldx, ldy, X, Y, s, calls);
-    else if (k <= 4) launch_gc<4, 1>(A, va, k, ldx, ldy, X, Y, s, calls);
-    else if (k <= 8) launch_gc<8, 1>(A, va, k, ldx, ldy, X, Y, s, calls);
-    else if (k <= 16) launch_gc<16, 1>(A, va, k, ldx, ldy, X, Y, s, calls);
-    else if (k <= 32) launch_gc<32, 1>(A, va, k, ldx, ldy, X, Y, s, calls);
-    else if (k <= 64) launch_gc<32, 2>(A, va, k, ldx, ldy, X, Y, s, calls);
-    else launch_gc<32, 4>(A, va, k, ldx, ldy, X, Y, s, calls);
+    if (k <= 1) launch_gc<2, 1, TV, TA>(A, va, k, ldx, ldy, X, Y, s, calls);
+    else if (k <= 2) launch_gc<2, 1, TV, TA>(A, va, k, ldx, ldy, X, Y, s, calls);
+    else if (k <= 4) launch_gc<4, 1, TV, TA>(A, va, k, ldx, ldy, X, Y, s, calls);
+    else if (k <= 8) launch_gc<8, 1, TV, TA>(A, va, k, ldx, ldy, X, Y, s, calls);
+    else if (k <= 16) launch_gc<16, 1, TV, TA>(A, va, k, ldx, ldy, X, Y, s, calls);
+    else if (k <= 32) launch_gc<32, 1, TV, TA>(A, va, k, ldx, ldy, X, Y, s, calls);
+    else if (k <= 64) launch_gc<32, 2, TV, TA>(A, va, k, ldx, ldy, X, Y, s, calls);
+    else launch_gc<32, 4, TV, TA>(A, va, k, ldx, ldy, X, Y, s, calls);
 }
 
-template <typename TV>
+template <typename TV, typename TA>
 cudaError_t spmm_xy(const sait_mat_s *A, const TV *va, int k, int64_t ldx, int64_t ldy, const void *X,
                     bool x_f32, void *Y, bool y_f32, cudaStream_t s, int *calls) {
     if (x_f32) {
-        if (y_f32) launch_shape(A, va, k, ldx, ldy, (const float *)X, (float *)Y, s, calls);
-        else launch_shape(A, va, k, ldx, ldy, (const float *)X, (double *)Y, s, calls);
+        if (y_f32) launch_shape<TV, TA>(A, va, k, ldx, ldy, (const float *)X, (float *)Y, s, calls);
+        else launch_shape<TV, TA>(A, va, k, ldx, ldy, (const float *)X, (double *)Y, s, calls);
     } else {
-        if (y_f32) launch_shape(A, va, k, ldx, ldy, (const double *)X, (float *)Y, s, calls);
-        else launch_shape(A, va, k, ldx, ldy, (const double *)X, (double *)Y, s, calls);
+        if (y_f32) launch_shape<TV, TA>(A, va, k, ldx, ldy, (const double *)X, (float *)Y, s, calls);
+        else launch_shape<TV, TA>(A, va, k, ldx, ldy, (const double *)X, (double *)Y, s, calls);
     }
     return cudaGetLastError();
 }
@@ -104,10 +95,18 @@ cudaError_t launch_spmm(const sait_mat_s *A, sait_dtype store, int k, int64_t ld
                         bool x_f32, void *Y, bool y_f32, cudaStream_t s, int *calls) {
     if (A->n == 0 || k <= 0) return cudaSuccess;
     switch (store) {
-        case SAIT_F32: return spmm_xy(A, (const float *)A->va32, k, ldx, ldy, X, x_f32, Y, y_f32, s, calls);
+        case SAIT_F32:
+            return spmm_xy<float, float>(A, (const float *)A->va32, k, ldx, ldy, X, x_f32, Y, y_f32, s, calls);
         case SAIT_BF16:
-            return spmm_xy(A, (const __nv_bfloat16 *)A->va16, k, ldx, ldy, X, x_f32, Y, y_f32, s, calls);
-        default: return spmm_xy(A, (const double *)A->va, k, ldx, ldy, X, x_f32, Y, y_f32, s, calls);
+            return spmm_xy<__nv_bfloat16, float>(A, (const __nv_bfloat16 *)A->va16, k, ldx, ldy, X, x_f32, Y, y_f32,
+                                                 s, calls);
+        case SAIT_F32_X64:
+            return spmm_xy<float, double>(A, (const float *)A->va32, k, ldx, ldy, X, x_f32, Y, y_f32, s, calls);
+        case SAIT_BF16_X64:
+            return spmm_xy<__nv_bfloat16, double>(A, (const __nv_bfloat16 *)A->va16, k, ldx, ldy, X, x_f32, Y,
+                                                  y_f32, s, calls);
+        default:
+            return spmm_xy<double, double>(A, (const double *)A->va, k, ldx, ldy, X, x_f32, Y, y_f32, s, calls);
     }
 }
 
@@ -124,7 +123,7 @@ extern "C" sait_status sait_spmm(sait_ctx ctx, sait_mat A, int32_t k, const doub
 
 sait_status apply_multi_impl(sait_ctx ctx, sait_mat ML, sait_mat MU, int k, const double *R, int64_t ldr,
                              double *Z, int64_t ldz, void *W) {
-    const bool f64 = ML->store == SAIT_F64 && MU->store == SAIT_F64;
+    const bool f64 = store_x64(ML->store) && store_x64(MU->store);
     ScopedTimer tm(ctx, SAIT_TIMER_APPLY);
     SAIT_CK(launch_spmm(ML, ML->store, k, ldr, k, R, false, W, !f64, ctx->stream,
                         group_counter(ctx, SAIT_TIMER_APPLY)));

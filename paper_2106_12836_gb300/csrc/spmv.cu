@@ -10,24 +10,15 @@
 
 namespace {
 
-template <typename T> struct Acc;
-template <> struct Acc<double> { using type = double; };
-template <> struct Acc<float> { using type = float; };
-template <> struct Acc<__nv_bfloat16> { using type = float; };
-
-__device__ __forceinline__ double ld(const double *p) { return __ldg(p); }
-__device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
-__device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
 
 __device__ __forceinline__ double fmac(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmac(float a, float b, float c) { return fmaf(a, b, c); }
 
-template <int G, typename TV, typename TX, typename TY>
+template <int G, typename TV, typename A, typename TX, typename TY>
 __global__ void __launch_bounds__(256)
 k_spmv_csr(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
            const TV *__restrict__ va, const TX *__restrict__ x, TY *__restrict__ y,
            const int *__restrict__ active, int *calls) {
-    using A = typename Acc<TV>::type;
     if (active && *active == 0) return;  // uniform over the grid
     if (calls && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(calls, 1);
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -36,41 +27,41 @@ k_spmv_csr(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict_
     A s = 0;
     if (row < n) {
         const int b = rp[row], e = rp[row + 1];
-        for (int k = b + lane; k < e; k += G) s = fmac(ld(va + k), (A)__ldg(x + ci[k]), s);
+        for (int k = b + lane; k < e; k += G) s = fmac(Load<A, TV>::get(va[k]), (A)__ldg(x + ci[k]), s);
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (row < n && lane == 0) y[row] = (TY)s;
 }
 
-template <typename TV, typename TX, typename TY>
+template <typename TV, typename TA, typename TX, typename TY>
 cudaError_t launch_g(int G, int64_t n, const int32_t *rp, const int32_t *ci, const TV *va,
                      const TX *x, TY *y, const int *active, cudaStream_t s, int *calls) {
     if (n == 0) return cudaSuccess;
     const int threads = 256;
     const unsigned blocks = (unsigned)cdiv(n * G, threads);
     switch (G) {
-        case 2: launch_k(k_spmv_csr<2, TV, TX, TY>, blocks, threads, 0, s, n, rp, ci, va, x, y, active, calls); break;
-        case 4: launch_k(k_spmv_csr<4, TV, TX, TY>, blocks, threads, 0, s, n, rp, ci, va, x, y, active, calls); break;
-        case 8: launch_k(k_spmv_csr<8, TV, TX, TY>, blocks, threads, 0, s, n, rp, ci, va, x, y, active, calls); break;
-        case 16: launch_k(k_spmv_csr<16, TV, TX, TY>, blocks, threads, 0, s, n, rp, ci, va, x, y, active, calls); break;
-        default: launch_k(k_spmv_csr<32, TV, TX, TY>, blocks, threads, 0, s, n, rp, ci, va, x, y, active, calls); break;
+        case 2: launch_k(k_spmv_csr<2, TV, TA, TX, TY>, blocks, threads, 0, s, n, rp, ci, va, x, y, active, calls); break;
+        case 4: launch_k(k_spmv_csr<4, TV, TA, TX, TY>, blocks, threads, 0, s, n, rp, ci, va, x, y, active, calls); break;
+        case 8: launch_k(k_spmv_csr<8, TV, TA, TX, TY>, blocks, threads, 0, s, n, rp, ci, va, x, y, active, calls); break;
+        case 16: launch_k(k_spmv_csr<16, TV, TA, TX, TY>, blocks, threads, 0, s, n, rp, ci, va, x, y, active, calls); break;
+        default: launch_k(k_spmv_csr<32, TV, TA, TX, TY>, blocks, threads, 0, s, n, rp, ci, va, x, y, active, calls); break;
     }
     return cudaGetLastError();
 }
 
-template <typename TV>
+template <typename TV, typename TA>
 cudaError_t launch_xy(const sait_mat_s *A, const TV *va, const void *x, bool x_f32, void *y,
                       bool y_f32, const int *active, cudaStream_t s, int *calls) {
     const int G = A->lanes;
     if (x_f32) {
         if (y_f32)
-            return launch_g(G, A->n, A->rp, A->ci, va, (const float *)x, (float *)y, active, s, calls);
-        return launch_g(G, A->n, A->rp, A->ci, va, (const float *)x, (double *)y, active, s, calls);
+            return launch_g<TV, TA>(G, A->n, A->rp, A->ci, va, (const float *)x, (float *)y, active, s, calls);
+        return launch_g<TV, TA>(G, A->n, A->rp, A->ci, va, (const float *)x, (double *)y, active, s, calls);
     }
     if (y_f32)
-        return launch_g(G, A->n, A->rp, A->ci, va, (const double *)x, (float *)y, active, s, calls);
-    return launch_g(G, A->n, A->rp, A->ci, va, (const double *)x, (double *)y, active, s, calls);
+        return launch_g<TV, TA>(G, A->n, A->rp, A->ci, va, (const double *)x, (float *)y, active, s, calls);
+    return launch_g<TV, TA>(G, A->n, A->rp, A->ci, va, (const double *)x, (double *)y, active, s, calls);
 }
 
 __global__ void k_cast(const double *__restrict__ src, float *d32, __nv_bfloat16 *d16, int64_t n) {
@@ -95,9 +86,12 @@ cudaError_t launch_spmv(const sait_mat_s *A, sait_dtype store, const void *x, bo
                         bool y_f32, const int *active, cudaStream_t s, int *calls) {
     if (sell_ready(A, store)) return launch_spmv_sell(A, store, x, x_f32, y, y_f32, active, s, calls);
     switch (store) {
-        case SAIT_F32: return launch_xy(A, A->va32, x, x_f32, y, y_f32, active, s, calls);
-        case SAIT_BF16: return launch_xy(A, A->va16, x, x_f32, y, y_f32, active, s, calls);
-        default: return launch_xy(A, A->va, x, x_f32, y, y_f32, active, s, calls);
+        case SAIT_F32: return launch_xy<float, float>(A, A->va32, x, x_f32, y, y_f32, active, s, calls);
+        case SAIT_BF16: return launch_xy<__nv_bfloat16, float>(A, A->va16, x, x_f32, y, y_f32, active, s, calls);
+        case SAIT_F32_X64: return launch_xy<float, double>(A, A->va32, x, x_f32, y, y_f32, active, s, calls);
+        case SAIT_BF16_X64:
+            return launch_xy<__nv_bfloat16, double>(A, A->va16, x, x_f32, y, y_f32, active, s, calls);
+        default: return launch_xy<double, double>(A, A->va, x, x_f32, y, y_f32, active, s, calls);
     }
 }
 

@@ -33,7 +33,7 @@ def block_diag(mats):
     return synth.CSR(B.shape[0], B.indptr.astype(np.int32), B.indices.astype(np.int32), B.data.copy())
 
 
-@pytest.mark.parametrize("store", ["f64", "f32"])
+@pytest.mark.parametrize("store", ["f64", "f32", "f32x64"])
 def test_batched_independent_systems(sg, oracle_lib, store):
     sides, eps = synth.aniso2d_batch_params(12, synth.SEED_BASE + 40, smin=5, smax=40)
     systems = [synth.aniso2d(int(s), float(e)) for s, e in zip(sides, eps)]

@@ -10,7 +10,7 @@ import torch
 import synth
 
 pytestmark = pytest.mark.gpu
-TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 1e-2}
+TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 1e-2, "f32x64": 1e-6, "bf16x64": 1e-2}
 
 
 @pytest.fixture(scope="module")
@@ -42,7 +42,7 @@ def test_spmm_matches_columns(sg, oracle_lib, k):
         assert np.all(np.abs(Y[:, t] - ref) <= 1e-12 * bound), t
 
 
-@pytest.mark.parametrize("store", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("store", ["f64", "f32", "bf16", "f32x64"])
 @pytest.mark.parametrize("k", [16, 64])
 def test_apply_multi_matches_columns(sg, oracle_lib, store, k):
     A = synth.varcoef3d(14, 1.0, 4)

@@ -175,7 +175,8 @@ def test_sait_errors(sg, ctx):
 
 
 # ---- products -------------------------------------------------------------------
-@pytest.mark.parametrize("store,tol", [("f64", 1e-12), ("f32", 1e-5), ("bf16", 1e-2)])
+@pytest.mark.parametrize("store,tol", [("f64", 1e-12), ("f32", 1e-5), ("bf16", 1e-2), ("f32x64", 1e-6),
+                                       ("bf16x64", 1e-2)])
 def test_apply_parity(sg, ctx, oracle_lib, store, tol):
     A = synth.convdiff3d(23)
     Lo, Uo = oracle_lib.ilu0(A)
@@ -189,6 +190,32 @@ def test_apply_parity(sg, ctx, oracle_lib, store, tol):
     absMU = synth.CSR(MUo.n, MUo.rp, MUo.ci, np.abs(MUo.va))
     bound = oracle_lib.apply(absML, absMU, np.abs(r))
     assert np.all(np.abs(z - zo) <= tol * bound)
+
+
+@pytest.mark.parametrize("store,rounding", [("f32x64", np.float32), ("bf16x64", "bf16")])
+def test_apply_x64_is_the_rounded_matrix_in_fp64(sg, ctx, oracle_lib, store, rounding):
+    """*_X64 storage applies exactly the rounded matrix: compare with the
+    oracle applying round(M) (rounded on the host) in FP64, FP64 tolerance."""
+    import torch as _t
+    A = synth.convdiff3d(21)
+    Lo, Uo = oracle_lib.ilu0(A)
+    MLo, MUo = oracle_lib.sait(Lo, 3, "rowrel", 1e-3), oracle_lib.sait(Uo, 3, "rowrel", 1e-3)
+
+    def rnd(v):
+        if rounding == "bf16":
+            return _t.from_numpy(v).to(_t.bfloat16).to(_t.float64).numpy()
+        return v.astype(np.float32).astype(np.float64)
+
+    MLr = synth.CSR(A.n, MLo.rp, MLo.ci, rnd(MLo.va))
+    MUr = synth.CSR(A.n, MUo.rp, MUo.ci, rnd(MUo.va))
+    ML = sg.sait_build(ctx, mat(sg, ctx, Lo), True, 3, "rowrel", 1e-3, store=store)
+    MU = sg.sait_build(ctx, mat(sg, ctx, Uo), False, 3, "rowrel", 1e-3, store=store)
+    r = synth.uniform(12, A.n)
+    z = sg.sait_apply(ctx, ML, MU, dev(r)).cpu().numpy()
+    zo = oracle_lib.apply(MLr, MUr, r)
+    bound = oracle_lib.apply(synth.CSR(A.n, MLr.rp, MLr.ci, np.abs(MLr.va)),
+                             synth.CSR(A.n, MUr.rp, MUr.ci, np.abs(MUr.va)), np.abs(r))
+    assert np.all(np.abs(z - zo) <= 1e-12 * bound)
 
 
 def test_spmv_parity_ragged(sg, ctx, oracle_lib):
