@@ -305,6 +305,19 @@ sait_status sait_prec_destroy(sait_prec P);
 sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const double *b, double *x,
                        int32_t restart, double tol, int32_t maxit, sait_info *info);
 
+/* The k smallest eigenpairs of symmetric positive definite A by LOBPCG
+ * (Knyazev 2001; the paper's block eigensolver, Section 4.4) with the SAIT
+ * preconditioner P applied to the residual block as two block products (or
+ * none when P is NULL).  X: device, n x k row-major; in: initial block (full
+ * rank), out: eigenvectors (orthonormal).  lambda: device, k doubles,
+ * ascending.  Converged columns (||A x_j - lambda_j x_j|| <= tol lambda_j
+ * ||x_j||) are locked softly; the Rayleigh-Ritz step on [X, W, P] is FP64
+ * (Cholesky, one-block Jacobi eigensolver).  1 <= k <= 20, 3k <= n.
+ * info->iters: iterations; info->rel_resid: largest column residual.
+ * Synchronizes every iteration (active count). */
+sait_status sait_lobpcg(sait_ctx ctx, sait_mat A, sait_prec P, int32_t k, double *X, double *lambda, double tol,
+                        int32_t maxit, sait_info *info);
+
 /* BiCGSTAB with right preconditioning (van der Vorst 1992; Saad,
  * Algorithm 7.7 on A P u = b).  Same conventions as sait_gmres; maxit bounds
  * the iterations (two products with A each). */

@@ -80,7 +80,11 @@ def _L():
                                                C.POINTER(C.c_int), C.POINTER(C.c_double)]
         _lib.ora_pcg.argtypes = solver + [C.c_double, C.c_int,
                                           C.POINTER(C.c_int), C.POINTER(C.c_double)]
-        for f in ("ora_trisolve", "ora_ilu0", "ora_sait", "ora_gmres", "ora_bicgstab", "ora_pcg"):
+        _lib.ora_lobpcg.argtypes = [i64, i32p, i32p, dp, C.POINTER(_Prec), C.c_int, dp, dp, C.c_double,
+                                    C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+        _lib.ora_sym_eig.argtypes = [C.c_int, dp, dp, dp]
+        for f in ("ora_trisolve", "ora_ilu0", "ora_sait", "ora_gmres", "ora_bicgstab", "ora_pcg",
+                  "ora_lobpcg", "ora_sym_eig"):
             getattr(_lib, f).restype = C.c_int
     return _lib
 
@@ -221,3 +225,29 @@ def pcg(A: CSR, b, prec: str = "none", lo: CSR | None = None, up: CSR | None = N
         tol: float = 1e-10, maxit: int = 10000, x0=None):
     """Preconditioned CG (the paper's solver).  Returns (x, iterations, true relres, status)."""
     return _solve(_L().ora_pcg, A, b, x0, prec, lo, up, C.c_double(tol), C.c_int(maxit))
+
+
+def lobpcg(A: CSR, X0: np.ndarray, prec: str = "none", lo: CSR | None = None, up: CSR | None = None,
+           tol: float = 1e-8, maxit: int = 500):
+    """k smallest eigenpairs of SPD A by LOBPCG.  Returns (lambda, X, iterations, max residual, status)."""
+    rp, ci, va = _csr_args(A)
+    X = np.array(X0, dtype=np.float64, order="C")
+    k = X.shape[1]
+    lam = np.zeros(k)
+    P, keep = _prec(prec, lo, up, A.n)
+    it = C.c_int(0)
+    rr = C.c_double(0.0)
+    st = _L().ora_lobpcg(A.n, _p(rp), _p(ci), _p(va), C.byref(P), k, _p(X), _p(lam), C.c_double(tol),
+                         C.c_int(maxit), C.byref(it), C.byref(rr))
+    del keep
+    return lam, X, int(it.value), float(rr.value), int(st)
+
+
+def sym_eig(Cm: np.ndarray):
+    """Eigenvalues (ascending) and eigenvectors of a small symmetric matrix (cyclic Jacobi)."""
+    Cc = np.array(Cm, dtype=np.float64, order="C")
+    m = Cc.shape[0]
+    w = np.zeros(m)
+    V = np.zeros((m, m))
+    _L().ora_sym_eig(m, _p(Cc), _p(w), _p(V))
+    return w, V

@@ -575,3 +575,305 @@ done:
     free(r); free(z); free(p); free(q); free(tmp);
     return st;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Dense helpers for LOBPCG (row-major blocks, column-major small matrices    */
+/* are avoided: every small matrix here is row-major m x m).                 */
+/* ------------------------------------------------------------------------ */
+
+/* G (p x q) = Y^T Z, Y n x p, Z n x q, row-major blocks */
+static void gram(int64_t n, const double *Y, int p, const double *Z, int q, double *G)
+{
+    for (int a = 0; a < p; a++)
+        for (int b = 0; b < q; b++) {
+            double s = 0.0;
+            for (int64_t i = 0; i < n; i++) s += Y[i * p + a] * Z[i * q + b];
+            G[a * q + b] = s;
+        }
+}
+
+/* Y (n x p) = Z (n x q) C (q x p) */
+static void block_mul(int64_t n, const double *Z, int q, const double *C, int p, double *Y)
+{
+    for (int64_t i = 0; i < n; i++)
+        for (int b = 0; b < p; b++) {
+            double s = 0.0;
+            for (int a = 0; a < q; a++) s += Z[i * q + a] * C[a * p + b];
+            Y[i * p + b] = s;
+        }
+}
+
+/* lower Cholesky factor of SPD G (m x m) in place; 1 if not positive definite */
+static int chol(int m, double *G)
+{
+    double mx = 0.0;
+    for (int i = 0; i < m; i++) if (G[i * m + i] > mx) mx = G[i * m + i];
+    for (int j = 0; j < m; j++) {
+        double d = G[j * m + j];
+        for (int k = 0; k < j; k++) d -= G[j * m + k] * G[j * m + k];
+        if (!(d > 1e-14 * mx)) return 1;
+        d = sqrt(d);
+        G[j * m + j] = d;
+        for (int i = j + 1; i < m; i++) {
+            double s = G[i * m + j];
+            for (int k = 0; k < j; k++) s -= G[i * m + k] * G[j * m + k];
+            G[i * m + j] = s / d;
+        }
+        for (int i = 0; i < j; i++) G[i * m + j] = 0.0;
+    }
+    return 0;
+}
+
+/* R (m x m) = L^{-1}, L lower triangular */
+static void tri_inv_lower(int m, const double *L, double *R)
+{
+    for (int j = 0; j < m; j++)
+        for (int i = 0; i < m; i++) {
+            if (i < j) { R[i * m + j] = 0.0; continue; }
+            double s = (i == j) ? 1.0 : 0.0;
+            for (int k = j; k < i; k++) s -= L[i * m + k] * R[k * m + j];
+            R[i * m + j] = s / L[i * m + i];
+        }
+}
+
+/* Cyclic Jacobi eigenvalue algorithm for symmetric C (Golub and Van Loan,
+ * Algorithm 8.5.3): C is overwritten; eigenvalues ascending in w, the
+ * corresponding eigenvectors are the columns of V (row-major m x m). */
+static void jacobi_eig(int m, double *C, double *w, double *V)
+{
+    for (int i = 0; i < m; i++)
+        for (int j = 0; j < m; j++) V[i * m + j] = (i == j) ? 1.0 : 0.0;
+    double fro = 0.0;
+    for (int i = 0; i < m * m; i++) fro += C[i] * C[i];
+    fro = sqrt(fro);
+    for (int sweep = 0; sweep < 60; sweep++) {
+        double off = 0.0;
+        for (int i = 0; i < m; i++)
+            for (int j = 0; j < m; j++) if (i != j) off += C[i * m + j] * C[i * m + j];
+        if (sqrt(off) <= 1e-15 * fro || fro == 0.0) break;
+        for (int p = 0; p < m - 1; p++)
+            for (int q = p + 1; q < m; q++) {
+                double apq = C[p * m + q];
+                if (apq == 0.0) continue;
+                /* symmetric 2x2 Schur decomposition (Golub and Van Loan, Algorithm 8.5.2) */
+                double tau = (C[q * m + q] - C[p * m + p]) / (2.0 * apq);
+                double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+                for (int k = 0; k < m; k++) {       /* C <- C J */
+                    double a = C[k * m + p], b = C[k * m + q];
+                    C[k * m + p] = c * a - s * b;
+                    C[k * m + q] = s * a + c * b;
+                }
+                for (int k = 0; k < m; k++) {       /* C <- J^T C */
+                    double a = C[p * m + k], b = C[q * m + k];
+                    C[p * m + k] = c * a - s * b;
+                    C[q * m + k] = s * a + c * b;
+                }
+                for (int k = 0; k < m; k++) {       /* V <- V J */
+                    double a = V[k * m + p], b = V[k * m + q];
+                    V[k * m + p] = c * a - s * b;
+                    V[k * m + q] = s * a + c * b;
+                }
+            }
+    }
+    for (int i = 0; i < m; i++) w[i] = C[i * m + i];
+    for (int i = 0; i < m; i++) {                   /* selection sort, ascending */
+        int best = i;
+        for (int j = i + 1; j < m; j++) if (w[j] < w[best]) best = j;
+        if (best != i) {
+            double t = w[i]; w[i] = w[best]; w[best] = t;
+            for (int k = 0; k < m; k++) { t = V[k * m + i]; V[k * m + i] = V[k * m + best]; V[k * m + best] = t; }
+        }
+    }
+}
+
+/* Y (n x p) <- Y D L^{-T} where D = diag(Y^T Y)^{-1/2} and D Y^T Y D = L L^T
+ * (Cholesky QR of the column-equilibrated block); AY likewise when given.
+ * Returns 1 when the Gram matrix is not numerically positive definite. */
+static int cholqr(int64_t n, double *Y, double *AY, int p, double *work)
+{
+    double *G = work, *R = work + p * p, *RT = work + 2 * p * p;
+    double dsc[64];
+    gram(n, Y, p, Y, p, G);
+    for (int a = 0; a < p; a++) {
+        if (!(G[a * p + a] > 0.0)) return 1;
+        dsc[a] = 1.0 / sqrt(G[a * p + a]);
+    }
+    for (int a = 0; a < p; a++) for (int b = 0; b < p; b++) G[a * p + b] *= dsc[a] * dsc[b];
+    if (chol(p, G)) return 1;
+    tri_inv_lower(p, G, R);
+    for (int a = 0; a < p; a++) for (int b = 0; b < p; b++) RT[a * p + b] = dsc[a] * R[b * p + a];
+    double *tmp = (double *)malloc((size_t)n * p * sizeof(double) + 8);
+    if (!tmp) return 1;
+    block_mul(n, Y, p, RT, p, tmp);
+    memcpy(Y, tmp, (size_t)n * p * sizeof(double));
+    if (AY) { block_mul(n, AY, p, RT, p, tmp); memcpy(AY, tmp, (size_t)n * p * sizeof(double)); }
+    free(tmp);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* LOBPCG for the k smallest eigenpairs of SPD A (Knyazev 2001, the method   */
+/* the paper's eigenvalue experiments use, Section 4.4) with a              */
+/* preconditioner T applied to the residual block, soft locking of          */
+/* converged columns, Cholesky-QR orthonormalisation of the W and P blocks, */
+/* and the Rayleigh-Ritz step on S = [X, W, P] in FP64.  Convergence of     */
+/* column j: ||A x_j - lambda_j x_j|| <= tol * lambda_j ||x_j||.            */
+/* X: n x k row-major, initial guess in, eigenvectors out.                   */
+/* ------------------------------------------------------------------------ */
+int ora_lobpcg(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, const ora_prec *P,
+               int k, double *X, double *lambda, double tol, int maxit, int *iters, double *resmax)
+{
+    if (k < 1 || 3 * k > n || maxit < 0) return ORA_INVALID;
+    const int m3 = 3 * k;
+    size_t nk = (size_t)n * k;
+    double *AX = malloc(nk * 8 + 8), *R = malloc(nk * 8 + 8), *W = malloc(nk * 8 + 8), *AW = malloc(nk * 8 + 8);
+    double *Pb = malloc(nk * 8 + 8), *AP = malloc(nk * 8 + 8), *S = malloc(nk * 3 * 8 + 8), *AS = malloc(nk * 3 * 8 + 8);
+    double *v = malloc((size_t)n * 8 + 8), *z = malloc((size_t)n * 8 + 8), *tmp = malloc((size_t)n * 8 + 8);
+    double *GA = malloc(m3 * m3 * 8), *GB = malloc(m3 * m3 * 8), *LI = malloc(m3 * m3 * 8), *C = malloc(m3 * m3 * 8);
+    double *Y = malloc(m3 * m3 * 8), *Cf = malloc(m3 * m3 * 8), *th = malloc(m3 * 8), *work = malloc(3 * m3 * m3 * 8);
+    double *res = malloc(k * 8);
+    int *act = malloc(k * sizeof(int));
+    int st = ORA_NOT_CONVERGED, havep = 0;
+    *iters = 0;
+    *resmax = 0.0;
+    if (!AX || !R || !W || !AW || !Pb || !AP || !S || !AS || !v || !z || !tmp || !GA || !GB || !LI || !C ||
+        !Y || !Cf || !th || !work || !res || !act) { st = ORA_OOM; goto done; }
+    /* initial Rayleigh-Ritz on span(X) */
+    if (cholqr(n, X, NULL, k, work)) { st = ORA_BREAKDOWN; goto done; }
+    for (int j = 0; j < k; j++) {
+        for (int64_t i = 0; i < n; i++) v[i] = X[i * k + j];
+        ora_spmv(n, rp, ci, va, v, z);
+        for (int64_t i = 0; i < n; i++) AX[i * k + j] = z[i];
+    }
+    gram(n, X, k, AX, k, GA);
+    for (int a = 0; a < k; a++) for (int b = 0; b < a; b++) {
+        double s = 0.5 * (GA[a * k + b] + GA[b * k + a]); GA[a * k + b] = GA[b * k + a] = s;
+    }
+    jacobi_eig(k, GA, th, Y);
+    block_mul(n, X, k, Y, k, S); memcpy(X, S, nk * 8);
+    block_mul(n, AX, k, Y, k, S); memcpy(AX, S, nk * 8);
+    for (int j = 0; j < k; j++) lambda[j] = th[j];
+
+    for (int it = 0; it <= maxit; it++) {
+        /* residuals and soft locking */
+        int na = 0;
+        *resmax = 0.0;
+        for (int j = 0; j < k; j++) {
+            double rn = 0.0, xn = 0.0;
+            for (int64_t i = 0; i < n; i++) {
+                double r = AX[i * k + j] - lambda[j] * X[i * k + j];
+                R[i * k + j] = r;
+                rn += r * r;
+                xn += X[i * k + j] * X[i * k + j];
+            }
+            res[j] = sqrt(rn) / (fabs(lambda[j]) * sqrt(xn));
+            if (res[j] > *resmax) *resmax = res[j];
+            if (res[j] > tol) act[na++] = j;
+        }
+        if (na == 0) { st = ORA_OK; break; }
+        if (it == maxit) break;
+        *iters = it + 1;
+        /* W = T R(:, active), orthogonal to X, orthonormal */
+        for (int a = 0; a < na; a++) {
+            for (int64_t i = 0; i < n; i++) v[i] = R[i * k + act[a]];
+            int ps = prec_apply(P, v, z, tmp);
+            if (ps) { st = ps; goto done; }
+            for (int64_t i = 0; i < n; i++) W[i * na + a] = z[i];
+        }
+        gram(n, X, k, W, na, C);                              /* C = X^T W (k x na) */
+        block_mul(n, X, k, C, na, S);
+        for (size_t q = 0; q < (size_t)n * na; q++) W[q] -= S[q];
+        if (cholqr(n, W, NULL, na, work)) { st = ORA_BREAKDOWN; goto done; }
+        for (int a = 0; a < na; a++) {
+            for (int64_t i = 0; i < n; i++) v[i] = W[i * na + a];
+            ora_spmv(n, rp, ci, va, v, z);
+            for (int64_t i = 0; i < n; i++) AW[i * na + a] = z[i];
+        }
+        /* P(:, active), orthonormal, with A P transformed alike */
+        int np = 0;
+        if (havep) {
+            for (int64_t i = 0; i < n; i++)
+                for (int a = 0; a < na; a++) {
+                    S[i * na + a] = Pb[i * k + act[a]];
+                    AS[i * na + a] = AP[i * k + act[a]];
+                }
+            memcpy(Pb, S, (size_t)n * na * 8);
+            memcpy(AP, AS, (size_t)n * na * 8);
+            np = cholqr(n, Pb, AP, na, work) ? 0 : na;
+        }
+        for (int attempt = 0; attempt < 2; attempt++) {
+            int m = k + na + np;
+            /* S = [X W P], AS = [AX AW AP] */
+            for (int64_t i = 0; i < n; i++) {
+                for (int a = 0; a < k; a++) { S[i * m + a] = X[i * k + a]; AS[i * m + a] = AX[i * k + a]; }
+                for (int a = 0; a < na; a++) { S[i * m + k + a] = W[i * na + a]; AS[i * m + k + a] = AW[i * na + a]; }
+                for (int a = 0; a < np; a++) {
+                    S[i * m + k + na + a] = Pb[i * na + a];
+                    AS[i * m + k + na + a] = AP[i * na + a];
+                }
+            }
+            gram(n, S, m, AS, m, GA);
+            gram(n, S, m, S, m, GB);
+            for (int a = 0; a < m; a++) for (int b = 0; b < a; b++) {
+                double s = 0.5 * (GA[a * m + b] + GA[b * m + a]); GA[a * m + b] = GA[b * m + a] = s;
+                s = 0.5 * (GB[a * m + b] + GB[b * m + a]); GB[a * m + b] = GB[b * m + a] = s;
+            }
+            if (chol(m, GB)) {
+                if (np > 0) { np = 0; continue; }              /* drop P and retry */
+                st = ORA_BREAKDOWN;
+                goto done;
+            }
+            tri_inv_lower(m, GB, LI);
+            /* C = L^{-1} GA L^{-T} */
+            for (int a = 0; a < m; a++) for (int b = 0; b < m; b++) {
+                double s = 0.0;
+                for (int q = 0; q <= a; q++) s += LI[a * m + q] * GA[q * m + b];
+                Cf[a * m + b] = s;
+            }
+            for (int a = 0; a < m; a++) for (int b = 0; b < m; b++) {
+                double s = 0.0;
+                for (int q = 0; q <= b; q++) s += Cf[a * m + q] * LI[b * m + q];
+                C[a * m + b] = s;
+            }
+            for (int a = 0; a < m; a++) for (int b = 0; b < a; b++) {
+                double s = 0.5 * (C[a * m + b] + C[b * m + a]); C[a * m + b] = C[b * m + a] = s;
+            }
+            jacobi_eig(m, C, th, Y);
+            /* coefficients c = L^{-T} Y(:, 0:k) */
+            for (int a = 0; a < m; a++) for (int b = 0; b < k; b++) {
+                double s = 0.0;
+                for (int q = a; q < m; q++) s += LI[q * m + a] * Y[q * m + b];
+                Cf[a * k + b] = s;
+            }
+            /* X = S c, AX = AS c, P = [W P] c(k:, :), AP = [AW AP] c(k:, :) */
+            block_mul(n, S, m, Cf, k, X);
+            block_mul(n, AS, m, Cf, k, AX);
+            int mw = na + np;
+            for (int64_t i = 0; i < n; i++)
+                for (int b = 0; b < k; b++) {
+                    double sp = 0.0, sa = 0.0;
+                    for (int a = 0; a < mw; a++) {
+                        sp += S[i * m + k + a] * Cf[(k + a) * k + b];
+                        sa += AS[i * m + k + a] * Cf[(k + a) * k + b];
+                    }
+                    Pb[i * k + b] = sp;
+                    AP[i * k + b] = sa;
+                }
+            havep = 1;
+            for (int j = 0; j < k; j++) lambda[j] = th[j];
+            break;
+        }
+    }
+done:
+    free(AX); free(R); free(W); free(AW); free(Pb); free(AP); free(S); free(AS); free(v); free(z); free(tmp);
+    free(GA); free(GB); free(LI); free(C); free(Y); free(Cf); free(th); free(work); free(res); free(act);
+    return st;
+}
+
+/* dense symmetric eigenvalues (Jacobi), exposed for pinning the helper */
+int ora_sym_eig(int m, double *C, double *w, double *V)
+{
+    jacobi_eig(m, C, w, V);
+    return ORA_OK;
+}

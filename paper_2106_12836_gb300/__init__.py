@@ -27,7 +27,7 @@ __all__ = [
     "sait_prec_destroy", "sait_gmres", "sait_bicgstab", "sait_ctx_set_timing", "sait_ctx_stats",
     "sait_apply_static", "APPLY_STATIC_MAX_N", "sait_spmm", "sait_apply_multi", "sait_mat_transpose",
     "sait_outer_on_pattern", "sait_bicgstab_batched", "sait_bicgstab_multi", "BatchInfo", "Stats",
-    "TIMERS", "lib_path", "EXPORTS",
+    "TIMERS", "lib_path", "EXPORTS", "sait_lobpcg",
 ]
 
 DROP = {"none": 0, "abs": 1, "rowrel": 2, "pattern": 3}
@@ -42,7 +42,7 @@ EXPORTS = [
     "sait_prec_create_sait", "sait_prec_create_ilu", "sait_prec_levels", "sait_prec_apply",
     "sait_prec_destroy", "sait_gmres", "sait_bicgstab", "sait_ctx_set_timing", "sait_ctx_stats",
     "sait_apply_static", "sait_spmm", "sait_apply_multi", "sait_mat_transpose", "sait_outer_on_pattern",
-    "sait_bicgstab_batched", "sait_bicgstab_multi",
+    "sait_bicgstab_batched", "sait_bicgstab_multi", "sait_lobpcg",
 ]
 APPLY_STATIC_MAX_N = 2097152  # SAIT_APPLY_STATIC_MAX_N in include/sait.h
 TIMERS = ["apply", "spmv", "ortho", "build", "ilu", "trisolve"]
@@ -128,6 +128,7 @@ def _L():
             "sait_outer_on_pattern": [vp, vp, d, vp, vp, vp],
             "sait_bicgstab_batched": [vp, vp, vp, i32, vp, vp, vp, d, i32, C.POINTER(BatchInfo), vp, vp],
             "sait_bicgstab_multi": [vp, vp, vp, i32, vp, vp, d, i32, C.POINTER(BatchInfo), vp, vp],
+            "sait_lobpcg": [vp, vp, vp, i32, vp, vp, d, i32, C.POINTER(Info)],
         }
         for name, args in sigs.items():
             f = getattr(lib, name)
@@ -493,3 +494,21 @@ def sait_bicgstab_multi(ctx: Context, A: Mat, P: Prec | None, B: torch.Tensor, X
     if check:
         _check(ctx, st, "sait_bicgstab_multi")
     return X, info, st, rr, its
+
+
+def sait_lobpcg(ctx: Context, A: Mat, P: Prec | None, X: torch.Tensor, tol: float = 1e-8, maxit: int = 500,
+                check: bool = True):
+    """k smallest eigenpairs of SPD A by LOBPCG; X (n x k, row-major) is the initial block.
+
+    Returns (lambda, X, info, status); X is overwritten with the eigenvectors.
+    """
+    if X.dim() != 2 or not X.is_contiguous():
+        raise ValueError("X: contiguous row-major n x k block")
+    _block(X, A.n, "X")
+    lam = torch.empty(X.shape[1], dtype=torch.float64, device=X.device)
+    info = Info()
+    st = _L().sait_lobpcg(ctx.h, A.h, P.h if P is not None else None, X.shape[1], _ptr_any(X), _ptr(lam),
+                          float(tol), int(maxit), C.byref(info))
+    if check:
+        _check(ctx, st, "sait_lobpcg")
+    return lam, X, info, st

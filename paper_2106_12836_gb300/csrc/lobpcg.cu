@@ -1,0 +1,573 @@
+// LOBPCG with a SAIT preconditioner (Knyazev 2001; the block eigensolver of
+// the paper's eigenvalue experiments, Section 4.4, where SAIT is applied to a
+// block of vectors as two sparse matrix-matrix products).
+//
+// Blocks are row-major n x p FP64 arrays.  Per iteration:
+//   R = A X - X diag(lambda); column residuals; soft locking of converged columns
+//   W = T R(:, active)                    (sait_apply_multi: one pass over M_L, M_U)
+//   W = W - X (X^T W); W = W L^{-T} with W^T W = L L^T      (Cholesky QR)
+//   P(:, active), A P(:, active) orthonormalised the same way (dropped if singular)
+//   Rayleigh-Ritz on S = [X W P]: G_A = S^T A S, G_B = S^T S (FP64), one-block
+//   dense solve: Cholesky of G_B, C = L^{-1} G_A L^{-T}, parallel cyclic
+//   Jacobi, coefficients L^{-T} Y(:, 0:k)
+//   X = S c, A X = (A S) c, P = [W P] c(k:, :), A P likewise.
+// The Rayleigh-Ritz step and all block products run in FP64 on the device.
+#include <algorithm>
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace {
+
+constexpr int kT = 256;
+constexpr int kMaxK = 20;           // block size limit (the Gram kernel holds <= 16 x 256 outputs)
+constexpr int kMaxM = 3 * kMaxK;    // Rayleigh-Ritz size limit
+constexpr int kRows = 32;           // rows per shared-memory tile of the Gram kernel
+
+// partial[b][a*q + c] = sum over block b's rows of Y[i, a] Z[i, c]
+__global__ void __launch_bounds__(kT)
+k_gram(int64_t n, int p, const double *__restrict__ Y, int64_t ldy, int q, const double *__restrict__ Z,
+       int64_t ldz, double *partial) {
+    extern __shared__ double sm[];
+    double *ys = sm;                  // kRows x p
+    double *zs = sm + kRows * p;      // kRows x q
+    const int pq = p * q;
+    double acc[16];
+    const int per = (pq + kT - 1) / kT;  // <= 9 for 48 x 48, <= 15 for 60 x 60
+#pragma unroll
+    for (int t = 0; t < 16; t++) acc[t] = 0.0;
+    for (int64_t r0 = (int64_t)blockIdx.x * kRows; r0 < n; r0 += (int64_t)gridDim.x * kRows) {
+        const int rows = (int)min((int64_t)kRows, n - r0);
+        for (int e = threadIdx.x; e < kRows * p; e += kT) {
+            const int r = e / p, a = e % p;
+            ys[e] = r < rows ? Y[(r0 + r) * ldy + a] : 0.0;
+        }
+        for (int e = threadIdx.x; e < kRows * q; e += kT) {
+            const int r = e / q, c = e % q;
+            zs[e] = r < rows ? Z[(r0 + r) * ldz + c] : 0.0;
+        }
+        __syncthreads();
+        for (int t = 0; t < per && t < 16; t++) {
+            const int o = threadIdx.x + t * kT;
+            if (o < pq) {
+                const int a = o / q, c = o % q;
+                double s = acc[t];
+                for (int r = 0; r < kRows; r++) s = fma(ys[r * p + a], zs[r * q + c], s);
+                acc[t] = s;
+            }
+        }
+        __syncthreads();
+    }
+    for (int t = 0; t < per && t < 16; t++) {
+        const int o = threadIdx.x + t * kT;
+        if (o < pq) partial[(int64_t)blockIdx.x * pq + o] = acc[t];
+    }
+}
+
+// G[o] = sum_b partial[b][o]
+__global__ void k_gram_reduce(int nb, int pq, const double *__restrict__ partial, double *G) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= pq) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; b++) s += partial[(int64_t)b * pq + o];
+    G[o] = s;
+}
+
+// Y (n x p, ldy) = (beta ? Y : 0) + sign * Z (n x q, ldz) C (q x p, row-major, ldc)
+__global__ void __launch_bounds__(kT)
+k_block_mul(int64_t n, int q, const double *__restrict__ Z, int64_t ldz, int p, const double *__restrict__ C,
+            int ldc, double *Y, int64_t ldy, int accumulate, double sign) {
+    __shared__ double cs[kMaxM * 16];
+    const int c0 = blockIdx.y * 16;  // output columns c0 .. c0+15
+    const int pc = min(16, p - c0);
+    for (int e = threadIdx.x; e < q * 16; e += kT) {
+        const int a = e / 16, b = e % 16;
+        cs[e] = b < pc ? C[a * ldc + c0 + b] : 0.0;
+    }
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
+        double acc[16];
+#pragma unroll
+        for (int b = 0; b < 16; b++) acc[b] = 0.0;
+        const double *zr = Z + i * ldz;
+        for (int a = 0; a < q; a++) {
+            const double z = zr[a];
+#pragma unroll
+            for (int b = 0; b < 16; b++) acc[b] = fma(z, cs[a * 16 + b], acc[b]);
+        }
+        double *yr = Y + i * ldy + c0;
+        for (int b = 0; b < pc; b++) yr[b] = accumulate ? yr[b] + sign * acc[b] : sign * acc[b];
+    }
+}
+
+// Y[:, dst_off + t] = Z[:, idx[t]] for t < cnt (column gather between blocks)
+__global__ void k_gather_cols(int64_t n, int cnt, const int *__restrict__ idx, const double *__restrict__ Z,
+                              int64_t ldz, double *Y, int64_t ldy, int dst_off) {
+    const int64_t tot = n * cnt;
+    for (int64_t e = (int64_t)blockIdx.x * kT + threadIdx.x; e < tot; e += (int64_t)gridDim.x * kT) {
+        const int64_t i = e / cnt;
+        const int t = (int)(e % cnt);
+        Y[i * ldy + dst_off + t] = Z[i * ldz + idx[t]];
+    }
+}
+
+// R = AX - X diag(lambda); partial sums of ||R_j||^2 and ||X_j||^2
+__global__ void __launch_bounds__(kT)
+k_residual_block(int64_t n, int k, const double *__restrict__ AX, const double *__restrict__ X,
+                 const double *__restrict__ lam, double *R, double *partial) {
+    __shared__ double red[2][kT];
+    const int c = threadIdx.x % k;
+    const int rpp = kT / k, r0 = threadIdx.x / k;
+    double sr = 0.0, sx = 0.0;
+    if ((int)threadIdx.x < rpp * k) {
+        const double l = lam[c];
+        for (int64_t i = (int64_t)blockIdx.x * rpp + r0; i < n; i += (int64_t)gridDim.x * rpp) {
+            const int64_t e = i * k + c;
+            const double x = X[e], r = AX[e] - l * x;
+            R[e] = r;
+            sr = fma(r, r, sr);
+            sx = fma(x, x, sx);
+        }
+    }
+    red[0][threadIdx.x] = sr;
+    red[1][threadIdx.x] = sx;
+    __syncthreads();
+    if ((int)threadIdx.x < k) {
+        double a = 0.0, b = 0.0;
+        for (int rr = 0; rr < rpp; rr++) {
+            a += red[0][rr * k + threadIdx.x];
+            b += red[1][rr * k + threadIdx.x];
+        }
+        partial[(int64_t)blockIdx.x * 2 * k + threadIdx.x] = a;
+        partial[(int64_t)blockIdx.x * 2 * k + k + threadIdx.x] = b;
+    }
+}
+
+// residual norms, soft-locking list of active columns (ascending), count
+__global__ void k_res_finish(int k, int nb, const double *__restrict__ partial, const double *__restrict__ lam,
+                             double tol, double *res, int *active, int *nact) {
+    __shared__ int flag[kMaxK];
+    const int c = threadIdx.x;
+    if (c < k) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < nb; q++) {
+            a += partial[(int64_t)q * 2 * k + c];
+            b += partial[(int64_t)q * 2 * k + k + c];
+        }
+        const double rr = sqrt(a) / (fabs(lam[c]) * sqrt(b));
+        res[c] = rr;
+        flag[c] = (rr > tol || !isfinite(rr)) ? 1 : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int na = 0;
+        for (int j = 0; j < k; j++)
+            if (flag[j]) active[na++] = j;
+        *nact = na;
+    }
+}
+
+// ---- small dense kernels (one block) ---------------------------------------------
+// In-place lower Cholesky of G (m x m, ld m) in shared memory; returns 1 on failure.
+__device__ int dev_chol(int m, double *G) {
+    __shared__ int fail;
+    __shared__ double mx;
+    if (threadIdx.x == 0) {
+        fail = 0;
+        mx = 0.0;
+        for (int i = 0; i < m; i++) mx = fmax(mx, G[i * m + i]);
+    }
+    __syncthreads();
+    for (int j = 0; j < m; j++) {
+        if (threadIdx.x == 0) {
+            double d = G[j * m + j];
+            for (int q = 0; q < j; q++) d -= G[j * m + q] * G[j * m + q];
+            if (!(d > 1e-14 * mx)) fail = 1;
+            G[j * m + j] = d > 0.0 ? sqrt(d) : 1.0;
+        }
+        __syncthreads();
+        const double djj = G[j * m + j];
+        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
+            double s = G[i * m + j];
+            for (int q = 0; q < j; q++) s -= G[i * m + q] * G[j * m + q];
+            G[i * m + j] = s / djj;
+        }
+        for (int i = threadIdx.x; i < j; i += blockDim.x) G[i * m + j] = 0.0;
+        __syncthreads();
+    }
+    return fail;
+}
+
+// R = L^{-1} (lower triangular), one column per thread
+__device__ void dev_tri_inv(int m, const double *L, double *R) {
+    for (int j = threadIdx.x; j < m; j += blockDim.x)
+        for (int i = 0; i < m; i++) {
+            if (i < j) { R[i * m + j] = 0.0; continue; }
+            double s = (i == j) ? 1.0 : 0.0;
+            for (int q = j; q < i; q++) s -= L[i * m + q] * R[q * m + j];
+            R[i * m + j] = s / L[i * m + i];
+        }
+    __syncthreads();
+}
+
+// Cholesky-QR factor for a block, with the Gram matrix equilibrated first
+// (columns of very different norms, e.g. residuals of nearly converged
+// columns, would otherwise fail the relative pivot test):
+// D = diag(G)^{-1/2}, D G D = L L^T, out (m x m) = D L^{-T}; flag on failure.
+__global__ void k_cholqr_factor(int m, const double *__restrict__ G, double *out, int *flag) {
+    extern __shared__ double sm[];
+    double *Gs = sm, *Ri = sm + m * m;
+    __shared__ double dsc[kMaxM];
+    for (int a = threadIdx.x; a < m; a += blockDim.x) {
+        const double g = G[a * m + a];
+        dsc[a] = g > 0.0 ? 1.0 / sqrt(g) : 0.0;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) Gs[e] = G[e] * dsc[e / m] * dsc[e % m];
+    __syncthreads();
+    int f = dev_chol(m, Gs);
+    if (threadIdx.x == 0)
+        for (int a = 0; a < m; a++) f |= dsc[a] == 0.0;
+    dev_tri_inv(m, Gs, Ri);
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int a = e / m, b = e % m;
+        out[e] = dsc[a] * Ri[b * m + a];  // D L^{-T}
+    }
+    if (threadIdx.x == 0) *flag = f;
+}
+
+// Rayleigh-Ritz: generalized symmetric eigenproblem GA c = theta GB c (m x m);
+// theta[0:k] ascending and coefficients c (m x k) = L^{-T} Y(:, 0:k); flag = 1
+// if GB is not numerically positive definite.
+__global__ void __launch_bounds__(kT) k_rayleigh_ritz(int m, int k, const double *__restrict__ GA,
+                                                      const double *__restrict__ GB, double *theta, double *coef,
+                                                      int *flag) {
+    extern __shared__ double sm[];
+    const int me = m + (m & 1);  // even size for the round-robin ordering
+    double *L = sm;              // m x m
+    double *Li = L + m * m;      // m x m
+    double *C = Li + m * m;      // me x me
+    double *V = C + me * me;     // me x me
+    double *T = V + me * me;     // m x m scratch
+    double *rot = T + m * m;     // me/2 x 2 (c, s)
+    int *pr = (int *)(rot + me); // me/2 x 2 pair indices
+    __shared__ double offn, fro;
+    for (int e = threadIdx.x; e < m * m; e += kT) {
+        const int a = e / m, b = e % m;
+        L[e] = 0.5 * (GB[a * m + b] + GB[b * m + a]);
+        T[e] = 0.5 * (GA[a * m + b] + GA[b * m + a]);
+    }
+    __syncthreads();
+    const int f = dev_chol(m, L);
+    if (threadIdx.x == 0) *flag = f;
+    if (f) return;  // uniform: f is read from shared memory by every thread
+    dev_tri_inv(m, L, Li);
+    // C = Li T Li^T (padded to me with a decoupled large diagonal entry)
+    for (int e = threadIdx.x; e < m * m; e += kT) {
+        const int a = e / m, b = e % m;
+        double s = 0.0;
+        for (int q = 0; q <= a; q++) s += Li[a * m + q] * T[q * m + b];
+        V[a * me + b] = s;  // temporary: Li T
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < me * me; e += kT) {
+        const int a = e / me, b = e % me;
+        double s = 0.0;
+        if (a < m && b < m)
+            for (int q = 0; q <= b; q++) s += V[a * me + q] * Li[b * m + q];
+        C[e] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < me * me; e += kT) {
+        const int a = e / me, b = e % me;
+        if (a < b) {
+            const double s = 0.5 * (C[a * me + b] + C[b * me + a]);
+            C[a * me + b] = s;
+            C[b * me + a] = s;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mx = 0.0, f2 = 0.0;
+        for (int i = 0; i < m; i++) mx = fmax(mx, fabs(C[i * me + i]));
+        if (me > m) C[m * me + m] = 10.0 * mx + 1.0;  // sorted last
+        for (int i = 0; i < me * me; i++) f2 += C[i] * C[i];
+        fro = sqrt(f2);
+    }
+    for (int e = threadIdx.x; e < me * me; e += kT) V[e] = (e / me == e % me) ? 1.0 : 0.0;
+    __syncthreads();
+    const int np = me / 2;
+    for (int sweep = 0; sweep < 40; sweep++) {
+        if (threadIdx.x == 0) {
+            double o = 0.0;
+            for (int a = 0; a < me; a++)
+                for (int b = 0; b < me; b++)
+                    if (a != b) o += C[a * me + b] * C[a * me + b];
+            offn = sqrt(o);
+        }
+        __syncthreads();
+        if (offn <= 1e-15 * fro || fro == 0.0) break;
+        for (int step = 0; step < me - 1; step++) {
+            // round-robin pairs: position 0 fixed, the others rotate
+            for (int t = threadIdx.x; t < np; t += kT) {
+                const int pa = t, pb = me - 1 - t;
+                const int p = pa == 0 ? 0 : ((pa - 1 + step) % (me - 1)) + 1;
+                const int q = ((pb - 1 + step) % (me - 1)) + 1;
+                const int lo = min(p, q), hi = max(p, q);
+                pr[2 * t] = lo;
+                pr[2 * t + 1] = hi;
+                const double apq = C[lo * me + hi];
+                double c = 1.0, s = 0.0;
+                if (apq != 0.0) {  // symmetric 2x2 Schur decomposition
+                    const double tau = (C[hi * me + hi] - C[lo * me + lo]) / (2.0 * apq);
+                    const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                    c = 1.0 / sqrt(1.0 + tt * tt);
+                    s = tt * c;
+                }
+                rot[2 * t] = c;
+                rot[2 * t + 1] = s;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < np * me; e += kT) {  // C <- C J, V <- V J (columns)
+                const int t = e / me, r = e % me;
+                const int p = pr[2 * t], q = pr[2 * t + 1];
+                const double c = rot[2 * t], s = rot[2 * t + 1];
+                double a = C[r * me + p], b = C[r * me + q];
+                C[r * me + p] = c * a - s * b;
+                C[r * me + q] = s * a + c * b;
+                a = V[r * me + p];
+                b = V[r * me + q];
+                V[r * me + p] = c * a - s * b;
+                V[r * me + q] = s * a + c * b;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < np * me; e += kT) {  // C <- J^T C (rows)
+                const int t = e / me, r = e % me;
+                const int p = pr[2 * t], q = pr[2 * t + 1];
+                const double c = rot[2 * t], s = rot[2 * t + 1];
+                const double a = C[p * me + r], b = C[q * me + r];
+                C[p * me + r] = c * a - s * b;
+                C[q * me + r] = s * a + c * b;
+            }
+            __syncthreads();
+        }
+    }
+    // sort: rank of each eigenvalue (ties by index), then pick the k smallest
+    __shared__ int order[kMaxM + 2];
+    for (int i = threadIdx.x; i < me; i += kT) {
+        const double wi = C[i * me + i];
+        int rank = 0;
+        for (int j = 0; j < me; j++) {
+            const double wj = C[j * me + j];
+            rank += (wj < wi) || (wj == wi && j < i);
+        }
+        order[rank] = i;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < k; j += kT) theta[j] = C[order[j] * me + order[j]];
+    // coef = Li^T V(:, order[0:k])  (rows 0..m-1)
+    for (int e = threadIdx.x; e < m * k; e += kT) {
+        const int a = e / k, j = e % k;
+        const int col = order[j];
+        double s = 0.0;
+        for (int q = a; q < m; q++) s += Li[q * m + a] * V[q * me + col];
+        coef[a * k + j] = s;
+    }
+}
+
+struct LWork {
+    int nb = 1;
+    DTemp<double> partial, G, G2, F, coef, theta, res, rpart;
+    DTemp<int> flag, active, nact;
+};
+
+sait_status gram(sait_ctx ctx, LWork &w, int64_t n, const double *Y, int p, int64_t ldy, const double *Z, int q,
+                 int64_t ldz, double *G) {
+    const size_t smem = (size_t)kRows * (p + q) * sizeof(double);
+    launch_k(k_gram, (unsigned)w.nb, kT, smem, ctx->stream, n, p, Y, ldy, q, Z, ldz, w.partial.p);
+    launch_k(k_gram_reduce, (unsigned)cdiv(p * q, 256), 256, 0, ctx->stream, w.nb, p * q,
+             (const double *)w.partial.p, G);
+    SAIT_CK(cudaGetLastError());
+    return SAIT_OK;
+}
+
+sait_status bmul(sait_ctx ctx, int64_t n, const double *Z, int q, int64_t ldz, const double *C, int p, int ldc,
+                 double *Y, int64_t ldy, bool accumulate, double sign) {
+    if (p <= 0 || q <= 0 || n == 0) return SAIT_OK;
+    dim3 grid((unsigned)std::min<int64_t>(cdiv(n, kT), (int64_t)ctx->num_sms * 8), (unsigned)cdiv(p, 16));
+    launch_k(k_block_mul, grid, kT, 0, ctx->stream, n, q, Z, ldz, p, C, ldc, Y, ldy, (int)accumulate, sign);
+    SAIT_CK(cudaGetLastError());
+    return SAIT_OK;
+}
+
+// Y (n x p) <- Y L^{-T}, AY likewise when given; returns 1 in *failed if singular
+sait_status cholqr(sait_ctx ctx, LWork &w, int64_t n, double *Y, double *AY, int p, double *tmp, int *failed) {
+    SAIT_TRY(gram(ctx, w, n, Y, p, p, Y, p, p, w.G.p));
+    launch_k(k_cholqr_factor, 1, kT, (size_t)2 * p * p * sizeof(double), ctx->stream, p, (const double *)w.G.p,
+             w.F.p, w.flag.p);
+    SAIT_CK(cudaGetLastError());
+    int *h = (int *)ctx->h_pinned;
+    SAIT_CK(cudaMemcpyAsync(h, w.flag.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    SAIT_CK(cudaStreamSynchronize(ctx->stream));
+    *failed = h[0];
+    if (h[0]) return SAIT_OK;
+    SAIT_TRY(bmul(ctx, n, Y, p, p, w.F.p, p, p, tmp, p, false, 1.0));
+    SAIT_CK(cudaMemcpyAsync(Y, tmp, (size_t)n * p * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    if (AY) {
+        SAIT_TRY(bmul(ctx, n, AY, p, p, w.F.p, p, p, tmp, p, false, 1.0));
+        SAIT_CK(cudaMemcpyAsync(AY, tmp, (size_t)n * p * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    return SAIT_OK;
+}
+
+}  // namespace
+
+extern "C" sait_status sait_lobpcg(sait_ctx ctx, sait_mat A, sait_prec P, int32_t k, double *X, double *lambda,
+                                   double tol, int32_t maxit, sait_info *info) {
+    if (!ctx) return SAIT_ERR_INVALID_ARG;
+    if (!A || k < 1 || k > kMaxK || 3 * (int64_t)k > A->n || !X || !lambda || !(tol > 0.0) || maxit < 0 ||
+        (P && P->kind != 1) || (P && P->n != A->n))
+        return ctx_fail(ctx, SAIT_ERR_INVALID_ARG,
+                        "sait_lobpcg: bad argument (1 <= k <= 20, 3k <= n, P a SAIT pair or NULL)");
+    const int64_t n = A->n;
+    cudaStream_t s = ctx->stream;
+    int *h = (int *)ctx->h_pinned;
+    const size_t nk = (size_t)n * k;
+    LWork w;
+    w.nb = (int)std::min<int64_t>(cdiv(n, kRows), 2LL * ctx->num_sms);
+    const int mmax = 3 * k;
+    DTemp<double> AX, R, W, AW, Pb, AP, S, AS, tmp, Wt;
+    for (DTemp<double> *d : {&AX, &R, &W, &AW, &Pb, &AP, &tmp, &Wt}) SAIT_CK(d->alloc(nk, s));
+    SAIT_CK(S.alloc(nk * 3, s));
+    SAIT_CK(AS.alloc(nk * 3, s));
+    SAIT_CK(w.partial.alloc((size_t)w.nb * mmax * mmax, s));
+    SAIT_CK(w.G.alloc((size_t)mmax * mmax, s));
+    SAIT_CK(w.G2.alloc((size_t)mmax * mmax, s));
+    SAIT_CK(w.F.alloc((size_t)mmax * mmax, s));
+    SAIT_CK(w.coef.alloc((size_t)mmax * k, s));
+    SAIT_CK(w.theta.alloc(k, s));
+    SAIT_CK(w.res.alloc(k, s));
+    const int rnb = (int)std::min<int64_t>(cdiv(n, kT / k), 2LL * ctx->num_sms);
+    SAIT_CK(w.rpart.alloc((size_t)rnb * 2 * k, s));
+    SAIT_CK(w.flag.alloc(1, s));
+    SAIT_CK(w.active.alloc(kMaxK, s));
+    SAIT_CK(w.nact.alloc(1, s));
+    const size_t rr_smem = (size_t)(2 * mmax * mmax + 3 * (mmax + 1) * (mmax + 1)) * sizeof(double) +
+                           (size_t)(mmax + 2) * sizeof(double) + (size_t)(mmax + 2) * sizeof(int) + 64;
+    SAIT_CK(cudaFuncSetAttribute(k_rayleigh_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rr_smem));
+    SAIT_CK(cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kRows * 2 * mmax * sizeof(double))));
+    auto spmm_a = [&](const double *Z, int p, double *Y) -> sait_status {
+        ScopedTimer tm(ctx, SAIT_TIMER_SPMV);
+        SAIT_CK(launch_spmm(A, SAIT_F64, p, p, p, Z, false, Y, false, s, group_counter(ctx, SAIT_TIMER_SPMV)));
+        return SAIT_OK;
+    };
+    auto rayleigh_ritz = [&](int m, const double *Sp, const double *ASp, int *failed) -> sait_status {
+        SAIT_TRY(gram(ctx, w, n, Sp, m, m, ASp, m, m, w.G.p));
+        SAIT_TRY(gram(ctx, w, n, Sp, m, m, Sp, m, m, w.G2.p));
+        launch_k(k_rayleigh_ritz, 1, kT, rr_smem, s, m, (int)k, (const double *)w.G.p, (const double *)w.G2.p,
+                 w.theta.p, w.coef.p, w.flag.p);
+        SAIT_CK(cudaGetLastError());
+        SAIT_CK(cudaMemcpyAsync(h, w.flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SAIT_CK(cudaStreamSynchronize(s));
+        *failed = h[0];
+        return SAIT_OK;
+    };
+    sait_info inf{0, 0, 0, 0, 0.0};
+    // initial Rayleigh-Ritz on span(X)
+    int failed = 0;
+    SAIT_TRY(cholqr(ctx, w, n, X, nullptr, k, tmp.p, &failed));
+    if (failed) return ctx_fail(ctx, SAIT_ERR_BREAKDOWN, "sait_lobpcg: initial block is rank deficient");
+    SAIT_TRY(spmm_a(X, k, AX.p));
+    SAIT_TRY(rayleigh_ritz(k, X, AX.p, &failed));
+    if (failed) return ctx_fail(ctx, SAIT_ERR_BREAKDOWN, "sait_lobpcg: initial Gram matrix singular");
+    SAIT_TRY(bmul(ctx, n, X, k, k, w.coef.p, k, k, tmp.p, k, false, 1.0));
+    SAIT_CK(cudaMemcpyAsync(X, tmp.p, nk * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    SAIT_TRY(bmul(ctx, n, AX.p, k, k, w.coef.p, k, k, tmp.p, k, false, 1.0));
+    SAIT_CK(cudaMemcpyAsync(AX.p, tmp.p, nk * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    SAIT_CK(cudaMemcpyAsync(lambda, w.theta.p, k * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    bool havep = false;
+    sait_status result = SAIT_ERR_NOT_CONVERGED;
+    std::vector<double> hres(k);
+    for (int it = 0; it <= maxit; it++) {
+        launch_k(k_residual_block, (unsigned)rnb, kT, 0, s, n, (int)k, (const double *)AX.p, (const double *)X,
+                 (const double *)lambda, R.p, w.rpart.p);
+        launch_k(k_res_finish, 1, 32 * (int)cdiv(k, 32), 0, s, (int)k, rnb, (const double *)w.rpart.p,
+                 (const double *)lambda, tol, w.res.p, w.active.p, w.nact.p);
+        SAIT_CK(cudaGetLastError());
+        SAIT_CK(cudaMemcpyAsync(h, w.nact.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SAIT_CK(cudaMemcpyAsync(hres.data(), w.res.p, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+        SAIT_CK(cudaStreamSynchronize(s));
+        const int na = h[0];
+        inf.rel_resid = *std::max_element(hres.begin(), hres.end());
+        if (!std::isfinite(inf.rel_resid)) { result = SAIT_ERR_NONFINITE; break; }
+        if (na == 0) { result = SAIT_OK; break; }
+        if (it == maxit) break;
+        inf.iters = it + 1;
+        // W = T R(:, active), orthogonalised against X, orthonormal
+        const unsigned gg = (unsigned)std::min<int64_t>(cdiv(n * na, kT), (int64_t)ctx->num_sms * 16);
+        launch_k(k_gather_cols, gg, kT, 0, s, n, na, (const int *)w.active.p, (const double *)R.p, (int64_t)k, Wt.p,
+                 (int64_t)na, 0);
+        if (P) SAIT_TRY(apply_multi_impl(ctx, P->lo, P->up, na, Wt.p, na, W.p, na, tmp.p));
+        else SAIT_CK(cudaMemcpyAsync(W.p, Wt.p, (size_t)n * na * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        SAIT_TRY(gram(ctx, w, n, X, k, k, W.p, na, na, w.G.p));                 // X^T W (k x na)
+        SAIT_TRY(bmul(ctx, n, X, k, k, w.G.p, na, na, W.p, na, true, -1.0));    // W -= X (X^T W)
+        SAIT_TRY(cholqr(ctx, w, n, W.p, nullptr, na, tmp.p, &failed));
+        if (failed) { result = SAIT_ERR_BREAKDOWN; break; }
+        SAIT_TRY(spmm_a(W.p, na, AW.p));
+        int np = 0;
+        if (havep) {  // P(:, active), A P(:, active)
+            launch_k(k_gather_cols, gg, kT, 0, s, n, na, (const int *)w.active.p, (const double *)Pb.p, (int64_t)k,
+                     Wt.p, (int64_t)na, 0);
+            launch_k(k_gather_cols, gg, kT, 0, s, n, na, (const int *)w.active.p, (const double *)AP.p, (int64_t)k,
+                     tmp.p, (int64_t)na, 0);
+            SAIT_CK(cudaMemcpyAsync(Pb.p, Wt.p, (size_t)n * na * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            SAIT_CK(cudaMemcpyAsync(AP.p, tmp.p, (size_t)n * na * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            SAIT_TRY(cholqr(ctx, w, n, Pb.p, AP.p, na, tmp.p, &failed));
+            np = failed ? 0 : na;
+        }
+        bool done = false;
+        for (int attempt = 0; attempt < 2 && !done; attempt++) {
+            const int m = k + na + np;
+            // S = [X W P], AS = [AX AW AP] (row-major n x m): column gathers by copies
+            SAIT_CK(cudaMemcpy2DAsync(S.p, m * sizeof(double), X, k * sizeof(double), k * sizeof(double), n,
+                                      cudaMemcpyDeviceToDevice, s));
+            SAIT_CK(cudaMemcpy2DAsync(S.p + k, m * sizeof(double), W.p, na * sizeof(double), na * sizeof(double), n,
+                                      cudaMemcpyDeviceToDevice, s));
+            SAIT_CK(cudaMemcpy2DAsync(AS.p, m * sizeof(double), AX.p, k * sizeof(double), k * sizeof(double), n,
+                                      cudaMemcpyDeviceToDevice, s));
+            SAIT_CK(cudaMemcpy2DAsync(AS.p + k, m * sizeof(double), AW.p, na * sizeof(double), na * sizeof(double),
+                                      n, cudaMemcpyDeviceToDevice, s));
+            if (np) {
+                SAIT_CK(cudaMemcpy2DAsync(S.p + k + na, m * sizeof(double), Pb.p, np * sizeof(double),
+                                          np * sizeof(double), n, cudaMemcpyDeviceToDevice, s));
+                SAIT_CK(cudaMemcpy2DAsync(AS.p + k + na, m * sizeof(double), AP.p, np * sizeof(double),
+                                          np * sizeof(double), n, cudaMemcpyDeviceToDevice, s));
+            }
+            SAIT_TRY(rayleigh_ritz(m, S.p, AS.p, &failed));
+            if (failed) {
+                if (np) { np = 0; continue; }  // drop P and retry
+                result = SAIT_ERR_BREAKDOWN;
+                break;
+            }
+            // X = S c, AX = AS c, P = [W P] c(k:, :), AP = [AW AP] c(k:, :)
+            SAIT_TRY(bmul(ctx, n, S.p, m, m, w.coef.p, k, k, X, k, false, 1.0));
+            SAIT_TRY(bmul(ctx, n, AS.p, m, m, w.coef.p, k, k, AX.p, k, false, 1.0));
+            SAIT_TRY(bmul(ctx, n, S.p + k, na + np, m, w.coef.p + (size_t)k * k, k, k, Pb.p, k, false, 1.0));
+            SAIT_TRY(bmul(ctx, n, AS.p + k, na + np, m, w.coef.p + (size_t)k * k, k, k, AP.p, k, false, 1.0));
+            SAIT_CK(cudaMemcpyAsync(lambda, w.theta.p, k * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            havep = true;
+            done = true;
+        }
+        if (!done) break;
+    }
+    if (info) *info = inf;
+    SAIT_CK(cudaStreamSynchronize(s));
+    if (result != SAIT_OK) {
+        char buf[160];
+        snprintf(buf, sizeof(buf), "sait_lobpcg: %s after %d iterations, max residual %.3e", sait_status_string(result),
+                 inf.iters, inf.rel_resid);
+        return ctx_fail(ctx, result, buf);
+    }
+    return SAIT_OK;
+}

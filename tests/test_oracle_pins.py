@@ -363,3 +363,50 @@ def test_errors(oracle_lib):
     assert e.value.code == 3
     M = oracle_lib.sait(synth.from_dense(np.diag([2.0, 4.0])), 1)
     assert np.allclose(M.to_dense(), np.diag([0.5, 0.25]))
+
+
+# --------------------------------------------------------------------------
+# LOBPCG (Knyazev 2001; the paper's eigenvalue solver, Section 4.4) and its
+# dense helper.
+# --------------------------------------------------------------------------
+def test_sym_eig_matches_lapack(oracle_lib):
+    rng = np.random.default_rng(8)
+    for m in (1, 2, 7, 31):
+        B = rng.standard_normal((m, m))
+        Cm = B + B.T
+        w, V = oracle_lib.sym_eig(Cm)
+        assert np.abs(w - np.linalg.eigvalsh(Cm)).max() <= 1e-13 * max(1.0, np.abs(w).max())
+        assert np.abs(Cm @ V - V * w).max() <= 1e-12 * max(1.0, np.abs(w).max())
+        assert np.abs(V.T @ V - np.eye(m)).max() <= 1e-13
+
+
+def laplace_eigs(N, k):
+    """Eigenvalues of the h^2-scaled 7-point Laplacian on N^3: sum_d 4 sin^2(j_d pi / (2(N+1)))."""
+    j = np.arange(1, N + 1)
+    l1 = 4 * np.sin(j * np.pi / (2 * (N + 1))) ** 2
+    return np.sort((l1[:, None, None] + l1[None, :, None] + l1[None, None, :]).ravel())[:k]
+
+
+@pytest.mark.parametrize("prec", ["none", "sait", "ilu"])
+def test_lobpcg_laplace_closed_form(oracle_lib, prec):
+    N, k = 10, 16                       # the 16th eigenvalue sits inside a degenerate cluster
+    A = synth.laplace3d(N)
+    L, U = oracle_lib.ilu0(A)
+    lo, up = ((oracle_lib.sait(L, 3, "rowrel", 1e-3), oracle_lib.sait(U, 3, "rowrel", 1e-3))
+              if prec == "sait" else (L, U))
+    X0 = synth.uniform(5, (A.n, k))
+    lam, X, it, rr, st = oracle_lib.lobpcg(A, X0, prec, lo, up, tol=1e-8, maxit=500)
+    assert st == 0 and rr <= 1e-8
+    assert np.abs(lam - laplace_eigs(N, k)).max() <= 1e-12 * lam.max()
+    assert np.abs(X.T @ X - np.eye(k)).max() <= 1e-10
+    R = A.to_scipy() @ X - X * lam
+    assert np.all(np.linalg.norm(R, axis=0) <= 1e-8 * lam * 1.0001)
+
+
+def test_lobpcg_variable_coefficients_dense(oracle_lib):
+    A = synth.varcoef3d(7, 1.0, 3)
+    k = 6
+    lam, X, it, rr, st = oracle_lib.lobpcg(A, synth.uniform(6, (A.n, k)), tol=1e-9, maxit=1000)
+    ref = np.linalg.eigvalsh(A.to_dense())[:k]
+    assert st == 0
+    assert np.abs(lam - ref).max() <= 1e-12 * ref.max()
