@@ -223,6 +223,39 @@ def batched_workloads(sg, ctx, torch, device, stream):
     return out
 
 
+def eigen_workload(sg, ctx, torch, device, stream, factors="ilu0"):
+    """16 smallest eigenpairs of 96^3 log-normal diffusion by SAIT-preconditioned LOBPCG."""
+    A = synth.varcoef3d(96, 1.0, synth.SEED_BASE + 3)
+    d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in
+         (("rp", A.rp), ("ci", A.ci), ("va", A.va))}
+    X0 = torch.from_numpy(synth.uniform(synth.SEED_BASE + 10, (A.n, 16))).to(device)
+
+    def solve(store):
+        if factors == "ilut":
+            L, U = sg.sait_ilut(ctx, A.n, d["rp"], d["ci"], d["va"], 1e-4, 10)
+        else:
+            L, U = sg.sait_ilu0(ctx, A.n, d["rp"], d["ci"], d["va"])
+        P = sg.sait_prec_create_sait(ctx, sg.sait_build(ctx, L, True, 3, DROP, TAU, store=store),
+                                     sg.sait_build(ctx, U, False, 3, DROP, TAU, store=store))
+        Am = sg.sait_mat_create_csr(ctx, A.n, d["rp"], d["ci"], d["va"])
+        lam, X, info, st = sg.sait_lobpcg(ctx, Am, P, X0.clone(), tol=TOL, maxit=1000, check=False)
+        return lam, info, st, (L, U, P, Am, X)
+
+    out = {"n": A.n, "k": 16, "factors": factors, "m_terms": 3, "tol": TOL}
+    ref = None
+    for store in ("f64", "f32", "bf16"):
+        solve(store)
+        ms, (lam, info, st, keep) = time_region(torch, stream, lambda: solve(store))
+        del keep
+        lam = lam.cpu().numpy()
+        if ref is None:
+            ref = lam
+        out[store] = {"ms": round(ms, 3), "iters": info.iters, "max_resid": info.rel_resid, "status": st,
+                      "max_rel_eig_diff_vs_f64": float(np.abs(lam - ref).max() / np.abs(ref).max()),
+                      "lambda_min": float(lam[0]), "lambda_max": float(lam[-1])}
+    return out
+
+
 def adjoint_workload(sg, ctx, torch, device, stream):
     """Forward + backward of the differentiable solve on 64^3 log-normal diffusion."""
     from paper_2106_12836_gb300.autograd import SolveOptions, sait_solve
@@ -496,6 +529,7 @@ def run_ours(a):
         sg.sait_ctx_set_timing(ctx, False)
         out["batched"] = batched_workloads(sg, ctx, torch, device, stream)
         out["adjoint"] = adjoint_workload(sg, ctx, torch, device, stream)
+        out["eigen"] = eigen_workload(sg, ctx, torch, device, stream)
 
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         v, sample, _ = oracle_sample(a.grid, a.m, gpu_iters=iters)
