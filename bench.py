@@ -256,6 +256,39 @@ def eigen_workload(sg, ctx, torch, device, stream, factors="ilu0"):
     return out
 
 
+def paper_replica_workload(sg, ctx, torch, device, stream):
+    """Section 4's experiment on the GPU: 100^3 Laplacian, ILU(0), PCG to 1e-10 with
+    SAIT_Thr(tau, 10), SAIT_Pat(p, 10), the exact substitution and k Jacobi sweeps."""
+    A = synth.laplace3d(100)
+    d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in
+         (("rp", A.rp), ("ci", A.ci), ("va", A.va))}
+    b = torch.from_numpy(synth.uniform(synth.SEED_BASE, A.n, 0.0, 1.0)).to(device)
+    Am = sg.sait_mat_create_csr(ctx, A.n, d["rp"], d["ci"], d["va"])
+    L, U = sg.sait_ilu0(ctx, A.n, d["rp"], d["ci"], d["va"])
+    tol, m = 1e-10, 10
+
+    def pcg(P):
+        sg.sait_pcg(ctx, Am, P, b, tol=tol)                  # warm-up
+        ms, (_, info, _) = time_region(torch, stream, lambda: sg.sait_pcg(ctx, Am, P, b, tol=tol))
+        return {"iters": info.iters, "pcg_ms": round(ms, 3), "rel_resid": info.rel_resid}
+
+    out = {"n": A.n, "tol": tol, "m": m, "rows": []}
+    out["exact_ilu0"] = pcg(sg.sait_prec_create_ilu(ctx, L, U))
+    for name, drop, tau, p in [("SAIT_Thr(0.05,10)", "abs", 0.05, 0), ("SAIT_Thr(0.02,10)", "abs", 0.02, 0),
+                               ("SAIT_Thr(0.01,10)", "abs", 0.01, 0), ("SAIT_Pat(1,10)", "pattern", 0.0, 1),
+                               ("SAIT_Pat(2,10)", "pattern", 0.0, 2), ("SAIT_Pat(3,10)", "pattern", 0.0, 3)]:
+        terms = m + 1 + p
+        sg.sait_build(ctx, L, True, terms, drop, tau, p)       # warm-up
+        ms_b, (ML, MU) = time_region(torch, stream, lambda: (sg.sait_build(ctx, L, True, terms, drop, tau, p),
+                                                             sg.sait_build(ctx, U, False, terms, drop, tau, p)))
+        row = {"name": name, "ratio": round(MU.nnz / U.nnz, 2), "build_ms": round(ms_b, 3)}
+        row.update(pcg(sg.sait_prec_create_sait(ctx, ML, MU)))
+        row["total_ms"] = round(row["build_ms"] + row["pcg_ms"], 3)
+        out["rows"].append(row)
+    out["jacobi"] = [{"sweeps": k, **pcg(sg.sait_prec_create_jacobi(ctx, L, U, k))} for k in (1, 2, 3, 4, 6, 10, 15)]
+    return out
+
+
 def adjoint_workload(sg, ctx, torch, device, stream):
     """Forward + backward of the differentiable solve on 64^3 log-normal diffusion."""
     from paper_2106_12836_gb300.autograd import SolveOptions, sait_solve
@@ -530,6 +563,7 @@ def run_ours(a):
         out["batched"] = batched_workloads(sg, ctx, torch, device, stream)
         out["adjoint"] = adjoint_workload(sg, ctx, torch, device, stream)
         out["eigen"] = eigen_workload(sg, ctx, torch, device, stream)
+        out["paper_replica"] = paper_replica_workload(sg, ctx, torch, device, stream)
 
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         v, sample, _ = oracle_sample(a.grid, a.m, gpu_iters=iters)

@@ -284,6 +284,15 @@ sait_status sait_prec_create_sait(sait_ctx ctx, sait_mat ML, sait_mat MU, sait_p
  * triangular solves SAIT replaces; the paper's comparison in Section 4).
  * Computes the level sets on the GPU.  Synchronizes. */
 sait_status sait_prec_create_ilu(sait_ctx ctx, sait_mat L, sait_mat U, sait_prec *P);
+/* Jacobi sweeps (Section 4, comparison with Jacobi iteration): `sweeps`
+ * iterations of x^j = T~ x^{j-1} + D^-1 b (Section 2, equation Jacobi_iter)
+ * from x^0 = 0, first on L y = r, then on U z = y.  This applies the undropped
+ * series M_k of both factors without forming it; it is the comparator the
+ * paper uses to show why the stored SAIT matrices are cheaper.  L and U are
+ * any square matrices with a nonzero diagonal (triangular in practice) and
+ * must outlive P.  sweeps >= 1, else SAIT_ERR_INVALID_ARG; a zero, missing or
+ * non-finite diagonal entry gives SAIT_ERR_ZERO_PIVOT.  Synchronizes. */
+sait_status sait_prec_create_jacobi(sait_ctx ctx, sait_mat L, sait_mat U, int32_t sweeps, sait_prec *P);
 /* Number of level sets of the lower and upper factor (ILU preconditioner). */
 sait_status sait_prec_levels(sait_prec P, int32_t *levels_lower, int32_t *levels_upper);
 /* z = P r; enqueues only. */
@@ -304,6 +313,15 @@ sait_status sait_prec_destroy(sait_prec P);
  * fills *info if info is not NULL. */
 sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const double *b, double *x,
                        int32_t restart, double tol, int32_t maxit, sait_info *info);
+
+/* Preconditioned conjugate gradients (Saad, Algorithm 9.1), the solver of the
+ * paper's experiments (Section 4).  The preconditioner is applied as given --
+ * the SAIT pair M_U M_L is not symmetric, as in the paper.  Stops when the
+ * recursive residual satisfies ||r|| <= tol ||b||; info->rel_resid is the true
+ * residual at exit, info->iters the iterations.  Same conventions as
+ * sait_gmres. */
+sait_status sait_pcg(sait_ctx ctx, sait_mat A, sait_prec P, const double *b, double *x, double tol, int32_t maxit,
+                     sait_info *info);
 
 /* The k smallest eigenpairs of symmetric positive definite A by LOBPCG
  * (Knyazev 2001; the paper's block eigensolver, Section 4.4) with the SAIT

@@ -56,7 +56,8 @@ class _Mat(C.Structure):
 class _Prec(C.Structure):
     _fields_ = [("kind", C.c_int), ("n", C.c_int64),
                 ("l_rp", C.c_void_p), ("l_ci", C.c_void_p), ("l_va", C.c_void_p),
-                ("u_rp", C.c_void_p), ("u_ci", C.c_void_p), ("u_va", C.c_void_p)]
+                ("u_rp", C.c_void_p), ("u_ci", C.c_void_p), ("u_va", C.c_void_p),
+                ("sweeps", C.c_int)]
 
 
 _lib = None
@@ -73,6 +74,7 @@ def _L():
         _lib.ora_sait.argtypes = [i64, i32p, i32p, dp, C.c_int, C.c_int, C.c_double, C.c_int,
                                   C.POINTER(_Mat)]
         _lib.ora_free.argtypes = [C.POINTER(_Mat)]
+        _lib.ora_jacobi.argtypes = [i64, i32p, i32p, dp, C.c_int, dp, dp]
         solver = [i64, i32p, i32p, dp, C.POINTER(_Prec), dp, dp]
         _lib.ora_gmres.argtypes = solver + [C.c_int, C.c_double, C.c_int,
                                             C.POINTER(C.c_int), C.POINTER(C.c_double)]
@@ -182,8 +184,12 @@ def apply(ML: CSR, MU: CSR, r: np.ndarray) -> np.ndarray:
 
 
 def _prec(kind: str, lo: CSR | None, up: CSR | None, n: int):
+    """kind: "none", "sait", "ilu" or "jacobiK" (K Jacobi sweeps per triangle)."""
     P = _Prec()
-    P.kind = {"none": 0, "sait": 1, "ilu": 2}[kind]
+    if kind.startswith("jacobi"):
+        P.kind, P.sweeps = 3, int(kind[6:])
+    else:
+        P.kind = {"none": 0, "sait": 1, "ilu": 2}[kind]
     P.n = n
     keep = []
     if kind != "none":
@@ -219,6 +225,17 @@ def bicgstab(A: CSR, b, prec: str = "none", lo: CSR | None = None, up: CSR | Non
              tol: float = 1e-8, maxit: int = 10000, x0=None):
     """Right-preconditioned BiCGSTAB.  Returns (x, iterations, true relres, status)."""
     return _solve(_L().ora_bicgstab, A, b, x0, prec, lo, up, C.c_double(tol), C.c_int(maxit))
+
+
+def jacobi(T: CSR, b, sweeps: int) -> np.ndarray:
+    """``sweeps`` Jacobi iterations for T x = b from x = 0 (equation Jacobi_iter)."""
+    rp, ci, va = _csr_args(T)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(T.n)
+    st = _L().ora_jacobi(T.n, _p(rp), _p(ci), _p(va), int(sweeps), _p(b), _p(x))
+    if st:
+        raise OracleError("jacobi", st)
+    return x
 
 
 def pcg(A: CSR, b, prec: str = "none", lo: CSR | None = None, up: CSR | None = None,

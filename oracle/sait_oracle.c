@@ -311,6 +311,9 @@ done:
 /*   kind 0: none (z = r)                                                    */
 /*   kind 1: SAIT pair, z = M_U (M_L r)        (Section 3.1)                 */
 /*   kind 2: exact ILU, z = U^-1 (L^-1 r)      (substitution; Section 3.1)   */
+/*   kind 3: Jacobi sweeps, `sweeps` iterations of equation Jacobi_iter on   */
+/*           L y = r and then on U z = y, each from a zero start             */
+/*           (Section 4, comparison with Jacobi iteration)                   */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     int kind;
@@ -319,7 +322,39 @@ typedef struct {
     const double *l_va;
     const int32_t *u_rp, *u_ci;
     const double *u_va;
+    int sweeps;
 } ora_prec;
+
+/* k sweeps of x^j = T~ x^{j-1} + D^-1 b from x^0 = 0 (Section 2, equation
+ * Jacobi_iter), T~ = I - D^-1 T, so (T~ x)_i = -sum_{j != i} (t_ij / t_ii) x_j.
+ * Works for any square T with a nonzero diagonal. */
+int ora_jacobi(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, int sweeps,
+               const double *b, double *x)
+{
+    if (n < 0 || sweeps < 0) return ORA_INVALID;
+    double *d = (double *)malloc((size_t)n * sizeof(double) + 8);
+    double *xo = (double *)malloc((size_t)n * sizeof(double) + 8);
+    if (!d || !xo) { free(d); free(xo); return ORA_OOM; }
+    int st = ORA_OK;
+    for (int64_t i = 0; i < n; i++) {
+        d[i] = 0.0;
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++)
+            if (ci[e] == i) d[i] = va[e];
+        if (d[i] == 0.0 || !isfinite(d[i])) st = ORA_ZERO_PIVOT;
+        x[i] = 0.0;
+    }
+    for (int k = 0; k < sweeps && st == ORA_OK; k++) {
+        memcpy(xo, x, (size_t)n * sizeof(double));
+        for (int64_t i = 0; i < n; i++) {
+            double s = 0.0;
+            for (int32_t e = rp[i]; e < rp[i + 1]; e++)
+                if (ci[e] != i) s += (-va[e] / d[i]) * xo[ci[e]];
+            x[i] = s + b[i] / d[i];
+        }
+    }
+    free(d); free(xo);
+    return st;
+}
 
 static int prec_apply(const ora_prec *P, const double *r, double *z, double *tmp)
 {
@@ -334,6 +369,11 @@ static int prec_apply(const ora_prec *P, const double *r, double *z, double *tmp
         int st = ora_trisolve(n, P->l_rp, P->l_ci, P->l_va, 1, r, tmp);
         if (st) return st;
         return ora_trisolve(n, P->u_rp, P->u_ci, P->u_va, 0, tmp, z);
+    }
+    if (P->kind == 3) {
+        int st = ora_jacobi(n, P->l_rp, P->l_ci, P->l_va, P->sweeps, r, tmp);
+        if (st) return st;
+        return ora_jacobi(n, P->u_rp, P->u_ci, P->u_va, P->sweeps, tmp, z);
     }
     return ORA_INVALID;
 }

@@ -27,7 +27,7 @@ __all__ = [
     "sait_prec_destroy", "sait_gmres", "sait_bicgstab", "sait_ctx_set_timing", "sait_ctx_stats",
     "sait_apply_static", "APPLY_STATIC_MAX_N", "sait_spmm", "sait_apply_multi", "sait_mat_transpose",
     "sait_outer_on_pattern", "sait_bicgstab_batched", "sait_bicgstab_multi", "BatchInfo", "Stats",
-    "TIMERS", "lib_path", "EXPORTS", "sait_lobpcg",
+    "TIMERS", "lib_path", "EXPORTS", "sait_lobpcg", "sait_pcg", "sait_prec_create_jacobi",
 ]
 
 DROP = {"none": 0, "abs": 1, "rowrel": 2, "pattern": 3}
@@ -42,7 +42,7 @@ EXPORTS = [
     "sait_prec_create_sait", "sait_prec_create_ilu", "sait_prec_levels", "sait_prec_apply",
     "sait_prec_destroy", "sait_gmres", "sait_bicgstab", "sait_ctx_set_timing", "sait_ctx_stats",
     "sait_apply_static", "sait_spmm", "sait_apply_multi", "sait_mat_transpose", "sait_outer_on_pattern",
-    "sait_bicgstab_batched", "sait_bicgstab_multi", "sait_lobpcg",
+    "sait_bicgstab_batched", "sait_bicgstab_multi", "sait_lobpcg", "sait_pcg", "sait_prec_create_jacobi",
 ]
 APPLY_STATIC_MAX_N = 2097152  # SAIT_APPLY_STATIC_MAX_N in include/sait.h
 TIMERS = ["apply", "spmv", "ortho", "build", "ilu", "trisolve"]
@@ -129,6 +129,8 @@ def _L():
             "sait_bicgstab_batched": [vp, vp, vp, i32, vp, vp, vp, d, i32, C.POINTER(BatchInfo), vp, vp],
             "sait_bicgstab_multi": [vp, vp, vp, i32, vp, vp, d, i32, C.POINTER(BatchInfo), vp, vp],
             "sait_lobpcg": [vp, vp, vp, i32, vp, vp, d, i32, C.POINTER(Info)],
+            "sait_pcg": [vp, vp, vp, vp, vp, d, i32, C.POINTER(Info)],
+            "sait_prec_create_jacobi": [vp, vp, vp, i32, C.POINTER(vp)],
         }
         for name, args in sigs.items():
             f = getattr(lib, name)
@@ -411,6 +413,13 @@ def sait_prec_create_ilu(ctx: Context, L: Mat, U: Mat) -> Prec:
     return Prec(ctx, h, (L, U))
 
 
+def sait_prec_create_jacobi(ctx: Context, L: Mat, U: Mat, sweeps: int) -> Prec:
+    h = C.c_void_p()
+    _check(ctx, _L().sait_prec_create_jacobi(ctx.h, L.h, U.h, int(sweeps), C.byref(h)),
+           "sait_prec_create_jacobi")
+    return Prec(ctx, h, [L, U])
+
+
 def sait_prec_levels(P: Prec):
     a, b = C.c_int32(), C.c_int32()
     _check(None, _L().sait_prec_levels(P.h, C.byref(a), C.byref(b)), "sait_prec_levels")
@@ -512,3 +521,16 @@ def sait_lobpcg(ctx: Context, A: Mat, P: Prec | None, X: torch.Tensor, tol: floa
     if check:
         _check(ctx, st, "sait_lobpcg")
     return lam, X, info, st
+
+
+def sait_pcg(ctx: Context, A: Mat, P: Prec | None, b: torch.Tensor, x: torch.Tensor | None = None,
+             tol: float = 1e-10, maxit: int = 10000, check: bool = True):
+    """Preconditioned CG (the paper's solver).  Returns (x, info, status)."""
+    _vec(b, A.n, "b")
+    x = torch.zeros_like(b) if x is None else _vec(x, A.n, "x")
+    info = Info()
+    st = _L().sait_pcg(ctx.h, A.h, P.h if P is not None else None, _ptr(b), _ptr(x), float(tol), int(maxit),
+                       C.byref(info))
+    if check:
+        _check(ctx, st, "sait_pcg")
+    return x, info, st

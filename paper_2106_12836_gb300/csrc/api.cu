@@ -433,6 +433,7 @@ sait_status prec_apply_impl(sait_ctx ctx, sait_prec P, const double *r, double *
         SAIT_CK(cudaGetLastError());
         return SAIT_OK;
     }
+    if (P->kind == 3) return jacobi_apply(ctx, P, r, z, active);
     return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "unknown preconditioner kind");
 }
 
@@ -450,6 +451,7 @@ extern "C" sait_status sait_prec_destroy(sait_prec P) {
     if (P->tmp) cudaFree(P->tmp);
     if (P->gin) cudaFree(P->gin);
     if (P->gout) cudaFree(P->gout);
+    if (P->dinv) cudaFree(P->dinv);
     delete P;
     return SAIT_OK;
 }

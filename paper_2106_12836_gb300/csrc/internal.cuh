@@ -88,7 +88,9 @@ struct LevelSchedule {
 };
 
 struct sait_prec_s {
-    int kind = 0;  // 1 SAIT pair, 2 exact ILU
+    int kind = 0;  // 1 SAIT pair, 2 exact ILU, 3 Jacobi sweeps
+    int sweeps = 0;             // kind 3: sweeps per triangle
+    double *dinv = nullptr;     // kind 3: 1 / diag(L) then 1 / diag(U), 2n
     sait_mat lo = nullptr, up = nullptr;
     LevelSchedule lev_lo, lev_up;
     double *tmp = nullptr;      // n-vector scratch
@@ -102,6 +104,7 @@ struct sait_prec_s {
 
 // ---- error helpers ---------------------------------------------------------
 sait_status ctx_fail(sait_ctx ctx, sait_status st, const std::string &msg);
+sait_status jacobi_apply(sait_ctx ctx, sait_prec P, const double *r, double *z, const int *active);
 sait_status ctx_cuda(sait_ctx ctx, cudaError_t e, const char *what, const char *file, int line);
 
 #define SAIT_CK(call)                                                         \

@@ -401,6 +401,65 @@ __global__ void k_bicg_check_r(Scal *sc, int remaining) {  // after (r, r) in r0
     sc->r3 = fmin(sc->r3, rn);
 }
 
+
+// ---- PCG kernels (Saad, Algorithm 9.1) ----------------------------------------------
+__global__ void k_pcg_alpha(Scal *sc) {  // after (p, q) in r0
+    if (sc->active == 0) return;
+    const double pq = sc->r0;
+    if (pq == 0.0 || !isfinite(pq)) {
+        sc->state = isfinite(pq) ? 2 : 3;
+        sc->active = 0;
+        return;
+    }
+    sc->alpha = sc->rho / pq;
+}
+
+// x += alpha p; r -= alpha q; partial ||r||^2
+__global__ void __launch_bounds__(kThreads)
+k_pcg_xr(int64_t n, double *x, double *r, const double *__restrict__ p, const double *__restrict__ q,
+         const Scal *sc, double *partial) {
+    if (sc->active == 0) return;
+    const double alpha = sc->alpha;
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        x[i] += alpha * p[i];
+        const double ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        s = fma(ri, ri, s);
+    }
+    s = block_sum(s);
+    if (threadIdx.x == 0) partial[blockIdx.x * 3] = s;
+}
+
+__global__ void k_pcg_check(Scal *sc, int remaining) {  // after ||r||^2 in r0
+    if (sc->active == 0) return;
+    sc->jdone += 1;
+    const double rn = sqrt(sc->r0);
+    if (!isfinite(rn)) { sc->state = 3; sc->active = 0; return; }
+    if (rn <= sc->tolb) { sc->state = 1; sc->active = 0; return; }
+    if (sc->jdone >= remaining) sc->active = 0;
+}
+
+__global__ void k_pcg_beta(Scal *sc) {  // after (r, z) in r0
+    if (sc->active == 0) return;
+    const double rho = sc->r0;
+    sc->beta_b = rho / sc->rho;
+    sc->rho = rho;
+}
+
+__global__ void k_pcg_p(int64_t n, const double *__restrict__ z, double *p, const Scal *sc) {
+    if (sc->active == 0) return;
+    const double beta = sc->beta_b;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+        p[i] = z[i] + beta * p[i];
+}
+
+__global__ void k_pcg_start(Scal *sc) {  // after (r, z) in r0
+    sc->rho = sc->r0;
+    sc->active = 1;
+    sc->state = 0;
+}
+
 // ---- host helpers ---------------------------------------------------------------
 struct Work {
     int nb = 1;
@@ -714,6 +773,97 @@ extern "C" sait_status sait_bicgstab(sait_ctx ctx, sait_mat A, sait_prec P, cons
         char buf[160];
         snprintf(buf, sizeof(buf), "sait_bicgstab: %s after %d iterations, relres %.3e",
                  sait_status_string(result), iters, inf.rel_resid);
+        return ctx_fail(ctx, result, buf);
+    }
+    return SAIT_OK;
+}
+
+extern "C" sait_status sait_pcg(sait_ctx ctx, sait_mat A, sait_prec P, const double *b, double *x, double tol,
+                                int32_t maxit, sait_info *info) {
+    if (!ctx) return SAIT_ERR_INVALID_ARG;
+    SAIT_TRY(check_solver_args(ctx, A, P, b, x, tol, maxit, "sait_pcg"));
+    const int64_t n = A->n;
+    cudaStream_t s = ctx->stream;
+    sait_info inf{0, 0, 0, 0, 0.0};
+    if (info) *info = inf;
+    if (n == 0) return SAIT_OK;
+    Work W;
+    W.nb = (int)std::min<int64_t>(cdiv(n, kThreads), 2LL * ctx->num_sms);
+    DTemp<double> r, z, p, q, part;
+    DTemp<Scal> scd;
+    for (DTemp<double> *d : {&r, &z, &p, &q}) SAIT_CK(d->alloc(n, s));
+    SAIT_CK(part.alloc((size_t)W.nb * 3, s));
+    SAIT_CK(scd.alloc(1, s));
+    SAIT_CK(cudaMemsetAsync(scd.p, 0, sizeof(Scal), s));
+    W.partial = part.p;
+    Scal *sc = scd.p;
+    const int *act = &sc->active;
+    double *r0 = &sc->r0;
+    const unsigned egrid = (unsigned)std::min<int64_t>(cdiv(n, kThreads), 8LL * ctx->num_sms);
+    SAIT_CK(dots(ctx, W, n, 1, b, b, nullptr, nullptr, nullptr, nullptr, r0, nullptr));
+    Scal hs;
+    SAIT_TRY(read_scal(ctx, sc, &hs));
+    const double bnorm = sqrt(hs.r0);
+    if (!std::isfinite(bnorm)) return ctx_fail(ctx, SAIT_ERR_NONFINITE, "sait_pcg: non-finite b");
+    if (bnorm == 0.0) {
+        SAIT_CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+        SAIT_CK(cudaStreamSynchronize(s));
+        return SAIT_OK;
+    }
+    const double tb = tol * bnorm;
+    SAIT_CK(cudaMemcpyAsync(&sc->tolb, &tb, sizeof(double), cudaMemcpyHostToDevice, s));
+    SAIT_CK(residual(ctx, A, x, b, r.p));
+    SAIT_CK(dots(ctx, W, n, 1, r.p, r.p, nullptr, nullptr, nullptr, nullptr, r0, nullptr));
+    SAIT_TRY(read_scal(ctx, sc, &hs));
+    inf.rel_resid = sqrt(hs.r0) / bnorm;
+    sait_status result = SAIT_ERR_NOT_CONVERGED;
+    if (inf.rel_resid <= tol) {
+        result = SAIT_OK;
+    } else {
+        SAIT_TRY(precondition(ctx, P, r.p, z.p, n, nullptr));
+        SAIT_CK(cudaMemcpyAsync(p.p, z.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        SAIT_CK(dots(ctx, W, n, 1, r.p, z.p, nullptr, nullptr, nullptr, nullptr, r0, nullptr));
+        launch_k(k_pcg_start, 1, 1, 0, s, sc);
+        const int poll = (P && P->kind == 2) ? 1 : kPoll;
+        for (int it = 0; it < maxit; it++) {
+            {
+                ScopedTimer tm(ctx, SAIT_TIMER_SPMV);
+                SAIT_CK(launch_spmv(A, SAIT_F64, p.p, false, q.p, false, act, s, group_counter(ctx, SAIT_TIMER_SPMV)));
+            }
+            SAIT_CK(dots(ctx, W, n, 1, p.p, q.p, nullptr, nullptr, nullptr, nullptr, r0, act));
+            launch_k(k_pcg_alpha, 1, 1, 0, s, sc);
+            launch_k(k_pcg_xr, (unsigned)W.nb, kThreads, 0, s, n, x, r.p, (const double *)p.p, (const double *)q.p,
+                     (const Scal *)sc, W.partial);
+            launch_k(k_reduce, 1, kThreads, 0, s, (const double *)W.partial, W.nb, 3, r0, act);
+            launch_k(k_pcg_check, 1, 1, 0, s, sc, (int)maxit);
+            SAIT_TRY(precondition(ctx, P, r.p, z.p, n, act));
+            SAIT_CK(dots(ctx, W, n, 1, r.p, z.p, nullptr, nullptr, nullptr, nullptr, r0, act));
+            launch_k(k_pcg_beta, 1, 1, 0, s, sc);
+            launch_k(k_pcg_p, egrid, kThreads, 0, s, n, (const double *)z.p, p.p, (const Scal *)sc);
+            SAIT_CK(cudaGetLastError());
+            if ((it + 1) % poll == 0 || it + 1 == maxit) {
+                SAIT_TRY(read_scal(ctx, sc, &hs));
+                if (!hs.active) break;
+            }
+        }
+        SAIT_TRY(read_scal(ctx, sc, &hs));
+        inf.iters = hs.jdone;
+        if (hs.state == 1) result = SAIT_OK;
+        else if (hs.state == 2) result = SAIT_ERR_BREAKDOWN;
+        else if (hs.state == 3) result = SAIT_ERR_NONFINITE;
+        // true residual at exit
+        SAIT_CK(residual(ctx, A, x, b, r.p));
+        SAIT_CK(dots(ctx, W, n, 1, r.p, r.p, nullptr, nullptr, nullptr, nullptr, r0, nullptr));
+        SAIT_TRY(read_scal(ctx, sc, &hs));
+        inf.rel_resid = sqrt(hs.r0) / bnorm;
+    }
+    inf.cycles = 1;
+    if (info) *info = inf;
+    SAIT_CK(cudaStreamSynchronize(s));
+    if (result != SAIT_OK) {
+        char buf[160];
+        snprintf(buf, sizeof(buf), "sait_pcg: %s after %d iterations, relres %.3e", sait_status_string(result),
+                 inf.iters, inf.rel_resid);
         return ctx_fail(ctx, result, buf);
     }
     return SAIT_OK;

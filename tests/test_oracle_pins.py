@@ -83,6 +83,58 @@ def test_series_equals_jacobi_sweeps(oracle_lib, lower, k):
 
 
 # --------------------------------------------------------------------------
+# Jacobi sweeps (equation Jacobi_iter; Section 4, comparison with Jacobi).
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("lower", [True, False])
+def test_jacobi_sweeps_exact_after_n(oracle_lib, lower):
+    """T~ of a triangular T is nilpotent, so n sweeps give T^-1 b exactly."""
+    n = 40
+    T = synth.random_triangular(n, lower, 5, max_row=8)
+    b = synth.uniform(7, n)
+    x = oracle_lib.jacobi(T, b, n)
+    ref = sla.solve_triangular(T.to_dense(), b, lower=lower)
+    assert np.abs(x - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 5])
+def test_jacobi_sweeps_equal_series(oracle_lib, k):
+    """k sweeps from zero apply M_k = sum_{j<k} T~^j D^-1 (Section 2): the pinned SAIT with no dropping."""
+    T = synth.random_triangular(150, True, 21 + k, max_row=12)
+    b = synth.uniform(9, T.n)
+    x = oracle_lib.jacobi(T, b, k)
+    if k == 0:
+        assert not x.any()
+        return
+    y = oracle_lib.sait(T, k, "none").to_dense() @ b
+    assert np.abs(x - y).max() <= 1e-13 * max(1.0, np.abs(y).max())
+
+
+def test_jacobi_sweeps_general_matrix(oracle_lib):
+    """On a strictly diagonally dominant non-triangular matrix the sweeps converge to A^-1 b."""
+    A = synth.poisson2d(6)
+    rows = np.repeat(np.arange(A.n), np.diff(A.rp))
+    va = np.where(A.ci == rows, 2.0 * A.va, A.va)      # diagonal 8 against off-diagonal sum 4
+    B = synth.CSR(A.n, A.rp, A.ci, va)
+    b = synth.uniform(13, A.n)
+    x = oracle_lib.jacobi(B, b, 80)
+    ref = np.linalg.solve(B.to_dense(), b)
+    assert np.abs(x - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_jacobi_prec_pcg_between_diagonal_and_exact(oracle_lib):
+    """More sweeps approach the exact ILU solves: iterations fall from the diagonal case towards the exact one."""
+    A = synth.laplace3d(14)
+    L, U = oracle_lib.ilu0(A)
+    b = synth.uniform(17, A.n)
+    its = []
+    for kind in ("jacobi1", "jacobi3", "jacobi40", "ilu"):
+        _, it, rr, st = oracle_lib.pcg(A, b, kind, L, U, tol=1e-10)
+        assert st == 0 and rr <= 1e-10
+        its.append(it)
+    assert its[0] > its[1] > its[3] and its[2] == its[3]
+
+
+# --------------------------------------------------------------------------
 # Algorithms 2-3 with brute force: a dense Horner loop with a mask on tiny
 # matrices.  Entries within 1e-12 of a threshold are not graded.
 # --------------------------------------------------------------------------
@@ -182,6 +234,19 @@ def test_paper_pcg_iteration_counts(oracle_lib, laplace100, golden_runtime):
     assert st2 == 0 and rr2 <= tol
     assert abs(it2 - row["pcg_iters"]) <= 0.1 * row["pcg_iters"]
     assert it2 > it      # SAIT never beats the exact triangular solves (Section 4.1)
+
+
+@pytest.mark.slow
+def test_paper_jacobi_pcg_iteration_counts(oracle_lib, laplace100):
+    """Table runtime_Jacobi, level-0 column, a few rows; right-hand side b ~ U[0,1) as above."""
+    with open(os.path.join(GOLDEN, "paper_runtime_jacobi.json")) as f:
+        g = json.load(f)
+    A, L, U = laplace100
+    b = synth.uniform(synth.SEED_BASE, A.n, 0.0, 1.0)
+    for k in (1, 3, 10):
+        _, it, rr, st = oracle_lib.pcg(A, b, f"jacobi{k}", L, U, tol=g["pcg_tol"])
+        assert st == 0 and rr <= g["pcg_tol"]
+        assert abs(it - g["level0_pcg_iters"][str(k)]) <= 0.05 * g["level0_pcg_iters"][str(k)], (k, it)
 
 
 def test_pattern_nnz_independent_of_m(oracle_lib):
