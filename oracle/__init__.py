@@ -75,6 +75,7 @@ def _L():
                                   C.POINTER(_Mat)]
         _lib.ora_free.argtypes = [C.POINTER(_Mat)]
         _lib.ora_jacobi.argtypes = [i64, i32p, i32p, dp, C.c_int, dp, dp]
+        _lib.ora_ilut.argtypes = [i64, i32p, i32p, dp, C.c_double, C.c_int, C.POINTER(_Mat)]
         solver = [i64, i32p, i32p, dp, C.POINTER(_Prec), dp, dp]
         _lib.ora_gmres.argtypes = solver + [C.c_int, C.c_double, C.c_int,
                                             C.POINTER(C.c_int), C.POINTER(C.c_double)]
@@ -128,6 +129,30 @@ def ilu0(A: CSR) -> tuple[CSR, CSR]:
     if st:
         raise OracleError("ilu0", st)
     return split_lu(CSR(A.n, rp, ci, lu))
+
+
+def _take(out) -> CSR:
+    try:
+        n, nnz = out.n, out.nnz
+        orp = np.ctypeslib.as_array(out.rp, shape=(n + 1,)).copy()
+        if nnz:
+            oci = np.ctypeslib.as_array(out.ci, shape=(nnz,)).copy()
+            ova = np.ctypeslib.as_array(out.va, shape=(nnz,)).copy()
+        else:
+            oci, ova = np.zeros(0, np.int32), np.zeros(0)
+    finally:
+        _L().ora_free(C.byref(out))
+    return CSR(int(n), orp, oci, ova)
+
+
+def ilut(A: CSR, tau: float, lfil: int) -> tuple[CSR, CSR]:
+    """ILUT(tau, lfil) factors (Saad, Algorithm 10.6), split as ilu0's."""
+    rp, ci, va = _csr_args(A)
+    out = _Mat()
+    st = _L().ora_ilut(A.n, _p(rp), _p(ci), _p(va), float(tau), int(lfil), C.byref(out))
+    if st:
+        raise OracleError("ilut", st)
+    return split_lu(_take(out))
 
 
 def split_lu(LU: CSR) -> tuple[CSR, CSR]:

@@ -170,6 +170,110 @@ done:
 }
 
 /* ------------------------------------------------------------------------ */
+/* ILUT(tau, lfil) (Saad, Iterative Methods for Sparse Linear Systems, 2nd   */
+/* ed., Algorithm 10.6), the threshold ILU whose factors the paper's         */
+/* experiments also feed to SAIT (level-1 and threshold factors, Section 4). */
+/* Row i:                                                                   */
+/*   w := a_i*,  tau_i := tau * ||a_i*||_2  (sum of squares in column order) */
+/*   for k < i with w_k != 0, in increasing k (fill included):              */
+/*       w_k := w_k / u_kk;  drop w_k if |w_k| < tau_i  (first rule)        */
+/*       if w_k != 0:  w_j := fma(-w_k, u_kj, w_j)  for u_kj != 0, j > k    */
+/*   second rule: drop |w_j| < tau_i, then keep the lfil largest |w_j| of   */
+/*   the L part (j < i) and of the U part (j > i); the diagonal is always   */
+/*   kept.  Ties in |w_j| keep the smaller column.                          */
+/* Output: combined CSR, strict lower part of L (unit diagonal implied) and  */
+/* U with its diagonal, columns ascending.  A zero or non-finite pivot      */
+/* u_ii returns ORA_ZERO_PIVOT.                                             */
+/* ------------------------------------------------------------------------ */
+static int keep_largest(const int32_t *cols, const double *w, int cnt, int lfil, int32_t *out)
+{
+    /* out gets the kept columns (rank < lfil), ascending; returns how many */
+    int m = 0;
+    for (int a = 0; a < cnt; a++) {
+        double va = fabs(w[cols[a]]);
+        int rank = 0;
+        for (int b = 0; b < cnt; b++) {
+            double vb = fabs(w[cols[b]]);
+            if (vb > va || (vb == va && cols[b] < cols[a])) rank++;
+        }
+        if (rank < lfil) out[m++] = cols[a];
+    }
+    qsort(out, (size_t)m, sizeof(int32_t), cmp_i32);
+    return m;
+}
+
+int ora_ilut(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, double tau, int lfil,
+             ora_mat *out)
+{
+    if (n < 0 || lfil < 0 || !(tau >= 0.0)) return ORA_INVALID;
+    ora_mat LU = {0};
+    double *w = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    int32_t *inw = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    int32_t *list = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    int32_t *cand = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    int32_t *kept = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    int64_t *udiag = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int st = ORA_OK;
+    if (!w || !inw || !list || !cand || !kept || !udiag || mat_init(&LU, n, rp[n] * 2 + 16)) { st = ORA_OOM; goto done; }
+    for (int64_t i = 0; i < n; i++) inw[i] = 0;
+    for (int64_t i = 0; i < n; i++) {
+        int nw = 0;
+        double ss = 0.0;
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
+            if (ci[e] < 0 || ci[e] >= n || (e > rp[i] && ci[e] <= ci[e - 1])) { st = ORA_INVALID; goto done; }
+            ss += va[e] * va[e];
+            w[ci[e]] = va[e];
+            inw[ci[e]] = 1;
+            list[nw++] = ci[e];
+        }
+        if (!inw[i]) { inw[i] = 1; w[i] = 0.0; list[nw++] = (int32_t)i; }
+        const double tau_i = tau * sqrt(ss);
+        int64_t k = -1;
+        for (;;) {
+            int64_t next = n;
+            for (int t = 0; t < nw; t++)
+                if (list[t] > k && list[t] < i && list[t] < next) next = list[t];
+            if (next == n) break;
+            k = next;
+            if (w[k] == 0.0) continue;
+            w[k] = w[k] / LU.va[udiag[k]];
+            if (fabs(w[k]) < tau_i) { w[k] = 0.0; continue; }
+            for (int64_t f = udiag[k] + 1; f < LU.rp[k + 1]; f++) {
+                int32_t j = LU.ci[f];
+                if (!inw[j]) { inw[j] = 1; w[j] = 0.0; list[nw++] = j; }
+                w[j] = fma(-w[k], LU.va[f], w[j]);
+            }
+        }
+        const double piv = w[i];
+        if (piv == 0.0 || !isfinite(piv)) { st = ORA_ZERO_PIVOT; goto done; }
+        /* L part */
+        int nc = 0;
+        for (int t = 0; t < nw; t++)
+            if (list[t] < i && w[list[t]] != 0.0 && fabs(w[list[t]]) >= tau_i) cand[nc++] = list[t];
+        int nk = keep_largest(cand, w, nc, lfil, kept);
+        for (int t = 0; t < nk; t++)
+            if (mat_push(&LU, kept[t], w[kept[t]])) { st = ORA_OOM; goto done; }
+        udiag[i] = LU.nnz;
+        if (mat_push(&LU, (int32_t)i, piv)) { st = ORA_OOM; goto done; }
+        /* U part */
+        nc = 0;
+        for (int t = 0; t < nw; t++)
+            if (list[t] > i && w[list[t]] != 0.0 && fabs(w[list[t]]) >= tau_i) cand[nc++] = list[t];
+        nk = keep_largest(cand, w, nc, lfil, kept);
+        for (int t = 0; t < nk; t++)
+            if (mat_push(&LU, kept[t], w[kept[t]])) { st = ORA_OOM; goto done; }
+        LU.rp[i + 1] = (int32_t)LU.nnz;
+        for (int t = 0; t < nw; t++) { inw[list[t]] = 0; w[list[t]] = 0.0; }
+    }
+    *out = LU;
+    LU.rp = NULL; LU.ci = NULL; LU.va = NULL;
+done:
+    ora_free(&LU);
+    free(w); free(inw); free(list); free(cand); free(kept); free(udiag);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
 /* SAIT (Algorithms 1-3).                                                   */
 /*                                                                          */
 /* With D = diag(T) and T~ = I - D^-1 T (strictly triangular, Section 2),    */

@@ -83,6 +83,101 @@ def test_series_equals_jacobi_sweeps(oracle_lib, lower, k):
 
 
 # --------------------------------------------------------------------------
+# ILUT(tau, lfil) (Saad, Algorithm 10.6).
+# --------------------------------------------------------------------------
+def _dense(L, U):
+    return L.to_dense(), U.to_dense()
+
+
+@pytest.mark.parametrize("make", [lambda: synth.convdiff3d(4), lambda: synth.varcoef3d(4, 1.0, 77),
+                                  lambda: synth.aniso2d(7, 0.01)])
+def test_ilut_without_dropping_is_exact_lu(oracle_lib, make):
+    """tau = 0 and lfil >= n keep every fill entry: L U = A with L unit lower, U upper (the unique LU)."""
+    A = make()
+    L, U = oracle_lib.ilut(A, 0.0, A.n)
+    Ld, Ud = _dense(L, U)
+    Ad = A.to_dense()
+    assert np.array_equal(np.diag(Ld), np.ones(A.n)) and not np.triu(Ld, 1).any() and not np.tril(Ud, -1).any()
+    assert np.abs(Ld @ Ud - Ad).max() <= 1e-13 * np.abs(Ad).max()
+    # the same factors by dense Doolittle elimination in LAPACK order: solve with them
+    b = synth.uniform(3, A.n)
+    x = sla.solve_triangular(Ud, sla.solve_triangular(Ld, b, lower=True), lower=False)
+    assert np.abs(x - np.linalg.solve(Ad, b)).max() <= 1e-11 * np.abs(x).max()
+
+
+def test_ilut_tridiagonal_equals_ilu0(oracle_lib):
+    """A tridiagonal LU has no fill, so ILUT(0, lfil >= 1) and ILU(0) run the same fma chain: bit-equal."""
+    A = synth.from_dense(np.diag(np.full(50, 4.0)) + np.diag(synth.uniform(5, 49, -1.5, -0.5), -1) +
+                         np.diag(synth.uniform(6, 49, -1.5, -0.5), 1))
+    L, U = oracle_lib.ilut(A, 0.0, 1)
+    L0, U0 = oracle_lib.ilu0(A)
+    for X, Y in ((L, L0), (U, U0)):
+        assert np.array_equal(X.rp, Y.rp) and np.array_equal(X.ci, Y.ci) and np.array_equal(X.va, Y.va)
+
+
+def test_ilut_closed_forms(oracle_lib):
+    """A huge tau drops every multiplier (first rule), lfil = 0 drops every off-diagonal (second rule):
+    both leave L = I and U = diag(A), since no update ever reaches the diagonal."""
+    A = synth.convdiff3d(6)
+    rows = np.repeat(np.arange(A.n), np.diff(A.rp))
+    dA = A.va[A.ci == rows]
+    for tau, lfil in ((1e30, 10), (0.0, 0)):
+        L, U = oracle_lib.ilut(A, tau, lfil)
+        assert L.nnz == A.n and U.nnz == A.n
+        assert np.array_equal(L.va, np.ones(A.n)) and np.array_equal(U.va, dA)
+
+
+@pytest.mark.parametrize("tau,lfil", [(1e-4, 10), (1e-2, 3), (0.0, 2)])
+def test_ilut_drop_invariants(oracle_lib, tau, lfil):
+    A = synth.varcoef3d(8, 1.0, 123)
+    L, U = oracle_lib.ilut(A, tau, lfil)
+    norms = np.sqrt(np.add.reduceat(A.va ** 2, A.rp[:-1]))
+    for T, lower in ((L, True), (U, False)):
+        rows = np.repeat(np.arange(T.n), np.diff(T.rp))
+        off = T.ci != rows
+        assert np.all(np.diff(T.rp) - 1 <= lfil)
+        assert np.all(np.abs(T.va[off]) >= tau * norms[rows[off]])
+        assert np.all(T.va[off] != 0.0)
+        assert np.all(T.ci[off] < rows[off]) if lower else np.all(T.ci[off] > rows[off])
+        assert np.count_nonzero(~off) == T.n
+    # (L U)_ij = a_ij wherever (i, j) is kept in U and no entry was dropped on that row (tau = 0, lfil large)
+    L2, U2 = oracle_lib.ilut(A, 0.0, A.n)
+    assert np.abs(L2.to_dense() @ U2.to_dense() - A.to_dense()).max() <= 1e-12 * np.abs(A.va).max()
+
+
+def test_ilut_error_decreases_with_tau(oracle_lib):
+    """Less dropping gives a better factorization: ||A - L U||_F falls as tau falls (lfil large)."""
+    A = synth.varcoef3d(6, 1.0, 321)
+    Ad = A.to_dense()
+    errs = []
+    for tau in (1e-1, 1e-2, 1e-3, 1e-4, 0.0):
+        L, U = oracle_lib.ilut(A, tau, A.n)
+        errs.append(np.linalg.norm(Ad - L.to_dense() @ U.to_dense()))
+    assert all(a > b for a, b in zip(errs, errs[1:-1])) and errs[-1] <= 1e-12 * np.linalg.norm(Ad)
+
+
+def test_ilut_keeps_largest(oracle_lib):
+    """Second rule on a row with one elimination step: the lfil kept U entries are the largest of w."""
+    # row 0 has three off-diagonals (all kept); row 1 = a_1 - (a_10 / a_00) a_0 has five candidates
+    n = 8
+    Ad = np.eye(n) * 10.0
+    Ad[0, [2, 3, 5]] = [-3.0, 2.0, 4.0]
+    Ad[1, [0, 3, 6, 7]] = [2.0, 0.5, 0.3, -0.7]
+    A = synth.from_dense(Ad)
+    L, U = oracle_lib.ilut(A, 0.0, 3)
+    w = Ad[1].copy()
+    l10 = w[0] / Ad[0, 0]
+    w[1:] = w[1:] - l10 * Ad[0, 1:]          # 0.6, 0.1, -0.8, 0.3, -0.7 at columns 2, 3, 5, 6, 7
+    off = np.arange(2, n)
+    top = off[np.argsort(-np.abs(w[off]), kind="stable")[:3]]
+    Ud = U.to_dense()
+    assert set(top) == {2, 5, 7}
+    assert set(np.nonzero(Ud[1, 2:])[0] + 2) == set(top)
+    assert np.abs(Ud[1, top] - w[top]).max() <= 1e-15
+    assert L.to_dense()[1, 0] == l10
+
+
+# --------------------------------------------------------------------------
 # Jacobi sweeps (equation Jacobi_iter; Section 4, comparison with Jacobi).
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("lower", [True, False])
