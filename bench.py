@@ -223,7 +223,7 @@ def batched_workloads(sg, ctx, torch, device, stream):
     return out
 
 
-def eigen_workload(sg, ctx, torch, device, stream, factors="ilu0"):
+def eigen_workload(sg, ctx, torch, device, stream, factors="ilut"):
     """16 smallest eigenpairs of 96^3 log-normal diffusion by SAIT-preconditioned LOBPCG."""
     A = synth.varcoef3d(96, 1.0, synth.SEED_BASE + 3)
     d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in

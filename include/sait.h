@@ -172,6 +172,22 @@ sait_status sait_mat_set_store(sait_ctx ctx, sait_mat M, sait_dtype store);
  * zero or non-finite.  Synchronizes. */
 sait_status sait_ilu0(sait_ctx ctx, const sait_csr *A, sait_mat *L, sait_mat *U);
 
+/* ILUT(tau, lfil) factors of A (Saad, Iterative Methods for Sparse Linear
+ * Systems, Algorithm 10.6); threshold ILU factors are among the triangular
+ * inputs the paper gives SAIT (Section 4).  Row i starts from a_i*, eliminates
+ * its columns k < i in increasing order (fill included) with w_k /= u_kk,
+ * drops w_k when |w_k| < tau ||a_i*||_2, then keeps the lfil largest entries
+ * of the L part and of the U part above the same threshold; the pivot is
+ * always kept.  Output as sait_ilu0: *L unit lower with the diagonal stored,
+ * *U upper with the pivots, both owned by the caller.  The factors are
+ * bit-identical to a row-by-row evaluation of the algorithm.
+ * Requirements: tau >= 0, 0 <= lfil <= 32 (else SAIT_ERR_INVALID_ARG /
+ * SAIT_ERR_UNSUPPORTED); every working row holds at most 256 entries, else
+ * SAIT_ERR_UNSUPPORTED.  A zero or non-finite pivot gives
+ * SAIT_ERR_ZERO_PIVOT.  Rows wait on earlier rows with bounded waits; a wait
+ * that runs out gives SAIT_ERR_TIMEOUT.  Synchronizes. */
+sait_status sait_ilut(sait_ctx ctx, const sait_csr *A, double tau, int32_t lfil, sait_mat *L, sait_mat *U);
+
 /* ---- SAIT build (Algorithms 1-3) ---------------------------------------- */
 
 /* Build M ~ T^-1 with m_terms series terms (m_terms >= 1; the loop of

@@ -27,7 +27,7 @@ __all__ = [
     "sait_prec_destroy", "sait_gmres", "sait_bicgstab", "sait_ctx_set_timing", "sait_ctx_stats",
     "sait_apply_static", "APPLY_STATIC_MAX_N", "sait_spmm", "sait_apply_multi", "sait_mat_transpose",
     "sait_outer_on_pattern", "sait_bicgstab_batched", "sait_bicgstab_multi", "BatchInfo", "Stats",
-    "TIMERS", "lib_path", "EXPORTS", "sait_lobpcg", "sait_pcg", "sait_prec_create_jacobi",
+    "TIMERS", "lib_path", "EXPORTS", "sait_lobpcg", "sait_pcg", "sait_prec_create_jacobi", "sait_ilut",
 ]
 
 DROP = {"none": 0, "abs": 1, "rowrel": 2, "pattern": 3}
@@ -42,7 +42,7 @@ EXPORTS = [
     "sait_prec_create_sait", "sait_prec_create_ilu", "sait_prec_levels", "sait_prec_apply",
     "sait_prec_destroy", "sait_gmres", "sait_bicgstab", "sait_ctx_set_timing", "sait_ctx_stats",
     "sait_apply_static", "sait_spmm", "sait_apply_multi", "sait_mat_transpose", "sait_outer_on_pattern",
-    "sait_bicgstab_batched", "sait_bicgstab_multi", "sait_lobpcg", "sait_pcg", "sait_prec_create_jacobi",
+    "sait_bicgstab_batched", "sait_bicgstab_multi", "sait_lobpcg", "sait_pcg", "sait_prec_create_jacobi", "sait_ilut",
 ]
 APPLY_STATIC_MAX_N = 2097152  # SAIT_APPLY_STATIC_MAX_N in include/sait.h
 TIMERS = ["apply", "spmv", "ortho", "build", "ilu", "trisolve"]
@@ -131,6 +131,7 @@ def _L():
             "sait_lobpcg": [vp, vp, vp, i32, vp, vp, d, i32, C.POINTER(Info)],
             "sait_pcg": [vp, vp, vp, vp, vp, d, i32, C.POINTER(Info)],
             "sait_prec_create_jacobi": [vp, vp, vp, i32, C.POINTER(vp)],
+            "sait_ilut": [vp, C.POINTER(_Csr), d, i32, C.POINTER(vp), C.POINTER(vp)],
         }
         for name, args in sigs.items():
             f = getattr(lib, name)
@@ -317,6 +318,14 @@ def sait_ilu0(ctx: Context, n: int, rp, ci, va):
     A = _csr(n, rp, ci, va)
     hl, hu = C.c_void_p(), C.c_void_p()
     _check(ctx, _L().sait_ilu0(ctx.h, C.byref(A), C.byref(hl), C.byref(hu)), "sait_ilu0")
+    return Mat(ctx, hl), Mat(ctx, hu)
+
+
+def sait_ilut(ctx: Context, n: int, rp, ci, va, tau: float, lfil: int):
+    """ILUT(tau, lfil) factors (Saad, Algorithm 10.6): (L, U) as sait_ilu0."""
+    A = _csr(n, rp, ci, va)
+    hl, hu = C.c_void_p(), C.c_void_p()
+    _check(ctx, _L().sait_ilut(ctx.h, C.byref(A), float(tau), int(lfil), C.byref(hl), C.byref(hu)), "sait_ilut")
     return Mat(ctx, hl), Mat(ctx, hu)
 
 
