@@ -395,6 +395,14 @@ def run_reference(a):
     }), flush=True)
 
 
+def max_over_ranks(dist, value: float, device) -> float:
+    """The slowest replica's time: every rank solves its own system (weak scaling)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t)
+
+
 # ---- our arm -----------------------------------------------------------------------
 def run_ours(a):
     import torch
@@ -447,9 +455,7 @@ def run_ours(a):
     sg.sait_ctx_set_timing(ctx, False)
     ms_step = statistics.mean(times)
     if dist:
-        t = torch.tensor([ms_step], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t)
+        ms_step = max_over_ranks(dist, ms_step, device)
         dist.barrier()
     torch.cuda.synchronize()
 
