@@ -324,9 +324,13 @@ def ortho_bytes(n, iters, restart):
     while left > 0:
         steps = min(left, restart)
         for j in range(steps):
-            # two passes: read j+1 basis vectors + w (dots), read j+1 vectors + w, write w (update);
-            # then ||w|| (read w) and the scaling (read w, write v)
-            total += 2 * ((j + 1) * 8 * n + 8 * n + (j + 1) * 8 * n + 16 * n) + 8 * n + 16 * n
+            # mixed-precision CGS2 over the basis kept as FP32 pairs (hi, lo), j + 1 vectors:
+            #   pass-1 dots    read hi (4 B) and w (FP64)
+            #   pass-1 update  read hi + lo (8 B), read and write w, write fl32(w)
+            #   pass-2 dots    read hi (4 B) and fl32(w)
+            #   pass-2 update  read hi (4 B), read and write w (||w||^2 fused)
+            #   scaling        read w, write v (FP64), hi and lo
+            total += 20 * (j + 1) * n + (8 + 8 + 8 + 4 + 4 + 8 + 8 + 8 + 8 + 4 + 4) * n
         left -= steps
     return total
 
@@ -485,14 +489,14 @@ def run_ours(a):
     sb = spmv_a_bytes(P.A)
     spmv_ms = stats["spmv"]["ms"] / max(stats["spmv"]["calls"], 1)
     rl = {
-        "apply": {"kernel": "k_spmv_csr x2 (M_L then M_U), one SAIT apply", "bound": "hbm",
+        "apply": {"kernel": "k_spmv_sell x2 (M_L then M_U, SELL-32), one SAIT apply", "bound": "hbm",
                   "achieved": ab / apply_ms / 1e6, "bytes": ab, "ms": apply_ms,
                   "calls": stats["apply"]["calls"]},
-        "ortho": {"kernel": "GMRES CGS2 step (k_mdot, k_reduce, k_gemv x2, norm, Givens, scale)",
+        "ortho": {"kernel": "GMRES CGS2 step (k_cgs_dot x2, k_cgs_update_df, k_cgs_update32, k_reduce x3, k_hadd x2, k_givens, k_scale3)",
                   "bound": "hbm", "achieved": ob / max(ortho_ms, 1e-9) / 1e6,
                   "bytes": ob / max(stats["ortho"]["calls"], 1), "ms": ortho_ms / max(stats["ortho"]["calls"], 1),
                   "calls": stats["ortho"]["calls"]},
-        "spmv": {"kernel": "k_spmv_csr (A, FP64)", "bound": "hbm", "achieved": sb / spmv_ms / 1e6,
+        "spmv": {"kernel": "k_spmv_sell (A, FP64)", "bound": "hbm", "achieved": sb / spmv_ms / 1e6,
                  "bytes": sb, "ms": spmv_ms, "calls": stats["spmv"]["calls"]},
     }
     for r in rl.values():

@@ -80,122 +80,220 @@ k_reduce(const double *__restrict__ partial, int nb, int stride, double *out, co
     if (threadIdx.x == 0) out[q] = s;
 }
 
-// Classical Gram-Schmidt with two passes, split by precision.  On GB300 the
-// FP64 pipe (1.2 TFLOP/s measured) bounds these passes, not HBM, so:
-//   pass 1 dots   h1 = V^T w   FP32 products on an FP32 copy of the basis;
-//   pass 1 update w -= V h1    FP64 (this subtraction cancels);
-//   pass 2 dots   h2 = V^T w   FP64 (it measures what pass 1 left in span V);
-//   pass 2 update w -= V h2    FP32 products (h2 is ~1e-6 |w|, so the FP32
-//                              error of the correction is ~1e-13 |w|),
-// and H(:, j) = h1 + h2 in FP64.  Pass 2 removes the FP32 error of pass 1, so
-// the basis is orthogonal to FP64 level and the Arnoldi relation holds in FP64.
+// Classical Gram-Schmidt with two passes, split by precision.  GB300's FP64
+// pipe (1.2 TFLOP/s measured, against 63.5 TFLOP/s FP32) would bound FP64
+// passes far below HBM speed, so no pass runs per-entry FP64 products.  The
+// basis is kept as V (FP64, the vectors the products read), and as the pair
+// (V_hi, V_lo) of FP32 arrays with V_hi = fl32(V), V_lo = fl32(V - V_hi):
+//   pass 1 dots   h1 = V^T w   FP32 products on V_hi;
+//   pass 1 update w -= V h1    double-float products on (V_hi, V_lo) and
+//                              (h_hi, h_lo), error-free two-sum accumulation
+//                              on the FP32 pipe, one FP64 subtraction per
+//                              entry (this subtraction cancels, so its error
+//                              must stay near FP64 level);
+//   pass 2 dots   h2 = V^T w   FP32 products on V_hi and fl32(w);
+//   pass 2 update w -= V h2    FP32 products on V_hi (h2 is ~1e-7 |w|),
+// and H(:, j) = h1 + h2 in FP64.  The updates keep the Arnoldi relation
+// A Z = V H at ~1e-14 relative; the FP32 dots leave the basis orthogonal to
+// ~1e-7, which does not move GMRES's residual estimate at the 1e-8 target.
 //
-// Dots: partial[b*ldp + q] = sum over block b's rows of V_q . w (q < nvec),
-// partial[b*ldp + nvec] = w . w when NORM.  One thread per row, one register
-// accumulator per vector of a chunk; the last chunk is instantiated for its
-// exact size so no FMA slot is wasted.  w is re-read from L2 for each chunk.
+// Layout: the basis columns have a leading dimension ldv = n rounded up to a
+// multiple of 4 with zero padding, so every kernel below moves 16-byte
+// vectors (four rows per thread) and never needs a ragged tail.
+//
+// Dots: partial[b*ldp + q] = sum over block b's rows of V_q . w (q < nvec).
+// One register accumulator per vector of a chunk; the last chunk is
+// instantiated for its exact size so no FMA slot is wasted.
 constexpr int kCH = 16;
 
-template <typename T, int CH, bool NORM>
-__device__ __forceinline__ void dot_chunk(int64_t n, const T *__restrict__ V, int64_t ldv, int q0,
-                                          const double *__restrict__ w, double *partial, int ldp, int nvec,
-                                          double (*red)[kCH + 1]) {
-    constexpr int NA = CH + (NORM ? 1 : 0);
+__device__ __forceinline__ float4 load_w4(const float4 *w, int64_t i4) { return w[i4]; }
+__device__ __forceinline__ float4 load_w4(const double2 *w, int64_t i4) {
+    const double2 a = w[2 * i4], b = w[2 * i4 + 1];
+    return make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+}
+
+template <typename TW, int CH>
+__device__ __forceinline__ void dot_chunk(int64_t n4, const float4 *__restrict__ V, int64_t ldv4, int q0,
+                                          const TW *__restrict__ w, double *partial, int ldp,
+                                          double (*red)[kCH]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    T acc[CH > 0 ? CH : 1];
-    double nacc = 0.0;
+    float acc[CH > 0 ? CH : 1];
 #pragma unroll
-    for (int t = 0; t < (CH > 0 ? CH : 1); t++) acc[t] = (T)0;
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
-        const double wd = w[i];
-        const T wi = (T)wd;
-        T vv[CH > 0 ? CH : 1];
+    for (int t = 0; t < (CH > 0 ? CH : 1); t++) acc[t] = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kThreads) {
+        const float4 wv = load_w4(w, i);
+        float4 vv[CH > 0 ? CH : 1];
 #pragma unroll
-        for (int t = 0; t < CH; t++) vv[t] = __ldg(V + (int64_t)(q0 + t) * ldv + i);
+        for (int t = 0; t < CH; t++) vv[t] = __ldg(V + (int64_t)(q0 + t) * ldv4 + i);
 #pragma unroll
-        for (int t = 0; t < CH; t++) acc[t] = fma(vv[t], wi, acc[t]);
-        if (NORM) nacc = fma(wd, wd, nacc);
+        for (int t = 0; t < CH; t++) {
+            float a = fmaf(vv[t].x, wv.x, acc[t]);
+            a = fmaf(vv[t].y, wv.y, a);
+            a = fmaf(vv[t].z, wv.z, a);
+            acc[t] = fmaf(vv[t].w, wv.w, a);
+        }
     }
 #pragma unroll
-    for (int t = 0; t < NA; t++) {
-        const double v = warp_sum(t < CH ? (double)acc[t < CH ? t : 0] : nacc);
+    for (int t = 0; t < CH; t++) {
+        const double v = warp_sum((double)acc[t]);
         if (lane == 0) red[warp][t] = v;
     }
     __syncthreads();
-    if (NA > 0 && (int)threadIdx.x < NA) {
+    if ((int)threadIdx.x < CH) {
         double sum = 0.0;
         for (int w2 = 0; w2 < kThreads / 32; w2++) sum += red[w2][threadIdx.x];
-        const int q = (int)threadIdx.x < CH ? q0 + (int)threadIdx.x : nvec;
-        partial[(int64_t)blockIdx.x * ldp + q] = sum;
+        partial[(int64_t)blockIdx.x * ldp + q0 + (int)threadIdx.x] = sum;
     }
     __syncthreads();
 }
 
-template <typename T, bool NORM>
-__device__ __forceinline__ void dot_tail(int rem, int64_t n, const T *V, int64_t ldv, int q0, const double *w,
-                                         double *partial, int ldp, int nvec, double (*red)[kCH + 1]) {
+template <typename TW>
+__device__ __forceinline__ void dot_tail(int rem, int64_t n4, const float4 *V, int64_t ldv4, int q0, const TW *w,
+                                         double *partial, int ldp, double (*red)[kCH]) {
     switch (rem) {
-#define SAIT_TAIL(k) case k: dot_chunk<T, k, NORM>(n, V, ldv, q0, w, partial, ldp, nvec, red); break;
-        SAIT_TAIL(0) SAIT_TAIL(1) SAIT_TAIL(2) SAIT_TAIL(3) SAIT_TAIL(4) SAIT_TAIL(5) SAIT_TAIL(6)
-        SAIT_TAIL(7) SAIT_TAIL(8) SAIT_TAIL(9) SAIT_TAIL(10) SAIT_TAIL(11) SAIT_TAIL(12) SAIT_TAIL(13)
-        SAIT_TAIL(14) SAIT_TAIL(15)
+#define SAIT_TAIL(k) case k: dot_chunk<TW, k>(n4, V, ldv4, q0, w, partial, ldp, red); break;
+        SAIT_TAIL(1) SAIT_TAIL(2) SAIT_TAIL(3) SAIT_TAIL(4) SAIT_TAIL(5) SAIT_TAIL(6) SAIT_TAIL(7)
+        SAIT_TAIL(8) SAIT_TAIL(9) SAIT_TAIL(10) SAIT_TAIL(11) SAIT_TAIL(12) SAIT_TAIL(13) SAIT_TAIL(14)
+        SAIT_TAIL(15)
 #undef SAIT_TAIL
         default: break;
     }
 }
 
-template <typename T>
+// h = V^T w with FP32 products: TW = double2 (w in FP64, rounded on load) or float4
+template <typename TW>
 __global__ void __launch_bounds__(kThreads)
-k_cgs_dot(int64_t n, const T *__restrict__ V, int64_t ldv, int nvec, const double *__restrict__ w,
-          double *partial, int ldp, int with_norm, const int *gate) {
+k_cgs_dot(int64_t n4, const float4 *__restrict__ V, int64_t ldv4, int nvec, const TW *__restrict__ w,
+          double *partial, int ldp, const int *gate) {
     if (gate && *gate == 0) return;
-    __shared__ double red[kThreads / 32][kCH + 1];
+    __shared__ double red[kThreads / 32][kCH];
     int q0 = 0;
-    for (; nvec - q0 >= kCH; q0 += kCH) dot_chunk<T, kCH, false>(n, V, ldv, q0, w, partial, ldp, nvec, red);
-    if (with_norm) dot_tail<T, true>(nvec - q0, n, V, ldv, q0, w, partial, ldp, nvec, red);
-    else dot_tail<T, false>(nvec - q0, n, V, ldv, q0, w, partial, ldp, nvec, red);
+    for (; nvec - q0 >= kCH; q0 += kCH) dot_chunk<TW, kCH>(n4, V, ldv4, q0, w, partial, ldp, red);
+    dot_tail<TW>(nvec - q0, n4, V, ldv4, q0, w, partial, ldp, red);
 }
 
-// Update: w -= V h over q < nvec with products in T (V stored in T, h rounded
-// to T), and partial[b] = ||w||^2 (FP64) of the updated rows of block b.
-template <typename T>
+// Knuth's two-sum of (S, p) into S plus the rounding error added to E; the
+// _rn intrinsics keep the compiler from contracting the error-free steps.
+__device__ __forceinline__ void df_add(float &S, float &E, float p, float e) {
+    const float sn = __fadd_rn(S, p);
+    const float bb = __fsub_rn(sn, S);
+    const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(sn, bb)), __fsub_rn(p, bb));
+    S = sn;
+    E = __fadd_rn(E, __fadd_rn(err, e));
+}
+
+// one double-float product term (vh + vl)(a + al), without the lo*lo part
+__device__ __forceinline__ void df_term(float &S, float &E, float vh, float vl, float a, float al) {
+    const float p = __fmul_rn(vh, a);
+    float e = __fmaf_rn(vh, a, -p);
+    e = __fmaf_rn(vh, al, e);
+    e = __fmaf_rn(vl, a, e);
+    df_add(S, E, p, e);
+}
+
+// Pass-1 update: w -= V h in double-float (see above), four rows per thread.
+// Writes w (FP64) and its FP32 rounding for the pass-2 dots.
 __global__ void __launch_bounds__(kThreads)
-k_cgs_update(int64_t n, const T *__restrict__ V, int64_t ldv, int nvec, const double *__restrict__ h,
-             double *w, double *partial, const int *gate) {
+k_cgs_update_df(int64_t n4, const float4 *__restrict__ Vh, const float4 *__restrict__ Vl, int64_t ldv4, int nvec,
+                const double *__restrict__ h, double2 *w, float4 *w32, const int *gate) {
     if (gate && *gate == 0) return;
-    __shared__ T hs[kMaxRestart + 1];
-    for (int q = threadIdx.x; q < nvec; q += kThreads) hs[q] = (T)h[q];
+    __shared__ float hh[kMaxRestart + 1], hl[kMaxRestart + 1];
+    for (int q = threadIdx.x; q < nvec; q += kThreads) {
+        const double hd = h[q];
+        const float a = (float)hd;
+        hh[q] = a;
+        hl[q] = (float)(hd - (double)a);
+    }
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kThreads) {
+        float S[4] = {0.0f, 0.0f, 0.0f, 0.0f}, E[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        int q = 0;
+        for (; q + 2 <= nvec; q += 2) {
+            const float4 h0 = __ldg(Vh + (int64_t)q * ldv4 + i), l0 = __ldg(Vl + (int64_t)q * ldv4 + i);
+            const float4 h1 = __ldg(Vh + (int64_t)(q + 1) * ldv4 + i), l1 = __ldg(Vl + (int64_t)(q + 1) * ldv4 + i);
+            const float a0 = hh[q], b0 = hl[q], a1 = hh[q + 1], b1 = hl[q + 1];
+            df_term(S[0], E[0], h0.x, l0.x, a0, b0);
+            df_term(S[1], E[1], h0.y, l0.y, a0, b0);
+            df_term(S[2], E[2], h0.z, l0.z, a0, b0);
+            df_term(S[3], E[3], h0.w, l0.w, a0, b0);
+            df_term(S[0], E[0], h1.x, l1.x, a1, b1);
+            df_term(S[1], E[1], h1.y, l1.y, a1, b1);
+            df_term(S[2], E[2], h1.z, l1.z, a1, b1);
+            df_term(S[3], E[3], h1.w, l1.w, a1, b1);
+        }
+        if (q < nvec) {
+            const float4 h0 = __ldg(Vh + (int64_t)q * ldv4 + i), l0 = __ldg(Vl + (int64_t)q * ldv4 + i);
+            const float a0 = hh[q], b0 = hl[q];
+            df_term(S[0], E[0], h0.x, l0.x, a0, b0);
+            df_term(S[1], E[1], h0.y, l0.y, a0, b0);
+            df_term(S[2], E[2], h0.z, l0.z, a0, b0);
+            df_term(S[3], E[3], h0.w, l0.w, a0, b0);
+        }
+        double2 wa = w[2 * i], wb = w[2 * i + 1];
+        wa.x -= (double)S[0] + (double)E[0];
+        wa.y -= (double)S[1] + (double)E[1];
+        wb.x -= (double)S[2] + (double)E[2];
+        wb.y -= (double)S[3] + (double)E[3];
+        w[2 * i] = wa;
+        w[2 * i + 1] = wb;
+        w32[i] = make_float4((float)wa.x, (float)wa.y, (float)wb.x, (float)wb.y);
+    }
+}
+
+// Pass-2 update: w -= V h with FP32 products on V_hi, four rows per thread;
+// partial[b] = ||w||^2 (FP64) of block b's rows.
+__global__ void __launch_bounds__(kThreads)
+k_cgs_update32(int64_t n4, const float4 *__restrict__ V, int64_t ldv4, int nvec, const double *__restrict__ h,
+               double2 *w, double *partial, const int *gate) {
+    if (gate && *gate == 0) return;
+    __shared__ float hs[kMaxRestart + 1];
+    for (int q = threadIdx.x; q < nvec; q += kThreads) hs[q] = (float)h[q];
     __syncthreads();
     double nrm = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
-        T s0 = 0, s1 = 0, s2 = 0, s3 = 0;  // four chains: FP64 latency is long
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kThreads) {
+        float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;  // two chains per row
         int q = 0;
-        for (; q + 4 <= nvec; q += 4) {
-            const T v0 = __ldg(V + (int64_t)q * ldv + i), v1 = __ldg(V + (int64_t)(q + 1) * ldv + i);
-            const T v2 = __ldg(V + (int64_t)(q + 2) * ldv + i), v3 = __ldg(V + (int64_t)(q + 3) * ldv + i);
-            s0 = fma(v0, hs[q], s0);
-            s1 = fma(v1, hs[q + 1], s1);
-            s2 = fma(v2, hs[q + 2], s2);
-            s3 = fma(v3, hs[q + 3], s3);
+        for (; q + 2 <= nvec; q += 2) {
+            const float4 v0 = __ldg(V + (int64_t)q * ldv4 + i), v1 = __ldg(V + (int64_t)(q + 1) * ldv4 + i);
+            const float a0 = hs[q], a1 = hs[q + 1];
+            s0.x = fmaf(v0.x, a0, s0.x); s0.y = fmaf(v0.y, a0, s0.y);
+            s0.z = fmaf(v0.z, a0, s0.z); s0.w = fmaf(v0.w, a0, s0.w);
+            s1.x = fmaf(v1.x, a1, s1.x); s1.y = fmaf(v1.y, a1, s1.y);
+            s1.z = fmaf(v1.z, a1, s1.z); s1.w = fmaf(v1.w, a1, s1.w);
         }
-        for (; q < nvec; q++) s0 = fma(__ldg(V + (int64_t)q * ldv + i), hs[q], s0);
-        const double wi = w[i] - (double)((s0 + s1) + (s2 + s3));
-        w[i] = wi;
-        nrm = fma(wi, wi, nrm);
+        if (q < nvec) {
+            const float4 v0 = __ldg(V + (int64_t)q * ldv4 + i);
+            const float a0 = hs[q];
+            s0.x = fmaf(v0.x, a0, s0.x); s0.y = fmaf(v0.y, a0, s0.y);
+            s0.z = fmaf(v0.z, a0, s0.z); s0.w = fmaf(v0.w, a0, s0.w);
+        }
+        double2 wa = w[2 * i], wb = w[2 * i + 1];
+        wa.x -= (double)(s0.x + s1.x);
+        wa.y -= (double)(s0.y + s1.y);
+        wb.x -= (double)(s0.z + s1.z);
+        wb.y -= (double)(s0.w + s1.w);
+        w[2 * i] = wa;
+        w[2 * i + 1] = wb;
+        nrm = fma(wa.x, wa.x, nrm);
+        nrm = fma(wa.y, wa.y, nrm);
+        nrm = fma(wb.x, wb.x, nrm);
+        nrm = fma(wb.y, wb.y, nrm);
     }
     nrm = block_sum(nrm);
     if (threadIdx.x == 0) partial[blockIdx.x] = nrm;
 }
 
-// v = w / ||w|| in FP64, plus its FP32 copy for the first Gram-Schmidt pass
-__global__ void k_scale2(int64_t n, const double *__restrict__ x, double *y, float *y32, const Scal *sc,
+// v = w / ||w|| in FP64 (rows < n), plus its FP32 pair (hi, lo)
+__global__ void k_scale3(int64_t n, const double *__restrict__ x, double *y, float *yh, float *yl, const Scal *sc,
                          const int *active) {
     if (active && *active == 0) return;
     const double a = sc->inv;
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
         const double v = x[i] * a;
+        const float hi = (float)v;
         y[i] = v;
-        y32[i] = (float)v;
+        yh[i] = hi;
+        yl[i] = (float)(v - (double)hi);
     }
 }
 
@@ -531,10 +629,19 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
     W.nb = (int)std::min<int64_t>(cdiv(n, kThreads), 4LL * ctx->num_sms);
     const int ldp = m + 2;
     DTemp<double> V, H, cs, sn, g, y, z, u, part, part2;
-    DTemp<float> V32;  // FP32 copy of the basis for the first Gram-Schmidt pass
+    DTemp<float> V32, VL, w32;  // the basis as FP32 (hi, lo) pairs; fl32(w) after pass 1
     DTemp<Scal> scd;
-    SAIT_CK(V.alloc((size_t)(m + 1) * n, s));
-    SAIT_CK(V32.alloc((size_t)(m + 1) * n, s));
+    const int64_t ldv = (n + 3) / 4 * 4, n4 = ldv / 4;  // columns padded to 16-byte vectors
+    SAIT_CK(V.alloc((size_t)(m + 1) * ldv, s));
+    SAIT_CK(V32.alloc((size_t)(m + 1) * ldv, s));
+    SAIT_CK(VL.alloc((size_t)(m + 1) * ldv, s));
+    SAIT_CK(w32.alloc((size_t)ldv, s));
+    if (ldv > n) {  // the padding rows stay zero for the whole solve
+        SAIT_CK(cudaMemset2DAsync(V.p + n, ldv * sizeof(double), 0, (ldv - n) * sizeof(double), m + 1, s));
+        SAIT_CK(cudaMemset2DAsync(V32.p + n, ldv * sizeof(float), 0, (ldv - n) * sizeof(float), m + 1, s));
+        SAIT_CK(cudaMemset2DAsync(VL.p + n, ldv * sizeof(float), 0, (ldv - n) * sizeof(float), m + 1, s));
+        SAIT_CK(cudaMemsetAsync(w32.p + n, 0, (ldv - n) * sizeof(float), s));
+    }
     SAIT_CK(H.alloc((size_t)(m + 1) * m, s));
     SAIT_CK(cs.alloc(m, s));
     SAIT_CK(sn.alloc(m, s));
@@ -543,7 +650,9 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
     SAIT_CK(z.alloc(n, s));
     SAIT_CK(u.alloc(n, s));
     SAIT_CK(part.alloc((size_t)W.nb * std::max(ldp, 3), s));
-    SAIT_CK(part2.alloc((size_t)W.nb, s));
+    const int nb_upd = (int)std::min<int64_t>(cdiv(n4, kThreads), 16LL * ctx->num_sms);
+    const int nb_dot = (int)std::min<int64_t>(cdiv(n4, kThreads), (int64_t)W.nb);
+    SAIT_CK(part2.alloc((size_t)std::max(W.nb, nb_upd), s));
     SAIT_CK(scd.alloc(1, s));
     SAIT_CK(cudaMemsetAsync(scd.p, 0, sizeof(Scal), s));
     W.partial = part.p;
@@ -589,11 +698,11 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
         if (!std::isfinite(hs.beta)) { result = SAIT_ERR_NONFINITE; break; }
         if (inf.rel_resid <= tol) { result = SAIT_OK; break; }
         if (iters >= maxit) break;
-        launch_k(k_scale2, egrid, kThreads, 0, s, n, (const double *)V.p, V.p, V32.p, (const Scal *)sc,
+        launch_k(k_scale3, egrid, kThreads, 0, s, n, (const double *)V.p, V.p, V32.p, VL.p, (const Scal *)sc,
                  nullptr);
         const int remaining = maxit - iters;
         for (int j = 0; j < m; j++) {
-            double *vj = V.p + (size_t)j * n, *w = V.p + (size_t)(j + 1) * n;
+            double *vj = V.p + (size_t)j * ldv, *w = V.p + (size_t)(j + 1) * ldv;
             SAIT_TRY(precondition(ctx, P, vj, z.p, n, act));
             {
                 ScopedTimer tm(ctx, SAIT_TIMER_SPMV);
@@ -604,25 +713,26 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
                 ScopedTimer tm(ctx, SAIT_TIMER_ORTHO);
                 double *Hj = H.p + (size_t)j * (m + 1);
                 const int nv = j + 1;
-                // pass 1: FP32 dots, FP64 update
-                launch_k(k_cgs_dot<float>, W.nb, kThreads, 0, s, n, (const float *)V32.p, (int64_t)n, nv,
-                         (const double *)w, W.partial, ldp, 0, act);
-                launch_k(k_reduce, nv, kThreads, 0, s, (const double *)W.partial, W.nb, ldp, y.p, act);
+                const float4 *Vh4 = (const float4 *)V32.p, *Vl4 = (const float4 *)VL.p;
+                // pass 1: FP32 dots, double-float update
+                launch_k(k_cgs_dot<double2>, nb_dot, kThreads, 0, s, n4, Vh4, n4, nv, (const double2 *)w,
+                         W.partial, ldp, act);
+                launch_k(k_reduce, nv, kThreads, 0, s, (const double *)W.partial, nb_dot, ldp, y.p, act);
                 launch_k(k_hadd, 1, 128, 0, s, Hj, (const double *)y.p, nv, 1, act);
-                launch_k(k_cgs_update<double>, W.nb, kThreads, 0, s, n, (const double *)V.p, (int64_t)n, nv,
-                         (const double *)y.p, w, W.partial2, act);
-                // pass 2: FP64 dots, FP32 update, ||w||^2
-                launch_k(k_cgs_dot<double>, W.nb, kThreads, 0, s, n, (const double *)V.p, (int64_t)n, nv,
-                         (const double *)w, W.partial, ldp, 0, act);
-                launch_k(k_reduce, nv, kThreads, 0, s, (const double *)W.partial, W.nb, ldp, y.p, act);
+                launch_k(k_cgs_update_df, nb_upd, kThreads, 0, s, n4, Vh4, Vl4, n4, nv, (const double *)y.p,
+                         (double2 *)w, (float4 *)w32.p, act);
+                // pass 2: FP32 dots and update, ||w||^2
+                launch_k(k_cgs_dot<float4>, nb_dot, kThreads, 0, s, n4, Vh4, n4, nv, (const float4 *)w32.p,
+                         W.partial, ldp, act);
+                launch_k(k_reduce, nv, kThreads, 0, s, (const double *)W.partial, nb_dot, ldp, y.p, act);
                 launch_k(k_hadd, 1, 128, 0, s, Hj, (const double *)y.p, nv, 0, act);
-                launch_k(k_cgs_update<float>, W.nb, kThreads, 0, s, n, (const float *)V32.p, (int64_t)n, nv,
-                         (const double *)y.p, w, W.partial2, act);
-                launch_k(k_reduce, 1, kThreads, 0, s, (const double *)W.partial2, W.nb, 1, r0, act);
+                launch_k(k_cgs_update32, nb_upd, kThreads, 0, s, n4, Vh4, n4, nv, (const double *)y.p,
+                         (double2 *)w, W.partial2, act);
+                launch_k(k_reduce, 1, kThreads, 0, s, (const double *)W.partial2, nb_upd, 1, r0, act);
                 launch_k(k_givens, 1, 1, 0, s, j, m, remaining, H.p, cs.p, sn.p, g.p, sc,
                          group_counter(ctx, SAIT_TIMER_ORTHO));
-                launch_k(k_scale2, egrid, kThreads, 0, s, n, (const double *)w, w, V32.p + (size_t)(j + 1) * n,
-                         (const Scal *)sc, act);
+                launch_k(k_scale3, egrid, kThreads, 0, s, n, (const double *)w, w, V32.p + (size_t)(j + 1) * ldv,
+                         VL.p + (size_t)(j + 1) * ldv, (const Scal *)sc, act);
             }
             SAIT_CK(cudaGetLastError());
             if ((j + 1) % poll == 0 || j + 1 == m) {
@@ -635,7 +745,7 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
         cycles++;
         if (hs.state == 3) { result = SAIT_ERR_NONFINITE; break; }
         launch_k(k_hsolve, 1, 1, 0, s, H.p, g.p, y.p, m, sc);
-        launch_k(k_gemv, egrid, kThreads, 0, s, n, V.p, n, 0, &sc->jdone, y.p, u.p, 0, nullptr);
+        launch_k(k_gemv, egrid, kThreads, 0, s, n, V.p, ldv, 0, &sc->jdone, y.p, u.p, 0, nullptr);
         SAIT_CK(cudaGetLastError());
         SAIT_TRY(precondition(ctx, P, u.p, z.p, n, nullptr));
         launch_k(k_axpy1, egrid, kThreads, 0, s, n, z.p, x);

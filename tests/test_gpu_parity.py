@@ -294,6 +294,23 @@ def test_bicgstab_convdiff(sg, ctx, oracle_lib, prec):
     assert abs(info.iters - ito) <= max(3, 0.1 * ito), (info.iters, ito)
 
 
+@pytest.mark.parametrize("restart", [7, 30])
+def test_gmres_ragged_n(sg, ctx, oracle_lib, restart):
+    """n = 17^3 = 4913 (not a multiple of 4: the padded basis rows must stay inert)."""
+    A = synth.convdiff3d(17)
+    b = oracle_lib.spmv(A, synth.uniform(21, A.n, -1.0, 1.0))
+    Lo, Uo = oracle_lib.ilu0(A)
+    L, U = sg.sait_ilu0(ctx, A.n, dev(A.rp), dev(A.ci), dev(A.va))
+    P = sg.sait_prec_create_sait(ctx, sg.sait_build(ctx, L, True, 3, "rowrel", 1e-3),
+                                 sg.sait_build(ctx, U, False, 3, "rowrel", 1e-3))
+    lo, up = oracle_lib.sait(Lo, 3, "rowrel", 1e-3), oracle_lib.sait(Uo, 3, "rowrel", 1e-3)
+    x, info, st = sg.sait_gmres(ctx, mat(sg, ctx, A), P, dev(b), restart=restart, tol=1e-10, maxit=3000)
+    xo, ito, rro, sto = oracle_lib.gmres(A, b, "sait", lo, up, restart=restart, tol=1e-10, maxit=3000)
+    rel = np.linalg.norm(b - oracle_lib.spmv(A, x.cpu().numpy())) / np.linalg.norm(b)
+    assert st == 0 and sto == 0 and rel <= 1e-10
+    assert abs(info.iters - ito) <= max(2, 0.02 * ito), (info.iters, ito)
+
+
 def test_gmres_nonconvergence_and_zero_rhs(sg, ctx, oracle_lib, c1):
     A, b, _, _ = c1
     Ag = mat(sg, ctx, A)
