@@ -133,10 +133,14 @@ __device__ __forceinline__ void dot_chunk(int64_t n4, const float4 *__restrict__
             acc[t] = fmaf(vv[t].w, wv.w, a);
         }
     }
+    // warp sums in FP32 (the products are FP32 anyway; FP64 adds here would
+    // cost more than the whole sweep on GB300), then FP64 across warps/blocks
 #pragma unroll
     for (int t = 0; t < CH; t++) {
-        const double v = warp_sum((double)acc[t]);
-        if (lane == 0) red[warp][t] = v;
+        float v = acc[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][t] = (double)v;
     }
     __syncthreads();
     if ((int)threadIdx.x < CH) {
@@ -283,6 +287,30 @@ k_cgs_update32(int64_t n4, const float4 *__restrict__ V, int64_t ldv4, int nvec,
     if (threadIdx.x == 0) partial[blockIdx.x] = nrm;
 }
 
+// (hi, lo) with hi = v truncated to 24 significant bits and lo = fl32(v - hi),
+// taken from the IEEE-754 fields with integer operations and one int->float
+// conversion, so no FP64 instruction is spent (conversions from FP64 share
+// GB300's narrow FP64 pipe).  |lo| < 2^-23 |hi| and |v - hi - lo| <=
+// 2^-47 |v|.  Values whose hi or lo would leave the FP32 normal range
+// (|v| < 2^-75 or |v| >= 2^128) take the conversion path.
+__device__ __forceinline__ void split_pair(double v, float &hi, float &lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ff);
+    const int ef = e - 896;  // FP32 biased exponent of hi (1023 - 127 = 896)
+    const int es = e - 948;  // FP32 biased exponent of 2^(e - 1075), the weight of the low fraction bits
+    if (es <= 0 || ef >= 255) {
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+        return;
+    }
+    const unsigned sign = (unsigned)(b >> 63) << 31;
+    const unsigned long long frac = b & ((1ULL << 52) - 1);
+    hi = __uint_as_float(sign | ((unsigned)ef << 23) | (unsigned)(frac >> 29));
+    const float r = __uint2float_rn((unsigned)(frac & ((1u << 29) - 1)));
+    const float m = r * __uint_as_float((unsigned)es << 23);
+    lo = sign ? -m : m;
+}
+
 // v = w / ||w|| in FP64 (rows < n), plus its FP32 pair (hi, lo)
 __global__ void k_scale3(int64_t n, const double *__restrict__ x, double *y, float *yh, float *yl, const Scal *sc,
                          const int *active) {
@@ -290,10 +318,11 @@ __global__ void k_scale3(int64_t n, const double *__restrict__ x, double *y, flo
     const double a = sc->inv;
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
         const double v = x[i] * a;
-        const float hi = (float)v;
+        float hi, lo;
+        split_pair(v, hi, lo);
         y[i] = v;
         yh[i] = hi;
-        yl[i] = (float)(v - (double)hi);
+        yl[i] = lo;
     }
 }
 
