@@ -69,15 +69,20 @@ k_dots(int64_t n, int nd, const double *__restrict__ x0, const double *__restric
     }
 }
 
-// out[q] = sum_b partial[b*stride + q]   (one block per q, fixed order)
+// out[q] = sum_b partial[b*stride + q]   (one block per q, fixed order);
+// with Hj given, also Hj[q] = out[q] (first) or Hj[q] += out[q]
 __global__ void __launch_bounds__(kThreads)
-k_reduce(const double *__restrict__ partial, int nb, int stride, double *out, const int *active) {
+k_reduce(const double *__restrict__ partial, int nb, int stride, double *out, const int *active, double *Hj,
+         int first) {
     if (active && *active == 0) return;
     const int q = blockIdx.x;
     double s = 0.0;
     for (int b = threadIdx.x; b < nb; b += kThreads) s += partial[(int64_t)b * stride + q];
     s = block_sum(s);
-    if (threadIdx.x == 0) out[q] = s;
+    if (threadIdx.x == 0) {
+        out[q] = s;
+        if (Hj) Hj[q] = first ? s : Hj[q] + s;
+    }
 }
 
 // Classical Gram-Schmidt with two passes, split by precision.  GB300's FP64
@@ -197,7 +202,7 @@ __device__ __forceinline__ void df_term(float &S, float &E, float vh, float vl, 
 
 // Pass-1 update: w -= V h in double-float (see above), four rows per thread.
 // Writes w (FP64) and its FP32 rounding for the pass-2 dots.
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 6)
 k_cgs_update_df(int64_t n4, const float4 *__restrict__ Vh, const float4 *__restrict__ Vl, int64_t ldv4, int nvec,
                 const double *__restrict__ h, double2 *w, float4 *w32, const int *gate) {
     if (gate && *gate == 0) return;
@@ -375,15 +380,17 @@ __global__ void k_gmres_start(Scal *sc, double *g, int m) {
     for (int i = 1; i <= m; i++) g[i] = 0.0;
 }
 
-// add the CGS coefficients of one pass into column j of H
-__global__ void k_hadd(double *Hj, const double *h, int nv, int first, const int *active) {
-    if (*active == 0) return;
-    for (int q = threadIdx.x; q < nv; q += blockDim.x) Hj[q] = first ? h[q] : Hj[q] + h[q];
-}
-
-__global__ void k_givens(int j, int m, int remaining, double *H, double *cs, double *sn, double *g, Scal *sc,
-                         int *calls) {
+// sc->r0 = ||w||^2 from the update's per-block partials (fixed order), then
+// one thread applies the previous rotations to column j of H and forms the new one
+__global__ void __launch_bounds__(kThreads)
+k_givens(int j, int m, int remaining, double *H, double *cs, double *sn, double *g, Scal *sc,
+         const double *__restrict__ partial, int nb, int *calls) {
     if (sc->active == 0) return;
+    double t0 = 0.0;
+    for (int b = threadIdx.x; b < nb; b += kThreads) t0 += partial[b];
+    t0 = block_sum(t0);
+    if (threadIdx.x != 0) return;
+    sc->r0 = t0;
     if (calls) atomicAdd(calls, 1);
     double *Hj = H + (int64_t)j * (m + 1);
     const double hn = sqrt(sc->r0);
@@ -598,7 +605,7 @@ cudaError_t dots(sait_ctx ctx, const Work &W, int64_t n, int nd, const double *x
                  const double *x1, const double *y1, const double *x2, const double *y2, double *out,
                  const int *active) {
     launch_k(k_dots, W.nb, kThreads, 0, ctx->stream, n, nd, x0, y0, x1, y1, x2, y2, W.partial, active);
-    launch_k(k_reduce, nd, kThreads, 0, ctx->stream, W.partial, W.nb, 3, out, active);
+    launch_k(k_reduce, nd, kThreads, 0, ctx->stream, W.partial, W.nb, 3, out, active, nullptr, 0);
     return cudaGetLastError();
 }
 
@@ -746,20 +753,17 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
                 // pass 1: FP32 dots, double-float update
                 launch_k(k_cgs_dot<double2>, nb_dot, kThreads, 0, s, n4, Vh4, n4, nv, (const double2 *)w,
                          W.partial, ldp, act);
-                launch_k(k_reduce, nv, kThreads, 0, s, (const double *)W.partial, nb_dot, ldp, y.p, act);
-                launch_k(k_hadd, 1, 128, 0, s, Hj, (const double *)y.p, nv, 1, act);
+                launch_k(k_reduce, nv, kThreads, 0, s, (const double *)W.partial, nb_dot, ldp, y.p, act, Hj, 1);
                 launch_k(k_cgs_update_df, nb_upd, kThreads, 0, s, n4, Vh4, Vl4, n4, nv, (const double *)y.p,
                          (double2 *)w, (float4 *)w32.p, act);
                 // pass 2: FP32 dots and update, ||w||^2
                 launch_k(k_cgs_dot<float4>, nb_dot, kThreads, 0, s, n4, Vh4, n4, nv, (const float4 *)w32.p,
                          W.partial, ldp, act);
-                launch_k(k_reduce, nv, kThreads, 0, s, (const double *)W.partial, nb_dot, ldp, y.p, act);
-                launch_k(k_hadd, 1, 128, 0, s, Hj, (const double *)y.p, nv, 0, act);
+                launch_k(k_reduce, nv, kThreads, 0, s, (const double *)W.partial, nb_dot, ldp, y.p, act, Hj, 0);
                 launch_k(k_cgs_update32, nb_upd, kThreads, 0, s, n4, Vh4, n4, nv, (const double *)y.p,
                          (double2 *)w, W.partial2, act);
-                launch_k(k_reduce, 1, kThreads, 0, s, (const double *)W.partial2, nb_upd, 1, r0, act);
-                launch_k(k_givens, 1, 1, 0, s, j, m, remaining, H.p, cs.p, sn.p, g.p, sc,
-                         group_counter(ctx, SAIT_TIMER_ORTHO));
+                launch_k(k_givens, 1, kThreads, 0, s, j, m, remaining, H.p, cs.p, sn.p, g.p, sc,
+                         (const double *)W.partial2, nb_upd, group_counter(ctx, SAIT_TIMER_ORTHO));
                 launch_k(k_scale3, egrid, kThreads, 0, s, n, (const double *)w, w, V32.p + (size_t)(j + 1) * ldv,
                          VL.p + (size_t)(j + 1) * ldv, (const Scal *)sc, act);
             }
@@ -973,7 +977,7 @@ extern "C" sait_status sait_pcg(sait_ctx ctx, sait_mat A, sait_prec P, const dou
             launch_k(k_pcg_alpha, 1, 1, 0, s, sc);
             launch_k(k_pcg_xr, (unsigned)W.nb, kThreads, 0, s, n, x, r.p, (const double *)p.p, (const double *)q.p,
                      (const Scal *)sc, W.partial);
-            launch_k(k_reduce, 1, kThreads, 0, s, (const double *)W.partial, W.nb, 3, r0, act);
+            launch_k(k_reduce, 1, kThreads, 0, s, (const double *)W.partial, W.nb, 3, r0, act, nullptr, 0);
             launch_k(k_pcg_check, 1, 1, 0, s, sc, (int)maxit);
             SAIT_TRY(precondition(ctx, P, r.p, z.p, n, act));
             SAIT_CK(dots(ctx, W, n, 1, r.p, z.p, nullptr, nullptr, nullptr, nullptr, r0, act));
