@@ -381,26 +381,35 @@ __global__ void k_gmres_start(Scal *sc, double *g, int m) {
 }
 
 // sc->r0 = ||w||^2 from the update's per-block partials (fixed order), then
-// one thread applies the previous rotations to column j of H and forms the new one
+// one thread applies the previous rotations to column j of H and forms the
+// new one.  The column and the rotations are staged in shared memory first:
+// the rotation chain is sequential, and global loads inside it would each
+// cost a full memory latency.
 __global__ void __launch_bounds__(kThreads)
 k_givens(int j, int m, int remaining, double *H, double *cs, double *sn, double *g, Scal *sc,
          const double *__restrict__ partial, int nb, int *calls) {
     if (sc->active == 0) return;
+    __shared__ double hc[kMaxRestart + 2], cc[kMaxRestart], ss[kMaxRestart];
+    double *Hj = H + (int64_t)j * (m + 1);
+    for (int i = threadIdx.x; i <= j; i += kThreads) hc[i] = Hj[i];
+    for (int i = threadIdx.x; i < j; i += kThreads) {
+        cc[i] = cs[i];
+        ss[i] = sn[i];
+    }
     double t0 = 0.0;
     for (int b = threadIdx.x; b < nb; b += kThreads) t0 += partial[b];
-    t0 = block_sum(t0);
+    t0 = block_sum(t0);  // synchronizes the block
     if (threadIdx.x != 0) return;
     sc->r0 = t0;
     if (calls) atomicAdd(calls, 1);
-    double *Hj = H + (int64_t)j * (m + 1);
-    const double hn = sqrt(sc->r0);
-    Hj[j + 1] = hn;
+    const double hn = sqrt(t0);
+    hc[j + 1] = hn;
     for (int i = 0; i < j; i++) {
-        const double t = cs[i] * Hj[i] + sn[i] * Hj[i + 1];
-        Hj[i + 1] = -sn[i] * Hj[i] + cs[i] * Hj[i + 1];
-        Hj[i] = t;
+        const double t = cc[i] * hc[i] + ss[i] * hc[i + 1];
+        hc[i + 1] = -ss[i] * hc[i] + cc[i] * hc[i + 1];
+        hc[i] = t;
     }
-    const double a = Hj[j], b = hn;
+    const double a = hc[j], b = hn;
     double c = 1.0, s = 0.0;
     if (b != 0.0) {
         const double t = hypot(a, b);
@@ -409,13 +418,15 @@ k_givens(int j, int m, int remaining, double *H, double *cs, double *sn, double 
     }
     cs[j] = c;
     sn[j] = s;
-    Hj[j] = c * a + s * b;
-    Hj[j + 1] = 0.0;
-    g[j + 1] = -s * g[j];
-    g[j] = c * g[j];
+    hc[j] = c * a + s * b;
+    hc[j + 1] = 0.0;
+    for (int i = 0; i <= j + 1; i++) Hj[i] = hc[i];
+    const double gj = g[j];
+    g[j + 1] = -s * gj;
+    g[j] = c * gj;
     sc->jdone = j + 1;
     sc->inv = hn != 0.0 ? 1.0 / hn : 0.0;
-    const double est = fabs(g[j + 1]);
+    const double est = fabs(s * gj);
     if (!isfinite(est) || !isfinite(hn)) {
         sc->state = 3;
         sc->active = 0;
@@ -424,16 +435,30 @@ k_givens(int j, int m, int remaining, double *H, double *cs, double *sn, double 
     }
 }
 
-// back substitution H y = g on the first jdone rows
-__global__ void k_hsolve(const double *H, const double *g, double *y, int m, Scal *sc) {
+// back substitution H y = g on the first jdone rows, column-oriented: once
+// y_i is known every thread removes its multiple from the rows above
+__global__ void __launch_bounds__(kThreads) k_hsolve(const double *H, const double *g, double *y, int m, Scal *sc) {
+    __shared__ double sv[kMaxRestart + 1], yv[kMaxRestart + 1];
     const int jd = sc->jdone;
+    for (int k = threadIdx.x; k < jd; k += kThreads) sv[k] = g[k];
+    __syncthreads();
     for (int i = jd - 1; i >= 0; i--) {
-        double s = g[i];
-        for (int k = i + 1; k < jd; k++) s -= H[(int64_t)k * (m + 1) + i] * y[k];
-        const double d = H[(int64_t)i * (m + 1) + i];
-        if (d == 0.0) { sc->state = 2; y[i] = 0.0; continue; }
-        y[i] = s / d;
+        const double *Hi = H + (int64_t)i * (m + 1);  // column i: Hi[k] = H(k, i)
+        if (threadIdx.x == 0) {
+            const double d = Hi[i];
+            if (d == 0.0) {
+                sc->state = 2;
+                yv[i] = 0.0;
+            } else {
+                yv[i] = sv[i] / d;
+            }
+        }
+        __syncthreads();
+        const double yi = yv[i];
+        for (int k = threadIdx.x; k < i; k += kThreads) sv[k] -= Hi[k] * yi;
+        __syncthreads();
     }
+    for (int k = threadIdx.x; k < jd; k += kThreads) y[k] = yv[k];
 }
 
 // ---- BiCGSTAB kernels ---------------------------------------------------------
@@ -777,7 +802,7 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
         iters += hs.jdone;
         cycles++;
         if (hs.state == 3) { result = SAIT_ERR_NONFINITE; break; }
-        launch_k(k_hsolve, 1, 1, 0, s, H.p, g.p, y.p, m, sc);
+        launch_k(k_hsolve, 1, kThreads, 0, s, H.p, g.p, y.p, m, sc);
         launch_k(k_gemv, egrid, kThreads, 0, s, n, V.p, ldv, 0, &sc->jdone, y.p, u.p, 0, nullptr);
         SAIT_CK(cudaGetLastError());
         SAIT_TRY(precondition(ctx, P, u.p, z.p, n, nullptr));
