@@ -172,6 +172,7 @@ def batched_workloads(sg, ctx, torch, device, stream):
     b = A.to_scipy() @ synth.uniform(synth.SEED_BASE + 5, A.n)
     d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in
          (("rp", A.rp), ("ci", A.ci), ("va", A.va), ("b", b), ("ptr", ptr))}
+    out["tile_autotune"] = sg.sait_batch_autotune(ctx, A.n, d["ptr"]).as_dict()  # setup, before the timed solves
 
     def solve_batch(store):
         L, U = sg.sait_ilu0(ctx, A.n, d["rp"], d["ci"], d["va"])
@@ -187,7 +188,8 @@ def batched_workloads(sg, ctx, torch, device, stream):
         solve_batch(store)                                   # warm-up (graph capture, pools)
         ms, (info, keep) = time_region(torch, stream, lambda: solve_batch(store))
         del keep
-        res[store] = {"ms": round(ms, 3), **info.as_dict()}
+        res[store] = {"ms": round(ms, 3), "ms_per_iteration": round(ms / max(info.graph_replays, 1), 4),
+                      **info.as_dict()}
     out["independent_systems"] = {"nsys": len(systems), "n": A.n, "nnz": A.nnz,
                                   "sides": [int(sides.min()), int(sides.max())], "solver": "bicgstab",
                                   "m_terms": 3, "tol": TOL, **res}
@@ -216,7 +218,8 @@ def batched_workloads(sg, ctx, torch, device, stream):
         solve_multi(store)
         ms, (info, keep) = time_region(torch, stream, lambda: solve_multi(store))
         del keep
-        res[store] = {"ms": round(ms, 3), **info.as_dict()}
+        res[store] = {"ms": round(ms, 3), "ms_per_iteration": round(ms / max(info.graph_replays, 1), 4),
+                      **info.as_dict()}
     out["many_rhs"] = {"n": A.n, "k": k, "solver": "bicgstab", "m_terms": 3, "tol": TOL, **res}
     del d
     torch.cuda.empty_cache()
@@ -287,6 +290,17 @@ def paper_replica_workload(sg, ctx, torch, device, stream):
         out["rows"].append(row)
     out["jacobi"] = [{"sweeps": k, **pcg(sg.sait_prec_create_jacobi(ctx, L, U, k))} for k in (1, 2, 3, 4, 6, 10, 15)]
     return out
+
+
+def autotune_workload(sg, ctx, torch, device, stream, P: "Problem", m, store):
+    """Product autotuning on the benchmark matrices: every candidate kernel's time and the choice."""
+    d = P.dev
+    L, U = sg.sait_ilu0(ctx, P.A.n, d["rp"], d["ci"], d["va"])
+    ML = sg.sait_build(ctx, L, True, m, DROP, TAU, store=store)
+    MU = sg.sait_build(ctx, U, False, m, DROP, TAU, store=store)
+    Am = sg.sait_mat_create_csr(ctx, P.A.n, d["rp"], d["ci"], d["va"])
+    return {"A": sg.sait_mat_autotune(ctx, Am).as_dict(), "M_L": sg.sait_mat_autotune(ctx, ML).as_dict(),
+            "M_U": sg.sait_mat_autotune(ctx, MU).as_dict()}
 
 
 def adjoint_workload(sg, ctx, torch, device, stream):
@@ -574,6 +588,7 @@ def run_ours(a):
         out["adjoint"] = adjoint_workload(sg, ctx, torch, device, stream)
         out["eigen"] = eigen_workload(sg, ctx, torch, device, stream)
         out["paper_replica"] = paper_replica_workload(sg, ctx, torch, device, stream)
+        out["autotune"] = autotune_workload(sg, ctx, torch, device, stream, P, a.m, a.store)
 
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         v, sample, _ = oracle_sample(a.grid, a.m, gpu_iters=iters)

@@ -225,6 +225,41 @@ sait_status sait_spmm(sait_ctx ctx, sait_mat A, int32_t k, const double *X, int6
 sait_status sait_apply_multi(sait_ctx ctx, sait_mat ML, sait_mat MU, int32_t k, const double *R,
                              int64_t ldr, double *Z, int64_t ldz);
 
+/* ---- autotuning ---------------------------------------------------------------- */
+
+typedef struct {
+    int32_t ncand;       /* candidates timed */
+    int32_t chosen;      /* index of the fastest */
+    int32_t format[6];   /* 0 CSR, 1 SELL-32 */
+    int32_t lanes[6];    /* lanes per row (32 for SELL-32) */
+    float us[6];         /* mean time of one product y = M x, microseconds */
+} sait_tune_report;
+
+/* Times every product kernel that can serve M in its current storage
+ * precision (SELL-32 when its padding stays under 20%, CSR with 2..32 lanes
+ * per row) on this context's stream and makes the fastest the one every later
+ * product with M uses (sait_spmv, the SAIT apply, solver products).  A
+ * project extension: the paper has no product kernels to choose between.
+ * Synchronizes. */
+sait_status sait_mat_autotune(sait_ctx ctx, sait_mat M, sait_tune_report *report);
+
+typedef struct {
+    int32_t ncand;
+    int32_t chosen;
+    int32_t tile_rows[6];  /* candidate tile sizes (rows) */
+    float us[6];           /* one tiled dot + per-system reduction, microseconds */
+} sait_batch_tune_report;
+
+/* Chooses the tile size of the batched solver's schedule (tiles never cross a
+ * system; one block reduces one tile) for the batch described by n and
+ * sys_ptr (device, as in sait_bicgstab_batched) by timing the tiled dot and
+ * the per-system reduction for 512..8192-row tiles, and keeps the fastest in
+ * ctx for later sait_bicgstab_batched calls.  Synchronizes. */
+sait_status sait_batch_autotune(sait_ctx ctx, int64_t n, int32_t nsys, const int64_t *sys_ptr,
+                                sait_batch_tune_report *report);
+/* Sets the tile size directly (32 .. 2^20 rows; default 2048). */
+sait_status sait_ctx_set_batch_tile(sait_ctx ctx, int64_t rows);
+
 /* ---- batched solves ---------------------------------------------------------- */
 
 typedef struct {

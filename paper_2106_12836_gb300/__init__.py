@@ -28,6 +28,7 @@ __all__ = [
     "sait_apply_static", "APPLY_STATIC_MAX_N", "sait_spmm", "sait_apply_multi", "sait_mat_transpose",
     "sait_outer_on_pattern", "sait_bicgstab_batched", "sait_bicgstab_multi", "BatchInfo", "Stats",
     "TIMERS", "lib_path", "EXPORTS", "sait_lobpcg", "sait_pcg", "sait_prec_create_jacobi", "sait_ilut",
+    "sait_mat_autotune", "sait_batch_autotune", "sait_ctx_set_batch_tile",
 ]
 
 DROP = {"none": 0, "abs": 1, "rowrel": 2, "pattern": 3}
@@ -43,6 +44,7 @@ EXPORTS = [
     "sait_prec_destroy", "sait_gmres", "sait_bicgstab", "sait_ctx_set_timing", "sait_ctx_stats",
     "sait_apply_static", "sait_spmm", "sait_apply_multi", "sait_mat_transpose", "sait_outer_on_pattern",
     "sait_bicgstab_batched", "sait_bicgstab_multi", "sait_lobpcg", "sait_pcg", "sait_prec_create_jacobi", "sait_ilut",
+    "sait_mat_autotune", "sait_batch_autotune", "sait_ctx_set_batch_tile",
 ]
 APPLY_STATIC_MAX_N = 2097152  # SAIT_APPLY_STATIC_MAX_N in include/sait.h
 TIMERS = ["apply", "spmv", "ortho", "build", "ilu", "trisolve"]
@@ -72,6 +74,24 @@ class BatchInfo(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("ncand", C.c_int32), ("chosen", C.c_int32), ("format", C.c_int32 * 6),
+                ("lanes", C.c_int32 * 6), ("us", C.c_float * 6)]
+
+    def as_dict(self):
+        return {"chosen": {"format": ("csr", "sell32")[self.format[self.chosen]], "lanes": self.lanes[self.chosen]},
+                "candidates": [{"format": ("csr", "sell32")[self.format[i]], "lanes": self.lanes[i],
+                                "us": round(self.us[i], 2)} for i in range(self.ncand)]}
+
+
+class BatchTuneReport(C.Structure):
+    _fields_ = [("ncand", C.c_int32), ("chosen", C.c_int32), ("tile_rows", C.c_int32 * 6), ("us", C.c_float * 6)]
+
+    def as_dict(self):
+        return {"chosen_tile_rows": self.tile_rows[self.chosen],
+                "candidates": [{"tile_rows": self.tile_rows[i], "us": round(self.us[i], 2)} for i in range(self.ncand)]}
 
 
 class Info(C.Structure):
@@ -132,6 +152,9 @@ def _L():
             "sait_pcg": [vp, vp, vp, vp, vp, d, i32, C.POINTER(Info)],
             "sait_prec_create_jacobi": [vp, vp, vp, i32, C.POINTER(vp)],
             "sait_ilut": [vp, C.POINTER(_Csr), d, i32, C.POINTER(vp), C.POINTER(vp)],
+            "sait_mat_autotune": [vp, vp, C.POINTER(TuneReport)],
+            "sait_batch_autotune": [vp, i64, i32, vp, C.POINTER(BatchTuneReport)],
+            "sait_ctx_set_batch_tile": [vp, i64],
         }
         for name, args in sigs.items():
             f = getattr(lib, name)
@@ -543,3 +566,24 @@ def sait_pcg(ctx: Context, A: Mat, P: Prec | None, b: torch.Tensor, x: torch.Ten
     if check:
         _check(ctx, st, "sait_pcg")
     return x, info, st
+
+
+def sait_mat_autotune(ctx: Context, M: Mat) -> TuneReport:
+    """Time M's product kernels and keep the fastest for later products."""
+    r = TuneReport()
+    _check(ctx, _L().sait_mat_autotune(ctx.h, M.h, C.byref(r)), "sait_mat_autotune")
+    return r
+
+
+def sait_batch_autotune(ctx: Context, n: int, sys_ptr: torch.Tensor) -> BatchTuneReport:
+    """Choose the batched solver's tile size for this batch (kept in ctx)."""
+    if sys_ptr.dtype != torch.int64 or not sys_ptr.is_cuda:
+        raise ValueError("sys_ptr: int64 CUDA tensor expected")
+    r = BatchTuneReport()
+    _check(ctx, _L().sait_batch_autotune(ctx.h, int(n), sys_ptr.numel() - 1, _ptr_any(sys_ptr), C.byref(r)),
+           "sait_batch_autotune")
+    return r
+
+
+def sait_ctx_set_batch_tile(ctx: Context, rows: int):
+    _check(ctx, _L().sait_ctx_set_batch_tile(ctx.h, int(rows)), "sait_ctx_set_batch_tile")

@@ -22,7 +22,6 @@
 namespace {
 
 constexpr int kT = 256;        // threads per block
-constexpr int kTile = 2048;    // rows per tile (8 per thread)
 constexpr int kPollB = 8;      // iterations replayed between status reads
 
 // per-system state (structure of arrays)
@@ -53,24 +52,24 @@ __device__ __forceinline__ double block_sum(double v) {
 }
 
 // ---- tile schedule ------------------------------------------------------------
-__global__ void k_tile_count(int nsys, const int64_t *__restrict__ sys_ptr, int32_t *cnt, int *err) {
+__global__ void k_tile_count(int nsys, const int64_t *__restrict__ sys_ptr, int64_t tile, int32_t *cnt, int *err) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsys) return;
     const int64_t len = sys_ptr[s + 1] - sys_ptr[s];
     if (len < 0) atomicOr(err, 1);
-    cnt[s] = len > 0 ? (int32_t)cdiv(len, kTile) : 0;
+    cnt[s] = len > 0 ? (int32_t)cdiv(len, tile) : 0;
 }
 
 // tiles[t] = (system, first row, end row)
-__global__ void k_tile_fill(int nsys, const int64_t *__restrict__ sys_ptr, const int64_t *__restrict__ tptr,
-                            int32_t *tsys, int64_t *tbeg, int64_t *tend) {
+__global__ void k_tile_fill(int nsys, const int64_t *__restrict__ sys_ptr, int64_t tile,
+                            const int64_t *__restrict__ tptr, int32_t *tsys, int64_t *tbeg, int64_t *tend) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsys) return;
     int64_t t = tptr[s];
-    for (int64_t r = sys_ptr[s]; r < sys_ptr[s + 1]; r += kTile, t++) {
+    for (int64_t r = sys_ptr[s]; r < sys_ptr[s + 1]; r += tile, t++) {
         tsys[t] = s;
         tbeg[t] = r;
-        tend[t] = min(r + (int64_t)kTile, sys_ptr[s + 1]);
+        tend[t] = min(r + tile, sys_ptr[s + 1]);
     }
 }
 
@@ -438,7 +437,8 @@ extern "C" sait_status sait_bicgstab_batched(sait_ctx ctx, sait_mat A, sait_prec
     SAIT_CK(tcnt.alloc(nsys, s0));
     SAIT_CK(tptr.alloc(nsys + 1, s0));
     SAIT_CK(cudaMemsetAsync(ctx->d_word, 0, sizeof(int), s0));
-    launch_k(k_tile_count, (unsigned)cdiv(nsys, 256), 256, 0, s0, (int)nsys, sys_ptr, tcnt.p, ctx->d_word);
+    const int64_t tile = ctx->batch_tile;
+    launch_k(k_tile_count, (unsigned)cdiv(nsys, 256), 256, 0, s0, (int)nsys, sys_ptr, tile, tcnt.p, ctx->d_word);
     SAIT_CK(scan_i32(tcnt.p, tptr.p, nsys, s0));
     int64_t *h64 = (int64_t *)((char *)ctx->h_pinned + 256);
     SAIT_CK(cudaMemcpyAsync(h, ctx->d_word, sizeof(int), cudaMemcpyDeviceToHost, s0));
@@ -453,8 +453,8 @@ extern "C" sait_status sait_bicgstab_batched(sait_ctx ctx, sait_mat A, sait_prec
     SAIT_CK(tsys.alloc(ntiles, s0));
     SAIT_CK(tbeg.alloc(ntiles, s0));
     SAIT_CK(tend.alloc(ntiles, s0));
-    launch_k(k_tile_fill, (unsigned)cdiv(nsys, 256), 256, 0, s0, (int)nsys, sys_ptr, (const int64_t *)tptr.p, tsys.p,
-             tbeg.p, tend.p);
+    launch_k(k_tile_fill, (unsigned)cdiv(nsys, 256), 256, 0, s0, (int)nsys, sys_ptr, tile, (const int64_t *)tptr.p,
+             tsys.p, tbeg.p, tend.p);
     Buffers B;
     for (DTemp<double> *d : {&B.r, &B.rh, &B.p, &B.v, &B.ph, &B.sv, &B.sh, &B.t}) SAIT_CK(d->alloc(n, s0));
     SAIT_CK(B.partial.alloc((size_t)ntiles * 3, s0));
@@ -747,5 +747,96 @@ extern "C" sait_status sait_bicgstab_multi(sait_ctx ctx, sait_mat A, sait_prec P
                  sait_status_string(result), bi.converged, (int)k, bi.max_rel_resid);
         return ctx_fail(ctx, result, buf);
     }
+    return SAIT_OK;
+}
+
+// ---- tile-size autotuning ---------------------------------------------------------
+// Times the schedule-dependent part of one batched iteration (the per-tile dot
+// kernel and the per-system reduction, the reductions that every BiCGSTAB
+// step runs four to five times) for each candidate tile size on the caller's
+// batch, and keeps the fastest in the context for later batched solves.
+extern "C" sait_status sait_batch_autotune(sait_ctx ctx, int64_t n, int32_t nsys, const int64_t *sys_ptr,
+                                           sait_batch_tune_report *report) {
+    if (!ctx) return SAIT_ERR_INVALID_ARG;
+    if (n < 0 || nsys < 1 || !sys_ptr || !report)
+        return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_batch_autotune: bad argument");
+    cudaStream_t s = ctx->stream;
+    const int64_t cand[] = {512, 1024, 2048, 4096, 8192};
+    const int nc = (int)(sizeof(cand) / sizeof(cand[0]));
+    *report = sait_batch_tune_report{};
+    report->ncand = nc;
+    int *h = (int *)ctx->h_pinned;
+    int64_t *h64 = (int64_t *)((char *)ctx->h_pinned + 256);
+    DTemp<double> x, red;
+    SAIT_CK(x.alloc(std::max<int64_t>(n, 1), s));
+    SAIT_CK(red.alloc((size_t)nsys * 3, s));
+    SAIT_CK(cudaMemsetAsync(x.p, 0, std::max<int64_t>(n, 1) * sizeof(double), s));
+    cudaEvent_t e0, e1;
+    SAIT_CK(cudaEventCreate(&e0));
+    SAIT_CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    sait_status st = SAIT_OK;
+    for (int c = 0; c < nc && st == SAIT_OK; c++) {
+        const int64_t tile = cand[c];
+        DTemp<int32_t> tcnt, tsys;
+        DTemp<int64_t> tptr, tbeg, tend;
+        DTemp<double> partial;
+        cudaError_t e = tcnt.alloc(nsys, s);
+        if (e == cudaSuccess) e = tptr.alloc(nsys + 1, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_word, 0, sizeof(int), s);
+        if (e != cudaSuccess) { st = ctx_cuda(ctx, e, "sait_batch_autotune", __FILE__, __LINE__); break; }
+        launch_k(k_tile_count, (unsigned)cdiv(nsys, 256), 256, 0, s, (int)nsys, sys_ptr, tile, tcnt.p, ctx->d_word);
+        e = scan_i32(tcnt.p, tptr.p, nsys, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, ctx->d_word, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h64, tptr.p + nsys, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h64 + 1, sys_ptr + nsys, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { st = ctx_cuda(ctx, e, "sait_batch_autotune", __FILE__, __LINE__); break; }
+        if (h[0] != 0 || h64[1] != n) {
+            st = ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_batch_autotune: sys_ptr must be non-decreasing to n");
+            break;
+        }
+        const int64_t ntiles = h64[0];
+        e = tsys.alloc(std::max<int64_t>(ntiles, 1), s);
+        if (e == cudaSuccess) e = tbeg.alloc(std::max<int64_t>(ntiles, 1), s);
+        if (e == cudaSuccess) e = tend.alloc(std::max<int64_t>(ntiles, 1), s);
+        if (e == cudaSuccess) e = partial.alloc((size_t)std::max<int64_t>(ntiles, 1) * 3, s);
+        if (e != cudaSuccess) { st = ctx_cuda(ctx, e, "sait_batch_autotune", __FILE__, __LINE__); break; }
+        launch_k(k_tile_fill, (unsigned)cdiv(nsys, 256), 256, 0, s, (int)nsys, sys_ptr, tile, (const int64_t *)tptr.p,
+                 tsys.p, tbeg.p, tend.p);
+        const unsigned gt = (unsigned)ntiles, gs = (unsigned)cdiv(nsys, 256);
+        auto one = [&]() {
+            launch_k(k_bt_dots, gt, kT, 0, s, (const int32_t *)tsys.p, (const int64_t *)tbeg.p, (const int64_t *)tend.p,
+                     (const int *)nullptr, 2, (const double *)x.p, (const double *)x.p, (const double *)x.p,
+                     (const double *)x.p, (const double *)nullptr, (const double *)nullptr, partial.p);
+            launch_k(k_bt_reduce, gs, 256, 0, s, (int)nsys, (const int64_t *)tptr.p, (const int *)nullptr, 2,
+                     (const double *)partial.p, red.p);
+        };
+        for (int w = 0; w < 3; w++) one();
+        constexpr int reps = 10;
+        e = cudaEventRecord(e0, s);
+        for (int r = 0; r < reps; r++) one();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) { st = ctx_cuda(ctx, e, "sait_batch_autotune", __FILE__, __LINE__); break; }
+        report->tile_rows[c] = (int32_t)tile;
+        report->us[c] = ms * 1e3f / reps;
+        if (report->us[c] < best) {
+            best = report->us[c];
+            report->chosen = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == SAIT_OK) ctx->batch_tile = cand[report->chosen];
+    return st;
+}
+
+extern "C" sait_status sait_ctx_set_batch_tile(sait_ctx ctx, int64_t rows) {
+    if (!ctx) return SAIT_ERR_INVALID_ARG;
+    if (rows < 32 || rows > (1 << 20)) return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_ctx_set_batch_tile: rows out of range");
+    ctx->batch_tile = rows;
     return SAIT_OK;
 }

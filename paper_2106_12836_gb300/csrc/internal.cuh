@@ -36,6 +36,7 @@ struct sait_ctx_s {
     double ms[SAIT_TIMER_COUNT] = {};
     int64_t host_calls[SAIT_TIMER_COUNT] = {};
     int64_t launch_base = 0;
+    int64_t batch_tile = 2048;  // rows per tile of the batched solver's schedule (sait_batch_autotune)
 };
 
 // Kernel launches made by this host thread (graph kernel nodes included).
@@ -72,6 +73,7 @@ struct sait_mat_s {
     int lanes = 8;                  // lanes per row for CSR products
     // SELL-32 copy for products (built on demand; see sell.cu)
     bool sell_rejected = false;     // padding above 20%: products stay on CSR
+    bool force_csr = false;         // set by sait_mat_autotune when CSR products won
     int64_t nslices = 0, sell_nnz = 0;
     int64_t *soff = nullptr;
     int32_t *sci = nullptr;

@@ -1,0 +1,103 @@
+"""Autotuners: the product kernel chosen per matrix and the batched tile size.
+
+Bars: every candidate is timed (positive times), the chosen one is the
+fastest, and results after tuning still meet the product / solver bars of
+the parity tests (FP64 products within 1e-12 (|M||x|)_i of the oracle;
+batched solves reach the tolerance on every system).
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sg():
+    from paper_2106_12836_gb300 import build
+    build.build()
+    import paper_2106_12836_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(sg):
+    torch.cuda.set_device(0)
+    c = sg.Context()
+    yield c
+    torch.cuda.synchronize()
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("store", ["f64", "f32"])
+def test_mat_autotune_keeps_products_exact(sg, ctx, oracle_lib, store):
+    A = synth.convdiff3d(24)
+    Lo, _ = oracle_lib.ilu0(A)
+    L, _ = sg.sait_ilu0(ctx, A.n, dev(A.rp), dev(A.ci), dev(A.va))
+    M = sg.sait_build(ctx, L, True, 3, "rowrel", 1e-3, store=store)
+    Mo = oracle_lib.sait(Lo, 3, "rowrel", 1e-3)
+    x = synth.uniform(3, A.n, -1.0, 1.0)
+    rep = sg.sait_mat_autotune(ctx, M)
+    assert rep.ncand >= 5 and 0 <= rep.chosen < rep.ncand
+    us = [rep.us[i] for i in range(rep.ncand)]
+    assert min(us) > 0.0 and rep.us[rep.chosen] == min(us)
+    y = sg.sait_spmv(ctx, M, dev(x)).cpu().numpy()
+    ref = oracle_lib.spmv(Mo, x)
+    bound = np.abs(Mo.to_scipy()) @ np.abs(x)
+    tol = 1e-12 if store == "f64" else 1e-5
+    assert np.all(np.abs(y - ref) <= tol * bound + 1e-300)
+
+
+def test_mat_autotune_ragged_matrix(sg, ctx, oracle_lib):
+    """A matrix too ragged for SELL-32: only CSR candidates, and the result is still exact."""
+    T = synth.random_triangular(3000, True, 7, max_row=20, long_frac=0.02, long_row=400)
+    M = sg.sait_mat_create_csr(ctx, T.n, dev(T.rp), dev(T.ci), dev(T.va))
+    rep = sg.sait_mat_autotune(ctx, M)
+    assert rep.ncand in (5, 6)
+    x = synth.uniform(5, T.n, -1.0, 1.0)
+    y = sg.sait_spmv(ctx, M, dev(x)).cpu().numpy()
+    bound = np.abs(T.to_scipy()) @ np.abs(x)
+    assert np.all(np.abs(y - oracle_lib.spmv(T, x)) <= 1e-12 * bound + 1e-300)
+
+
+def test_batch_autotune_then_solve(sg, ctx, oracle_lib):
+    sides, eps = synth.aniso2d_batch_params(24, 99, smin=8, smax=40)
+    systems = [synth.aniso2d(int(s), float(e)) for s, e in zip(sides, eps)]
+    n = sum(m.n for m in systems)
+    rp = np.zeros(n + 1, np.int64)
+    ci, va, r0, e0 = [], [], 0, 0
+    for m in systems:
+        rp[r0 + 1:r0 + m.n + 1] = m.rp[1:].astype(np.int64) + e0
+        ci.append(m.ci.astype(np.int64) + r0)
+        va.append(m.va)
+        r0 += m.n
+        e0 += m.nnz
+    A = synth.CSR(n, rp.astype(np.int32), np.concatenate(ci).astype(np.int32), np.concatenate(va))
+    ptr = np.concatenate([[0], np.cumsum([m.n for m in systems])]).astype(np.int64)
+    b = oracle_lib.spmv(A, synth.uniform(11, n, -1.0, 1.0))
+    rep = sg.sait_batch_autotune(ctx, n, dev(ptr))
+    assert rep.ncand == 5 and rep.tile_rows[rep.chosen] in (512, 1024, 2048, 4096, 8192)
+    assert rep.us[rep.chosen] == min(rep.us[i] for i in range(rep.ncand))
+    L, U = sg.sait_ilu0(ctx, A.n, dev(A.rp), dev(A.ci), dev(A.va))
+    P = sg.sait_prec_create_sait(ctx, sg.sait_build(ctx, L, True, 3, "rowrel", 1e-3),
+                                 sg.sait_build(ctx, U, False, 3, "rowrel", 1e-3))
+    Am = sg.sait_mat_create_csr(ctx, A.n, dev(A.rp), dev(A.ci), dev(A.va))
+    for tile in (rep.tile_rows[rep.chosen], 32):  # the tuned tile and a tiny one give the same answers
+        sg.sait_ctx_set_batch_tile(ctx, tile)
+        x, info, st, rr, its = sg.sait_bicgstab_batched(ctx, Am, P, dev(ptr), dev(b), tol=1e-10, maxit=2000)
+        assert st == 0 and info.converged == len(systems) and info.max_rel_resid <= 1e-10
+        xr = x.cpu().numpy()
+        for s in range(len(systems)):
+            sl = slice(ptr[s], ptr[s + 1])
+            r = b[sl] - oracle_lib.spmv(systems[s], xr[sl])
+            assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b[sl]) * 1.0001
+    sg.sait_ctx_set_batch_tile(ctx, 2048)
+    with pytest.raises(sg.SaitError) as e:
+        sg.sait_ctx_set_batch_tile(ctx, 8)
+    assert e.value.status == 1
