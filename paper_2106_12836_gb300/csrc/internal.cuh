@@ -148,6 +148,56 @@ struct DTemp {
 
 __host__ __device__ static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Double-float arithmetic on the FP32 pipe.  GB300 runs FP64 at 1/53 of its
+// FP32 rate, so long FP64 reductions and block products carry ~48-bit values
+// as (hi, lo) FP32 pairs instead, with error-free transformations.
+//
+// Knuth's two-sum of (S, p) into S plus the rounding error added to E; the
+// _rn intrinsics keep the compiler from contracting the error-free steps.
+__device__ __forceinline__ void df_add(float &S, float &E, float p, float e) {
+    const float sn = __fadd_rn(S, p);
+    const float bb = __fsub_rn(sn, S);
+    const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(sn, bb)), __fsub_rn(p, bb));
+    S = sn;
+    E = __fadd_rn(E, __fadd_rn(err, e));
+}
+
+// one double-float product term (vh + vl)(a + al), without the lo*lo part
+__device__ __forceinline__ void df_term(float &S, float &E, float vh, float vl, float a, float al) {
+    const float p = __fmul_rn(vh, a);
+    float e = __fmaf_rn(vh, a, -p);
+    e = __fmaf_rn(vh, al, e);
+    e = __fmaf_rn(vl, a, e);
+    df_add(S, E, p, e);
+}
+
+// (hi, lo) with hi = v truncated to 24 significant bits and lo = fl32(v - hi),
+// taken from the IEEE-754 fields with integer operations and one int->float
+// conversion, so no FP64 instruction is spent (conversions from FP64 share
+// GB300's narrow FP64 pipe).  |lo| < 2^-23 |hi| and |v - hi - lo| <=
+// 2^-47 |v|.  Values whose hi or lo would leave the FP32 normal range
+// (|v| < 2^-75 or |v| >= 2^128) take the conversion path.
+__device__ __forceinline__ void split_pair(double v, float &hi, float &lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ff);
+    const int ef = e - 896;  // FP32 biased exponent of hi (1023 - 127 = 896)
+    const int es = e - 948;  // FP32 biased exponent of 2^(e - 1075), the weight of the low fraction bits
+    if (es <= 0 || ef >= 255) {
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+        return;
+    }
+    const unsigned sign = (unsigned)(b >> 63) << 31;
+    const unsigned long long frac = b & ((1ULL << 52) - 1);
+    hi = __uint_as_float(sign | ((unsigned)ef << 23) | (unsigned)(frac >> 29));
+    const float r = __uint2float_rn((unsigned)(frac & ((1u << 29) - 1)));
+    const float m = r * __uint_as_float((unsigned)es << 23);
+    lo = sign ? -m : m;
+}
+
+// S + E as an FP64 value
+__device__ __forceinline__ double df_value(float S, float E) { return (double)S + (double)E; }
+
 // Exact widening of stored FP32 / BF16 values to FP64 (a hardware
 // conversion; integer bit assembly measured slower on GB300).
 __device__ __forceinline__ double widen(float f) { return (double)f; }

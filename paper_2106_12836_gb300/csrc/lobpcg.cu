@@ -11,7 +11,9 @@
 //   dense solve: Cholesky of G_B, C = L^{-1} G_A L^{-T}, parallel cyclic
 //   Jacobi, coefficients L^{-T} Y(:, 0:k)
 //   X = S c, A X = (A S) c, P = [W P] c(k:, :), A P likewise.
-// The Rayleigh-Ritz step and all block products run in FP64 on the device.
+// The Gram matrices and block products keep ~48-bit accuracy in double-float
+// arithmetic on the FP32 pipe (GB300's FP64 rate would bound them otherwise);
+// the Rayleigh-Ritz solve itself runs in FP64 on the device.
 #include <algorithm>
 #include <cmath>
 
@@ -24,79 +26,133 @@ constexpr int kMaxK = 20;           // block size limit (the Gram kernel holds <
 constexpr int kMaxM = 3 * kMaxK;    // Rayleigh-Ritz size limit
 constexpr int kRows = 32;           // rows per shared-memory tile of the Gram kernel
 
-// partial[b][a*q + c] = sum over block b's rows of Y[i, a] Z[i, c]
+// partial[b][a*q + c] = sum over block b's rows of Y[i, a] Z[i, c], in
+// double-float: the rows are staged in shared memory as (hi, lo) FP32 pairs
+// and every product is accumulated with error-free two-sums, so the Gram
+// entries keep ~48-bit accuracy while running on the FP32 pipe (FP64 FMAs
+// would bound this kernel on GB300).  Each thread owns a 4 x 4 tile of
+// outputs (16-byte shared loads, four products per loaded value) for one
+// residue class of the staged rows; SYM forms only the tiles on or above the
+// diagonal (the reduction mirrors them).  Phases are summed in a fixed order.
+constexpr int kGramSmem = 32 * 1024;  // bytes of dynamic shared memory of k_gram
+
+__device__ __forceinline__ float comp(const float4 &v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+
+template <bool SYM>
 __global__ void __launch_bounds__(kT)
 k_gram(int64_t n, int p, const double *__restrict__ Y, int64_t ldy, int q, const double *__restrict__ Z,
        int64_t ldz, double *partial) {
-    extern __shared__ double sm[];
-    double *ys = sm;                  // kRows x p
-    double *zs = sm + kRows * p;      // kRows x q
-    const int pq = p * q;
-    double acc[16];
-    const int per = (pq + kT - 1) / kT;  // <= 9 for 48 x 48, <= 15 for 60 x 60
+    extern __shared__ float4 smf4[];
+    const int p4 = (p + 3) / 4, q4 = (q + 3) / 4;
+    float4 *yh = smf4, *yl = yh + kRows * p4, *zh = yl + kRows * p4, *zl = zh + kRows * q4;
+    const int nmt = SYM ? p4 * (p4 + 1) / 2 : p4 * q4;
+    const int nph = kT / nmt;
+    const int mt = threadIdx.x % nmt, ph = threadIdx.x / nmt;
+    const bool active = ph < nph;
+    int ta = 0, tc = 0;
+    if (SYM) {
+        int rem = mt;
+        while (rem >= p4 - ta) {
+            rem -= p4 - ta;
+            ta++;
+        }
+        tc = ta + rem;
+    } else {
+        ta = mt / q4;
+        tc = mt % q4;
+    }
+    float S[16], E[16];
 #pragma unroll
-    for (int t = 0; t < 16; t++) acc[t] = 0.0;
+    for (int t = 0; t < 16; t++) S[t] = E[t] = 0.0f;
+    float *yhf = (float *)yh, *ylf = (float *)yl, *zhf = (float *)zh, *zlf = (float *)zl;
     for (int64_t r0 = (int64_t)blockIdx.x * kRows; r0 < n; r0 += (int64_t)gridDim.x * kRows) {
         const int rows = (int)min((int64_t)kRows, n - r0);
-        for (int e = threadIdx.x; e < kRows * p; e += kT) {
-            const int r = e / p, a = e % p;
-            ys[e] = r < rows ? Y[(r0 + r) * ldy + a] : 0.0;
+        for (int e = threadIdx.x; e < kRows * p4 * 4; e += kT) {
+            const int r = e / (p4 * 4), a = e % (p4 * 4);
+            split_pair(r < rows && a < p ? Y[(r0 + r) * ldy + a] : 0.0, yhf[e], ylf[e]);
         }
-        for (int e = threadIdx.x; e < kRows * q; e += kT) {
-            const int r = e / q, c = e % q;
-            zs[e] = r < rows ? Z[(r0 + r) * ldz + c] : 0.0;
+        for (int e = threadIdx.x; e < kRows * q4 * 4; e += kT) {
+            const int r = e / (q4 * 4), c = e % (q4 * 4);
+            split_pair(r < rows && c < q ? Z[(r0 + r) * ldz + c] : 0.0, zhf[e], zlf[e]);
         }
         __syncthreads();
-        for (int t = 0; t < per && t < 16; t++) {
-            const int o = threadIdx.x + t * kT;
-            if (o < pq) {
-                const int a = o / q, c = o % q;
-                double s = acc[t];
-                for (int r = 0; r < kRows; r++) s = fma(ys[r * p + a], zs[r * q + c], s);
-                acc[t] = s;
+        if (active) {
+            for (int r = ph; r < kRows; r += nph) {
+                const float4 ah = yh[r * p4 + ta], al = yl[r * p4 + ta];
+                const float4 bh = zh[r * q4 + tc], bl = zl[r * q4 + tc];
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++)
+                        df_term(S[i * 4 + j], E[i * 4 + j], comp(ah, i), comp(al, i), comp(bh, j), comp(bl, j));
             }
         }
         __syncthreads();
     }
-    for (int t = 0; t < per && t < 16; t++) {
-        const int o = threadIdx.x + t * kT;
-        if (o < pq) partial[(int64_t)blockIdx.x * pq + o] = acc[t];
+    double *red = (double *)smf4;  // nph x nmt x 16
+    if (active)
+#pragma unroll
+        for (int t = 0; t < 16; t++) red[((int64_t)ph * nmt + mt) * 16 + t] = df_value(S[t], E[t]);
+    __syncthreads();
+    const int pq = p * q;
+    for (int o = threadIdx.x; o < pq; o += kT) {
+        const int a = o / q, c = o % q;
+        double v = 0.0;
+        if (!SYM || a <= c) {
+            const int xa = a / 4, xc = c / 4;
+            const int m2 = SYM ? xa * p4 - xa * (xa - 1) / 2 + (xc - xa) : xa * q4 + xc;
+            const int t = (a % 4) * 4 + (c % 4);
+            for (int f = 0; f < nph; f++) v += red[((int64_t)f * nmt + m2) * 16 + t];
+        }
+        partial[(int64_t)blockIdx.x * pq + o] = v;
     }
 }
 
-// G[o] = sum_b partial[b][o]
-__global__ void k_gram_reduce(int nb, int pq, const double *__restrict__ partial, double *G) {
+// G[o] = sum_b partial[b][o] (FP64, fixed order); sym: G[a][c] = G[c][a] for a > c
+__global__ void k_gram_reduce(int nb, int p, int q, int sym, const double *__restrict__ partial, double *G) {
+    const int pq = p * q;
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= pq) return;
+    const int a = o / q, c = o % q;
+    const int src = (sym && a > c) ? c * q + a : o;
     double s = 0.0;
-    for (int b = 0; b < nb; b++) s += partial[(int64_t)b * pq + o];
+    for (int b = 0; b < nb; b++) s += partial[(int64_t)b * pq + src];
     G[o] = s;
 }
 
-// Y (n x p, ldy) = (beta ? Y : 0) + sign * Z (n x q, ldz) C (q x p, row-major, ldc)
+// Y (n x p, ldy) = (accumulate ? Y : 0) + sign * Z (n x q, ldz) C (q x p, row-major, ldc),
+// each output accumulated in double-float on the FP32 pipe (C staged as
+// (hi, lo) pairs, Z split on load) and rounded to FP64 once
 __global__ void __launch_bounds__(kT)
 k_block_mul(int64_t n, int q, const double *__restrict__ Z, int64_t ldz, int p, const double *__restrict__ C,
             int ldc, double *Y, int64_t ldy, int accumulate, double sign) {
-    __shared__ double cs[kMaxM * 16];
+    __shared__ float ch[kMaxM * 16], cl[kMaxM * 16];
     const int c0 = blockIdx.y * 16;  // output columns c0 .. c0+15
     const int pc = min(16, p - c0);
     for (int e = threadIdx.x; e < q * 16; e += kT) {
         const int a = e / 16, b = e % 16;
-        cs[e] = b < pc ? C[a * ldc + c0 + b] : 0.0;
+        split_pair(b < pc ? C[a * ldc + c0 + b] : 0.0, ch[e], cl[e]);
     }
     __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
-        double acc[16];
+        float S[16], E[16];
 #pragma unroll
-        for (int b = 0; b < 16; b++) acc[b] = 0.0;
+        for (int b = 0; b < 16; b++) S[b] = E[b] = 0.0f;
         const double *zr = Z + i * ldz;
         for (int a = 0; a < q; a++) {
-            const double z = zr[a];
+            float zh, zl;
+            split_pair(zr[a], zh, zl);
 #pragma unroll
-            for (int b = 0; b < 16; b++) acc[b] = fma(z, cs[a * 16 + b], acc[b]);
+            for (int b = 0; b < 16; b++) df_term(S[b], E[b], zh, zl, ch[a * 16 + b], cl[a * 16 + b]);
         }
         double *yr = Y + i * ldy + c0;
-        for (int b = 0; b < pc; b++) yr[b] = accumulate ? yr[b] + sign * acc[b] : sign * acc[b];
+#pragma unroll
+        for (int b = 0; b < 16; b++) {
+            if (b < pc) {
+                const double v = df_value(S[b], E[b]);
+                yr[b] = accumulate ? yr[b] + sign * v : sign * v;
+            }
+        }
     }
 }
 
@@ -108,6 +164,33 @@ __global__ void k_gather_cols(int64_t n, int cnt, const int *__restrict__ idx, c
         const int64_t i = e / cnt;
         const int t = (int)(e % cnt);
         Y[i * ldy + dst_off + t] = Z[i * ldz + idx[t]];
+    }
+}
+
+// S = [X W P], AS = [AX AW AP] (row-major n x m, m = k + na + np) in one pass:
+// strided 2D copies of 16-column blocks run row by row on the copy engines
+// and cost milliseconds at this shape
+__global__ void k_assemble(int64_t n, int k, int na, int np, const double *__restrict__ X,
+                           const double *__restrict__ W, const double *__restrict__ P, const double *__restrict__ AX,
+                           const double *__restrict__ AW, const double *__restrict__ AP, double *S, double *AS) {
+    const int m = k + na + np;
+    const int64_t tot = n * m;
+    for (int64_t e = (int64_t)blockIdx.x * kT + threadIdx.x; e < tot; e += (int64_t)gridDim.x * kT) {
+        const int64_t i = e / m;
+        const int t = (int)(e - i * m);
+        double a, b;
+        if (t < k) {
+            a = X[i * k + t];
+            b = AX[i * k + t];
+        } else if (t < k + na) {
+            a = W[i * na + t - k];
+            b = AW[i * na + t - k];
+        } else {
+            a = P[i * np + t - k - na];
+            b = AP[i * np + t - k - na];
+        }
+        S[e] = a;
+        AS[e] = b;
     }
 }
 
@@ -297,13 +380,22 @@ __global__ void __launch_bounds__(kT) k_rayleigh_ritz(int m, int k, const double
     for (int e = threadIdx.x; e < me * me; e += kT) V[e] = (e / me == e % me) ? 1.0 : 0.0;
     __syncthreads();
     const int np = me / 2;
+    // a pair whose off-diagonal entry is already below thr cannot matter at the
+    // stopping level (offn <= 1e-15 fro) and is not rotated: in the later
+    // sweeps most pairs are skipped, which saves the FP64 rotation work
+    const double thr = 1e-17 * fro / me;
+    __shared__ double opart[kT / 32];
     for (int sweep = 0; sweep < 40; sweep++) {
+        double o = 0.0;
+        for (int e = threadIdx.x; e < me * me; e += kT)
+            if (e / me != e % me) o += C[e] * C[e];
+        for (int d = 16; d > 0; d >>= 1) o += __shfl_xor_sync(0xffffffffu, o, d);
+        if ((threadIdx.x & 31) == 0) opart[threadIdx.x >> 5] = o;
+        __syncthreads();
         if (threadIdx.x == 0) {
-            double o = 0.0;
-            for (int a = 0; a < me; a++)
-                for (int b = 0; b < me; b++)
-                    if (a != b) o += C[a * me + b] * C[a * me + b];
-            offn = sqrt(o);
+            double t = 0.0;
+            for (int w = 0; w < kT / 32; w++) t += opart[w];
+            offn = sqrt(t);
         }
         __syncthreads();
         if (offn <= 1e-15 * fro || fro == 0.0) break;
@@ -318,7 +410,7 @@ __global__ void __launch_bounds__(kT) k_rayleigh_ritz(int m, int k, const double
                 pr[2 * t + 1] = hi;
                 const double apq = C[lo * me + hi];
                 double c = 1.0, s = 0.0;
-                if (apq != 0.0) {  // symmetric 2x2 Schur decomposition
+                if (fabs(apq) > thr) {  // symmetric 2x2 Schur decomposition
                     const double tau = (C[hi * me + hi] - C[lo * me + lo]) / (2.0 * apq);
                     const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
                     c = 1.0 / sqrt(1.0 + tt * tt);
@@ -332,6 +424,7 @@ __global__ void __launch_bounds__(kT) k_rayleigh_ritz(int m, int k, const double
                 const int t = e / me, r = e % me;
                 const int p = pr[2 * t], q = pr[2 * t + 1];
                 const double c = rot[2 * t], s = rot[2 * t + 1];
+                if (s == 0.0) continue;
                 double a = C[r * me + p], b = C[r * me + q];
                 C[r * me + p] = c * a - s * b;
                 C[r * me + q] = s * a + c * b;
@@ -345,6 +438,7 @@ __global__ void __launch_bounds__(kT) k_rayleigh_ritz(int m, int k, const double
                 const int t = e / me, r = e % me;
                 const int p = pr[2 * t], q = pr[2 * t + 1];
                 const double c = rot[2 * t], s = rot[2 * t + 1];
+                if (s == 0.0) continue;
                 const double a = C[p * me + r], b = C[q * me + r];
                 C[p * me + r] = c * a - s * b;
                 C[q * me + r] = s * a + c * b;
@@ -381,11 +475,16 @@ struct LWork {
     DTemp<int> flag, active, nact;
 };
 
+// G = Y^T Z (p x q); sym when the result is known to be symmetric (Y^T Y, S^T A S)
 sait_status gram(sait_ctx ctx, LWork &w, int64_t n, const double *Y, int p, int64_t ldy, const double *Z, int q,
-                 int64_t ldz, double *G) {
-    const size_t smem = (size_t)kRows * (p + q) * sizeof(double);
-    launch_k(k_gram, (unsigned)w.nb, kT, smem, ctx->stream, n, p, Y, ldy, q, Z, ldz, w.partial.p);
-    launch_k(k_gram_reduce, (unsigned)cdiv(p * q, 256), 256, 0, ctx->stream, w.nb, p * q,
+                 int64_t ldz, double *G, bool sym = false) {
+    if (sym && p == q)
+        launch_k(k_gram<true>, (unsigned)w.nb, kT, (size_t)kGramSmem, ctx->stream, n, p, Y, ldy, q, Z, ldz,
+                 w.partial.p);
+    else
+        launch_k(k_gram<false>, (unsigned)w.nb, kT, (size_t)kGramSmem, ctx->stream, n, p, Y, ldy, q, Z, ldz,
+                 w.partial.p);
+    launch_k(k_gram_reduce, (unsigned)cdiv(p * q, 256), 256, 0, ctx->stream, w.nb, p, q, (int)(sym && p == q),
              (const double *)w.partial.p, G);
     SAIT_CK(cudaGetLastError());
     return SAIT_OK;
@@ -402,7 +501,7 @@ sait_status bmul(sait_ctx ctx, int64_t n, const double *Z, int q, int64_t ldz, c
 
 // Y (n x p) <- Y L^{-T}, AY likewise when given; returns 1 in *failed if singular
 sait_status cholqr(sait_ctx ctx, LWork &w, int64_t n, double *Y, double *AY, int p, double *tmp, int *failed) {
-    SAIT_TRY(gram(ctx, w, n, Y, p, p, Y, p, p, w.G.p));
+    SAIT_TRY(gram(ctx, w, n, Y, p, p, Y, p, p, w.G.p, true));
     launch_k(k_cholqr_factor, 1, kT, (size_t)2 * p * p * sizeof(double), ctx->stream, p, (const double *)w.G.p,
              w.F.p, w.flag.p);
     SAIT_CK(cudaGetLastError());
@@ -455,16 +554,16 @@ extern "C" sait_status sait_lobpcg(sait_ctx ctx, sait_mat A, sait_prec P, int32_
     const size_t rr_smem = (size_t)(2 * mmax * mmax + 3 * (mmax + 1) * (mmax + 1)) * sizeof(double) +
                            (size_t)(mmax + 2) * sizeof(double) + (size_t)(mmax + 2) * sizeof(int) + 64;
     SAIT_CK(cudaFuncSetAttribute(k_rayleigh_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rr_smem));
-    SAIT_CK(cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(kRows * 2 * mmax * sizeof(double))));
+    SAIT_CK(cudaFuncSetAttribute(k_gram<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGramSmem));
+    SAIT_CK(cudaFuncSetAttribute(k_gram<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGramSmem));
     auto spmm_a = [&](const double *Z, int p, double *Y) -> sait_status {
         ScopedTimer tm(ctx, SAIT_TIMER_SPMV);
         SAIT_CK(launch_spmm(A, SAIT_F64, p, p, p, Z, false, Y, false, s, group_counter(ctx, SAIT_TIMER_SPMV)));
         return SAIT_OK;
     };
     auto rayleigh_ritz = [&](int m, const double *Sp, const double *ASp, int *failed) -> sait_status {
-        SAIT_TRY(gram(ctx, w, n, Sp, m, m, ASp, m, m, w.G.p));
-        SAIT_TRY(gram(ctx, w, n, Sp, m, m, Sp, m, m, w.G2.p));
+        SAIT_TRY(gram(ctx, w, n, Sp, m, m, ASp, m, m, w.G.p, true));   // A symmetric
+        SAIT_TRY(gram(ctx, w, n, Sp, m, m, Sp, m, m, w.G2.p, true));
         launch_k(k_rayleigh_ritz, 1, kT, rr_smem, s, m, (int)k, (const double *)w.G.p, (const double *)w.G2.p,
                  w.theta.p, w.coef.p, w.flag.p);
         SAIT_CK(cudaGetLastError());
@@ -529,21 +628,11 @@ extern "C" sait_status sait_lobpcg(sait_ctx ctx, sait_mat A, sait_prec P, int32_
         bool done = false;
         for (int attempt = 0; attempt < 2 && !done; attempt++) {
             const int m = k + na + np;
-            // S = [X W P], AS = [AX AW AP] (row-major n x m): column gathers by copies
-            SAIT_CK(cudaMemcpy2DAsync(S.p, m * sizeof(double), X, k * sizeof(double), k * sizeof(double), n,
-                                      cudaMemcpyDeviceToDevice, s));
-            SAIT_CK(cudaMemcpy2DAsync(S.p + k, m * sizeof(double), W.p, na * sizeof(double), na * sizeof(double), n,
-                                      cudaMemcpyDeviceToDevice, s));
-            SAIT_CK(cudaMemcpy2DAsync(AS.p, m * sizeof(double), AX.p, k * sizeof(double), k * sizeof(double), n,
-                                      cudaMemcpyDeviceToDevice, s));
-            SAIT_CK(cudaMemcpy2DAsync(AS.p + k, m * sizeof(double), AW.p, na * sizeof(double), na * sizeof(double),
-                                      n, cudaMemcpyDeviceToDevice, s));
-            if (np) {
-                SAIT_CK(cudaMemcpy2DAsync(S.p + k + na, m * sizeof(double), Pb.p, np * sizeof(double),
-                                          np * sizeof(double), n, cudaMemcpyDeviceToDevice, s));
-                SAIT_CK(cudaMemcpy2DAsync(AS.p + k + na, m * sizeof(double), AP.p, np * sizeof(double),
-                                          np * sizeof(double), n, cudaMemcpyDeviceToDevice, s));
-            }
+            // S = [X W P], AS = [AX AW AP] (row-major n x m)
+            launch_k(k_assemble, (unsigned)std::min<int64_t>(cdiv(n * m, kT), (int64_t)ctx->num_sms * 16), kT, 0, s,
+                     n, (int)k, na, np, (const double *)X, (const double *)W.p, (const double *)Pb.p,
+                     (const double *)AX.p, (const double *)AW.p, (const double *)AP.p, S.p, AS.p);
+            SAIT_CK(cudaGetLastError());
             SAIT_TRY(rayleigh_ritz(m, S.p, AS.p, &failed));
             if (failed) {
                 if (np) { np = 0; continue; }  // drop P and retry
