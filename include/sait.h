@@ -75,9 +75,12 @@ typedef struct {
  *                  intermediate vector in the SAIT apply (fewest bytes; the
  *                  rounding depends on the input, so the apply is not exactly
  *                  linear -- restarted GMRES absorbs that, BiCGSTAB can stall);
- *   SAIT_F32_X64/BF16_X64  FP32 / BF16 values, FP64 arithmetic and FP64
- *                  intermediate (the rounded matrix applied exactly: a fixed
- *                  linear preconditioner, with the byte savings of the storage). */
+ *   SAIT_F32_X64/BF16_X64  FP32 / BF16 values and an FP64 intermediate;
+ *                  single-vector products are summed in double-float (~47
+ *                  significant bits, error-free two-sums on the FP32 pipe),
+ *                  block products in FP64: the rounded matrix applied to
+ *                  ~1e-14 relative, a fixed linear preconditioner with the
+ *                  byte savings of the storage. */
 typedef enum {
     SAIT_F64 = 0,
     SAIT_F32 = 1,
@@ -209,8 +212,8 @@ sait_status sait_build(sait_ctx ctx, sait_mat T, sait_uplo uplo, int32_t m_terms
 sait_status sait_spmv(sait_ctx ctx, sait_mat A, const double *x, double *y);
 
 /* SAIT preconditioner apply z = M_U (M_L r) (Section 3.1).  The intermediate
- * vector is FP64 when both matrices use FP64 arithmetic (SAIT_F64, *_X64),
- * otherwise FP32.  r and z must not overlap.  Enqueues only. */
+ * vector is FP64 when both matrices use FP64-accurate arithmetic (SAIT_F64,
+ * *_X64), otherwise FP32.  r and z must not overlap.  Enqueues only. */
 sait_status sait_apply(sait_ctx ctx, sait_mat ML, sait_mat MU, const double *r, double *z);
 
 /* Block products for many right-hand sides / block eigenvectors.  X, Y, R, Z

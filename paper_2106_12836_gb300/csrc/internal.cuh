@@ -171,18 +171,18 @@ __device__ __forceinline__ void df_term(float &S, float &E, float vh, float vl, 
     df_add(S, E, p, e);
 }
 
-// (hi, lo) with hi = v truncated to 24 significant bits and lo = fl32(v - hi),
-// taken from the IEEE-754 fields with integer operations and one int->float
-// conversion, so no FP64 instruction is spent (conversions from FP64 share
-// GB300's narrow FP64 pipe).  |lo| < 2^-23 |hi| and |v - hi - lo| <=
-// 2^-47 |v|.  Values whose hi or lo would leave the FP32 normal range
-// (|v| < 2^-75 or |v| >= 2^128) take the conversion path.
+// (hi, lo) with hi = v truncated to 24 significant bits and lo the next 23
+// bits of v, both taken from the IEEE-754 fields with integer operations and
+// one exact FP32 subtraction, so no FP64 or conversion instruction is spent
+// (conversions from FP64 share GB300's narrow FP64 pipe).  |lo| < 2^-23 |hi|
+// and |v - hi - lo| < 2^-46 |v|.  Values outside 2^-75 <= |v| < 2^128 take
+// the conversion path.
 __device__ __forceinline__ void split_pair(double v, float &hi, float &lo) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const int e = (int)((b >> 52) & 0x7ff);
     const int ef = e - 896;  // FP32 biased exponent of hi (1023 - 127 = 896)
-    const int es = e - 948;  // FP32 biased exponent of 2^(e - 1075), the weight of the low fraction bits
-    if (es <= 0 || ef >= 255) {
+    const int el = e - 919;  // FP32 biased exponent whose mantissa ulp weighs the fraction bits 6..28
+    if (e <= 948 || ef >= 255) {
         hi = (float)v;
         lo = (float)(v - (double)hi);
         return;
@@ -190,13 +190,46 @@ __device__ __forceinline__ void split_pair(double v, float &hi, float &lo) {
     const unsigned sign = (unsigned)(b >> 63) << 31;
     const unsigned long long frac = b & ((1ULL << 52) - 1);
     hi = __uint_as_float(sign | ((unsigned)ef << 23) | (unsigned)(frac >> 29));
-    const float r = __uint2float_rn((unsigned)(frac & ((1u << 29) - 1)));
-    const float m = r * __uint_as_float((unsigned)es << 23);
-    lo = sign ? -m : m;
+    const unsigned base = (unsigned)el << 23;
+    const unsigned mid = (unsigned)(frac >> 6) & ((1u << 23) - 1);  // fraction bits 6..28
+    lo = __fsub_rn(__uint_as_float(sign | base | mid), __uint_as_float(sign | base));
 }
 
 // S + E as an FP64 value
 __device__ __forceinline__ double df_value(float S, float E) { return (double)S + (double)E; }
+
+// Double-float accumulator of the *_X64 storage modes: products of the rounded
+// (exact FP32) matrix values with FP64 or FP32 vector entries, summed with
+// error-free transformations, ~48 significant bits without FP64 instructions.
+struct DF {
+    float S = 0.0f, E = 0.0f;
+};
+__device__ __forceinline__ void mac(DF &acc, float v, double x) {
+    float xh, xl;
+    split_pair(x, xh, xl);
+    const float p = __fmul_rn(xh, v);
+    float e = __fmaf_rn(xh, v, -p);
+    e = __fmaf_rn(xl, v, e);
+    df_add(acc.S, acc.E, p, e);
+}
+__device__ __forceinline__ void mac(DF &acc, float v, float x) {
+    const float p = __fmul_rn(x, v);
+    df_add(acc.S, acc.E, p, __fmaf_rn(x, v, -p));
+}
+__device__ __forceinline__ void mac(double &acc, double v, double x) { acc = fma(v, x, acc); }
+__device__ __forceinline__ void mac(float &acc, float v, float x) { acc = fmaf(v, x, acc); }
+// b into a (both double-float partial sums)
+__device__ __forceinline__ void df_merge(DF &a, const DF &b) { df_add(a.S, a.E, b.S, b.E); }
+__device__ __forceinline__ double acc_value(const DF &a) { return df_value(a.S, a.E); }
+__device__ __forceinline__ double acc_value(double a) { return a; }
+__device__ __forceinline__ float acc_value(float a) { return a; }
+// vector entry as the multiplier type of accumulator A
+template <typename A, typename TX> struct XCast {
+    __device__ __forceinline__ static A get(TX x) { return (A)x; }
+};
+template <typename TX> struct XCast<DF, TX> {
+    __device__ __forceinline__ static TX get(TX x) { return x; }
+};
 
 // Exact widening of stored FP32 / BF16 values to FP64 (a hardware
 // conversion; integer bit assembly measured slower on GB300).
@@ -215,6 +248,12 @@ template <> struct Load<float, float> {
     __device__ __forceinline__ static float get(float v) { return v; }
 };
 template <> struct Load<float, __nv_bfloat16> {
+    __device__ __forceinline__ static float get(__nv_bfloat16 v) { return __bfloat162float(v); }
+};
+template <> struct Load<DF, float> {
+    __device__ __forceinline__ static float get(float v) { return v; }
+};
+template <> struct Load<DF, __nv_bfloat16> {
     __device__ __forceinline__ static float get(__nv_bfloat16 v) { return __bfloat162float(v); }
 };
 

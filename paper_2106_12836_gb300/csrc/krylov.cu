@@ -89,7 +89,7 @@ k_reduce(const double *__restrict__ partial, int nb, int stride, double *out, co
 // pipe (1.2 TFLOP/s measured, against 63.5 TFLOP/s FP32) would bound FP64
 // passes far below HBM speed, so no pass runs per-entry FP64 products.  The
 // basis is kept as V (FP64, the vectors the products read), and as the pair
-// (V_hi, V_lo) of FP32 arrays with V_hi = fl32(V), V_lo = fl32(V - V_hi):
+// (V_hi, V_lo) of FP32 arrays carrying V to ~2^-46 (split_pair):
 //   pass 1 dots   h1 = V^T w   FP32 products on V_hi;
 //   pass 1 update w -= V h1    double-float products on (V_hi, V_lo) and
 //                              (h_hi, h_lo), error-free two-sum accumulation

@@ -21,8 +21,6 @@ template <typename TV> struct Ahead { static constexpr int value = 8; };
 template <> struct Ahead<double> { static constexpr int value = 4; };
 
 
-__device__ __forceinline__ double fmac(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ float fmac(float a, float b, float c) { return fmaf(a, b, c); }
 
 // streaming loads: columns and values are read once per product
 __device__ __forceinline__ int32_t lds(const int32_t *p) { return __ldcs(p); }
@@ -48,32 +46,35 @@ k_spmv_sell(int64_t n, int64_t nslices, const int64_t *__restrict__ soff, const 
     const int len = (int)((soff[s + 1] - b) >> 5);
     const int32_t *c = ci + b + lane;
     const TV *v = va + b + lane;
-    A acc = 0;
+    using VT = decltype(Load<A, TV>::get(TV{}));
+    using XT = decltype(XCast<A, TX>::get(TX{}));
+    A acc{};
     int k = 0;
     for (; k + kU <= len; k += kU) {
         int32_t cc[kU];
-        A vv[kU], xx[kU];
+        VT vv[kU];
+        XT xx[kU];
 #pragma unroll
         for (int u = 0; u < kU; u++) {
             cc[u] = lds(c + 32 * u);
             vv[u] = Load<A, TV>::get(lds(v + 32 * u));
         }
 #pragma unroll
-        for (int u = 0; u < kU; u++) xx[u] = cc[u] >= 0 ? (A)__ldg(x + cc[u]) : (A)0;
+        for (int u = 0; u < kU; u++) xx[u] = cc[u] >= 0 ? XCast<A, TX>::get(__ldg(x + cc[u])) : (XT)0;
 #pragma unroll
-        for (int u = 0; u < kU; u++) acc = fmac(vv[u], xx[u], acc);
+        for (int u = 0; u < kU; u++) mac(acc, vv[u], xx[u]);
         c += 32 * kU;
         v += 32 * kU;
     }
     for (; k < len; k++) {
         const int32_t cc = lds(c);
-        const A vv = Load<A, TV>::get(lds(v));
-        if (cc >= 0) acc = fmac(vv, (A)__ldg(x + cc), acc);
+        const VT vv = Load<A, TV>::get(lds(v));
+        if (cc >= 0) mac(acc, vv, XCast<A, TX>::get(__ldg(x + cc)));
         c += 32;
         v += 32;
     }
     const int64_t row = s * 32 + lane;
-    if (row < n) y[row] = (TY)acc;
+    if (row < n) y[row] = (TY)acc_value(acc);
 }
 
 // slice lengths (in column slots) and the padded-entry count per slice
@@ -200,9 +201,9 @@ cudaError_t launch_spmv_sell(const sait_mat_s *A, sait_dtype store, const void *
     switch (store) {
         case SAIT_F32: return sell_xy<float, float>(A, A->sva32, x, x_f32, y, y_f32, active, s, calls);
         case SAIT_BF16: return sell_xy<__nv_bfloat16, float>(A, A->sva16, x, x_f32, y, y_f32, active, s, calls);
-        case SAIT_F32_X64: return sell_xy<float, double>(A, A->sva32, x, x_f32, y, y_f32, active, s, calls);
+        case SAIT_F32_X64: return sell_xy<float, DF>(A, A->sva32, x, x_f32, y, y_f32, active, s, calls);
         case SAIT_BF16_X64:
-            return sell_xy<__nv_bfloat16, double>(A, A->sva16, x, x_f32, y, y_f32, active, s, calls);
+            return sell_xy<__nv_bfloat16, DF>(A, A->sva16, x, x_f32, y, y_f32, active, s, calls);
         default: return sell_xy<double, double>(A, A->sva64, x, x_f32, y, y_f32, active, s, calls);
     }
 }

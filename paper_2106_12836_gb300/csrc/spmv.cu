@@ -6,13 +6,13 @@
 // is the matrix's storage precision: FP64 values accumulate in FP64, FP32 and
 // BF16 values in FP32 (the SAIT matrices approximate T^-1 anyway, so their
 // product precision can be reduced; Section 3.1).
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace {
 
 
-__device__ __forceinline__ double fmac(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ float fmac(float a, float b, float c) { return fmaf(a, b, c); }
 
 template <int G, typename TV, typename A, typename TX, typename TY>
 __global__ void __launch_bounds__(256)
@@ -24,14 +24,24 @@ k_spmv_csr(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict_
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t row = gid / G;
     const int lane = threadIdx.x & (G - 1);
-    A s = 0;
+    A s{};
     if (row < n) {
         const int b = rp[row], e = rp[row + 1];
-        for (int k = b + lane; k < e; k += G) s = fmac(Load<A, TV>::get(va[k]), (A)__ldg(x + ci[k]), s);
+        for (int k = b + lane; k < e; k += G) mac(s, Load<A, TV>::get(va[k]), XCast<A, TX>::get(__ldg(x + ci[k])));
     }
+    if constexpr (std::is_same<A, DF>::value) {
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (row < n && lane == 0) y[row] = (TY)s;
+        for (int o = G / 2; o > 0; o >>= 1) {
+            DF t;
+            t.S = __shfl_xor_sync(0xffffffffu, s.S, o);
+            t.E = __shfl_xor_sync(0xffffffffu, s.E, o);
+            df_merge(s, t);
+        }
+    } else {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    if (row < n && lane == 0) y[row] = (TY)acc_value(s);
 }
 
 template <typename TV, typename TA, typename TX, typename TY>
@@ -88,9 +98,9 @@ cudaError_t launch_spmv(const sait_mat_s *A, sait_dtype store, const void *x, bo
     switch (store) {
         case SAIT_F32: return launch_xy<float, float>(A, A->va32, x, x_f32, y, y_f32, active, s, calls);
         case SAIT_BF16: return launch_xy<__nv_bfloat16, float>(A, A->va16, x, x_f32, y, y_f32, active, s, calls);
-        case SAIT_F32_X64: return launch_xy<float, double>(A, A->va32, x, x_f32, y, y_f32, active, s, calls);
+        case SAIT_F32_X64: return launch_xy<float, DF>(A, A->va32, x, x_f32, y, y_f32, active, s, calls);
         case SAIT_BF16_X64:
-            return launch_xy<__nv_bfloat16, double>(A, A->va16, x, x_f32, y, y_f32, active, s, calls);
+            return launch_xy<__nv_bfloat16, DF>(A, A->va16, x, x_f32, y, y_f32, active, s, calls);
         default: return launch_xy<double, double>(A, A->va, x, x_f32, y, y_f32, active, s, calls);
     }
 }
