@@ -50,28 +50,25 @@ k_spmv_sell(int64_t n, int64_t nslices, const int64_t *__restrict__ soff, const 
     using XT = decltype(XCast<A, TX>::get(TX{}));
     A acc{};
     int k = 0;
-    for (; k + kU <= len; k += kU) {
+    // kU column slots per round, the last round predicated: every load of a
+    // round is issued before the first use, also for short rows
+    for (; k < len; k += kU) {
+        const int m = min(kU, len - k);
         int32_t cc[kU];
         VT vv[kU];
         XT xx[kU];
 #pragma unroll
         for (int u = 0; u < kU; u++) {
-            cc[u] = lds(c + 32 * u);
-            vv[u] = Load<A, TV>::get(lds(v + 32 * u));
+            cc[u] = u < m ? lds(c + 32 * u) : -1;
+            vv[u] = u < m ? Load<A, TV>::get(lds(v + 32 * u)) : (VT)0;
         }
 #pragma unroll
         for (int u = 0; u < kU; u++) xx[u] = cc[u] >= 0 ? XCast<A, TX>::get(__ldg(x + cc[u])) : (XT)0;
 #pragma unroll
-        for (int u = 0; u < kU; u++) mac(acc, vv[u], xx[u]);
+        for (int u = 0; u < kU; u++)
+            if (cc[u] >= 0) mac(acc, vv[u], xx[u]);
         c += 32 * kU;
         v += 32 * kU;
-    }
-    for (; k < len; k++) {
-        const int32_t cc = lds(c);
-        const VT vv = Load<A, TV>::get(lds(v));
-        if (cc >= 0) mac(acc, vv, XCast<A, TX>::get(__ldg(x + cc)));
-        c += 32;
-        v += 32;
     }
     const int64_t row = s * 32 + lane;
     if (row < n) y[row] = (TY)acc_value(acc);
