@@ -338,13 +338,11 @@ def ortho_bytes(n, iters, restart):
     while left > 0:
         steps = min(left, restart)
         for j in range(steps):
-            # mixed-precision CGS2 over the basis kept as FP32 pairs (hi, lo), j + 1 vectors:
-            #   pass-1 dots    read hi (4 B) and w (FP64)
-            #   pass-1 update  read hi + lo (8 B), read and write w, write fl32(w)
-            #   pass-2 dots    read hi (4 B) and fl32(w)
-            #   pass-2 update  read hi (4 B), read and write w (||w||^2 fused)
-            #   scaling        read w, write v (FP64), hi and lo
-            total += 20 * (j + 1) * n + (8 + 8 + 8 + 4 + 4 + 8 + 8 + 8 + 8 + 4 + 4) * n
+            # DCGS2 step j over the j final basis vectors kept as FP32 pairs (hi, lo):
+            #   dual dot sweep  read hi (4 B per vector), fl32(u) and w (FP64)
+            #   update sweep    read hi + lo (8 B per vector), read and write u and w (FP64),
+            #                   write v_j's hi and lo and fl32(w1')
+            total += 12 * j * n + (4 + 8 + 16 + 16 + 8 + 4) * n
         left -= steps
     return total
 
@@ -506,7 +504,7 @@ def run_ours(a):
         "apply": {"kernel": "k_spmv_sell x2 (M_L then M_U, SELL-32), one SAIT apply", "bound": "hbm",
                   "achieved": ab / apply_ms / 1e6, "bytes": ab, "ms": apply_ms,
                   "calls": stats["apply"]["calls"]},
-        "ortho": {"kernel": "GMRES CGS2 step (k_cgs_dot x2, k_cgs_update_df, k_cgs_update32, k_reduce x3, k_hadd x2, k_givens, k_scale3)",
+        "ortho": {"kernel": "GMRES DCGS2 step (k_dcgs_dot, k_reduce, k_dcgs_small, k_dcgs_update)",
                   "bound": "hbm", "achieved": ob / max(ortho_ms, 1e-9) / 1e6,
                   "bytes": ob / max(stats["ortho"]["calls"], 1), "ms": ortho_ms / max(stats["ortho"]["calls"], 1),
                   "calls": stats["ortho"]["calls"]},

@@ -85,207 +85,324 @@ k_reduce(const double *__restrict__ partial, int nb, int stride, double *out, co
     }
 }
 
-// Classical Gram-Schmidt with two passes, split by precision.  GB300's FP64
-// pipe (1.2 TFLOP/s measured, against 63.5 TFLOP/s FP32) would bound FP64
-// passes far below HBM speed, so no pass runs per-entry FP64 products.  The
-// basis is kept as V (FP64, the vectors the products read), and as the pair
-// (V_hi, V_lo) of FP32 arrays carrying V to ~2^-46 (split_pair):
-//   pass 1 dots   h1 = V^T w   FP32 products on V_hi;
-//   pass 1 update w -= V h1    double-float products on (V_hi, V_lo) and
-//                              (h_hi, h_lo), error-free two-sum accumulation
-//                              on the FP32 pipe, one FP64 subtraction per
-//                              entry (this subtraction cancels, so its error
-//                              must stay near FP64 level);
-//   pass 2 dots   h2 = V^T w   FP32 products on V_hi and fl32(w);
-//   pass 2 update w -= V h2    FP32 products on V_hi (h2 is ~1e-7 |w|),
-// and H(:, j) = h1 + h2 in FP64.  The updates keep the Arnoldi relation
-// A Z = V H at ~1e-14 relative; the FP32 dots leave the basis orthogonal to
-// ~1e-7, which does not move GMRES's residual estimate at the 1e-8 target.
+// Precision on GB300: its FP64 pipe (1.2 TFLOP/s measured, against 63.5
+// TFLOP/s FP32) would bound FP64 Gram-Schmidt passes far below HBM speed, so
+// the basis is kept both as V (FP64, the vectors the products read) and as a
+// pair (V_hi, V_lo) of FP32 arrays carrying V to ~2^-46 (split_pair): the
+// dots run in FP32 on V_hi, the updates in double-float on (V_hi, V_lo) with
+// error-free two-sums, and only one FP64 operation per entry and step remains.
 //
 // Layout: the basis columns have a leading dimension ldv = n rounded up to a
-// multiple of 4 with zero padding, so every kernel below moves 16-byte
-// vectors (four rows per thread) and never needs a ragged tail.
-//
-// Dots: partial[b*ldp + q] = sum over block b's rows of V_q . w (q < nvec).
-// One register accumulator per vector of a chunk; the last chunk is
-// instantiated for its exact size so no FMA slot is wasted.
-constexpr int kCH = 16;
-
-__device__ __forceinline__ float4 load_w4(const float4 *w, int64_t i4) { return w[i4]; }
+// multiple of 4 with zero padding, so the kernels below move 16-byte vectors
+// (four rows per thread) and never need a ragged tail.
 __device__ __forceinline__ float4 load_w4(const double2 *w, int64_t i4) {
     const double2 a = w[2 * i4], b = w[2 * i4 + 1];
     return make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
 }
 
-template <typename TW, int CH>
-__device__ __forceinline__ void dot_chunk(int64_t n4, const float4 *__restrict__ V, int64_t ldv4, int q0,
-                                          const TW *__restrict__ w, double *partial, int ldp,
-                                          double (*red)[kCH]) {
+// ---- GMRES with delayed reorthogonalization (DCGS2) --------------------------
+// Classical Gram-Schmidt twice, with the second pass of each Arnoldi vector
+// delayed to the next step (Bielich, Langou, Thomas, Swirydowicz, Yamazaki and
+// Boman, "Low-synch Gram-Schmidt with delayed reorthogonalization for Krylov
+// solvers", Parallel Computing 2022), written here for right-preconditioned
+// GMRES.  Step j holds the final orthonormal v_0 .. v_{j-1} and a tentative
+// u_j = w1 / eta (w1 stored unnormalized in column j, eta = ||w1||):
+//   w = A M w1                                (the SAIT apply and A product)
+//   one sweep:  c = V^T w1 / eta,  d = V^T w / eta,  delta = w1^T w / eta^2
+//   gamma = sqrt(1 - c.c);  v_j = (u_j - V c) / gamma     (u_j reorthogonalized)
+//   column j-1 becomes final: H(0:j-1, j-1) += eta c, H(j, j-1) = eta gamma
+//   A M v_j = (w/eta - V_{j+1} H c) / gamma, so its first-pass coefficients
+//   follow from d, delta and t = H c without another sweep, and
+//   one sweep:  v_j and the next tentative w1' = A M v_j - V_{j+1} h_j.
+// Two sweeps over the basis per step instead of four; the Givens rotation of a
+// column is applied once it is final, so convergence is seen one step later.
+// Precision as in the two-pass kernels above: dots in FP32 on V_hi, updates in
+// double-float on (V_hi, V_lo).
+constexpr int kDCH = 8;  // basis vectors per chunk of the dual dot sweep
+
+// partial[b*ldp + q] = V_q . U, partial[b*ldp + j + q] = V_q . W (q < j);
+// with DELTA also partial[b*ldp + 2j] = U . W (block b's rows)
+template <int CH, bool DELTA>
+__device__ __forceinline__ void dual_chunk(int64_t n4, const float4 *__restrict__ V, int64_t ldv4, int q0, int j,
+                                           const float4 *__restrict__ U, const double2 *__restrict__ W,
+                                           double *partial, int ldp, double (*red)[2 * kDCH + 1]) {
+    constexpr int NA = 2 * CH + (DELTA ? 1 : 0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float acc[CH > 0 ? CH : 1];
+    float au[CH > 0 ? CH : 1], aw[CH > 0 ? CH : 1], ad = 0.0f;
 #pragma unroll
-    for (int t = 0; t < (CH > 0 ? CH : 1); t++) acc[t] = 0.0f;
+    for (int t = 0; t < (CH > 0 ? CH : 1); t++) au[t] = aw[t] = 0.0f;
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kThreads) {
-        const float4 wv = load_w4(w, i);
+        const float4 u = U[i];
+        const float4 w = load_w4(W, i);
         float4 vv[CH > 0 ? CH : 1];
 #pragma unroll
         for (int t = 0; t < CH; t++) vv[t] = __ldg(V + (int64_t)(q0 + t) * ldv4 + i);
 #pragma unroll
         for (int t = 0; t < CH; t++) {
-            float a = fmaf(vv[t].x, wv.x, acc[t]);
-            a = fmaf(vv[t].y, wv.y, a);
-            a = fmaf(vv[t].z, wv.z, a);
-            acc[t] = fmaf(vv[t].w, wv.w, a);
+            float a = fmaf(vv[t].x, u.x, au[t]);
+            a = fmaf(vv[t].y, u.y, a);
+            a = fmaf(vv[t].z, u.z, a);
+            au[t] = fmaf(vv[t].w, u.w, a);
+            float b = fmaf(vv[t].x, w.x, aw[t]);
+            b = fmaf(vv[t].y, w.y, b);
+            b = fmaf(vv[t].z, w.z, b);
+            aw[t] = fmaf(vv[t].w, w.w, b);
+        }
+        if (DELTA) {
+            ad = fmaf(u.x, w.x, ad);
+            ad = fmaf(u.y, w.y, ad);
+            ad = fmaf(u.z, w.z, ad);
+            ad = fmaf(u.w, w.w, ad);
         }
     }
-    // warp sums in FP32 (the products are FP32 anyway; FP64 adds here would
-    // cost more than the whole sweep on GB300), then FP64 across warps/blocks
 #pragma unroll
-    for (int t = 0; t < CH; t++) {
-        float v = acc[t];
+    for (int t = 0; t < NA; t++) {
+        float v = t < CH ? au[t < CH ? t : 0] : t < 2 * CH ? aw[t >= CH && t < 2 * CH ? t - CH : 0] : ad;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) red[warp][t] = (double)v;
     }
     __syncthreads();
-    if ((int)threadIdx.x < CH) {
+    if ((int)threadIdx.x < NA) {
         double sum = 0.0;
         for (int w2 = 0; w2 < kThreads / 32; w2++) sum += red[w2][threadIdx.x];
-        partial[(int64_t)blockIdx.x * ldp + q0 + (int)threadIdx.x] = sum;
+        const int t = threadIdx.x;
+        const int slot = t < CH ? q0 + t : t < 2 * CH ? j + q0 + (t - CH) : 2 * j;
+        partial[(int64_t)blockIdx.x * ldp + slot] = sum;
     }
     __syncthreads();
 }
 
-template <typename TW>
-__device__ __forceinline__ void dot_tail(int rem, int64_t n4, const float4 *V, int64_t ldv4, int q0, const TW *w,
-                                         double *partial, int ldp, double (*red)[kCH]) {
+template <bool DELTA>
+__device__ __forceinline__ void dual_tail(int rem, int64_t n4, const float4 *V, int64_t ldv4, int q0, int j,
+                                          const float4 *U, const double2 *W, double *partial, int ldp,
+                                          double (*red)[2 * kDCH + 1]) {
     switch (rem) {
-#define SAIT_TAIL(k) case k: dot_chunk<TW, k>(n4, V, ldv4, q0, w, partial, ldp, red); break;
-        SAIT_TAIL(1) SAIT_TAIL(2) SAIT_TAIL(3) SAIT_TAIL(4) SAIT_TAIL(5) SAIT_TAIL(6) SAIT_TAIL(7)
-        SAIT_TAIL(8) SAIT_TAIL(9) SAIT_TAIL(10) SAIT_TAIL(11) SAIT_TAIL(12) SAIT_TAIL(13) SAIT_TAIL(14)
-        SAIT_TAIL(15)
-#undef SAIT_TAIL
+#define SAIT_DT(k) case k: dual_chunk<k, DELTA>(n4, V, ldv4, q0, j, U, W, partial, ldp, red); break;
+        SAIT_DT(0) SAIT_DT(1) SAIT_DT(2) SAIT_DT(3) SAIT_DT(4) SAIT_DT(5) SAIT_DT(6) SAIT_DT(7)
+#undef SAIT_DT
         default: break;
     }
 }
 
-// h = V^T w with FP32 products: TW = double2 (w in FP64, rounded on load) or float4
-template <typename TW>
 __global__ void __launch_bounds__(kThreads)
-k_cgs_dot(int64_t n4, const float4 *__restrict__ V, int64_t ldv4, int nvec, const TW *__restrict__ w,
-          double *partial, int ldp, const int *gate) {
+k_dcgs_dot(int64_t n4, const float4 *__restrict__ V, int64_t ldv4, int j, const float4 *__restrict__ U,
+           const double2 *__restrict__ W, double *partial, int ldp, const int *gate) {
     if (gate && *gate == 0) return;
-    __shared__ double red[kThreads / 32][kCH];
+    __shared__ double red[kThreads / 32][2 * kDCH + 1];
     int q0 = 0;
-    for (; nvec - q0 >= kCH; q0 += kCH) dot_chunk<TW, kCH>(n4, V, ldv4, q0, w, partial, ldp, red);
-    dot_tail<TW>(nvec - q0, n4, V, ldv4, q0, w, partial, ldp, red);
+    for (; j - q0 > kDCH; q0 += kDCH) dual_chunk<kDCH, false>(n4, V, ldv4, q0, j, U, W, partial, ldp, red);
+    if (j - q0 == kDCH) dual_chunk<kDCH, true>(n4, V, ldv4, q0, j, U, W, partial, ldp, red);
+    else dual_tail<true>(j - q0, n4, V, ldv4, q0, j, U, W, partial, ldp, red);
 }
 
-// Pass-1 update: w -= V h in double-float (see above), four rows per thread.
-// Writes w (FP64) and its FP32 rounding for the pass-2 dots.
-__global__ void __launch_bounds__(kThreads, 6)
-k_cgs_update_df(int64_t n4, const float4 *__restrict__ Vh, const float4 *__restrict__ Vl, int64_t ldv4, int nvec,
-                const double *__restrict__ h, double2 *w, float4 *w32, const int *gate) {
-    if (gate && *gate == 0) return;
-    __shared__ float hh[kMaxRestart + 1], hl[kMaxRestart + 1];
-    for (int q = threadIdx.x; q < nvec; q += kThreads) {
-        const double hd = h[q];
-        const float a = (float)hd;
-        hh[q] = a;
-        hl[q] = (float)(hd - (double)a);
+// Finalize column c of the raw Hessenberg Hr: copy it into R, apply the
+// previous rotations, form rotation c, update g; returns |g_{c+1}| (thread 0)
+__device__ double givens_column(int c, int m, const double *Hr, double *R, double *cs, double *sn, double *g,
+                                double *hc) {
+    const double *Hc = Hr + (int64_t)c * (m + 1);
+    double *Rc = R + (int64_t)c * (m + 1);
+    for (int i = threadIdx.x; i <= c + 1; i += kThreads) hc[i] = Hc[i];
+    __syncthreads();
+    double est = 0.0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < c; i++) {
+            const double t = cs[i] * hc[i] + sn[i] * hc[i + 1];
+            hc[i + 1] = -sn[i] * hc[i] + cs[i] * hc[i + 1];
+            hc[i] = t;
+        }
+        const double a = hc[c], b = hc[c + 1];
+        double cc = 1.0, ss = 0.0;
+        if (b != 0.0) {
+            const double t = hypot(a, b);
+            cc = a / t;
+            ss = b / t;
+        }
+        cs[c] = cc;
+        sn[c] = ss;
+        hc[c] = cc * a + ss * b;
+        hc[c + 1] = 0.0;
+        for (int i = 0; i <= c + 1; i++) Rc[i] = hc[i];
+        const double gc = g[c];
+        g[c + 1] = -ss * gc;
+        g[c] = cc * gc;
+        est = fabs(ss * gc);
     }
     __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kThreads) {
-        float S[4] = {0.0f, 0.0f, 0.0f, 0.0f}, E[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        int q = 0;
-        for (; q + 2 <= nvec; q += 2) {
-            const float4 h0 = __ldg(Vh + (int64_t)q * ldv4 + i), l0 = __ldg(Vl + (int64_t)q * ldv4 + i);
-            const float4 h1 = __ldg(Vh + (int64_t)(q + 1) * ldv4 + i), l1 = __ldg(Vl + (int64_t)(q + 1) * ldv4 + i);
-            const float a0 = hh[q], b0 = hl[q], a1 = hh[q + 1], b1 = hl[q + 1];
-            df_term(S[0], E[0], h0.x, l0.x, a0, b0);
-            df_term(S[1], E[1], h0.y, l0.y, a0, b0);
-            df_term(S[2], E[2], h0.z, l0.z, a0, b0);
-            df_term(S[3], E[3], h0.w, l0.w, a0, b0);
-            df_term(S[0], E[0], h1.x, l1.x, a1, b1);
-            df_term(S[1], E[1], h1.y, l1.y, a1, b1);
-            df_term(S[2], E[2], h1.z, l1.z, a1, b1);
-            df_term(S[3], E[3], h1.w, l1.w, a1, b1);
-        }
-        if (q < nvec) {
-            const float4 h0 = __ldg(Vh + (int64_t)q * ldv4 + i), l0 = __ldg(Vl + (int64_t)q * ldv4 + i);
-            const float a0 = hh[q], b0 = hl[q];
-            df_term(S[0], E[0], h0.x, l0.x, a0, b0);
-            df_term(S[1], E[1], h0.y, l0.y, a0, b0);
-            df_term(S[2], E[2], h0.z, l0.z, a0, b0);
-            df_term(S[3], E[3], h0.w, l0.w, a0, b0);
-        }
-        double2 wa = w[2 * i], wb = w[2 * i + 1];
-        wa.x -= (double)S[0] + (double)E[0];
-        wa.y -= (double)S[1] + (double)E[1];
-        wb.x -= (double)S[2] + (double)E[2];
-        wb.y -= (double)S[3] + (double)E[3];
-        w[2 * i] = wa;
-        w[2 * i + 1] = wb;
-        w32[i] = make_float4((float)wa.x, (float)wa.y, (float)wb.x, (float)wb.y);
-    }
+    return est;
 }
 
-// Pass-2 update: w -= V h with FP32 products on V_hi, four rows per thread;
-// partial[b] = ||w||^2 (FP64) of block b's rows.
+// One block.  dots = [c' (j), d' (j), delta'] (unscaled); partial/nb: the
+// squared norm of the tentative vector by blocks (j >= 1; eta = sc->beta at
+// j = 0).  close: only make column j-1 final (the end of a cycle).
+// Writes coef = [p (j), r (j)] and kk = [k1, k2, k3] for k_dcgs_update.
 __global__ void __launch_bounds__(kThreads)
-k_cgs_update32(int64_t n4, const float4 *__restrict__ V, int64_t ldv4, int nvec, const double *__restrict__ h,
-               double2 *w, double *partial, const int *gate) {
-    if (gate && *gate == 0) return;
-    __shared__ float hs[kMaxRestart + 1];
-    for (int q = threadIdx.x; q < nvec; q += kThreads) hs[q] = (float)h[q];
+k_dcgs_small(int j, int m, int remaining, int close, double *Hr, double *R, double *cs, double *sn, double *g,
+             Scal *sc, const double *__restrict__ dots, const double *__restrict__ partial, int nb, double *coef,
+             double *kk, int *calls) {
+    if (sc->active == 0) return;
+    __shared__ double c2[kMaxRestart + 1], dh[kMaxRestart + 1], t[kMaxRestart + 2], hc[kMaxRestart + 2];
+    __shared__ double sh_gamma, sh_eta;
+    double e2 = 0.0;
+    if (j >= 1)
+        for (int b = threadIdx.x; b < nb; b += kThreads) e2 += partial[b];
+    e2 = block_sum(e2);
+    if (threadIdx.x == 0) sh_eta = j >= 1 ? sqrt(e2) : sc->beta;
     __syncthreads();
+    const double eta = sh_eta;
+    if (!(eta > 0.0) || !isfinite(eta)) {  // invariant subspace (or a non-finite vector)
+        if (j >= 1) {
+            if (threadIdx.x == 0) Hr[(int64_t)(j - 1) * (m + 1) + j] = 0.0;
+            givens_column(j - 1, m, Hr, R, cs, sn, g, hc);
+        }
+        if (threadIdx.x == 0) {
+            if (calls) atomicAdd(calls, 1);
+            sc->jdone = j;
+            if (!isfinite(eta)) sc->state = 3;
+            sc->active = 0;
+        }
+        return;
+    }
+    const double ie = 1.0 / eta;
+    double cc = 0.0;
+    for (int q = threadIdx.x; q < j; q += kThreads) {
+        const double a = dots[q] * ie;
+        c2[q] = a;
+        dh[q] = dots[j + q] * ie;
+        cc += a * a;
+    }
+    cc = block_sum(cc);
+    if (threadIdx.x == 0) sh_gamma = sqrt(fmax(1.0 - cc, 0.0));
+    __syncthreads();
+    const double gamma = sh_gamma;
+    if (j >= 1) {  // column j-1 is final now
+        double *Hc = Hr + (int64_t)(j - 1) * (m + 1);
+        for (int q = threadIdx.x; q < j; q += kThreads) Hc[q] += eta * c2[q];
+        if (threadIdx.x == 0) Hc[j] = eta * gamma;
+        __syncthreads();
+        const double est = givens_column(j - 1, m, Hr, R, cs, sn, g, hc);
+        if (threadIdx.x == 0) {
+            if (calls) atomicAdd(calls, 1);
+            sc->jdone = j;
+            if (!isfinite(est)) {
+                sc->state = 3;
+                sc->active = 0;
+            } else if (est <= sc->tolb || j >= remaining || close || !(gamma > 0.0)) {
+                sc->active = 0;
+            }
+        }
+        __syncthreads();
+        if (sc->active == 0) return;
+    }
+    // t = H c over the final columns 0..j-1 (rows 0..j)
+    for (int i = threadIdx.x; i <= j; i += kThreads) {
+        double a = 0.0;
+        for (int k = (i > 0 ? i - 1 : 0); k < j; k++) a += Hr[(int64_t)k * (m + 1) + i] * c2[k];
+        t[i] = a;
+    }
+    double cd = 0.0;
+    for (int q = threadIdx.x; q < j; q += kThreads) cd += c2[q] * dh[q];
+    cd = block_sum(cd);
+    __syncthreads();
+    const double dl = dots[2 * j] * ie * ie;
+    const double ig = 1.0 / gamma;
+    // first-pass coefficients of A M v_j (tentative column j) and the update weights
+    double *Hj = Hr + (int64_t)j * (m + 1);
+    const double cj = ((dl - cd) * ig - t[j]) * ig;
+    const double av = t[j] + gamma * cj;
+    for (int q = threadIdx.x; q < j; q += kThreads) {
+        const double c1 = (dh[q] - t[q]) * ig;
+        Hj[q] = c1;
+        const double aV = t[q] + gamma * c1;
+        coef[q] = c2[q] * ig;                          // p
+        coef[j + q] = (aV - av * ig * c2[q]) * ig;     // r
+    }
+    if (threadIdx.x == 0) {
+        Hj[j] = cj;
+        kk[0] = ie * ig;            // v_j   = k1 w1 - V p
+        kk[1] = ie * ig;            // w1'   = k2 w - k3 w1 - V r
+        kk[2] = av * ie * ig * ig;
+    }
+}
+
+// v_j = k1 w1 - V p (written over w1 in column j, with its (hi, lo) pair) and
+// w1' = k2 w - k3 w1 - V r (written over w in column j + 1, with its FP32
+// copy for the next dual sweep); partial[b] = ||w1'||^2 of block b's rows.
+__global__ void __launch_bounds__(kThreads, 4)
+k_dcgs_update(int64_t n4, const float4 *__restrict__ Vh, const float4 *__restrict__ Vl, int64_t ldv4, int j,
+              const double *__restrict__ coef, const double *__restrict__ kk, double2 *wcol1, double2 *wcol,
+              float4 *vh_out, float4 *vl_out, float4 *w32, double *partial, const int *gate) {
+    if (gate && *gate == 0) return;
+    __shared__ float ph[kMaxRestart + 1], pl[kMaxRestart + 1], rh[kMaxRestart + 1], rl[kMaxRestart + 1];
+    for (int q = threadIdx.x; q < j; q += kThreads) {
+        split_pair(coef[q], ph[q], pl[q]);
+        split_pair(coef[j + q], rh[q], rl[q]);
+    }
+    __syncthreads();
+    const double k1 = kk[0], k2 = kk[1], k3 = kk[2];
     double nrm = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kThreads) {
-        float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;  // two chains per row
-        int q = 0;
-        for (; q + 2 <= nvec; q += 2) {
-            const float4 v0 = __ldg(V + (int64_t)q * ldv4 + i), v1 = __ldg(V + (int64_t)(q + 1) * ldv4 + i);
-            const float a0 = hs[q], a1 = hs[q + 1];
-            s0.x = fmaf(v0.x, a0, s0.x); s0.y = fmaf(v0.y, a0, s0.y);
-            s0.z = fmaf(v0.z, a0, s0.z); s0.w = fmaf(v0.w, a0, s0.w);
-            s1.x = fmaf(v1.x, a1, s1.x); s1.y = fmaf(v1.y, a1, s1.y);
-            s1.z = fmaf(v1.z, a1, s1.z); s1.w = fmaf(v1.w, a1, s1.w);
+        float S1[4] = {0.f, 0.f, 0.f, 0.f}, E1[4] = {0.f, 0.f, 0.f, 0.f};
+        float S2[4] = {0.f, 0.f, 0.f, 0.f}, E2[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int q = 0; q < j; q++) {
+            const float4 h = __ldg(Vh + (int64_t)q * ldv4 + i), l = __ldg(Vl + (int64_t)q * ldv4 + i);
+            const float a = ph[q], al = pl[q], b = rh[q], bl = rl[q];
+            df_term(S1[0], E1[0], h.x, l.x, a, al);
+            df_term(S1[1], E1[1], h.y, l.y, a, al);
+            df_term(S1[2], E1[2], h.z, l.z, a, al);
+            df_term(S1[3], E1[3], h.w, l.w, a, al);
+            df_term(S2[0], E2[0], h.x, l.x, b, bl);
+            df_term(S2[1], E2[1], h.y, l.y, b, bl);
+            df_term(S2[2], E2[2], h.z, l.z, b, bl);
+            df_term(S2[3], E2[3], h.w, l.w, b, bl);
         }
-        if (q < nvec) {
-            const float4 v0 = __ldg(V + (int64_t)q * ldv4 + i);
-            const float a0 = hs[q];
-            s0.x = fmaf(v0.x, a0, s0.x); s0.y = fmaf(v0.y, a0, s0.y);
-            s0.z = fmaf(v0.z, a0, s0.z); s0.w = fmaf(v0.w, a0, s0.w);
+        const double2 ua = wcol1[2 * i], ub = wcol1[2 * i + 1];
+        const double2 wa = wcol[2 * i], wb = wcol[2 * i + 1];
+        const double u[4] = {ua.x, ua.y, ub.x, ub.y}, w[4] = {wa.x, wa.y, wb.x, wb.y};
+        double v[4], x[4];
+        float vh[4], vl[4], xh[4], xl[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            v[r] = fma(k1, u[r], -df_value(S1[r], E1[r]));
+            x[r] = fma(k2, w[r], fma(-k3, u[r], -df_value(S2[r], E2[r])));
+            split_pair(v[r], vh[r], vl[r]);
+            split_pair(x[r], xh[r], xl[r]);
+            nrm = fma(x[r], x[r], nrm);
         }
-        double2 wa = w[2 * i], wb = w[2 * i + 1];
-        wa.x -= (double)(s0.x + s1.x);
-        wa.y -= (double)(s0.y + s1.y);
-        wb.x -= (double)(s0.z + s1.z);
-        wb.y -= (double)(s0.w + s1.w);
-        w[2 * i] = wa;
-        w[2 * i + 1] = wb;
-        nrm = fma(wa.x, wa.x, nrm);
-        nrm = fma(wa.y, wa.y, nrm);
-        nrm = fma(wb.x, wb.x, nrm);
-        nrm = fma(wb.y, wb.y, nrm);
+        wcol1[2 * i] = make_double2(v[0], v[1]);
+        wcol1[2 * i + 1] = make_double2(v[2], v[3]);
+        wcol[2 * i] = make_double2(x[0], x[1]);
+        wcol[2 * i + 1] = make_double2(x[2], x[3]);
+        vh_out[i] = make_float4(vh[0], vh[1], vh[2], vh[3]);
+        vl_out[i] = make_float4(vl[0], vl[1], vl[2], vl[3]);
+        w32[i] = make_float4(xh[0], xh[1], xh[2], xh[3]);
     }
     nrm = block_sum(nrm);
     if (threadIdx.x == 0) partial[blockIdx.x] = nrm;
 }
 
-// v = w / ||w|| in FP64 (rows < n), plus its FP32 pair (hi, lo)
-__global__ void k_scale3(int64_t n, const double *__restrict__ x, double *y, float *yh, float *yl, const Scal *sc,
-                         const int *active) {
-    if (active && *active == 0) return;
-    const double a = sc->inv;
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
-        const double v = x[i] * a;
-        float hi, lo;
-        split_pair(v, hi, lo);
-        y[i] = v;
-        yh[i] = hi;
-        yl[i] = lo;
+// FP32 copy (hi part) of an FP64 vector, four rows per thread
+__global__ void k_hi4(int64_t n4, const double2 *__restrict__ x, float4 *y) {
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kThreads) {
+        const double2 a = x[2 * i], b = x[2 * i + 1];
+        float h[4], l;
+        split_pair(a.x, h[0], l);
+        split_pair(a.y, h[1], l);
+        split_pair(b.x, h[2], l);
+        split_pair(b.y, h[3], l);
+        y[i] = make_float4(h[0], h[1], h[2], h[3]);
     }
+}
+
+// start of a cycle: eta = beta = ||r||, g = beta e_1
+__global__ void k_dcgs_start(Scal *sc, double *g, int m) {
+    const double beta = sqrt(sc->r0);
+    sc->beta = beta;
+    sc->active = 1;
+    sc->jdone = 0;
+    sc->state = 0;
+    g[0] = beta;
+    for (int i = 1; i <= m; i++) g[i] = 0.0;
 }
 
 // w -= V h (sub = true) or w = V h (sub = false); nvec from *nvec_dev if given.
@@ -326,71 +443,6 @@ __global__ void k_axpy1(int64_t n, const double *__restrict__ x, double *y) {
 }
 
 // ---- GMRES scalar kernels (one thread) -------------------------------------
-__global__ void k_gmres_start(Scal *sc, double *g, int m) {
-    const double beta = sqrt(sc->r0);
-    sc->beta = beta;
-    sc->inv = beta > 0.0 ? 1.0 / beta : 0.0;
-    sc->active = 1;
-    sc->jdone = 0;
-    sc->state = 0;
-    g[0] = beta;
-    for (int i = 1; i <= m; i++) g[i] = 0.0;
-}
-
-// sc->r0 = ||w||^2 from the update's per-block partials (fixed order), then
-// one thread applies the previous rotations to column j of H and forms the
-// new one.  The column and the rotations are staged in shared memory first:
-// the rotation chain is sequential, and global loads inside it would each
-// cost a full memory latency.
-__global__ void __launch_bounds__(kThreads)
-k_givens(int j, int m, int remaining, double *H, double *cs, double *sn, double *g, Scal *sc,
-         const double *__restrict__ partial, int nb, int *calls) {
-    if (sc->active == 0) return;
-    __shared__ double hc[kMaxRestart + 2], cc[kMaxRestart], ss[kMaxRestart];
-    double *Hj = H + (int64_t)j * (m + 1);
-    for (int i = threadIdx.x; i <= j; i += kThreads) hc[i] = Hj[i];
-    for (int i = threadIdx.x; i < j; i += kThreads) {
-        cc[i] = cs[i];
-        ss[i] = sn[i];
-    }
-    double t0 = 0.0;
-    for (int b = threadIdx.x; b < nb; b += kThreads) t0 += partial[b];
-    t0 = block_sum(t0);  // synchronizes the block
-    if (threadIdx.x != 0) return;
-    sc->r0 = t0;
-    if (calls) atomicAdd(calls, 1);
-    const double hn = sqrt(t0);
-    hc[j + 1] = hn;
-    for (int i = 0; i < j; i++) {
-        const double t = cc[i] * hc[i] + ss[i] * hc[i + 1];
-        hc[i + 1] = -ss[i] * hc[i] + cc[i] * hc[i + 1];
-        hc[i] = t;
-    }
-    const double a = hc[j], b = hn;
-    double c = 1.0, s = 0.0;
-    if (b != 0.0) {
-        const double t = hypot(a, b);
-        c = a / t;
-        s = b / t;
-    }
-    cs[j] = c;
-    sn[j] = s;
-    hc[j] = c * a + s * b;
-    hc[j + 1] = 0.0;
-    for (int i = 0; i <= j + 1; i++) Hj[i] = hc[i];
-    const double gj = g[j];
-    g[j + 1] = -s * gj;
-    g[j] = c * gj;
-    sc->jdone = j + 1;
-    sc->inv = hn != 0.0 ? 1.0 / hn : 0.0;
-    const double est = fabs(s * gj);
-    if (!isfinite(est) || !isfinite(hn)) {
-        sc->state = 3;
-        sc->active = 0;
-    } else if (est <= sc->tolb || hn == 0.0 || j + 1 >= remaining || j + 1 >= m) {
-        sc->active = 0;
-    }
-}
 
 // back substitution H y = g on the first jdone rows, column-oriented: once
 // y_i is known every thread removes its multiple from the rows above
@@ -645,7 +697,6 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
 
     Work W;
     W.nb = (int)std::min<int64_t>(cdiv(n, kThreads), 4LL * ctx->num_sms);
-    const int ldp = m + 2;
     DTemp<double> V, H, cs, sn, g, y, z, u, part, part2;
     DTemp<float> V32, VL, w32;  // the basis as FP32 (hi, lo) pairs; fl32(w) after pass 1
     DTemp<Scal> scd;
@@ -661,13 +712,19 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
         SAIT_CK(cudaMemsetAsync(w32.p + n, 0, (ldv - n) * sizeof(float), s));
     }
     SAIT_CK(H.alloc((size_t)(m + 1) * m, s));
+    DTemp<double> R, yd, coef, kk;
+    SAIT_CK(R.alloc((size_t)(m + 1) * m, s));
+    SAIT_CK(yd.alloc((size_t)2 * m + 2, s));
+    SAIT_CK(coef.alloc((size_t)2 * m + 2, s));
+    SAIT_CK(kk.alloc(4, s));
     SAIT_CK(cs.alloc(m, s));
     SAIT_CK(sn.alloc(m, s));
     SAIT_CK(g.alloc(m + 1, s));
     SAIT_CK(y.alloc(m + 2, s));
     SAIT_CK(z.alloc(n, s));
     SAIT_CK(u.alloc(n, s));
-    SAIT_CK(part.alloc((size_t)W.nb * std::max(ldp, 3), s));
+    const int ldp2 = 2 * m + 2;  // dual sweep: V^T u, V^T w, u . w
+    SAIT_CK(part.alloc((size_t)W.nb * std::max(ldp2, 3), s));
     const int nb_upd = (int)std::min<int64_t>(cdiv(n4, kThreads), 16LL * ctx->num_sms);
     const int nb_dot = (int)std::min<int64_t>(cdiv(n4, kThreads), (int64_t)W.nb);
     SAIT_CK(part2.alloc((size_t)std::max(W.nb, nb_upd), s));
@@ -706,60 +763,58 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
     const int poll = (P && P->kind == 2) ? 1 : kPoll;
     sait_status result = SAIT_ERR_NOT_CONVERGED;
     for (;;) {
-        // r = b - A x  -> V_0, beta = ||r||
+        // r = b - A x -> column 0 (the first tentative vector, eta = beta = ||r||)
         SAIT_CK(residual(ctx, A, x, b, V.p));
         SAIT_CK(dots(ctx, W, n, 1, V.p, V.p, nullptr, nullptr, nullptr, nullptr, r0, nullptr));
-        launch_k(k_gmres_start, 1, 1, 0, s, sc, g.p, m);
+        launch_k(k_dcgs_start, 1, 1, 0, s, sc, g.p, m);
         SAIT_CK(cudaGetLastError());
         SAIT_TRY(read_scal(ctx, sc, &hs));
         inf.rel_resid = hs.beta / bnorm;
         if (!std::isfinite(hs.beta)) { result = SAIT_ERR_NONFINITE; break; }
         if (inf.rel_resid <= tol) { result = SAIT_OK; break; }
         if (iters >= maxit) break;
-        launch_k(k_scale3, egrid, kThreads, 0, s, n, (const double *)V.p, V.p, V32.p, VL.p, (const Scal *)sc,
-                 nullptr);
+        launch_k(k_hi4, egrid, kThreads, 0, s, n4, (const double2 *)V.p, (float4 *)w32.p);
         const int remaining = maxit - iters;
+        const float4 *Vh4 = (const float4 *)V32.p, *Vl4 = (const float4 *)VL.p;
+        auto ortho = [&](int j, int close) {
+            double *wj = V.p + (size_t)j * ldv;
+            const double2 *wn = (const double2 *)(close ? wj : V.p + (size_t)(j + 1) * ldv);
+            ScopedTimer tm(ctx, SAIT_TIMER_ORTHO);
+            launch_k(k_dcgs_dot, nb_dot, kThreads, 0, s, n4, Vh4, n4, j, (const float4 *)w32.p, wn, W.partial,
+                     ldp2, act);
+            launch_k(k_reduce, 2 * j + 1, kThreads, 0, s, (const double *)W.partial, nb_dot, ldp2, yd.p, act,
+                     (double *)nullptr, 0);
+            launch_k(k_dcgs_small, 1, kThreads, 0, s, j, m, remaining, close, H.p, R.p, cs.p, sn.p, g.p, sc,
+                     (const double *)yd.p, (const double *)W.partial2, nb_upd, coef.p, kk.p,
+                     group_counter(ctx, SAIT_TIMER_ORTHO));
+            if (!close)
+                launch_k(k_dcgs_update, nb_upd, kThreads, 0, s, n4, Vh4, Vl4, n4, j, (const double *)coef.p,
+                         (const double *)kk.p, (double2 *)wj, (double2 *)(V.p + (size_t)(j + 1) * ldv),
+                         (float4 *)(V32.p + (size_t)j * ldv), (float4 *)(VL.p + (size_t)j * ldv), (float4 *)w32.p,
+                         W.partial2, act);
+        };
         for (int j = 0; j < m; j++) {
-            double *vj = V.p + (size_t)j * ldv, *w = V.p + (size_t)(j + 1) * ldv;
-            SAIT_TRY(precondition(ctx, P, vj, z.p, n, act));
+            double *wj = V.p + (size_t)j * ldv, *w = V.p + (size_t)(j + 1) * ldv;
+            SAIT_TRY(precondition(ctx, P, wj, z.p, n, act));
             {
                 ScopedTimer tm(ctx, SAIT_TIMER_SPMV);
                 SAIT_CK(launch_spmv(A, SAIT_F64, z.p, false, w, false, act, s,
                                     group_counter(ctx, SAIT_TIMER_SPMV)));
             }
-            {
-                ScopedTimer tm(ctx, SAIT_TIMER_ORTHO);
-                double *Hj = H.p + (size_t)j * (m + 1);
-                const int nv = j + 1;
-                const float4 *Vh4 = (const float4 *)V32.p, *Vl4 = (const float4 *)VL.p;
-                // pass 1: FP32 dots, double-float update
-                launch_k(k_cgs_dot<double2>, nb_dot, kThreads, 0, s, n4, Vh4, n4, nv, (const double2 *)w,
-                         W.partial, ldp, act);
-                launch_k(k_reduce, nv, kThreads, 0, s, (const double *)W.partial, nb_dot, ldp, y.p, act, Hj, 1);
-                launch_k(k_cgs_update_df, nb_upd, kThreads, 0, s, n4, Vh4, Vl4, n4, nv, (const double *)y.p,
-                         (double2 *)w, (float4 *)w32.p, act);
-                // pass 2: FP32 dots and update, ||w||^2
-                launch_k(k_cgs_dot<float4>, nb_dot, kThreads, 0, s, n4, Vh4, n4, nv, (const float4 *)w32.p,
-                         W.partial, ldp, act);
-                launch_k(k_reduce, nv, kThreads, 0, s, (const double *)W.partial, nb_dot, ldp, y.p, act, Hj, 0);
-                launch_k(k_cgs_update32, nb_upd, kThreads, 0, s, n4, Vh4, n4, nv, (const double *)y.p,
-                         (double2 *)w, W.partial2, act);
-                launch_k(k_givens, 1, kThreads, 0, s, j, m, remaining, H.p, cs.p, sn.p, g.p, sc,
-                         (const double *)W.partial2, nb_upd, group_counter(ctx, SAIT_TIMER_ORTHO));
-                launch_k(k_scale3, egrid, kThreads, 0, s, n, (const double *)w, w, V32.p + (size_t)(j + 1) * ldv,
-                         VL.p + (size_t)(j + 1) * ldv, (const Scal *)sc, act);
-            }
+            ortho(j, 0);
             SAIT_CK(cudaGetLastError());
             if ((j + 1) % poll == 0 || j + 1 == m) {
                 SAIT_TRY(read_scal(ctx, sc, &hs));
                 if (!hs.active) break;
             }
         }
+        ortho(m, 1);  // the last column becomes final (no-op after an earlier stop)
+        SAIT_CK(cudaGetLastError());
         SAIT_TRY(read_scal(ctx, sc, &hs));
         iters += hs.jdone;
         cycles++;
         if (hs.state == 3) { result = SAIT_ERR_NONFINITE; break; }
-        launch_k(k_hsolve, 1, kThreads, 0, s, H.p, g.p, y.p, m, sc);
+        launch_k(k_hsolve, 1, kThreads, 0, s, (const double *)R.p, (const double *)g.p, y.p, m, sc);
         launch_k(k_gemv, egrid, kThreads, 0, s, n, V.p, ldv, 0, &sc->jdone, y.p, u.p, 0, nullptr);
         SAIT_CK(cudaGetLastError());
         SAIT_TRY(precondition(ctx, P, u.p, z.p, n, nullptr));

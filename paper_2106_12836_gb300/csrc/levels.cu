@@ -92,72 +92,120 @@ __global__ void k_front_init(int *q, int32_t *lptr) {
     lptr[1] = q[2];
 }
 
-__global__ void k_front_advance(int *q, int32_t *lptr) {
-    q[0] = q[1];
-    q[1] = q[2];
-    if (q[1] > q[0]) {
-        q[3] += 1;
-        lptr[q[3]] = q[1];
-    }
-}
 
 // ILU(0), IKJ order (Saad, Algorithm 10.4), for row i whose dependencies are
-// final: for each k < i in row i (ascending) a_ik /= a_kk, then
-// a_ij -= a_ik a_kj for every j > k of row k that is also in row i's pattern.
-__device__ __forceinline__ void ilu0_row(int i, int lane, const int32_t *__restrict__ rp,
-                                         const int32_t *__restrict__ ci, const int32_t *__restrict__ dpos,
-                                         double *a, int *err) {
-    const int b = rp[i], e = rp[i + 1];
-    for (int q = b; q < e; q++) {
-        const int k = ci[q];
-        if (k >= i) break;
-        const double ukk = a[dpos[k]];
+// final, from precomputed update triples (q, f, p): for each L entry q of row
+// i (column k, ascending) a_iq /= a_kk, then a_p -= a_iq a_f for the entries
+// f of U row k (past its diagonal) that match position p of row i.  The
+// triples replace the pattern searches, so the chain of dependent loads per
+// row is short; the fma chain per entry is the IKJ one.
+__device__ __forceinline__ void ilu0_row_triples(int i, const int32_t *__restrict__ rp,
+                                                 const int32_t *__restrict__ dpos, const int32_t *__restrict__ ldiag,
+                                                 const int64_t *__restrict__ tp, const int3 *__restrict__ tr,
+                                                 double *a, int *err) {
+    const int b = rp[i], dq = dpos[i];
+    int64_t t = tp[i];
+    const int64_t te = tp[i + 1];
+    for (int q = b; q < dq; q++) {
+        const double ukk = a[ldiag[q]];
         if (ukk == 0.0 || !isfinite(ukk)) {
-            if (lane == 0) atomicOr(err, 1);
+            atomicOr(err, 1);
             return;
         }
         const double aik = a[q] / ukk;
-        __syncwarp();
-        if (lane == 0) a[q] = aik;
-        for (int f = dpos[k] + 1 + lane; f < rp[k + 1]; f += 32) {
-            const int j = ci[f];
-            int lo = q + 1, hi = e - 1;  // j > k: search the rest of row i
-            while (lo <= hi) {
-                const int mid = (lo + hi) >> 1;
-                const int c = ci[mid];
-                if (c == j) {
-                    a[mid] = fma(-aik, a[f], a[mid]);
-                    break;
-                }
-                if (c < j) lo = mid + 1;
-                else hi = mid - 1;
-            }
+        a[q] = aik;
+        for (; t < te; t++) {
+            const int3 x = tr[t];
+            if (x.x != q) break;
+            a[x.z] = fma(-aik, a[x.y], a[x.z]);
         }
-        __syncwarp();
     }
-    if (lane == 0) {
-        const double d = a[dpos[i]];
-        if (d == 0.0 || !isfinite(d)) atomicOr(err, 1);
-    }
+    const double d = a[dq];
+    if (d == 0.0 || !isfinite(d)) atomicOr(err, 1);
 }
 
-// One level: a warp per frontier row (factor it if ILU), then release its
-// dependents; a dependent whose in-degree reaches zero joins the next level.
+// Symbolic ILU(0) step, a thread per row: ldiag[q] = position of a_kk for the
+// L entries q of row i (column k), and the triples (q, f, p) with ci[f] ==
+// ci[p], f in U row k past its diagonal, p in row i past q.  Counts only
+// (into cnt) when tr is null.
+__global__ void k_ilu_triples(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                              const int32_t *__restrict__ dpos, int32_t *ldiag, const int64_t *__restrict__ tp,
+                              int32_t *cnt, int3 *tr) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int b = rp[i], e = rp[i + 1], dq = dpos[i];
+    int64_t out = tr ? tp[i] : 0;
+    int c = 0;
+    for (int q = b; q < dq; q++) {
+        const int k = ci[q];
+        const int dk = dpos[k];
+        if (!tr) ldiag[q] = dk;
+        int p = q + 1;
+        for (int f = dk + 1; f < rp[k + 1]; f++) {
+            const int j = ci[f];
+            while (p < e && ci[p] < j) p++;
+            if (p < e && ci[p] == j) {
+                if (tr) tr[out++] = make_int3(q, f, p);
+                else c++;
+            }
+        }
+    }
+    if (!tr) cnt[i] = c;
+}
+
+// One level, a thread per frontier row: factor it (ILU) from its triples,
+// then release its dependents; a dependent whose in-degree reaches zero joins
+// the next level (one queue atomic per warp).  The last block to finish
+// publishes the next level, so a level costs one launch.
 template <bool ILU>
 __global__ void __launch_bounds__(256)
-k_front_step(int32_t *order, int *q, const int64_t *__restrict__ trp, const int32_t *__restrict__ tcol,
-             int32_t *indeg, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-             const int32_t *__restrict__ dpos, double *a, int *err) {
+k_front_step(int32_t *order, int *q, int32_t *lptr, unsigned *done_blocks, const int64_t *__restrict__ trp,
+             const int32_t *__restrict__ tcol, int32_t *indeg, const int32_t *__restrict__ rp,
+             const int32_t *__restrict__ dpos, const int32_t *__restrict__ ldiag, const int64_t *__restrict__ tp,
+             const int3 *__restrict__ tr, double *a, int *err) {
     const int begin = q[0], end = q[1];
     const int lane = threadIdx.x & 31;
-    const int w0 = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
-    for (int r = begin + w0; r < end; r += nw) {
-        const int i = order[r];
-        if (ILU) ilu0_row(i, lane, rp, ci, dpos, a, err);
-        for (int64_t t = trp[i] + lane; t < trp[i + 1]; t += 32) {
-            const int d = tcol[t];
-            if (atomicSub(indeg + d, 1) == 1) order[atomicAdd(q + 2, 1)] = d;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = begin + gt; r - lane < end; r += nt) {  // warp-uniform trip count
+        const bool valid = r < end;
+        const int i = valid ? order[r] : 0;
+        if (ILU && valid) ilu0_row_triples(i, rp, dpos, ldiag, tp, tr, a, err);
+        int64_t t = valid ? trp[i] : 0;
+        const int64_t te = valid ? trp[i + 1] : 0;
+        while (__any_sync(0xffffffffu, t < te)) {
+            bool rel = false;
+            int d = 0;
+            if (t < te) {
+                d = tcol[t];
+                rel = atomicSub(indeg + d, 1) == 1;
+                t++;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, rel);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                int pos = 0;
+                if (lane == leader) pos = atomicAdd(q + 2, __popc(m));
+                pos = __shfl_sync(0xffffffffu, pos, leader);
+                if (rel) order[pos + __popc(m & ((1u << lane) - 1u))] = d;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(done_blocks, 1u) == gridDim.x - 1) {  // every block of this level is done
+            __threadfence();
+            const int tail = atomicAdd(q + 2, 0);
+            q[0] = end;
+            q[1] = tail;
+            if (tail > end) {
+                const int l = q[3] + 1;
+                q[3] = l;
+                lptr[l] = tail;
+            }
+            *done_blocks = 0;
+            __threadfence();
         }
     }
 }
@@ -254,24 +302,84 @@ sait_status frontier_schedule(sait_ctx ctx, const int32_t *rp, const int32_t *ci
     launch_k(k_front0, grid, 256, 0, s, n, (const int32_t *)indeg.p, order.p, q.p);
     launch_k(k_front_init, 1, 1, 0, s, q.p, lptr.p);
     SAIT_CK(cudaGetLastError());
-    const unsigned sgrid = (unsigned)std::min<int64_t>(cdiv(n * 32, 256), (int64_t)ctx->num_sms * 4);
     const bool ilu = a != nullptr;
-    for (int64_t batch = 0;; batch++) {
-        if (batch * 32 > n + 64) return ctx_fail(ctx, SAIT_ERR_CUDA, "level schedule did not terminate");
-        for (int t = 0; t < 32; t++) {
-            if (ilu)
-                launch_k(k_front_step<true>, sgrid, 256, 0, s, order.p, q.p, (const int64_t *)trp.p,
-                         (const int32_t *)tcol.p, indeg.p, rp, ci, dpos, a, err_word);
-            else
-                launch_k(k_front_step<false>, sgrid, 256, 0, s, order.p, q.p, (const int64_t *)trp.p,
-                         (const int32_t *)tcol.p, indeg.p, rp, ci, dpos, a, err_word);
-            launch_k(k_front_advance, 1, 1, 0, s, q.p, lptr.p);
-        }
-        SAIT_CK(cudaGetLastError());
-        SAIT_CK(cudaMemcpyAsync(h, q.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    // ILU: the update triples of every row (symbolic, all rows in parallel)
+    DTemp<int32_t> ldiag, tcnt2;
+    DTemp<int64_t> tp;
+    DTemp<int3> tr;
+    if (ilu) {
+        SAIT_CK(cudaMemcpyAsync(h, rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         SAIT_CK(cudaStreamSynchronize(s));
+        SAIT_CK(ldiag.alloc(std::max<int64_t>(h[0], 1), s));
+        SAIT_CK(tcnt2.alloc(n, s));
+        SAIT_CK(tp.alloc(n + 1, s));
+        launch_k(k_ilu_triples, grid, 256, 0, s, n, rp, ci, dpos, ldiag.p, (const int64_t *)nullptr, tcnt2.p,
+                 (int3 *)nullptr);
+        SAIT_CK(scan_i32(tcnt2.p, tp.p, n, s));
+        SAIT_CK(cudaMemcpyAsync(h64 + 1, tp.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        SAIT_CK(cudaStreamSynchronize(s));
+        SAIT_CK(tr.alloc(std::max<int64_t>(h64[1], 1), s));
+        launch_k(k_ilu_triples, grid, 256, 0, s, n, rp, ci, dpos, ldiag.p, (const int64_t *)tp.p, tcnt2.p, tr.p);
+        SAIT_CK(cudaGetLastError());
+    }
+    // few blocks: the level work is short and every block of a level meets at one counter
+    const unsigned sgrid = (unsigned)std::min<int64_t>(cdiv(n, 256), (int64_t)ctx->num_sms * 2);
+    DTemp<unsigned> done_blocks;
+    SAIT_CK(done_blocks.alloc(1, s));
+    SAIT_CK(cudaMemsetAsync(done_blocks.p, 0, sizeof(unsigned), s));
+    // kBatch levels (one launch each) are captured once in a CUDA graph and
+    // replayed until the frontier is empty; a level past the last one is a
+    // no-op (empty frontier), so replaying whole batches is safe
+    constexpr int kBatch = 32;
+    cudaGraphExec_t gexec = nullptr;
+    {
+        cudaStream_t cs;
+        SAIT_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        const int64_t launches0 = g_sait_launches;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            for (int t = 0; t < kBatch; t++) {
+                if (ilu)
+                    launch_k(k_front_step<true>, sgrid, 256, 0, cs, order.p, q.p, lptr.p, done_blocks.p,
+                             (const int64_t *)trp.p, (const int32_t *)tcol.p, indeg.p, rp, dpos,
+                             (const int32_t *)ldiag.p, (const int64_t *)tp.p, (const int3 *)tr.p, a, err_word);
+                else
+                    launch_k(k_front_step<false>, sgrid, 256, 0, cs, order.p, q.p, lptr.p, done_blocks.p,
+                             (const int64_t *)trp.p, (const int32_t *)tcol.p, indeg.p, rp, dpos,
+                             (const int32_t *)nullptr, (const int64_t *)nullptr, (const int3 *)nullptr, a, err_word);
+            }
+            cudaError_t e1 = cudaGetLastError();
+            e = cudaStreamEndCapture(cs, &g);
+            if (e == cudaSuccess && e1 != cudaSuccess) e = e1;
+        }
+        g_sait_launches = launches0;  // captured, not executed
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) {
+            if (gexec) cudaGraphExecDestroy(gexec);
+            return ctx_cuda(ctx, e, "frontier graph", __FILE__, __LINE__);
+        }
+    }
+    sait_status st = SAIT_OK;
+    for (int64_t batch = 0;; batch++) {
+        if (batch * kBatch > n + 64) {
+            st = ctx_fail(ctx, SAIT_ERR_CUDA, "level schedule did not terminate");
+            break;
+        }
+        cudaError_t e = cudaGraphLaunch(gexec, s);
+        g_sait_launches += kBatch;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, q.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            st = ctx_cuda(ctx, e, "frontier sweep", __FILE__, __LINE__);
+            break;
+        }
         if (h[0] == h[1]) break;  // empty frontier: every row is scheduled
     }
+    cudaGraphExecDestroy(gexec);
+    if (st != SAIT_OK) return st;
     if (h[1] != n) return ctx_fail(ctx, SAIT_ERR_CUDA, "level schedule lost rows");
     if (out) {
         const int nlev = h[3];

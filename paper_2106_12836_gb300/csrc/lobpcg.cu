@@ -639,11 +639,13 @@ extern "C" sait_status sait_lobpcg(sait_ctx ctx, sait_mat A, sait_prec P, int32_
                 result = SAIT_ERR_BREAKDOWN;
                 break;
             }
-            // X = S c, AX = AS c, P = [W P] c(k:, :), AP = [AW AP] c(k:, :)
+            // X = S c, P = [W P] c(k:, :); A X and A P are formed by products with A
+            // rather than as AS c: that is as cheap and keeps them from drifting away
+            // from A X over the iterations (the residuals need them to ~1e-14 ||A||)
             SAIT_TRY(bmul(ctx, n, S.p, m, m, w.coef.p, k, k, X, k, false, 1.0));
-            SAIT_TRY(bmul(ctx, n, AS.p, m, m, w.coef.p, k, k, AX.p, k, false, 1.0));
             SAIT_TRY(bmul(ctx, n, S.p + k, na + np, m, w.coef.p + (size_t)k * k, k, k, Pb.p, k, false, 1.0));
-            SAIT_TRY(bmul(ctx, n, AS.p + k, na + np, m, w.coef.p + (size_t)k * k, k, k, AP.p, k, false, 1.0));
+            SAIT_TRY(spmm_a(X, k, AX.p));
+            SAIT_TRY(spmm_a(Pb.p, k, AP.p));
             SAIT_CK(cudaMemcpyAsync(lambda, w.theta.p, k * sizeof(double), cudaMemcpyDeviceToDevice, s));
             havep = true;
             done = true;
