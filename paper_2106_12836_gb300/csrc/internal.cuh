@@ -195,6 +195,16 @@ __device__ __forceinline__ void split_pair(double v, float &hi, float &lo) {
     lo = __fsub_rn(__uint_as_float(sign | base | mid), __uint_as_float(sign | base));
 }
 
+// v truncated to FP32 (the hi part of split_pair) with integer operations
+__device__ __forceinline__ float hi_part(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ff);
+    const int ef = e - 896;
+    if (ef <= 0 || ef >= 255) return (float)v;
+    return __uint_as_float(((unsigned)(b >> 63) << 31) | ((unsigned)ef << 23) |
+                           (unsigned)((b & ((1ULL << 52) - 1)) >> 29));
+}
+
 // S + E as an FP64 value
 __device__ __forceinline__ double df_value(float S, float E) { return (double)S + (double)E; }
 

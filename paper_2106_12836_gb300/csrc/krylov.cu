@@ -97,7 +97,7 @@ k_reduce(const double *__restrict__ partial, int nb, int stride, double *out, co
 // (four rows per thread) and never need a ragged tail.
 __device__ __forceinline__ float4 load_w4(const double2 *w, int64_t i4) {
     const double2 a = w[2 * i4], b = w[2 * i4 + 1];
-    return make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+    return make_float4(hi_part(a.x), hi_part(a.y), hi_part(b.x), hi_part(b.y));
 }
 
 // ---- GMRES with delayed reorthogonalization (DCGS2) --------------------------
@@ -344,8 +344,7 @@ k_dcgs_update(int64_t n4, const float4 *__restrict__ Vh, const float4 *__restric
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kThreads) {
         float S1[4] = {0.f, 0.f, 0.f, 0.f}, E1[4] = {0.f, 0.f, 0.f, 0.f};
         float S2[4] = {0.f, 0.f, 0.f, 0.f}, E2[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int q = 0; q < j; q++) {
-            const float4 h = __ldg(Vh + (int64_t)q * ldv4 + i), l = __ldg(Vl + (int64_t)q * ldv4 + i);
+        auto term = [&](const float4 &h, const float4 &l, int q) {
             const float a = ph[q], al = pl[q], b = rh[q], bl = rl[q];
             df_term(S1[0], E1[0], h.x, l.x, a, al);
             df_term(S1[1], E1[1], h.y, l.y, a, al);
@@ -355,7 +354,15 @@ k_dcgs_update(int64_t n4, const float4 *__restrict__ Vh, const float4 *__restric
             df_term(S2[1], E2[1], h.y, l.y, b, bl);
             df_term(S2[2], E2[2], h.z, l.z, b, bl);
             df_term(S2[3], E2[3], h.w, l.w, b, bl);
+        };
+        int q = 0;
+        for (; q + 2 <= j; q += 2) {  // two basis vectors' loads in flight
+            const float4 h0 = __ldg(Vh + (int64_t)q * ldv4 + i), l0 = __ldg(Vl + (int64_t)q * ldv4 + i);
+            const float4 h1 = __ldg(Vh + (int64_t)(q + 1) * ldv4 + i), l1 = __ldg(Vl + (int64_t)(q + 1) * ldv4 + i);
+            term(h0, l0, q);
+            term(h1, l1, q + 1);
         }
+        if (q < j) term(__ldg(Vh + (int64_t)q * ldv4 + i), __ldg(Vl + (int64_t)q * ldv4 + i), q);
         const double2 ua = wcol1[2 * i], ub = wcol1[2 * i + 1];
         const double2 wa = wcol[2 * i], wb = wcol[2 * i + 1];
         const double u[4] = {ua.x, ua.y, ub.x, ub.y}, w[4] = {wa.x, wa.y, wb.x, wb.y};
