@@ -26,7 +26,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sait_oracle.c")
 _LIB = os.path.join(_HERE, "libsait_oracle.so")
 
-DROP = {"none": 0, "abs": 1, "rowrel": 2, "pattern": 3}
+DROP = {"none": 0, "abs": 1, "rowrel": 2, "pattern": 3, "hybrid": 4}
 STATUS = {0: "ok", 1: "invalid argument", 2: "not triangular", 3: "zero pivot",
           4: "out of memory", 5: "not converged", 6: "breakdown"}
 

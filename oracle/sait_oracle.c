@@ -21,6 +21,8 @@
  *   2 rowrel   drop |v| < tau * max_j |v_ij| of the current row (diagonal included)
  *   3 pattern  Algorithm 3 (SAIT_Pat): p undropped iterations fix the pattern S,
  *              the remaining iterations drop every entry outside S
+ *   4 hybrid   the hybrid strategy the paper's source leaves commented out after
+ *              Algorithm 3: p undropped iterations, then drop |v| < tau
  * The diagonal is never dropped (Section 3: the unit diagonal keeps M full rank).
  *
  * Parity pins: see tests/test_oracle_pins.py.  Every function here is pinned.
@@ -295,8 +297,8 @@ int ora_sait(int64_t n, const int32_t *rp, const int32_t *ci, const double *va,
              int m_terms, int drop_kind, double tau, int p, ora_mat *out)
 {
     memset(out, 0, sizeof(*out));
-    if (n < 0 || m_terms < 1 || drop_kind < 0 || drop_kind > 3 || p < 0 ||
-        ((drop_kind == 1 || drop_kind == 2) && !(tau >= 0.0)))
+    if (n < 0 || m_terms < 1 || drop_kind < 0 || drop_kind > 4 || p < 0 ||
+        ((drop_kind == 1 || drop_kind == 2 || drop_kind == 4) && !(tau >= 0.0)))
         return ORA_INVALID;
     int st = ORA_OK;
     int side = 0;   /* -1 lower, +1 upper, 0 diagonal only so far */
@@ -367,6 +369,7 @@ int ora_sait(int64_t n, const int32_t *rp, const int32_t *ci, const double *va,
             /* dropping rule on the whole new row */
             int kind = drop_kind;
             if (kind == 3 && it <= p) kind = 0;          /* pattern-building iterations */
+            if (kind == 4) kind = it <= p ? 0 : 1;       /* hybrid: undropped, then threshold */
             double thr = tau;
             if (kind == 2) {
                 double mx = 0.0;

@@ -252,6 +252,9 @@ def _dense_sait(Td, m_terms, rule, tau=0.0, p=0):
             near |= struct & (np.abs(np.abs(full) - thr) <= 1e-12 * np.maximum(thr, 1e-300))
         elif rule == "pattern" and it > p:
             keep &= S
+        elif rule == "hybrid" and it > p:
+            keep &= ~(np.abs(full) < tau)
+            near |= struct & (np.abs(np.abs(full) - tau) <= 1e-12 * max(tau, 1e-300))
         keep |= np.eye(n, dtype=bool)
         MD = np.where(keep, full, 0.0)
         if rule == "pattern" and it == p:
@@ -261,7 +264,8 @@ def _dense_sait(Td, m_terms, rule, tau=0.0, p=0):
 
 @pytest.mark.parametrize("rule,tau,p", [("abs", 0.05, 0), ("abs", 0.2, 0), ("rowrel", 0.1, 0),
                                         ("pattern", 0.0, 1), ("pattern", 0.0, 2),
-                                        ("pattern", 0.0, 0), ("none", 0.0, 0)])
+                                        ("pattern", 0.0, 0), ("none", 0.0, 0), ("hybrid", 0.05, 2),
+                                        ("hybrid", 0.2, 1)])
 @pytest.mark.parametrize("lower", [True, False])
 def test_dropping_against_dense_brute_force(oracle_lib, rule, tau, p, lower):
     n, m_terms = 60, 5
@@ -342,6 +346,18 @@ def test_paper_jacobi_pcg_iteration_counts(oracle_lib, laplace100):
         _, it, rr, st = oracle_lib.pcg(A, b, f"jacobi{k}", L, U, tol=g["pcg_tol"])
         assert st == 0 and rr <= g["pcg_tol"]
         assert abs(it - g["level0_pcg_iters"][str(k)]) <= 0.05 * g["level0_pcg_iters"][str(k)], (k, it)
+
+
+def test_hybrid_limits(oracle_lib):
+    """Hybrid with every product undropped is the exact series; with no undropped product it is SAIT_Thr."""
+    L, _ = oracle_lib.ilu0(synth.convdiff3d(10))
+    for m in (3, 5):
+        H = oracle_lib.sait(L, m, "hybrid", 0.05, m - 1)
+        N = oracle_lib.sait(L, m, "none")
+        assert np.array_equal(H.rp, N.rp) and np.array_equal(H.ci, N.ci) and np.array_equal(H.va, N.va)
+        H0 = oracle_lib.sait(L, m, "hybrid", 0.05, 0)
+        A0 = oracle_lib.sait(L, m, "abs", 0.05)
+        assert np.array_equal(H0.rp, A0.rp) and np.array_equal(H0.ci, A0.ci) and np.array_equal(H0.va, A0.va)
 
 
 def test_pattern_nnz_independent_of_m(oracle_lib):
