@@ -58,14 +58,18 @@ typedef enum {
     SAIT_DROP_NONE = 0,    /* keep every structural entry (exact series) */
     SAIT_DROP_ABS = 1,     /* Algorithm 2, SAIT_Thr: drop |v| < tau */
     SAIT_DROP_ROWREL = 2,  /* drop |v| < tau * max_j |(M D)_ij| of the current row */
-    SAIT_DROP_PATTERN = 3  /* Algorithm 3, SAIT_Pat: the first p products are not dropped
+    SAIT_DROP_PATTERN = 3, /* Algorithm 3, SAIT_Pat: the first p products are not dropped
                               and fix the pattern S; later products drop entries outside S */
+    SAIT_DROP_HYBRID = 4   /* the hybrid strategy the paper's source leaves commented out
+                              after Algorithm 3: the first p products are not dropped, later
+                              ones drop |v| < tau */
 } sait_drop_kind;
 
 typedef struct {
     int32_t kind;   /* sait_drop_kind */
-    int32_t p;      /* SAIT_DROP_PATTERN: number of pattern-building products, 0 <= p */
-    double tau;     /* SAIT_DROP_ABS / SAIT_DROP_ROWREL: threshold, 0 <= tau < 1 */
+    int32_t p;      /* SAIT_DROP_PATTERN: pattern-building products; SAIT_DROP_HYBRID:
+                       undropped products; 0 <= p */
+    double tau;     /* SAIT_DROP_ABS / ROWREL / HYBRID: threshold, 0 <= tau < 1 */
 } sait_drop;
 
 /* Storage precision of a matrix's values for products (the FP64 values are

@@ -31,7 +31,7 @@ __all__ = [
     "sait_mat_autotune", "sait_batch_autotune", "sait_ctx_set_batch_tile",
 ]
 
-DROP = {"none": 0, "abs": 1, "rowrel": 2, "pattern": 3}
+DROP = {"none": 0, "abs": 1, "rowrel": 2, "pattern": 3, "hybrid": 4}
 DTYPE = {"f64": 0, "f32": 1, "bf16": 2, "f32x64": 3, "bf16x64": 4}
 LOWER, UPPER = 0, 1
 

@@ -572,12 +572,12 @@ extern "C" sait_status sait_build(sait_ctx ctx, sait_mat T, sait_uplo uplo, int3
     if (m_terms < 1) return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_build: m_terms < 1");
     if (uplo != SAIT_LOWER && uplo != SAIT_UPPER)
         return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_build: bad uplo");
-    if (drop.kind < SAIT_DROP_NONE || drop.kind > SAIT_DROP_PATTERN)
+    if (drop.kind < SAIT_DROP_NONE || drop.kind > SAIT_DROP_HYBRID)
         return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_build: bad drop kind");
-    if ((drop.kind == SAIT_DROP_ABS || drop.kind == SAIT_DROP_ROWREL) &&
+    if ((drop.kind == SAIT_DROP_ABS || drop.kind == SAIT_DROP_ROWREL || drop.kind == SAIT_DROP_HYBRID) &&
         !(drop.tau >= 0.0 && drop.tau < 1.0))
         return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_build: tau must lie in [0, 1)");
-    if (drop.kind == SAIT_DROP_PATTERN && drop.p < 0)
+    if ((drop.kind == SAIT_DROP_PATTERN || drop.kind == SAIT_DROP_HYBRID) && drop.p < 0)
         return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_build: p < 0");
     if (!store_valid(store))
         return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_build: bad storage type");
@@ -649,7 +649,9 @@ extern "C" sait_status sait_build(sait_ctx ctx, sait_mat T, sait_uplo uplo, int3
         SAIT_CK(cudaMemsetAsync(hash_err, 0, sizeof(int), s));
         for (int it = 1; it < m_terms; it++) {
             const bool masked = pattern && it > drop.p;
-            const int kind = pattern ? kDropNone : (int)drop.kind;
+            const int kind = pattern ? kDropNone
+                             : drop.kind == SAIT_DROP_HYBRID ? (it <= drop.p ? kDropNone : kDropAbs)
+                                                             : (int)drop.kind;
             const bool last = it == m_terms - 1;
             const int32_t *s_cnt = masked && have_S ? S.cnt.p : nullptr;
             const int64_t *s_off = masked && have_S ? S.off.p : nullptr;

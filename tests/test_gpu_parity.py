@@ -60,7 +60,7 @@ def assert_sait_parity(G: synth.CSR, O: synth.CSR, T: synth.CSR, drop: str, tau:
         assert np.all(np.abs(G.va - O.va) <= 1e-12 * np.abs(O.va))
         return
     # structures differ: every differing entry must sit at the threshold
-    assert drop in ("abs", "rowrel"), "structure mismatch without a threshold rule"
+    assert drop in ("abs", "rowrel", "hybrid"), "structure mismatch without a threshold rule"
 
     def entries(M):
         rows = np.repeat(np.arange(M.n), np.diff(M.rp))
@@ -101,6 +101,7 @@ def test_ilu0_zero_pivot(sg, ctx):
 CASES = [
     ("rowrel", 1e-3, 0, 3), ("rowrel", 1e-3, 0, 6), ("abs", 0.05, 0, 11), ("abs", 0.01, 0, 5),
     ("none", 0.0, 0, 4), ("pattern", 0.0, 2, 8), ("pattern", 0.0, 0, 4), ("pattern", 0.0, 3, 3),
+    ("hybrid", 0.02, 2, 6), ("hybrid", 0.05, 0, 4),
 ]
 
 
