@@ -367,15 +367,25 @@ k_spgemm_reg(int nrows, const int32_t *__restrict__ rows, const int32_t *__restr
     }
     const int next_key = __shfl_down_sync(gmask, skey, 1, W);
     const bool tail = skey != INT_MAX && (gl == W - 1 || next_key != skey);
+    // The magnitude tests run on the IEEE bit patterns (non-negative doubles
+    // order like their encodings), which keeps them off GB300's narrow FP64
+    // pipe: |acc| < thr  <=>  absbits(acc) < bits(thr) for thr >= 0, and a
+    // NaN (encoding above infinity) is kept, as !(NaN < thr) keeps it.
+    constexpr unsigned long long kAbs = 0x7fffffffffffffffULL, kInf = 0x7ff0000000000000ULL;
+    const unsigned long long ab = (unsigned long long)__double_as_longlong(acc) & kAbs;
     double thr = tau;
     if (kind == kDropRowRel) {
-        double mx = tail ? fabs(acc) : 0.0;
+        unsigned long long mb = tail && ab <= kInf ? ab : 0ULL;  // the row maximum ignores NaN
 #pragma unroll
-        for (int o = W / 2; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(gmask, mx, o, W));
-        thr = tau * mx;
+        for (int o = W / 2; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_xor_sync(gmask, mb, o, W);
+            mb = ob > mb ? ob : mb;
+        }
+        thr = tau * __longlong_as_double((long long)mb);
     }
     bool keep = tail;
-    if (keep && (kind == kDropAbs || kind == kDropRowRel) && skey != i) keep = !(fabs(acc) < thr);
+    if (keep && (kind == kDropAbs || kind == kDropRowRel) && skey != i)
+        keep = !(ab < (unsigned long long)__double_as_longlong(thr));
     const unsigned km = (__ballot_sync(gmask, keep) >> gbase) & (W == 32 ? 0xffffffffu : ((1u << W) - 1u));
     if (keep) {
         const int64_t dst = o_off[i] + __popc(km & lt);
