@@ -395,20 +395,24 @@ k_dcgs_update2(int64_t n2, const float2 *__restrict__ Vh, const float2 *__restri
                const double *__restrict__ coef, const double *__restrict__ kk, double2 *wcol1, double2 *wcol,
                float2 *vh_out, float2 *vl_out, float2 *w32, double *partial, const int *gate) {
     if (gate && *gate == 0) return;
-    __shared__ float ph[kMaxRestart + 1], pl[kMaxRestart + 1], rh[kMaxRestart + 1], rl[kMaxRestart + 1];
+    __shared__ float ph[kMaxRestart + 1], rh[kMaxRestart + 1], rl[kMaxRestart + 1];
     for (int q = threadIdx.x; q < j; q += kThreads) {
-        split_pair(coef[q], ph[q], pl[q]);
+        ph[q] = (float)coef[q];
         split_pair(coef[j + q], rh[q], rl[q]);
     }
     __syncthreads();
     const double k1 = kk[0], k2 = kk[1], k3 = kk[2];
     double nrm = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n2; i += (int64_t)gridDim.x * kThreads) {
-        float S1[2] = {0.f, 0.f}, E1[2] = {0.f, 0.f}, S2[2] = {0.f, 0.f}, E2[2] = {0.f, 0.f};
+        // V p is the reorthogonalization correction: p = c / gamma holds the
+        // residual projections (FP32-dot error level, |p| << 1), so V_hi p in FP32
+        // is accurate to |p| 2^-24 -- far below the FP64 rounding of v_j.  V r
+        // carries the O(1) projections and cancels: double-float.
+        float S1[2] = {0.f, 0.f}, S2[2] = {0.f, 0.f}, E2[2] = {0.f, 0.f};
         auto term = [&](const float2 &h, const float2 &l, int q) {
-            const float a = ph[q], al = pl[q], b = rh[q], bl = rl[q];
-            df_term(S1[0], E1[0], h.x, l.x, a, al);
-            df_term(S1[1], E1[1], h.y, l.y, a, al);
+            const float a = ph[q], b = rh[q], bl = rl[q];
+            S1[0] = fmaf(h.x, a, S1[0]);
+            S1[1] = fmaf(h.y, a, S1[1]);
             df_term(S2[0], E2[0], h.x, l.x, b, bl);
             df_term(S2[1], E2[1], h.y, l.y, b, bl);
         };
@@ -425,8 +429,8 @@ k_dcgs_update2(int64_t n2, const float2 *__restrict__ Vh, const float2 *__restri
         }
         for (; q < j; q++) term(__ldg(Vh + (int64_t)q * ldv2 + i), __ldg(Vl + (int64_t)q * ldv2 + i), q);
         const double2 u = wcol1[i], w = wcol[i];
-        const double v0 = fma(k1, u.x, -df_value(S1[0], E1[0]));
-        const double v1 = fma(k1, u.y, -df_value(S1[1], E1[1]));
+        const double v0 = fma(k1, u.x, -(double)S1[0]);
+        const double v1 = fma(k1, u.y, -(double)S1[1]);
         const double x0 = fma(k2, w.x, fma(-k3, u.x, -df_value(S2[0], E2[0])));
         const double x1 = fma(k2, w.y, fma(-k3, u.y, -df_value(S2[1], E2[1])));
         float vh0, vl0, vh1, vl1;
