@@ -465,6 +465,7 @@ def run_ours(a):
         dist.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(local)
+    time.sleep(1.0)  # let the sampler start up before the timed steps (its start-up competes for the host)
     times, infos, extra = [], [], {}
     for _ in range(a.steps):
         flush_l2()
