@@ -328,68 +328,8 @@ k_dcgs_small(int j, int m, int remaining, int close, double *Hr, double *R, doub
 // v_j = k1 w1 - V p (written over w1 in column j, with its (hi, lo) pair) and
 // w1' = k2 w - k3 w1 - V r (written over w in column j + 1, with its FP32
 // copy for the next dual sweep); partial[b] = ||w1'||^2 of block b's rows.
-__global__ void __launch_bounds__(kThreads, 4)
-k_dcgs_update(int64_t n4, const float4 *__restrict__ Vh, const float4 *__restrict__ Vl, int64_t ldv4, int j,
-              const double *__restrict__ coef, const double *__restrict__ kk, double2 *wcol1, double2 *wcol,
-              float4 *vh_out, float4 *vl_out, float4 *w32, double *partial, const int *gate) {
-    if (gate && *gate == 0) return;
-    __shared__ float ph[kMaxRestart + 1], pl[kMaxRestart + 1], rh[kMaxRestart + 1], rl[kMaxRestart + 1];
-    for (int q = threadIdx.x; q < j; q += kThreads) {
-        split_pair(coef[q], ph[q], pl[q]);
-        split_pair(coef[j + q], rh[q], rl[q]);
-    }
-    __syncthreads();
-    const double k1 = kk[0], k2 = kk[1], k3 = kk[2];
-    double nrm = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kThreads) {
-        float S1[4] = {0.f, 0.f, 0.f, 0.f}, E1[4] = {0.f, 0.f, 0.f, 0.f};
-        float S2[4] = {0.f, 0.f, 0.f, 0.f}, E2[4] = {0.f, 0.f, 0.f, 0.f};
-        auto term = [&](const float4 &h, const float4 &l, int q) {
-            const float a = ph[q], al = pl[q], b = rh[q], bl = rl[q];
-            df_term(S1[0], E1[0], h.x, l.x, a, al);
-            df_term(S1[1], E1[1], h.y, l.y, a, al);
-            df_term(S1[2], E1[2], h.z, l.z, a, al);
-            df_term(S1[3], E1[3], h.w, l.w, a, al);
-            df_term(S2[0], E2[0], h.x, l.x, b, bl);
-            df_term(S2[1], E2[1], h.y, l.y, b, bl);
-            df_term(S2[2], E2[2], h.z, l.z, b, bl);
-            df_term(S2[3], E2[3], h.w, l.w, b, bl);
-        };
-        int q = 0;
-        for (; q + 2 <= j; q += 2) {  // two basis vectors' loads in flight
-            const float4 h0 = __ldg(Vh + (int64_t)q * ldv4 + i), l0 = __ldg(Vl + (int64_t)q * ldv4 + i);
-            const float4 h1 = __ldg(Vh + (int64_t)(q + 1) * ldv4 + i), l1 = __ldg(Vl + (int64_t)(q + 1) * ldv4 + i);
-            term(h0, l0, q);
-            term(h1, l1, q + 1);
-        }
-        if (q < j) term(__ldg(Vh + (int64_t)q * ldv4 + i), __ldg(Vl + (int64_t)q * ldv4 + i), q);
-        const double2 ua = wcol1[2 * i], ub = wcol1[2 * i + 1];
-        const double2 wa = wcol[2 * i], wb = wcol[2 * i + 1];
-        const double u[4] = {ua.x, ua.y, ub.x, ub.y}, w[4] = {wa.x, wa.y, wb.x, wb.y};
-        double v[4], x[4];
-        float vh[4], vl[4], xh[4], xl[4];
-#pragma unroll
-        for (int r = 0; r < 4; r++) {
-            v[r] = fma(k1, u[r], -df_value(S1[r], E1[r]));
-            x[r] = fma(k2, w[r], fma(-k3, u[r], -df_value(S2[r], E2[r])));
-            split_pair(v[r], vh[r], vl[r]);
-            split_pair(x[r], xh[r], xl[r]);
-            nrm = fma(x[r], x[r], nrm);
-        }
-        wcol1[2 * i] = make_double2(v[0], v[1]);
-        wcol1[2 * i + 1] = make_double2(v[2], v[3]);
-        wcol[2 * i] = make_double2(x[0], x[1]);
-        wcol[2 * i + 1] = make_double2(x[2], x[3]);
-        vh_out[i] = make_float4(vh[0], vh[1], vh[2], vh[3]);
-        vl_out[i] = make_float4(vl[0], vl[1], vl[2], vl[3]);
-        w32[i] = make_float4(xh[0], xh[1], xh[2], xh[3]);
-    }
-    nrm = block_sum(nrm);
-    if (threadIdx.x == 0) partial[blockIdx.x] = nrm;
-}
-
-// The same update with two rows per thread (8-byte pair loads): half the
-// accumulators, so more resident warps hide the load latency.
+// Two rows per thread (8-byte pair loads), so many resident warps hide the
+// load latency.
 __global__ void __launch_bounds__(kThreads, 6)
 k_dcgs_update2(int64_t n2, const float2 *__restrict__ Vh, const float2 *__restrict__ Vl, int64_t ldv2, int j,
                const double *__restrict__ coef, const double *__restrict__ kk, double2 *wcol1, double2 *wcol,
@@ -542,20 +482,10 @@ __global__ void k_bicg_init(Scal *sc) {  // r0 holds ||r||^2 of the (re)start re
     sc->rho_old = sc->alpha = sc->omega = 1.0;
     sc->active = 1;
     sc->state = 0;
+    sc->r2 = sc->r0;        // rho = (rh, r) with rh = r
     sc->r3 = sqrt(sc->r0);  // smallest residual norm of this recurrence
 }
 
-__global__ void k_bicg_beta(Scal *sc) {  // after rho = (rh, r) in r0
-    if (sc->active == 0) return;
-    const double rho = sc->r0;
-    sc->rho = rho;
-    if (rho == 0.0 || sc->omega == 0.0 || !isfinite(rho)) {
-        sc->state = !isfinite(rho) ? 3 : 2;
-        sc->active = 0;
-        return;
-    }
-    sc->beta_b = (rho / sc->rho_old) * (sc->alpha / sc->omega);
-}
 
 __global__ void k_bicg_p(int64_t n, const double *__restrict__ r, const double *__restrict__ v, double *p,
                          const Scal *sc) {
@@ -565,33 +495,8 @@ __global__ void k_bicg_p(int64_t n, const double *__restrict__ r, const double *
         p[i] = r[i] + beta * (p[i] - omega * v[i]);
 }
 
-__global__ void k_bicg_alpha(Scal *sc) {  // after (rh, v) in r0
-    if (sc->active == 0) return;
-    const double rv = sc->r0;
-    if (rv == 0.0 || !isfinite(rv)) {
-        sc->state = !isfinite(rv) ? 3 : 2;
-        sc->active = 0;
-        return;
-    }
-    sc->alpha = sc->rho / rv;
-}
 
-// s = r - alpha v
-__global__ void k_bicg_s(int64_t n, const double *__restrict__ r, const double *__restrict__ v, double *s,
-                         const Scal *sc) {
-    if (sc->active == 0) return;
-    const double alpha = sc->alpha;
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
-        s[i] = r[i] - alpha * v[i];
-}
 
-__global__ void k_bicg_check_s(Scal *sc) {  // after (s, s) in r0
-    if (sc->active == 0) return;
-    sc->jdone += 1;
-    const double sn = sqrt(sc->r0);
-    if (!isfinite(sn)) { sc->state = 3; sc->active = 0; return; }
-    if (sn <= sc->tolb) { sc->state = 4; sc->active = 0; }
-}
 
 // half step converged: x += alpha ph (runs once, when state == 4)
 __global__ void k_bicg_xhalf(int64_t n, double *x, const double *__restrict__ ph, Scal *sc) {
@@ -605,37 +510,110 @@ __global__ void k_bicg_xhalf_done(Scal *sc) {
     if (sc->state == 4) sc->state = 1;
 }
 
-__global__ void k_bicg_omega(Scal *sc) {  // after (t,t) in r0, (t,s) in r1
+
+
+
+
+// ---- fused BiCGSTAB steps ---------------------------------------------------
+// The residual-side dot products are formed inside the vector updates that
+// produce their operands, and each scalar step runs in the block that sums
+// the per-block partials (fixed order), so an iteration reads s and r once
+// and launches two reductions fewer.
+
+// s = r - alpha v;  partial[b*3] = sum (s, s)
+__global__ void __launch_bounds__(kThreads)
+k_bicg_s_dot(int64_t n, const double *__restrict__ r, const double *__restrict__ v, double *s, const Scal *sc,
+             double *partial) {
     if (sc->active == 0) return;
-    const double tt = sc->r0;
-    sc->omega = tt == 0.0 ? 0.0 : sc->r1 / tt;
+    const double alpha = sc->alpha;
+    double a = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        const double si = r[i] - alpha * v[i];
+        s[i] = si;
+        a = fma(si, si, a);
+    }
+    a = block_sum(a);
+    if (threadIdx.x == 0) partial[blockIdx.x * 3] = a;
 }
 
-// x += alpha ph + omega sh;  r = s - omega t
-__global__ void k_bicg_xr(int64_t n, double *x, double *r, const double *__restrict__ ph,
-                          const double *__restrict__ sh, const double *__restrict__ s,
-                          const double *__restrict__ t, const Scal *sc) {
+// x += alpha ph + omega sh;  r = s - omega t;  partial[b*3] = (r, r), [b*3+1] = (rh, r)
+__global__ void __launch_bounds__(kThreads)
+k_bicg_xr_dot(int64_t n, double *x, double *r, const double *__restrict__ ph, const double *__restrict__ sh,
+              const double *__restrict__ s, const double *__restrict__ t, const double *__restrict__ rh,
+              const Scal *sc, double *partial) {
     if (sc->active == 0) return;
     const double alpha = sc->alpha, omega = sc->omega;
+    double a = 0.0, c = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
         x[i] += alpha * ph[i] + omega * sh[i];
-        r[i] = s[i] - omega * t[i];
+        const double ri = s[i] - omega * t[i];
+        r[i] = ri;
+        a = fma(ri, ri, a);
+        c = fma(rh[i], ri, c);
+    }
+    a = block_sum(a);
+    c = block_sum(c);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x * 3] = a;
+        partial[blockIdx.x * 3 + 1] = c;
     }
 }
 
-__global__ void k_bicg_check_r(Scal *sc, int remaining) {  // after (r, r) in r0
+// one block: sums nd columns of the partials into sc->r0, r1, then one scalar step
+enum { kStepAlpha = 0, kStepCheckS = 1, kStepOmega = 2, kStepCheckR = 3 };
+__global__ void __launch_bounds__(kThreads)
+k_bicg_step(int step, int nd, const double *__restrict__ partial, int nb, Scal *sc, int remaining) {
     if (sc->active == 0) return;
-    sc->rho_old = sc->rho;
-    const double rn = sqrt(sc->r0);
-    if (!isfinite(rn)) { sc->state = 3; sc->active = 0; return; }
-    if (rn <= sc->tolb) { sc->state = 1; sc->active = 0; return; }
-    if (sc->jdone >= remaining) { sc->active = 0; return; }
-    // divergence guard: restart the recurrence from the current iterate once
-    // the residual has grown four orders of magnitude above its minimum
-    if (rn > 1e4 * sc->r3) { sc->state = 5; sc->active = 0; return; }
-    sc->r3 = fmin(sc->r3, rn);
+    double q0 = 0.0, q1 = 0.0;
+    for (int b = threadIdx.x; b < nb; b += kThreads) {
+        q0 += partial[(int64_t)b * 3];
+        if (nd > 1) q1 += partial[(int64_t)b * 3 + 1];
+    }
+    q0 = block_sum(q0);
+    if (nd > 1) q1 = block_sum(q1);
+    if (threadIdx.x != 0) return;
+    sc->r0 = q0;
+    sc->r1 = q1;
+    if (step == kStepAlpha) {
+        if (q0 == 0.0 || !isfinite(q0)) {
+            sc->state = !isfinite(q0) ? 3 : 2;
+            sc->active = 0;
+            return;
+        }
+        sc->alpha = sc->rho / q0;
+    } else if (step == kStepCheckS) {
+        sc->jdone += 1;
+        const double sn = sqrt(q0);
+        if (!isfinite(sn)) { sc->state = 3; sc->active = 0; return; }
+        if (sn <= sc->tolb) { sc->state = 4; sc->active = 0; }
+    } else if (step == kStepOmega) {
+        sc->omega = q0 == 0.0 ? 0.0 : q1 / q0;
+    } else {  // check r; q1 = (rh, r) is the next rho
+        sc->rho_old = sc->rho;
+        sc->r2 = q1;
+        const double rn = sqrt(q0);
+        if (!isfinite(rn)) { sc->state = 3; sc->active = 0; return; }
+        if (rn <= sc->tolb) { sc->state = 1; sc->active = 0; return; }
+        if (sc->jdone >= remaining) { sc->active = 0; return; }
+        // divergence guard: restart the recurrence from the current iterate once
+        // the residual has grown four orders of magnitude above its minimum
+        if (rn > 1e4 * sc->r3) { sc->state = 5; sc->active = 0; return; }
+        sc->r3 = fmin(sc->r3, rn);
+    }
 }
 
+// beta from rho = (rh, r) (sc->r2: the previous check step, or ||r||^2 at a restart)
+__global__ void k_bicg_beta2(Scal *sc) {
+    if (sc->active == 0) return;
+    const double rho = sc->r2;
+    sc->rho = rho;
+    if (rho == 0.0 || sc->omega == 0.0 || !isfinite(rho)) {
+        sc->state = !isfinite(rho) ? 3 : 2;
+        sc->active = 0;
+        return;
+    }
+    sc->beta_b = (rho / sc->rho_old) * (sc->alpha / sc->omega);
+}
 
 // ---- PCG kernels (Saad, Algorithm 9.1) ----------------------------------------------
 __global__ void k_pcg_alpha(Scal *sc) {  // after (p, q) in r0
@@ -842,7 +820,7 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
         if (iters >= maxit) break;
         launch_k(k_hi4, egrid, kThreads, 0, s, n4, (const double2 *)V.p, (float4 *)w32.p);
         const int remaining = maxit - iters;
-        const float4 *Vh4 = (const float4 *)V32.p, *Vl4 = (const float4 *)VL.p;
+        const float4 *Vh4 = (const float4 *)V32.p;
         auto ortho = [&](int j, int close) {
             double *wj = V.p + (size_t)j * ldv;
             const double2 *wn = (const double2 *)(close ? wj : V.p + (size_t)(j + 1) * ldv);
@@ -968,9 +946,9 @@ extern "C" sait_status sait_bicgstab(sait_ctx ctx, sait_mat A, sait_prec P, cons
         SAIT_CK(cudaMemsetAsync(&sc->jdone, 0, sizeof(int), s));
         launch_k(k_bicg_init, 1, 1, 0, s, sc);
         const int remaining = maxit - iters;
+        const unsigned vgrid = (unsigned)W.nb;  // the fused kernels write one partial per block
         for (int it = 0; it < remaining; it++) {
-            SAIT_CK(dots(ctx, W, n, 1, rh.p, r.p, nullptr, nullptr, nullptr, nullptr, r0, act));
-            launch_k(k_bicg_beta, 1, 1, 0, s, sc);
+            launch_k(k_bicg_beta2, 1, 1, 0, s, sc);
             launch_k(k_bicg_p, egrid, kThreads, 0, s, n, r.p, v.p, p.p, sc);
             SAIT_TRY(precondition(ctx, P, p.p, ph.p, n, act));
             {
@@ -978,11 +956,15 @@ extern "C" sait_status sait_bicgstab(sait_ctx ctx, sait_mat A, sait_prec P, cons
                 SAIT_CK(launch_spmv(A, SAIT_F64, ph.p, false, v.p, false, act, s,
                                     group_counter(ctx, SAIT_TIMER_SPMV)));
             }
-            SAIT_CK(dots(ctx, W, n, 1, rh.p, v.p, nullptr, nullptr, nullptr, nullptr, r0, act));
-            launch_k(k_bicg_alpha, 1, 1, 0, s, sc);
-            launch_k(k_bicg_s, egrid, kThreads, 0, s, n, r.p, v.p, sv.p, sc);
-            SAIT_CK(dots(ctx, W, n, 1, sv.p, sv.p, nullptr, nullptr, nullptr, nullptr, r0, act));
-            launch_k(k_bicg_check_s, 1, 1, 0, s, sc);
+            launch_k(k_dots, W.nb, kThreads, 0, s, n, 1, (const double *)rh.p, (const double *)v.p,
+                     (const double *)nullptr, (const double *)nullptr, (const double *)nullptr,
+                     (const double *)nullptr, W.partial, act);
+            launch_k(k_bicg_step, 1, kThreads, 0, s, (int)kStepAlpha, 1, (const double *)W.partial, W.nb, sc,
+                     remaining);
+            launch_k(k_bicg_s_dot, vgrid, kThreads, 0, s, n, (const double *)r.p, (const double *)v.p, sv.p,
+                     (const Scal *)sc, W.partial);
+            launch_k(k_bicg_step, 1, kThreads, 0, s, (int)kStepCheckS, 1, (const double *)W.partial, W.nb, sc,
+                     remaining);
             launch_k(k_bicg_xhalf, egrid, kThreads, 0, s, n, x, ph.p, sc);
             launch_k(k_bicg_xhalf_done, 1, 1, 0, s, sc);
             SAIT_TRY(precondition(ctx, P, sv.p, sh.p, n, act));
@@ -991,11 +973,15 @@ extern "C" sait_status sait_bicgstab(sait_ctx ctx, sait_mat A, sait_prec P, cons
                 SAIT_CK(launch_spmv(A, SAIT_F64, sh.p, false, t.p, false, act, s,
                                     group_counter(ctx, SAIT_TIMER_SPMV)));
             }
-            SAIT_CK(dots(ctx, W, n, 2, t.p, t.p, t.p, sv.p, nullptr, nullptr, r0, act));
-            launch_k(k_bicg_omega, 1, 1, 0, s, sc);
-            launch_k(k_bicg_xr, egrid, kThreads, 0, s, n, x, r.p, ph.p, sh.p, sv.p, t.p, sc);
-            SAIT_CK(dots(ctx, W, n, 1, r.p, r.p, nullptr, nullptr, nullptr, nullptr, r0, act));
-            launch_k(k_bicg_check_r, 1, 1, 0, s, sc, remaining);
+            launch_k(k_dots, W.nb, kThreads, 0, s, n, 2, (const double *)t.p, (const double *)t.p,
+                     (const double *)t.p, (const double *)sv.p, (const double *)nullptr, (const double *)nullptr,
+                     W.partial, act);
+            launch_k(k_bicg_step, 1, kThreads, 0, s, (int)kStepOmega, 2, (const double *)W.partial, W.nb, sc,
+                     remaining);
+            launch_k(k_bicg_xr_dot, vgrid, kThreads, 0, s, n, x, r.p, (const double *)ph.p, (const double *)sh.p,
+                     (const double *)sv.p, (const double *)t.p, (const double *)rh.p, (const Scal *)sc, W.partial);
+            launch_k(k_bicg_step, 1, kThreads, 0, s, (int)kStepCheckR, 2, (const double *)W.partial, W.nb, sc,
+                     remaining);
             SAIT_CK(cudaGetLastError());
             if ((it + 1) % poll == 0 || it + 1 == remaining) {
                 SAIT_TRY(read_scal(ctx, sc, &hs));
