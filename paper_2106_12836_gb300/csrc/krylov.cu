@@ -616,17 +616,6 @@ __global__ void k_bicg_beta2(Scal *sc) {
 }
 
 // ---- PCG kernels (Saad, Algorithm 9.1) ----------------------------------------------
-__global__ void k_pcg_alpha(Scal *sc) {  // after (p, q) in r0
-    if (sc->active == 0) return;
-    const double pq = sc->r0;
-    if (pq == 0.0 || !isfinite(pq)) {
-        sc->state = isfinite(pq) ? 2 : 3;
-        sc->active = 0;
-        return;
-    }
-    sc->alpha = sc->rho / pq;
-}
-
 // x += alpha p; r -= alpha q; partial ||r||^2
 __global__ void __launch_bounds__(kThreads)
 k_pcg_xr(int64_t n, double *x, double *r, const double *__restrict__ p, const double *__restrict__ q,
@@ -644,20 +633,35 @@ k_pcg_xr(int64_t n, double *x, double *r, const double *__restrict__ p, const do
     if (threadIdx.x == 0) partial[blockIdx.x * 3] = s;
 }
 
-__global__ void k_pcg_check(Scal *sc, int remaining) {  // after ||r||^2 in r0
+// one block: the sum of the per-block partials (fixed order), then one scalar
+// step of the iteration: alpha = rho / (p, q), the convergence test on
+// ||r||^2, or beta = (r, z) / rho
+enum { kPcgAlpha = 0, kPcgCheck = 1, kPcgBeta = 2 };
+__global__ void __launch_bounds__(kThreads)
+k_pcg_step(int step, const double *__restrict__ partial, int nb, Scal *sc, int remaining) {
     if (sc->active == 0) return;
-    sc->jdone += 1;
-    const double rn = sqrt(sc->r0);
-    if (!isfinite(rn)) { sc->state = 3; sc->active = 0; return; }
-    if (rn <= sc->tolb) { sc->state = 1; sc->active = 0; return; }
-    if (sc->jdone >= remaining) sc->active = 0;
-}
-
-__global__ void k_pcg_beta(Scal *sc) {  // after (r, z) in r0
-    if (sc->active == 0) return;
-    const double rho = sc->r0;
-    sc->beta_b = rho / sc->rho;
-    sc->rho = rho;
+    double q = 0.0;
+    for (int b = threadIdx.x; b < nb; b += kThreads) q += partial[(int64_t)b * 3];
+    q = block_sum(q);
+    if (threadIdx.x != 0) return;
+    sc->r0 = q;
+    if (step == kPcgAlpha) {
+        if (q == 0.0 || !isfinite(q)) {
+            sc->state = isfinite(q) ? 2 : 3;
+            sc->active = 0;
+            return;
+        }
+        sc->alpha = sc->rho / q;
+    } else if (step == kPcgCheck) {
+        sc->jdone += 1;
+        const double rn = sqrt(q);
+        if (!isfinite(rn)) { sc->state = 3; sc->active = 0; return; }
+        if (rn <= sc->tolb) { sc->state = 1; sc->active = 0; return; }
+        if (sc->jdone >= remaining) sc->active = 0;
+    } else {
+        sc->beta_b = q / sc->rho;
+        sc->rho = q;
+    }
 }
 
 __global__ void k_pcg_p(int64_t n, const double *__restrict__ z, double *p, const Scal *sc) {
@@ -1064,15 +1068,18 @@ extern "C" sait_status sait_pcg(sait_ctx ctx, sait_mat A, sait_prec P, const dou
                 ScopedTimer tm(ctx, SAIT_TIMER_SPMV);
                 SAIT_CK(launch_spmv(A, SAIT_F64, p.p, false, q.p, false, act, s, group_counter(ctx, SAIT_TIMER_SPMV)));
             }
-            SAIT_CK(dots(ctx, W, n, 1, p.p, q.p, nullptr, nullptr, nullptr, nullptr, r0, act));
-            launch_k(k_pcg_alpha, 1, 1, 0, s, sc);
+            launch_k(k_dots, W.nb, kThreads, 0, s, n, 1, (const double *)p.p, (const double *)q.p,
+                     (const double *)nullptr, (const double *)nullptr, (const double *)nullptr,
+                     (const double *)nullptr, W.partial, act);
+            launch_k(k_pcg_step, 1, kThreads, 0, s, (int)kPcgAlpha, (const double *)W.partial, W.nb, sc, (int)maxit);
             launch_k(k_pcg_xr, (unsigned)W.nb, kThreads, 0, s, n, x, r.p, (const double *)p.p, (const double *)q.p,
                      (const Scal *)sc, W.partial);
-            launch_k(k_reduce, 1, kThreads, 0, s, (const double *)W.partial, W.nb, 3, r0, act, nullptr, 0);
-            launch_k(k_pcg_check, 1, 1, 0, s, sc, (int)maxit);
+            launch_k(k_pcg_step, 1, kThreads, 0, s, (int)kPcgCheck, (const double *)W.partial, W.nb, sc, (int)maxit);
             SAIT_TRY(precondition(ctx, P, r.p, z.p, n, act));
-            SAIT_CK(dots(ctx, W, n, 1, r.p, z.p, nullptr, nullptr, nullptr, nullptr, r0, act));
-            launch_k(k_pcg_beta, 1, 1, 0, s, sc);
+            launch_k(k_dots, W.nb, kThreads, 0, s, n, 1, (const double *)r.p, (const double *)z.p,
+                     (const double *)nullptr, (const double *)nullptr, (const double *)nullptr,
+                     (const double *)nullptr, W.partial, act);
+            launch_k(k_pcg_step, 1, kThreads, 0, s, (int)kPcgBeta, (const double *)W.partial, W.nb, sc, (int)maxit);
             launch_k(k_pcg_p, egrid, kThreads, 0, s, n, (const double *)z.p, p.p, (const Scal *)sc);
             SAIT_CK(cudaGetLastError());
             if ((it + 1) % poll == 0 || it + 1 == maxit) {
