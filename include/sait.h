@@ -361,8 +361,12 @@ sait_status sait_prec_destroy(sait_prec P);
  * the nonsymmetric case) ------------------------------------------------ */
 
 /* Restarted GMRES(restart) with right preconditioning (Saad, Algorithm 9.5):
- * Arnoldi with classical Gram-Schmidt and one reorthogonalisation, Givens
- * rotations on the device, x <- x + P (V y) at the end of each cycle.
+ * Arnoldi with classical Gram-Schmidt and one reorthogonalisation, the second
+ * pass of each vector delayed into the next step's sweep (DCGS2: two sweeps
+ * over the basis per step), Givens rotations on the device applied once a
+ * column is final, x <- x + P (V y) at the end of each cycle.  Dots run in
+ * FP32 and updates in double-float on an FP32 (hi, lo) copy of the basis; the
+ * Arnoldi relation holds to ~1e-14 and the basis is orthogonal to ~1e-7.
  * P may be NULL (no preconditioner).  x: in, the initial guess; out, the
  * solution.  Stops when the true relative residual ||b - A x|| / ||b|| <= tol
  * (checked at the end of every cycle; the rotated residual estimate ends a

@@ -312,6 +312,23 @@ def test_gmres_ragged_n(sg, ctx, oracle_lib, restart):
     assert abs(info.iters - ito) <= max(2, 0.02 * ito), (info.iters, ito)
 
 
+@pytest.mark.parametrize("restart", [1, 2, 3])
+def test_gmres_short_restarts(sg, ctx, oracle_lib, restart):
+    """The delayed reorthogonalization at its smallest cycles (the close step finalizes every column)."""
+    A = synth.poisson2d(12)
+    b = oracle_lib.spmv(A, synth.uniform(31, A.n, -1.0, 1.0))
+    Lo, Uo = oracle_lib.ilu0(A)
+    L, U = sg.sait_ilu0(ctx, A.n, dev(A.rp), dev(A.ci), dev(A.va))
+    P = sg.sait_prec_create_sait(ctx, sg.sait_build(ctx, L, True, 3, "rowrel", 1e-3),
+                                 sg.sait_build(ctx, U, False, 3, "rowrel", 1e-3))
+    lo, up = oracle_lib.sait(Lo, 3, "rowrel", 1e-3), oracle_lib.sait(Uo, 3, "rowrel", 1e-3)
+    x, info, st = sg.sait_gmres(ctx, mat(sg, ctx, A), P, dev(b), restart=restart, tol=1e-9, maxit=20000)
+    xo, ito, rro, sto = oracle_lib.gmres(A, b, "sait", lo, up, restart=restart, tol=1e-9, maxit=20000)
+    rel = np.linalg.norm(b - oracle_lib.spmv(A, x.cpu().numpy())) / np.linalg.norm(b)
+    assert st == 0 and sto == 0 and rel <= 1e-9
+    assert abs(info.iters - ito) <= max(3, 0.05 * ito), (info.iters, ito)
+
+
 def test_gmres_nonconvergence_and_zero_rhs(sg, ctx, oracle_lib, c1):
     A, b, _, _ = c1
     Ag = mat(sg, ctx, A)
