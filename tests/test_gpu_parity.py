@@ -229,6 +229,44 @@ def test_spmv_parity_ragged(sg, ctx, oracle_lib):
     assert np.all(np.abs(y - yo) <= 1e-12 * bound)
 
 
+def _banded(n, far, lower, seed):
+    """Triangular rows with the diagonal, a neighbour and one entry at distance
+    `far` (where it exists): the band is exactly `far` wide."""
+    rng = np.random.default_rng(seed)
+    rows, cols = [], []
+    for i in range(n):
+        c = [i]
+        j = i - 1 if lower else i + 1
+        if 0 <= j < n:
+            c.append(j)
+        j = i - far if lower else i + far
+        if 0 <= j < n:
+            c.append(j)
+        c.sort()
+        rows.append(len(c))
+        cols.extend(c)
+    rp = np.zeros(n + 1, np.int32)
+    rp[1:] = np.cumsum(rows)
+    return synth.CSR(n, rp, np.array(cols, np.int32), rng.uniform(-1.0, 1.0, len(cols)))
+
+
+@pytest.mark.parametrize("far,lower", [(65535, True), (70000, False), (300, True)])
+def test_sell_wide_band(sg, ctx, oracle_lib, far, lower):
+    """SELL-32 with columns far from the diagonal (beyond any 16-bit offset)
+    and a ragged tail: the FP64 product bar, then the same after tuning."""
+    T = _banded(70001, far, lower, far)
+    M = mat(sg, ctx, T)
+    x = synth.uniform(9, T.n, -1.0, 1.0)
+    bound = oracle_lib.spmv(synth.CSR(T.n, T.rp, T.ci, np.abs(T.va)), np.abs(x))
+    ref = oracle_lib.spmv(T, x)
+    y = sg.sait_spmv(ctx, M, dev(x)).cpu().numpy()  # SELL-32 until a tuner says otherwise
+    assert np.all(np.abs(y - ref) <= 1e-12 * bound)
+    rep = sg.sait_mat_autotune(ctx, M).as_dict()
+    assert rep["candidates"][0]["format"] == "sell32"
+    y = sg.sait_spmv(ctx, M, dev(x)).cpu().numpy()
+    assert np.all(np.abs(y - ref) <= 1e-12 * bound)
+
+
 def test_exact_ilu_preconditioner(sg, ctx, oracle_lib):
     A = synth.convdiff3d(21)
     L, U = sg.sait_ilu0(ctx, A.n, dev(A.rp), dev(A.ci), dev(A.va))
