@@ -325,6 +325,25 @@ k_dcgs_small(int j, int m, int remaining, int close, double *Hr, double *R, doub
     }
 }
 
+// Exact FP32 -> FP64 widening from the IEEE-754 fields with integer
+// operations only (zero, subnormal, infinite and NaN inputs included, no
+// branch).  On GB300 a hardware float-to-double conversion occupies the narrow
+// FP64 pipe longer than a DFMA; the update sweep below widens three FP32 sums
+// per row, which made it FP64-pipe bound for short bases.
+__device__ __forceinline__ double widen_exact(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu;
+    unsigned m = b & 0x7fffffu;
+    unsigned ed = e + 896u;                                   // normal
+    const int sh = __clz(m | 1u) - 8;                         // subnormal: bring the leading 1 to bit 23
+    const unsigned ms = (m << sh) & 0x7fffffu;
+    ed = e == 0xffu ? 0x7ffu : ed;                            // infinity / NaN
+    ed = e == 0u ? (m ? 897u - (unsigned)sh : 0u) : ed;       // subnormal / zero
+    m = (e == 0u && m) ? ms : m;
+    const unsigned hi = (b & 0x80000000u) | (ed << 20) | (m >> 3);
+    return __hiloint2double((int)hi, (int)((m & 7u) << 29));
+}
+
 // v_j = k1 w1 - V p (written over w1 in column j, with its (hi, lo) pair) and
 // w1' = k2 w - k3 w1 - V r (written over w in column j + 1, with its FP32
 // copy for the next dual sweep); partial[b] = ||w1'||^2 of block b's rows.
@@ -369,10 +388,10 @@ k_dcgs_update2(int64_t n2, const float2 *__restrict__ Vh, const float2 *__restri
         }
         for (; q < j; q++) term(__ldg(Vh + (int64_t)q * ldv2 + i), __ldg(Vl + (int64_t)q * ldv2 + i), q);
         const double2 u = wcol1[i], w = wcol[i];
-        const double v0 = fma(k1, u.x, -(double)S1[0]);
-        const double v1 = fma(k1, u.y, -(double)S1[1]);
-        const double x0 = fma(k2, w.x, fma(-k3, u.x, -df_value(S2[0], E2[0])));
-        const double x1 = fma(k2, w.y, fma(-k3, u.y, -df_value(S2[1], E2[1])));
+        const double v0 = fma(k1, u.x, -widen_exact(S1[0]));
+        const double v1 = fma(k1, u.y, -widen_exact(S1[1]));
+        const double x0 = fma(k2, w.x, fma(-k3, u.x, -(widen_exact(S2[0]) + widen_exact(E2[0]))));
+        const double x1 = fma(k2, w.y, fma(-k3, u.y, -(widen_exact(S2[1]) + widen_exact(E2[1]))));
         float vh0, vl0, vh1, vl1;
         split_pair(v0, vh0, vl0);
         split_pair(v1, vh1, vl1);
