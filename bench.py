@@ -10,11 +10,12 @@ scheduled), the SAIT matrices of L and U (m = 3 series terms, row-relative drop
 
 Printed: one JSON line.  `value` is the time to a 1e-8 solution in ms (lower is
 better); `roofline` is the dominant kernel group of the step, `apply_roofline`
-the SAIT apply (two CSR products) measured live in the timed steps;
+the SAIT apply (two SELL-32 products) measured live in the timed steps;
 `baseline_trisolve` is the same GMRES with the exact level-scheduled ILU
 substitutions; `cpu_baseline` is the FP64 oracle on a bounded sample.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --summarize-launches launches.csv   # per-kernel table of an ncu launch list
 """
 from __future__ import annotations
 
@@ -53,7 +54,33 @@ def parse():
     ap.add_argument("--store", default="f64", choices=["f64", "f32", "bf16", "f32x64", "bf16x64"])
     ap.add_argument("--no-extras", action="store_true", help="skip comparator and sweep runs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--summarize-launches", metavar="CSV",
+                    help="print the per-kernel table of an ncu launch list (--metrics gpu__time_duration.sum --csv)")
     return ap.parse_args()
+
+
+def summarize_launches(path):
+    """Per-kernel launches, total time and share of an ncu launch list."""
+    import collections
+    import csv
+    scale = {"ns": 1e-3, "nsecond": 1e-3, "us": 1.0, "usecond": 1.0, "ms": 1e3, "msecond": 1e3}
+    with open(path) as f:
+        rows = list(csv.reader(f))
+    hdr = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    h = rows[hdr]
+    ki, mi, vi, ui = (h.index(k) for k in ("Kernel Name", "Metric Name", "Metric Value", "Metric Unit"))
+    agg = collections.defaultdict(lambda: [0, 0.0])
+    for r in rows[hdr + 1:]:
+        if len(r) > vi and r[mi] == "gpu__time_duration.sum":
+            name = r[ki].split("(")[0].replace("<unnamed>::", "")
+            agg[name][0] += 1
+            agg[name][1] += float(r[vi].replace(",", "")) * scale[r[ui]]
+    tot = sum(v[1] for v in agg.values())
+    print(f"launches {sum(v[0] for v in agg.values())}, total {tot / 1e3:.1f} ms (serialised, cold cache)")
+    print("| kernel | launches | total ms | share | avg us |\n|---|---|---|---|---|")
+    for k, (c, t) in sorted(agg.items(), key=lambda x: -x[1][1]):
+        if t / tot >= 0.001:
+            print(f"| {k} | {c} | {t / 1e3:.2f} | {100 * t / tot:.1f}% | {t / c:.1f} |")
 
 
 def peaks():
@@ -609,6 +636,9 @@ def run_ours(a):
 
 def main():
     a = parse()
+    if a.summarize_launches:
+        summarize_launches(a.summarize_launches)
+        return
     if a.impl == "reference":
         run_reference(a)
     else:
