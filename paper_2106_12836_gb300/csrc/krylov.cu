@@ -349,7 +349,7 @@ __device__ __forceinline__ double widen_exact(float f) {
 // copy for the next dual sweep); partial[b] = ||w1'||^2 of block b's rows.
 // Two rows per thread (8-byte pair loads), so many resident warps hide the
 // load latency.
-__global__ void __launch_bounds__(kThreads, 6)
+__global__ void __launch_bounds__(kThreads, 4)
 k_dcgs_update2(int64_t n2, const float2 *__restrict__ Vh, const float2 *__restrict__ Vl, int64_t ldv2, int j,
                const double *__restrict__ coef, const double *__restrict__ kk, double2 *wcol1, double2 *wcol,
                float2 *vh_out, float2 *vl_out, float2 *w32, double *partial, const int *gate) {
@@ -376,7 +376,17 @@ k_dcgs_update2(int64_t n2, const float2 *__restrict__ Vh, const float2 *__restri
             df_term(S2[1], E2[1], h.y, l.y, b, bl);
         };
         int q = 0;
-        for (; q + 4 <= j; q += 4) {  // four basis vectors' loads in flight
+        for (; q + 8 <= j; q += 8) {  // eight basis vectors' loads in flight (128 B per thread)
+            float2 h[8], l[8];
+#pragma unroll
+            for (int t = 0; t < 8; t++) {
+                h[t] = __ldg(Vh + (int64_t)(q + t) * ldv2 + i);
+                l[t] = __ldg(Vl + (int64_t)(q + t) * ldv2 + i);
+            }
+#pragma unroll
+            for (int t = 0; t < 8; t++) term(h[t], l[t], q + t);
+        }
+        for (; q + 4 <= j; q += 4) {
             float2 h[4], l[4];
 #pragma unroll
             for (int t = 0; t < 4; t++) {
