@@ -330,6 +330,29 @@ def autotune_workload(sg, ctx, torch, device, stream, P: "Problem", m, store):
             "M_U": sg.sait_mat_autotune(ctx, MU).as_dict()}
 
 
+PARAM_CANDIDATES = [
+    {"m_terms": 2, "drop": "rowrel", "tau": 1e-3}, {"m_terms": 3, "drop": "rowrel", "tau": 1e-3},
+    {"m_terms": 4, "drop": "rowrel", "tau": 1e-3}, {"m_terms": 3, "drop": "rowrel", "tau": 3e-3},
+    {"m_terms": 4, "drop": "rowrel", "tau": 1e-2}, {"m_terms": 4, "drop": "hybrid", "tau": 1e-2, "p": 1},
+    {"m_terms": 3, "drop": "pattern", "p": 1},
+]
+
+
+def optimal_params_workload(sg, ctx, P: "Problem", store):
+    """The optimal parameters of Section 3 on the benchmark problem: each
+    candidate's SAIT build + GMRES(50) solve timed by sait_tune_params."""
+    n = P.A.n
+    d = P.dev
+    L, U = sg.sait_ilu0(ctx, n, d["rp"], d["ci"], d["va"])
+    Am = sg.sait_mat_create_csr(ctx, n, d["rp"], d["ci"], d["va"])
+    _, rep = sg.sait_tune_params(ctx, Am, L, U, d["b"], PARAM_CANDIDATES, solver="gmres", restart=RESTART,
+                                 tol=TOL, maxit=20000, store=store, count_build=True)
+    out = rep.as_dict(PARAM_CANDIDATES)
+    out["chosen_param"] = PARAM_CANDIDATES[rep.chosen] if rep.chosen >= 0 else None
+    out["measure"] = "build_ms + solve_ms (one solve per preconditioner), ILU(0) excluded"
+    return out
+
+
 def adjoint_workload(sg, ctx, torch, device, stream):
     """Forward + backward of the differentiable solve on 64^3 log-normal diffusion."""
     from paper_2106_12836_gb300.autograd import SolveOptions, sait_solve
@@ -622,6 +645,7 @@ def run_ours(a):
         out["eigen"] = eigen_workload(sg, ctx, torch, device, stream)
         out["paper_replica"] = paper_replica_workload(sg, ctx, torch, device, stream)
         out["autotune"] = autotune_workload(sg, ctx, torch, device, stream, P, a.m, a.store)
+        out["optimal_params"] = optimal_params_workload(sg, ctx, P, a.store)
 
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         v, sample, _ = oracle_sample(a.grid, a.m, gpu_iters=iters)

@@ -267,6 +267,53 @@ sait_status sait_batch_autotune(sait_ctx ctx, int64_t n, int32_t nsys, const int
 /* Sets the tile size directly (32 .. 2^20 rows; default 2048). */
 sait_status sait_ctx_set_batch_tile(sait_ctx ctx, int64_t rows);
 
+/* ---- optimal parameters (Section 3, "Optimal parameters") -------------------------
+ * The solver's runtime is iter(M_L, M_U) x (comp(M_L, M_U) + othercomp): a
+ * more accurate SAIT pair (smaller tau, larger p or m) lowers the iteration
+ * count but raises the cost of every apply, so some parameters minimise the
+ * runtime, and they depend on the problem, the solver and the machine.
+ * sait_tune_params measures them instead of guessing. */
+
+typedef enum { SAIT_SOLVER_GMRES = 0, SAIT_SOLVER_BICGSTAB = 1, SAIT_SOLVER_PCG = 2 } sait_solver;
+
+typedef struct {
+    int32_t m_terms; /* series terms, as in sait_build */
+    int32_t pad;
+    sait_drop drop;  /* dropping rule, as in sait_build */
+} sait_param;
+
+#define SAIT_PARAM_MAX 16
+
+typedef struct {
+    int32_t ncand;
+    int32_t chosen;                  /* index of the shortest runtime among the converged
+                                        candidates; -1 when none converged */
+    int32_t status[SAIT_PARAM_MAX];  /* sait_status of the candidate's build, or else of its solve */
+    int32_t iters[SAIT_PARAM_MAX];   /* solver iterations (GMRES: Arnoldi steps) */
+    int64_t nnz[SAIT_PARAM_MAX];     /* nnz(M_L) + nnz(M_U) */
+    float build_ms[SAIT_PARAM_MAX];  /* both sait_build calls, CUDA events on the ctx stream */
+    float solve_ms[SAIT_PARAM_MAX];  /* the solve from x = 0, CUDA events on the ctx stream */
+    double rel_resid[SAIT_PARAM_MAX];
+} sait_param_report;
+
+/* For each of the ncand (1..SAIT_PARAM_MAX) candidates in cand (host array):
+ * builds M_L = SAIT(L) and M_U = SAIT(U) in storage precision store, solves
+ * A x = b from x = 0 with the given solver (restart is used by GMRES only)
+ * preconditioned by z = M_U (M_L r), times both with CUDA events, and frees
+ * the pair.  A candidate's runtime is build_ms + solve_ms when count_build is
+ * nonzero (one solve per preconditioner), else solve_ms (the preconditioner
+ * is reused).  L (unit lower, diagonal stored) and U come from sait_ilu0 or
+ * sait_ilut; A, L, U stay untouched.  b, x: device, n doubles; on return x
+ * holds the chosen candidate's solution.  A candidate whose build runs out
+ * of memory, or whose solve does not converge or breaks down, is recorded
+ * and skipped; any other failure ends the call.  Returns SAIT_OK when at
+ * least one candidate converged, else SAIT_ERR_NOT_CONVERGED (report filled
+ * either way).  Synchronizes. */
+sait_status sait_tune_params(sait_ctx ctx, sait_mat A, sait_mat L, sait_mat U, const double *b, double *x,
+                             sait_solver solver, int32_t restart, double tol, int32_t maxit, int32_t ncand,
+                             const sait_param *cand, sait_dtype store, int32_t count_build,
+                             sait_param_report *report);
+
 /* ---- batched solves ---------------------------------------------------------- */
 
 typedef struct {

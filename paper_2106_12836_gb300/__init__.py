@@ -28,7 +28,8 @@ __all__ = [
     "sait_apply_static", "APPLY_STATIC_MAX_N", "sait_spmm", "sait_apply_multi", "sait_mat_transpose",
     "sait_outer_on_pattern", "sait_bicgstab_batched", "sait_bicgstab_multi", "BatchInfo", "Stats",
     "TIMERS", "lib_path", "EXPORTS", "sait_lobpcg", "sait_pcg", "sait_prec_create_jacobi", "sait_ilut",
-    "sait_mat_autotune", "sait_batch_autotune", "sait_ctx_set_batch_tile",
+    "sait_mat_autotune", "sait_batch_autotune", "sait_ctx_set_batch_tile", "sait_tune_params",
+    "SOLVER", "ParamReport",
 ]
 
 DROP = {"none": 0, "abs": 1, "rowrel": 2, "pattern": 3, "hybrid": 4}
@@ -44,8 +45,10 @@ EXPORTS = [
     "sait_prec_destroy", "sait_gmres", "sait_bicgstab", "sait_ctx_set_timing", "sait_ctx_stats",
     "sait_apply_static", "sait_spmm", "sait_apply_multi", "sait_mat_transpose", "sait_outer_on_pattern",
     "sait_bicgstab_batched", "sait_bicgstab_multi", "sait_lobpcg", "sait_pcg", "sait_prec_create_jacobi", "sait_ilut",
-    "sait_mat_autotune", "sait_batch_autotune", "sait_ctx_set_batch_tile",
+    "sait_mat_autotune", "sait_batch_autotune", "sait_ctx_set_batch_tile", "sait_tune_params",
 ]
+SOLVER = {"gmres": 0, "bicgstab": 1, "pcg": 2}
+PARAM_MAX = 16  # SAIT_PARAM_MAX in include/sait.h
 APPLY_STATIC_MAX_N = 2097152  # SAIT_APPLY_STATIC_MAX_N in include/sait.h
 TIMERS = ["apply", "spmv", "ortho", "build", "ilu", "trisolve"]
 
@@ -84,6 +87,28 @@ class TuneReport(C.Structure):
         return {"chosen": {"format": ("csr", "sell32")[self.format[self.chosen]], "lanes": self.lanes[self.chosen]},
                 "candidates": [{"format": ("csr", "sell32")[self.format[i]], "lanes": self.lanes[i],
                                 "us": round(self.us[i], 2)} for i in range(self.ncand)]}
+
+
+class _Param(C.Structure):
+    _fields_ = [("m_terms", C.c_int32), ("pad", C.c_int32), ("drop", _Drop)]
+
+
+class ParamReport(C.Structure):
+    _fields_ = [("ncand", C.c_int32), ("chosen", C.c_int32), ("status", C.c_int32 * PARAM_MAX),
+                ("iters", C.c_int32 * PARAM_MAX), ("nnz", C.c_int64 * PARAM_MAX),
+                ("build_ms", C.c_float * PARAM_MAX), ("solve_ms", C.c_float * PARAM_MAX),
+                ("rel_resid", C.c_double * PARAM_MAX)]
+
+    def as_dict(self, cands=None):
+        rows = []
+        for i in range(self.ncand):
+            r = {"status": self.status[i], "iters": self.iters[i], "nnz": self.nnz[i],
+                 "build_ms": round(self.build_ms[i], 3), "solve_ms": round(self.solve_ms[i], 3),
+                 "rel_resid": self.rel_resid[i]}
+            if cands is not None:
+                r["param"] = cands[i]
+            rows.append(r)
+        return {"chosen": self.chosen, "candidates": rows}
 
 
 class BatchTuneReport(C.Structure):
@@ -155,6 +180,8 @@ def _L():
             "sait_mat_autotune": [vp, vp, C.POINTER(TuneReport)],
             "sait_batch_autotune": [vp, i64, i32, vp, C.POINTER(BatchTuneReport)],
             "sait_ctx_set_batch_tile": [vp, i64],
+            "sait_tune_params": [vp, vp, vp, vp, vp, vp, C.c_int, i32, d, i32, i32, C.POINTER(_Param), C.c_int,
+                                 i32, C.POINTER(ParamReport)],
         }
         for name, args in sigs.items():
             f = getattr(lib, name)
@@ -573,6 +600,28 @@ def sait_mat_autotune(ctx: Context, M: Mat) -> TuneReport:
     r = TuneReport()
     _check(ctx, _L().sait_mat_autotune(ctx.h, M.h, C.byref(r)), "sait_mat_autotune")
     return r
+
+
+def sait_tune_params(ctx: Context, A: Mat, L: Mat, U: Mat, b: torch.Tensor, candidates,
+                     solver: str = "gmres", restart: int = 50, tol: float = 1e-8, maxit: int = 10000,
+                     store: str = "f64", count_build: bool = True, x: torch.Tensor | None = None):
+    """Time SAIT(L), SAIT(U) + the solve for each candidate and pick the fastest
+    (the optimal parameters of Section 3).  candidates: list of dicts with keys
+    m_terms, drop (name), tau, p.  Returns (x of the chosen candidate, report)."""
+    _vec(b, A.n, "b")
+    x = torch.zeros_like(b) if x is None else _vec(x, A.n, "x")
+    cands = list(candidates)
+    if not 1 <= len(cands) <= PARAM_MAX:
+        raise ValueError(f"1..{PARAM_MAX} candidates expected")
+    arr = (_Param * len(cands))()
+    for i, c in enumerate(cands):
+        arr[i].m_terms = int(c["m_terms"])
+        arr[i].drop = _Drop(DROP[c.get("drop", "rowrel")], int(c.get("p", 0)), float(c.get("tau", 0.0)))
+    r = ParamReport()
+    st = _L().sait_tune_params(ctx.h, A.h, L.h, U.h, _ptr(b), _ptr(x), SOLVER[solver], int(restart), float(tol),
+                               int(maxit), len(cands), arr, DTYPE[store], int(bool(count_build)), C.byref(r))
+    _check(ctx, st, "sait_tune_params")
+    return x, r
 
 
 def sait_batch_autotune(ctx: Context, n: int, sys_ptr: torch.Tensor) -> BatchTuneReport:

@@ -101,3 +101,72 @@ def test_batch_autotune_then_solve(sg, ctx, oracle_lib):
     with pytest.raises(sg.SaitError) as e:
         sg.sait_ctx_set_batch_tile(ctx, 8)
     assert e.value.status == 1
+
+
+def _tune_problem(sg, ctx, oracle_lib, side=24):
+    A = synth.convdiff3d(side)
+    b = oracle_lib.spmv(A, synth.uniform(21, A.n, -1.0, 1.0))
+    L, U = sg.sait_ilu0(ctx, A.n, dev(A.rp), dev(A.ci), dev(A.va))
+    Am = sg.sait_mat_create_csr(ctx, A.n, dev(A.rp), dev(A.ci), dev(A.va))
+    return A, b, L, U, Am
+
+
+CANDS = [{"m_terms": 2, "drop": "rowrel", "tau": 1e-3}, {"m_terms": 3, "drop": "rowrel", "tau": 1e-3},
+         {"m_terms": 4, "drop": "rowrel", "tau": 1e-3}, {"m_terms": 4, "drop": "hybrid", "tau": 1e-2, "p": 1},
+         {"m_terms": 3, "drop": "pattern", "p": 1}, {"m_terms": 1, "drop": "none"}]
+
+
+@pytest.mark.parametrize("solver,count_build", [("gmres", True), ("bicgstab", False)])
+def test_tune_params_picks_the_fastest_and_solves(sg, ctx, oracle_lib, solver, count_build):
+    """Optimal parameters (Section 3): every candidate converges to the
+    tolerance, the report's structure counts are the oracle's SAIT sizes, the
+    chosen candidate has the smallest runtime by the requested measure, and
+    x is a solution (true residual recomputed by the oracle)."""
+    A, b, L, U, Am = _tune_problem(sg, ctx, oracle_lib)
+    Lo, Uo = oracle_lib.ilu0(A)
+    x, rep = sg.sait_tune_params(ctx, Am, L, U, dev(b), CANDS, solver=solver, restart=30, tol=1e-8,
+                                 count_build=count_build)
+    d = rep.as_dict(CANDS)
+    assert rep.ncand == len(CANDS) and all(r["status"] == 0 for r in d["candidates"])
+    for c, r in zip(CANDS, d["candidates"]):
+        assert r["solve_ms"] > 0.0 and r["build_ms"] > 0.0 and r["rel_resid"] <= 1e-8
+        want = (oracle_lib.sait(Lo, c["m_terms"], c["drop"], c.get("tau", 0.0), c.get("p", 0)).nnz
+                + oracle_lib.sait(Uo, c["m_terms"], c["drop"], c.get("tau", 0.0), c.get("p", 0)).nnz)
+        assert abs(r["nnz"] - want) <= 2  # entries exactly at a drop threshold may fall either way
+    cost = [r["solve_ms"] + (r["build_ms"] if count_build else 0.0) for r in d["candidates"]]
+    assert rep.chosen == int(np.argmin(cost))
+    # more series terms at the same threshold never need more iterations here
+    its = [r["iters"] for r in d["candidates"]]
+    assert its[2] <= its[1] <= its[0] <= its[5]
+    xr = x.cpu().numpy()
+    assert np.linalg.norm(b - oracle_lib.spmv(A, xr)) <= 1e-8 * np.linalg.norm(b) * 1.0001
+
+
+def test_tune_params_nonconvergence(sg, ctx, oracle_lib):
+    """Candidates that miss the tolerance within maxit are recorded and
+    skipped; when none converges the call reports SAIT_ERR_NOT_CONVERGED."""
+    A, b, L, U, Am = _tune_problem(sg, ctx, oracle_lib, side=16)
+    cands = [{"m_terms": 1, "drop": "none"}, {"m_terms": 4, "drop": "rowrel", "tau": 1e-4}]
+    with pytest.raises(sg.SaitError) as e:  # 5 Arnoldi steps are far from enough (oracle: 65 and 18)
+        sg.sait_tune_params(ctx, Am, L, U, dev(b), cands, solver="gmres", restart=10, tol=1e-8, maxit=5)
+    assert e.value.status == 6
+
+
+def test_tune_params_partial_convergence(sg, ctx, oracle_lib):
+    A, b, L, U, Am = _tune_problem(sg, ctx, oracle_lib, side=16)
+    NOT_CONVERGED = 6
+    # oracle GMRES(40) steps to 1e-8: 65 with one term (no preconditioning), 18 with the m=4 pair
+    cands = [{"m_terms": 1, "drop": "none"}, {"m_terms": 4, "drop": "rowrel", "tau": 1e-4}]
+    x, rep = sg.sait_tune_params(ctx, Am, L, U, dev(b), cands, solver="gmres", restart=40, tol=1e-8, maxit=40)
+    assert rep.status[0] == NOT_CONVERGED and rep.status[1] == 0 and rep.chosen == 1
+    xr = x.cpu().numpy()
+    assert np.linalg.norm(b - oracle_lib.spmv(A, xr)) <= 1e-8 * np.linalg.norm(b) * 1.0001
+
+
+def test_tune_params_errors(sg, ctx, oracle_lib):
+    A, b, L, U, Am = _tune_problem(sg, ctx, oracle_lib, side=8)
+    with pytest.raises(ValueError):
+        sg.sait_tune_params(ctx, Am, L, U, dev(b), [])
+    with pytest.raises(sg.SaitError) as e:  # m_terms = 0 is invalid: the call stops at once
+        sg.sait_tune_params(ctx, Am, L, U, dev(b), [{"m_terms": 0, "drop": "none"}])
+    assert e.value.status == 1
