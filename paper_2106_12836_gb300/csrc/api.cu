@@ -317,7 +317,8 @@ static sait_status apply_pair(sait_ctx ctx, sait_mat ML, sait_mat MU, const doub
     ScopedTimer tm(ctx, SAIT_TIMER_APPLY);
     SAIT_CK(launch_spmv(ML, ML->store, r, false, w, !f64, active, ctx->stream,
                         group_counter(ctx, SAIT_TIMER_APPLY)));
-    SAIT_CK(launch_spmv(MU, MU->store, w, !f64, z, false, active, ctx->stream));
+    // M_U's product may start while M_L's drains (its SELL kernel waits for it first)
+    SAIT_CK(launch_spmv(MU, MU->store, w, !f64, z, false, active, ctx->stream, nullptr, true));
     return SAIT_OK;
 }
 

@@ -50,6 +50,32 @@ inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t sme
     ++g_sait_launches;
 }
 
+// Programmatic dependent launch: the kernel may be scheduled while its
+// predecessor in the stream drains; it must call pdl_wait() before touching
+// any memory the predecessor writes.  A dependent grid starts only after every
+// block of the predecessor has called pdl_trigger() or exited, so waiting
+// blocks never hold back the predecessor.  Both calls are no-ops in a kernel
+// launched without the attribute.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    ++g_sait_launches;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Event pair around a group of launches on the context stream (timing on only).
 struct ScopedTimer {
     sait_ctx ctx;
@@ -284,7 +310,7 @@ cudaError_t scan_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s)
 int choose_lanes(int64_t n, int64_t nnz);
 // y = A x for the value storage of A; x/y element types given by flags.
 cudaError_t launch_spmv(const sait_mat_s *A, sait_dtype store, const void *x, bool x_f32, void *y,
-                        bool y_f32, const int *active, cudaStream_t s, int *calls = nullptr);
+                        bool y_f32, const int *active, cudaStream_t s, int *calls = nullptr, bool pdl = false);
 cudaError_t cast_values(const double *src, float *d32, __nv_bfloat16 *d16, int64_t nnz,
                         cudaStream_t s);
 
@@ -298,7 +324,7 @@ sait_status apply_multi_impl(sait_ctx ctx, sait_mat ML, sait_mat MU, int k, cons
 sait_status mat_prepare_sell(sait_ctx ctx, sait_mat M, sait_dtype store);
 bool sell_ready(const sait_mat_s *A, sait_dtype store);
 cudaError_t launch_spmv_sell(const sait_mat_s *A, sait_dtype store, const void *x, bool x_f32, void *y,
-                             bool y_f32, const int *active, cudaStream_t s, int *calls);
+                             bool y_f32, const int *active, cudaStream_t s, int *calls, bool pdl = false);
 
 // levels.cu
 sait_status build_levels(sait_ctx ctx, const int32_t *rp, const int32_t *ci, int64_t n, bool lower,

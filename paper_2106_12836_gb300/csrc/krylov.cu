@@ -74,6 +74,8 @@ k_dots(int64_t n, int nd, const double *__restrict__ x0, const double *__restric
 __global__ void __launch_bounds__(kThreads)
 k_reduce(const double *__restrict__ partial, int nb, int stride, double *out, const int *active, double *Hj,
          int first) {
+    pdl_wait();
+    pdl_trigger();
     if (active && *active == 0) return;
     const int q = blockIdx.x;
     double s = 0.0;
@@ -188,6 +190,8 @@ __device__ __forceinline__ void dual_tail(int rem, int64_t n4, const float4 *V, 
 __global__ void __launch_bounds__(kThreads)
 k_dcgs_dot(int64_t n4, const float4 *__restrict__ V, int64_t ldv4, int j, const float4 *__restrict__ U,
            const double2 *__restrict__ W, double *partial, int ldp, const int *gate) {
+    pdl_wait();
+    pdl_trigger();
     if (gate && *gate == 0) return;
     __shared__ double red[kThreads / 32][2 * kDCH + 1];
     int q0 = 0;
@@ -240,6 +244,8 @@ __global__ void __launch_bounds__(kThreads)
 k_dcgs_small(int j, int m, int remaining, int close, double *Hr, double *R, double *cs, double *sn, double *g,
              Scal *sc, const double *__restrict__ dots, const double *__restrict__ partial, int nb, double *coef,
              double *kk, int *calls) {
+    pdl_wait();
+    pdl_trigger();
     if (sc->active == 0) return;
     __shared__ double c2[kMaxRestart + 1], dh[kMaxRestart + 1], t[kMaxRestart + 2], hc[kMaxRestart + 2];
     __shared__ double sh_gamma, sh_eta;
@@ -353,6 +359,8 @@ __global__ void __launch_bounds__(kThreads, 4)
 k_dcgs_update2(int64_t n2, const float2 *__restrict__ Vh, const float2 *__restrict__ Vl, int64_t ldv2, int j,
                const double *__restrict__ coef, const double *__restrict__ kk, double2 *wcol1, double2 *wcol,
                float2 *vh_out, float2 *vl_out, float2 *w32, double *partial, const int *gate) {
+    pdl_wait();
+    pdl_trigger();
     if (gate && *gate == 0) return;
     __shared__ float ph[kMaxRestart + 1], rh[kMaxRestart + 1], rl[kMaxRestart + 1];
     for (int q = threadIdx.x; q < j; q += kThreads) {
@@ -860,13 +868,14 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
             ScopedTimer tm(ctx, SAIT_TIMER_ORTHO);
             launch_k(k_dcgs_dot, nb_dot, kThreads, 0, s, n4, Vh4, n4, j, (const float4 *)w32.p, wn, W.partial,
                      ldp2, act);
-            launch_k(k_reduce, 2 * j + 1, kThreads, 0, s, (const double *)W.partial, nb_dot, ldp2, yd.p, act,
-                     (double *)nullptr, 0);
-            launch_k(k_dcgs_small, 1, kThreads, 0, s, j, m, remaining, close, H.p, R.p, cs.p, sn.p, g.p, sc,
-                     (const double *)yd.p, (const double *)W.partial2, nb_upd, coef.p, kk.p,
-                     group_counter(ctx, SAIT_TIMER_ORTHO));
+            // reduce, small and update may each start while their predecessor drains
+            (void)launch_pdl(k_reduce, 2 * j + 1, kThreads, 0, s, (const double *)W.partial, nb_dot, ldp2, yd.p,
+                             act, (double *)nullptr, 0);
+            (void)launch_pdl(k_dcgs_small, 1, kThreads, 0, s, j, m, remaining, close, H.p, R.p, cs.p, sn.p, g.p,
+                             sc, (const double *)yd.p, (const double *)W.partial2, nb_upd, coef.p, kk.p,
+                             group_counter(ctx, SAIT_TIMER_ORTHO));
             if (!close)
-                launch_k(k_dcgs_update2, nb_upd, kThreads, 0, s, 2 * n4, (const float2 *)V32.p,
+                (void)launch_pdl(k_dcgs_update2, nb_upd, kThreads, 0, s, 2 * n4, (const float2 *)V32.p,
                          (const float2 *)VL.p, 2 * n4, j, (const double *)coef.p, (const double *)kk.p,
                          (double2 *)wj, (double2 *)(V.p + (size_t)(j + 1) * ldv),
                          (float2 *)(V32.p + (size_t)j * ldv), (float2 *)(VL.p + (size_t)j * ldv), (float2 *)w32.p,

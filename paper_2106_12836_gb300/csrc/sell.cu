@@ -37,6 +37,8 @@ k_spmv_sell(int64_t n, int64_t nslices, const int64_t *__restrict__ soff, const 
             const TV *__restrict__ va, const TX *__restrict__ x, TY *__restrict__ y,
             const int *__restrict__ active, int *calls) {
     constexpr int kU = Ahead<TV>::value;
+    pdl_wait();
+    pdl_trigger();
     if (active && *active == 0) return;
     if (calls && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(calls, 1);
     const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -111,8 +113,11 @@ __global__ void k_sell_fill(int64_t n, int64_t nslices, const int32_t *__restric
 
 template <typename TV, typename TA, typename TX, typename TY>
 cudaError_t sell_launch(const sait_mat_s *A, const TV *va, const TX *x, TY *y, const int *active,
-                        cudaStream_t s, int *calls) {
+                        cudaStream_t s, int *calls, bool pdl) {
     const unsigned grid = (unsigned)cdiv(A->nslices * 32, 256);
+    if (pdl)
+        return launch_pdl(k_spmv_sell<TV, TA, TX, TY>, grid, 256, 0, s, A->n, A->nslices, (const int64_t *)A->soff,
+                          (const int32_t *)A->sci, va, x, y, active, calls);
     launch_k(k_spmv_sell<TV, TA, TX, TY>, grid, 256, 0, s, A->n, A->nslices, (const int64_t *)A->soff,
              (const int32_t *)A->sci, va, x, y, active, calls);
     return cudaGetLastError();
@@ -120,13 +125,13 @@ cudaError_t sell_launch(const sait_mat_s *A, const TV *va, const TX *x, TY *y, c
 
 template <typename TV, typename TA>
 cudaError_t sell_xy(const sait_mat_s *A, const TV *va, const void *x, bool x_f32, void *y, bool y_f32,
-                    const int *active, cudaStream_t s, int *calls) {
+                    const int *active, cudaStream_t s, int *calls, bool pdl) {
     if (x_f32) {
-        if (y_f32) return sell_launch<TV, TA>(A, va, (const float *)x, (float *)y, active, s, calls);
-        return sell_launch<TV, TA>(A, va, (const float *)x, (double *)y, active, s, calls);
+        if (y_f32) return sell_launch<TV, TA>(A, va, (const float *)x, (float *)y, active, s, calls, pdl);
+        return sell_launch<TV, TA>(A, va, (const float *)x, (double *)y, active, s, calls, pdl);
     }
-    if (y_f32) return sell_launch<TV, TA>(A, va, (const double *)x, (float *)y, active, s, calls);
-    return sell_launch<TV, TA>(A, va, (const double *)x, (double *)y, active, s, calls);
+    if (y_f32) return sell_launch<TV, TA>(A, va, (const double *)x, (float *)y, active, s, calls, pdl);
+    return sell_launch<TV, TA>(A, va, (const double *)x, (double *)y, active, s, calls, pdl);
 }
 
 }  // namespace
@@ -194,13 +199,13 @@ bool sell_ready(const sait_mat_s *A, sait_dtype store) {
 }
 
 cudaError_t launch_spmv_sell(const sait_mat_s *A, sait_dtype store, const void *x, bool x_f32, void *y,
-                             bool y_f32, const int *active, cudaStream_t s, int *calls) {
+                             bool y_f32, const int *active, cudaStream_t s, int *calls, bool pdl) {
     switch (store) {
-        case SAIT_F32: return sell_xy<float, float>(A, A->sva32, x, x_f32, y, y_f32, active, s, calls);
-        case SAIT_BF16: return sell_xy<__nv_bfloat16, float>(A, A->sva16, x, x_f32, y, y_f32, active, s, calls);
-        case SAIT_F32_X64: return sell_xy<float, DF>(A, A->sva32, x, x_f32, y, y_f32, active, s, calls);
+        case SAIT_F32: return sell_xy<float, float>(A, A->sva32, x, x_f32, y, y_f32, active, s, calls, pdl);
+        case SAIT_BF16: return sell_xy<__nv_bfloat16, float>(A, A->sva16, x, x_f32, y, y_f32, active, s, calls, pdl);
+        case SAIT_F32_X64: return sell_xy<float, DF>(A, A->sva32, x, x_f32, y, y_f32, active, s, calls, pdl);
         case SAIT_BF16_X64:
-            return sell_xy<__nv_bfloat16, DF>(A, A->sva16, x, x_f32, y, y_f32, active, s, calls);
-        default: return sell_xy<double, double>(A, A->sva64, x, x_f32, y, y_f32, active, s, calls);
+            return sell_xy<__nv_bfloat16, DF>(A, A->sva16, x, x_f32, y, y_f32, active, s, calls, pdl);
+        default: return sell_xy<double, double>(A, A->sva64, x, x_f32, y, y_f32, active, s, calls, pdl);
     }
 }

@@ -93,8 +93,9 @@ int choose_lanes(int64_t n, int64_t nnz) {
 }
 
 cudaError_t launch_spmv(const sait_mat_s *A, sait_dtype store, const void *x, bool x_f32, void *y,
-                        bool y_f32, const int *active, cudaStream_t s, int *calls) {
-    if (!A->force_csr && sell_ready(A, store)) return launch_spmv_sell(A, store, x, x_f32, y, y_f32, active, s, calls);
+                        bool y_f32, const int *active, cudaStream_t s, int *calls, bool pdl) {
+    if (!A->force_csr && sell_ready(A, store))
+        return launch_spmv_sell(A, store, x, x_f32, y, y_f32, active, s, calls, pdl);
     switch (store) {
         case SAIT_F32: return launch_xy<float, float>(A, A->va32, x, x_f32, y, y_f32, active, s, calls);
         case SAIT_BF16: return launch_xy<__nv_bfloat16, float>(A, A->va16, x, x_f32, y, y_f32, active, s, calls);
