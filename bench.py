@@ -390,7 +390,7 @@ TRAFFIC = {"128:3:f64": {"apply": round(115.7e6 * 20726144 / 8709408 * 2)}}
 
 
 def ortho_bytes(n, iters, restart):
-    """Algorithmic bytes of the CGS2 + norm + scale work of `iters` Arnoldi steps."""
+    """Algorithmic bytes of the DCGS2 Gram-Schmidt work of `iters` Arnoldi steps."""
     total, left = 0, iters
     while left > 0:
         steps = min(left, restart)

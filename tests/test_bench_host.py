@@ -1,0 +1,64 @@
+"""Host logic of bench.py that needs no GPU: the algorithmic byte models
+behind the roofline numerators and the launch-list summary.
+
+Bars: the byte models equal the per-unit figures written out by hand
+(entries x (value + column bytes) + row pointers + vectors; DCGS2 step j:
+12 j n + 56 n), exactly; the launch summary converts units, counts launches
+and reports shares that add up.
+"""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_apply_bytes_by_hand():
+    n, nl, nu = 2097152, 20726144, 20726144  # 128^3 SAIT pair, m_terms = 3, rowrel 1e-3
+    # FP64 values + int32 columns, two row-pointer arrays, r in, w out and in, z out
+    assert bench.apply_bytes(n, nl, nu, "f64") == (nl + nu) * 12 + 2 * 4 * (n + 1) + 4 * 8 * n == 581313544
+    # FP32 values: the intermediate w is FP32 (4 B out + 4 B in)
+    assert bench.apply_bytes(n, nl, nu, "f32") == (nl + nu) * 8 + 2 * 4 * (n + 1) + (8 + 4 + 4 + 8) * n
+    assert bench.apply_bytes(n, nl, nu, "bf16") == (nl + nu) * 6 + 2 * 4 * (n + 1) + 24 * n
+    # *_X64 keep an FP64 intermediate
+    assert bench.apply_bytes(n, nl, nu, "f32x64") == (nl + nu) * 8 + 2 * 4 * (n + 1) + 32 * n
+
+
+def test_spmv_a_bytes_by_hand():
+    class A:
+        n, nnz = 2097152, 14581760
+    assert bench.spmv_a_bytes(A) == 14581760 * 12 + 4 * (2097152 + 1) + 16 * 2097152 == 216924164
+
+
+def test_ortho_bytes_closed_form():
+    n, m = 1000, 50
+    step = lambda j: 12 * j * n + 56 * n  # noqa: E731
+    # full cycles restart at j = 0
+    assert bench.ortho_bytes(n, 2 * m, m) == 2 * sum(step(j) for j in range(m))
+    assert bench.ortho_bytes(n, m, m) == 12 * n * m * (m - 1) // 2 + 56 * n * m
+    # a partial last cycle
+    assert bench.ortho_bytes(n, m + 7, m) == sum(step(j) for j in range(m)) + sum(step(j) for j in range(7))
+    # the benchmark's 172 steps at 128^3: the per-step figure in the bench line
+    assert int(bench.ortho_bytes(2097152, 172, 50) / 172) == 688938817
+
+
+def test_summarize_launches(tmp_path, capsys):
+    hdr = '"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"\n'
+    rows = [
+        '"0","void <unnamed>::k_spmv_sell<double>(long)","gpu__time_duration.sum","us","30"\n',
+        '"1","<unnamed>::k_dcgs_dot(long)","gpu__time_duration.sum","ns","10,000"\n',
+        '"2","void <unnamed>::k_spmv_sell<double>(long)","gpu__time_duration.sum","usecond","20"\n',
+        '"3","k_other(int)","gpu__time_duration.sum","ms","0.04"\n',
+        '"4","k_other(int)","dram__bytes_read.sum","byte","123"\n',  # other metrics are ignored
+    ]
+    p = tmp_path / "launches.csv"
+    p.write_text("==PROF== Connected\n" + hdr + "".join(rows))
+    bench.summarize_launches(str(p))
+    out = capsys.readouterr().out.splitlines()
+    assert out[0] == "launches 4, total 0.1 ms (serialised, cold cache)"
+    table = {line.split(" | ")[0].lstrip("| "): line for line in out[3:]}
+    assert "void k_spmv_sell<double>" in table and table["void k_spmv_sell<double>"].endswith("| 2 | 0.05 | 50.0% | 25.0 |")
+    assert table["k_other"].endswith("| 1 | 0.04 | 40.0% | 40.0 |")
+    assert table["k_dcgs_dot"].endswith("| 1 | 0.01 | 10.0% | 10.0 |")
