@@ -383,10 +383,10 @@ def apply_bytes(n, nnz_l, nnz_u, store):
 
 
 # DRAM bytes (read + write) per launch from ncu captures, scaled to the benchmark size
-# where the capture ran on a smaller grid (profiles/dcgs2_and_sell_kernels_ncu.md):
-# one SELL-32 FP64 product of a 96^3 SAIT factor (8,709,408 entries) moved 115.7 MB;
+# where the capture ran on a smaller grid (profiles/spmv_sell_dram_traffic_convdiff96.md):
+# one SELL-32 FP64 product of a 96^3 SAIT factor (8,709,408 entries) moved 113,786,880 B;
 # scaled by entries to the two 128^3 factors (20,726,144 each) of one apply.
-TRAFFIC = {"128:3:f64": {"apply": round(115.7e6 * 20726144 / 8709408 * 2)}}
+TRAFFIC = {"128:3:f64": {"apply": round(113786880 * 20726144 / 8709408 * 2)}}
 
 
 def ortho_bytes(n, iters, restart):
