@@ -305,8 +305,8 @@ typedef struct {
  * is reused).  L (unit lower, diagonal stored) and U come from sait_ilu0 or
  * sait_ilut; A, L, U stay untouched.  b, x: device, n doubles; on return x
  * holds the chosen candidate's solution.  A candidate whose build runs out
- * of memory, or whose solve does not converge or breaks down, is recorded
- * and skipped; any other failure ends the call.  Returns SAIT_OK when at
+ * of memory, or whose solve does not converge, breaks down or meets a
+ * non-finite value, is recorded and skipped; any other failure ends the call.  Returns SAIT_OK when at
  * least one candidate converged, else SAIT_ERR_NOT_CONVERGED (report filled
  * either way).  Synchronizes. */
 sait_status sait_tune_params(sait_ctx ctx, sait_mat A, sait_mat L, sait_mat U, const double *b, double *x,

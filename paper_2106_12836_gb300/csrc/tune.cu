@@ -124,7 +124,8 @@ extern "C" sait_status sait_tune_params(sait_ctx ctx, sait_mat A, sait_mat L, sa
             if (solver == SAIT_SOLVER_GMRES) st = sait_gmres(ctx, A, P, b, x, restart, tol, maxit, &info);
             else if (solver == SAIT_SOLVER_BICGSTAB) st = sait_bicgstab(ctx, A, P, b, x, tol, maxit, &info);
             else st = sait_pcg(ctx, A, P, b, x, tol, maxit, &info);
-            const bool ran = st == SAIT_OK || st == SAIT_ERR_NOT_CONVERGED || st == SAIT_ERR_BREAKDOWN;
+            const bool ran = st == SAIT_OK || st == SAIT_ERR_NOT_CONVERGED || st == SAIT_ERR_BREAKDOWN ||
+                             st == SAIT_ERR_NONFINITE;
             e = cudaEventRecord(ev[2], s);
             if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
             float b_ms = 0.0f, s_ms = 0.0f;
@@ -154,7 +155,8 @@ extern "C" sait_status sait_tune_params(sait_ctx ctx, sait_mat A, sait_mat L, sa
                     return ctx_cuda(ctx, e, "sait_tune_params", __FILE__, __LINE__);
                 }
             }
-        } else if (st != SAIT_ERR_OOM && st != SAIT_ERR_NOT_CONVERGED && st != SAIT_ERR_BREAKDOWN) {
+        } else if (st != SAIT_ERR_OOM && st != SAIT_ERR_NOT_CONVERGED && st != SAIT_ERR_BREAKDOWN &&
+                   st != SAIT_ERR_NONFINITE) {
             destroy_events();
             return st;  // invalid input or a CUDA failure: stop (the message is in ctx)
         }
