@@ -40,3 +40,70 @@ def test_status_strings_without_gpu():
     assert sg.sait_status_string(0) == "ok"
     assert "triangular" in sg.sait_status_string(2)
     assert sg.sait_status_string(99) == "unknown status"
+
+
+# (C struct, ctypes class name in the binding, fields)
+LAYOUTS = [
+    ("sait_csr", "_Csr", ["n", "nnz", "row_ptr", "col", "val"]),
+    ("sait_drop", "_Drop", ["kind", "p", "tau"]),
+    ("sait_info", "Info", ["iters", "cycles", "reorth_steps", "pad", "rel_resid"]),
+    ("sait_stats", "Stats", ["launches", "ms", "calls"]),
+    ("sait_batch_info", "BatchInfo", ["nsys", "converged", "max_iters", "graph_replays", "max_rel_resid"]),
+    ("sait_tune_report", "TuneReport", ["ncand", "chosen", "format", "lanes", "us"]),
+    ("sait_batch_tune_report", "BatchTuneReport", ["ncand", "chosen", "tile_rows", "us"]),
+    ("sait_param", "_Param", ["m_terms", "pad", "drop"]),
+    ("sait_param_report", "ParamReport",
+     ["ncand", "chosen", "status", "iters", "nnz", "build_ms", "solve_ms", "rel_resid"]),
+]
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct the binding passes by pointer has the header's size and
+    field offsets (a C program compiled against include/sait.h prints them)."""
+    import shutil
+    import subprocess
+    import paper_2106_12836_gb300 as sg
+    cc = shutil.which("gcc") or shutil.which("cc")
+    assert cc, "a C compiler is needed to read the header's layouts"
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "sait.h"', "int main(void) {"]
+    for cname, _, fields in LAYOUTS:
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in fields:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c = {}
+    for line in out:
+        if line:
+            name, key, val = line.split()
+            c[(name, key)] = int(val)
+    for cname, pyname, fields in LAYOUTS:
+        cls = getattr(sg, pyname)
+        assert ctypes.sizeof(cls) == c[(cname, "size")], cname
+        for f in fields:
+            assert getattr(cls, f).offset == c[(cname, f)], (cname, f)
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: with the library missing, the first call raises."""
+    import pytest
+    import paper_2106_12836_gb300 as sg
+    monkeypatch.setattr(sg, "_lib", None)
+    monkeypatch.setattr(sg._build, "LIB", str(tmp_path / "missing" / "libsait.so"))
+    with pytest.raises(ImportError):
+        sg.sait_status_string(0)
+
+
+def test_binding_rejects_host_tensors():
+    """Vectors must be device tensors: host memory is refused before any call."""
+    import pytest
+    import torch
+    import paper_2106_12836_gb300 as sg
+    with pytest.raises(ValueError):
+        sg._vec(torch.zeros(4, dtype=torch.float64), 4, "x")
+    with pytest.raises(ValueError):
+        sg._ptr(torch.zeros(4, dtype=torch.float64))
