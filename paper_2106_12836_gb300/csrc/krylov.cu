@@ -239,7 +239,7 @@ __device__ double givens_column(int c, int m, const double *Hr, double *R, doubl
 // One block.  dots = [c' (j), d' (j), delta'] (unscaled); partial/nb: the
 // squared norm of the tentative vector by blocks (j >= 1; eta = sc->beta at
 // j = 0).  close: only make column j-1 final (the end of a cycle).
-// Writes coef = [p (j), r (j)] and kk = [k1, k2, k3] for k_dcgs_update.
+// Writes coef = [p (j), r (j)] and kk = [k1, k2, k3] for k_dcgs_update2.
 __global__ void __launch_bounds__(kThreads)
 k_dcgs_small(int j, int m, int remaining, int close, double *Hr, double *R, double *cs, double *sn, double *g,
              Scal *sc, const double *__restrict__ dots, const double *__restrict__ partial, int nb, double *coef,
