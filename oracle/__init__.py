@@ -76,6 +76,9 @@ def _L():
         _lib.ora_free.argtypes = [C.POINTER(_Mat)]
         _lib.ora_jacobi.argtypes = [i64, i32p, i32p, dp, C.c_int, dp, dp]
         _lib.ora_ilut.argtypes = [i64, i32p, i32p, dp, C.c_double, C.c_int, C.POINTER(_Mat)]
+        _lib.ora_iluk.argtypes = [i64, i32p, i32p, dp, C.c_int, C.POINTER(_Mat),
+                                  C.POINTER(C.POINTER(C.c_int32))]
+        _lib.ora_free_i32.argtypes = [C.POINTER(C.c_int32)]
         solver = [i64, i32p, i32p, dp, C.POINTER(_Prec), dp, dp]
         _lib.ora_gmres.argtypes = solver + [C.c_int, C.c_double, C.c_int,
                                             C.POINTER(C.c_int), C.POINTER(C.c_double)]
@@ -153,6 +156,27 @@ def ilut(A: CSR, tau: float, lfil: int) -> tuple[CSR, CSR]:
     if st:
         raise OracleError("ilut", st)
     return split_lu(_take(out))
+
+
+def iluk(A: CSR, p: int, levels: bool = False):
+    """Level-of-fill ILU(p) factors (Saad, Algorithm 10.5), split as ilu0's.
+
+    With levels=True also returns the level of fill of every entry of the
+    combined factor (strict L part, then U with its diagonal, CSR order)."""
+    rp, ci, va = _csr_args(A)
+    out = _Mat()
+    lev = C.POINTER(C.c_int32)()
+    st = _L().ora_iluk(A.n, _p(rp), _p(ci), _p(va), int(p), C.byref(out), C.byref(lev))
+    if st:
+        raise OracleError("iluk", st)
+    nnz = int(out.nnz)
+    try:
+        lv = np.ctypeslib.as_array(lev, shape=(nnz,)).copy() if nnz else np.zeros(0, np.int32)
+    finally:
+        _L().ora_free_i32(lev)
+    LU = _take(out)
+    L, U = split_lu(LU)
+    return (L, U, LU, lv) if levels else (L, U)
 
 
 def split_lu(LU: CSR) -> tuple[CSR, CSR]:

@@ -276,6 +276,97 @@ done:
 }
 
 /* ------------------------------------------------------------------------ */
+/* ILU(p), level-of-fill incomplete LU (Saad, Iterative Methods for Sparse    */
+/* Linear Systems, 2nd ed., Section 10.3.3, Algorithm 10.5).  The paper      */
+/* feeds level-0 and level-1 ILU factors to SAIT (Section 4, Tables          */
+/* runtime_SAIT and runtime_Jacobi).                                         */
+/* Every structural entry of A has level 0.  Row i:                          */
+/*   w := a_i*, lev_ij := 0 on A's pattern (infinite elsewhere)              */
+/*   for k < i in increasing order with lev_ik <= p (fill included):         */
+/*       w_k := w_k / u_kk                                                   */
+/*       w_j := fma(-w_k, u_kj, w_j)  for u_kj stored, j > k                 */
+/*       lev_ij := min(lev_ij, lev_ik + lev_kj + 1)                          */
+/*   keep the entries with lev_ij <= p (the diagonal included).              */
+/* A level only decreases while the row is processed, and every update of   */
+/* lev_ik comes from a column before k, so lev_ik is final when k is         */
+/* reached.  Output as ora_ilut: strict lower part of L (unit diagonal       */
+/* implied) and U with its diagonal, columns ascending, plus the level of    */
+/* every stored entry in lev_out (may be NULL).  The diagonal must be in     */
+/* A's pattern; a zero or non-finite pivot returns ORA_ZERO_PIVOT.  p = 0 is  */
+/* ILU(0) (same fma chains), and p >= n is the complete LU without pivoting. */
+/* ------------------------------------------------------------------------ */
+int ora_iluk(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, int p, ora_mat *out,
+             int32_t **lev_out)
+{
+    if (n < 0 || p < 0) return ORA_INVALID;
+    const int32_t INF = 0x7fffffff;
+    ora_mat LU = {0};
+    int64_t lcap = rp[n] * 2 + 16, lnnz = 0;
+    int32_t *levs = (int32_t *)malloc((size_t)lcap * sizeof(int32_t));   /* level of each stored entry */
+    double *w = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    int32_t *lev = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    int32_t *list = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    int64_t *udiag = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int st = ORA_OK;
+    if (!levs || !w || !lev || !list || !udiag || mat_init(&LU, n, lcap)) { st = ORA_OOM; goto done; }
+    for (int64_t i = 0; i < n; i++) lev[i] = INF;
+    for (int64_t i = 0; i < n; i++) {
+        int nw = 0, have_d = 0;
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
+            if (ci[e] < 0 || ci[e] >= n || (e > rp[i] && ci[e] <= ci[e - 1])) { st = ORA_INVALID; goto done; }
+            w[ci[e]] = va[e];
+            lev[ci[e]] = 0;
+            list[nw++] = ci[e];
+            if (ci[e] == i) have_d = 1;
+        }
+        if (!have_d) { st = ORA_ZERO_PIVOT; goto done; }
+        int64_t k = -1;
+        for (;;) {
+            int64_t next = n;   /* the smallest column above k and below i in the row */
+            for (int t = 0; t < nw; t++)
+                if (list[t] > k && list[t] < i && list[t] < next) next = list[t];
+            if (next == n) break;
+            k = next;
+            if (lev[k] > p) continue;
+            w[k] = w[k] / LU.va[udiag[k]];
+            for (int64_t f = udiag[k] + 1; f < LU.rp[k + 1]; f++) {
+                int32_t j = LU.ci[f];
+                if (lev[j] == INF) { w[j] = 0.0; list[nw++] = j; }
+                w[j] = fma(-w[k], LU.va[f], w[j]);
+                int32_t lj = lev[k] + levs[f] + 1;
+                if (lj < lev[j]) lev[j] = lj;
+            }
+        }
+        if (w[i] == 0.0 || !isfinite(w[i])) { st = ORA_ZERO_PIVOT; goto done; }
+        qsort(list, (size_t)nw, sizeof(int32_t), cmp_i32);
+        for (int t = 0; t < nw; t++) {
+            int32_t j = list[t];
+            if (lev[j] > p) continue;
+            if (j == i) udiag[i] = LU.nnz;
+            if (mat_push(&LU, j, w[j])) { st = ORA_OOM; goto done; }
+            if (lnnz == lcap) {
+                int32_t *nl = (int32_t *)realloc(levs, (size_t)(lcap * 2) * sizeof(int32_t));
+                if (!nl) { st = ORA_OOM; goto done; }
+                levs = nl;
+                lcap *= 2;
+            }
+            levs[lnnz++] = lev[j];
+        }
+        LU.rp[i + 1] = (int32_t)LU.nnz;
+        for (int t = 0; t < nw; t++) { lev[list[t]] = INF; w[list[t]] = 0.0; }
+    }
+    *out = LU;
+    LU.rp = NULL; LU.ci = NULL; LU.va = NULL;
+    if (lev_out) { *lev_out = levs; levs = NULL; }
+done:
+    ora_free(&LU);
+    free(levs); free(w); free(lev); free(list); free(udiag);
+    return st;
+}
+
+void ora_free_i32(int32_t *p) { free(p); }
+
+/* ------------------------------------------------------------------------ */
 /* SAIT (Algorithms 1-3).                                                   */
 /*                                                                          */
 /* With D = diag(T) and T~ = I - D^-1 T (strictly triangular, Section 2),    */

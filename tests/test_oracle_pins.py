@@ -437,6 +437,111 @@ def test_ilu0_tridiagonal_closed_form(oracle_lib):
 
 
 # --------------------------------------------------------------------------
+# ILU(p) (level of fill, Saad Algorithm 10.5): p = 0 is ILU(0) bit for bit;
+# p >= n is the complete LU; LU = A on the ILU(p) pattern; the level-1 fill of
+# the 5- and 7-point stencils in closed form; the paper's level-1 columns.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("make", [lambda: synth.poisson2d(9), lambda: synth.convdiff3d(6),
+                                  lambda: synth.varcoef3d(5, 1.0, 3), lambda: synth.aniso2d(11, 0.01)])
+def test_iluk_level0_is_ilu0(oracle_lib, make):
+    A = make()
+    L0, U0 = oracle_lib.ilu0(A)
+    L, U = oracle_lib.iluk(A, 0)
+    for X, Y in ((L, L0), (U, U0)):
+        assert np.array_equal(X.rp, Y.rp) and np.array_equal(X.ci, Y.ci)
+        assert np.array_equal(X.va, Y.va)          # same fma chains
+
+
+def test_iluk_complete_is_exact_lu(oracle_lib):
+    rng = np.random.default_rng(5)
+    n = 40
+    Ad = np.where(rng.uniform(size=(n, n)) < 0.1, rng.uniform(-1, 1, (n, n)), 0.0) + n * np.eye(n)
+    L, U = oracle_lib.iluk(synth.from_dense(Ad), n)
+    assert np.abs(L.to_dense() @ U.to_dense() - Ad).max() <= 1e-12 * n
+    y = sla.solve_triangular(L.to_dense(), np.ones(n), lower=True)
+    x = sla.solve_triangular(U.to_dense(), y, lower=False)
+    assert np.allclose(x, np.linalg.solve(Ad, np.ones(n)), rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("make", [lambda: synth.poisson2d(9), lambda: synth.convdiff3d(6),
+                                  lambda: synth.varcoef3d(5, 1.0, 3)])
+def test_iluk_reproduces_a_on_its_pattern(oracle_lib, make, p):
+    """Incomplete LU on a pattern P leaves LU - A zero on P (Saad, Proposition 10.3's setting)."""
+    A = make()
+    L, U, LUc, lev = oracle_lib.iluk(A, p, levels=True)
+    LU = L.to_dense() @ U.to_dense()
+    Ad = A.to_dense()
+    P = LUc.to_dense() != 0
+    P[np.arange(A.n), np.arange(A.n)] = True
+    assert np.abs(LU[P] - Ad[P]).max() <= 1e-13 * np.abs(Ad).max()
+    # the levels: A's pattern is level 0, every other stored entry is fill of level 1..p
+    rows = np.repeat(np.arange(A.n), np.diff(LUc.rp))
+    in_a = Ad[rows, LUc.ci] != 0
+    assert np.all(lev[in_a] == 0) and np.all((lev[~in_a] >= 1) & (lev[~in_a] <= p))
+
+
+def test_iluk_level1_fill_closed_form(oracle_lib):
+    """Level-1 fill of the natural-order 5-point (g x g) and 7-point (N^3) stencils:
+    products of one L offset and one U offset, at grid points that exist."""
+    g = 13
+    L, U = oracle_lib.iluk(synth.poisson2d(g), 1)
+    assert L.nnz == g * g + 2 * g * (g - 1) + (g - 1) ** 2     # diagonal, -1, -g, -(g-1)
+    assert U.nnz == L.nnz
+    rows = np.repeat(np.arange(L.n), np.diff(L.rp))
+    assert set(np.unique(rows - L.ci)) == {0, 1, g, g - 1}
+    N = 9
+    L, U = oracle_lib.iluk(synth.laplace3d(N), 1)
+    assert L.nnz == N ** 3 + 3 * N * N * (N - 1) + 3 * N * (N - 1) ** 2
+    rows = np.repeat(np.arange(L.n), np.diff(L.rp))
+    assert set(np.unique(rows - L.ci)) == {0, 1, N, N * N, N - 1, N * N - 1, N * N - N}
+
+
+@pytest.fixture(scope="module")
+def laplace100_level1(oracle_lib):
+    A = synth.laplace3d(100)
+    L, U = oracle_lib.iluk(A, 1)
+    return A, L, U
+
+
+@pytest.fixture(scope="module")
+def golden_level1():
+    with open(os.path.join(GOLDEN, "paper_runtime_sait_level1.json")) as f:
+        return json.load(f)
+
+
+@pytest.mark.slow
+def test_paper_ratios_level1(oracle_lib, laplace100_level1, golden_level1):
+    """Table runtime_SAIT, level-1 ILU columns: the nnz ratios of SAIT_Thr and SAIT_Pat."""
+    A, L, U = laplace100_level1
+    assert L.nnz == 100 ** 3 + 3 * 100 ** 2 * 99 + 3 * 100 * 99 ** 2 == 6_910_300
+    m = golden_level1["loop_iterations_m"]
+    for row in golden_level1["sait_thr"]:
+        M = oracle_lib.sait(L, m + 1, "abs", row["tau"])
+        assert round(M.nnz / L.nnz, 2) == row["ratio"], row
+    for row in golden_level1["sait_pat"]:
+        M = oracle_lib.sait(U, row["p"] + m + 1, "pattern", 0.0, row["p"])
+        assert round(M.nnz / U.nnz, 2) == row["ratio"], row
+
+
+@pytest.mark.slow
+def test_paper_pcg_iteration_counts_level1(oracle_lib, laplace100_level1, golden_level1):
+    """Exact ILU(1) substitution (the commented-out row of Table runtime_SAIT) and four
+    Jacobi sweeps on the level-1 factors (Table runtime_Jacobi); b ~ U[0,1) as for level 0."""
+    A, L, U = laplace100_level1
+    b = synth.uniform(synth.SEED_BASE, A.n, 0.0, 1.0)
+    tol = golden_level1["pcg_tol"]
+    _, it, rr, st = oracle_lib.pcg(A, b, "ilu", L, U, tol=tol)
+    assert st == 0 and rr <= tol
+    assert abs(it - golden_level1["exact_ilu1_pcg_iters"]) <= 3
+    _, it4, rr4, st4 = oracle_lib.pcg(A, b, "jacobi4", L, U, tol=tol)
+    assert st4 == 0 and rr4 <= tol
+    ref = golden_level1["jacobi_level1_pcg_iters"]["4"]
+    assert abs(it4 - ref) <= 0.05 * ref
+    assert it < it4      # the exact substitution needs the fewest iterations
+
+
+# --------------------------------------------------------------------------
 # Apply, substitution, SpMV, solvers against dense direct solves.
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("lower", [True, False])
