@@ -8,11 +8,16 @@ step is the whole hot path on the device: ILU(0) factors (GPU, level
 scheduled), the SAIT matrices of L and U (m = 3 series terms, row-relative drop
 1e-3), and GMRES(50) with z = M_U (M_L r) to a relative residual of 1e-8.
 
-Printed: one JSON line.  `value` is the time to a 1e-8 solution in ms (lower is
-better); `roofline` is the dominant kernel group of the step, `apply_roofline`
-the SAIT apply (two SELL-32 products) measured live in the timed steps;
-`baseline_trisolve` is the same GMRES with the exact level-scheduled ILU
-substitutions; `cpu_baseline` is the FP64 oracle on a bounded sample.
+Printed: the benchmark JSON line, last.  `value` is the time to a 1e-8
+solution in ms (lower is better); `roofline` is the dominant kernel group of
+the step, the SAIT apply (two SELL-32 products), measured live in the timed
+steps; `rooflines` adds the A product and the Gram-Schmidt step;
+`apply_rooflines` times the apply alone with the factors stored in FP64, FP32
+and BF16; `baseline_trisolve` is the same GMRES with the exact
+level-scheduled ILU substitutions; `cpu_baseline` is the whole step run by the
+FP64 oracle on one host core.  With the extra workloads on (the default), a
+`{"bench_detail": ...}` line with their full record comes before the
+benchmark line, and `extras` in the benchmark line summarizes it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
     python bench.py --summarize-launches launches.csv   # per-kernel table of an ncu launch list
@@ -90,6 +95,14 @@ def peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def config_dict(a, A, world=1):
+    """The workload, identical for both arms."""
+    return {"workload": workload_name(a), "n": A.n, "nnz_A": A.nnz, "m_terms": a.m, "drop": DROP, "tau": TAU,
+            "store": a.store, "solver": f"gmres({RESTART})", "tol": TOL,
+            "l2": "inputs larger than L2 (A 175 MB, SAIT pair 0.5 GB, GMRES basis 0.86 GB)",
+            "parallelism": "replicas" if world > 1 else "single device"}
 
 
 def workload_name(a):
@@ -376,6 +389,33 @@ def adjoint_workload(sg, ctx, torch, device, stream):
     return {"n": A.n, "ms_forward_backward": round(ms, 3), "store": "f32", "restart": 50, "tol": TOL}
 
 
+def apply_precisions(sg, ctx, torch, device, stream, P: "Problem", m, flush_l2, peak, reps=20):
+    """The SAIT apply z = M_U (M_L r) of the benchmark factors stored in FP64, FP32
+    and BF16: each apply timed alone with CUDA events on the context stream, L2
+    flushed before each, against its algorithmic bytes."""
+    d = P.dev
+    L, U = sg.sait_ilu0(ctx, P.A.n, d["rp"], d["ci"], d["va"])
+    r = torch.from_numpy(synth.uniform(synth.SEED_BASE + 11, P.A.n)).to(device)
+    z = torch.empty_like(r)
+    out = {}
+    for store in ("f64", "f32", "bf16"):
+        ML = sg.sait_build(ctx, L, True, m, DROP, TAU, store=store)
+        MU = sg.sait_build(ctx, U, False, m, DROP, TAU, store=store)
+        for _ in range(3):
+            sg.sait_apply(ctx, ML, MU, r, z)
+        ms = []
+        for _ in range(reps):
+            flush_l2()
+            t, _ = time_region(torch, stream, lambda: sg.sait_apply(ctx, ML, MU, r, z))
+            ms.append(t)
+        t = statistics.median(ms)
+        b = apply_bytes(P.A.n, ML.nnz, MU.nnz, store)
+        out[store] = {"ms": round(t, 4), "algorithmic_bytes": b, "achieved": round(b / t / 1e6, 1),
+                      "peak": peak, "unit": "GB/s", "frac": round(b / t / 1e6 / peak, 4)}
+        del ML, MU
+    return out
+
+
 def apply_bytes(n, nnz_l, nnz_u, store):
     sv = {"f64": 8, "f32": 4, "bf16": 2, "f32x64": 4, "bf16x64": 2}[store]
     vec = 32 * n if store in ("f64", "f32x64", "bf16x64") else 24 * n   # r in, w out+in, z out
@@ -417,54 +457,54 @@ def time_region(torch, ctx_stream, fn):
     return s.elapsed_time(e), out
 
 
-# ---- CPU baseline: the oracle on a bounded sample ------------------------------------
-def oracle_sample(grid, m, gpu_iters=None):
-    """Full-size oracle ILU(0) + SAIT build, plus the first GMRES(50) cycle; the
-    solve time is scaled to the number of Arnoldi steps (the GPU's count when
-    given, else a log-linear estimate from the first cycle's residual drop)."""
-    import oracle
+# ---- CPU baseline: the oracle, the whole solve ------------------------------------
+def oracle_problem(grid):
+    """The benchmark's matrix and right-hand side (same seed as the GPU arm)."""
     A = synth.convdiff3d(grid)
     xt = synth.uniform(synth.SEED_BASE + 2, A.n)
-    b = A.to_scipy() @ xt
+    return A, A.to_scipy() @ xt
+
+
+def oracle_solve(A, b, m, maxit=20000):
+    """One full step on the host: oracle ILU(0) + SAIT build of L and U + GMRES(50)
+    to the tolerance, one thread.  Returns (ms, sample description, steps, relres)."""
+    import oracle
     t0 = time.perf_counter()
     L, U = oracle.ilu0(A)
     ML = oracle.sait(L, m, DROP, TAU)
     MU = oracle.sait(U, m, DROP, TAU)
     t1 = time.perf_counter()
-    _, it, rr, st = oracle.gmres(A, b, "sait", ML, MU, restart=RESTART, tol=TOL, maxit=RESTART)
+    _, it, rr, st = oracle.gmres(A, b, "sait", ML, MU, restart=RESTART, tol=TOL, maxit=maxit)
     t2 = time.perf_counter()
-    if gpu_iters is None:
-        est = it if rr <= TOL else int(math.ceil(it * math.log(TOL) / math.log(max(rr, 1e-300))))
-        steps, how = est, "log-linear estimate from the first cycle's residual"
-    else:
-        steps, how = gpu_iters, "the GPU path's Arnoldi step count"
-    total_s = (t1 - t0) + (t2 - t1) * steps / max(it, 1)
-    sample = (f"oracle, 1 thread: full-size ILU(0) + SAIT build of L and U ({t1 - t0:.1f} s) and the "
-              f"first GMRES({RESTART}) cycle, {it} Arnoldi steps ({t2 - t1:.1f} s); solve time scaled "
-              f"to {steps} steps ({how})")
-    return total_s * 1e3, sample, t2 - t0
+    sample = (f"oracle, 1 thread, the whole step measured (nothing scaled): ILU(0) + SAIT build of L and U "
+              f"({t1 - t0:.2f} s) and GMRES({RESTART}) to {TOL:g}, {it} Arnoldi steps ({t2 - t1:.2f} s, "
+              f"status {st}, relres {rr:.2e})")
+    return (t2 - t0) * 1e3, sample, it, rr
 
 
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    # warm-up: page the oracle in on a small instance (untimed)
+    A, b = oracle_problem(a.grid)
+    # warm-up (untimed): page the oracle and the problem in with a bounded step,
+    # the factors and one GMRES cycle
     for _ in range(a.warmup):
-        oracle_sample(16, a.m)
+        oracle_solve(A, b, a.m, maxit=RESTART)
     vals, last = [], ""
     for _ in range(a.steps):
-        v, sample, _ = oracle_sample(a.grid, a.m)
+        v, sample, _, _ = oracle_solve(A, b, a.m)
         vals.append(v)
         last = sample
     v = statistics.mean(vals)
     print(json.dumps({
-        "metric": METRIC, "impl": "reference", "value": v, "unit": "ms", "n_gpus": a.gpus,
-        "steps": a.steps, "warmup": a.warmup, "ms_per_step": v, "higher_is_better": False,
+        "metric": METRIC, "impl": "reference", "value": round(v, 1), "unit": "ms", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(v, 1), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(a), "parallelism": "replicas"},
-        "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": last},
-        "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config": config_dict(a, A),
+        "cpu_baseline": {"value": round(v, 1), "unit": "ms", "cores": 1, "kind": "oracle", "sample": last,
+                         "step_ms": [round(x, 1) for x in vals]},
+        "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
@@ -578,29 +618,27 @@ def run_ours(a):
     traffic = {"apply": None, "ortho": None, "spmv": None}
     traffic.update(TRAFFIC.get(f"{a.grid}:{a.m}:{a.store}", {}))
 
-    def roof(g):
+    def roof(g, full=True):
         r = rl[g]
-        return {"bound": r["bound"], "achieved": round(r["achieved"], 1), "peak": peak, "unit": "GB/s",
-                "frac": round(r["frac"], 4), "traffic": traffic.get(g), "kernel": r["kernel"],
-                "algorithmic_bytes_per_launch": int(r["bytes"]), "avg_ms": round(r["ms"], 4),
-                "launches_timed": r["calls"], "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"}
+        o = {"bound": r["bound"], "achieved": round(r["achieved"], 1), "peak": peak, "unit": "GB/s",
+             "frac": round(r["frac"], 4), "traffic": traffic.get(g), "algorithmic_bytes_per_launch": int(r["bytes"]),
+             "avg_ms": round(r["ms"], 4), "launches_timed": r["calls"]}
+        if full:
+            o.update(kernel=r["kernel"], peak_source=f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)")
+        return o
 
     out = {
         "metric": METRIC, "value": round(ms_step, 3), "unit": "ms", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(a), "n": n, "nnz_A": P.A.nnz, "m_terms": a.m, "drop": DROP,
-                   "tau": TAU, "store": a.store, "solver": f"gmres({RESTART})", "tol": TOL,
-                   "l2": "inputs larger than L2 (A 175 MB, SAIT pair 0.5 GB, basis 0.86 GB); L2 also "
-                         "flushed (512 MB write) before every timed step",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": config_dict(a, P.A, world),
+        "l2_flush": "a 512 MB write before every timed step",
         "clocks": clk,
         "e2e": {"value": round(statistics.mean(e2e_times), 3), "unit": "ms",
                 "h2d_bytes_per_step": P.h2d_bytes, "d2h_bytes_per_step": P.d2h_bytes},
         "gpu_launches": stats["launches"],
         "roofline": roof(dom),
-        "apply_roofline": roof("apply"),
-        "rooflines": {g: roof(g) for g in rl},
+        "rooflines": {g: roof(g, full=False) for g in rl},
         "breakdown_ms_per_step": {g: round(v / a.steps, 3) for g, v in groups.items()},
         "solve": {"iters": iters, "cycles": infos[-1]["cycles"], "rel_resid": infos[-1]["rel_resid"],
                   "rel_resid_host_check": relres, "step_ms": [round(t, 3) for t in times],
@@ -608,6 +646,7 @@ def run_ours(a):
                   "ratio_U": extra["nnz_MU"] / extra["nnz_U"]},
     }
 
+    detail = {}
     if not a.no_extras:
         # exact level-scheduled ILU substitution in the same GMRES (comparator)
         flush_l2()
@@ -618,18 +657,35 @@ def run_ours(a):
         st_t = sg.sait_ctx_stats(ctx, reset=True).as_dict()
         out["baseline_trisolve"] = {
             "ms": round(ms_t, 3), "iters": info_t.iters, "rel_resid": info_t.rel_resid,
-            "levels": list(levels), "avg_trisolve_pair_ms": st_t["trisolve"]["ms"] / max(st_t["trisolve"]["calls"], 1),
+            "levels": list(levels),
+            "avg_trisolve_pair_ms": round(st_t["trisolve"]["ms"] / max(st_t["trisolve"]["calls"], 1), 4),
             "speedup_of_sait": round(ms_t / ms_step, 3)}
+        sg.sait_ctx_set_timing(ctx, False)
+        # the apply with the factors stored in FP64 / FP32 / BF16
+        out["apply_rooflines"] = apply_precisions(sg, ctx, torch, device, stream, P, a.m, flush_l2, peak)
+        # the whole step with reduced-precision SAIT storage (one run each)
+        ss = {}
+        for store in ("f32", "bf16"):
+            sait_step(sg, ctx, P, P.dev, a.m, store)
+            flush_l2()
+            ms_s, (xs, info_s, _, keep) = time_region(torch, stream,
+                                                      lambda: sait_step(sg, ctx, P, P.dev, a.m, store))
+            del keep
+            rr = float(np.linalg.norm(P.b - P.A.to_scipy() @ xs.cpu().numpy()) / np.linalg.norm(P.b))
+            ss[store] = {"ms": round(ms_s, 3), "iters": info_s.iters, "rel_resid_host_check": rr}
+        out["store_sweep"] = ss
         # BiCGSTAB with the same SAIT preconditioner
         flush_l2()
         ms_b, (_, info_b, _, keep) = time_region(
             torch, stream, lambda: sait_step(sg, ctx, P, P.dev, a.m, a.store, "bicgstab"))
         del keep
-        out["bicgstab"] = {"ms": round(ms_b, 3), "iters": info_b.iters, "rel_resid": info_b.rel_resid}
+        detail["bicgstab"] = {"ms": round(ms_b, 3), "iters": info_b.iters, "rel_resid": info_b.rel_resid}
         # m sweep (one run each)
         sweep = []
+        sg.sait_ctx_set_timing(ctx, True)
         for m in (2, 3, 4, 6):
             flush_l2()
+            sg.sait_ctx_stats(ctx, reset=True)
             ms_m, (_, info_m, ex_m, keep) = time_region(torch, stream,
                                                         lambda: sait_step(sg, ctx, P, P.dev, m, a.store))
             del keep
@@ -638,24 +694,61 @@ def run_ours(a):
                           "nnz_ML": ex_m["nnz_ML"], "nnz_MU": ex_m["nnz_MU"],
                           "build_ms": round(st_m["build"]["ms"], 3),
                           "apply_ms": round(st_m["apply"]["ms"] / max(st_m["apply"]["calls"], 1), 4)})
-        out["m_sweep"] = sweep
+        detail["m_sweep"] = sweep
         sg.sait_ctx_set_timing(ctx, False)
-        out["batched"] = batched_workloads(sg, ctx, torch, device, stream)
-        out["adjoint"] = adjoint_workload(sg, ctx, torch, device, stream)
-        out["eigen"] = eigen_workload(sg, ctx, torch, device, stream)
-        out["paper_replica"] = paper_replica_workload(sg, ctx, torch, device, stream)
-        out["autotune"] = autotune_workload(sg, ctx, torch, device, stream, P, a.m, a.store)
-        out["optimal_params"] = optimal_params_workload(sg, ctx, P, a.store)
+        detail["batched"] = batched_workloads(sg, ctx, torch, device, stream)
+        detail["adjoint"] = adjoint_workload(sg, ctx, torch, device, stream)
+        detail["eigen"] = eigen_workload(sg, ctx, torch, device, stream)
+        detail["paper_replica"] = paper_replica_workload(sg, ctx, torch, device, stream)
+        detail["autotune"] = autotune_workload(sg, ctx, torch, device, stream, P, a.m, a.store)
+        detail["optimal_params"] = optimal_params_workload(sg, ctx, P, a.store)
+        out["extras"] = summarize_extras(detail)
 
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        v, sample, _ = oracle_sample(a.grid, a.m, gpu_iters=iters)
+        A_h, b_h = oracle_problem(a.grid)
+        v, sample, it_o, _ = oracle_solve(A_h, b_h, a.m)
         out["cpu_baseline"] = {"value": round(v, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-                               "sample": sample}
+                               "sample": sample, "oracle_steps": it_o}
     if rank == 0:
+        if detail:
+            # the full record of the extra workloads first; the benchmark line is the last line
+            print(json.dumps({"bench_detail": detail}), flush=True)
         print(json.dumps(out), flush=True)
     ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def summarize_extras(d):
+    """A few numbers per extra workload, short enough to stay in the benchmark line."""
+    s = {}
+    if "bicgstab" in d:
+        s["bicgstab"] = {k: d["bicgstab"][k] for k in ("ms", "iters")}
+    if "m_sweep" in d:
+        s["m_sweep_ms"] = {str(r["m_terms"]): r["ms"] for r in d["m_sweep"]}
+    if "batched" in d:
+        b = d["batched"]
+        s["batched_512_systems_ms"] = {k: b["independent_systems"][k]["ms"] for k in ("f64", "f32", "f32x64")
+                                       if k in b["independent_systems"]}
+        s["many_rhs_64_ms"] = {k: b["many_rhs"][k]["ms"] for k in ("f64", "f32", "f32x64") if k in b["many_rhs"]}
+        for key in ("build_roofline", "spmm_roofline"):
+            if key in b:
+                s["batched_" + key] = b[key]
+    if "adjoint" in d:
+        s["adjoint_ms"] = d["adjoint"]["ms_forward_backward"]
+    if "eigen" in d:
+        e = d["eigen"]
+        s["eigen"] = {k: {"ms": e[k]["ms"], "iters": e[k]["iters"],
+                          "err_vs_f64": e[k].get("max_rel_eig_diff_vs_f64")}
+                      for k in ("f64", "f32", "bf16") if k in e}
+        if "vs_oracle" in e:
+            s["eigen_vs_oracle"] = e["vs_oracle"]
+    if "paper_replica" in d:
+        p = d["paper_replica"]
+        s["paper_replica"] = {r["name"]: [r["ratio"], r["iters"]] for r in p["rows"]}
+    if "optimal_params" in d:
+        s["optimal_params_chosen"] = d["optimal_params"].get("chosen_param")
+    return s
 
 
 def main():

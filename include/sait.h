@@ -362,10 +362,10 @@ sait_status sait_outer_on_pattern(sait_ctx ctx, sait_mat A, double alpha, const 
 
 /* z = M_U (M_L r) like sait_apply, but allocating nothing.  The paper has no
  * counterpart: this is for callers that cannot let the library allocate
- * device memory when the preconditioner is applied -- code running inside
- * CUDA stream capture, loops whose latency budget forbids allocator calls, and
- * frameworks that hand out all device memory through their own pools.  The
- * caller still owns r and z (device, n doubles, not overlapping); the
+ * device memory when the preconditioner is applied -- loops whose latency
+ * budget forbids allocator calls, and frameworks or embedded runtimes that
+ * hand out all device memory from their own pools, sized once at start-up.
+ * The caller still owns r and z (device, n doubles, not overlapping); the
  * intermediate vector lives in a fixed 16 MiB array compiled into the
  * library, present on every device that loads the library until the process
  * exits.  Requirements and behaviour:
@@ -376,6 +376,9 @@ sait_status sait_outer_on_pattern(sait_ctx ctx, sait_mat A, double alpha, const 
  *    not see its failures.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    A device reset (cudaDeviceReset) frees the array together with every
+ *    matrix on the device; the context that has to be created again to
+ *    rebuild the matrices makes the next call look the address up again.
  *  - Every call on a device shares the one array: calls whose work overlaps
  *    on the GPU (different streams, no ordering between them) race and give
  *    wrong results.  Calls ordered on one stream are safe. */

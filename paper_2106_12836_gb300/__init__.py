@@ -406,10 +406,10 @@ def sait_apply_static(ML: Mat, MU: Mat, r: torch.Tensor, z: torch.Tensor,
                       stream: torch.cuda.Stream | None = None) -> int:
     """z = M_U (M_L r) without any allocation by the library (see include/sait.h).
 
-    For callers that cannot allow device allocations at apply time (stream
-    capture, allocator-free loops, framework-owned memory): the intermediate
-    vector lives in a fixed array inside the library, shared by all calls on a
-    device, so calls that overlap on the GPU race.  n must not exceed
+    For callers that cannot allow device allocations at apply time
+    (allocator-free loops, runtimes that own all device memory): the
+    intermediate vector lives in a fixed array inside the library, shared by
+    all calls on a device, so calls that overlap on the GPU race.  n must not exceed
     APPLY_STATIC_MAX_N.  Returns the status code (0 = ok) instead of raising,
     since no context records a message.
     """

@@ -141,6 +141,7 @@ extern "C" sait_status sait_ctx_create(sait_ctx *ctx, void *stream) {
         return e == cudaErrorMemoryAllocation ? SAIT_ERR_OOM : SAIT_ERR_CUDA;
     }
     c->launch_base = g_sait_launches;
+    static_apply_forget(c->device);
     *ctx = c;
     return SAIT_OK;
 }

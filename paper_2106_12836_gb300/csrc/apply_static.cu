@@ -2,11 +2,12 @@
 //
 // sait_apply obtains its intermediate vector w = M_L r from the stream-ordered
 // pool.  Some callers cannot let a library allocate device memory when they
-// apply the preconditioner: code that runs inside CUDA stream capture, loops
-// with hard latency budgets that forbid allocator calls, and frameworks that
-// own all device memory through their own pools.  sait_apply_static keeps w in
-// a fixed array compiled into the library instead.  The array exists once per
-// device that loads the library and stays allocated until the process exits.
+// apply the preconditioner: loops with hard latency budgets that forbid
+// allocator calls, and frameworks or embedded runtimes that hand out all device
+// memory from their own pools, sized once at start-up.  sait_apply_static
+// keeps w in a fixed array compiled into the library instead.  The array exists
+// once per device that loads the library and stays allocated until the
+// process exits.
 #include <mutex>
 
 #include "internal.cuh"
@@ -23,7 +24,10 @@ std::mutex g_scratch_mu;
 
 // Device address of g_apply_scratch on the current device.  In host code the
 // symbol itself is only a host-side stand-in, so its address is looked up once
-// per device and cached.
+// per device and cached.  A device reset frees the array with everything else
+// on the device; sait_ctx_create (which every caller needs again after a reset,
+// to rebuild its matrices) drops the cached address through
+// static_apply_forget, so the next call looks it up again.
 cudaError_t scratch_address(int dev, void **out) {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     if (!g_scratch_addr[dev]) {
@@ -37,6 +41,11 @@ cudaError_t scratch_address(int dev, void **out) {
 }
 
 }  // namespace
+
+void static_apply_forget(int dev) {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (dev >= 0 && dev < kMaxDevices) g_scratch_addr[dev] = nullptr;
+}
 
 extern "C" sait_status sait_apply_static(sait_mat ML, sait_mat MU, const double *r, double *z, void *stream) {
     if (!ML || !MU || ML->n != MU->n || (ML->n > 0 && (!r || !z))) return SAIT_ERR_INVALID_ARG;

@@ -335,6 +335,9 @@ cudaError_t launch_trisolve(const sait_mat_s *T, const LevelSchedule &lev, bool 
 sait_status frontier_schedule(sait_ctx ctx, const int32_t *rp, const int32_t *ci, int64_t n, bool lower,
                               const int32_t *dpos, double *a, int *err_word, LevelSchedule *out);
 
+// apply_static.cu: drop the cached device address of the static apply's array
+void static_apply_forget(int dev);
+
 // mat helpers (api.cu)
 sait_status mat_copy_csr(sait_ctx ctx, const sait_csr *A, sait_mat *out);  // validated copy, CSR only
 sait_status mat_alloc(sait_ctx ctx, int64_t n, int64_t nnz, sait_mat *out);
