@@ -22,7 +22,10 @@ struct Scal {        // device-resident solver scalars
     int active;      // 1 while the current cycle / iteration runs
     int jdone;       // GMRES: Arnoldi steps done in this cycle; BiCGSTAB: iterations done
     int state;       // 0 running, 1 converged, 2 breakdown, 3 non-finite, 4 x updated (half step)
-    int pad;
+    int ticket;      // GMRES: blocks of the dot sweep that finished (last-block pattern)
+    int sweep;       // GMRES: 1 when the update sweep of this step runs
+    int stop_after;  // GMRES: stop the cycle once column j-1 is rotated
+    double gamma_last;
     double bnorm, beta, tolb, inv;
     double rho, rho_old, alpha, omega, beta_b;
     double r0, r1, r2, r3;    // reduction results
@@ -120,20 +123,35 @@ __device__ __forceinline__ float4 load_w4(const double2 *w, int64_t i4) {
 // column is applied once it is final, so convergence is seen one step later.
 // Precision as in the two-pass kernels above: dots in FP32 on V_hi, updates in
 // double-float on (V_hi, V_lo).
-constexpr int kDCH = 8;  // basis vectors per chunk of the dual dot sweep
+constexpr int kDCH = 8;          // basis vectors per chunk of the dual dot sweep
+constexpr int kDotThreads = 512; // dual dot sweep: two blocks of 512 threads per SM
 
-// partial[b*ldp + q] = V_q . U, partial[b*ldp + j + q] = V_q . W (q < j);
-// with DELTA also partial[b*ldp + 2j] = U . W (block b's rows)
+// Everything the last block of the dot sweep and the Givens step touch.
+struct DcgsState {
+    float *part;           // dot partials, column-major: part[slot * ldp + block]
+    int ldp;               // leading dimension (>= blocks, multiple of 4, padding zero)
+    const float *upart;    // ||w1||^2 of the update sweep's blocks (j >= 1), nbu of them
+    int nbu;
+    double *Hr, *R, *cs, *sn, *g;  // raw Hessenberg, rotated copy, rotations, rhs (ld m + 1)
+    double *coef, *kk;             // update weights: coef = [p (j), r (j)], kk = [k1, k2, k3]
+    Scal *sc;
+    int *calls;            // timer-group counter (or null)
+    int m;
+};
+
+// partial[slot * ldp + b] (FP32): V_q . U (slot q < j), V_q . W (slot j + q) and,
+// with DELTA, U . W (slot 2j), over block b's rows
 template <int CH, bool DELTA>
 __device__ __forceinline__ void dual_chunk(int64_t n4, const float4 *__restrict__ V, int64_t ldv4, int q0, int j,
                                            const float4 *__restrict__ U, const double2 *__restrict__ W,
-                                           double *partial, int ldp, double (*red)[2 * kDCH + 1]) {
+                                           float *part, int ldp, float (*red)[2 * kDCH + 1]) {
     constexpr int NA = 2 * CH + (DELTA ? 1 : 0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float au[CH > 0 ? CH : 1], aw[CH > 0 ? CH : 1], ad = 0.0f;
 #pragma unroll
     for (int t = 0; t < (CH > 0 ? CH : 1); t++) au[t] = aw[t] = 0.0f;
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kThreads) {
+    for (int64_t i = (int64_t)blockIdx.x * kDotThreads + threadIdx.x; i < n4;
+         i += (int64_t)gridDim.x * kDotThreads) {
         const float4 u = U[i];
         const float4 w = load_w4(W, i);
         float4 vv[CH > 0 ? CH : 1];
@@ -162,173 +180,270 @@ __device__ __forceinline__ void dual_chunk(int64_t n4, const float4 *__restrict_
         float v = t < CH ? au[t < CH ? t : 0] : t < 2 * CH ? aw[t >= CH && t < 2 * CH ? t - CH : 0] : ad;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp][t] = (double)v;
+        if (lane == 0) red[warp][t] = v;
     }
     __syncthreads();
     if ((int)threadIdx.x < NA) {
-        double sum = 0.0;
-        for (int w2 = 0; w2 < kThreads / 32; w2++) sum += red[w2][threadIdx.x];
+        float sum = 0.0f;
+        for (int w2 = 0; w2 < kDotThreads / 32; w2++) sum += red[w2][threadIdx.x];
         const int t = threadIdx.x;
         const int slot = t < CH ? q0 + t : t < 2 * CH ? j + q0 + (t - CH) : 2 * j;
-        partial[(int64_t)blockIdx.x * ldp + slot] = sum;
+        part[(int64_t)slot * ldp + blockIdx.x] = sum;
     }
     __syncthreads();
 }
 
 template <bool DELTA>
 __device__ __forceinline__ void dual_tail(int rem, int64_t n4, const float4 *V, int64_t ldv4, int q0, int j,
-                                          const float4 *U, const double2 *W, double *partial, int ldp,
-                                          double (*red)[2 * kDCH + 1]) {
+                                          const float4 *U, const double2 *W, float *part, int ldp,
+                                          float (*red)[2 * kDCH + 1]) {
     switch (rem) {
-#define SAIT_DT(k) case k: dual_chunk<k, DELTA>(n4, V, ldv4, q0, j, U, W, partial, ldp, red); break;
+#define SAIT_DT(k) case k: dual_chunk<k, DELTA>(n4, V, ldv4, q0, j, U, W, part, ldp, red); break;
         SAIT_DT(0) SAIT_DT(1) SAIT_DT(2) SAIT_DT(3) SAIT_DT(4) SAIT_DT(5) SAIT_DT(6) SAIT_DT(7)
 #undef SAIT_DT
         default: break;
     }
 }
 
-__global__ void __launch_bounds__(kThreads)
-k_dcgs_dot(int64_t n4, const float4 *__restrict__ V, int64_t ldv4, int j, const float4 *__restrict__ U,
-           const double2 *__restrict__ W, double *partial, int ldp, const int *gate) {
-    pdl_wait();
-    pdl_trigger();
-    if (gate && *gate == 0) return;
-    __shared__ double red[kThreads / 32][2 * kDCH + 1];
-    int q0 = 0;
-    for (; j - q0 > kDCH; q0 += kDCH) dual_chunk<kDCH, false>(n4, V, ldv4, q0, j, U, W, partial, ldp, red);
-    if (j - q0 == kDCH) dual_chunk<kDCH, true>(n4, V, ldv4, q0, j, U, W, partial, ldp, red);
-    else dual_tail<true>(j - q0, n4, V, ldv4, q0, j, U, W, partial, ldp, red);
+// Sum of the FP32 values x[0 .. cnt) (a 16-byte aligned run, cnt a multiple of 4)
+// by the 8 lanes of a quarter warp, returned in FP64 to all 8 lanes.
+__device__ __forceinline__ double quarter_sum(const float *x, int cnt, int sub) {
+    const float4 *x4 = (const float4 *)x;
+    float s0 = 0.0f, s1 = 0.0f;
+    for (int i = sub; i < cnt / 4; i += 16) {
+        const float4 a = __ldcg(x4 + i);
+        s0 += (a.x + a.y) + (a.z + a.w);
+        if (i + 8 < cnt / 4) {
+            const float4 b = __ldcg(x4 + i + 8);
+            s1 += (b.x + b.y) + (b.z + b.w);
+        }
+    }
+    float s = s0 + s1;
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    s += __shfl_xor_sync(0xffffffffu, s, 4);
+    return (double)s;
 }
 
-// Finalize column c of the raw Hessenberg Hr: copy it into R, apply the
-// previous rotations, form rotation c, update g; returns |g_{c+1}| (thread 0)
-__device__ double givens_column(int c, int m, const double *Hr, double *R, double *cs, double *sn, double *g,
-                                double *hc) {
-    const double *Hc = Hr + (int64_t)c * (m + 1);
-    double *Rc = R + (int64_t)c * (m + 1);
-    for (int i = threadIdx.x; i <= c + 1; i += kThreads) hc[i] = Hc[i];
+// The scalar step of DCGS2 step j, run by the last block of the dot sweep once
+// every block's partial sums are in.  dots (reduced here) = [c' (j), d' (j),
+// delta']; eta^2 = ||w1||^2 from the update sweep's partials (j >= 1; eta = beta
+// at j = 0).  Column j-1 of H becomes final (its rotation is applied later, by
+// dcgs_givens); writes coef = [p (j), r (j)], kk = [k1, k2, k3] and the first-pass
+// column j of H, or with `close` only finalizes column j-1.
+//
+// GB300's FP64 pipe has a 64-cycle dependent latency (sqrt and division about
+// 650), so this step avoids long FP64 chains: the partial sums are added in
+// FP32 (they are FP32 dot products already), every thread evaluates the
+// scalar recurrences itself instead of waiting on a broadcast, reciprocal
+// square roots replace square roots and divisions, and t = H c is split
+// over eight threads per row.
+__device__ void dcgs_scalar_step(const DcgsState &S, int j, int close, int nbd) {
+    __shared__ double colsum[2 * kMaxRestart + 2];
+    __shared__ double c2[kMaxRestart + 1], dh[kMaxRestart + 1], tv[kMaxRestart + 2];
+    __shared__ double s_cc, s_cd, s_e2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarp = kDotThreads / 32;
+    Scal *sc = S.sc;
+    const int ncol = 2 * j + 1;
+    // (1) column sums of the partials: four columns per warp and round (quarter warps)
+    const int ngroups = nwarp * 4;
+    const int cnt = (nbd + 3) / 4 * 4;
+    for (int q0 = 0; q0 < ncol; q0 += ngroups) {
+        const int q = q0 + warp * 4 + (lane >> 3);
+        const double v = quarter_sum(S.part + (int64_t)(q < ncol ? q : 0) * S.ldp, cnt, lane & 7);
+        if (q < ncol && (lane & 7) == 0) colsum[q] = v;
+    }
+    if (j >= 1 && warp == nwarp - 1) {  // ||w1||^2 by the last warp
+        float s0 = 0.0f;
+        for (int i = lane; i < S.nbu; i += 32) s0 += __ldcg(S.upart + i);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        if (lane == 0) s_e2 = (double)s0;
+    }
     __syncthreads();
-    double est = 0.0;
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < c; i++) {
-            const double t = cs[i] * hc[i] + sn[i] * hc[i + 1];
-            hc[i + 1] = -sn[i] * hc[i] + cs[i] * hc[i + 1];
-            hc[i] = t;
+    // (2) eta = ||w1||, computed by every thread
+    double eta, ie;
+    if (j >= 1) {
+        const double e2 = s_e2;
+        ie = rsqrt(e2);
+        eta = e2 * ie;
+    } else {
+        eta = sc->beta;
+        ie = 1.0 / eta;
+    }
+    double *Hc = S.Hr + (int64_t)(j - 1) * (S.m + 1);  // column j-1 (j >= 1)
+    if (!(eta > 0.0) || !isfinite(eta) || !isfinite(ie)) {  // invariant subspace (or a non-finite vector)
+        if (tid == 0) {
+            if (S.calls) atomicAdd(S.calls, 1);
+            if (!isfinite(eta)) sc->state = 3;
+            sc->sweep = 0;
+            if (j >= 1) {
+                Hc[j] = 0.0;
+                sc->stop_after = 1;   // rotate column j-1, then stop
+            } else {
+                sc->jdone = 0;
+                sc->active = 0;
+            }
         }
-        const double a = hc[c], b = hc[c + 1];
+        return;
+    }
+    for (int q = tid; q < j; q += kDotThreads) {
+        c2[q] = colsum[q] * ie;
+        dh[q] = colsum[j + q] * ie;
+    }
+    __syncthreads();
+    // (3) warp 0: cc = c.c and cd = c.d; the other warps: column j-1 of H and t = H c
+    if (warp == 0) {
+        double a = 0.0, b = 0.0;
+        for (int q = lane; q < j; q += 32) {
+            a = fma(c2[q], c2[q], a);
+            b = fma(c2[q], dh[q], b);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) {
+            s_cc = a;
+            s_cd = b;
+        }
+    } else if (!close) {
+        // t_i = sum_{k = max(i-1,0)}^{j-1} H(i,k) c_k over the final columns, with
+        // column j-1 taken as H(i,j-1) + eta c_i; H(j,j-1) = eta gamma is added below
+        const int rid = (tid - 32) >> 3, sub = tid & 7;
+        const int rows_per_round = (kDotThreads - 32) / 8;
+        for (int i0 = 0; i0 <= j; i0 += rows_per_round) {
+            const int i = i0 + rid;
+            double a = 0.0;
+            if (i <= j)
+                for (int k = (i > 0 ? i - 1 : 0) + sub; k < j; k += 8) {
+                    double h = S.Hr[(int64_t)k * (S.m + 1) + i];
+                    if (k == j - 1) h = i < j ? fma(eta, c2[i], h) : 0.0;
+                    a = fma(h, c2[k], a);
+                }
+            a += __shfl_xor_sync(0xffffffffu, a, 1);
+            a += __shfl_xor_sync(0xffffffffu, a, 2);
+            a += __shfl_xor_sync(0xffffffffu, a, 4);
+            if (i <= j && sub == 0) tv[i] = a;
+        }
+    }
+    __syncthreads();
+    if (j >= 1)  // column j-1 final: H(0:j-1, j-1) += eta c (t above read the old column)
+        for (int q = tid; q < j; q += kDotThreads) Hc[q] = fma(eta, c2[q], Hc[q]);
+    // (4) gamma = sqrt(1 - c.c), every thread
+    const double cc = s_cc, om = 1.0 - cc;
+    const double ig = om > 0.0 ? rsqrt(om) : 0.0;
+    const double gamma = om > 0.0 ? om * ig : 0.0;
+    if (tid == 0) {
+        if (S.calls) atomicAdd(S.calls, 1);
+        if (j >= 1) Hc[j] = eta * gamma;
+        sc->gamma_last = gamma;
+        sc->sweep = (!close && gamma > 0.0) ? 1 : 0;
+        sc->stop_after = (close || !(gamma > 0.0)) ? 1 : 0;
+    }
+    if (close || !(gamma > 0.0)) return;
+    // (5) first-pass coefficients of A M v_j (tentative column j) and the update weights
+    const double dl = colsum[2 * j] * ie * ie;
+    const double tj = j >= 1 ? fma(eta * gamma, c2[j - 1], tv[j]) : 0.0;
+    const double cj = ((dl - s_cd) * ig - tj) * ig;
+    const double av = fma(gamma, cj, tj);
+    double *Hj = S.Hr + (int64_t)j * (S.m + 1);
+    for (int q = tid; q < j; q += kDotThreads) {
+        const double c1 = (dh[q] - tv[q]) * ig;
+        Hj[q] = c1;
+        const double aV = fma(gamma, c1, tv[q]);
+        S.coef[q] = c2[q] * ig;                          // p
+        S.coef[j + q] = (aV - av * ig * c2[q]) * ig;     // r
+    }
+    if (tid == 0) {
+        Hj[j] = cj;
+        S.kk[0] = ie * ig;            // v_j   = k1 w1 - V p
+        S.kk[1] = ie * ig;            // w1'   = k2 w - k3 w1 - V r
+        S.kk[2] = av * ie * ig * ig;
+    }
+}
+
+// Dual dot sweep of DCGS2 step j over the blocks' rows; the last block to finish
+// then runs the scalar step.  remaining/close: see dcgs_givens.
+__global__ void __launch_bounds__(kDotThreads, 2)
+k_dcgs_dot(int64_t n4, const float4 *__restrict__ V, int64_t ldv4, int j, const float4 *__restrict__ U,
+           const double2 *__restrict__ W, DcgsState S, int close) {
+    pdl_wait();
+    pdl_trigger();
+    if (S.sc->active == 0) return;
+    __shared__ float red[kDotThreads / 32][2 * kDCH + 1];
+    __shared__ int s_last;
+    int q0 = 0;
+    for (; j - q0 > kDCH; q0 += kDCH) dual_chunk<kDCH, false>(n4, V, ldv4, q0, j, U, W, S.part, S.ldp, red);
+    if (j - q0 == kDCH) dual_chunk<kDCH, true>(n4, V, ldv4, q0, j, U, W, S.part, S.ldp, red);
+    else dual_tail<true>(j - q0, n4, V, ldv4, q0, j, U, W, S.part, S.ldp, red);
+    // the last block to finish sums the partials (threadfence-reduction pattern)
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int ticket = atomicAdd(&S.sc->ticket, 1);
+        s_last = ticket == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) S.sc->ticket = 0;
+    dcgs_scalar_step(S, j, close, gridDim.x);
+}
+
+// Column c = j-1 of H is final: copy it into R, apply the previous rotations,
+// form rotation c and update g; then jdone = j, and the cycle stops when
+// |g_{c+1}| <= tol ||b||, when j reaches `remaining` steps, at the end of the
+// cycle, or when the scalar step asked for it (invariant subspace, gamma = 0).
+// One warp; the rotations are a serial chain (thread 0).
+__device__ void dcgs_givens(const DcgsState &S, int j, int remaining) {
+    Scal *sc = S.sc;
+    const int c = j - 1, m = S.m;
+    const double *Hc = S.Hr + (int64_t)c * (m + 1);
+    double *Rc = S.R + (int64_t)c * (m + 1);
+    __shared__ double hc[kMaxRestart + 2];
+    for (int i = threadIdx.x; i <= c + 1; i += 32) hc[i] = Hc[i];
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        double carry = hc[0];
+        for (int i = 0; i < c; i++) {
+            const double ci = S.cs[i], si = S.sn[i], b = hc[i + 1];
+            hc[i] = fma(ci, carry, si * b);
+            carry = fma(ci, b, -si * carry);
+        }
+        const double a = carry, b = hc[c + 1];
         double cc = 1.0, ss = 0.0;
         if (b != 0.0) {
             const double t = hypot(a, b);
             cc = a / t;
             ss = b / t;
         }
-        cs[c] = cc;
-        sn[c] = ss;
-        hc[c] = cc * a + ss * b;
+        S.cs[c] = cc;
+        S.sn[c] = ss;
+        hc[c] = fma(cc, a, ss * b);
         hc[c + 1] = 0.0;
-        for (int i = 0; i <= c + 1; i++) Rc[i] = hc[i];
-        const double gc = g[c];
-        g[c + 1] = -ss * gc;
-        g[c] = cc * gc;
-        est = fabs(ss * gc);
-    }
-    __syncthreads();
-    return est;
-}
-
-// One block.  dots = [c' (j), d' (j), delta'] (unscaled); partial/nb: the
-// squared norm of the tentative vector by blocks (j >= 1; eta = sc->beta at
-// j = 0).  close: only make column j-1 final (the end of a cycle).
-// Writes coef = [p (j), r (j)] and kk = [k1, k2, k3] for k_dcgs_update2.
-__global__ void __launch_bounds__(kThreads)
-k_dcgs_small(int j, int m, int remaining, int close, double *Hr, double *R, double *cs, double *sn, double *g,
-             Scal *sc, const double *__restrict__ dots, const double *__restrict__ partial, int nb, double *coef,
-             double *kk, int *calls) {
-    pdl_wait();
-    pdl_trigger();
-    if (sc->active == 0) return;
-    __shared__ double c2[kMaxRestart + 1], dh[kMaxRestart + 1], t[kMaxRestart + 2], hc[kMaxRestart + 2];
-    __shared__ double sh_gamma, sh_eta;
-    double e2 = 0.0;
-    if (j >= 1)
-        for (int b = threadIdx.x; b < nb; b += kThreads) e2 += partial[b];
-    e2 = block_sum(e2);
-    if (threadIdx.x == 0) sh_eta = j >= 1 ? sqrt(e2) : sc->beta;
-    __syncthreads();
-    const double eta = sh_eta;
-    if (!(eta > 0.0) || !isfinite(eta)) {  // invariant subspace (or a non-finite vector)
-        if (j >= 1) {
-            if (threadIdx.x == 0) Hr[(int64_t)(j - 1) * (m + 1) + j] = 0.0;
-            givens_column(j - 1, m, Hr, R, cs, sn, g, hc);
-        }
-        if (threadIdx.x == 0) {
-            if (calls) atomicAdd(calls, 1);
-            sc->jdone = j;
-            if (!isfinite(eta)) sc->state = 3;
+        const double gc = S.g[c];
+        S.g[c + 1] = -ss * gc;
+        S.g[c] = cc * gc;
+        const double est = fabs(ss * gc);
+        sc->jdone = j;
+        if (!isfinite(est)) {
+            sc->state = 3;
+            sc->active = 0;
+        } else if (est <= sc->tolb || j >= remaining || sc->stop_after) {
             sc->active = 0;
         }
-        return;
     }
-    const double ie = 1.0 / eta;
-    double cc = 0.0;
-    for (int q = threadIdx.x; q < j; q += kThreads) {
-        const double a = dots[q] * ie;
-        c2[q] = a;
-        dh[q] = dots[j + q] * ie;
-        cc += a * a;
-    }
-    cc = block_sum(cc);
-    if (threadIdx.x == 0) sh_gamma = sqrt(fmax(1.0 - cc, 0.0));
-    __syncthreads();
-    const double gamma = sh_gamma;
-    if (j >= 1) {  // column j-1 is final now
-        double *Hc = Hr + (int64_t)(j - 1) * (m + 1);
-        for (int q = threadIdx.x; q < j; q += kThreads) Hc[q] += eta * c2[q];
-        if (threadIdx.x == 0) Hc[j] = eta * gamma;
-        __syncthreads();
-        const double est = givens_column(j - 1, m, Hr, R, cs, sn, g, hc);
-        if (threadIdx.x == 0) {
-            if (calls) atomicAdd(calls, 1);
-            sc->jdone = j;
-            if (!isfinite(est)) {
-                sc->state = 3;
-                sc->active = 0;
-            } else if (est <= sc->tolb || j >= remaining || close || !(gamma > 0.0)) {
-                sc->active = 0;
-            }
-        }
-        __syncthreads();
-        if (sc->active == 0) return;
-    }
-    // t = H c over the final columns 0..j-1 (rows 0..j)
-    for (int i = threadIdx.x; i <= j; i += kThreads) {
-        double a = 0.0;
-        for (int k = (i > 0 ? i - 1 : 0); k < j; k++) a += Hr[(int64_t)k * (m + 1) + i] * c2[k];
-        t[i] = a;
-    }
-    double cd = 0.0;
-    for (int q = threadIdx.x; q < j; q += kThreads) cd += c2[q] * dh[q];
-    cd = block_sum(cd);
-    __syncthreads();
-    const double dl = dots[2 * j] * ie * ie;
-    const double ig = 1.0 / gamma;
-    // first-pass coefficients of A M v_j (tentative column j) and the update weights
-    double *Hj = Hr + (int64_t)j * (m + 1);
-    const double cj = ((dl - cd) * ig - t[j]) * ig;
-    const double av = t[j] + gamma * cj;
-    for (int q = threadIdx.x; q < j; q += kThreads) {
-        const double c1 = (dh[q] - t[q]) * ig;
-        Hj[q] = c1;
-        const double aV = t[q] + gamma * c1;
-        coef[q] = c2[q] * ig;                          // p
-        coef[j + q] = (aV - av * ig * c2[q]) * ig;     // r
-    }
-    if (threadIdx.x == 0) {
-        Hj[j] = cj;
-        kk[0] = ie * ig;            // v_j   = k1 w1 - V p
-        kk[1] = ie * ig;            // w1'   = k2 w - k3 w1 - V r
-        kk[2] = av * ie * ig * ig;
-    }
+    __syncwarp();
+    for (int i = threadIdx.x; i <= c + 1; i += 32) Rc[i] = hc[i];
+}
+
+// The rotation of the last column at the end of a cycle (no update sweep follows).
+__global__ void k_dcgs_givens(DcgsState S, int j, int remaining) {
+    pdl_wait();
+    if (S.sc->active == 0 || j < 1) return;
+    dcgs_givens(S, j, remaining);
 }
 
 // Exact FP32 -> FP64 widening from the IEEE-754 fields with integer
@@ -350,27 +465,37 @@ __device__ __forceinline__ double widen_exact(float f) {
     return __hiloint2double((int)hi, (int)((m & 7u) << 29));
 }
 
+// Block 0 applies the Givens rotation of column j-1 (dcgs_givens), concurrently
+// with the sweep of the other blocks:
 // v_j = k1 w1 - V p (written over w1 in column j, with its (hi, lo) pair) and
 // w1' = k2 w - k3 w1 - V r (written over w in column j + 1, with its FP32
-// copy for the next dual sweep); partial[b] = ||w1'||^2 of block b's rows.
-// Two rows per thread (8-byte pair loads), so many resident warps hide the
-// load latency.
+// copy for the next dual sweep); upart[b] = ||w1'||^2 (FP32) of sweep block b's
+// rows.  Two rows per thread (8-byte pair loads), so many resident warps hide
+// the load latency.
 __global__ void __launch_bounds__(kThreads, 4)
-k_dcgs_update2(int64_t n2, const float2 *__restrict__ Vh, const float2 *__restrict__ Vl, int64_t ldv2, int j,
-               const double *__restrict__ coef, const double *__restrict__ kk, double2 *wcol1, double2 *wcol,
-               float2 *vh_out, float2 *vl_out, float2 *w32, double *partial, const int *gate) {
+k_dcgs_update(int64_t n2, const float2 *__restrict__ Vh, const float2 *__restrict__ Vl, int64_t ldv2, int j,
+              double2 *wcol1, double2 *wcol, float2 *vh_out, float2 *vl_out, float2 *w32, float *upart,
+              DcgsState S, int remaining) {
     pdl_wait();
     pdl_trigger();
-    if (gate && *gate == 0) return;
+    if (blockIdx.x == 0) {
+        if (threadIdx.x < 32 && S.sc->active != 0 && j >= 1) dcgs_givens(S, j, remaining);
+        return;
+    }
+    // a stop decided by block 0 in this launch leaves the sweep's columns unused
+    if (S.sc->active == 0 || S.sc->sweep == 0) return;
+    const int bid = blockIdx.x - 1, nbs = gridDim.x - 1;
     __shared__ float ph[kMaxRestart + 1], rh[kMaxRestart + 1], rl[kMaxRestart + 1];
+    __shared__ float red[kThreads / 32];
+    const double *coef = S.coef;
     for (int q = threadIdx.x; q < j; q += kThreads) {
         ph[q] = (float)coef[q];
         split_pair(coef[j + q], rh[q], rl[q]);
     }
     __syncthreads();
-    const double k1 = kk[0], k2 = kk[1], k3 = kk[2];
-    double nrm = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n2; i += (int64_t)gridDim.x * kThreads) {
+    const double k1 = S.kk[0], k2 = S.kk[1], k3 = S.kk[2];
+    float nrm = 0.0f;
+    for (int64_t i = (int64_t)bid * kThreads + threadIdx.x; i < n2; i += (int64_t)nbs * kThreads) {
         // V p is the reorthogonalization correction: p = c / gamma holds the
         // residual projections (FP32-dot error level, |p| << 1), so V_hi p in FP32
         // is accurate to |p| 2^-24 -- far below the FP64 rounding of v_j.  V r
@@ -417,12 +542,20 @@ k_dcgs_update2(int64_t n2, const float2 *__restrict__ Vh, const float2 *__restri
         wcol[i] = make_double2(x0, x1);
         vh_out[i] = make_float2(vh0, vh1);
         vl_out[i] = make_float2(vl0, vl1);
-        w32[i] = make_float2(hi_part(x0), hi_part(x1));
-        nrm = fma(x0, x0, nrm);
-        nrm = fma(x1, x1, nrm);
+        const float xh0 = hi_part(x0), xh1 = hi_part(x1);
+        w32[i] = make_float2(xh0, xh1);
+        nrm = fmaf(xh0, xh0, nrm);
+        nrm = fmaf(xh1, xh1, nrm);
     }
-    nrm = block_sum(nrm);
-    if (threadIdx.x == 0) partial[blockIdx.x] = nrm;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.0f;
+        for (int w2 = 0; w2 < kThreads / 32; w2++) s += red[w2];
+        upart[bid] = s;
+    }
 }
 
 // FP32 copy (hi part) of an FP64 vector, four rows per thread
@@ -783,7 +916,7 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
 
     Work W;
     W.nb = (int)std::min<int64_t>(cdiv(n, kThreads), 4LL * ctx->num_sms);
-    DTemp<double> V, H, cs, sn, g, y, z, u, part, part2;
+    DTemp<double> V, H, cs, sn, g, y, z, u, part;
     DTemp<float> V32, VL, w32;  // the basis as FP32 (hi, lo) pairs; fl32(w) after pass 1
     DTemp<Scal> scd;
     const int64_t ldv = (n + 3) / 4 * 4, n4 = ldv / 4;  // columns padded to 16-byte vectors
@@ -798,9 +931,8 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
         SAIT_CK(cudaMemsetAsync(w32.p + n, 0, (ldv - n) * sizeof(float), s));
     }
     SAIT_CK(H.alloc((size_t)(m + 1) * m, s));
-    DTemp<double> R, yd, coef, kk;
+    DTemp<double> R, coef, kk;
     SAIT_CK(R.alloc((size_t)(m + 1) * m, s));
-    SAIT_CK(yd.alloc((size_t)2 * m + 2, s));
     SAIT_CK(coef.alloc((size_t)2 * m + 2, s));
     SAIT_CK(kk.alloc(4, s));
     SAIT_CK(cs.alloc(m, s));
@@ -809,15 +941,20 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
     SAIT_CK(y.alloc(m + 2, s));
     SAIT_CK(z.alloc(n, s));
     SAIT_CK(u.alloc(n, s));
-    const int ldp2 = 2 * m + 2;  // dual sweep: V^T u, V^T w, u . w
-    SAIT_CK(part.alloc((size_t)W.nb * std::max(ldp2, 3), s));
-    const int nb_upd = (int)std::min<int64_t>(cdiv(2 * n4, kThreads), 16LL * ctx->num_sms);
-    const int nb_dot = (int)std::min<int64_t>(cdiv(n4, kThreads), (int64_t)W.nb);
-    SAIT_CK(part2.alloc((size_t)std::max(W.nb, nb_upd), s));
+    SAIT_CK(part.alloc((size_t)W.nb * 3, s));
+    // DCGS2: dual dot sweep on two 512-thread blocks per SM, partials column-major
+    // (2m + 1 slots, leading dimension a multiple of 4, padding zero); update
+    // sweep on up to 16 blocks of 256 per SM plus the Givens block
+    const int nb_dot = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n4, kDotThreads), 2LL * ctx->num_sms));
+    const int ldp = (nb_dot + 3) / 4 * 4;
+    const int nb_upd = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(2 * n4, kThreads), 16LL * ctx->num_sms));
+    DTemp<float> dpart, upart;
+    SAIT_CK(dpart.alloc((size_t)(2 * m + 2) * ldp, s));
+    SAIT_CK(cudaMemsetAsync(dpart.p, 0, (size_t)(2 * m + 2) * ldp * sizeof(float), s));
+    SAIT_CK(upart.alloc((size_t)nb_upd, s));
     SAIT_CK(scd.alloc(1, s));
     SAIT_CK(cudaMemsetAsync(scd.p, 0, sizeof(Scal), s));
     W.partial = part.p;
-    W.partial2 = part2.p;
     Scal *sc = scd.p;
     const int *act = &sc->active;
     double *r0 = &sc->r0;
@@ -862,24 +999,22 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
         launch_k(k_hi4, egrid, kThreads, 0, s, n4, (const double2 *)V.p, (float4 *)w32.p);
         const int remaining = maxit - iters;
         const float4 *Vh4 = (const float4 *)V32.p;
+        DcgsState S{dpart.p, ldp, upart.p, nb_upd, H.p, R.p, cs.p, sn.p, g.p, coef.p, kk.p, sc,
+                    group_counter(ctx, SAIT_TIMER_ORTHO), m};
         auto ortho = [&](int j, int close) {
             double *wj = V.p + (size_t)j * ldv;
             const double2 *wn = (const double2 *)(close ? wj : V.p + (size_t)(j + 1) * ldv);
             ScopedTimer tm(ctx, SAIT_TIMER_ORTHO);
-            launch_k(k_dcgs_dot, nb_dot, kThreads, 0, s, n4, Vh4, n4, j, (const float4 *)w32.p, wn, W.partial,
-                     ldp2, act);
-            // reduce, small and update may each start while their predecessor drains
-            (void)launch_pdl(k_reduce, 2 * j + 1, kThreads, 0, s, (const double *)W.partial, nb_dot, ldp2, yd.p,
-                             act, (double *)nullptr, 0);
-            (void)launch_pdl(k_dcgs_small, 1, kThreads, 0, s, j, m, remaining, close, H.p, R.p, cs.p, sn.p, g.p,
-                             sc, (const double *)yd.p, (const double *)W.partial2, nb_upd, coef.p, kk.p,
-                             group_counter(ctx, SAIT_TIMER_ORTHO));
+            // each kernel may be scheduled while its predecessor drains
+            (void)launch_pdl(k_dcgs_dot, nb_dot, kDotThreads, 0, s, n4, Vh4, n4, j, (const float4 *)w32.p, wn, S,
+                             close);
             if (!close)
-                (void)launch_pdl(k_dcgs_update2, nb_upd, kThreads, 0, s, 2 * n4, (const float2 *)V32.p,
-                         (const float2 *)VL.p, 2 * n4, j, (const double *)coef.p, (const double *)kk.p,
-                         (double2 *)wj, (double2 *)(V.p + (size_t)(j + 1) * ldv),
-                         (float2 *)(V32.p + (size_t)j * ldv), (float2 *)(VL.p + (size_t)j * ldv), (float2 *)w32.p,
-                         W.partial2, act);
+                (void)launch_pdl(k_dcgs_update, 1 + nb_upd, kThreads, 0, s, 2 * n4, (const float2 *)V32.p,
+                                 (const float2 *)VL.p, 2 * n4, j, (double2 *)wj,
+                                 (double2 *)(V.p + (size_t)(j + 1) * ldv), (float2 *)(V32.p + (size_t)j * ldv),
+                                 (float2 *)(VL.p + (size_t)j * ldv), (float2 *)w32.p, upart.p, S, remaining);
+            else
+                (void)launch_pdl(k_dcgs_givens, 1, 32, 0, s, S, j, remaining);
         };
         for (int j = 0; j < m; j++) {
             double *wj = V.p + (size_t)j * ldv, *w = V.p + (size_t)(j + 1) * ldv;
