@@ -296,6 +296,37 @@ def eigen_workload(sg, ctx, torch, device, stream, factors="ilut"):
         out[store] = {"ms": round(ms, 3), "iters": info.iters, "max_resid": info.rel_resid, "status": st,
                       "max_rel_eig_diff_vs_f64": float(np.abs(lam - ref).max() / np.abs(ref).max()),
                       "lambda_min": float(lam[0]), "lambda_max": float(lam[-1])}
+    out["vs_oracle"] = eigen_vs_oracle(sg, ctx, torch, device)
+    return out
+
+
+def eigen_vs_oracle(sg, ctx, torch, device):
+    """The same eigenproblem at the size of the stored FP64 oracle run
+    (tests/golden/eigen_varcoef<G>.json, written by make_eigen_fixture.py): the
+    largest relative eigenvalue error of each storage against the oracle."""
+    here = os.path.join(ROOT, "tests", "golden")
+    fixtures = sorted(f for f in os.listdir(here) if f.startswith("eigen_varcoef") and f.endswith(".json"))
+    if not fixtures:
+        return None
+    with open(os.path.join(here, fixtures[-1])) as f:
+        fx = json.load(f)
+    A = synth.varcoef3d(fx["grid"], 1.0, synth.SEED_BASE + 3)
+    d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in
+         (("rp", A.rp), ("ci", A.ci), ("va", A.va))}
+    X0 = torch.from_numpy(synth.uniform(synth.SEED_BASE + 10, (A.n, fx["k"]))).to(device)
+    ref8 = np.array(fx["tol_1e-8"]["lambda"])
+    ref11 = np.array(fx["tol_1e-11"]["lambda"])
+    out = {"grid": fx["grid"], "n": A.n, "oracle_iters_1e-8": fx["tol_1e-8"]["iters"]}
+    for store in ("f64", "f32", "bf16"):
+        L, U = sg.sait_ilut(ctx, A.n, d["rp"], d["ci"], d["va"], 1e-4, 10)
+        P = sg.sait_prec_create_sait(ctx, sg.sait_build(ctx, L, True, 3, DROP, TAU, store=store),
+                                     sg.sait_build(ctx, U, False, 3, DROP, TAU, store=store))
+        Am = sg.sait_mat_create_csr(ctx, A.n, d["rp"], d["ci"], d["va"])
+        lam, X, info, st = sg.sait_lobpcg(ctx, Am, P, X0.clone(), tol=TOL, maxit=1000, check=False)
+        lam = lam.cpu().numpy()
+        out[store] = {"iters": info.iters, "status": st,
+                      "max_rel_eig_err_vs_oracle": float(np.abs(lam - ref8).max() / np.abs(ref8).max()),
+                      "max_rel_eig_err_vs_oracle_tight": float(np.abs(lam - ref11).max() / np.abs(ref11).max())}
     return out
 
 

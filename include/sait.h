@@ -170,14 +170,29 @@ sait_status sait_mat_export_csr(sait_ctx ctx, sait_mat M, int32_t *row_ptr, int3
  * creates the reduced copy of the values on first use.  Synchronizes. */
 sait_status sait_mat_set_store(sait_ctx ctx, sait_mat M, sait_dtype store);
 
-/* ---- ILU(0) factors (Section 4: level-0 ILU factors are SAIT's input) ---- */
+/* ---- ILU factors (Section 4: level-0 and level-1 ILU factors are SAIT's input) */
 
-/* Level-0 incomplete LU of A on A's pattern (Saad, Algorithm 10.4, IKJ order),
- * computed on the GPU by level scheduling.  *L: unit lower triangular with
- * its unit diagonal stored; *U: upper triangular with the pivots.  A needs
- * every diagonal entry stored.  Returns SAIT_ERR_ZERO_PIVOT if a pivot is
- * zero or non-finite.  Synchronizes. */
+/* Level-0 incomplete LU of A on A's pattern (Saad, Algorithm 10.4, IKJ order):
+ * sait_iluk with level 0. */
 sait_status sait_ilu0(sait_ctx ctx, const sait_csr *A, sait_mat *L, sait_mat *U);
+
+/* Level-of-fill incomplete LU, ILU(level) for level 0 or 1 (Saad, Algorithm
+ * 10.5): the entries of A's pattern have level 0, an update a_ij -= l_ik u_kj
+ * gives (i,j) the level lev_ik + lev_kj + 1, and entries above `level` are
+ * dropped; the elimination runs in IKJ order on the kept pattern, so the
+ * factors are bit-identical to a row-by-row evaluation of the algorithm.  The
+ * paper feeds level-0 and level-1 factors to SAIT (Section 4, Tables
+ * runtime_SAIT and runtime_Jacobi).  Computed on the GPU: the level-1 pattern
+ * row by row, then the numeric rows by warps that wait for the rows they
+ * depend on (bounded waits).
+ * A: device CSR, sorted columns, every diagonal entry stored.  *L: unit lower
+ * triangular with its unit diagonal stored; *U: upper triangular with the
+ * pivots; both new matrices owned by the caller.  Errors: level < 0 gives
+ * SAIT_ERR_INVALID_ARG, level > 1 or a row with more than 512 level-1
+ * candidate columns SAIT_ERR_UNSUPPORTED, a missing diagonal or a zero or
+ * non-finite pivot SAIT_ERR_ZERO_PIVOT, a dependency wait that runs out
+ * SAIT_ERR_TIMEOUT.  Synchronizes. */
+sait_status sait_iluk(sait_ctx ctx, const sait_csr *A, int32_t level, sait_mat *L, sait_mat *U);
 
 /* ILUT(tau, lfil) factors of A (Saad, Iterative Methods for Sparse Linear
  * Systems, Algorithm 10.6); threshold ILU factors are among the triangular

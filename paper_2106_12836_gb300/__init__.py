@@ -22,7 +22,7 @@ __all__ = [
     "SaitError", "Context", "Mat", "Prec", "Info", "DROP", "DTYPE",
     "sait_ctx_create", "sait_ctx_destroy", "sait_status_string", "sait_ctx_last_error",
     "sait_mat_create_csr", "sait_mat_destroy", "sait_mat_info", "sait_mat_export_csr",
-    "sait_mat_set_store", "sait_ilu0", "sait_build", "sait_spmv", "sait_apply",
+    "sait_mat_set_store", "sait_ilu0", "sait_iluk", "sait_build", "sait_spmv", "sait_apply",
     "sait_prec_create_sait", "sait_prec_create_ilu", "sait_prec_levels", "sait_prec_apply",
     "sait_prec_destroy", "sait_gmres", "sait_bicgstab", "sait_ctx_set_timing", "sait_ctx_stats",
     "sait_apply_static", "APPLY_STATIC_MAX_N", "sait_spmm", "sait_apply_multi", "sait_mat_transpose",
@@ -40,7 +40,7 @@ LOWER, UPPER = 0, 1
 EXPORTS = [
     "sait_ctx_create", "sait_ctx_destroy", "sait_status_string", "sait_ctx_last_error",
     "sait_mat_create_csr", "sait_mat_destroy", "sait_mat_info", "sait_mat_export_csr",
-    "sait_mat_set_store", "sait_ilu0", "sait_build", "sait_spmv", "sait_apply",
+    "sait_mat_set_store", "sait_ilu0", "sait_iluk", "sait_build", "sait_spmv", "sait_apply",
     "sait_prec_create_sait", "sait_prec_create_ilu", "sait_prec_levels", "sait_prec_apply",
     "sait_prec_destroy", "sait_gmres", "sait_bicgstab", "sait_ctx_set_timing", "sait_ctx_stats",
     "sait_apply_static", "sait_spmm", "sait_apply_multi", "sait_mat_transpose", "sait_outer_on_pattern",
@@ -154,6 +154,7 @@ def _L():
             "sait_mat_export_csr": [vp, vp, vp, vp, vp],
             "sait_mat_set_store": [vp, vp, C.c_int],
             "sait_ilu0": [vp, C.POINTER(_Csr), C.POINTER(vp), C.POINTER(vp)],
+            "sait_iluk": [vp, C.POINTER(_Csr), i32, C.POINTER(vp), C.POINTER(vp)],
             "sait_build": [vp, vp, C.c_int, i32, _Drop, C.c_int, C.POINTER(vp)],
             "sait_spmv": [vp, vp, vp, vp],
             "sait_apply": [vp, vp, vp, vp, vp],
@@ -368,6 +369,14 @@ def sait_ilu0(ctx: Context, n: int, rp, ci, va):
     A = _csr(n, rp, ci, va)
     hl, hu = C.c_void_p(), C.c_void_p()
     _check(ctx, _L().sait_ilu0(ctx.h, C.byref(A), C.byref(hl), C.byref(hu)), "sait_ilu0")
+    return Mat(ctx, hl), Mat(ctx, hu)
+
+
+def sait_iluk(ctx: Context, n: int, rp, ci, va, level: int):
+    """Level-of-fill ILU(level) factors, level 0 or 1 (Saad, Algorithm 10.5): (L, U) as sait_ilu0."""
+    A = _csr(n, rp, ci, va)
+    hl, hu = C.c_void_p(), C.c_void_p()
+    _check(ctx, _L().sait_iluk(ctx.h, C.byref(A), int(level), C.byref(hl), C.byref(hu)), "sait_iluk")
     return Mat(ctx, hl), Mat(ctx, hu)
 
 

@@ -10,7 +10,7 @@
 
 #include "sait.h"
 
-// d_word layout: [0] per-call error flags, [1] ILU(0) row ticket, [2..6] SpGEMM
+// d_word layout: [0] per-call error flags, [2..6] SpGEMM
 // row-bin counters, [8..9] level analysis, [10] SpGEMM error flags, [16 + g]
 // device-side call counters of timer group g (incremented by kernels that did
 // real work).
@@ -197,6 +197,17 @@ __device__ __forceinline__ void df_term(float &S, float &E, float vh, float vl, 
     df_add(S, E, p, e);
 }
 
+// Out-of-line conversions for the rare values outside the integer paths
+// below.  Kept out of line so that the compiler cannot evaluate them
+// speculatively for every value: on GB300 a float <-> double conversion takes
+// the narrow FP64 pipe, and a speculated one per vector entry made the
+// Gram-Schmidt sweeps FP64-pipe bound.
+static __device__ __noinline__ void split_pair_slow(double v, float &hi, float &lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+static __device__ __noinline__ float hi_part_slow(double v) { return (float)v; }
+
 // (hi, lo) with hi = v truncated to 24 significant bits and lo the next 23
 // bits of v, both taken from the IEEE-754 fields with integer operations and
 // one exact FP32 subtraction, so no FP64 or conversion instruction is spent
@@ -209,8 +220,7 @@ __device__ __forceinline__ void split_pair(double v, float &hi, float &lo) {
     const int ef = e - 896;  // FP32 biased exponent of hi (1023 - 127 = 896)
     const int el = e - 919;  // FP32 biased exponent whose mantissa ulp weighs the fraction bits 6..28
     if (e <= 948 || ef >= 255) {
-        hi = (float)v;
-        lo = (float)(v - (double)hi);
+        split_pair_slow(v, hi, lo);
         return;
     }
     const unsigned sign = (unsigned)(b >> 63) << 31;
@@ -226,9 +236,51 @@ __device__ __forceinline__ float hi_part(double v) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const int e = (int)((b >> 52) & 0x7ff);
     const int ef = e - 896;
-    if (ef <= 0 || ef >= 255) return (float)v;
+    if (ef <= 0 || ef >= 255) return hi_part_slow(v);
     return __uint_as_float(((unsigned)(b >> 63) << 31) | ((unsigned)ef << 23) |
                            (unsigned)((b & ((1ULL << 52) - 1)) >> 29));
+}
+
+// Exact FP32 -> FP64 widening from the IEEE-754 fields with integer
+// operations only (zero, subnormal, infinite and NaN inputs included, no
+// branch).  On GB300 a hardware float-to-double conversion occupies the narrow
+// FP64 pipe longer than a DFMA, and the sweeps and products widen one value
+// per row.
+__device__ __forceinline__ double widen_exact(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu;
+    unsigned m = b & 0x7fffffu;
+    unsigned ed = e + 896u;                                   // normal
+    const int sh = __clz(m | 1u) - 8;                         // subnormal: bring the leading 1 to bit 23
+    const unsigned ms = (m << sh) & 0x7fffffu;
+    ed = e == 0xffu ? 0x7ffu : ed;                            // infinity / NaN
+    ed = e == 0u ? (m ? 897u - (unsigned)sh : 0u) : ed;       // subnormal / zero
+    m = (e == 0u && m) ? ms : m;
+    const unsigned hi = (b & 0x80000000u) | (ed << 20) | (m >> 3);
+    return __hiloint2double((int)hi, (int)((m & 7u) << 29));
+}
+
+static __device__ __noinline__ float narrow_slow(double v) { return (float)v; }
+
+// FP64 -> FP32 rounded to nearest (ties to even) with integer operations:
+// the 23 leading fraction bits, rounded up when the 29 dropped bits exceed
+// half an FP32 ulp or equal it with an odd last bit (a carry moves into the
+// exponent, and past the largest finite value gives infinity, as IEEE
+// rounding does).  |v| < 2^-126 gives a signed zero (no FP32 subnormals);
+// |v| >= 2^128, infinities and NaNs take the conversion instruction.  The
+// products of FP32- and BF16-stored matrices narrow one FP64 vector entry per
+// matrix entry, which as conversions would keep GB300's FP64 pipe busy.
+__device__ __forceinline__ float narrow_rn(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int ef = (int)((b >> 52) & 0x7ff) - 896;
+    const unsigned sign = (unsigned)(b >> 63) << 31;
+    if (ef >= 255) return narrow_slow(v);
+    if (ef <= 0) return __uint_as_float(sign);
+    const unsigned long long frac = b & ((1ULL << 52) - 1);
+    const unsigned m = (unsigned)(frac >> 29);
+    const unsigned rest = (unsigned)frac & ((1u << 29) - 1);
+    const unsigned up = (rest > (1u << 28)) | ((rest == (1u << 28)) & (m & 1u));
+    return __uint_as_float(sign | ((((unsigned)ef << 23) | m) + up));
 }
 
 // S + E as an FP64 value
@@ -263,9 +315,21 @@ __device__ __forceinline__ float acc_value(float a) { return a; }
 template <typename A, typename TX> struct XCast {
     __device__ __forceinline__ static A get(TX x) { return (A)x; }
 };
+template <> struct XCast<float, double> {
+    __device__ __forceinline__ static float get(double x) { return narrow_rn(x); }
+};
 template <typename TX> struct XCast<DF, TX> {
     __device__ __forceinline__ static TX get(TX x) { return x; }
 };
+
+// accumulator A stored as output element type TY (FP32 sums widen exactly and
+// FP64 sums narrow with integer operations, see widen_exact and narrow_rn)
+__device__ __forceinline__ void put_out(double *p, double a) { *p = a; }
+__device__ __forceinline__ void put_out(double *p, float a) { *p = widen_exact(a); }
+__device__ __forceinline__ void put_out(double *p, const DF &a) { *p = widen_exact(a.S) + widen_exact(a.E); }
+__device__ __forceinline__ void put_out(float *p, float a) { *p = a; }
+__device__ __forceinline__ void put_out(float *p, double a) { *p = narrow_rn(a); }
+__device__ __forceinline__ void put_out(float *p, const DF &a) { *p = narrow_rn(widen_exact(a.S) + widen_exact(a.E)); }
 
 // Exact widening of stored FP32 / BF16 values to FP64 (a hardware
 // conversion; integer bit assembly measured slower on GB300).
@@ -332,8 +396,6 @@ sait_status build_levels(sait_ctx ctx, const int32_t *rp, const int32_t *ci, int
 void free_levels(LevelSchedule *L);
 cudaError_t launch_trisolve(const sait_mat_s *T, const LevelSchedule &lev, bool lower,
                             const double *b, double *x, cudaStream_t s);
-sait_status frontier_schedule(sait_ctx ctx, const int32_t *rp, const int32_t *ci, int64_t n, bool lower,
-                              const int32_t *dpos, double *a, int *err_word, LevelSchedule *out);
 
 // apply_static.cu: drop the cached device address of the static apply's array
 void static_apply_forget(int dev);

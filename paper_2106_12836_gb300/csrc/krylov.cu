@@ -232,16 +232,18 @@ __device__ __forceinline__ double quarter_sum(const float *x, int cnt, int sub) 
 // dcgs_givens); writes coef = [p (j), r (j)], kk = [k1, k2, k3] and the first-pass
 // column j of H, or with `close` only finalizes column j-1.
 //
-// GB300's FP64 pipe has a 64-cycle dependent latency (sqrt and division about
-// 650), so this step avoids long FP64 chains: the partial sums are added in
-// FP32 (they are FP32 dot products already), every thread evaluates the
-// scalar recurrences itself instead of waiting on a broadcast, reciprocal
-// square roots replace square roots and divisions, and t = H c is split
-// over eight threads per row.
+// GB300's FP64 pipe issues about two thread operations per cycle per SM with
+// a 64-cycle dependent latency (sqrt and division about 650), so this step
+// keeps FP64 work short and off the wide paths: the partial sums are added in
+// FP32 (they are FP32 dot products already), the scalar recurrences run on
+// one thread and are broadcast through shared memory, reciprocal square roots
+// replace square roots and divisions, and t = H c is split over eight
+// threads per row.
 __device__ void dcgs_scalar_step(const DcgsState &S, int j, int close, int nbd) {
     __shared__ double colsum[2 * kMaxRestart + 2];
     __shared__ double c2[kMaxRestart + 1], dh[kMaxRestart + 1], tv[kMaxRestart + 2];
-    __shared__ double s_cc, s_cd, s_e2;
+    __shared__ double s_cc, s_cd, s_e2, s_eta, s_ie, s_ig, s_gamma, s_av;
+    __shared__ int s_ok;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarp = kDotThreads / 32;
     Scal *sc = S.sc;
@@ -262,19 +264,19 @@ __device__ void dcgs_scalar_step(const DcgsState &S, int j, int close, int nbd) 
         if (lane == 0) s_e2 = (double)s0;
     }
     __syncthreads();
-    // (2) eta = ||w1||, computed by every thread
-    double eta, ie;
-    if (j >= 1) {
-        const double e2 = s_e2;
-        ie = rsqrt(e2);
-        eta = e2 * ie;
-    } else {
-        eta = sc->beta;
-        ie = 1.0 / eta;
-    }
+    // (2) eta = ||w1|| (one thread)
     double *Hc = S.Hr + (int64_t)(j - 1) * (S.m + 1);  // column j-1 (j >= 1)
-    if (!(eta > 0.0) || !isfinite(eta) || !isfinite(ie)) {  // invariant subspace (or a non-finite vector)
-        if (tid == 0) {
+    if (tid == 0) {
+        double eta, ie;
+        if (j >= 1) {
+            ie = rsqrt(s_e2);
+            eta = s_e2 * ie;
+        } else {
+            eta = sc->beta;
+            ie = 1.0 / eta;
+        }
+        const int ok = eta > 0.0 && isfinite(eta) && isfinite(ie);
+        if (!ok) {  // invariant subspace (or a non-finite vector)
             if (S.calls) atomicAdd(S.calls, 1);
             if (!isfinite(eta)) sc->state = 3;
             sc->sweep = 0;
@@ -286,14 +288,19 @@ __device__ void dcgs_scalar_step(const DcgsState &S, int j, int close, int nbd) 
                 sc->active = 0;
             }
         }
-        return;
+        s_ok = ok;
+        s_eta = eta;
+        s_ie = ie;
     }
+    __syncthreads();
+    if (!s_ok) return;
+    const double eta = s_eta, ie = s_ie;
     for (int q = tid; q < j; q += kDotThreads) {
         c2[q] = colsum[q] * ie;
         dh[q] = colsum[j + q] * ie;
     }
     __syncthreads();
-    // (3) warp 0: cc = c.c and cd = c.d; the other warps: column j-1 of H and t = H c
+    // (3) warp 0: cc = c.c and cd = c.d; the other warps: t = H c
     if (warp == 0) {
         double a = 0.0, b = 0.0;
         for (int q = lane; q < j; q += 32) {
@@ -332,23 +339,36 @@ __device__ void dcgs_scalar_step(const DcgsState &S, int j, int close, int nbd) 
     __syncthreads();
     if (j >= 1)  // column j-1 final: H(0:j-1, j-1) += eta c (t above read the old column)
         for (int q = tid; q < j; q += kDotThreads) Hc[q] = fma(eta, c2[q], Hc[q]);
-    // (4) gamma = sqrt(1 - c.c), every thread
-    const double cc = s_cc, om = 1.0 - cc;
-    const double ig = om > 0.0 ? rsqrt(om) : 0.0;
-    const double gamma = om > 0.0 ? om * ig : 0.0;
+    // (4) gamma = sqrt(1 - c.c) and the scalars of column j (one thread)
     if (tid == 0) {
+        const double om = 1.0 - s_cc;
+        const double ig = om > 0.0 ? rsqrt(om) : 0.0;
+        const double gamma = om > 0.0 ? om * ig : 0.0;
         if (S.calls) atomicAdd(S.calls, 1);
         if (j >= 1) Hc[j] = eta * gamma;
         sc->gamma_last = gamma;
         sc->sweep = (!close && gamma > 0.0) ? 1 : 0;
         sc->stop_after = (close || !(gamma > 0.0)) ? 1 : 0;
+        if (!close && gamma > 0.0) {
+            // first-pass coefficients of A M v_j (tentative column j): a_j and the
+            // weights k1, k2, k3 of the update
+            const double dl = colsum[2 * j] * ie * ie;
+            const double tj = j >= 1 ? fma(eta * gamma, c2[j - 1], tv[j]) : 0.0;
+            const double cj = ((dl - s_cd) * ig - tj) * ig;
+            const double av = fma(gamma, cj, tj);
+            S.Hr[(int64_t)j * (S.m + 1) + j] = cj;
+            S.kk[0] = ie * ig;            // v_j   = k1 w1 - V p
+            S.kk[1] = ie * ig;            // w1'   = k2 w - k3 w1 - V r
+            S.kk[2] = av * ie * ig * ig;
+            s_av = av;
+        }
+        s_ig = ig;
+        s_gamma = gamma;
     }
+    __syncthreads();
+    const double gamma = s_gamma, ig = s_ig;
     if (close || !(gamma > 0.0)) return;
-    // (5) first-pass coefficients of A M v_j (tentative column j) and the update weights
-    const double dl = colsum[2 * j] * ie * ie;
-    const double tj = j >= 1 ? fma(eta * gamma, c2[j - 1], tv[j]) : 0.0;
-    const double cj = ((dl - s_cd) * ig - tj) * ig;
-    const double av = fma(gamma, cj, tj);
+    const double av = s_av;
     double *Hj = S.Hr + (int64_t)j * (S.m + 1);
     for (int q = tid; q < j; q += kDotThreads) {
         const double c1 = (dh[q] - tv[q]) * ig;
@@ -356,12 +376,6 @@ __device__ void dcgs_scalar_step(const DcgsState &S, int j, int close, int nbd) 
         const double aV = fma(gamma, c1, tv[q]);
         S.coef[q] = c2[q] * ig;                          // p
         S.coef[j + q] = (aV - av * ig * c2[q]) * ig;     // r
-    }
-    if (tid == 0) {
-        Hj[j] = cj;
-        S.kk[0] = ie * ig;            // v_j   = k1 w1 - V p
-        S.kk[1] = ie * ig;            // w1'   = k2 w - k3 w1 - V r
-        S.kk[2] = av * ie * ig * ig;
     }
 }
 
@@ -444,25 +458,6 @@ __global__ void k_dcgs_givens(DcgsState S, int j, int remaining) {
     pdl_wait();
     if (S.sc->active == 0 || j < 1) return;
     dcgs_givens(S, j, remaining);
-}
-
-// Exact FP32 -> FP64 widening from the IEEE-754 fields with integer
-// operations only (zero, subnormal, infinite and NaN inputs included, no
-// branch).  On GB300 a hardware float-to-double conversion occupies the narrow
-// FP64 pipe longer than a DFMA; the update sweep below widens three FP32 sums
-// per row, which made it FP64-pipe bound for short bases.
-__device__ __forceinline__ double widen_exact(float f) {
-    const unsigned b = __float_as_uint(f);
-    const unsigned e = (b >> 23) & 0xffu;
-    unsigned m = b & 0x7fffffu;
-    unsigned ed = e + 896u;                                   // normal
-    const int sh = __clz(m | 1u) - 8;                         // subnormal: bring the leading 1 to bit 23
-    const unsigned ms = (m << sh) & 0x7fffffu;
-    ed = e == 0xffu ? 0x7ffu : ed;                            // infinity / NaN
-    ed = e == 0u ? (m ? 897u - (unsigned)sh : 0u) : ed;       // subnormal / zero
-    m = (e == 0u && m) ? ms : m;
-    const unsigned hi = (b & 0x80000000u) | (ed << 20) | (m >> 3);
-    return __hiloint2double((int)hi, (int)((m & 7u) << 29));
 }
 
 // Block 0 applies the Givens rotation of column j-1 (dcgs_givens), concurrently

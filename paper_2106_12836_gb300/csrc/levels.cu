@@ -6,11 +6,11 @@
 // are found by a frontier sweep over the transposed dependency graph (Kahn's
 // topological order): one launch per level processes the current frontier and
 // releases its dependents, whose in-degree drops to zero, into the next one.
-// ILU(0) is fused into that sweep (a row is factored in the launch of its
-// level), so the factorisation costs one launch per level and O(nnz) work.
 //
-// These are the "exact triangular solvers" that SAIT replaces (Section 3.1)
-// and the level-0 ILU factorisation that supplies SAIT's input (Section 4).
+// These are the "exact triangular solvers" that SAIT replaces (Section 3.1),
+// and the same sweep factors ILU(0) and ILU(1), SAIT's input (Section 4): a
+// row is factored in the launch of its level, so the factorisation costs one
+// launch per level and O(nnz) work.
 #include <algorithm>
 #include <climits>
 
@@ -71,63 +71,24 @@ __global__ void k_dep_fill(int64_t n, const int32_t *__restrict__ rp, const int3
     }
 }
 
-// q[0] begin and q[1] end of the current level in `order`, q[2] append tail,
-// q[3] number of levels found; lptr[l] = start of level l in `order`.
-__global__ void k_front0(int64_t n, const int32_t *__restrict__ indeg, int32_t *order, int *q) {
+// Level 0: the rows without dependencies, appended to order[0 ..) with lcnt[0]
+// as the tail (one atomic per warp).
+__global__ void k_front0(int64_t n, const int32_t *__restrict__ indeg, int32_t *order, int32_t *lcnt) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || indeg[i] != 0) return;
     const unsigned act = __activemask();
     const int lane = threadIdx.x & 31, leader = __ffs(act) - 1;
     int base = 0;
-    if (lane == leader) base = atomicAdd(q + 2, __popc(act));
+    if (lane == leader) base = atomicAdd(lcnt, __popc(act));
     base = __shfl_sync(act, base, leader);
     order[base + __popc(act & ((1u << lane) - 1u))] = (int32_t)i;
 }
 
-__global__ void k_front_init(int *q, int32_t *lptr) {
-    q[0] = 0;
-    q[1] = q[2];
-    q[3] = q[2] > 0 ? 1 : 0;
-    lptr[0] = 0;
-    lptr[1] = q[2];
-}
-
-
-// ILU(0), IKJ order (Saad, Algorithm 10.4), for row i whose dependencies are
-// final, from precomputed update triples (q, f, p): for each L entry q of row
-// i (column k, ascending) a_iq /= a_kk, then a_p -= a_iq a_f for the entries
-// f of U row k (past its diagonal) that match position p of row i.  The
-// triples replace the pattern searches, so the chain of dependent loads per
-// row is short; the fma chain per entry is the IKJ one.
-__device__ __forceinline__ void ilu0_row_triples(int i, const int32_t *__restrict__ rp,
-                                                 const int32_t *__restrict__ dpos, const int32_t *__restrict__ ldiag,
-                                                 const int64_t *__restrict__ tp, const int3 *__restrict__ tr,
-                                                 double *a, int *err) {
-    const int b = rp[i], dq = dpos[i];
-    int64_t t = tp[i];
-    const int64_t te = tp[i + 1];
-    for (int q = b; q < dq; q++) {
-        const double ukk = a[ldiag[q]];
-        if (ukk == 0.0 || !isfinite(ukk)) {
-            atomicOr(err, 1);
-            return;
-        }
-        const double aik = a[q] / ukk;
-        a[q] = aik;
-        for (; t < te; t++) {
-            const int3 x = tr[t];
-            if (x.x != q) break;
-            a[x.z] = fma(-aik, a[x.y], a[x.z]);
-        }
-    }
-    const double d = a[dq];
-    if (d == 0.0 || !isfinite(d)) atomicOr(err, 1);
-}
-
-// Symbolic ILU(0) step, a thread per row: ldiag[q] = position of a_kk for the
-// L entries q of row i (column k), and the triples (q, f, p) with ci[f] ==
-// ci[p], f in U row k past its diagonal, p in row i past q.  Counts only
-// (into cnt) when tr is null.
+// Symbolic ILU step on a fixed pattern, a thread per row: ldiag[q] = position
+// of u_kk for the L entries q of row i (column k), and the update triples
+// (q, f, p) with ci[f] == ci[p], f in U row k past its diagonal, p in row i
+// past q, ordered by q then f (the IKJ order).  Counts only (into cnt) when tr
+// is null.
 __global__ void k_ilu_triples(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                               const int32_t *__restrict__ dpos, int32_t *ldiag, const int64_t *__restrict__ tp,
                               int32_t *cnt, int3 *tr) {
@@ -151,63 +112,6 @@ __global__ void k_ilu_triples(int64_t n, const int32_t *__restrict__ rp, const i
         }
     }
     if (!tr) cnt[i] = c;
-}
-
-// One level, a thread per frontier row: factor it (ILU) from its triples,
-// then release its dependents; a dependent whose in-degree reaches zero joins
-// the next level (one queue atomic per warp).  The last block to finish
-// publishes the next level, so a level costs one launch.
-template <bool ILU>
-__global__ void __launch_bounds__(256)
-k_front_step(int32_t *order, int *q, int32_t *lptr, unsigned *done_blocks, const int64_t *__restrict__ trp,
-             const int32_t *__restrict__ tcol, int32_t *indeg, const int32_t *__restrict__ rp,
-             const int32_t *__restrict__ dpos, const int32_t *__restrict__ ldiag, const int64_t *__restrict__ tp,
-             const int3 *__restrict__ tr, double *a, int *err) {
-    const int begin = q[0], end = q[1];
-    const int lane = threadIdx.x & 31;
-    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t nt = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = begin + gt; r - lane < end; r += nt) {  // warp-uniform trip count
-        const bool valid = r < end;
-        const int i = valid ? order[r] : 0;
-        if (ILU && valid) ilu0_row_triples(i, rp, dpos, ldiag, tp, tr, a, err);
-        int64_t t = valid ? trp[i] : 0;
-        const int64_t te = valid ? trp[i + 1] : 0;
-        while (__any_sync(0xffffffffu, t < te)) {
-            bool rel = false;
-            int d = 0;
-            if (t < te) {
-                d = tcol[t];
-                rel = atomicSub(indeg + d, 1) == 1;
-                t++;
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, rel);
-            if (m) {
-                const int leader = __ffs(m) - 1;
-                int pos = 0;
-                if (lane == leader) pos = atomicAdd(q + 2, __popc(m));
-                pos = __shfl_sync(0xffffffffu, pos, leader);
-                if (rel) order[pos + __popc(m & ((1u << lane) - 1u))] = d;
-            }
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(done_blocks, 1u) == gridDim.x - 1) {  // every block of this level is done
-            __threadfence();
-            const int tail = atomicAdd(q + 2, 0);
-            q[0] = end;
-            q[1] = tail;
-            if (tail > end) {
-                const int l = q[3] + 1;
-                q[3] = l;
-                lptr[l] = tail;
-            }
-            *done_blocks = 0;
-            __threadfence();
-        }
-    }
 }
 
 __global__ void k_diag_pos(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
@@ -257,6 +161,205 @@ __global__ void k_lu_fill(int64_t n, const int32_t *__restrict__ rp, const int32
     lva[lo] = 1.0;
 }
 
+// ---- ILU(p), p = 0 or 1 -------------------------------------------------------------
+// The factorisation (Saad, Algorithm 10.4 on a fixed pattern; Algorithm 10.5
+// chooses the pattern) runs on the pattern S = A's pattern for ILU(0) and
+// S = A's pattern plus the level-1 fill for ILU(1).  Level-1 fill of row i is
+// {j : (i,k) and (k,j) in A's pattern, k < i, j > k}: the level of an entry
+// depends only on levels already fixed, and for p = 1 only on A's pattern,
+// so the rows of S are built independently.  Entries outside S are never
+// pivots and never feed an entry of S, so eliminating on S gives the
+// level-of-fill factors with the same fma chains.
+constexpr int kIluThreads = 256;
+constexpr int kIluCap = 512;               // candidate columns per row for the ILU(1) pattern
+enum : int { kIluErrPivot = 1, kIluErrRow = 8 };
+
+// ILU(1) pattern of row i, one warp: the columns of A's row i, then the strict U
+// part of A's row k for every L column k, deduplicated and ranked.  Count pass
+// (ci_s null): cnt[i] = |S_i|.  Fill pass: sorted columns, A's values (0 for
+// fill) and the diagonal position.
+__global__ void __launch_bounds__(kIluThreads)
+k_ilu1_pattern(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+               const double *__restrict__ va, const int32_t *__restrict__ dpos, int32_t *cnt,
+               const int64_t *__restrict__ rp_s, int32_t *ci_s, double *va_s, int32_t *dpos_s, int *err) {
+    __shared__ int cand[kIluThreads / 32][kIluCap];
+    __shared__ unsigned char first[kIluThreads / 32][kIluCap];
+    const int lane = threadIdx.x & 31;
+    int *C = cand[threadIdx.x >> 5];
+    unsigned char *F = first[threadIdx.x >> 5];
+    const int64_t i = ((int64_t)blockIdx.x * kIluThreads + threadIdx.x) >> 5;
+    if (i >= n) return;
+    const int b = rp[i], e = rp[i + 1], dq = dpos[i];
+    int nc = e - b;
+    bool over = nc > kIluCap;
+    if (!over)
+        for (int q = b + lane; q < e; q += 32) C[q - b] = ci[q];  // A's row first (unique, sorted)
+    for (int q = b; q < dq && !over; q++) {  // then the strict U part of A's row k = ci[q]
+        const int k = ci[q];
+        const int fb = dpos[k] + 1, fe = rp[k + 1];
+        if (nc + (fe - fb) > kIluCap) { over = true; break; }
+        for (int f = fb + lane; f < fe; f += 32) C[nc + f - fb] = ci[f];
+        nc += fe - fb;
+    }
+    __syncwarp();
+    if (over) {
+        if (lane == 0) atomicOr(err, kIluErrRow);
+        return;
+    }
+    for (int x = lane; x < nc; x += 32) {  // first occurrence of its column?
+        const int c = C[x];
+        bool f = true;
+        for (int y = 0; y < x && f; y++) f = C[y] != c;
+        F[x] = f;
+    }
+    __syncwarp();
+    int uniq = 0;
+    for (int x = lane; x < nc; x += 32) {
+        if (!F[x]) continue;
+        uniq++;
+        if (ci_s) {
+            const int c = C[x];
+            int rank = 0;  // distinct columns below c
+            for (int y = 0; y < nc; y++) rank += F[y] && C[y] < c;
+            const int64_t o = rp_s[i] + rank;
+            ci_s[o] = c;
+            va_s[o] = x < e - b ? va[b + x] : 0.0;
+            if (c == (int)i) dpos_s[i] = (int32_t)o;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) uniq += __shfl_xor_sync(0xffffffffu, uniq, o);
+    if (!ci_s && lane == 0) cnt[i] = uniq;
+}
+
+__global__ void k_i64_to_i32(int64_t n, const int64_t *__restrict__ in, int32_t *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= n) out[i] = (int32_t)in[i];
+}
+
+struct IluNum {                // the numeric ILU of a level sweep (null a: no factorisation)
+    const int32_t *dpos, *ldiag;  // diagonal position per row; position of u_kk per L entry
+    const int64_t *tp;            // update triples of row i: tr[tp[i] .. tp[i+1])
+    const int3 *tr;
+    double *a;                    // values on the pattern, overwritten with L\U
+    int *err;
+};
+
+// Row i of the factorisation, one thread, once the rows it depends on are
+// final (earlier levels).  Every load of the row is issued before the
+// arithmetic: the L entries, their pivots u_kk and the update triples with
+// their u_kj.  When no update lands on an L position (the 5- and 7-point
+// stencils with ILU(0)) the divisions a_ik / u_kk are independent and run
+// together; then a_ij -= l_ik u_kj in (k, j) order, the IKJ fma chain of each
+// entry.  Longer rows, and rows whose updates reach their own L part, run the
+// IKJ loop entry by entry.  One thread per row keeps the FP64 work of a level
+// off GB300's narrow FP64 pipe, which a warp per row (one lane busy in each
+// FP64 instruction) had kept half occupied.
+constexpr int kRowL = 4, kRowT = 4;
+
+__device__ __forceinline__ void ilu_row_thread(int i, const int32_t *__restrict__ rp, const IluNum &F) {
+    const int b = rp[i], dq = F.dpos[i];
+    const int nl = dq - b;
+    const int64_t t0 = F.tp[i];
+    const int nt = (int)(F.tp[i + 1] - t0);
+    double *a = F.a;
+    bool fast = nl <= kRowL && nt <= kRowT;
+    int3 tr[kRowT];
+    double uf[kRowT], lv[kRowL], ukk[kRowL];
+    if (fast) {
+#pragma unroll
+        for (int t = 0; t < kRowT; t++)
+            if (t < nt) {
+                tr[t] = F.tr[t0 + t];
+                fast = fast && tr[t].z >= dq;
+            }
+    }
+    if (fast) {
+#pragma unroll
+        for (int q = 0; q < kRowL; q++)
+            if (q < nl) {
+                lv[q] = a[b + q];
+                ukk[q] = a[F.ldiag[b + q]];
+            }
+#pragma unroll
+        for (int t = 0; t < kRowT; t++)
+            if (t < nt) uf[t] = a[tr[t].y];
+#pragma unroll
+        for (int q = 0; q < kRowL; q++)
+            if (q < nl) {
+                lv[q] = lv[q] / ukk[q];  // l_ik = a_ik / u_kk
+                a[b + q] = lv[q];
+            }
+#pragma unroll
+        for (int t = 0; t < kRowT; t++)
+            if (t < nt) {
+                const int qq = tr[t].x - b;
+                double l = lv[0];
+#pragma unroll
+                for (int q = 1; q < kRowL; q++) l = q == qq ? lv[q] : l;
+                a[tr[t].z] = fma(-l, uf[t], a[tr[t].z]);  // a_ij -= l_ik u_kj
+            }
+    } else {
+        int64_t t = t0;
+        const int64_t te = t0 + nt;
+        for (int q = b; q < dq; q++) {
+            const double aik = a[q] / a[F.ldiag[q]];
+            a[q] = aik;
+            for (; t < te; t++) {
+                const int3 y = F.tr[t];
+                if (y.x != q) break;
+                a[y.z] = fma(-aik, a[y.y], a[y.z]);
+            }
+        }
+    }
+    const double piv = a[dq];
+    if (!(piv != 0.0) || !isfinite(piv)) atomicOr(F.err, kIluErrPivot);
+}
+
+// Level l of the sweep, a thread per row: level l is order[lptr[l] ..) with
+// lcnt[l] rows (final when this launch starts).  Each row is factored (with
+// F.a), then releases its dependents; a dependent whose in-degree reaches
+// zero joins level l + 1 through the counter lcnt[l + 1] (one atomic per
+// warp).  Block 0 publishes lptr[l + 1] for the next launch, so a level costs
+// one launch and no hand-off between blocks.
+template <bool ILU>
+__global__ void __launch_bounds__(kIluThreads, 4)
+k_level(int l, int32_t *order, int32_t *lptr, int32_t *lcnt, const int64_t *__restrict__ trp,
+        const int32_t *__restrict__ tcol, int32_t *indeg, const int32_t *__restrict__ rp, IluNum F) {
+    pdl_wait();
+    pdl_trigger();
+    const int begin = lptr[l], cnt = lcnt[l];
+    if (cnt == 0) return;
+    const int next = begin + cnt;
+    if (blockIdx.x == 0 && threadIdx.x == 0) lptr[l + 1] = next;
+    const int lane = threadIdx.x & 31;
+    const int64_t nt = (int64_t)gridDim.x * kIluThreads;
+    for (int64_t r = (int64_t)blockIdx.x * kIluThreads + threadIdx.x; r - lane < cnt; r += nt) {  // warp-uniform
+        const bool valid = r < cnt;
+        const int i = valid ? order[begin + r] : 0;
+        if (ILU && valid) ilu_row_thread(i, rp, F);
+        int64_t t = valid ? trp[i] : 0;
+        const int64_t te = valid ? trp[i + 1] : 0;
+        while (__any_sync(0xffffffffu, t < te)) {  // release the dependents
+            bool rel = false;
+            int d = 0;
+            if (t < te) {
+                d = tcol[t];
+                rel = atomicSub(indeg + d, 1) == 1;
+                t++;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, rel);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                int pos = 0;
+                if (lane == leader) pos = atomicAdd(lcnt + l + 1, __popc(m));
+                pos = __shfl_sync(0xffffffffu, pos, leader);
+                if (rel) order[next + pos + __popc(m & ((1u << lane) - 1u))] = d;
+            }
+        }
+    }
+}
+
 }  // namespace
 
 void free_levels(LevelSchedule *L) {
@@ -266,11 +369,12 @@ void free_levels(LevelSchedule *L) {
     L->nlev = 0;
 }
 
-// Frontier sweep over the dependency graph of (rp, ci); fills `out` (level
-// sets on the device, level pointers on the host) when given, and factors
-// ILU(0) in place in `a` when `a` is given (err_word collects pivot errors).
-sait_status frontier_schedule(sait_ctx ctx, const int32_t *rp, const int32_t *ci, int64_t n, bool lower,
-                              const int32_t *dpos, double *a, int *err_word, LevelSchedule *out) {
+// Level sweep over the dependency graph of (rp, ci): one launch of k_level per
+// level (programmatic dependent launches, 32 per host check of the frontier).
+// Fills `out` (level sets on the device, level pointers on the host) when
+// given, and factors on the pattern when F.a is given.
+sait_status level_sweep(sait_ctx ctx, const int32_t *rp, const int32_t *ci, int64_t n, bool lower,
+                        const IluNum &F, LevelSchedule *out) {
     cudaStream_t s = ctx->stream;
     int *h = (int *)ctx->h_pinned;
     if (out) {
@@ -278,126 +382,89 @@ sait_status frontier_schedule(sait_ctx ctx, const int32_t *rp, const int32_t *ci
         out->ptr.assign(1, 0);
     }
     if (n == 0) return SAIT_OK;
+    constexpr int kBatch = 32;
     const unsigned grid = (unsigned)cdiv(n, 256);
-    DTemp<int32_t> indeg, tcnt, order, lptr;
+    const int64_t nl_cap = n + 2 * kBatch + 2;  // levels never exceed n
+    DTemp<int32_t> indeg, tcnt, order, lptr, lcnt, tcol;
     DTemp<int64_t> trp;
-    DTemp<int32_t> tcol;
-    DTemp<int> q;
     SAIT_CK(indeg.alloc(n, s));
     SAIT_CK(tcnt.alloc(n, s));
     SAIT_CK(order.alloc(n, s));
-    SAIT_CK(lptr.alloc(n + 2, s));
+    SAIT_CK(lptr.alloc(nl_cap, s));
+    SAIT_CK(lcnt.alloc(nl_cap, s));
     SAIT_CK(trp.alloc(n + 1, s));
-    SAIT_CK(q.alloc(4, s));
     SAIT_CK(cudaMemsetAsync(tcnt.p, 0, n * sizeof(int32_t), s));
-    SAIT_CK(cudaMemsetAsync(q.p, 0, 4 * sizeof(int), s));
+    SAIT_CK(cudaMemsetAsync(lcnt.p, 0, nl_cap * sizeof(int32_t), s));
+    SAIT_CK(cudaMemsetAsync(lptr.p, 0, sizeof(int32_t), s));
     launch_k(k_dep_count, grid, 256, 0, s, n, rp, ci, (int)lower, indeg.p, tcnt.p);
     SAIT_CK(scan_i32(tcnt.p, trp.p, n, s));
     int64_t *h64 = (int64_t *)((char *)ctx->h_pinned + 256);
     SAIT_CK(cudaMemcpyAsync(h64, trp.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     SAIT_CK(cudaStreamSynchronize(s));
-    SAIT_CK(tcol.alloc(h64[0], s));
+    SAIT_CK(tcol.alloc(std::max<int64_t>(h64[0], 1), s));
     SAIT_CK(cudaMemsetAsync(tcnt.p, 0, n * sizeof(int32_t), s));  // reused as fill cursors
     launch_k(k_dep_fill, grid, 256, 0, s, n, rp, ci, (int)lower, (const int64_t *)trp.p, tcnt.p, tcol.p);
-    launch_k(k_front0, grid, 256, 0, s, n, (const int32_t *)indeg.p, order.p, q.p);
-    launch_k(k_front_init, 1, 1, 0, s, q.p, lptr.p);
+    launch_k(k_front0, grid, 256, 0, s, n, (const int32_t *)indeg.p, order.p, lcnt.p);
     SAIT_CK(cudaGetLastError());
-    const bool ilu = a != nullptr;
-    // ILU: the update triples of every row (symbolic, all rows in parallel)
-    DTemp<int32_t> ldiag, tcnt2;
-    DTemp<int64_t> tp;
-    DTemp<int3> tr;
-    if (ilu) {
-        SAIT_CK(cudaMemcpyAsync(h, rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    const bool ilu = F.a != nullptr;
+    int per_sm = 0;
+    cudaError_t oe = ilu ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level<true>, kIluThreads, 0)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level<false>, kIluThreads, 0);
+    if (oe != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const unsigned lgrid = (unsigned)std::min<int64_t>((int64_t)per_sm * ctx->num_sms, cdiv(n, kIluThreads));
+    // kBatch levels per batch; the frontier check of batch b is read while batch
+    // b + 1 runs (a batch past the last level is 32 no-op launches)
+    auto launch_batch = [&](int l0) -> cudaError_t {
+        for (int t = 0; t < kBatch; t++) {
+            cudaError_t e = ilu ? launch_pdl(k_level<true>, lgrid, kIluThreads, 0, s, l0 + t, order.p, lptr.p,
+                                             lcnt.p, (const int64_t *)trp.p, (const int32_t *)tcol.p, indeg.p, rp, F)
+                                : launch_pdl(k_level<false>, lgrid, kIluThreads, 0, s, l0 + t, order.p, lptr.p,
+                                             lcnt.p, (const int64_t *)trp.p, (const int32_t *)tcol.p, indeg.p, rp, F);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
+    int l0 = 0;
+    cudaError_t le = launch_batch(0);
+    for (;; l0 += kBatch) {
+        if (le != cudaSuccess) return ctx_cuda(ctx, le, "level sweep", __FILE__, __LINE__);
+        if (l0 > n) return ctx_fail(ctx, SAIT_ERR_CUDA, "level schedule did not terminate");
+        SAIT_CK(cudaMemcpyAsync(h, lcnt.p + l0 + kBatch, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        le = launch_batch(l0 + kBatch);  // runs while the host waits for the check
         SAIT_CK(cudaStreamSynchronize(s));
-        SAIT_CK(ldiag.alloc(std::max<int64_t>(h[0], 1), s));
-        SAIT_CK(tcnt2.alloc(n, s));
-        SAIT_CK(tp.alloc(n + 1, s));
-        launch_k(k_ilu_triples, grid, 256, 0, s, n, rp, ci, dpos, ldiag.p, (const int64_t *)nullptr, tcnt2.p,
-                 (int3 *)nullptr);
-        SAIT_CK(scan_i32(tcnt2.p, tp.p, n, s));
-        SAIT_CK(cudaMemcpyAsync(h64 + 1, tp.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        SAIT_CK(cudaStreamSynchronize(s));
-        SAIT_CK(tr.alloc(std::max<int64_t>(h64[1], 1), s));
-        launch_k(k_ilu_triples, grid, 256, 0, s, n, rp, ci, dpos, ldiag.p, (const int64_t *)tp.p, tcnt2.p, tr.p);
-        SAIT_CK(cudaGetLastError());
+        if (h[0] == 0) break;  // empty frontier: every row is scheduled
     }
-    // few blocks: the level work is short and every block of a level meets at one counter
-    const unsigned sgrid = (unsigned)std::min<int64_t>(cdiv(n, 256), (int64_t)ctx->num_sms * 2);
-    DTemp<unsigned> done_blocks;
-    SAIT_CK(done_blocks.alloc(1, s));
-    SAIT_CK(cudaMemsetAsync(done_blocks.p, 0, sizeof(unsigned), s));
-    // kBatch levels (one launch each) are captured once in a CUDA graph and
-    // replayed until the frontier is empty; a level past the last one is a
-    // no-op (empty frontier), so replaying whole batches is safe
-    constexpr int kBatch = 32;
-    cudaGraphExec_t gexec = nullptr;
-    {
-        cudaStream_t cs;
-        SAIT_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        cudaGraph_t g = nullptr;
-        const int64_t launches0 = g_sait_launches;
-        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            for (int t = 0; t < kBatch; t++) {
-                if (ilu)
-                    launch_k(k_front_step<true>, sgrid, 256, 0, cs, order.p, q.p, lptr.p, done_blocks.p,
-                             (const int64_t *)trp.p, (const int32_t *)tcol.p, indeg.p, rp, dpos,
-                             (const int32_t *)ldiag.p, (const int64_t *)tp.p, (const int3 *)tr.p, a, err_word);
-                else
-                    launch_k(k_front_step<false>, sgrid, 256, 0, cs, order.p, q.p, lptr.p, done_blocks.p,
-                             (const int64_t *)trp.p, (const int32_t *)tcol.p, indeg.p, rp, dpos,
-                             (const int32_t *)nullptr, (const int64_t *)nullptr, (const int3 *)nullptr, a, err_word);
-            }
-            cudaError_t e1 = cudaGetLastError();
-            e = cudaStreamEndCapture(cs, &g);
-            if (e == cudaSuccess && e1 != cudaSuccess) e = e1;
-        }
-        g_sait_launches = launches0;  // captured, not executed
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, g, 0);
-        if (g) cudaGraphDestroy(g);
-        cudaStreamDestroy(cs);
-        if (e != cudaSuccess) {
-            if (gexec) cudaGraphExecDestroy(gexec);
-            return ctx_cuda(ctx, e, "frontier graph", __FILE__, __LINE__);
-        }
-    }
-    sait_status st = SAIT_OK;
-    for (int64_t batch = 0;; batch++) {
-        if (batch * kBatch > n + 64) {
-            st = ctx_fail(ctx, SAIT_ERR_CUDA, "level schedule did not terminate");
-            break;
-        }
-        cudaError_t e = cudaGraphLaunch(gexec, s);
-        g_sait_launches += kBatch;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h, q.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) {
-            st = ctx_cuda(ctx, e, "frontier sweep", __FILE__, __LINE__);
-            break;
-        }
-        if (h[0] == h[1]) break;  // empty frontier: every row is scheduled
-    }
-    cudaGraphExecDestroy(gexec);
-    if (st != SAIT_OK) return st;
-    if (h[1] != n) return ctx_fail(ctx, SAIT_ERR_CUDA, "level schedule lost rows");
+    l0 += kBatch;  // the batch launched last
+    // level sizes: levels past the last one are empty
+    std::vector<int32_t> cnts((size_t)l0 + kBatch + 1);
+    SAIT_CK(cudaMemcpyAsync(cnts.data(), lcnt.p, cnts.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SAIT_CK(cudaStreamSynchronize(s));
+    int nlev = 0;
+    int64_t rows = 0;
+    while (nlev < (int)cnts.size() && cnts[nlev] > 0) rows += cnts[nlev++];
+    if (rows != n) return ctx_fail(ctx, SAIT_ERR_CUDA, "level schedule lost rows");
     if (out) {
-        const int nlev = h[3];
         out->nlev = nlev;
         out->ptr.resize(nlev + 1);
-        SAIT_CK(cudaMemcpyAsync(out->ptr.data(), lptr.p, (nlev + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        out->ptr[0] = 0;
+        out->max_width = 0;
+        for (int l = 0; l < nlev; l++) {
+            out->ptr[l + 1] = out->ptr[l] + cnts[l];
+            out->max_width = std::max(out->max_width, cnts[l]);
+        }
         SAIT_CK(cudaMalloc((void **)&out->rows, n * sizeof(int32_t)));
         SAIT_CK(cudaMemcpyAsync(out->rows, order.p, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
         SAIT_CK(cudaStreamSynchronize(s));
-        out->max_width = 0;
-        for (int l = 0; l < nlev; l++) out->max_width = std::max(out->max_width, out->ptr[l + 1] - out->ptr[l]);
     }
     return SAIT_OK;
 }
 
 sait_status build_levels(sait_ctx ctx, const int32_t *rp, const int32_t *ci, int64_t n, bool lower,
                          LevelSchedule *out) {
-    return frontier_schedule(ctx, rp, ci, n, lower, nullptr, nullptr, nullptr, out);
+    return level_sweep(ctx, rp, ci, n, lower, IluNum{}, out);
 }
 
 cudaError_t launch_trisolve(const sait_mat_s *T, const LevelSchedule &lev, bool lower, const double *b,
@@ -416,73 +483,127 @@ cudaError_t launch_trisolve(const sait_mat_s *T, const LevelSchedule &lev, bool 
     return cudaGetLastError();
 }
 
-extern "C" sait_status sait_ilu0(sait_ctx ctx, const sait_csr *A, sait_mat *L, sait_mat *U) {
+extern "C" sait_status sait_iluk(sait_ctx ctx, const sait_csr *A, int32_t level, sait_mat *L, sait_mat *U) {
     if (!ctx) return SAIT_ERR_INVALID_ARG;
-    if (!A || !L || !U) return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_ilu0: null argument");
+    if (!A || !L || !U || level < 0) return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_iluk: bad argument");
+    if (level > 1) return ctx_fail(ctx, SAIT_ERR_UNSUPPORTED, "sait_iluk: level of fill above 1");
     *L = *U = nullptr;
     ScopedTimer tm(ctx, SAIT_TIMER_ILU);
-    sait_mat W = nullptr;  // validated working copy of A, overwritten with L\U
+    sait_mat W = nullptr;  // validated working copy of A (ILU(0): overwritten with L\U)
     SAIT_TRY(mat_copy_csr(ctx, A, &W));
-    const int64_t n = W->n;
+    const int64_t n = W->n, n1 = std::max<int64_t>(n, 1);
     cudaStream_t s = ctx->stream;
     int *h = (int *)ctx->h_pinned;
+    int64_t *h64 = (int64_t *)((char *)ctx->h_pinned + 256);
     sait_status st = SAIT_OK;
-    DTemp<int32_t> dpos, lc, uc;
-    DTemp<int64_t> lrp, urp;
+    DTemp<int32_t> dpos, lc, uc, cnt, ldiag, rp_s, ci_s, dpos_s;
+    DTemp<int64_t> lrp, urp, rp64, tp;
+    DTemp<double> va_s;
+    DTemp<int3> tr;
+    DTemp<int> err;
     sait_mat Lm = nullptr, Um = nullptr;
-    const unsigned grid = (unsigned)cdiv(std::max<int64_t>(n, 1), 256);
+    const int32_t *prp = W->rp, *pci = W->ci, *pdpos = nullptr;
+    double *pva = W->va;
+    int64_t nnz_s = W->nnz;
+    const unsigned grid = (unsigned)cdiv(n1, 256);
+    const unsigned wgrid = (unsigned)cdiv(n1 * 32, kIluThreads);  // a warp per row (ILU(1) pattern)
     auto cuda_fail = [&](cudaError_t e, const char *what) {
         st = ctx_cuda(ctx, e, what, __FILE__, __LINE__);
     };
-    cudaError_t e = dpos.alloc(n, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_word, 0, sizeof(int), s);
-    if (e != cudaSuccess) { cuda_fail(e, "sait_ilu0 setup"); goto done; }
-    if (n > 0) launch_k(k_diag_pos, grid, 256, 0, s, n, W->rp, W->ci, dpos.p, ctx->d_word);
-    e = cudaMemcpyAsync(h, ctx->d_word, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = dpos.alloc(n1, s);
+    if (e == cudaSuccess) e = err.alloc(1, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err.p, 0, sizeof(int), s);
+    if (e != cudaSuccess) { cuda_fail(e, "sait_iluk setup"); goto done_; }
+    if (n > 0) launch_k(k_diag_pos, grid, 256, 0, s, n, W->rp, W->ci, dpos.p, err.p);
+    e = cudaMemcpyAsync(h, err.p, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) { cuda_fail(e, "sait_ilu0 diagonal"); goto done; }
-    if (h[0]) { st = ctx_fail(ctx, SAIT_ERR_ZERO_PIVOT, "sait_ilu0: missing diagonal entry"); goto done; }
-    e = cudaMemsetAsync(ctx->d_word, 0, sizeof(int), s);
-    if (e != cudaSuccess) { cuda_fail(e, "sait_ilu0 setup"); goto done; }
-    st = frontier_schedule(ctx, W->rp, W->ci, n, true, dpos.p, W->va, ctx->d_word, nullptr);
-    if (st != SAIT_OK) goto done;
-    e = cudaMemcpyAsync(h, ctx->d_word, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) { cuda_fail(e, "sait_ilu0 factorisation"); goto done; }
-    if (h[0]) { st = ctx_fail(ctx, SAIT_ERR_ZERO_PIVOT, "sait_ilu0: zero or non-finite pivot"); goto done; }
+    if (e != cudaSuccess) { cuda_fail(e, "sait_iluk diagonal"); goto done_; }
+    if (h[0]) { st = ctx_fail(ctx, SAIT_ERR_ZERO_PIVOT, "sait_iluk: missing diagonal entry"); goto done_; }
+    pdpos = dpos.p;
+    if (level == 1 && n > 0) {  // the ILU(1) pattern S, built row by row
+        e = cnt.alloc(n1, s);
+        if (e == cudaSuccess) e = rp64.alloc(n + 1, s);
+        if (e != cudaSuccess) { cuda_fail(e, "sait_iluk pattern"); goto done_; }
+        launch_k(k_ilu1_pattern, wgrid, kIluThreads, 0, s, n, (const int32_t *)W->rp, (const int32_t *)W->ci,
+                 (const double *)W->va, (const int32_t *)dpos.p, cnt.p, (const int64_t *)nullptr, (int32_t *)nullptr,
+                 (double *)nullptr, (int32_t *)nullptr, err.p);
+        e = scan_i32(cnt.p, rp64.p, n, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h64, rp64.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, err.p, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { cuda_fail(e, "sait_iluk pattern"); goto done_; }
+        if (h[0]) { st = ctx_fail(ctx, SAIT_ERR_UNSUPPORTED, "sait_iluk: a row's level-1 candidates exceed 512"); goto done_; }
+        nnz_s = h64[0];
+        if (nnz_s > INT_MAX) { st = ctx_fail(ctx, SAIT_ERR_UNSUPPORTED, "sait_iluk: more than 2^31 entries"); goto done_; }
+        e = rp_s.alloc(n + 1, s);
+        if (e == cudaSuccess) e = ci_s.alloc(std::max<int64_t>(nnz_s, 1), s);
+        if (e == cudaSuccess) e = va_s.alloc(std::max<int64_t>(nnz_s, 1), s);
+        if (e == cudaSuccess) e = dpos_s.alloc(n1, s);
+        if (e != cudaSuccess) { cuda_fail(e, "sait_iluk pattern"); goto done_; }
+        launch_k(k_i64_to_i32, (unsigned)cdiv(n + 1, 256), 256, 0, s, n, (const int64_t *)rp64.p, rp_s.p);
+        launch_k(k_ilu1_pattern, wgrid, kIluThreads, 0, s, n, (const int32_t *)W->rp, (const int32_t *)W->ci,
+                 (const double *)W->va, (const int32_t *)dpos.p, cnt.p, (const int64_t *)rp64.p, ci_s.p, va_s.p,
+                 dpos_s.p, err.p);
+        prp = rp_s.p;
+        pci = ci_s.p;
+        pva = va_s.p;
+        pdpos = dpos_s.p;
+    }
+    if (n > 0) {  // update triples, then the level sweep with the numeric rows
+        e = ldiag.alloc(std::max<int64_t>(nnz_s, 1), s);
+        if (e == cudaSuccess) e = cnt.alloc(n1, s);
+        if (e == cudaSuccess) e = tp.alloc(n + 1, s);
+        if (e != cudaSuccess) { cuda_fail(e, "sait_iluk triples"); goto done_; }
+        launch_k(k_ilu_triples, grid, 256, 0, s, n, prp, pci, pdpos, ldiag.p, (const int64_t *)nullptr, cnt.p,
+                 (int3 *)nullptr);
+        e = scan_i32(cnt.p, tp.p, n, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h64 + 1, tp.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = tr.alloc(std::max<int64_t>(h64[1], 1), s);
+        if (e != cudaSuccess) { cuda_fail(e, "sait_iluk triples"); goto done_; }
+        launch_k(k_ilu_triples, grid, 256, 0, s, n, prp, pci, pdpos, ldiag.p, (const int64_t *)tp.p, cnt.p, tr.p);
+        st = level_sweep(ctx, prp, pci, n, true, IluNum{pdpos, ldiag.p, tp.p, tr.p, pva, err.p}, nullptr);
+        if (st != SAIT_OK) goto done_;
+        e = cudaMemcpyAsync(h, err.p, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { cuda_fail(e, "sait_iluk factorisation"); goto done_; }
+        if (h[0] & kIluErrPivot) { st = ctx_fail(ctx, SAIT_ERR_ZERO_PIVOT, "sait_iluk: zero or non-finite pivot"); goto done_; }
+        if (h[0]) { st = ctx_fail(ctx, SAIT_ERR_CUDA, "sait_iluk: factorisation failed"); goto done_; }
+    }
     // split into L (unit diagonal stored) and U
-    e = lc.alloc(n, s);
-    if (e == cudaSuccess) e = uc.alloc(n, s);
+    e = lc.alloc(n1, s);
+    if (e == cudaSuccess) e = uc.alloc(n1, s);
     if (e == cudaSuccess) e = lrp.alloc(n + 1, s);
     if (e == cudaSuccess) e = urp.alloc(n + 1, s);
-    if (e != cudaSuccess) { cuda_fail(e, "sait_ilu0 split"); goto done; }
-    if (n > 0) launch_k(k_lu_counts, grid, 256, 0, s, n, W->rp, W->ci, lc.p, uc.p);
+    if (e != cudaSuccess) { cuda_fail(e, "sait_iluk split"); goto done_; }
+    if (n > 0) launch_k(k_lu_counts, grid, 256, 0, s, n, prp, pci, lc.p, uc.p);
     e = scan_i32(lc.p, lrp.p, n, s);
     if (e == cudaSuccess) e = scan_i32(uc.p, urp.p, n, s);
-    {
-        int64_t *h64 = (int64_t *)((char *)ctx->h_pinned + 256);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h64, lrp.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h64 + 1, urp.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) { cuda_fail(e, "sait_ilu0 split"); goto done; }
-        st = mat_alloc(ctx, n, h64[0], &Lm);
-        if (st == SAIT_OK) st = mat_alloc(ctx, n, h64[1], &Um);
-        if (st != SAIT_OK) goto done;
-    }
-    launch_k(k_lu_fill, (unsigned)cdiv(n + 1, 256), 256, 0, s, n, W->rp, W->ci, W->va, lrp.p, urp.p, Lm->rp,
-                                                         Lm->ci, Lm->va, Um->rp, Um->ci, Um->va);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h64, lrp.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h64 + 1, urp.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { cuda_fail(e, "sait_iluk split"); goto done_; }
+    st = mat_alloc(ctx, n, h64[0], &Lm);
+    if (st == SAIT_OK) st = mat_alloc(ctx, n, h64[1], &Um);
+    if (st != SAIT_OK) goto done_;
+    launch_k(k_lu_fill, (unsigned)cdiv(n + 1, 256), 256, 0, s, n, prp, pci, (const double *)pva, lrp.p, urp.p,
+             Lm->rp, Lm->ci, Lm->va, Um->rp, Um->ci, Um->va);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) { cuda_fail(e, "sait_ilu0 split"); goto done; }
+    if (e != cudaSuccess) { cuda_fail(e, "sait_iluk split"); goto done_; }
     Lm->lanes = choose_lanes(n, Lm->nnz);
     Um->lanes = choose_lanes(n, Um->nnz);
     *L = Lm;
     *U = Um;
     Lm = Um = nullptr;
-done:
+done_:
     if (Lm) sait_mat_destroy(Lm);
     if (Um) sait_mat_destroy(Um);
     cudaStreamSynchronize(s);
     sait_mat_destroy(W);
     return st;
+}
+
+extern "C" sait_status sait_ilu0(sait_ctx ctx, const sait_csr *A, sait_mat *L, sait_mat *U) {
+    return sait_iluk(ctx, A, 0, L, U);
 }

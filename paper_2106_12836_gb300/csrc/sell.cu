@@ -73,7 +73,7 @@ k_spmv_sell(int64_t n, int64_t nslices, const int64_t *__restrict__ soff, const 
         v += 32 * kU;
     }
     const int64_t row = s * 32 + lane;
-    if (row < n) y[row] = (TY)acc_value(acc);
+    if (row < n) put_out(y + row, acc);
 }
 
 // slice lengths (in column slots) and the padded-entry count per slice

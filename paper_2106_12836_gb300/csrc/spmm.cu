@@ -51,7 +51,7 @@ k_spmm_csr(int64_t n, int k, int64_t ldx, int64_t ldy, const int32_t *__restrict
 #pragma unroll
     for (int t = 0; t < CPL; t++) {
         const int col = gl + t * G;
-        if (col < k) yr[col] = (TY)acc_value(acc[t]);
+        if (col < k) put_out(yr + col, acc[t]);
     }
 }
 

@@ -41,7 +41,7 @@ k_spmv_csr(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict_
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     }
-    if (row < n && lane == 0) y[row] = (TY)acc_value(s);
+    if (row < n && lane == 0) put_out(y + row, s);
 }
 
 template <typename TV, typename TA, typename TX, typename TY>

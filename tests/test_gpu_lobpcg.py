@@ -78,6 +78,35 @@ def test_lobpcg_variable_coefficients(sg, oracle_lib):
     assert abs(info.iters - it) <= max(3, 0.25 * it), (info.iters, it)
 
 
+@pytest.mark.parametrize("store", ["f64", "f32", "bf16"])
+def test_lobpcg_matches_oracle_fixture(sg, store):
+    """The variable-coefficient eigenproblem of the benchmark (log-normal kappa,
+    ILUT(1e-4, 10) factors, SAIT with 3 terms and a row-relative drop of 1e-3,
+    16 smallest eigenpairs from the same X0) at 32^3, against the FP64 oracle's
+    eigenvalues stored by tests/golden/make_eigen_fixture.py: with the factors
+    stored in FP64, FP32 or BF16 the eigenvalues agree with the oracle's
+    tight (1e-11) run to 1e-10 relative."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "eigen_varcoef32.json")) as f:
+        fx = json.load(f)
+    A = synth.varcoef3d(fx["grid"], 1.0, synth.SEED_BASE + 3)
+    X0 = synth.uniform(synth.SEED_BASE + 10, (A.n, fx["k"]))
+    with sg.Context() as ctx:
+        L, U = sg.sait_ilut(ctx, A.n, dev(A.rp), dev(A.ci), dev(A.va), 1e-4, 10)
+        P = sg.sait_prec_create_sait(ctx, sg.sait_build(ctx, L, True, 3, "rowrel", 1e-3, store=store),
+                                     sg.sait_build(ctx, U, False, 3, "rowrel", 1e-3, store=store))
+        Am = sg.sait_mat_create_csr(ctx, A.n, dev(A.rp), dev(A.ci), dev(A.va))
+        lam, X, info, st = sg.sait_lobpcg(ctx, Am, P, dev(X0), tol=1e-8, maxit=1000)
+        torch.cuda.synchronize()
+    lam = lam.cpu().numpy()
+    ref = np.array(fx["tol_1e-11"]["lambda"])
+    assert st == 0 and info.rel_resid <= 1e-8
+    assert np.abs(lam - ref).max() <= 1e-10 * ref.max(), np.abs(lam - ref).max() / ref.max()
+    # the oracle's own 1e-8 run agrees with its tight run at the same level
+    assert np.abs(np.array(fx["tol_1e-8"]["lambda"]) - ref).max() <= 1e-10 * ref.max()
+
+
 def test_lobpcg_rejects_bad_sizes(sg):
     A = synth.laplace3d(3)
     with sg.Context() as ctx:

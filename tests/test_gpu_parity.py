@@ -90,6 +90,31 @@ def test_ilu0_bit_exact(sg, ctx, oracle_lib, make):
         assert np.array_equal(G.va, O.va), np.abs(G.va - O.va).max()
 
 
+# ---- ILU(1) (level of fill) ---------------------------------------------------------
+@pytest.mark.parametrize("make", [lambda: synth.poisson2d(37), lambda: synth.convdiff3d(17),
+                                  lambda: synth.varcoef3d(13, 1.0, 5), lambda: synth.aniso2d(50, 1e-3),
+                                  lambda: synth.from_dense(np.where(np.random.default_rng(3).uniform(size=(90, 90)) < 0.08,
+                                                                    np.random.default_rng(4).uniform(-1, 1, (90, 90)),
+                                                                    0.0) + 9 * np.eye(90))])
+@pytest.mark.parametrize("level", [0, 1])
+def test_iluk_bit_exact(sg, ctx, oracle_lib, make, level):
+    """ILU(level) through sait_iluk: structure and values bit-identical to the
+    oracle's row-by-row level-of-fill elimination (Saad, Algorithm 10.5)."""
+    A = make()
+    L, U = sg.sait_iluk(ctx, A.n, dev(A.rp), dev(A.ci), dev(A.va), level)
+    Lo, Uo = oracle_lib.iluk(A, level)
+    for G, O in ((host_csr(L), Lo), (host_csr(U), Uo)):
+        assert np.array_equal(G.rp, O.rp) and np.array_equal(G.ci, O.ci)
+        assert np.array_equal(G.va, O.va), np.abs(G.va - O.va).max()
+
+
+def test_iluk_rejects_level_two(sg, ctx):
+    A = synth.poisson2d(5)
+    with pytest.raises(sg.SaitError) as e:
+        sg.sait_iluk(ctx, A.n, dev(A.rp), dev(A.ci), dev(A.va), 2)
+    assert e.value.status == 10    # SAIT_ERR_UNSUPPORTED
+
+
 def test_ilu0_zero_pivot(sg, ctx):
     A = synth.from_dense(np.array([[1.0, 2.0], [2.0, 4.0]]))   # U_11 = 4 - 2*2 = 0
     with pytest.raises(sg.SaitError) as e:
@@ -217,6 +242,34 @@ def test_apply_x64_is_the_rounded_matrix_in_fp64(sg, ctx, oracle_lib, store, rou
     bound = oracle_lib.apply(synth.CSR(A.n, MLr.rp, MLr.ci, np.abs(MLr.va)),
                              synth.CSR(A.n, MUr.rp, MUr.ci, np.abs(MUr.va)), np.abs(r))
     assert np.all(np.abs(z - zo) <= 1e-12 * bound)
+
+
+def test_fp32_storage_narrows_like_ieee(sg, ctx):
+    """An FP32-stored identity applied to FP64 x gives float(x) widened back: the
+    products narrow FP64 entries to FP32 with integer round-to-nearest-even and
+    widen FP32 sums exactly, so the result must equal numpy's IEEE conversion bit
+    for bit, ties and the top of the range included; below the smallest normal
+    FP32 magnitude (2^-126) the narrowing gives zero."""
+    rng = np.random.default_rng(11)
+    f = rng.uniform(1, 2, 4000).astype(np.float32).astype(np.float64) * np.exp2(rng.integers(-120, 120, 4000))
+    ulp = np.spacing(f.astype(np.float32)).astype(np.float64)
+    x = np.concatenate([
+        rng.standard_normal(20000) * np.exp2(rng.integers(-100, 100, 20000)),  # generic values
+        f + ulp / 2, f - ulp / 4, f + 3 * ulp / 4,                                # exact ties and near ties
+        -(f + ulp / 2),
+        [np.float64(np.finfo(np.float32).max), 3.4028235e38 * (1 + 2 ** -30), 2.0 ** -126, -(2.0 ** -126),
+         0.0, -0.0, 1.0, 1 + 2 ** -24, 1 + 3 * 2 ** -24, 2.0 ** -130, -(2.0 ** -140)],
+    ])
+    n = len(x)
+    I = synth.CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.ones(n))
+    M = sg.sait_mat_create_csr(ctx, n, dev(I.rp), dev(I.ci), dev(I.va))
+    sg.sait_mat_set_store(ctx, M, "f32")
+    y = sg.sait_spmv(ctx, M, dev(x)).cpu().numpy()
+    with np.errstate(over="ignore"):
+        want = x.astype(np.float32).astype(np.float64)
+    normal = np.abs(x) >= 2.0 ** -126
+    assert np.array_equal(y[normal].view(np.int64), want[normal].view(np.int64))
+    assert np.all(y[~normal] == 0.0)   # (the sum starts from +0, so the sign of a zero is not kept)
 
 
 def test_spmv_parity_ragged(sg, ctx, oracle_lib):
