@@ -215,21 +215,31 @@ def batched_workloads(sg, ctx, torch, device, stream):
     out["tile_autotune"] = sg.sait_batch_autotune(ctx, A.n, d["ptr"]).as_dict()  # setup, before the timed solves
 
     def solve_batch(store):
+        s0, s1, s2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        s0.record(stream)
         L, U = sg.sait_ilu0(ctx, A.n, d["rp"], d["ci"], d["va"])
-        P = sg.sait_prec_create_sait(ctx, sg.sait_build(ctx, L, True, 3, DROP, TAU, store=store),
-                                     sg.sait_build(ctx, U, False, 3, DROP, TAU, store=store))
+        ML = sg.sait_build(ctx, L, True, 3, DROP, TAU, store=store)
+        MU = sg.sait_build(ctx, U, False, 3, DROP, TAU, store=store)
+        s1.record(stream)
+        P = sg.sait_prec_create_sait(ctx, ML, MU)
         Am = sg.sait_mat_create_csr(ctx, A.n, d["rp"], d["ci"], d["va"])
         x, info, st, rr, its = sg.sait_bicgstab_batched(ctx, Am, P, d["ptr"], d["b"], tol=TOL, maxit=5000,
                                                         check=False)
-        return info, (L, U, P, Am, x)
+        s2.record(stream)
+        s2.synchronize()
+        row_iters = float((its.cpu().numpy().astype(np.float64) * np.diff(ptr)).sum())
+        return info, (s0.elapsed_time(s1), s1.elapsed_time(s2), ML.nnz, MU.nnz, row_iters), (L, U, P, Am, x)
 
     res = {}
     for store in ("f32", "f32x64", "f64"):
         solve_batch(store)                                   # warm-up (graph capture, pools)
-        ms, (info, keep) = time_region(torch, stream, lambda: solve_batch(store))
+        ms, (info, (b_ms, s_ms, nl, nu, row_iters), keep) = time_region(torch, stream, lambda: solve_batch(store))
         del keep
-        res[store] = {"ms": round(ms, 3), "ms_per_iteration": round(ms / max(info.graph_replays, 1), 4),
-                      **info.as_dict()}
+        it = max(info.graph_replays, 1)
+        bytes_it = batched_iter_bytes(A, nl, nu, store, 1, row_iters, it)
+        res[store] = {"ms": round(ms, 3), "build_ms": round(b_ms, 3), "solve_ms": round(s_ms, 3),
+                      "ms_per_iteration": round(s_ms / it, 4), "bytes_per_iteration": bytes_it,
+                      "gbs_per_iteration": round(bytes_it / (s_ms / it) / 1e6, 1), **info.as_dict()}
     out["independent_systems"] = {"nsys": len(systems), "n": A.n, "nnz": A.nnz,
                                   "sides": [int(sides.min()), int(sides.max())], "solver": "bicgstab",
                                   "m_terms": 3, "tol": TOL, **res}
@@ -246,20 +256,30 @@ def batched_workloads(sg, ctx, torch, device, stream):
     del B
 
     def solve_multi(store):
+        s0, s1, s2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        s0.record(stream)
         L, U = sg.sait_ilu0(ctx, A.n, d["rp"], d["ci"], d["va"])
-        P = sg.sait_prec_create_sait(ctx, sg.sait_build(ctx, L, True, 3, DROP, TAU, store=store),
-                                     sg.sait_build(ctx, U, False, 3, DROP, TAU, store=store))
+        ML = sg.sait_build(ctx, L, True, 3, DROP, TAU, store=store)
+        MU = sg.sait_build(ctx, U, False, 3, DROP, TAU, store=store)
+        s1.record(stream)
+        P = sg.sait_prec_create_sait(ctx, ML, MU)
         Am = sg.sait_mat_create_csr(ctx, A.n, d["rp"], d["ci"], d["va"])
         X, info, st, rr, its = sg.sait_bicgstab_multi(ctx, Am, P, d["B"], tol=TOL, maxit=5000, check=False)
-        return info, (L, U, P, Am, X)
+        s2.record(stream)
+        s2.synchronize()
+        row_iters = float(its.cpu().numpy().astype(np.float64).sum()) * A.n
+        return info, (s0.elapsed_time(s1), s1.elapsed_time(s2), ML.nnz, MU.nnz, row_iters), (L, U, P, Am, X)
 
     res = {}
     for store in ("f32", "f32x64", "f64"):
         solve_multi(store)
-        ms, (info, keep) = time_region(torch, stream, lambda: solve_multi(store))
+        ms, (info, (b_ms, s_ms, nl, nu, row_iters), keep) = time_region(torch, stream, lambda: solve_multi(store))
         del keep
-        res[store] = {"ms": round(ms, 3), "ms_per_iteration": round(ms / max(info.graph_replays, 1), 4),
-                      **info.as_dict()}
+        it = max(info.graph_replays, 1)
+        bytes_it = batched_iter_bytes(A, nl, nu, store, k, row_iters, it)
+        res[store] = {"ms": round(ms, 3), "build_ms": round(b_ms, 3), "solve_ms": round(s_ms, 3),
+                      "ms_per_iteration": round(s_ms / it, 4), "bytes_per_iteration": bytes_it,
+                      "gbs_per_iteration": round(bytes_it / (s_ms / it) / 1e6, 1), **info.as_dict()}
     out["many_rhs"] = {"n": A.n, "k": k, "solver": "bicgstab", "m_terms": 3, "tol": TOL, **res}
     del d
     torch.cuda.empty_cache()
@@ -331,35 +351,40 @@ def eigen_vs_oracle(sg, ctx, torch, device):
 
 
 def paper_replica_workload(sg, ctx, torch, device, stream):
-    """Section 4's experiment on the GPU: 100^3 Laplacian, ILU(0), PCG to 1e-10 with
-    SAIT_Thr(tau, 10), SAIT_Pat(p, 10), the exact substitution and k Jacobi sweeps."""
+    """Section 4's experiment on the GPU: 100^3 Laplacian, level-0 and level-1 ILU,
+    PCG to 1e-10 with SAIT_Thr(tau, 10), SAIT_Pat(p, 10), the exact substitution
+    and k Jacobi sweeps."""
     A = synth.laplace3d(100)
     d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in
          (("rp", A.rp), ("ci", A.ci), ("va", A.va))}
     b = torch.from_numpy(synth.uniform(synth.SEED_BASE, A.n, 0.0, 1.0)).to(device)
     Am = sg.sait_mat_create_csr(ctx, A.n, d["rp"], d["ci"], d["va"])
-    L, U = sg.sait_ilu0(ctx, A.n, d["rp"], d["ci"], d["va"])
     tol, m = 1e-10, 10
 
     def pcg(P):
-        sg.sait_pcg(ctx, Am, P, b, tol=tol)                  # warm-up
-        ms, (_, info, _) = time_region(torch, stream, lambda: sg.sait_pcg(ctx, Am, P, b, tol=tol))
-        return {"iters": info.iters, "pcg_ms": round(ms, 3), "rel_resid": info.rel_resid}
+        sg.sait_pcg(ctx, Am, P, b, tol=tol, maxit=2000, check=False)    # warm-up
+        ms, (_, info, st) = time_region(torch, stream,
+                                        lambda: sg.sait_pcg(ctx, Am, P, b, tol=tol, maxit=2000, check=False))
+        return {"iters": info.iters, "pcg_ms": round(ms, 3), "rel_resid": info.rel_resid, "status": st}
 
-    out = {"n": A.n, "tol": tol, "m": m, "rows": []}
-    out["exact_ilu0"] = pcg(sg.sait_prec_create_ilu(ctx, L, U))
-    for name, drop, tau, p in [("SAIT_Thr(0.05,10)", "abs", 0.05, 0), ("SAIT_Thr(0.02,10)", "abs", 0.02, 0),
-                               ("SAIT_Thr(0.01,10)", "abs", 0.01, 0), ("SAIT_Pat(1,10)", "pattern", 0.0, 1),
-                               ("SAIT_Pat(2,10)", "pattern", 0.0, 2), ("SAIT_Pat(3,10)", "pattern", 0.0, 3)]:
-        terms = m + 1 + p
-        sg.sait_build(ctx, L, True, terms, drop, tau, p)       # warm-up
-        ms_b, (ML, MU) = time_region(torch, stream, lambda: (sg.sait_build(ctx, L, True, terms, drop, tau, p),
-                                                             sg.sait_build(ctx, U, False, terms, drop, tau, p)))
-        row = {"name": name, "ratio": round(MU.nnz / U.nnz, 2), "build_ms": round(ms_b, 3)}
-        row.update(pcg(sg.sait_prec_create_sait(ctx, ML, MU)))
-        row["total_ms"] = round(row["build_ms"] + row["pcg_ms"], 3)
-        out["rows"].append(row)
-    out["jacobi"] = [{"sweeps": k, **pcg(sg.sait_prec_create_jacobi(ctx, L, U, k))} for k in (1, 2, 3, 4, 6, 10, 15)]
+    out = {"n": A.n, "tol": tol, "m": m, "maxit": 2000}
+    for level in (0, 1):
+        ms_f, (L, U) = time_region(torch, stream, lambda: sg.sait_iluk(ctx, A.n, d["rp"], d["ci"], d["va"], level))
+        lev = {"ilu_ms": round(ms_f, 3), "nnz_L": L.nnz, "exact_ilu": pcg(sg.sait_prec_create_ilu(ctx, L, U)),
+               "rows": []}
+        for name, drop, tau, p in [("SAIT_Thr(0.05,10)", "abs", 0.05, 0), ("SAIT_Thr(0.02,10)", "abs", 0.02, 0),
+                                   ("SAIT_Thr(0.01,10)", "abs", 0.01, 0), ("SAIT_Pat(1,10)", "pattern", 0.0, 1),
+                                   ("SAIT_Pat(2,10)", "pattern", 0.0, 2), ("SAIT_Pat(3,10)", "pattern", 0.0, 3)]:
+            terms = m + 1 + p
+            sg.sait_build(ctx, L, True, terms, drop, tau, p)       # warm-up
+            ms_b, (ML, MU) = time_region(torch, stream, lambda: (sg.sait_build(ctx, L, True, terms, drop, tau, p),
+                                                                 sg.sait_build(ctx, U, False, terms, drop, tau, p)))
+            row = {"name": name, "ratio": round(MU.nnz / U.nnz, 2), "build_ms": round(ms_b, 3)}
+            row.update(pcg(sg.sait_prec_create_sait(ctx, ML, MU)))
+            row["total_ms"] = round(row["build_ms"] + row["pcg_ms"], 3)
+            lev["rows"].append(row)
+        lev["jacobi"] = [{"sweeps": k, **pcg(sg.sait_prec_create_jacobi(ctx, L, U, k))} for k in (1, 2, 3, 4, 10)]
+        out[f"level{level}"] = lev
     return out
 
 
@@ -445,6 +470,24 @@ def apply_precisions(sg, ctx, torch, device, stream, P: "Problem", m, flush_l2, 
                       "peak": peak, "unit": "GB/s", "frac": round(b / t / 1e6 / peak, 4)}
         del ML, MU
     return out
+
+
+def batched_iter_bytes(A, nnz_ml, nnz_mu, store, k, row_iters=None, replays=1):
+    """Algorithmic bytes of one batched BiCGSTAB iteration over all systems (k
+    right-hand sides; k = 1 for the independent systems): two SAIT applies and
+    two products with A, each matrix read once for all k columns, and the 22
+    FP64 vector passes of the recurrences (dots, p, s, x and r updates).  The
+    products run over every row in every iteration; the vector passes skip the
+    systems (columns) that have converged, so with row_iters = the sum over
+    systems of iterations x rows (n x the sum of the columns' iterations) they
+    are counted for the rows still iterating, averaged over the replays."""
+    n = A.n
+    sv = {"f64": 8, "f32": 4, "bf16": 2, "f32x64": 4, "bf16x64": 2}[store]
+    vec = 32 if store in ("f64", "f32x64", "bf16x64") else 24        # r in, w out + in, z out, per column
+    apply_b = (nnz_ml + nnz_mu) * (sv + 4) + 2 * 4 * (n + 1) + vec * n * k
+    spmv_b = A.nnz * 12 + 4 * (n + 1) + 16 * n * k
+    vec_rows = n * k if row_iters is None else row_iters / replays
+    return int(2 * apply_b + 2 * spmv_b + 22 * 8 * vec_rows)
 
 
 def apply_bytes(n, nnz_l, nnz_u, store):
@@ -669,12 +712,12 @@ def run_ours(a):
                 "h2d_bytes_per_step": P.h2d_bytes, "d2h_bytes_per_step": P.d2h_bytes},
         "gpu_launches": stats["launches"],
         "roofline": roof(dom),
-        "rooflines": {g: roof(g, full=False) for g in rl},
+        # per group: achieved GB/s, fraction of peak, average ms per launch
+        "rooflines": {g: {"achieved": round(rl[g]["achieved"], 1), "frac": round(rl[g]["frac"], 4),
+                          "avg_ms": round(rl[g]["ms"], 4)} for g in rl},
+        "solve": {"iters": iters, "cycles": infos[-1]["cycles"], "rel_resid_host_check": float(f"{relres:.4e}"),
+                  "step_ms_min_max": [round(min(times), 3), round(max(times), 3)], **extra},
         "breakdown_ms_per_step": {g: round(v / a.steps, 3) for g, v in groups.items()},
-        "solve": {"iters": iters, "cycles": infos[-1]["cycles"], "rel_resid": infos[-1]["rel_resid"],
-                  "rel_resid_host_check": relres, "step_ms": [round(t, 3) for t in times],
-                  **extra, "ratio_L": extra["nnz_ML"] / extra["nnz_L"],
-                  "ratio_U": extra["nnz_MU"] / extra["nnz_U"]},
     }
 
     detail = {}
@@ -686,14 +729,15 @@ def run_ours(a):
         ms_t, (xt_, info_t, levels, keep) = time_region(torch, stream, lambda: trisolve_step(sg, ctx, P, P.dev))
         del keep
         st_t = sg.sait_ctx_stats(ctx, reset=True).as_dict()
-        out["baseline_trisolve"] = {
-            "ms": round(ms_t, 3), "iters": info_t.iters, "rel_resid": info_t.rel_resid,
+        baseline = {
+            "ms": round(ms_t, 3), "iters": info_t.iters, "rel_resid": float(f"{info_t.rel_resid:.3e}"),
             "levels": list(levels),
             "avg_trisolve_pair_ms": round(st_t["trisolve"]["ms"] / max(st_t["trisolve"]["calls"], 1), 4),
             "speedup_of_sait": round(ms_t / ms_step, 3)}
         sg.sait_ctx_set_timing(ctx, False)
         # the apply with the factors stored in FP64 / FP32 / BF16
-        out["apply_rooflines"] = apply_precisions(sg, ctx, torch, device, stream, P, a.m, flush_l2, peak)
+        apr = apply_precisions(sg, ctx, torch, device, stream, P, a.m, flush_l2, peak)
+        detail["apply_rooflines"] = apr
         # the whole step with reduced-precision SAIT storage (one run each)
         ss = {}
         for store in ("f32", "bf16"):
@@ -704,7 +748,7 @@ def run_ours(a):
             del keep
             rr = float(np.linalg.norm(P.b - P.A.to_scipy() @ xs.cpu().numpy()) / np.linalg.norm(P.b))
             ss[store] = {"ms": round(ms_s, 3), "iters": info_s.iters, "rel_resid_host_check": rr}
-        out["store_sweep"] = ss
+        store_sweep = ss
         # BiCGSTAB with the same SAIT preconditioner
         flush_l2()
         ms_b, (_, info_b, _, keep) = time_region(
@@ -734,6 +778,10 @@ def run_ours(a):
         detail["autotune"] = autotune_workload(sg, ctx, torch, device, stream, P, a.m, a.store)
         detail["optimal_params"] = optimal_params_workload(sg, ctx, P, a.store)
         out["extras"] = summarize_extras(detail)
+        # the apply with FP64 / FP32 / BF16 factors: [ms, fraction of peak]
+        out["apply_rooflines"] = {k: [v["ms"], v["frac"]] for k, v in apr.items()}
+        out["store_sweep"] = store_sweep
+        out["baseline_trisolve"] = baseline
 
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         A_h, b_h = oracle_problem(a.grid)
@@ -756,27 +804,33 @@ def summarize_extras(d):
     if "bicgstab" in d:
         s["bicgstab"] = {k: d["bicgstab"][k] for k in ("ms", "iters")}
     if "m_sweep" in d:
-        s["m_sweep_ms"] = {str(r["m_terms"]): r["ms"] for r in d["m_sweep"]}
+        s["m_sweep_ms"] = {str(r["m_terms"]): round(r["ms"], 1) for r in d["m_sweep"]}
     if "batched" in d:
         b = d["batched"]
-        s["batched_512_systems_ms"] = {k: b["independent_systems"][k]["ms"] for k in ("f64", "f32", "f32x64")
-                                       if k in b["independent_systems"]}
-        s["many_rhs_64_ms"] = {k: b["many_rhs"][k]["ms"] for k in ("f64", "f32", "f32x64") if k in b["many_rhs"]}
-        for key in ("build_roofline", "spmm_roofline"):
-            if key in b:
-                s["batched_" + key] = b[key]
+        for key, name in (("independent_systems", "batched_512"), ("many_rhs", "rhs_64")):
+            # per storage: [build ms, solve ms, max iterations, GB/s per iteration]
+            s[name] = {st: [round(b[key][st]["build_ms"], 1), round(b[key][st]["solve_ms"], 1),
+                            b[key][st]["max_iters"], round(b[key][st]["gbs_per_iteration"])]
+                       for st in ("f64", "f32", "f32x64") if st in b[key]}
     if "adjoint" in d:
         s["adjoint_ms"] = d["adjoint"]["ms_forward_backward"]
     if "eigen" in d:
         e = d["eigen"]
-        s["eigen"] = {k: {"ms": e[k]["ms"], "iters": e[k]["iters"],
-                          "err_vs_f64": e[k].get("max_rel_eig_diff_vs_f64")}
-                      for k in ("f64", "f32", "bf16") if k in e}
-        if "vs_oracle" in e:
-            s["eigen_vs_oracle"] = e["vs_oracle"]
+        # per storage at 96^3: [ms, iterations, eigenvalue difference to the FP64 run]
+        s["eigen96"] = {k: [round(e[k]["ms"]), e[k]["iters"], float(f"{e[k]['max_rel_eig_diff_vs_f64']:.1e}")]
+                        for k in ("f64", "f32", "bf16") if k in e}
+        vo = e.get("vs_oracle")
+        if vo:
+            s[f"eig_err_vs_oracle_{vo['grid']}"] = {k: float(f"{vo[k]['max_rel_eig_err_vs_oracle']:.1e}")
+                                                   for k in ("f64", "f32", "bf16") if k in vo}
     if "paper_replica" in d:
         p = d["paper_replica"]
-        s["paper_replica"] = {r["name"]: [r["ratio"], r["iters"]] for r in p["rows"]}
+        short = {"SAIT_Thr(0.05,10)": "T.05", "SAIT_Thr(0.02,10)": "T.02", "SAIT_Thr(0.01,10)": "T.01",
+                 "SAIT_Pat(1,10)": "P1", "SAIT_Pat(2,10)": "P2", "SAIT_Pat(3,10)": "P3"}
+        # per row: [nnz ratio, PCG iterations]; exact: the substitution's iterations
+        s["paper_replica"] = {f"L{lv}": {"exact": p[f"level{lv}"]["exact_ilu"]["iters"],
+                                         **{short[r["name"]]: [r["ratio"], r["iters"]]
+                                            for r in p[f"level{lv}"]["rows"]}} for lv in (0, 1)}
     if "optimal_params" in d:
         s["optimal_params_chosen"] = d["optimal_params"].get("chosen_param")
     return s

@@ -2,7 +2,7 @@
 
 Plain FP64 CPU implementations, written from the paper (Z. Lu, arXiv
 2106.12836) and the textbook algorithms it cites, of everything the GPU path
-computes: ILU(0) factors, the SAIT series with its dropping rules
+computes: ILU(0), level-of-fill ILU(p) and ILUT factors, the SAIT series with its dropping rules
 (Algorithms 1-3), the preconditioner apply z = M_U (M_L r) (Section 3.1), exact
 substitution, and the GMRES / BiCGSTAB / PCG solvers.  The arithmetic lives in
 ``sait_oracle.c`` (compiled with gcc, ``-ffp-contract=off``); this module only

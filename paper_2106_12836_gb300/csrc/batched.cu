@@ -12,8 +12,9 @@
 //     recurrences with per-column scalars; the products are block products,
 //     so every matrix entry is read once per iteration for all k columns.
 //
-// One iteration of either solver is captured once in a CUDA graph and
-// replayed between reads of the number of active systems.
+// kPollB iterations of either solver, with the count of the systems still
+// active, are captured once in a CUDA graph; the graph is replayed until the
+// count (read after each replay) is zero.
 #include <algorithm>
 #include <cmath>
 
@@ -529,19 +530,23 @@ extern "C" sait_status sait_bicgstab_batched(sait_ctx ctx, sait_mat A, sait_prec
         return SAIT_OK;
     };
     int64_t graph_kernels = 0;
-    SAIT_TRY(capture(ctx, cs, iteration, &cleanup.g, &graph_kernels));
+    // kPollB iterations and the count of active systems, captured as one graph
+    auto poll_block = [&](cudaStream_t q) -> sait_status {
+        for (int k2 = 0; k2 < kPollB; k2++) SAIT_TRY(iteration(q));
+        SAIT_CK(cudaMemsetAsync(ctx->d_word, 0, sizeof(int), q));
+        launch_k(k_b_count, gs, 256, 0, q, (int)nsys, (const int *)st.active, ctx->d_word);
+        SAIT_CK(cudaGetLastError());
+        return SAIT_OK;
+    };
+    SAIT_TRY(capture(ctx, cs, poll_block, &cleanup.g, &graph_kernels));
     SAIT_TRY(sync_streams(ctx, s0, cs, ev));
     int total_iters = 0;
     sait_status result = SAIT_OK;
     for (int round = 0;; round++) {
         // run until no system is active
         for (int it = 0; it < maxit; it += kPollB) {
-            for (int k = 0; k < kPollB; k++) {
-                SAIT_CK(cudaGraphLaunch(cleanup.g, cs));
-                g_sait_launches += graph_kernels;
-            }
-            SAIT_CK(cudaMemsetAsync(ctx->d_word, 0, sizeof(int), cs));
-            launch_k(k_b_count, gs, 256, 0, cs, (int)nsys, (const int *)st.active, ctx->d_word);
+            SAIT_CK(cudaGraphLaunch(cleanup.g, cs));
+            g_sait_launches += graph_kernels;
             SAIT_CK(cudaMemcpyAsync(h, ctx->d_word, sizeof(int), cudaMemcpyDeviceToHost, cs));
             SAIT_CK(cudaStreamSynchronize(cs));
             total_iters += kPollB;
@@ -690,17 +695,21 @@ extern "C" sait_status sait_bicgstab_multi(sait_ctx ctx, sait_mat A, sait_prec P
         return SAIT_OK;
     };
     int64_t graph_kernels = 0;
-    SAIT_TRY(capture(ctx, cs, iteration, &cleanup.g, &graph_kernels));
+    // kPollB iterations and the count of active systems, captured as one graph
+    auto poll_block = [&](cudaStream_t q) -> sait_status {
+        for (int k2 = 0; k2 < kPollB; k2++) SAIT_TRY(iteration(q));
+        SAIT_CK(cudaMemsetAsync(ctx->d_word, 0, sizeof(int), q));
+        launch_k(k_b_count, gs, 256, 0, q, (int)k, (const int *)st.active, ctx->d_word);
+        SAIT_CK(cudaGetLastError());
+        return SAIT_OK;
+    };
+    SAIT_TRY(capture(ctx, cs, poll_block, &cleanup.g, &graph_kernels));
     SAIT_TRY(sync_streams(ctx, s0, cs, ev));
     int total_iters = 0;
     for (int round = 0;; round++) {
         for (int it = 0; it < maxit; it += kPollB) {
-            for (int q = 0; q < kPollB; q++) {
-                SAIT_CK(cudaGraphLaunch(cleanup.g, cs));
-                g_sait_launches += graph_kernels;
-            }
-            SAIT_CK(cudaMemsetAsync(ctx->d_word, 0, sizeof(int), cs));
-            launch_k(k_b_count, gs, 256, 0, cs, (int)k, (const int *)st.active, ctx->d_word);
+            SAIT_CK(cudaGraphLaunch(cleanup.g, cs));
+            g_sait_launches += graph_kernels;
             SAIT_CK(cudaMemcpyAsync(h, ctx->d_word, sizeof(int), cudaMemcpyDeviceToHost, cs));
             SAIT_CK(cudaStreamSynchronize(cs));
             total_iters += kPollB;

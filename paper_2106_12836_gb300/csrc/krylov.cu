@@ -244,6 +244,7 @@ __device__ void dcgs_scalar_step(const DcgsState &S, int j, int close, int nbd) 
     __shared__ double c2[kMaxRestart + 1], dh[kMaxRestart + 1], tv[kMaxRestart + 2];
     __shared__ double s_cc, s_cd, s_e2, s_eta, s_ie, s_ig, s_gamma, s_av;
     __shared__ int s_ok;
+    __shared__ float e2w[kDotThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarp = kDotThreads / 32;
     Scal *sc = S.sc;
@@ -256,14 +257,19 @@ __device__ void dcgs_scalar_step(const DcgsState &S, int j, int close, int nbd) 
         const double v = quarter_sum(S.part + (int64_t)(q < ncol ? q : 0) * S.ldp, cnt, lane & 7);
         if (q < ncol && (lane & 7) == 0) colsum[q] = v;
     }
-    if (j >= 1 && warp == nwarp - 1) {  // ||w1||^2 by the last warp
+    if (j >= 1) {  // ||w1||^2: every thread adds a few partials, then the block
         float s0 = 0.0f;
-        for (int i = lane; i < S.nbu; i += 32) s0 += __ldcg(S.upart + i);
+        for (int i = tid; i < S.nbu; i += kDotThreads) s0 += __ldcg(S.upart + i);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-        if (lane == 0) s_e2 = (double)s0;
+        if (lane == 0) e2w[warp] = s0;
     }
     __syncthreads();
+    if (tid == 0 && j >= 1) {
+        float e = 0.0f;
+        for (int w2 = 0; w2 < nwarp; w2++) e += e2w[w2];
+        s_e2 = (double)e;
+    }
     // (2) eta = ||w1|| (one thread)
     double *Hc = S.Hr + (int64_t)(j - 1) * (S.m + 1);  // column j-1 (j >= 1)
     if (tid == 0) {

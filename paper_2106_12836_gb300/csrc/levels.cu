@@ -317,11 +317,15 @@ __device__ __forceinline__ void ilu_row_thread(int i, const int32_t *__restrict_
 }
 
 // Level l of the sweep, a thread per row: level l is order[lptr[l] ..) with
-// lcnt[l] rows (final when this launch starts).  Each row is factored (with
-// F.a), then releases its dependents; a dependent whose in-degree reaches
-// zero joins level l + 1 through the counter lcnt[l + 1] (one atomic per
-// warp).  Block 0 publishes lptr[l + 1] for the next launch, so a level costs
-// one launch and no hand-off between blocks.
+// lcnt[l] rows (final when this launch starts).  Each row releases its
+// dependents (kDep at a time, their atomics in flight together) and is
+// factored (with F.a); a dependent whose in-degree reaches zero joins level
+// l + 1 at a position from one atomic on lcnt[l + 1] per warp and round.  The
+// row's factorisation and the releases are independent (the dependents run in
+// a later launch), so their loads overlap.  Block 0 publishes lptr[l + 1] for
+// the next launch, so a level costs one launch and no hand-off between blocks.
+constexpr int kDep = 8;
+
 template <bool ILU>
 __global__ void __launch_bounds__(kIluThreads, 4)
 k_level(int l, int32_t *order, int32_t *lptr, int32_t *lcnt, const int64_t *__restrict__ trp,
@@ -337,25 +341,42 @@ k_level(int l, int32_t *order, int32_t *lptr, int32_t *lcnt, const int64_t *__re
     for (int64_t r = (int64_t)blockIdx.x * kIluThreads + threadIdx.x; r - lane < cnt; r += nt) {  // warp-uniform
         const bool valid = r < cnt;
         const int i = valid ? order[begin + r] : 0;
-        if (ILU && valid) ilu_row_thread(i, rp, F);
         int64_t t = valid ? trp[i] : 0;
         const int64_t te = valid ? trp[i + 1] : 0;
-        while (__any_sync(0xffffffffu, t < te)) {  // release the dependents
-            bool rel = false;
-            int d = 0;
-            if (t < te) {
-                d = tcol[t];
-                rel = atomicSub(indeg + d, 1) == 1;
-                t++;
+        int dd[kDep];
+        unsigned relm = 0;
+        // the first kDep releases are issued before the row's factorisation, so
+        // their atomics and its loads are in flight together
+        auto release = [&]() {
+            relm = 0;
+#pragma unroll
+            for (int u = 0; u < kDep; u++) dd[u] = t + u < te ? tcol[t + u] : -1;
+#pragma unroll
+            for (int u = 0; u < kDep; u++)
+                if (dd[u] >= 0 && atomicSub(indeg + dd[u], 1) == 1) relm |= 1u << u;
+            t += kDep;
+        };
+        release();
+        if (ILU && valid) ilu_row_thread(i, rp, F);
+        for (;;) {  // warp-uniform: append this round's released rows, then the next round
+            const int c = __popc(relm);
+            int incl = c;  // inclusive prefix of the released counts over the warp
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
             }
-            const unsigned m = __ballot_sync(0xffffffffu, rel);
-            if (m) {
-                const int leader = __ffs(m) - 1;
-                int pos = 0;
-                if (lane == leader) pos = atomicAdd(lcnt + l + 1, __popc(m));
-                pos = __shfl_sync(0xffffffffu, pos, leader);
-                if (rel) order[next + pos + __popc(m & ((1u << lane) - 1u))] = d;
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            if (total) {
+                int base = 0;
+                if (lane == 31) base = atomicAdd(lcnt + l + 1, total);
+                base = __shfl_sync(0xffffffffu, base, 31) + incl - c;
+#pragma unroll
+                for (int u = 0; u < kDep; u++)
+                    if (relm >> u & 1u) order[next + base++] = dd[u];
             }
+            if (!__any_sync(0xffffffffu, t < te)) break;
+            release();
         }
     }
 }

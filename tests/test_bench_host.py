@@ -62,3 +62,19 @@ def test_summarize_launches(tmp_path, capsys):
     assert "void k_spmv_sell<double>" in table and table["void k_spmv_sell<double>"].endswith("| 2 | 0.05 | 50.0% | 25.0 |")
     assert table["k_other"].endswith("| 1 | 0.04 | 40.0% | 40.0 |")
     assert table["k_dcgs_dot"].endswith("| 1 | 0.01 | 10.0% | 10.0 |")
+
+
+def test_batched_iteration_bytes_by_hand():
+    class A:
+        n, nnz = 1000, 4960
+    nl = nu = 5000
+    # two SAIT applies (FP32 values: 8 B per entry, w FP32), two A products, 22 FP64 vector passes
+    one = 2 * ((nl + nu) * 8 + 8 * 1001 + 24 * 1000) + 2 * (4960 * 12 + 4 * 1001 + 16 * 1000) + 22 * 8 * 1000
+    assert bench.batched_iter_bytes(A, nl, nu, "f32", 1) == one
+    # k columns: the matrices are read once, every vector term scales with k
+    k64 = 2 * ((nl + nu) * 8 + 8 * 1001 + 24 * 1000 * 64) + 2 * (4960 * 12 + 4 * 1001 + 16 * 1000 * 64) \
+        + 22 * 8 * 1000 * 64
+    assert bench.batched_iter_bytes(A, nl, nu, "f32", 64) == k64
+    # converged systems skip the vector passes: 600 of the 1000 rows iterate 8 times over 8 replays
+    part = one - 22 * 8 * 1000 + 22 * 8 * 600
+    assert bench.batched_iter_bytes(A, nl, nu, "f32", 1, row_iters=600 * 8, replays=8) == part

@@ -183,3 +183,62 @@ def test_paper_table_runtime_jacobi_on_gpu(sg, ctx, laplace100):
         _, info, st = sg.sait_pcg(ctx, Ag, sg.sait_prec_create_jacobi(ctx, L, U, k), b, tol=g["pcg_tol"])
         want = g["level0_pcg_iters"][str(k)]
         assert st == 0 and abs(info.iters - want) <= 0.05 * want, (k, info.iters)
+
+
+# ---------------------------------------------------------------------------
+# The same experiment with level-1 ILU factors (the right-hand columns of
+# Tables runtime_SAIT and runtime_Jacobi).  The nnz ratios and the exact and
+# Jacobi rows match the paper; the SAIT rows' PCG counts are checked against
+# the FP64 oracle's counts (tests/golden/make_level1_counts.py), which lie
+# 6-26% above the printed ones (SAIT_Thr(0.02,10) stalls at 1.5e-10 after
+# 2000 iterations: PCG with the nonsymmetric M_U M_L has no guarantee).
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def laplace100_level1(sg, ctx, oracle_lib):
+    A = synth.laplace3d(100)
+    Ag = mat(sg, ctx, A)
+    L, U = sg.sait_iluk(ctx, A.n, dev(A.rp), dev(A.ci), dev(A.va), 1)
+    b = dev(synth.uniform(synth.SEED_BASE, A.n, 0.0, 1.0))
+    return A, Ag, L, U, b
+
+
+def test_paper_table_runtime_sait_level1_on_gpu(sg, ctx, oracle_lib, laplace100_level1):
+    with open(os.path.join(GOLDEN, "paper_runtime_sait_level1.json")) as f:
+        g = json.load(f)
+    path = os.path.join(GOLDEN, "oracle_runtime_sait_level1.json")
+    if not os.path.exists(path):
+        pytest.skip("oracle level-1 counts not generated")
+    with open(path) as f:
+        o = json.load(f)
+    A, Ag, L, U, b = laplace100_level1
+    assert L.nnz == U.nnz == 6_910_300
+    tol, m, maxit = g["pcg_tol"], g["loop_iterations_m"], o["maxit"]
+    _, info, st = sg.sait_pcg(ctx, Ag, sg.sait_prec_create_ilu(ctx, L, U), b, tol=tol, maxit=maxit)
+    assert st == 0 and abs(info.iters - g["exact_ilu1_pcg_iters"]) <= 3
+    assert abs(info.iters - o["exact_ilu1"]["iters"]) <= 3
+    rows = [("abs", r["tau"], 0, m + 1, r, orow) for r, orow in zip(g["sait_thr"], o["sait_thr"])] + \
+           [("pattern", 0.0, r["p"], r["p"] + m + 1, r, orow) for r, orow in zip(g["sait_pat"], o["sait_pat"])]
+    for drop, tau, p, terms, row, orow in rows:
+        ML = sg.sait_build(ctx, L, True, terms, drop, tau, p)
+        MU = sg.sait_build(ctx, U, False, terms, drop, tau, p)
+        # SAIT_Thr ratios on L (rounding splits threshold ties between L and U = D L^T
+        # differently: 5.174 on L, 5.180 on U for tau = 0.01), SAIT_Pat on U
+        M, T = (ML, L) if drop == "abs" else (MU, U)
+        assert round(M.nnz / T.nnz, 2) == row["ratio"], (drop, tau, p, M.nnz)
+        _, info, st = sg.sait_pcg(ctx, Ag, sg.sait_prec_create_sait(ctx, ML, MU), b, tol=tol, maxit=maxit,
+                                  check=False)
+        if orow["status"] == 0:
+            assert st == 0 and info.rel_resid <= tol
+            assert abs(info.iters - orow["iters"]) <= max(3, 0.03 * orow["iters"]), (drop, tau, p, info.iters)
+        else:  # the oracle stalls near the tolerance within maxit: so does the GPU
+            assert st != 0 or info.iters >= 0.9 * maxit, (drop, tau, p, info.iters)
+
+
+def test_paper_table_runtime_jacobi_level1_on_gpu(sg, ctx, laplace100_level1):
+    with open(os.path.join(GOLDEN, "paper_runtime_sait_level1.json")) as f:
+        g = json.load(f)
+    A, Ag, L, U, b = laplace100_level1
+    for k in (1, 2, 4):
+        _, info, st = sg.sait_pcg(ctx, Ag, sg.sait_prec_create_jacobi(ctx, L, U, k), b, tol=g["pcg_tol"])
+        want = g["jacobi_level1_pcg_iters"][str(k)]
+        assert st == 0 and abs(info.iters - want) <= 0.05 * want, (k, info.iters)
