@@ -310,33 +310,50 @@ k_mc_dots(int64_t n, int k, int nd, const int *__restrict__ active, const double
     }
 }
 
-__global__ void k_mc_reduce(int k, int nb, int nd, const int *__restrict__ active, const double *__restrict__ partial,
-                            double *red) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= k || (active && !active[c])) return;
+// red[c*3 + q] = sum_b partial[b*k*3 + q*k + c]: one block per column c, the
+// block's threads each add a stride of the partials, then a tree (fixed
+// order; a serial FP64 sum over the blocks would cost 64 cycles per partial).
+__global__ void __launch_bounds__(kT)
+k_mc_reduce(int k, int nb, int nd, const int *__restrict__ active, const double *__restrict__ partial,
+            double *red) {
+    const int c = blockIdx.x;
+    if (active && !active[c]) return;
     for (int q = 0; q < nd; q++) {
-        double acc = 0.0;
-        for (int b = 0; b < nb; b++) acc += partial[(int64_t)b * k * 3 + q * k + c];
-        red[c * 3 + q] = acc;
+        double a0 = 0.0, a1 = 0.0;
+        int b = threadIdx.x;
+        for (; b + kT < nb; b += 2 * kT) {
+            a0 += partial[(int64_t)b * k * 3 + q * k + c];
+            a1 += partial[(int64_t)(b + kT) * k * 3 + q * k + c];
+        }
+        if (b < nb) a0 += partial[(int64_t)b * k * 3 + q * k + c];
+        const double t = block_sum(a0 + a1);
+        if (threadIdx.x == 0) red[c * 3 + q] = t;
     }
 }
 
+// Vector updates of the many-right-hand-side recurrences, n x k row-major:
+// thread (c = tid % k) handles column c over rows tid / k, stepping by the
+// grid's row count, so its column's scalars are read once.
 template <int OP>
-__global__ void k_mc_update(int64_t n, int k, BState st, const double *__restrict__ a, const double *__restrict__ b,
-                            const double *__restrict__ c2, const double *__restrict__ d, double *o1, double *o2) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * k; e += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(e % k);
-        if (OP == 3) {  // half step: x += alpha ph where state == 4
-            if (st.state[c] == 4) o1[e] += st.alpha[c] * a[e];
-            continue;
-        }
-        if (!st.active[c]) continue;
-        if (OP == 0) o1[e] = a[e] + st.beta[c] * (o1[e] - st.omega[c] * b[e]);      // p = r + beta (p - omega v)
-        else if (OP == 1) o1[e] = a[e] - st.alpha[c] * b[e];                          // s = r - alpha v
-        else if (OP == 2) {                                                            // x, r update
-            o1[e] += st.alpha[c] * a[e] + st.omega[c] * b[e];
-            o2[e] = c2[e] - st.omega[c] * d[e];
-        } else if (OP == 4) {                                                          // reset rh, p, v
+__global__ void __launch_bounds__(kT)
+k_mc_update(int64_t n, int k, BState st, const double *__restrict__ a, const double *__restrict__ b,
+            const double *__restrict__ c2, const double *__restrict__ d, double *o1, double *o2) {
+    const int c = threadIdx.x % k;
+    const int rows_per_pass = kT / k;
+    if ((int)threadIdx.x >= rows_per_pass * k) return;
+    if (OP == 3 ? st.state[c] != 4 : !st.active[c]) return;
+    const double alpha = st.alpha[c], beta = st.beta[c], omega = st.omega[c];
+    for (int64_t i = (int64_t)blockIdx.x * rows_per_pass + threadIdx.x / k; i < n;
+         i += (int64_t)gridDim.x * rows_per_pass) {
+        const int64_t e = i * k + c;
+        if (OP == 0) o1[e] = a[e] + beta * (o1[e] - omega * b[e]);       // p = r + beta (p - omega v)
+        else if (OP == 1) o1[e] = a[e] - alpha * b[e];                    // s = r - alpha v
+        else if (OP == 2) {                                               // x, r update
+            o1[e] += alpha * a[e] + omega * b[e];
+            o2[e] = c2[e] - omega * d[e];
+        } else if (OP == 3) {                                             // half step: x += alpha ph
+            o1[e] += alpha * a[e];
+        } else if (OP == 4) {                                             // reset rh, p, v
             o1[e] = a[e];
             o2[e] = 0.0;
             ((double *)c2)[e] = 0.0;
@@ -646,7 +663,7 @@ extern "C" sait_status sait_bicgstab_multi(sait_ctx ctx, sait_mat A, sait_prec P
     auto dots = [&](cudaStream_t q, const int *act, int nd, const double *x0, const double *y0, const double *x1,
                     const double *y1) {
         launch_k(k_mc_dots, (unsigned)nb, kT, 0, q, n, (int)k, nd, act, x0, y0, x1, y1, Bf.partial.p);
-        launch_k(k_mc_reduce, 1, 256, 0, q, (int)k, nb, nd, act, (const double *)Bf.partial.p, Bf.red.p);
+        launch_k(k_mc_reduce, (unsigned)k, kT, 0, q, (int)k, nb, nd, act, (const double *)Bf.partial.p, Bf.red.p);
     };
     launch_k(k_mc_residual, ge, 256, 0, s0, n, (int)k, (const int32_t *)A->rp, (const int32_t *)A->ci,
              (const double *)A->va, (const double *)X, B, Bf.r.p);

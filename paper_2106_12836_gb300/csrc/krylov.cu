@@ -124,7 +124,7 @@ __device__ __forceinline__ float4 load_w4(const double2 *w, int64_t i4) {
 // Precision as in the two-pass kernels above: dots in FP32 on V_hi, updates in
 // double-float on (V_hi, V_lo).
 constexpr int kDCH = 8;          // basis vectors per chunk of the dual dot sweep
-constexpr int kDotThreads = 512; // dual dot sweep: two blocks of 512 threads per SM
+constexpr int kDotThreads = 1024; // dual dot sweep: one block of 1024 threads per SM
 
 // Everything the last block of the dot sweep and the Givens step touch.
 struct DcgsState {
@@ -206,19 +206,24 @@ __device__ __forceinline__ void dual_tail(int rem, int64_t n4, const float4 *V, 
 }
 
 // Sum of the FP32 values x[0 .. cnt) (a 16-byte aligned run, cnt a multiple of 4)
-// by the 8 lanes of a quarter warp, returned in FP64 to all 8 lanes.
+// by the 8 lanes of a quarter warp, returned in FP64 to all 8 lanes; each lane
+// issues its loads (up to kQ float4) together, so the sum costs one L2 round
+// trip for up to 32 kQ values.
+constexpr int kQ = 8;
 __device__ __forceinline__ double quarter_sum(const float *x, int cnt, int sub) {
     const float4 *x4 = (const float4 *)x;
-    float s0 = 0.0f, s1 = 0.0f;
-    for (int i = sub; i < cnt / 4; i += 16) {
-        const float4 a = __ldcg(x4 + i);
-        s0 += (a.x + a.y) + (a.z + a.w);
-        if (i + 8 < cnt / 4) {
-            const float4 b = __ldcg(x4 + i + 8);
-            s1 += (b.x + b.y) + (b.z + b.w);
+    const int c4 = cnt / 4;
+    float s = 0.0f;
+    for (int i0 = 0; i0 < c4; i0 += 8 * kQ) {
+        float4 a[kQ];
+#pragma unroll
+        for (int u = 0; u < kQ; u++) {
+            const int i = i0 + sub + 8 * u;
+            a[u] = i < c4 ? __ldcg(x4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+#pragma unroll
+        for (int u = 0; u < kQ; u++) s += (a[u].x + a[u].y) + (a[u].z + a[u].w);
     }
-    float s = s0 + s1;
     s += __shfl_xor_sync(0xffffffffu, s, 1);
     s += __shfl_xor_sync(0xffffffffu, s, 2);
     s += __shfl_xor_sync(0xffffffffu, s, 4);
@@ -249,6 +254,19 @@ __device__ void dcgs_scalar_step(const DcgsState &S, int j, int close, int nbd) 
     const int nwarp = kDotThreads / 32;
     Scal *sc = S.sc;
     const int ncol = 2 * j + 1;
+    // the H entries of t = H c (below), loaded now so that their latency overlaps
+    // the partial sums: warps 1.. take row i = (tid - 32) / kTR, kTR threads per row
+    constexpr int kTR = 16, kTH = 4;
+    const int rid = (tid - 32) / kTR, sub = (tid - 32) % kTR;
+    double hreg[kTH];
+    const bool tpre = warp != 0 && !close && j <= kTH * kTR && rid <= j;
+    if (tpre) {
+#pragma unroll
+        for (int u = 0; u < kTH; u++) {
+            const int k = (rid > 0 ? rid - 1 : 0) + sub + kTR * u;
+            hreg[u] = k < j ? S.Hr[(int64_t)k * (S.m + 1) + rid] : 0.0;
+        }
+    }
     // (1) column sums of the partials: four columns per warp and round (quarter warps)
     const int ngroups = nwarp * 4;
     const int cnt = (nbd + 3) / 4 * 4;
@@ -325,20 +343,31 @@ __device__ void dcgs_scalar_step(const DcgsState &S, int j, int close, int nbd) 
     } else if (!close) {
         // t_i = sum_{k = max(i-1,0)}^{j-1} H(i,k) c_k over the final columns, with
         // column j-1 taken as H(i,j-1) + eta c_i; H(j,j-1) = eta gamma is added below
-        const int rid = (tid - 32) >> 3, sub = tid & 7;
-        const int rows_per_round = (kDotThreads - 32) / 8;
+        const int rows_per_round = (kDotThreads - 32) / kTR;
         for (int i0 = 0; i0 <= j; i0 += rows_per_round) {
             const int i = i0 + rid;
             double a = 0.0;
-            if (i <= j)
-                for (int k = (i > 0 ? i - 1 : 0) + sub; k < j; k += 8) {
-                    double h = S.Hr[(int64_t)k * (S.m + 1) + i];
-                    if (k == j - 1) h = i < j ? fma(eta, c2[i], h) : 0.0;
-                    a = fma(h, c2[k], a);
+            if (i <= j) {
+                const int kb = (i > 0 ? i - 1 : 0) + sub;
+                if (i0 == 0 && tpre) {
+#pragma unroll
+                    for (int u = 0; u < kTH; u++) {
+                        const int k = kb + kTR * u;
+                        if (k < j) {
+                            const double h = k == j - 1 ? (i < j ? fma(eta, c2[i], hreg[u]) : 0.0) : hreg[u];
+                            a = fma(h, c2[k], a);
+                        }
+                    }
+                } else {
+                    for (int k = kb; k < j; k += kTR) {
+                        double h = S.Hr[(int64_t)k * (S.m + 1) + i];
+                        if (k == j - 1) h = i < j ? fma(eta, c2[i], h) : 0.0;
+                        a = fma(h, c2[k], a);
+                    }
                 }
-            a += __shfl_xor_sync(0xffffffffu, a, 1);
-            a += __shfl_xor_sync(0xffffffffu, a, 2);
-            a += __shfl_xor_sync(0xffffffffu, a, 4);
+            }
+#pragma unroll
+            for (int o = 1; o < kTR; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
             if (i <= j && sub == 0) tv[i] = a;
         }
     }
@@ -387,7 +416,7 @@ __device__ void dcgs_scalar_step(const DcgsState &S, int j, int close, int nbd) 
 
 // Dual dot sweep of DCGS2 step j over the blocks' rows; the last block to finish
 // then runs the scalar step.  remaining/close: see dcgs_givens.
-__global__ void __launch_bounds__(kDotThreads, 2)
+__global__ void __launch_bounds__(kDotThreads, 1)
 k_dcgs_dot(int64_t n4, const float4 *__restrict__ V, int64_t ldv4, int j, const float4 *__restrict__ U,
            const double2 *__restrict__ W, DcgsState S, int close) {
     pdl_wait();
@@ -943,10 +972,10 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
     SAIT_CK(z.alloc(n, s));
     SAIT_CK(u.alloc(n, s));
     SAIT_CK(part.alloc((size_t)W.nb * 3, s));
-    // DCGS2: dual dot sweep on two 512-thread blocks per SM, partials column-major
+    // DCGS2: dual dot sweep on one 1024-thread block per SM, partials column-major
     // (2m + 1 slots, leading dimension a multiple of 4, padding zero); update
     // sweep on up to 16 blocks of 256 per SM plus the Givens block
-    const int nb_dot = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n4, kDotThreads), 2LL * ctx->num_sms));
+    const int nb_dot = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n4, kDotThreads), (int64_t)ctx->num_sms));
     const int ldp = (nb_dot + 3) / 4 * 4;
     const int nb_upd = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(2 * n4, kThreads), 16LL * ctx->num_sms));
     DTemp<float> dpart, upart;

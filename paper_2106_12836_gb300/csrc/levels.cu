@@ -326,6 +326,10 @@ __device__ __forceinline__ void ilu_row_thread(int i, const int32_t *__restrict_
 // the next launch, so a level costs one launch and no hand-off between blocks.
 constexpr int kDep = 8;
 
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 template <bool ILU>
 __global__ void __launch_bounds__(kIluThreads, 4)
 k_level(int l, int32_t *order, int32_t *lptr, int32_t *lcnt, const int64_t *__restrict__ trp,
@@ -373,7 +377,17 @@ k_level(int l, int32_t *order, int32_t *lptr, int32_t *lcnt, const int64_t *__re
                 base = __shfl_sync(0xffffffffu, base, 31) + incl - c;
 #pragma unroll
                 for (int u = 0; u < kDep; u++)
-                    if (relm >> u & 1u) order[next + base++] = dd[u];
+                    if (relm >> u & 1u) {
+                        const int d = dd[u];
+                        order[next + base++] = d;
+                        // the next launch reads these first: have them in L2 by then
+                        prefetch_l2(rp + d);
+                        prefetch_l2(trp + d);
+                        if (ILU) {
+                            prefetch_l2(F.dpos + d);
+                            prefetch_l2(F.tp + d);
+                        }
+                    }
             }
             if (!__any_sync(0xffffffffu, t < te)) break;
             release();
