@@ -20,6 +20,7 @@ FP64 oracle on one host core.  With the extra workloads on (the default), a
 benchmark line, and `extras` in the benchmark line summarizes it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --case eigen --grid 48               # one extra workload once (profiling)
     python bench.py --summarize-launches launches.csv   # per-kernel table of an ncu launch list
 """
 from __future__ import annotations
@@ -59,6 +60,8 @@ def parse():
     ap.add_argument("--store", default="f64", choices=["f64", "f32", "bf16", "f32x64", "bf16x64"])
     ap.add_argument("--no-extras", action="store_true", help="skip comparator and sweep runs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", choices=["bicgstab", "pcg", "trisolve", "batched", "rhs", "eigen", "adjoint"],
+                    help="run one extra workload once at --grid (for profiling) and print its record")
     ap.add_argument("--summarize-launches", metavar="CSV",
                     help="print the per-kernel table of an ncu launch list (--metrics gpu__time_duration.sum --csv)")
     return ap.parse_args()
@@ -509,11 +512,11 @@ def ortho_bytes(n, iters, restart):
     while left > 0:
         steps = min(left, restart)
         for j in range(steps):
-            # DCGS2 step j over the j final basis vectors kept as FP32 pairs (hi, lo):
+            # DCGS2 step j over the j final basis vectors kept as (hi FP32, m16) pairs:
             #   dual dot sweep  read hi (4 B per vector), fl32(u) and w (FP64)
-            #   update sweep    read hi + lo (8 B per vector), read and write u and w (FP64),
-            #                   write v_j's hi and lo and fl32(w1')
-            total += 12 * j * n + (4 + 8 + 16 + 16 + 8 + 4) * n
+            #   update sweep    read hi + m16 (6 B per vector), read u and w (FP64), write
+            #                   w1' (FP64), v_j's hi and m16 and fl32(w1')
+            total += 10 * j * n + (4 + 8 + 16 + 8 + 6 + 4) * n
         left -= steps
     return total
 
@@ -677,7 +680,7 @@ def run_ours(a):
         "apply": {"kernel": "k_spmv_sell x2 (M_L then M_U, SELL-32), one SAIT apply", "bound": "hbm",
                   "achieved": ab / apply_ms / 1e6, "bytes": ab, "ms": apply_ms,
                   "calls": stats["apply"]["calls"]},
-        "ortho": {"kernel": "GMRES DCGS2 step (k_dcgs_dot, k_reduce, k_dcgs_small, k_dcgs_update)",
+        "ortho": {"kernel": "GMRES DCGS2 step (k_dcgs_dot with its scalar step, k_dcgs_update with the rotation)",
                   "bound": "hbm", "achieved": ob / max(ortho_ms, 1e-9) / 1e6,
                   "bytes": ob / max(stats["ortho"]["calls"], 1), "ms": ortho_ms / max(stats["ortho"]["calls"], 1),
                   "calls": stats["ortho"]["calls"]},
@@ -836,10 +839,89 @@ def summarize_extras(d):
     return s
 
 
+def run_case(a):
+    """One extra workload, once, at a size chosen for profiling (--grid): the
+    same code paths as the benchmark's extras."""
+    import torch
+    import paper_2106_12836_gb300 as sg
+    from paper_2106_12836_gb300 import build as sgb
+    sgb.build()
+    torch.cuda.set_device(0)
+    device = torch.device("cuda", 0)
+    ctx = sg.Context()
+    stream = ctx.stream
+    g = a.grid
+    if a.case in ("bicgstab", "trisolve"):
+        P = Problem(g, device)
+        if a.case == "bicgstab":
+            _, info, _, keep = sait_step(sg, ctx, P, P.dev, a.m, a.store, "bicgstab")
+        else:
+            _, info, _, keep = trisolve_step(sg, ctx, P, P.dev)
+        out = {"case": a.case, "n": P.A.n, "iters": info.iters, "rel_resid": info.rel_resid}
+        del keep
+    elif a.case == "pcg":
+        A = synth.laplace3d(g)
+        d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in
+             (("rp", A.rp), ("ci", A.ci), ("va", A.va))}
+        b = torch.from_numpy(synth.uniform(synth.SEED_BASE, A.n, 0.0, 1.0)).to(device)
+        Am = sg.sait_mat_create_csr(ctx, A.n, d["rp"], d["ci"], d["va"])
+        L, U = sg.sait_ilu0(ctx, A.n, d["rp"], d["ci"], d["va"])
+        P1 = sg.sait_prec_create_sait(ctx, sg.sait_build(ctx, L, True, 11, "abs", 0.05),
+                                      sg.sait_build(ctx, U, False, 11, "abs", 0.05))
+        _, i1, _ = sg.sait_pcg(ctx, Am, P1, b, tol=1e-10)
+        _, i2, _ = sg.sait_pcg(ctx, Am, sg.sait_prec_create_jacobi(ctx, L, U, 2), b, tol=1e-10)
+        out = {"case": a.case, "n": A.n, "sait_iters": i1.iters, "jacobi2_iters": i2.iters}
+    elif a.case == "batched":
+        sides, eps = synth.aniso2d_batch_params(64, synth.SEED_BASE + 4, smax=min(256, max(16, g)))
+        systems = [synth.aniso2d(int(s_), float(e_)) for s_, e_ in zip(sides, eps)]
+        A = concat_block_diag(systems)
+        ptr = np.concatenate([[0], np.cumsum([m.n for m in systems])]).astype(np.int64)
+        b = A.to_scipy() @ synth.uniform(synth.SEED_BASE + 5, A.n)
+        d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in
+             (("rp", A.rp), ("ci", A.ci), ("va", A.va), ("b", b), ("ptr", ptr))}
+        L, U = sg.sait_ilu0(ctx, A.n, d["rp"], d["ci"], d["va"])
+        P = sg.sait_prec_create_sait(ctx, sg.sait_build(ctx, L, True, 3, DROP, TAU, store="f32"),
+                                     sg.sait_build(ctx, U, False, 3, DROP, TAU, store="f32"))
+        Am = sg.sait_mat_create_csr(ctx, A.n, d["rp"], d["ci"], d["va"])
+        _, info, st, _, _ = sg.sait_bicgstab_batched(ctx, Am, P, d["ptr"], d["b"], tol=TOL, maxit=5000, check=False)
+        out = {"case": a.case, "n": A.n, **info.as_dict()}
+    elif a.case == "rhs":
+        A = synth.laplace3d(g)
+        k = 64
+        B = np.ascontiguousarray(A.to_scipy() @ synth.uniform(synth.SEED_BASE + 6, (A.n, k)))
+        d = {kk: torch.from_numpy(np.ascontiguousarray(v)).to(device) for kk, v in
+             (("rp", A.rp), ("ci", A.ci), ("va", A.va), ("B", B))}
+        L, U = sg.sait_ilu0(ctx, A.n, d["rp"], d["ci"], d["va"])
+        P = sg.sait_prec_create_sait(ctx, sg.sait_build(ctx, L, True, 3, DROP, TAU, store="f32"),
+                                     sg.sait_build(ctx, U, False, 3, DROP, TAU, store="f32"))
+        Am = sg.sait_mat_create_csr(ctx, A.n, d["rp"], d["ci"], d["va"])
+        _, info, st, _, _ = sg.sait_bicgstab_multi(ctx, Am, P, d["B"], tol=TOL, maxit=5000, check=False)
+        out = {"case": a.case, "n": A.n, "k": k, **info.as_dict()}
+    elif a.case == "eigen":
+        A = synth.varcoef3d(g, 1.0, synth.SEED_BASE + 3)
+        d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in
+             (("rp", A.rp), ("ci", A.ci), ("va", A.va))}
+        X0 = torch.from_numpy(synth.uniform(synth.SEED_BASE + 10, (A.n, 16))).to(device)
+        L, U = sg.sait_ilut(ctx, A.n, d["rp"], d["ci"], d["va"], 1e-4, 10)
+        P = sg.sait_prec_create_sait(ctx, sg.sait_build(ctx, L, True, 3, DROP, TAU, store=a.store),
+                                     sg.sait_build(ctx, U, False, 3, DROP, TAU, store=a.store))
+        Am = sg.sait_mat_create_csr(ctx, A.n, d["rp"], d["ci"], d["va"])
+        lam, X, info, st = sg.sait_lobpcg(ctx, Am, P, X0, tol=TOL, maxit=1000, check=False)
+        out = {"case": a.case, "n": A.n, "iters": info.iters, "lambda_min": float(lam[0])}
+    else:
+        out = {"case": a.case, **adjoint_workload(sg, ctx, torch, device, stream)}
+    torch.cuda.synchronize()
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     a = parse()
     if a.summarize_launches:
         summarize_launches(a.summarize_launches)
+        return
+    if a.case:
+        run_case(a)
         return
     if a.impl == "reference":
         run_reference(a)

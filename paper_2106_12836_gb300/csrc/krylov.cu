@@ -495,16 +495,48 @@ __global__ void k_dcgs_givens(DcgsState S, int j, int remaining) {
     dcgs_givens(S, j, remaining);
 }
 
+// The basis is kept as (hi, m16): hi = v truncated to 24 significant bits (as
+// hi_part) and m16 = the next 16 bits of v's mantissa, rounded, an unsigned
+// magnitude with hi's sign, so v = hi + sign(hi) m16 2^(E-39) (E = hi's
+// unbiased exponent) to within 2^(E-40), ~2^-39 relative.  Six bytes per entry
+// instead of eight for an FP32 (hi, lo) pair; the Arnoldi relation holds to
+// ~1e-12, far below the 1e-8 the solver targets.  Values outside the normal
+// FP32 range of hi keep hi = fl32(v) and m16 = 0.
+__device__ __forceinline__ void split_hi16(double v, float &hi, unsigned short &m16) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int ef = (int)((b >> 52) & 0x7ff) - 896;
+    if (ef <= 0 || ef >= 255) {
+        hi = hi_part_slow(v);
+        m16 = 0;
+        return;
+    }
+    const unsigned long long frac = b & ((1ULL << 52) - 1);
+    hi = __uint_as_float(((unsigned)(b >> 63) << 31) | ((unsigned)ef << 23) | (unsigned)(frac >> 29));
+    const unsigned r = (unsigned)(frac & ((1ULL << 29) - 1));  // the 29 bits below hi
+    const unsigned m = (r + (1u << 12)) >> 13;
+    m16 = (unsigned short)(m > 0xffffu ? 0xffffu : m);
+}
+
+// The low part sign(hi) m16 2^(E-39) as an FP32 value (exact, integer
+// operations and one subtraction: m16 < 2^16 is exact in FP32).
+__device__ __forceinline__ float lo16_value(float hi, unsigned short m16) {
+    const unsigned hb = __float_as_uint(hi);
+    const unsigned e = (hb >> 23) & 0xffu;
+    const unsigned sb = e >= 40u ? ((hb & 0x80000000u) | ((e - 39u) << 23)) : 0u;
+    const float mf = __uint_as_float(0x4B000000u | (unsigned)m16) - 8388608.0f;
+    return mf * __uint_as_float(sb);
+}
+
 // Block 0 applies the Givens rotation of column j-1 (dcgs_givens), concurrently
 // with the sweep of the other blocks:
-// v_j = k1 w1 - V p (written over w1 in column j, with its (hi, lo) pair) and
+// v_j = k1 w1 - V p (stored as its (hi, m16) pair in column j of the basis) and
 // w1' = k2 w - k3 w1 - V r (written over w in column j + 1, with its FP32
 // copy for the next dual sweep); upart[b] = ||w1'||^2 (FP32) of sweep block b's
-// rows.  Two rows per thread (8-byte pair loads), so many resident warps hide
-// the load latency.
+// rows.  Two rows per thread (8-byte hi and 4-byte m16 pair loads), so many
+// resident warps hide the load latency.
 __global__ void __launch_bounds__(kThreads, 4)
-k_dcgs_update(int64_t n2, const float2 *__restrict__ Vh, const float2 *__restrict__ Vl, int64_t ldv2, int j,
-              double2 *wcol1, double2 *wcol, float2 *vh_out, float2 *vl_out, float2 *w32, float *upart,
+k_dcgs_update(int64_t n2, const float2 *__restrict__ Vh, const ushort2 *__restrict__ Vm, int64_t ldv2, int j,
+              const double2 *wcol1, double2 *wcol, float2 *vh_out, ushort2 *vm_out, float2 *w32, float *upart,
               DcgsState S, int remaining) {
     pdl_wait();
     pdl_trigger();
@@ -531,47 +563,49 @@ k_dcgs_update(int64_t n2, const float2 *__restrict__ Vh, const float2 *__restric
         // is accurate to |p| 2^-24 -- far below the FP64 rounding of v_j.  V r
         // carries the O(1) projections and cancels: double-float.
         float S1[2] = {0.f, 0.f}, S2[2] = {0.f, 0.f}, E2[2] = {0.f, 0.f};
-        auto term = [&](const float2 &h, const float2 &l, int q) {
+        auto term = [&](const float2 &h, const ushort2 &m, int q) {
             const float a = ph[q], b = rh[q], bl = rl[q];
             S1[0] = fmaf(h.x, a, S1[0]);
             S1[1] = fmaf(h.y, a, S1[1]);
-            df_term(S2[0], E2[0], h.x, l.x, b, bl);
-            df_term(S2[1], E2[1], h.y, l.y, b, bl);
+            df_term(S2[0], E2[0], h.x, lo16_value(h.x, m.x), b, bl);
+            df_term(S2[1], E2[1], h.y, lo16_value(h.y, m.y), b, bl);
         };
         int q = 0;
-        for (; q + 8 <= j; q += 8) {  // eight basis vectors' loads in flight (128 B per thread)
-            float2 h[8], l[8];
+        for (; q + 8 <= j; q += 8) {  // eight basis vectors' loads in flight (96 B per thread)
+            float2 h[8];
+            ushort2 l[8];
 #pragma unroll
             for (int t = 0; t < 8; t++) {
                 h[t] = __ldg(Vh + (int64_t)(q + t) * ldv2 + i);
-                l[t] = __ldg(Vl + (int64_t)(q + t) * ldv2 + i);
+                l[t] = __ldg(Vm + (int64_t)(q + t) * ldv2 + i);
             }
 #pragma unroll
             for (int t = 0; t < 8; t++) term(h[t], l[t], q + t);
         }
         for (; q + 4 <= j; q += 4) {
-            float2 h[4], l[4];
+            float2 h[4];
+            ushort2 l[4];
 #pragma unroll
             for (int t = 0; t < 4; t++) {
                 h[t] = __ldg(Vh + (int64_t)(q + t) * ldv2 + i);
-                l[t] = __ldg(Vl + (int64_t)(q + t) * ldv2 + i);
+                l[t] = __ldg(Vm + (int64_t)(q + t) * ldv2 + i);
             }
 #pragma unroll
             for (int t = 0; t < 4; t++) term(h[t], l[t], q + t);
         }
-        for (; q < j; q++) term(__ldg(Vh + (int64_t)q * ldv2 + i), __ldg(Vl + (int64_t)q * ldv2 + i), q);
+        for (; q < j; q++) term(__ldg(Vh + (int64_t)q * ldv2 + i), __ldg(Vm + (int64_t)q * ldv2 + i), q);
         const double2 u = wcol1[i], w = wcol[i];
         const double v0 = fma(k1, u.x, -widen_exact(S1[0]));
         const double v1 = fma(k1, u.y, -widen_exact(S1[1]));
         const double x0 = fma(k2, w.x, fma(-k3, u.x, -(widen_exact(S2[0]) + widen_exact(E2[0]))));
         const double x1 = fma(k2, w.y, fma(-k3, u.y, -(widen_exact(S2[1]) + widen_exact(E2[1]))));
-        float vh0, vl0, vh1, vl1;
-        split_pair(v0, vh0, vl0);
-        split_pair(v1, vh1, vl1);
-        wcol1[i] = make_double2(v0, v1);
+        float vh0, vh1;
+        unsigned short vm0, vm1;
+        split_hi16(v0, vh0, vm0);
+        split_hi16(v1, vh1, vm1);
         wcol[i] = make_double2(x0, x1);
         vh_out[i] = make_float2(vh0, vh1);
-        vl_out[i] = make_float2(vl0, vl1);
+        vm_out[i] = make_ushort2(vm0, vm1);
         const float xh0 = hi_part(x0), xh1 = hi_part(x1);
         w32[i] = make_float2(xh0, xh1);
         nrm = fmaf(xh0, xh0, nrm);
@@ -612,19 +646,22 @@ __global__ void k_dcgs_start(Scal *sc, double *g, int m) {
     for (int i = 1; i <= m; i++) g[i] = 0.0;
 }
 
-// w -= V h (sub = true) or w = V h (sub = false); nvec from *nvec_dev if given.
+// u = V y over the first *nvec basis vectors, V kept as (hi, m16) pairs: the
+// sums in double-float on the FP32 pipe (y split once per block), u in FP64.
 __global__ void __launch_bounds__(kThreads)
-k_gemv(int64_t n, const double *__restrict__ V, int64_t ldv, int nvec, const int *nvec_dev,
-       const double *__restrict__ h, double *w, int sub, const int *active) {
-    if (active && *active == 0) return;
-    __shared__ double hs[kMaxRestart + 1];
-    const int nv = nvec_dev ? *nvec_dev : nvec;
-    for (int q = threadIdx.x; q < nv; q += kThreads) hs[q] = h[q];
+k_gemv_basis(int64_t n, const float *__restrict__ Vh, const unsigned short *__restrict__ Vm, int64_t ldv,
+             const int *nvec_dev, const double *__restrict__ y, double *u) {
+    __shared__ float yh[kMaxRestart + 1], yl[kMaxRestart + 1];
+    const int nv = *nvec_dev;
+    for (int q = threadIdx.x; q < nv; q += kThreads) split_pair(y[q], yh[q], yl[q]);
     __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
-        double s = 0.0;
-        for (int q = 0; q < nv; q++) s = fma(V[(int64_t)q * ldv + i], hs[q], s);
-        w[i] = sub ? w[i] - s : s;
+        float S = 0.0f, E = 0.0f;
+        for (int q = 0; q < nv; q++) {
+            const float h = __ldg(Vh + (int64_t)q * ldv + i);
+            df_term(S, E, h, lo16_value(h, __ldg(Vm + (int64_t)q * ldv + i)), yh[q], yl[q]);
+        }
+        u[i] = widen_exact(S) + widen_exact(E);
     }
 }
 
@@ -947,17 +984,18 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
     Work W;
     W.nb = (int)std::min<int64_t>(cdiv(n, kThreads), 4LL * ctx->num_sms);
     DTemp<double> V, H, cs, sn, g, y, z, u, part;
-    DTemp<float> V32, VL, w32;  // the basis as FP32 (hi, lo) pairs; fl32(w) after pass 1
+    DTemp<float> V32, w32;      // the basis's hi parts; fl32(w) after pass 1
+    DTemp<unsigned short> VM;  // the basis's m16 parts (see split_hi16)
     DTemp<Scal> scd;
     const int64_t ldv = (n + 3) / 4 * 4, n4 = ldv / 4;  // columns padded to 16-byte vectors
     SAIT_CK(V.alloc((size_t)(m + 1) * ldv, s));
     SAIT_CK(V32.alloc((size_t)(m + 1) * ldv, s));
-    SAIT_CK(VL.alloc((size_t)(m + 1) * ldv, s));
+    SAIT_CK(VM.alloc((size_t)(m + 1) * ldv, s));
     SAIT_CK(w32.alloc((size_t)ldv, s));
     if (ldv > n) {  // the padding rows stay zero for the whole solve
         SAIT_CK(cudaMemset2DAsync(V.p + n, ldv * sizeof(double), 0, (ldv - n) * sizeof(double), m + 1, s));
         SAIT_CK(cudaMemset2DAsync(V32.p + n, ldv * sizeof(float), 0, (ldv - n) * sizeof(float), m + 1, s));
-        SAIT_CK(cudaMemset2DAsync(VL.p + n, ldv * sizeof(float), 0, (ldv - n) * sizeof(float), m + 1, s));
+        SAIT_CK(cudaMemset2DAsync(VM.p + n, ldv * sizeof(unsigned short), 0, (ldv - n) * sizeof(unsigned short), m + 1, s));
         SAIT_CK(cudaMemsetAsync(w32.p + n, 0, (ldv - n) * sizeof(float), s));
     }
     SAIT_CK(H.alloc((size_t)(m + 1) * m, s));
@@ -1040,9 +1078,9 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
                              close);
             if (!close)
                 (void)launch_pdl(k_dcgs_update, 1 + nb_upd, kThreads, 0, s, 2 * n4, (const float2 *)V32.p,
-                                 (const float2 *)VL.p, 2 * n4, j, (double2 *)wj,
+                                 (const ushort2 *)VM.p, 2 * n4, j, (const double2 *)wj,
                                  (double2 *)(V.p + (size_t)(j + 1) * ldv), (float2 *)(V32.p + (size_t)j * ldv),
-                                 (float2 *)(VL.p + (size_t)j * ldv), (float2 *)w32.p, upart.p, S, remaining);
+                                 (ushort2 *)(VM.p + (size_t)j * ldv), (float2 *)w32.p, upart.p, S, remaining);
             else
                 (void)launch_pdl(k_dcgs_givens, 1, 32, 0, s, S, j, remaining);
         };
@@ -1068,7 +1106,8 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
         cycles++;
         if (hs.state == 3) { result = SAIT_ERR_NONFINITE; break; }
         launch_k(k_hsolve, 1, kThreads, 0, s, (const double *)R.p, (const double *)g.p, y.p, m, sc);
-        launch_k(k_gemv, egrid, kThreads, 0, s, n, V.p, ldv, 0, &sc->jdone, y.p, u.p, 0, nullptr);
+        launch_k(k_gemv_basis, egrid, kThreads, 0, s, n, (const float *)V32.p, (const unsigned short *)VM.p, ldv,
+                 (const int *)&sc->jdone, (const double *)y.p, u.p);
         SAIT_CK(cudaGetLastError());
         SAIT_TRY(precondition(ctx, P, u.p, z.p, n, nullptr));
         launch_k(k_axpy1, egrid, kThreads, 0, s, n, z.p, x);

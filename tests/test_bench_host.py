@@ -3,7 +3,7 @@ behind the roofline numerators and the launch-list summary.
 
 Bars: the byte models equal the per-unit figures written out by hand
 (entries x (value + column bytes) + row pointers + vectors; DCGS2 step j:
-12 j n + 56 n), exactly; the launch summary converts units, counts launches
+10 j n + 46 n), exactly; the launch summary converts units, counts launches
 and reports shares that add up.
 """
 import os
@@ -34,14 +34,15 @@ def test_spmv_a_bytes_by_hand():
 
 def test_ortho_bytes_closed_form():
     n, m = 1000, 50
-    step = lambda j: 12 * j * n + 56 * n  # noqa: E731
+    step = lambda j: 10 * j * n + 46 * n  # noqa: E731
     # full cycles restart at j = 0
     assert bench.ortho_bytes(n, 2 * m, m) == 2 * sum(step(j) for j in range(m))
-    assert bench.ortho_bytes(n, m, m) == 12 * n * m * (m - 1) // 2 + 56 * n * m
+    assert bench.ortho_bytes(n, m, m) == 10 * n * m * (m - 1) // 2 + 46 * n * m
     # a partial last cycle
     assert bench.ortho_bytes(n, m + 7, m) == sum(step(j) for j in range(m)) + sum(step(j) for j in range(7))
-    # the benchmark's 172 steps at 128^3: the per-step figure in the bench line
-    assert int(bench.ortho_bytes(2097152, 172, 50) / 172) == 688938817
+    # the benchmark's 172 steps at 128^3 (3 cycles of 50 and one of 22): per step
+    # (3 (10 * 1225 + 46 * 50) + 10 * 231 + 46 * 22) n / 172
+    assert int(bench.ortho_bytes(2097152, 172, 50) / 172) == 46972 * 2097152 // 172 == 572717579
 
 
 def test_summarize_launches(tmp_path, capsys):
