@@ -97,9 +97,11 @@ k_reduce(const double *__restrict__ partial, int nb, int stride, double *out, co
 // dots run in FP32 on V_hi, the updates in double-float on (V_hi, V_lo) with
 // error-free two-sums, and only one FP64 operation per entry and step remains.
 //
-// Layout: the basis columns have a leading dimension ldv = n rounded up to a
-// multiple of 4 with zero padding, so the kernels below move 16-byte vectors
-// (four rows per thread) and never need a ragged tail.
+// Layout: the kernels below work on n rounded up to a multiple of 4 rows with
+// zero padding, so they move 16-byte vectors (four rows per thread) and never
+// need a ragged tail; the basis columns' leading dimension ldv adds kColPad
+// more entries, so that the columns do not all start at the same offset
+// modulo a large power of two.
 __device__ __forceinline__ float4 load_w4(const double2 *w, int64_t i4) {
     const double2 a = w[2 * i4], b = w[2 * i4 + 1];
     return make_float4(hi_part(a.x), hi_part(a.y), hi_part(b.x), hi_part(b.y));
@@ -125,6 +127,8 @@ __device__ __forceinline__ float4 load_w4(const double2 *w, int64_t i4) {
 // double-float on (V_hi, V_lo).
 constexpr int kDCH = 8;          // basis vectors per chunk of the dual dot sweep
 constexpr int kDotThreads = 1024; // dual dot sweep: one block of 1024 threads per SM
+constexpr int kUpdPre = 16;      // basis vectors an update thread prefetches before its wait
+constexpr int kColPad = 32;      // extra entries per basis column (see the layout in sait_gmres)
 
 // Everything the last block of the dot sweep and the Givens step touch.
 struct DcgsState {
@@ -139,70 +143,71 @@ struct DcgsState {
     int m;
 };
 
-// partial[slot * ldp + b] (FP32): V_q . U (slot q < j), V_q . W (slot j + q) and,
-// with DELTA, U . W (slot 2j), over block b's rows
-template <int CH, bool DELTA>
-__device__ __forceinline__ void dual_chunk(int64_t n4, const float4 *__restrict__ V, int64_t ldv4, int q0, int j,
-                                           const float4 *__restrict__ U, const double2 *__restrict__ W,
-                                           float *part, int ldp, float (*red)[2 * kDCH + 1]) {
-    constexpr int NA = 2 * CH + (DELTA ? 1 : 0);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float au[CH > 0 ? CH : 1], aw[CH > 0 ? CH : 1], ad = 0.0f;
+// The dual sweep of one warp: tiles of 32 float4 rows (128 rows) of the warp's
+// run, u and w loaded once per tile, every basis vector streamed through the tile in
+// batches of 8 (their loads in flight together).  Each batch's 16 dot products
+// over the tile are summed across the warp and added to the warp's shared
+// slots wacc[q] (V_q . U) and wacc[j + q] (V_q . W); wacc[2j] gets U . W.
+// No barrier inside the sweep, and u, w and every V entry are read once.
+__device__ __forceinline__ void dual_sweep_warp(int64_t n4, const float4 *__restrict__ V, int64_t ldv4, int j,
+                                                const float4 *__restrict__ U, const double2 *__restrict__ W,
+                                                float *wacc) {
+    const int lane = threadIdx.x & 31;
+    // one contiguous run of rows per warp, equal lengths in whole 32-byte
+    // sectors (a warp holding one more tile than another would set the time)
+    const int64_t gw = ((int64_t)blockIdx.x * kDotThreads + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * kDotThreads) >> 5;
+    const int64_t run = ((n4 + nw - 1) / nw + 1) & ~(int64_t)1;
+    const int64_t beg = min(n4, gw * run), end = min(n4, beg + run);
+    float ad = 0.0f;
+    for (int64_t i0 = beg; i0 < end; i0 += 32) {
+        const int64_t i = i0 + lane;
+        const bool ok = i < end;
+        const float4 u = ok ? U[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 w = ok ? load_w4(W, i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        ad = fmaf(u.x, w.x, ad);
+        ad = fmaf(u.y, w.y, ad);
+        ad = fmaf(u.z, w.z, ad);
+        ad = fmaf(u.w, w.w, ad);
+        for (int q0 = 0; q0 < j; q0 += kDCH) {
+            float4 vv[kDCH];
 #pragma unroll
-    for (int t = 0; t < (CH > 0 ? CH : 1); t++) au[t] = aw[t] = 0.0f;
-    for (int64_t i = (int64_t)blockIdx.x * kDotThreads + threadIdx.x; i < n4;
-         i += (int64_t)gridDim.x * kDotThreads) {
-        const float4 u = U[i];
-        const float4 w = load_w4(W, i);
-        float4 vv[CH > 0 ? CH : 1];
+            for (int t = 0; t < kDCH; t++)
+                vv[t] = ok && q0 + t < j ? __ldg(V + (int64_t)(q0 + t) * ldv4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            float v[2 * kDCH];  // v[t] = V_{q0+t} . U, v[kDCH + t] = V_{q0+t} . W over this lane's 4 rows
 #pragma unroll
-        for (int t = 0; t < CH; t++) vv[t] = __ldg(V + (int64_t)(q0 + t) * ldv4 + i);
+            for (int t = 0; t < kDCH; t++) {
+                float a = vv[t].x * u.x;
+                a = fmaf(vv[t].y, u.y, a);
+                a = fmaf(vv[t].z, u.z, a);
+                v[t] = fmaf(vv[t].w, u.w, a);
+                float b = vv[t].x * w.x;
+                b = fmaf(vv[t].y, w.y, b);
+                b = fmaf(vv[t].z, w.z, b);
+                v[kDCH + t] = fmaf(vv[t].w, w.w, b);
+            }
+            // Warp sum of the 16 values by recursive halving: at offset o a lane
+            // keeps the half of its values picked by its lane bit o and adds the
+            // partner's copy of that half (16 shuffles for 16 sums instead of 80);
+            // afterwards lanes 2i and 2i + 1 hold the sum of value i.
 #pragma unroll
-        for (int t = 0; t < CH; t++) {
-            float a = fmaf(vv[t].x, u.x, au[t]);
-            a = fmaf(vv[t].y, u.y, a);
-            a = fmaf(vv[t].z, u.z, a);
-            au[t] = fmaf(vv[t].w, u.w, a);
-            float b = fmaf(vv[t].x, w.x, aw[t]);
-            b = fmaf(vv[t].y, w.y, b);
-            b = fmaf(vv[t].z, w.z, b);
-            aw[t] = fmaf(vv[t].w, w.w, b);
+            for (int h = kDCH, o = 16; h >= 1; h >>= 1, o >>= 1) {
+                const bool up = lane & o;
+#pragma unroll
+                for (int i = 0; i < h; i++) {
+                    const float send = up ? v[i] : v[i + h];
+                    const float keep = up ? v[i + h] : v[i];
+                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                }
+            }
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+            const int vi = lane >> 1, t = vi & (kDCH - 1);
+            if (!(lane & 1) && q0 + t < j) wacc[(vi < kDCH ? 0 : j) + q0 + t] += v[0];
         }
-        if (DELTA) {
-            ad = fmaf(u.x, w.x, ad);
-            ad = fmaf(u.y, w.y, ad);
-            ad = fmaf(u.z, w.z, ad);
-            ad = fmaf(u.w, w.w, ad);
-        }
     }
 #pragma unroll
-    for (int t = 0; t < NA; t++) {
-        float v = t < CH ? au[t < CH ? t : 0] : t < 2 * CH ? aw[t >= CH && t < 2 * CH ? t - CH : 0] : ad;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp][t] = v;
-    }
-    __syncthreads();
-    if ((int)threadIdx.x < NA) {
-        float sum = 0.0f;
-        for (int w2 = 0; w2 < kDotThreads / 32; w2++) sum += red[w2][threadIdx.x];
-        const int t = threadIdx.x;
-        const int slot = t < CH ? q0 + t : t < 2 * CH ? j + q0 + (t - CH) : 2 * j;
-        part[(int64_t)slot * ldp + blockIdx.x] = sum;
-    }
-    __syncthreads();
-}
-
-template <bool DELTA>
-__device__ __forceinline__ void dual_tail(int rem, int64_t n4, const float4 *V, int64_t ldv4, int q0, int j,
-                                          const float4 *U, const double2 *W, float *part, int ldp,
-                                          float (*red)[2 * kDCH + 1]) {
-    switch (rem) {
-#define SAIT_DT(k) case k: dual_chunk<k, DELTA>(n4, V, ldv4, q0, j, U, W, part, ldp, red); break;
-        SAIT_DT(0) SAIT_DT(1) SAIT_DT(2) SAIT_DT(3) SAIT_DT(4) SAIT_DT(5) SAIT_DT(6) SAIT_DT(7)
-#undef SAIT_DT
-        default: break;
-    }
+    for (int o = 16; o > 0; o >>= 1) ad += __shfl_xor_sync(0xffffffffu, ad, o);
+    if (lane == 0) wacc[2 * j] += ad;
 }
 
 // Sum of the FP32 values x[0 .. cnt) (a 16-byte aligned run, cnt a multiple of 4)
@@ -247,6 +252,7 @@ __device__ __forceinline__ double quarter_sum(const float *x, int cnt, int sub) 
 __device__ void dcgs_scalar_step(const DcgsState &S, int j, int close, int nbd) {
     __shared__ double colsum[2 * kMaxRestart + 2];
     __shared__ double c2[kMaxRestart + 1], dh[kMaxRestart + 1], tv[kMaxRestart + 2];
+    __shared__ float c2f[kMaxRestart + 1], dhf[kMaxRestart + 1];
     __shared__ double s_cc, s_cd, s_e2, s_eta, s_ie, s_ig, s_gamma, s_av;
     __shared__ int s_ok;
     __shared__ float e2w[kDotThreads / 32];
@@ -254,6 +260,14 @@ __device__ void dcgs_scalar_step(const DcgsState &S, int j, int close, int nbd) 
     const int nwarp = kDotThreads / 32;
     Scal *sc = S.sc;
     const int ncol = 2 * j + 1;
+    // the update sweep's ||w1||^2 partials, loaded now (summed after the column sums)
+    constexpr int kE = 4;
+    float ep[kE];
+#pragma unroll
+    for (int u = 0; u < kE; u++) {
+        const int i = tid + u * kDotThreads;
+        ep[u] = j >= 1 && i < S.nbu ? __ldcg(S.upart + i) : 0.0f;
+    }
     // the H entries of t = H c (below), loaded now so that their latency overlaps
     // the partial sums: warps 1.. take row i = (tid - 32) / kTR, kTR threads per row
     constexpr int kTR = 16, kTH = 4;
@@ -277,7 +291,9 @@ __device__ void dcgs_scalar_step(const DcgsState &S, int j, int close, int nbd) 
     }
     if (j >= 1) {  // ||w1||^2: every thread adds a few partials, then the block
         float s0 = 0.0f;
-        for (int i = tid; i < S.nbu; i += kDotThreads) s0 += __ldcg(S.upart + i);
+        for (int i = tid + kE * kDotThreads; i < S.nbu; i += kDotThreads) s0 += __ldcg(S.upart + i);
+#pragma unroll
+        for (int u = 0; u < kE; u++) s0 += ep[u];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, o);
         if (lane == 0) e2w[warp] = s0;
@@ -322,14 +338,19 @@ __device__ void dcgs_scalar_step(const DcgsState &S, int j, int close, int nbd) 
     for (int q = tid; q < j; q += kDotThreads) {
         c2[q] = colsum[q] * ie;
         dh[q] = colsum[j + q] * ie;
+        c2f[q] = narrow_rn(c2[q]);
+        dhf[q] = narrow_rn(dh[q]);
     }
     __syncthreads();
-    // (3) warp 0: cc = c.c and cd = c.d; the other warps: t = H c
+    // (3) warp 0: cc = c.c and cd = c.d; the other warps: t = H c.  In FP32:
+    // c and d come from FP32 dot products and carry absolute errors of order
+    // 2^-24 already, which FP32 sums of their products do not raise, while one
+    // SM's FP64 pipe would spend microseconds on these few hundred terms.
     if (warp == 0) {
-        double a = 0.0, b = 0.0;
+        float a = 0.0f, b = 0.0f;
         for (int q = lane; q < j; q += 32) {
-            a = fma(c2[q], c2[q], a);
-            b = fma(c2[q], dh[q], b);
+            a = fmaf(c2f[q], c2f[q], a);
+            b = fmaf(c2f[q], dhf[q], b);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -337,16 +358,17 @@ __device__ void dcgs_scalar_step(const DcgsState &S, int j, int close, int nbd) 
             b += __shfl_xor_sync(0xffffffffu, b, o);
         }
         if (lane == 0) {
-            s_cc = a;
-            s_cd = b;
+            s_cc = widen_exact(a);
+            s_cd = widen_exact(b);
         }
     } else if (!close) {
+        const float etaf = narrow_rn(eta);
         // t_i = sum_{k = max(i-1,0)}^{j-1} H(i,k) c_k over the final columns, with
         // column j-1 taken as H(i,j-1) + eta c_i; H(j,j-1) = eta gamma is added below
         const int rows_per_round = (kDotThreads - 32) / kTR;
         for (int i0 = 0; i0 <= j; i0 += rows_per_round) {
             const int i = i0 + rid;
-            double a = 0.0;
+            float a = 0.0f;
             if (i <= j) {
                 const int kb = (i > 0 ? i - 1 : 0) + sub;
                 if (i0 == 0 && tpre) {
@@ -354,21 +376,22 @@ __device__ void dcgs_scalar_step(const DcgsState &S, int j, int close, int nbd) 
                     for (int u = 0; u < kTH; u++) {
                         const int k = kb + kTR * u;
                         if (k < j) {
-                            const double h = k == j - 1 ? (i < j ? fma(eta, c2[i], hreg[u]) : 0.0) : hreg[u];
-                            a = fma(h, c2[k], a);
+                            const float hf = narrow_rn(hreg[u]);
+                            const float h = k == j - 1 ? (i < j ? fmaf(etaf, c2f[i], hf) : 0.0f) : hf;
+                            a = fmaf(h, c2f[k], a);
                         }
                     }
                 } else {
                     for (int k = kb; k < j; k += kTR) {
-                        double h = S.Hr[(int64_t)k * (S.m + 1) + i];
-                        if (k == j - 1) h = i < j ? fma(eta, c2[i], h) : 0.0;
-                        a = fma(h, c2[k], a);
+                        float h = narrow_rn(S.Hr[(int64_t)k * (S.m + 1) + i]);
+                        if (k == j - 1) h = i < j ? fmaf(etaf, c2f[i], h) : 0.0f;
+                        a = fmaf(h, c2f[k], a);
                     }
                 }
             }
 #pragma unroll
             for (int o = 1; o < kTR; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            if (i <= j && sub == 0) tv[i] = a;
+            if (i <= j && sub == 0) tv[i] = widen_exact(a);
         }
     }
     __syncthreads();
@@ -422,12 +445,19 @@ k_dcgs_dot(int64_t n4, const float4 *__restrict__ V, int64_t ldv4, int j, const 
     pdl_wait();
     pdl_trigger();
     if (S.sc->active == 0) return;
-    __shared__ float red[kDotThreads / 32][2 * kDCH + 1];
+    extern __shared__ float wacc_all[];  // per warp: the 2j + 1 sums of its tiles
     __shared__ int s_last;
-    int q0 = 0;
-    for (; j - q0 > kDCH; q0 += kDCH) dual_chunk<kDCH, false>(n4, V, ldv4, q0, j, U, W, S.part, S.ldp, red);
-    if (j - q0 == kDCH) dual_chunk<kDCH, true>(n4, V, ldv4, q0, j, U, W, S.part, S.ldp, red);
-    else dual_tail<true>(j - q0, n4, V, ldv4, q0, j, U, W, S.part, S.ldp, red);
+    const int nslot = 2 * j + 1, warp = threadIdx.x >> 5;
+    for (int t = threadIdx.x; t < (kDotThreads / 32) * nslot; t += kDotThreads) wacc_all[t] = 0.0f;
+    __syncthreads();
+    dual_sweep_warp(n4, V, ldv4, j, U, W, wacc_all + warp * nslot);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nslot; t += kDotThreads) {  // the block's partials, warps in order
+        float sum = 0.0f;
+        for (int w2 = 0; w2 < kDotThreads / 32; w2++) sum += wacc_all[w2 * nslot + t];
+        S.part[(int64_t)t * S.ldp + blockIdx.x] = sum;
+    }
+    __syncthreads();
     // the last block to finish sums the partials (threadfence-reduction pattern)
     if (threadIdx.x == 0) {
         __threadfence();
@@ -517,14 +547,25 @@ __device__ __forceinline__ void split_hi16(double v, float &hi, unsigned short &
     m16 = (unsigned short)(m > 0xffffu ? 0xffffu : m);
 }
 
-// The low part sign(hi) m16 2^(E-39) as an FP32 value (exact, integer
-// operations and one subtraction: m16 < 2^16 is exact in FP32).
-__device__ __forceinline__ float lo16_value(float hi, unsigned short m16) {
-    const unsigned hb = __float_as_uint(hi);
-    const unsigned e = (hb >> 23) & 0xffu;
-    const unsigned sb = e >= 40u ? ((hb & 0x80000000u) | ((e - 39u) << 23)) : 0u;
+// The low part without its constant factor: sign(hi) m16 2^E, exact in FP32
+// (m16 < 2^16; 2^E is hi with its mantissa bits cleared).  The low part itself
+// is this times 2^-39, a factor the callers fold into their coefficients, so a
+// basis entry costs four operations to widen instead of a dozen.
+constexpr float kTail = 0x1p-39f;
+__device__ __forceinline__ float lo16_unscaled(float hi, unsigned short m16) {
     const float mf = __uint_as_float(0x4B000000u | (unsigned)m16) - 8388608.0f;
-    return mf * __uint_as_float(sb);
+    return mf * __uint_as_float(__float_as_uint(hi) & 0xff800000u);
+}
+
+// df_term with the low part of the basis entry given unscaled (lu, from
+// lo16_unscaled) and the coefficient's hi part premultiplied by kTail (as):
+// lu * as equals lo * a exactly, so the sum matches df_term's.
+__device__ __forceinline__ void df_term_t(float &S, float &E, float vh, float lu, float a, float al, float as) {
+    const float p = __fmul_rn(vh, a);
+    float e = __fmaf_rn(vh, a, -p);
+    e = __fmaf_rn(vh, al, e);
+    e = __fmaf_rn(lu, as, e);
+    df_add(S, E, p, e);
 }
 
 // Block 0 applies the Givens rotation of column j-1 (dcgs_givens), concurrently
@@ -538,6 +579,20 @@ __global__ void __launch_bounds__(kThreads, 4)
 k_dcgs_update(int64_t n2, const float2 *__restrict__ Vh, const ushort2 *__restrict__ Vm, int64_t ldv2, int j,
               const double2 *wcol1, double2 *wcol, float2 *vh_out, ushort2 *vm_out, float2 *w32, float *upart,
               DcgsState S, int remaining) {
+    // Everything this sweep reads but the coefficients is final before the dot
+    // sweep starts, so the blocks that become resident while its last block
+    // runs the scalar step pull their first rows into L2 before waiting.
+    if (blockIdx.x > 0) {
+        const int64_t i = (int64_t)(blockIdx.x - 1) * kThreads + threadIdx.x;
+        if (i < n2) {
+            prefetch_l2(wcol1 + i);
+            prefetch_l2(wcol + i);
+            for (int q = 0; q < min(j, kUpdPre); q++) {
+                prefetch_l2(Vh + (int64_t)q * ldv2 + i);
+                prefetch_l2(Vm + (int64_t)q * ldv2 + i);
+            }
+        }
+    }
     pdl_wait();
     pdl_trigger();
     if (blockIdx.x == 0) {
@@ -547,12 +602,13 @@ k_dcgs_update(int64_t n2, const float2 *__restrict__ Vh, const ushort2 *__restri
     // a stop decided by block 0 in this launch leaves the sweep's columns unused
     if (S.sc->active == 0 || S.sc->sweep == 0) return;
     const int bid = blockIdx.x - 1, nbs = gridDim.x - 1;
-    __shared__ float ph[kMaxRestart + 1], rh[kMaxRestart + 1], rl[kMaxRestart + 1];
+    __shared__ float ph[kMaxRestart + 1], rh[kMaxRestart + 1], rl[kMaxRestart + 1], rs[kMaxRestart + 1];
     __shared__ float red[kThreads / 32];
     const double *coef = S.coef;
     for (int q = threadIdx.x; q < j; q += kThreads) {
         ph[q] = (float)coef[q];
         split_pair(coef[j + q], rh[q], rl[q]);
+        rs[q] = rh[q] * kTail;
     }
     __syncthreads();
     const double k1 = S.kk[0], k2 = S.kk[1], k3 = S.kk[2];
@@ -564,11 +620,11 @@ k_dcgs_update(int64_t n2, const float2 *__restrict__ Vh, const ushort2 *__restri
         // carries the O(1) projections and cancels: double-float.
         float S1[2] = {0.f, 0.f}, S2[2] = {0.f, 0.f}, E2[2] = {0.f, 0.f};
         auto term = [&](const float2 &h, const ushort2 &m, int q) {
-            const float a = ph[q], b = rh[q], bl = rl[q];
+            const float a = ph[q], b = rh[q], bl = rl[q], bs = rs[q];
             S1[0] = fmaf(h.x, a, S1[0]);
             S1[1] = fmaf(h.y, a, S1[1]);
-            df_term(S2[0], E2[0], h.x, lo16_value(h.x, m.x), b, bl);
-            df_term(S2[1], E2[1], h.y, lo16_value(h.y, m.y), b, bl);
+            df_term_t(S2[0], E2[0], h.x, lo16_unscaled(h.x, m.x), b, bl, bs);
+            df_term_t(S2[1], E2[1], h.y, lo16_unscaled(h.y, m.y), b, bl, bs);
         };
         int q = 0;
         for (; q + 8 <= j; q += 8) {  // eight basis vectors' loads in flight (96 B per thread)
@@ -651,15 +707,18 @@ __global__ void k_dcgs_start(Scal *sc, double *g, int m) {
 __global__ void __launch_bounds__(kThreads)
 k_gemv_basis(int64_t n, const float *__restrict__ Vh, const unsigned short *__restrict__ Vm, int64_t ldv,
              const int *nvec_dev, const double *__restrict__ y, double *u) {
-    __shared__ float yh[kMaxRestart + 1], yl[kMaxRestart + 1];
+    __shared__ float yh[kMaxRestart + 1], yl[kMaxRestart + 1], ys[kMaxRestart + 1];
     const int nv = *nvec_dev;
-    for (int q = threadIdx.x; q < nv; q += kThreads) split_pair(y[q], yh[q], yl[q]);
+    for (int q = threadIdx.x; q < nv; q += kThreads) {
+        split_pair(y[q], yh[q], yl[q]);
+        ys[q] = yh[q] * kTail;
+    }
     __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
         float S = 0.0f, E = 0.0f;
         for (int q = 0; q < nv; q++) {
             const float h = __ldg(Vh + (int64_t)q * ldv + i);
-            df_term(S, E, h, lo16_value(h, __ldg(Vm + (int64_t)q * ldv + i)), yh[q], yl[q]);
+            df_term_t(S, E, h, lo16_unscaled(h, __ldg(Vm + (int64_t)q * ldv + i)), yh[q], yl[q], ys[q]);
         }
         u[i] = widen_exact(S) + widen_exact(E);
     }
@@ -987,7 +1046,10 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
     DTemp<float> V32, w32;      // the basis's hi parts; fl32(w) after pass 1
     DTemp<unsigned short> VM;  // the basis's m16 parts (see split_hi16)
     DTemp<Scal> scd;
-    const int64_t ldv = (n + 3) / 4 * 4, n4 = ldv / 4;  // columns padded to 16-byte vectors
+    // rows padded to 16-byte vectors (n4 of them), and the columns' leading
+    // dimension kColPad entries longer still: at power-of-two n the columns would
+    // otherwise start at the same offset modulo every power of two up to n
+    const int64_t n4 = (n + 3) / 4, ldv = 4 * n4 + kColPad;
     SAIT_CK(V.alloc((size_t)(m + 1) * ldv, s));
     SAIT_CK(V32.alloc((size_t)(m + 1) * ldv, s));
     SAIT_CK(VM.alloc((size_t)(m + 1) * ldv, s));
@@ -1016,6 +1078,10 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
     const int nb_dot = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n4, kDotThreads), (int64_t)ctx->num_sms));
     const int ldp = (nb_dot + 3) / 4 * 4;
     const int nb_upd = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(2 * n4, kThreads), 16LL * ctx->num_sms));
+    // per-warp sums of the dual sweep in dynamic shared memory (2j + 1 per warp)
+    auto dot_smem = [](int j) { return (size_t)(kDotThreads / 32) * (2 * j + 1) * sizeof(float); };
+    if (dot_smem(m) > 48 * 1024)
+        SAIT_CK(cudaFuncSetAttribute(k_dcgs_dot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dot_smem(m)));
     DTemp<float> dpart, upart;
     SAIT_CK(dpart.alloc((size_t)(2 * m + 2) * ldp, s));
     SAIT_CK(cudaMemsetAsync(dpart.p, 0, (size_t)(2 * m + 2) * ldp * sizeof(float), s));
@@ -1074,11 +1140,11 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
             const double2 *wn = (const double2 *)(close ? wj : V.p + (size_t)(j + 1) * ldv);
             ScopedTimer tm(ctx, SAIT_TIMER_ORTHO);
             // each kernel may be scheduled while its predecessor drains
-            (void)launch_pdl(k_dcgs_dot, nb_dot, kDotThreads, 0, s, n4, Vh4, n4, j, (const float4 *)w32.p, wn, S,
-                             close);
+            (void)launch_pdl(k_dcgs_dot, nb_dot, kDotThreads, dot_smem(j), s, n4, Vh4, ldv / 4, j,
+                             (const float4 *)w32.p, wn, S, close);
             if (!close)
                 (void)launch_pdl(k_dcgs_update, 1 + nb_upd, kThreads, 0, s, 2 * n4, (const float2 *)V32.p,
-                                 (const ushort2 *)VM.p, 2 * n4, j, (const double2 *)wj,
+                                 (const ushort2 *)VM.p, ldv / 2, j, (const double2 *)wj,
                                  (double2 *)(V.p + (size_t)(j + 1) * ldv), (float2 *)(V32.p + (size_t)j * ldv),
                                  (ushort2 *)(VM.p + (size_t)j * ldv), (float2 *)w32.p, upart.p, S, remaining);
             else

@@ -326,10 +326,6 @@ __device__ __forceinline__ void ilu_row_thread(int i, const int32_t *__restrict_
 // the next launch, so a level costs one launch and no hand-off between blocks.
 constexpr int kDep = 8;
 
-__device__ __forceinline__ void prefetch_l2(const void *p) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 template <bool ILU>
 __global__ void __launch_bounds__(kIluThreads, 4)
 k_level(int l, int32_t *order, int32_t *lptr, int32_t *lcnt, const int64_t *__restrict__ trp,
