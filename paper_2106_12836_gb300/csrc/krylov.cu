@@ -143,33 +143,49 @@ struct DcgsState {
     int m;
 };
 
-// The dual sweep of one warp: tiles of 32 float4 rows (128 rows) of the warp's
-// run, u and w loaded once per tile, every basis vector streamed through the tile in
-// batches of 8 (their loads in flight together).  Each batch's 16 dot products
+// The dual sweep of one warp.  The work is cut into units (tile, batch): a
+// tile is 32 float4 rows (128 rows), a batch up to 8 basis vectors, and each
+// warp takes an equal run of consecutive units (tile-major), so no warp waits
+// on a partly filled last tile.  u and w are loaded when the tile changes, the
+// batch's vector loads are in flight together; each batch's 16 dot products
 // over the tile are summed across the warp and added to the warp's shared
-// slots wacc[q] (V_q . U) and wacc[j + q] (V_q . W); wacc[2j] gets U . W.
-// No barrier inside the sweep, and u, w and every V entry are read once.
+// slots wacc[q] (V_q . U) and wacc[j + q] (V_q . W); wacc[2j] gets U . W from
+// the unit holding the tile's first batch.  No barrier inside the sweep.
 __device__ __forceinline__ void dual_sweep_warp(int64_t n4, const float4 *__restrict__ V, int64_t ldv4, int j,
                                                 const float4 *__restrict__ U, const double2 *__restrict__ W,
                                                 float *wacc) {
     const int lane = threadIdx.x & 31;
-    // one contiguous run of rows per warp, equal lengths in whole 32-byte
-    // sectors (a warp holding one more tile than another would set the time)
     const int64_t gw = ((int64_t)blockIdx.x * kDotThreads + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * kDotThreads) >> 5;
-    const int64_t run = ((n4 + nw - 1) / nw + 1) & ~(int64_t)1;
-    const int64_t beg = min(n4, gw * run), end = min(n4, beg + run);
+    const int nbat = j > 0 ? (j + kDCH - 1) / kDCH : 1;
+    const int64_t units = (n4 + 31) / 32 * nbat;
+    const int64_t per = (units + nw - 1) / nw;
+    const int64_t ub = min(units, gw * per), ue = min(units, ub + per);
+    int64_t tile = ub / nbat;
+    int bat = (int)(ub - tile * nbat);
     float ad = 0.0f;
-    for (int64_t i0 = beg; i0 < end; i0 += 32) {
-        const int64_t i = i0 + lane;
-        const bool ok = i < end;
-        const float4 u = ok ? U[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 w = ok ? load_w4(W, i) : make_float4(0.f, 0.f, 0.f, 0.f);
-        ad = fmaf(u.x, w.x, ad);
-        ad = fmaf(u.y, w.y, ad);
-        ad = fmaf(u.z, w.z, ad);
-        ad = fmaf(u.w, w.w, ad);
-        for (int q0 = 0; q0 < j; q0 += kDCH) {
+    float4 u = make_float4(0.f, 0.f, 0.f, 0.f), w = u;
+    bool ok = false;
+    for (int64_t un = ub; un < ue; un++) {
+        const int64_t i = tile * 32 + lane;
+        if (un == ub || bat == 0) {  // a new tile
+            ok = i < n4;
+            u = ok ? U[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            w = ok ? load_w4(W, i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (bat == 0) {
+                ad = fmaf(u.x, w.x, ad);
+                ad = fmaf(u.y, w.y, ad);
+                ad = fmaf(u.z, w.z, ad);
+                ad = fmaf(u.w, w.w, ad);
+            }
+        }
+        const int q0 = bat * kDCH;
+        if (++bat == nbat) {
+            bat = 0;
+            tile++;
+        }
+        if (q0 >= j) continue;
+        {
             float4 vv[kDCH];
 #pragma unroll
             for (int t = 0; t < kDCH; t++)
@@ -194,10 +210,10 @@ __device__ __forceinline__ void dual_sweep_warp(int64_t n4, const float4 *__rest
             for (int h = kDCH, o = 16; h >= 1; h >>= 1, o >>= 1) {
                 const bool up = lane & o;
 #pragma unroll
-                for (int i = 0; i < h; i++) {
-                    const float send = up ? v[i] : v[i + h];
-                    const float keep = up ? v[i + h] : v[i];
-                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                for (int e = 0; e < h; e++) {
+                    const float send = up ? v[e] : v[e + h];
+                    const float keep = up ? v[e + h] : v[e];
+                    v[e] = keep + __shfl_xor_sync(0xffffffffu, send, o);
                 }
             }
             v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
@@ -211,28 +227,41 @@ __device__ __forceinline__ void dual_sweep_warp(int64_t n4, const float4 *__rest
 }
 
 // Sum of the FP32 values x[0 .. cnt) (a 16-byte aligned run, cnt a multiple of 4)
-// by the 8 lanes of a quarter warp, returned in FP64 to all 8 lanes; each lane
-// issues its loads (up to kQ float4) together, so the sum costs one L2 round
-// trip for up to 32 kQ values.
-constexpr int kQ = 8;
-__device__ __forceinline__ double quarter_sum(const float *x, int cnt, int sub) {
+// by a group of LPC lanes (LPC = 8, 16 or 32, aligned in the warp), returned to
+// all of them; each lane issues its loads (up to KQ float4) together, so the
+// sum costs one L2 round trip for up to 4 LPC KQ values.
+template <int LPC, int KQ>
+__device__ __forceinline__ float group_sum(const float *x, int cnt, int sub) {
     const float4 *x4 = (const float4 *)x;
     const int c4 = cnt / 4;
     float s = 0.0f;
-    for (int i0 = 0; i0 < c4; i0 += 8 * kQ) {
-        float4 a[kQ];
+    for (int i0 = 0; i0 < c4; i0 += LPC * KQ) {
+        float4 a[KQ];
 #pragma unroll
-        for (int u = 0; u < kQ; u++) {
-            const int i = i0 + sub + 8 * u;
+        for (int u = 0; u < KQ; u++) {
+            const int i = i0 + sub + LPC * u;
             a[u] = i < c4 ? __ldcg(x4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
-        for (int u = 0; u < kQ; u++) s += (a[u].x + a[u].y) + (a[u].z + a[u].w);
+        for (int u = 0; u < KQ; u++) s += (a[u].x + a[u].y) + (a[u].z + a[u].w);
     }
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    s += __shfl_xor_sync(0xffffffffu, s, 4);
-    return (double)s;
+#pragma unroll
+    for (int o = 1; o < LPC; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// colsum[q] = sum over the dot sweep's blocks of part[q * ldp + b], q < ncol:
+// LPC lanes per column, so that ncol columns of cnt partials take one or two rounds.
+template <int LPC, int KQ>
+__device__ __forceinline__ void column_sums(const DcgsState &S, int ncol, int cnt, double *colsum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kPerWarp = 32 / LPC;
+    const int groups = (kDotThreads / 32) * kPerWarp;
+    for (int q0 = 0; q0 < ncol; q0 += groups) {
+        const int q = q0 + warp * kPerWarp + lane / LPC;
+        const float v = group_sum<LPC, KQ>(S.part + (int64_t)(q < ncol ? q : 0) * S.ldp, cnt, lane % LPC);
+        if (q < ncol && lane % LPC == 0) colsum[q] = widen_exact(v);
+    }
 }
 
 // The scalar step of DCGS2 step j, run by the last block of the dot sweep once
@@ -281,14 +310,11 @@ __device__ void dcgs_scalar_step(const DcgsState &S, int j, int close, int nbd) 
             hreg[u] = k < j ? S.Hr[(int64_t)k * (S.m + 1) + rid] : 0.0;
         }
     }
-    // (1) column sums of the partials: four columns per warp and round (quarter warps)
-    const int ngroups = nwarp * 4;
+    // (1) column sums of the partials: a warp, half warp or quarter warp per column
     const int cnt = (nbd + 3) / 4 * 4;
-    for (int q0 = 0; q0 < ncol; q0 += ngroups) {
-        const int q = q0 + warp * 4 + (lane >> 3);
-        const double v = quarter_sum(S.part + (int64_t)(q < ncol ? q : 0) * S.ldp, cnt, lane & 7);
-        if (q < ncol && (lane & 7) == 0) colsum[q] = v;
-    }
+    if (ncol <= nwarp) column_sums<32, 5>(S, ncol, cnt, colsum);
+    else if (ncol <= 2 * nwarp) column_sums<16, 10>(S, ncol, cnt, colsum);
+    else column_sums<8, 10>(S, ncol, cnt, colsum);
     if (j >= 1) {  // ||w1||^2: every thread adds a few partials, then the block
         float s0 = 0.0f;
         for (int i = tid + kE * kDotThreads; i < S.nbu; i += kDotThreads) s0 += __ldcg(S.upart + i);
