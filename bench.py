@@ -500,10 +500,10 @@ def apply_bytes(n, nnz_l, nnz_u, store):
 
 
 # DRAM bytes (read + write) per launch from ncu captures, scaled to the benchmark size
-# where the capture ran on a smaller grid (profiles/spmv_sell_dram_traffic_convdiff96.md):
-# one SELL-32 FP64 product of a 96^3 SAIT factor (8,709,408 entries) moved 113,786,880 B;
-# scaled by entries to the two 128^3 factors (20,726,144 each) of one apply.
-TRAFFIC = {"128:3:f64": {"apply": round(113786880 * 20726144 / 8709408 * 2)}}
+# where the capture ran on a smaller grid: the two SELL-32 FP64 products of one SAIT
+# apply on the 96^3 factors (8,709,408 entries each) moved 115,658,752 B (M_L) and
+# 115,724,544 B (M_U); scaled by entries to the two 128^3 factors (20,726,144 each).
+TRAFFIC = {"128:3:f64": {"apply": round((115658752 + 115724544) * 20726144 / 8709408)}}
 
 
 def ortho_bytes(n, iters, restart):
