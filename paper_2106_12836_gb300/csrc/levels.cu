@@ -316,14 +316,15 @@ __device__ __forceinline__ void ilu_row_thread(int i, const int32_t *__restrict_
     if (!(piv != 0.0) || !isfinite(piv)) atomicOr(F.err, kIluErrPivot);
 }
 
-// Level l of the sweep, a thread per row: level l is order[lptr[l] ..) with
-// lcnt[l] rows (final when this launch starts).  Each row releases its
+// Level l of the sweep, a thread per row and role: level l is order[lptr[l] ..)
+// with lcnt[l] rows (final when this launch starts).  Each row releases its
 // dependents (kDep at a time, their atomics in flight together) and is
 // factored (with F.a); a dependent whose in-degree reaches zero joins level
 // l + 1 at a position from one atomic on lcnt[l + 1] per warp and round.  The
 // row's factorisation and the releases are independent (the dependents run in
-// a later launch), so their loads overlap.  Block 0 publishes lptr[l + 1] for
-// the next launch, so a level costs one launch and no hand-off between blocks.
+// a later launch), so they run in different warps at the same time.  Block 0
+// publishes lptr[l + 1] for the next launch, so a level costs one launch and
+// no hand-off between blocks.
 constexpr int kDep = 8;
 
 template <bool ILU>
@@ -337,16 +338,25 @@ k_level(int l, int32_t *order, int32_t *lptr, int32_t *lcnt, const int64_t *__re
     const int next = begin + cnt;
     if (blockIdx.x == 0 && threadIdx.x == 0) lptr[l + 1] = next;
     const int lane = threadIdx.x & 31;
-    const int64_t nt = (int64_t)gridDim.x * kIluThreads;
-    for (int64_t r = (int64_t)blockIdx.x * kIluThreads + threadIdx.x; r - lane < cnt; r += nt) {  // warp-uniform
+    // With ILU the warps come in pairs over the same 32 rows: the even warp
+    // factors them, the odd one releases their dependents.  A thread's loads
+    // wait behind its own atomics, so one thread doing both would serialise
+    // the two round-trip chains; two warps run them side by side.
+    const int64_t gw = ((int64_t)blockIdx.x * kIluThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kIluThreads) >> 5;
+    const int64_t unit = ILU ? gw >> 1 : gw, nunits = ILU ? nwarps >> 1 : nwarps;
+    const bool factor = ILU && !(gw & 1);
+    for (int64_t r = unit * 32 + lane; r - lane < cnt; r += nunits * 32) {  // warp-uniform
         const bool valid = r < cnt;
         const int i = valid ? order[begin + r] : 0;
+        if (factor) {
+            if (valid) ilu_row_thread(i, rp, F);
+            continue;
+        }
         int64_t t = valid ? trp[i] : 0;
         const int64_t te = valid ? trp[i + 1] : 0;
         int dd[kDep];
         unsigned relm = 0;
-        // the first kDep releases are issued before the row's factorisation, so
-        // their atomics and its loads are in flight together
         auto release = [&]() {
             relm = 0;
 #pragma unroll
@@ -357,7 +367,6 @@ k_level(int l, int32_t *order, int32_t *lptr, int32_t *lcnt, const int64_t *__re
             t += kDep;
         };
         release();
-        if (ILU && valid) ilu_row_thread(i, rp, F);
         for (;;) {  // warp-uniform: append this round's released rows, then the next round
             const int c = __popc(relm);
             int incl = c;  // inclusive prefix of the released counts over the warp
