@@ -179,15 +179,20 @@ extern "C" const char *sait_ctx_last_error(sait_ctx ctx) {
 }
 
 // ---- matrices -----------------------------------------------------------------
+cudaError_t mat_array(sait_ctx ctx, sait_mat M, void **p, size_t bytes) {
+    M->pooled = true;
+    return cudaMallocAsync(p, bytes ? bytes : 1, ctx->stream);
+}
+
 sait_status mat_alloc(sait_ctx ctx, int64_t n, int64_t nnz, sait_mat *out) {
     sait_mat M = new (std::nothrow) sait_mat_s();
     if (!M) return ctx_fail(ctx, SAIT_ERR_OOM, "host allocation failed");
     M->n = n;
     M->nnz = nnz;
     M->device = ctx->device;
-    cudaError_t e = cudaMalloc((void **)&M->rp, (n + 1) * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&M->ci, (nnz ? nnz : 1) * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&M->va, (nnz ? nnz : 1) * sizeof(double));
+    cudaError_t e = mat_array(ctx, M, (void **)&M->rp, (n + 1) * sizeof(int32_t));
+    if (e == cudaSuccess) e = mat_array(ctx, M, (void **)&M->ci, (nnz ? nnz : 1) * sizeof(int32_t));
+    if (e == cudaSuccess) e = mat_array(ctx, M, (void **)&M->va, (nnz ? nnz : 1) * sizeof(double));
     if (e != cudaSuccess) {
         sait_mat_destroy(M);
         return ctx_cuda(ctx, e, "mat_alloc", __FILE__, __LINE__);
@@ -201,10 +206,10 @@ sait_status mat_prepare_store(sait_ctx ctx, sait_mat M, sait_dtype store_mode) {
     SAIT_TRY(mat_prepare_sell(ctx, M, store_mode));
     const sait_dtype store = store_base(store_mode);
     if (store == SAIT_F32 && !M->va32) {
-        SAIT_CK(cudaMalloc((void **)&M->va32, (M->nnz ? M->nnz : 1) * sizeof(float)));
+        SAIT_CK(mat_array(ctx, M, (void **)&M->va32, (M->nnz ? M->nnz : 1) * sizeof(float)));
         SAIT_CK(cast_values(M->va, M->va32, nullptr, M->nnz, ctx->stream));
     } else if (store == SAIT_BF16 && !M->va16) {
-        SAIT_CK(cudaMalloc((void **)&M->va16, (M->nnz ? M->nnz : 1) * sizeof(__nv_bfloat16)));
+        SAIT_CK(mat_array(ctx, M, (void **)&M->va16, (M->nnz ? M->nnz : 1) * sizeof(__nv_bfloat16)));
         SAIT_CK(cast_values(M->va, nullptr, M->va16, M->nnz, ctx->stream));
     }
     M->store = store_mode;
@@ -261,6 +266,13 @@ extern "C" sait_status sait_mat_create_csr(sait_ctx ctx, const sait_csr *A, sait
 
 extern "C" sait_status sait_mat_destroy(sait_mat M) {
     if (!M) return SAIT_ERR_INVALID_ARG;
+    if (M->pooled) {  // cudaFree does not wait for work still reading pool memory
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != M->device) cudaSetDevice(M->device);
+        cudaDeviceSynchronize();
+        if (cur >= 0 && cur != M->device) cudaSetDevice(cur);
+    }
     if (M->rp) cudaFree(M->rp);
     if (M->ci) cudaFree(M->ci);
     if (M->va) cudaFree(M->va);
@@ -344,8 +356,11 @@ extern "C" sait_status sait_prec_create_sait(sait_ctx ctx, sait_mat ML, sait_mat
     p->up = MU;
     p->n = ML->n;
     p->device = ctx->device;
-    cudaError_t e = cudaMalloc((void **)&p->tmp, (p->n ? p->n : 1) * sizeof(double));
+    p->pooled = true;
+    cudaError_t e = cudaMallocAsync((void **)&p->tmp, (p->n ? p->n : 1) * sizeof(double), ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // usable from any stream on return
     if (e != cudaSuccess) {
+        if (p->tmp) cudaFreeAsync(p->tmp, ctx->stream);
         delete p;
         return ctx_cuda(ctx, e, "sait_prec_create_sait", __FILE__, __LINE__);
     }
@@ -447,6 +462,13 @@ extern "C" sait_status sait_prec_apply(sait_ctx ctx, sait_prec P, const double *
 
 extern "C" sait_status sait_prec_destroy(sait_prec P) {
     if (!P) return SAIT_ERR_INVALID_ARG;
+    if (P->pooled) {  // cudaFree does not wait for work still reading pool memory
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != P->device) cudaSetDevice(P->device);
+        cudaDeviceSynchronize();
+        if (cur >= 0 && cur != P->device) cudaSetDevice(cur);
+    }
     if (P->graph) cudaGraphExecDestroy(P->graph);
     free_levels(&P->lev_lo);
     free_levels(&P->lev_up);

@@ -99,6 +99,7 @@ struct sait_mat_s {
     sait_dtype store = SAIT_F64;
     int device = 0;
     int lanes = 8;                  // lanes per row for CSR products
+    bool pooled = false;            // arrays from the stream-ordered pool (see mat_array)
     // SELL-32 copy for products (built on demand; see sell.cu)
     bool sell_rejected = false;     // padding above 20%: products stay on CSR
     bool force_csr = false;         // set by sait_mat_autotune when CSR products won
@@ -110,6 +111,14 @@ struct sait_mat_s {
     __nv_bfloat16 *sva16 = nullptr;
 };
 
+// A device array of M from the context's stream-ordered pool: a large
+// cudaMalloc maps fresh memory and its cudaFree synchronises the device, both
+// per matrix, while the pool hands back memory freed earlier (the ILU factors,
+// SAIT factors and their SELL copies are rebuilt for every system).
+// sait_mat_destroy synchronises the device before returning pooled arrays,
+// since cudaFree does not wait for work still using them.
+cudaError_t mat_array(sait_ctx ctx, sait_mat M, void **p, size_t bytes);
+
 struct LevelSchedule {
     int32_t nlev = 0;
     int32_t *rows = nullptr;            // device: rows ordered by level
@@ -119,6 +128,7 @@ struct LevelSchedule {
 
 struct sait_prec_s {
     int kind = 0;  // 1 SAIT pair, 2 exact ILU, 3 Jacobi sweeps
+    bool pooled = false;        // tmp from the stream-ordered pool (kind 1, see mat_array)
     int sweeps = 0;             // kind 3: sweeps per triangle
     double *dinv = nullptr;     // kind 3: 1 / diag(L) then 1 / diag(U), 2n
     sait_mat lo = nullptr, up = nullptr;

@@ -148,26 +148,26 @@ sait_status mat_prepare_sell(sait_ctx ctx, sait_mat M, sait_dtype store) {
         DTemp<int64_t> slots;
         SAIT_CK(slots.alloc(nslices, s));
         int64_t *soff = nullptr;
-        SAIT_CK(cudaMalloc((void **)&soff, (nslices + 1) * sizeof(int64_t)));
+        SAIT_CK(mat_array(ctx, M, (void **)&soff, (nslices + 1) * sizeof(int64_t)));
         launch_k(k_sell_len, grid, 256, 0, s, n, nslices, (const int32_t *)M->rp, slots.p);
         cudaError_t e = scan_i64(slots.p, soff, nslices, s);
         int64_t total = 0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&total, soff + nslices, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
-            cudaFree(soff);
+            cudaFreeAsync(soff, s);
             return ctx_cuda(ctx, e, "mat_prepare_sell", __FILE__, __LINE__);
         }
         if ((double)total > 1.2 * (double)std::max<int64_t>(M->nnz, 1)) {
-            cudaFree(soff);
+            cudaFreeAsync(soff, s);
             M->sell_rejected = true;  // too ragged: products stay on CSR
             return SAIT_OK;
         }
         M->soff = soff;
         M->nslices = nslices;
         M->sell_nnz = total;
-        SAIT_CK(cudaMalloc((void **)&M->sci, std::max<int64_t>(total, 1) * sizeof(int32_t)));
-        SAIT_CK(cudaMalloc((void **)&M->sva64, std::max<int64_t>(total, 1) * sizeof(double)));
+        SAIT_CK(mat_array(ctx, M, (void **)&M->sci, std::max<int64_t>(total, 1) * sizeof(int32_t)));
+        SAIT_CK(mat_array(ctx, M, (void **)&M->sva64, std::max<int64_t>(total, 1) * sizeof(double)));
         launch_k(k_sell_fill<double>, grid, 256, 0, s, n, nslices, (const int32_t *)M->rp,
                  (const int32_t *)M->ci, (const double *)M->va, (const int64_t *)M->soff, M->sci, M->sva64,
                  true);
@@ -176,13 +176,13 @@ sait_status mat_prepare_sell(sait_ctx ctx, sait_mat M, sait_dtype store) {
     const int64_t total = M->sell_nnz;
     store = store_base(store);
     if (store == SAIT_F32 && !M->sva32) {
-        SAIT_CK(cudaMalloc((void **)&M->sva32, std::max<int64_t>(total, 1) * sizeof(float)));
+        SAIT_CK(mat_array(ctx, M, (void **)&M->sva32, std::max<int64_t>(total, 1) * sizeof(float)));
         launch_k(k_sell_fill<float>, grid, 256, 0, s, n, nslices, (const int32_t *)M->rp,
                  (const int32_t *)M->ci, (const double *)M->va, (const int64_t *)M->soff, M->sci, M->sva32,
                  false);
         SAIT_CK(cudaGetLastError());
     } else if (store == SAIT_BF16 && !M->sva16) {
-        SAIT_CK(cudaMalloc((void **)&M->sva16, std::max<int64_t>(total, 1) * sizeof(__nv_bfloat16)));
+        SAIT_CK(mat_array(ctx, M, (void **)&M->sva16, std::max<int64_t>(total, 1) * sizeof(__nv_bfloat16)));
         launch_k(k_sell_fill<__nv_bfloat16>, grid, 256, 0, s, n, nslices, (const int32_t *)M->rp,
                  (const int32_t *)M->ci, (const double *)M->va, (const int64_t *)M->soff, M->sci, M->sva16,
                  false);
