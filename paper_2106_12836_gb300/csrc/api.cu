@@ -328,8 +328,17 @@ static sait_status apply_pair(sait_ctx ctx, sait_mat ML, sait_mat MU, const doub
                               void *w, const int *active) {
     const bool f64 = store_x64(ML->store) && store_x64(MU->store);
     ScopedTimer tm(ctx, SAIT_TIMER_APPLY);
-    SAIT_CK(launch_spmv(ML, ML->store, r, false, w, !f64, active, ctx->stream,
-                        group_counter(ctx, SAIT_TIMER_APPLY)));
+    if (!f64 && !store_x64(ML->store)) {
+        // FP32 products round every gathered entry of r to FP32: round r once
+        // into the second half of the n-double scratch and gather 4-byte values
+        float *r32 = (float *)w + ML->n;
+        SAIT_CK(launch_narrow(ML->n, r, r32, active, ctx->stream, ctx->num_sms));
+        SAIT_CK(launch_spmv(ML, ML->store, r32, true, w, true, active, ctx->stream,
+                            group_counter(ctx, SAIT_TIMER_APPLY), true));
+    } else {
+        SAIT_CK(launch_spmv(ML, ML->store, r, false, w, !f64, active, ctx->stream,
+                            group_counter(ctx, SAIT_TIMER_APPLY)));
+    }
     // M_U's product may start while M_L's drains (its SELL kernel waits for it first)
     SAIT_CK(launch_spmv(MU, MU->store, w, !f64, z, false, active, ctx->stream, nullptr, true));
     return SAIT_OK;

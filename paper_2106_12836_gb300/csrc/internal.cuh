@@ -387,6 +387,8 @@ int choose_lanes(int64_t n, int64_t nnz);
 // y = A x for the value storage of A; x/y element types given by flags.
 cudaError_t launch_spmv(const sait_mat_s *A, sait_dtype store, const void *x, bool x_f32, void *y,
                         bool y_f32, const int *active, cudaStream_t s, int *calls = nullptr, bool pdl = false);
+// y = fl32(x), rounded to nearest (the narrowing of the FP32 products' inputs)
+cudaError_t launch_narrow(int64_t n, const double *x, float *y, const int *active, cudaStream_t s, int num_sms);
 cudaError_t cast_values(const double *src, float *d32, __nv_bfloat16 *d16, int64_t nnz,
                         cudaStream_t s);
 

@@ -83,7 +83,24 @@ __global__ void k_cast(const double *__restrict__ src, float *d32, __nv_bfloat16
     }
 }
 
+// y = fl32(x) with round to nearest even (narrow_rn, integer operations), the
+// rounding the FP32 products otherwise apply to every gathered entry of x
+__global__ void k_narrow(int64_t n, const double *__restrict__ x, float *__restrict__ y,
+                         const int *__restrict__ active) {
+    pdl_wait();
+    pdl_trigger();
+    if (active && *active == 0) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = narrow_rn(x[i]);
+}
+
 }  // namespace
+
+cudaError_t launch_narrow(int64_t n, const double *x, float *y, const int *active, cudaStream_t s, int num_sms) {
+    if (n == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)std::min<int64_t>(cdiv(n, 256), (int64_t)num_sms * 8);
+    return launch_pdl(k_narrow, blocks, 256, 0, s, n, x, y, active);
+}
 
 int choose_lanes(int64_t n, int64_t nnz) {
     double avg = n > 0 ? (double)nnz / (double)n : 1.0;
