@@ -88,6 +88,17 @@ cudaError_t spmm_xy(const sait_mat_s *A, const TV *va, int k, int64_t ldx, int64
     return cudaGetLastError();
 }
 
+// Y = fl32(X), n x k row-major with leading dimensions ldx and k, rounded to
+// nearest (narrow_rn): the rounding the FP32 products otherwise apply to every
+// gathered entry of X
+__global__ void k_narrow_block(int64_t n, int k, int64_t ldx, const double *__restrict__ X, float *__restrict__ Y) {
+    const int64_t total = n * k;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / k;
+        Y[i] = narrow_rn(X[r * ldx + (i - r * k)]);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_spmm(const sait_mat_s *A, sait_dtype store, int k, int64_t ldx, int64_t ldy, const void *X,
@@ -127,8 +138,22 @@ sait_status apply_multi_impl(sait_ctx ctx, sait_mat ML, sait_mat MU, int k, cons
                              double *Z, int64_t ldz, void *W) {
     const bool f64 = store_x64(ML->store) && store_x64(MU->store);
     ScopedTimer tm(ctx, SAIT_TIMER_APPLY);
-    SAIT_CK(launch_spmm(ML, ML->store, k, ldr, k, R, false, W, !f64, ctx->stream,
-                        group_counter(ctx, SAIT_TIMER_APPLY)));
+    if (!f64 && !store_x64(ML->store)) {
+        // FP32 products round every gathered entry of R: round R once into the
+        // second half of the n x k-double scratch and gather 4-byte values
+        float *R32 = (float *)W + (size_t)ML->n * k;
+        if (ldr == k) {
+            SAIT_CK(launch_narrow((int64_t)ML->n * k, R, R32, nullptr, ctx->stream, ctx->num_sms));
+        } else {
+            const unsigned blocks = (unsigned)std::min<int64_t>(cdiv((int64_t)ML->n * k, 256), 8LL * ctx->num_sms);
+            launch_k(k_narrow_block, blocks, 256, 0, ctx->stream, ML->n, k, ldr, R, R32);
+        }
+        SAIT_CK(launch_spmm(ML, ML->store, k, k, k, R32, true, W, true, ctx->stream,
+                            group_counter(ctx, SAIT_TIMER_APPLY)));
+    } else {
+        SAIT_CK(launch_spmm(ML, ML->store, k, ldr, k, R, false, W, !f64, ctx->stream,
+                            group_counter(ctx, SAIT_TIMER_APPLY)));
+    }
     SAIT_CK(launch_spmm(MU, MU->store, k, k, ldz, W, !f64, Z, false, ctx->stream, nullptr));
     return SAIT_OK;
 }
