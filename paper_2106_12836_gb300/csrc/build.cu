@@ -523,21 +523,36 @@ k_spgemm_dense(int nrows, const int32_t *__restrict__ rows, int64_t n,
     }
 }
 
-// Gapped rows -> CSR.  One warp per row.
+// Gapped rows -> CSR.  kCompactG lanes per row (a SAIT row holds a few tens of
+// entries at most, so a warp per row left most lanes idle), each lane moving
+// two entries per round with both loads in flight.
+constexpr int kCompactG = 8;
 __global__ void k_compact(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ cnt,
                           const int32_t *__restrict__ ci, const double *__restrict__ va,
                           const int64_t *__restrict__ rp64, int32_t *__restrict__ rp,
                           int32_t *__restrict__ oci, double *__restrict__ ova) {
-    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kCompactG;
+    const int sub = threadIdx.x & (kCompactG - 1);
     if (w > n) return;
-    if (w == n) { if (lane == 0) rp[n] = (int32_t)rp64[n]; return; }
+    if (w == n) {
+        if (sub == 0) rp[n] = (int32_t)rp64[n];
+        return;
+    }
     const int64_t src = off[w], dst = rp64[w];
     const int c = cnt[w];
-    if (lane == 0) rp[w] = (int32_t)dst;
-    for (int t = lane; t < c; t += 32) {
-        oci[dst + t] = ci[src + t];
-        ova[dst + t] = va[src + t];
+    if (sub == 0) rp[w] = (int32_t)dst;
+    for (int t = sub; t < c; t += 2 * kCompactG) {
+        const bool two = t + kCompactG < c;
+        const int32_t c0 = ci[src + t];
+        const double v0 = va[src + t];
+        const int32_t c1 = two ? ci[src + t + kCompactG] : 0;
+        const double v1 = two ? va[src + t + kCompactG] : 0.0;
+        oci[dst + t] = c0;
+        ova[dst + t] = v0;
+        if (two) {
+            oci[dst + t + kCompactG] = c1;
+            ova[dst + t + kCompactG] = v1;
+        }
     }
 }
 
@@ -759,7 +774,7 @@ extern "C" sait_status sait_build(sait_ctx ctx, sait_mat T, sait_uplo uplo, int3
         if (nnzM >= (int64_t)INT_MAX)
             return ctx_fail(ctx, SAIT_ERR_UNSUPPORTED, "sait_build: nnz(M) >= 2^31");
         SAIT_TRY(mat_alloc(ctx, n, nnzM, &M));
-        launch_k(k_compact, (unsigned)cdiv((n + 1) * 32, 256), 256, 0, s, n, fin.off, fin.cnt, fin.ci, fin.va,
+        launch_k(k_compact, (unsigned)cdiv((n + 1) * kCompactG, 256), 256, 0, s, n, fin.off, fin.cnt, fin.ci, fin.va,
                                                                    rp64.p, M->rp, M->ci, M->va);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) { sait_mat_destroy(M); return ctx_cuda(ctx, e, "k_compact", __FILE__, __LINE__); }
