@@ -99,28 +99,30 @@ __global__ void k_rowub(int64_t n, const int32_t *__restrict__ tt_rp,
                         const int32_t *__restrict__ tt_ci, const int32_t *__restrict__ m_cnt,
                         int masked, const int32_t *__restrict__ s_cnt, int64_t *__restrict__ ub,
                         int *bin_count, int32_t *__restrict__ bin_rows) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int64_t u;
-    int bin;
-    if (masked) {
-        u = s_cnt ? s_cnt[i] : 1;
-        bin = u <= kWarpMaxUb ? 3 : 4;
-    } else {
-        u = 1;
-        for (int e = tt_rp[i]; e < tt_rp[i + 1]; e++) u += m_cnt[tt_ci[e]];
-        bin = u <= 8 ? 0 : u <= 16 ? 1 : u <= 32 ? 2 : u <= kWarpMaxUb ? 3 : 4;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ int s_n[kBins], s_base[kBins];
+    if (threadIdx.x < kBins) s_n[threadIdx.x] = 0;
+    __syncthreads();
+    int bin = -1, rank = 0;
+    if (i < n) {
+        int64_t u;
+        if (masked) {
+            u = s_cnt ? s_cnt[i] : 1;
+            bin = u <= kWarpMaxUb ? 3 : 4;
+        } else {
+            u = 1;
+            for (int e = tt_rp[i]; e < tt_rp[i + 1]; e++) u += m_cnt[tt_ci[e]];
+            bin = u <= 8 ? 0 : u <= 16 ? 1 : u <= 32 ? 2 : u <= kWarpMaxUb ? 3 : 4;
+        }
+        ub[i] = u;
+        rank = atomicAdd(&s_n[bin], 1);  // position within the block's share of the bin
     }
-    ub[i] = u;
-    // warp-aggregated append: one atomic per (warp, bin)
-    const unsigned act = __activemask();
-    const unsigned peers = __match_any_sync(act, bin);
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(bin_count + bin, __popc(peers));
-    base = __shfl_sync(peers, base, leader);
-    bin_rows[(int64_t)bin * n + base + __popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
+    __syncthreads();
+    // block-aggregated append: one global atomic per (block, bin); the counters
+    // are few, so per-warp atomics on them serialised
+    if (threadIdx.x < kBins) s_base[threadIdx.x] = s_n[threadIdx.x] ? atomicAdd(bin_count + threadIdx.x, s_n[threadIdx.x]) : 0;
+    __syncthreads();
+    if (bin >= 0) bin_rows[(int64_t)bin * n + s_base[bin] + rank] = (int32_t)i;
 }
 
 __device__ __forceinline__ int hslot(int32_t j, int logcap) {

@@ -138,27 +138,58 @@ __global__ void k_lu_counts(int64_t n, const int32_t *__restrict__ rp, const int
     uc[i] = u;
 }
 
+// kLuG lanes per row: each lane takes one entry per round, its position in L or
+// U is the count of the group's earlier L or U entries (a ballot), so the row's
+// order is kept and its loads are in flight together
+constexpr int kLuG = 8;
 __global__ void k_lu_fill(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                           const double *__restrict__ a, const int64_t *__restrict__ lrp64,
                           const int64_t *__restrict__ urp64, int32_t *lrp, int32_t *lci, double *lva,
                           int32_t *urp, int32_t *uci, double *uva) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i > n) return;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kLuG;
+    const int sub = threadIdx.x & (kLuG - 1);
+    const unsigned gmask = ((1u << kLuG) - 1u) << ((threadIdx.x & 31) & ~(kLuG - 1));
+    if (i > n) return;  // whole groups leave together
     if (i == n) {
-        lrp[n] = (int32_t)lrp64[n];
-        urp[n] = (int32_t)urp64[n];
+        if (sub == 0) {
+            lrp[n] = (int32_t)lrp64[n];
+            urp[n] = (int32_t)urp64[n];
+        }
         return;
     }
-    int64_t lo = lrp64[i], uo = urp64[i];
-    lrp[i] = (int32_t)lo;
-    urp[i] = (int32_t)uo;
-    for (int k = rp[i]; k < rp[i + 1]; k++) {
-        const int j = ci[k];
-        if (j < i) { lci[lo] = j; lva[lo] = a[k]; lo++; }
-        else { uci[uo] = j; uva[uo] = a[k]; uo++; }
+    const int64_t lo = lrp64[i], uo = urp64[i];
+    if (sub == 0) {
+        lrp[i] = (int32_t)lo;
+        urp[i] = (int32_t)uo;
     }
-    lci[lo] = (int32_t)i;
-    lva[lo] = 1.0;
+    const unsigned below = (1u << sub) - 1u;
+    const int shift = (threadIdx.x & 31) & ~(kLuG - 1);
+    int lc = 0, uc = 0;
+    for (int base = rp[i]; base < rp[i + 1]; base += kLuG) {
+        const int k = base + sub;
+        const bool valid = k < rp[i + 1];
+        const int j = valid ? ci[k] : 0;
+        const double v = valid ? a[k] : 0.0;
+        const bool isl = valid && j < i, isu = valid && j >= i;
+        const unsigned bl = (__ballot_sync(gmask, isl) >> shift) & ((1u << kLuG) - 1u);
+        const unsigned bu = (__ballot_sync(gmask, isu) >> shift) & ((1u << kLuG) - 1u);
+        if (isl) {
+            const int64_t d = lo + lc + __popc(bl & below);
+            lci[d] = j;
+            lva[d] = v;
+        }
+        if (isu) {
+            const int64_t d = uo + uc + __popc(bu & below);
+            uci[d] = j;
+            uva[d] = v;
+        }
+        lc += __popc(bl);
+        uc += __popc(bu);
+    }
+    if (sub == 0) {
+        lci[lo + lc] = (int32_t)i;
+        lva[lo + lc] = 1.0;
+    }
 }
 
 // ---- ILU(p), p = 0 or 1 -------------------------------------------------------------
@@ -626,7 +657,7 @@ extern "C" sait_status sait_iluk(sait_ctx ctx, const sait_csr *A, int32_t level,
     st = mat_alloc(ctx, n, h64[0], &Lm);
     if (st == SAIT_OK) st = mat_alloc(ctx, n, h64[1], &Um);
     if (st != SAIT_OK) goto done_;
-    launch_k(k_lu_fill, (unsigned)cdiv(n + 1, 256), 256, 0, s, n, prp, pci, (const double *)pva, lrp.p, urp.p,
+    launch_k(k_lu_fill, (unsigned)cdiv((n + 1) * kLuG, 256), 256, 0, s, n, prp, pci, (const double *)pva, lrp.p, urp.p,
              Lm->rp, Lm->ci, Lm->va, Um->rp, Um->ci, Um->va);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
