@@ -742,7 +742,19 @@ k_gemv_basis(int64_t n, const float *__restrict__ Vh, const unsigned short *__re
     __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
         float S = 0.0f, E = 0.0f;
-        for (int q = 0; q < nv; q++) {
+        int q = 0;
+        for (; q + 8 <= nv; q += 8) {  // eight vectors' loads in flight together, summed in order
+            float h[8];
+            unsigned short l[8];
+#pragma unroll
+            for (int t = 0; t < 8; t++) {
+                h[t] = __ldg(Vh + (int64_t)(q + t) * ldv + i);
+                l[t] = __ldg(Vm + (int64_t)(q + t) * ldv + i);
+            }
+#pragma unroll
+            for (int t = 0; t < 8; t++) df_term_t(S, E, h[t], lo16_unscaled(h[t], l[t]), yh[q + t], yl[q + t], ys[q + t]);
+        }
+        for (; q < nv; q++) {
             const float h = __ldg(Vh + (int64_t)q * ldv + i);
             df_term_t(S, E, h, lo16_unscaled(h, __ldg(Vm + (int64_t)q * ldv + i)), yh[q], yl[q], ys[q]);
         }
@@ -797,6 +809,37 @@ __global__ void __launch_bounds__(kThreads) k_hsolve(const double *H, const doub
         __syncthreads();
     }
     for (int k = threadIdx.x; k < jd; k += kThreads) y[k] = yv[k];
+}
+
+// The same back substitution for restart lengths up to kHsolveSmem, by one
+// warp: the triangle of R and g staged in shared memory with one parallel
+// load, the reciprocals of the diagonal formed in parallel, then a chain of
+// one multiply and one FMA per row with no block barrier (the kernel above
+// waits on a global load and a division at every row)
+constexpr int kHsolveSmem = 64;
+__global__ void __launch_bounds__(32) k_hsolve_warp(const double *H, const double *g, double *y, int m, Scal *sc) {
+    __shared__ double rs[kHsolveSmem * kHsolveSmem], rinv[kHsolveSmem], sv[kHsolveSmem];
+    const int jd = sc->jdone, lane = threadIdx.x;
+    for (int idx = lane; idx < jd * jd; idx += 32) {
+        const int c = idx / jd, r = idx - c * jd;
+        rs[idx] = r <= c ? H[(int64_t)c * (m + 1) + r] : 0.0;
+    }
+    bool zero = false;
+    for (int k = lane; k < jd; k += 32) {
+        sv[k] = g[k];
+        const double d = H[(int64_t)k * (m + 1) + k];
+        zero |= d == 0.0;
+        rinv[k] = d == 0.0 ? 0.0 : 1.0 / d;
+    }
+    if (__any_sync(0xffffffffu, zero) && lane == 0) sc->state = 2;
+    __syncwarp();
+    for (int i = jd - 1; i >= 0; i--) {
+        const double yi = sv[i] * rinv[i];
+        const double *ri = rs + i * jd;
+        for (int k = lane; k < i; k += 32) sv[k] = fma(-ri[k], yi, sv[k]);
+        if (lane == 0) y[i] = yi;
+        __syncwarp();
+    }
 }
 
 // ---- BiCGSTAB kernels ---------------------------------------------------------
@@ -1014,7 +1057,19 @@ cudaError_t dots(sait_ctx ctx, const Work &W, int64_t n, int nd, const double *x
     return cudaGetLastError();
 }
 
+__global__ void k_bsub(int64_t n, const double *__restrict__ b, double *r) {
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+        r[i] = b[i] - r[i];
+}
+
 cudaError_t residual(sait_ctx ctx, sait_mat A, const double *x, const double *b, double *r) {
+    if (A->n > 0 && !A->force_csr && sell_ready(A, SAIT_F64)) {  // the SELL product, then r = b - A x
+        cudaError_t e = launch_spmv(A, SAIT_F64, x, false, r, false, nullptr, ctx->stream);
+        if (e != cudaSuccess) return e;
+        launch_k(k_bsub, (unsigned)std::min<int64_t>(cdiv(A->n, kThreads), 8LL * ctx->num_sms), kThreads, 0,
+                 ctx->stream, A->n, b, r);
+        return cudaGetLastError();
+    }
     const int G = A->lanes;
     const unsigned grid = (unsigned)cdiv(A->n * G, kThreads);
     cudaStream_t s = ctx->stream;
@@ -1197,7 +1252,10 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
         iters += hs.jdone;
         cycles++;
         if (hs.state == 3) { result = SAIT_ERR_NONFINITE; break; }
-        launch_k(k_hsolve, 1, kThreads, 0, s, (const double *)R.p, (const double *)g.p, y.p, m, sc);
+        if (m <= kHsolveSmem)
+            launch_k(k_hsolve_warp, 1, 32, 0, s, (const double *)R.p, (const double *)g.p, y.p, m, sc);
+        else
+            launch_k(k_hsolve, 1, kThreads, 0, s, (const double *)R.p, (const double *)g.p, y.p, m, sc);
         launch_k(k_gemv_basis, egrid, kThreads, 0, s, n, (const float *)V32.p, (const unsigned short *)VM.p, ldv,
                  (const int *)&sc->jdone, (const double *)y.p, u.p);
         SAIT_CK(cudaGetLastError());
