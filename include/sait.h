@@ -149,6 +149,13 @@ const char *sait_ctx_last_error(sait_ctx ctx);
 /* Turn event timing of the launch groups of sait_timer on (1) or off (0).
  * Timing adds two event records per timed call; it is off by default. */
 sait_status sait_ctx_set_timing(sait_ctx ctx, int enable);
+/* Polls a device-side dependency wait makes before it gives up with
+ * SAIT_ERR_TIMEOUT (the waits of sait_ilut's rows on the rows they depend on).
+ * polls <= 0 restores the default (2^22 polls with a growing sleep between them,
+ * about a second).  A small limit makes a factorisation whose rows have to wait
+ * at all return SAIT_ERR_TIMEOUT; the context stays usable.  Affects later
+ * calls on this context only. */
+sait_status sait_ctx_set_wait_limit(sait_ctx ctx, int64_t polls);
 /* Read the launch count and timer totals accumulated since the last reset
  * (launches made by this host thread).  reset = 1 clears them afterwards.
  * Synchronizes. */

@@ -29,7 +29,7 @@ __all__ = [
     "sait_outer_on_pattern", "sait_bicgstab_batched", "sait_bicgstab_multi", "BatchInfo", "Stats",
     "TIMERS", "lib_path", "EXPORTS", "sait_lobpcg", "sait_pcg", "sait_prec_create_jacobi", "sait_ilut",
     "sait_mat_autotune", "sait_batch_autotune", "sait_ctx_set_batch_tile", "sait_tune_params",
-    "SOLVER", "ParamReport",
+    "sait_ctx_set_wait_limit", "SOLVER", "ParamReport",
 ]
 
 DROP = {"none": 0, "abs": 1, "rowrel": 2, "pattern": 3, "hybrid": 4}
@@ -46,6 +46,7 @@ EXPORTS = [
     "sait_apply_static", "sait_spmm", "sait_apply_multi", "sait_mat_transpose", "sait_outer_on_pattern",
     "sait_bicgstab_batched", "sait_bicgstab_multi", "sait_lobpcg", "sait_pcg", "sait_prec_create_jacobi", "sait_ilut",
     "sait_mat_autotune", "sait_batch_autotune", "sait_ctx_set_batch_tile", "sait_tune_params",
+    "sait_ctx_set_wait_limit",
 ]
 SOLVER = {"gmres": 0, "bicgstab": 1, "pcg": 2}
 PARAM_MAX = 16  # SAIT_PARAM_MAX in include/sait.h
@@ -166,6 +167,7 @@ def _L():
             "sait_gmres": [vp, vp, vp, vp, vp, i32, d, i32, C.POINTER(Info)],
             "sait_bicgstab": [vp, vp, vp, vp, vp, d, i32, C.POINTER(Info)],
             "sait_ctx_set_timing": [vp, C.c_int],
+            "sait_ctx_set_wait_limit": [vp, i64],
             "sait_ctx_stats": [vp, C.POINTER(Stats), C.c_int],
             "sait_apply_static": [vp, vp, vp, vp, vp],
             "sait_spmm": [vp, vp, i32, vp, i64, vp, i64],
@@ -322,6 +324,11 @@ def sait_ctx_destroy(ctx: Context):
 
 def sait_ctx_set_timing(ctx: Context, enable: bool):
     _check(ctx, _L().sait_ctx_set_timing(ctx.h, int(bool(enable))), "sait_ctx_set_timing")
+
+
+def sait_ctx_set_wait_limit(ctx: Context, polls: int = 0):
+    """Polls a device-side dependency wait makes before giving up (0: the default)."""
+    _check(ctx, _L().sait_ctx_set_wait_limit(ctx.h, int(polls)), "sait_ctx_set_wait_limit")
 
 
 def sait_ctx_stats(ctx: Context, reset: bool = False) -> Stats:

@@ -57,6 +57,12 @@ extern "C" sait_status sait_ctx_set_timing(sait_ctx ctx, int enable) {
     return SAIT_OK;
 }
 
+extern "C" sait_status sait_ctx_set_wait_limit(sait_ctx ctx, int64_t polls) {
+    if (!ctx) return SAIT_ERR_INVALID_ARG;
+    ctx->wait_limit = polls > 0 ? polls : 0;
+    return SAIT_OK;
+}
+
 extern "C" sait_status sait_ctx_stats(sait_ctx ctx, sait_stats *out, int reset) {
     if (!ctx || !out) return SAIT_ERR_INVALID_ARG;
     SAIT_CK(cudaStreamSynchronize(ctx->stream));

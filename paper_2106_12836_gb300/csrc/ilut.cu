@@ -9,7 +9,7 @@
 // atomic ticket, and a warp that reaches column k of its row waits for the flag
 // of row k.  Every row k < i was taken earlier by a running warp that itself
 // waits only on smaller rows, so the waits always end; each is still bounded
-// (kSpinLimit polls), after which the kernel records a timeout and all warps
+// (kSpinLimit polls, or the context's wait limit), after which the kernel records a timeout and all warps
 // leave.
 //
 // One warp holds its working row w in a shared-memory hash table (column ->
@@ -158,14 +158,14 @@ __device__ int keep_part(WarpSmem &S, int lane, int64_t i, int part, double tau_
 
 // Waits (lane 0 polls, bounded) until row k is published.  Returns false on a
 // timeout or when another warp reported an error.
-__device__ bool wait_row(const int *done, int64_t k, int *err, int lane) {
+__device__ bool wait_row(const int *done, int64_t k, int *err, int lane, long long limit) {
     int ok = 1;
     if (lane == 0) {
         long long polls = 0;
         unsigned ns = 32;
         while (ld_acquire(done + k) == 0) {
             if (ld_volatile(err) != 0) { ok = 0; break; }
-            if (++polls > kSpinLimit) {
+            if (++polls > limit) {
                 atomicOr(err, kErrTimeout);
                 ok = 0;
                 break;
@@ -181,7 +181,7 @@ __device__ bool wait_row(const int *done, int64_t k, int *err, int lane) {
 
 __global__ void __launch_bounds__(kWarps * 32)
 k_ilut(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ va,
-       double tau, int lfil, Slots out, unsigned long long *ticket, int *err) {
+       double tau, int lfil, Slots out, unsigned long long *ticket, int *err, long long limit) {
     __shared__ WarpSmem smem[kWarps];
     const int lane = threadIdx.x & 31;
     WarpSmem &S = smem[threadIdx.x >> 5];
@@ -235,7 +235,7 @@ k_ilut(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci
             const int slot = __shfl_sync(0xffffffffu, bslot, __ffs(who) - 1);
             double wk = S.vals[slot];
             if (wk == 0.0) continue;
-            if (!wait_row(out.done, k, err, lane)) return;
+            if (!wait_row(out.done, k, err, lane, limit)) return;
             wk = wk / __ldcg(out.udiag + k);
             __syncwarp();
             if (fabs(wk) < tau_i) {  // first dropping rule
@@ -360,7 +360,8 @@ extern "C" sait_status sait_ilut(sait_ctx ctx, const sait_csr *A, double tau, in
         if (e != cudaSuccess || per_sm < 1) per_sm = 1;
         const int64_t blocks = std::min<int64_t>((int64_t)per_sm * ctx->num_sms, cdiv(n, kWarps));
         launch_k(k_ilut, (unsigned)blocks, kWarps * 32, 0, s, n, (const int32_t *)W->rp, (const int32_t *)W->ci,
-                 (const double *)W->va, tau, (int)lfil, sl, ticket.p, err.p);
+                 (const double *)W->va, tau, (int)lfil, sl, ticket.p, err.p,
+                 (long long)(ctx->wait_limit > 0 ? ctx->wait_limit : kSpinLimit));
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(h, err.p, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);

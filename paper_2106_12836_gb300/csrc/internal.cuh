@@ -37,6 +37,7 @@ struct sait_ctx_s {
     int64_t host_calls[SAIT_TIMER_COUNT] = {};
     int64_t launch_base = 0;
     int64_t batch_tile = 2048;  // rows per tile of the batched solver's schedule (sait_batch_autotune)
+    int64_t wait_limit = 0;     // polls of a device-side dependency wait (0: the kernel's default)
 };
 
 // Kernel launches made by this host thread (graph kernel nodes included).

@@ -133,3 +133,22 @@ def test_ilut_feeds_sait(sg, ctx, oracle_lib):
         Mo = oracle_lib.sait(To, 3, "rowrel", 1e-3)
         assert np.array_equal(M.rp, Mo.rp) and np.array_equal(M.ci, Mo.ci)
         assert np.all(np.abs(M.va - Mo.va) <= 1e-12 * np.abs(Mo.va))
+
+
+def test_dependency_wait_limit_times_out_and_context_recovers(sg, ctx, oracle_lib):
+    """A one-poll limit on the rows' dependency waits: rows whose predecessors
+    are still being factored give up, the call returns SAIT_ERR_TIMEOUT (the
+    kernel ends, nothing traps or hangs), and the same context then factors the
+    matrix bit for bit like the oracle with the default limit."""
+    A = synth.varcoef3d(24, 1.0, 5)
+    sg.sait_ctx_set_wait_limit(ctx, 1)
+    try:
+        with pytest.raises(sg.SaitError) as ei:
+            gpu_ilut(sg, ctx, A, 1e-4, 10)
+        assert ei.value.status == 8  # SAIT_ERR_TIMEOUT
+    finally:
+        sg.sait_ctx_set_wait_limit(ctx, 0)
+    L, U = gpu_ilut(sg, ctx, A, 1e-4, 10)
+    Lo, Uo = oracle_lib.ilut(A, 1e-4, 10)
+    assert_same(L, Lo)
+    assert_same(U, Uo)
