@@ -285,6 +285,7 @@ extern "C" sait_status sait_mat_destroy(sait_mat M) {
     if (M->va32) cudaFree(M->va32);
     if (M->va16) cudaFree(M->va16);
     if (M->soff) cudaFree(M->soff);
+    if (M->sperm) cudaFree(M->sperm);
     if (M->sci) cudaFree(M->sci);
     if (M->sva64) cudaFree(M->sva64);
     if (M->sva32) cudaFree(M->sva32);

@@ -102,10 +102,11 @@ struct sait_mat_s {
     int lanes = 8;                  // lanes per row for CSR products
     bool pooled = false;            // arrays from the stream-ordered pool (see mat_array)
     // SELL-32 copy for products (built on demand; see sell.cu)
-    bool sell_rejected = false;     // padding above 20%: products stay on CSR
+    bool sell_rejected = false;     // padding above 20% even sorted: products stay on CSR
     bool force_csr = false;         // set by sait_mat_autotune when CSR products won
     int64_t nslices = 0, sell_nnz = 0;
     int64_t *soff = nullptr;
+    int32_t *sperm = nullptr;       // SELL-C-sigma: row held by slot position p (null: natural order)
     int32_t *sci = nullptr;
     double *sva64 = nullptr;
     float *sva32 = nullptr;

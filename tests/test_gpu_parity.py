@@ -282,6 +282,46 @@ def test_spmv_parity_ragged(sg, ctx, oracle_lib):
     assert np.all(np.abs(y - yo) <= 1e-12 * bound)
 
 
+def _sigma_case(n=8192, seed=17):
+    """Rows of 2 and 40 entries, 24 short then 8 long in every 32 rows: each
+    natural 32-row slice pads to 40 slots, while sorting 256-row windows by
+    length puts the long rows into slices of their own."""
+    rng = np.random.default_rng(seed)
+    lens = np.where(np.arange(n) % 32 < 24, 2, 40)
+    ci = np.concatenate([np.sort(rng.choice(n, size=k, replace=False)) for k in lens]).astype(np.int32)
+    rp = np.zeros(n + 1, np.int32)
+    rp[1:] = np.cumsum(lens)
+    return synth.CSR(n, rp, ci, rng.uniform(-1.0, 1.0, size=int(rp[-1])))
+
+
+def _sell_padding(lens, sigma):
+    """Padded slots / entries of SELL-32 after sorting windows of sigma rows by
+    length (longest first, stable); sigma = 1 keeps the natural order."""
+    n = len(lens)
+    order = np.arange(n)
+    if sigma > 1:
+        order = np.concatenate([w + np.argsort(-lens[w:w + sigma], kind="stable") for w in range(0, n, sigma)])
+    ls = lens[order]
+    return sum(32 * int(ls[s:s + 32].max()) for s in range(0, n, 32)) / int(lens.sum())
+
+
+def test_spmv_sigma_sorted_sell(sg, ctx, oracle_lib):
+    """A matrix too ragged for natural-order SELL-32 (3.5x padding) gets the
+    sorted-window layout (no padding) instead of CSR products; the product
+    writes each row back to its place."""
+    A = _sigma_case()
+    lens = np.diff(A.rp)
+    assert _sell_padding(lens, 1) > 1.2 and _sell_padding(lens, 256) <= 1.2
+    M = mat(sg, ctx, A)
+    x = synth.uniform(5, A.n)
+    y = sg.sait_spmv(ctx, M, dev(x)).cpu().numpy()
+    yo = oracle_lib.spmv(A, x)
+    bound = oracle_lib.spmv(synth.CSR(A.n, A.rp, A.ci, np.abs(A.va)), np.abs(x))
+    assert np.all(np.abs(y - yo) <= 1e-12 * bound)
+    rep = sg.sait_mat_autotune(ctx, M).as_dict()
+    assert any(c["format"] == "sell32" for c in rep["candidates"])
+
+
 def _banded(n, far, lower, seed):
     """Triangular rows with the diagonal, a neighbour and one entry at distance
     `far` (where it exists): the band is exactly `far` wide."""
