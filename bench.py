@@ -242,7 +242,8 @@ def batched_workloads(sg, ctx, torch, device, stream):
         bytes_it = batched_iter_bytes(A, nl, nu, store, 1, row_iters, it)
         res[store] = {"ms": round(ms, 3), "build_ms": round(b_ms, 3), "solve_ms": round(s_ms, 3),
                       "ms_per_iteration": round(s_ms / it, 4), "bytes_per_iteration": bytes_it,
-                      "gbs_per_iteration": round(bytes_it / (s_ms / it) / 1e6, 1), **info.as_dict()}
+                      "gbs_per_iteration": round(bytes_it / (s_ms / it) / 1e6, 1),
+                      "frac_per_iteration": round(bytes_it / (s_ms / it) / 1e6 / peaks()[0], 4), **info.as_dict()}
     out["independent_systems"] = {"nsys": len(systems), "n": A.n, "nnz": A.nnz,
                                   "sides": [int(sides.min()), int(sides.max())], "solver": "bicgstab",
                                   "m_terms": 3, "tol": TOL, **res}
@@ -282,7 +283,8 @@ def batched_workloads(sg, ctx, torch, device, stream):
         bytes_it = batched_iter_bytes(A, nl, nu, store, k, row_iters, it)
         res[store] = {"ms": round(ms, 3), "build_ms": round(b_ms, 3), "solve_ms": round(s_ms, 3),
                       "ms_per_iteration": round(s_ms / it, 4), "bytes_per_iteration": bytes_it,
-                      "gbs_per_iteration": round(bytes_it / (s_ms / it) / 1e6, 1), **info.as_dict()}
+                      "gbs_per_iteration": round(bytes_it / (s_ms / it) / 1e6, 1),
+                      "frac_per_iteration": round(bytes_it / (s_ms / it) / 1e6 / peaks()[0], 4), **info.as_dict()}
     out["many_rhs"] = {"n": A.n, "k": k, "solver": "bicgstab", "m_terms": 3, "tol": TOL, **res}
     del d
     torch.cuda.empty_cache()
@@ -811,9 +813,10 @@ def summarize_extras(d):
     if "batched" in d:
         b = d["batched"]
         for key, name in (("independent_systems", "batched_512"), ("many_rhs", "rhs_64")):
-            # per storage: [build ms, solve ms, max iterations, GB/s per iteration]
+            # per storage: [build ms, solve ms, max iterations, GB/s per iteration, fraction of peak]
             s[name] = {st: [round(b[key][st]["build_ms"], 1), round(b[key][st]["solve_ms"], 1),
-                            b[key][st]["max_iters"], round(b[key][st]["gbs_per_iteration"])]
+                            b[key][st]["max_iters"], round(b[key][st]["gbs_per_iteration"]),
+                            b[key][st]["frac_per_iteration"]]
                        for st in ("f64", "f32", "f32x64") if st in b[key]}
     if "adjoint" in d:
         s["adjoint_ms"] = d["adjoint"]["ms_forward_backward"]
