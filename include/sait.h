@@ -149,6 +149,11 @@ const char *sait_ctx_last_error(sait_ctx ctx);
 /* Turn event timing of the launch groups of sait_timer on (1) or off (0).
  * Timing adds two event records per timed call; it is off by default. */
 sait_status sait_ctx_set_timing(sait_ctx ctx, int enable);
+/* Restrict event timing to the groups whose bit (1 << sait_timer) is set in
+ * groups (all groups by default): the events between the timed groups cost
+ * launch overlap, so a caller that needs one group's time can leave the
+ * others untouched. */
+sait_status sait_ctx_set_timing_groups(sait_ctx ctx, uint32_t groups);
 /* Polls a device-side dependency wait makes before it gives up with
  * SAIT_ERR_TIMEOUT (the waits of sait_ilut's rows on the rows they depend on).
  * polls <= 0 restores the default (2^22 polls with a growing sleep between them,

@@ -29,7 +29,7 @@ __all__ = [
     "sait_outer_on_pattern", "sait_bicgstab_batched", "sait_bicgstab_multi", "BatchInfo", "Stats",
     "TIMERS", "lib_path", "EXPORTS", "sait_lobpcg", "sait_pcg", "sait_prec_create_jacobi", "sait_ilut",
     "sait_mat_autotune", "sait_batch_autotune", "sait_ctx_set_batch_tile", "sait_tune_params",
-    "sait_ctx_set_wait_limit", "SOLVER", "ParamReport",
+    "sait_ctx_set_wait_limit", "sait_ctx_set_timing_groups", "SOLVER", "ParamReport",
 ]
 
 DROP = {"none": 0, "abs": 1, "rowrel": 2, "pattern": 3, "hybrid": 4}
@@ -46,7 +46,7 @@ EXPORTS = [
     "sait_apply_static", "sait_spmm", "sait_apply_multi", "sait_mat_transpose", "sait_outer_on_pattern",
     "sait_bicgstab_batched", "sait_bicgstab_multi", "sait_lobpcg", "sait_pcg", "sait_prec_create_jacobi", "sait_ilut",
     "sait_mat_autotune", "sait_batch_autotune", "sait_ctx_set_batch_tile", "sait_tune_params",
-    "sait_ctx_set_wait_limit",
+    "sait_ctx_set_wait_limit", "sait_ctx_set_timing_groups",
 ]
 SOLVER = {"gmres": 0, "bicgstab": 1, "pcg": 2}
 PARAM_MAX = 16  # SAIT_PARAM_MAX in include/sait.h
@@ -168,6 +168,7 @@ def _L():
             "sait_bicgstab": [vp, vp, vp, vp, vp, d, i32, C.POINTER(Info)],
             "sait_ctx_set_timing": [vp, C.c_int],
             "sait_ctx_set_wait_limit": [vp, i64],
+            "sait_ctx_set_timing_groups": [vp, C.c_uint32],
             "sait_ctx_stats": [vp, C.POINTER(Stats), C.c_int],
             "sait_apply_static": [vp, vp, vp, vp, vp],
             "sait_spmm": [vp, vp, i32, vp, i64, vp, i64],
@@ -324,6 +325,12 @@ def sait_ctx_destroy(ctx: Context):
 
 def sait_ctx_set_timing(ctx: Context, enable: bool):
     _check(ctx, _L().sait_ctx_set_timing(ctx.h, int(bool(enable))), "sait_ctx_set_timing")
+
+
+def sait_ctx_set_timing_groups(ctx: Context, groups=None):
+    """Time only the named groups (names of TIMERS; None: all of them)."""
+    mask = 0xFFFFFFFF if groups is None else sum(1 << TIMERS.index(g) for g in groups)
+    _check(ctx, _L().sait_ctx_set_timing_groups(ctx.h, mask), "sait_ctx_set_timing_groups")
 
 
 def sait_ctx_set_wait_limit(ctx: Context, polls: int = 0):

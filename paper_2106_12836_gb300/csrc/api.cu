@@ -31,7 +31,7 @@ static cudaEvent_t get_event(sait_ctx ctx) {
 }
 
 ScopedTimer::ScopedTimer(sait_ctx c, int g) : ctx(c), group(g) {
-    if (!ctx || !ctx->timing) return;
+    if (!ctx || !ctx->timing || !(ctx->timing_groups >> g & 1u)) return;
     a = get_event(ctx);
     if (a) cudaEventRecord(a, ctx->stream);
 }
@@ -46,7 +46,7 @@ ScopedTimer::~ScopedTimer() {
 }
 
 int *group_counter(sait_ctx ctx, int group) {
-    return ctx && ctx->timing ? ctx->d_word + kCounterBase + group : nullptr;
+    return ctx && ctx->timing && (ctx->timing_groups >> group & 1u) ? ctx->d_word + kCounterBase + group : nullptr;
 }
 
 extern "C" sait_status sait_ctx_set_timing(sait_ctx ctx, int enable) {
@@ -54,6 +54,12 @@ extern "C" sait_status sait_ctx_set_timing(sait_ctx ctx, int enable) {
     if (enable && !ctx->timing)
         SAIT_CK(cudaMemsetAsync(ctx->d_word + kCounterBase, 0, SAIT_TIMER_COUNT * sizeof(int), ctx->stream));
     ctx->timing = enable != 0;
+    return SAIT_OK;
+}
+
+extern "C" sait_status sait_ctx_set_timing_groups(sait_ctx ctx, uint32_t groups) {
+    if (!ctx) return SAIT_ERR_INVALID_ARG;
+    ctx->timing_groups = groups;
     return SAIT_OK;
 }
 

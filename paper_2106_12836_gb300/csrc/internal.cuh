@@ -31,6 +31,7 @@ struct sait_ctx_s {
     int *d_word = nullptr;     // device scratch words (error flags, counters)
     void *h_pinned = nullptr;  // pinned host staging (4 KB)
     bool timing = false;
+    unsigned timing_groups = ~0u;  // groups timed while timing is on (bit per sait_timer)
     std::vector<TimerRec> pending;
     std::vector<cudaEvent_t> spare;
     double ms[SAIT_TIMER_COUNT] = {};
