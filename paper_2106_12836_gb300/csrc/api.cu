@@ -350,7 +350,7 @@ static sait_status apply_pair(sait_ctx ctx, sait_mat ML, sait_mat MU, const doub
                             group_counter(ctx, SAIT_TIMER_APPLY), true));
     } else {
         SAIT_CK(launch_spmv(ML, ML->store, r, false, w, !f64, active, ctx->stream,
-                            group_counter(ctx, SAIT_TIMER_APPLY)));
+                            group_counter(ctx, SAIT_TIMER_APPLY), true));
     }
     // M_U's product may start while M_L's drains (its SELL kernel waits for it first)
     SAIT_CK(launch_spmv(MU, MU->store, w, !f64, z, false, active, ctx->stream, nullptr, true));

@@ -1237,7 +1237,7 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
             {
                 ScopedTimer tm(ctx, SAIT_TIMER_SPMV);
                 SAIT_CK(launch_spmv(A, SAIT_F64, z.p, false, w, false, act, s,
-                                    group_counter(ctx, SAIT_TIMER_SPMV)));
+                                    group_counter(ctx, SAIT_TIMER_SPMV), true));
             }
             ortho(j, 0);
             SAIT_CK(cudaGetLastError());
