@@ -44,6 +44,7 @@ if ROOT not in sys.path:
 import synth  # noqa: E402
 
 METRIC = "time-to-1e-8 residual & SAIT-apply HBM GB/s (% peak) vs level-scheduled trisolve"
+APPLY_EVERY = 8  # the timed steps time one SAIT apply in APPLY_EVERY
 TOL = 1e-8
 RESTART = 50
 DROP, TAU = "rowrel", 1e-3
@@ -622,13 +623,13 @@ def run_ours(a):
     def flush_l2():
         flush.fill_(1)
 
-    # The timed steps record CUDA events around the SAIT applies only (the dominant
-    # kernel, whose roofline they give): events between kernels cost launch
-    # overlap.  The other groups' times come from as many further steps with every
-    # group timed.  The timers are on during the warm-up too, so their CUDA events
-    # already exist when the timed steps start.
+    # The timed steps record CUDA events around every APPLY_EVERY-th SAIT apply only
+    # (the dominant kernel, whose roofline they give): events between kernels cost
+    # launch overlap.  The other groups' times come from as many further steps with
+    # every call of every group timed.  The timers are on during the warm-up too, so
+    # their CUDA events already exist when the timed steps start.
     sg.sait_ctx_set_timing(ctx, True)
-    sg.sait_ctx_set_timing_groups(ctx, ["apply"])
+    sg.sait_ctx_set_timing_groups(ctx, ["apply"], APPLY_EVERY)
     for _ in range(max(a.warmup, 0)):
         res = sait_step(sg, ctx, P, P.dev, a.m, a.store)
         del res
@@ -651,7 +652,7 @@ def run_ours(a):
     clk = clocks.stop()
     stats = sg.sait_ctx_stats(ctx, reset=True).as_dict()
     # the same steps again with every group timed: the breakdown and the other rooflines
-    sg.sait_ctx_set_timing_groups(ctx, None)
+    sg.sait_ctx_set_timing_groups(ctx, None, 1)
     times_all = []
     for _ in range(a.steps):
         flush_l2()
@@ -672,14 +673,19 @@ def run_ours(a):
     relres = float(np.linalg.norm(P.b - P.A.to_scipy() @ xr) / np.linalg.norm(P.b))
 
     # ---- end to end through the C ABI from host (pinned) buffers
+    def e2e():
+        d = {k: v.to(device, non_blocking=True) for k, v in P.host.items()}
+        xx, _, _, keep = sait_step(sg, ctx, P, d, a.m, a.store)
+        return xx.to("cpu", non_blocking=True), keep, d
+
+    # one untimed pass first: the device copies of the inputs come from torch's
+    # caching allocator, whose first request for them maps new memory
+    flush_l2()
+    _ = time_region(torch, stream, e2e)
+    del _
     e2e_times = []
     for _ in range(min(a.steps, 3)):
         flush_l2()
-
-        def e2e():
-            d = {k: v.to(device, non_blocking=True) for k, v in P.host.items()}
-            xx, _, _, keep = sait_step(sg, ctx, P, d, a.m, a.store)
-            return xx.to("cpu", non_blocking=True), keep, d
         ms, _ = time_region(torch, stream, e2e)
         e2e_times.append(ms)
 
@@ -737,7 +743,7 @@ def run_ours(a):
         "solve": {"iters": iters, "cycles": infos[-1]["cycles"], "rel_resid_host_check": float(f"{relres:.4e}"),
                   "step_ms_min_max": [round(min(times), 3), round(max(times), 3)], **extra},
         "breakdown_ms_per_step": {g: round(v / a.steps, 3) for g, v in groups.items()},
-        "group_timing": {"timed_steps": "CUDA events around the SAIT applies only (roofline)",
+        "group_timing": {"timed_steps": f"CUDA events around every {APPLY_EVERY}th SAIT apply only (roofline)",
                          "breakdown_and_other_rooflines": f"{a.steps} further steps with every group timed, "
                                                           f"{statistics.mean(times_all):.3f} ms per step"},
     }

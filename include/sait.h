@@ -150,10 +150,12 @@ const char *sait_ctx_last_error(sait_ctx ctx);
  * Timing adds two event records per timed call; it is off by default. */
 sait_status sait_ctx_set_timing(sait_ctx ctx, int enable);
 /* Restrict event timing to the groups whose bit (1 << sait_timer) is set in
- * groups (all groups by default): the events between the timed groups cost
- * launch overlap, so a caller that needs one group's time can leave the
- * others untouched. */
-sait_status sait_ctx_set_timing_groups(sait_ctx ctx, uint32_t groups);
+ * groups (all groups by default), and within each of them to one call in
+ * every (every >= 1, else SAIT_ERR_INVALID_ARG): the events around a timed
+ * call cost the launch overlap of the kernels they separate, so a caller that
+ * needs one group's average can leave the other calls untouched.  Timer totals
+ * and call counts then cover the timed calls only. */
+sait_status sait_ctx_set_timing_groups(sait_ctx ctx, uint32_t groups, int32_t every);
 /* Polls a device-side dependency wait makes before it gives up with
  * SAIT_ERR_TIMEOUT (the waits of sait_ilut's rows on the rows they depend on).
  * polls <= 0 restores the default (2^22 polls with a growing sleep between them,

@@ -168,7 +168,7 @@ def _L():
             "sait_bicgstab": [vp, vp, vp, vp, vp, d, i32, C.POINTER(Info)],
             "sait_ctx_set_timing": [vp, C.c_int],
             "sait_ctx_set_wait_limit": [vp, i64],
-            "sait_ctx_set_timing_groups": [vp, C.c_uint32],
+            "sait_ctx_set_timing_groups": [vp, C.c_uint32, i32],
             "sait_ctx_stats": [vp, C.POINTER(Stats), C.c_int],
             "sait_apply_static": [vp, vp, vp, vp, vp],
             "sait_spmm": [vp, vp, i32, vp, i64, vp, i64],
@@ -327,10 +327,11 @@ def sait_ctx_set_timing(ctx: Context, enable: bool):
     _check(ctx, _L().sait_ctx_set_timing(ctx.h, int(bool(enable))), "sait_ctx_set_timing")
 
 
-def sait_ctx_set_timing_groups(ctx: Context, groups=None):
-    """Time only the named groups (names of TIMERS; None: all of them)."""
+def sait_ctx_set_timing_groups(ctx: Context, groups=None, every: int = 1):
+    """Time only the named groups (names of TIMERS; None: all of them), one call
+    in `every` of each."""
     mask = 0xFFFFFFFF if groups is None else sum(1 << TIMERS.index(g) for g in groups)
-    _check(ctx, _L().sait_ctx_set_timing_groups(ctx.h, mask), "sait_ctx_set_timing_groups")
+    _check(ctx, _L().sait_ctx_set_timing_groups(ctx.h, mask, int(every)), "sait_ctx_set_timing_groups")
 
 
 def sait_ctx_set_wait_limit(ctx: Context, polls: int = 0):

@@ -32,12 +32,16 @@ static cudaEvent_t get_event(sait_ctx ctx) {
 
 ScopedTimer::ScopedTimer(sait_ctx c, int g) : ctx(c), group(g) {
     if (!ctx || !ctx->timing || !(ctx->timing_groups >> g & 1u)) return;
+    if (ctx->group_seen[g]++ % ctx->timing_every != 0) return;  // one call in timing_every
     a = get_event(ctx);
-    if (a) cudaEventRecord(a, ctx->stream);
+    if (!a) return;
+    cudaEventRecord(a, ctx->stream);
+    ctx->group_live[g] = true;
 }
 
 ScopedTimer::~ScopedTimer() {
     if (!a) return;
+    ctx->group_live[group] = false;
     cudaEvent_t b = get_event(ctx);
     if (!b) { ctx->spare.push_back(a); return; }
     cudaEventRecord(b, ctx->stream);
@@ -46,7 +50,7 @@ ScopedTimer::~ScopedTimer() {
 }
 
 int *group_counter(sait_ctx ctx, int group) {
-    return ctx && ctx->timing && (ctx->timing_groups >> group & 1u) ? ctx->d_word + kCounterBase + group : nullptr;
+    return ctx && ctx->timing && ctx->group_live[group] ? ctx->d_word + kCounterBase + group : nullptr;
 }
 
 extern "C" sait_status sait_ctx_set_timing(sait_ctx ctx, int enable) {
@@ -57,9 +61,12 @@ extern "C" sait_status sait_ctx_set_timing(sait_ctx ctx, int enable) {
     return SAIT_OK;
 }
 
-extern "C" sait_status sait_ctx_set_timing_groups(sait_ctx ctx, uint32_t groups) {
+extern "C" sait_status sait_ctx_set_timing_groups(sait_ctx ctx, uint32_t groups, int32_t every) {
     if (!ctx) return SAIT_ERR_INVALID_ARG;
+    if (every < 1) return ctx_fail(ctx, SAIT_ERR_INVALID_ARG, "sait_ctx_set_timing_groups: every < 1");
     ctx->timing_groups = groups;
+    ctx->timing_every = every;
+    for (int g = 0; g < SAIT_TIMER_COUNT; g++) ctx->group_seen[g] = 0;
     return SAIT_OK;
 }
 

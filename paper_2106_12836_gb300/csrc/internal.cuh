@@ -32,6 +32,9 @@ struct sait_ctx_s {
     void *h_pinned = nullptr;  // pinned host staging (4 KB)
     bool timing = false;
     unsigned timing_groups = ~0u;  // groups timed while timing is on (bit per sait_timer)
+    int timing_every = 1;          // a timed group records one call in timing_every
+    int64_t group_seen[SAIT_TIMER_COUNT] = {};  // calls of each group since timing was set
+    bool group_live[SAIT_TIMER_COUNT] = {};     // the group's current call records events
     std::vector<TimerRec> pending;
     std::vector<cudaEvent_t> spare;
     double ms[SAIT_TIMER_COUNT] = {};
@@ -88,7 +91,7 @@ struct ScopedTimer {
     ScopedTimer(sait_ctx c, int g);
     ~ScopedTimer();
 };
-// device counter of a timer group, or null when timing is off
+// device counter of a timer group while its current call is timed, else null
 int *group_counter(sait_ctx ctx, int group);
 
 struct sait_mat_s {

@@ -1220,6 +1220,7 @@ extern "C" sait_status sait_gmres(sait_ctx ctx, sait_mat A, sait_prec P, const d
             double *wj = V.p + (size_t)j * ldv;
             const double2 *wn = (const double2 *)(close ? wj : V.p + (size_t)(j + 1) * ldv);
             ScopedTimer tm(ctx, SAIT_TIMER_ORTHO);
+            S.calls = group_counter(ctx, SAIT_TIMER_ORTHO);  // counted only while this call is timed
             // each kernel may be scheduled while its predecessor drains
             (void)launch_pdl(k_dcgs_dot, nb_dot, kDotThreads, dot_smem(j), s, n4, Vh4, ldv / 4, j,
                              (const float4 *)w32.p, wn, S, close);
