@@ -143,14 +143,54 @@ struct DcgsState {
     int m;
 };
 
-// The dual sweep of one warp.  The work is cut into units (tile, batch): a
-// tile is 32 float4 rows (128 rows), a batch up to 8 basis vectors, and each
-// warp takes an equal run of consecutive units (tile-major), so no warp waits
-// on a partly filled last tile.  u and w are loaded when the tile changes, the
-// batch's vector loads are in flight together; each batch's 16 dot products
-// over the tile are summed across the warp and added to the warp's shared
-// slots wacc[q] (V_q . U) and wacc[j + q] (V_q . W); wacc[2j] gets U . W from
-// the unit holding the tile's first batch.  No barrier inside the sweep.
+// One unit of the dual sweep: batch q0 .. q0 + 7 of the basis over one tile
+// (32 float4 rows) with that tile's u and w in registers.  The batch's 16 dot
+// products over the tile are summed across the warp and added to the warp's
+// shared slots wacc[q] (V_q . U) and wacc[j + q] (V_q . W).
+__device__ __forceinline__ void dual_unit(int64_t i, bool ok, int q0, int j, const float4 *__restrict__ V,
+                                          int64_t ldv4, const float4 &u, const float4 &w, float *wacc, int lane) {
+    float4 vv[kDCH];
+#pragma unroll
+    for (int t = 0; t < kDCH; t++)
+        vv[t] = ok && q0 + t < j ? __ldg(V + (int64_t)(q0 + t) * ldv4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float v[2 * kDCH];  // v[t] = V_{q0+t} . U, v[kDCH + t] = V_{q0+t} . W over this lane's 4 rows
+#pragma unroll
+    for (int t = 0; t < kDCH; t++) {
+        float a = vv[t].x * u.x;
+        a = fmaf(vv[t].y, u.y, a);
+        a = fmaf(vv[t].z, u.z, a);
+        v[t] = fmaf(vv[t].w, u.w, a);
+        float b = vv[t].x * w.x;
+        b = fmaf(vv[t].y, w.y, b);
+        b = fmaf(vv[t].z, w.z, b);
+        v[kDCH + t] = fmaf(vv[t].w, w.w, b);
+    }
+    // warp sum of the 16 values by recursive halving: at offset o a lane keeps
+    // the half of its values picked by its lane bit o and adds the partner's
+    // copy of that half (16 shuffles for 16 sums instead of 80); afterwards
+    // lanes 2i and 2i + 1 hold the sum of value i
+#pragma unroll
+    for (int h = kDCH, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = lane & o;
+#pragma unroll
+        for (int e = 0; e < h; e++) {
+            const float send = up ? v[e] : v[e + h];
+            const float keep = up ? v[e + h] : v[e];
+            v[e] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    const int vi = lane >> 1, tt = vi & (kDCH - 1);
+    if (!(lane & 1) && q0 + tt < j) wacc[(vi < kDCH ? 0 : j) + q0 + tt] += v[0];
+}
+
+// The dual sweep of one warp over tiles of 32 float4 rows (128 rows).  Warps
+// take whole tiles round robin for as many full rounds as there are, so the
+// GPU's warps read one contiguous front of rows of every vector at a time
+// (DRAM streams that far better than one run per warp scattered over the
+// columns) and load each tile's u and w once; the tiles left over are cut
+// into units (tile, batch of 8 vectors), also taken round robin, so no warp
+// holds more than one unit beyond another.  wacc[2j] gets U . W.
 __device__ __forceinline__ void dual_sweep_warp(int64_t n4, const float4 *__restrict__ V, int64_t ldv4, int j,
                                                 const float4 *__restrict__ U, const double2 *__restrict__ W,
                                                 float *wacc) {
@@ -158,68 +198,37 @@ __device__ __forceinline__ void dual_sweep_warp(int64_t n4, const float4 *__rest
     const int64_t gw = ((int64_t)blockIdx.x * kDotThreads + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * kDotThreads) >> 5;
     const int nbat = j > 0 ? (j + kDCH - 1) / kDCH : 1;
-    const int64_t units = (n4 + 31) / 32 * nbat;
-    const int64_t per = (units + nw - 1) / nw;
-    const int64_t ub = min(units, gw * per), ue = min(units, ub + per);
-    int64_t tile = ub / nbat;
-    int bat = (int)(ub - tile * nbat);
+    const int64_t ntiles = (n4 + 31) / 32, main_tiles = ntiles / nw * nw;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     float ad = 0.0f;
-    float4 u = make_float4(0.f, 0.f, 0.f, 0.f), w = u;
-    bool ok = false;
-    for (int64_t un = ub; un < ue; un++) {
-        const int64_t i = tile * 32 + lane;
-        if (un == ub || bat == 0) {  // a new tile
-            ok = i < n4;
-            u = ok ? U[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-            w = ok ? load_w4(W, i) : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (bat == 0) {
-                ad = fmaf(u.x, w.x, ad);
-                ad = fmaf(u.y, w.y, ad);
-                ad = fmaf(u.z, w.z, ad);
-                ad = fmaf(u.w, w.w, ad);
-            }
+    auto tile_uw = [&](int64_t tile, bool first, int64_t &i, bool &ok, float4 &u, float4 &w) {
+        i = tile * 32 + lane;
+        ok = i < n4;
+        u = ok ? U[i] : z4;
+        w = ok ? load_w4(W, i) : z4;
+        if (first) {
+            ad = fmaf(u.x, w.x, ad);
+            ad = fmaf(u.y, w.y, ad);
+            ad = fmaf(u.z, w.z, ad);
+            ad = fmaf(u.w, w.w, ad);
         }
-        const int q0 = bat * kDCH;
-        if (++bat == nbat) {
-            bat = 0;
-            tile++;
-        }
-        if (q0 >= j) continue;
-        {
-            float4 vv[kDCH];
-#pragma unroll
-            for (int t = 0; t < kDCH; t++)
-                vv[t] = ok && q0 + t < j ? __ldg(V + (int64_t)(q0 + t) * ldv4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-            float v[2 * kDCH];  // v[t] = V_{q0+t} . U, v[kDCH + t] = V_{q0+t} . W over this lane's 4 rows
-#pragma unroll
-            for (int t = 0; t < kDCH; t++) {
-                float a = vv[t].x * u.x;
-                a = fmaf(vv[t].y, u.y, a);
-                a = fmaf(vv[t].z, u.z, a);
-                v[t] = fmaf(vv[t].w, u.w, a);
-                float b = vv[t].x * w.x;
-                b = fmaf(vv[t].y, w.y, b);
-                b = fmaf(vv[t].z, w.z, b);
-                v[kDCH + t] = fmaf(vv[t].w, w.w, b);
-            }
-            // Warp sum of the 16 values by recursive halving: at offset o a lane
-            // keeps the half of its values picked by its lane bit o and adds the
-            // partner's copy of that half (16 shuffles for 16 sums instead of 80);
-            // afterwards lanes 2i and 2i + 1 hold the sum of value i.
-#pragma unroll
-            for (int h = kDCH, o = 16; h >= 1; h >>= 1, o >>= 1) {
-                const bool up = lane & o;
-#pragma unroll
-                for (int e = 0; e < h; e++) {
-                    const float send = up ? v[e] : v[e + h];
-                    const float keep = up ? v[e + h] : v[e];
-                    v[e] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-                }
-            }
-            v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-            const int vi = lane >> 1, t = vi & (kDCH - 1);
-            if (!(lane & 1) && q0 + t < j) wacc[(vi < kDCH ? 0 : j) + q0 + t] += v[0];
-        }
+    };
+    for (int64_t tile = gw; tile < main_tiles; tile += nw) {  // whole tiles
+        int64_t i;
+        bool ok;
+        float4 u, w;
+        tile_uw(tile, true, i, ok, u, w);
+        for (int q0 = 0; q0 < j; q0 += kDCH) dual_unit(i, ok, q0, j, V, ldv4, u, w, wacc, lane);
+    }
+    const int64_t units = (ntiles - main_tiles) * nbat;  // the rest as (tile, batch) units
+    for (int64_t un = gw; un < units; un += nw) {
+        const int64_t tile = main_tiles + un / nbat;
+        const int bat = (int)(un % nbat);
+        int64_t i;
+        bool ok;
+        float4 u, w;
+        tile_uw(tile, bat == 0, i, ok, u, w);
+        if (bat * kDCH < j) dual_unit(i, ok, bat * kDCH, j, V, ldv4, u, w, wacc, lane);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ad += __shfl_xor_sync(0xffffffffu, ad, o);
