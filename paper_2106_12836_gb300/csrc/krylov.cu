@@ -92,10 +92,11 @@ k_reduce(const double *__restrict__ partial, int nb, int stride, double *out, co
 
 // Precision on GB300: its FP64 pipe (1.2 TFLOP/s measured, against 63.5
 // TFLOP/s FP32) would bound FP64 Gram-Schmidt passes far below HBM speed, so
-// the basis is kept both as V (FP64, the vectors the products read) and as a
-// pair (V_hi, V_lo) of FP32 arrays carrying V to ~2^-46 (split_pair): the
-// dots run in FP32 on V_hi, the updates in double-float on (V_hi, V_lo) with
-// error-free two-sums, and only one FP64 operation per entry and step remains.
+// the final basis vectors are kept as (hi, m16) pairs: hi = the vector's top
+// 24 bits in FP32 and m16 = its next 16 bits (split_hi16), ~2^-39 relative in
+// six bytes; FP64 columns hold only the tentative vectors the products read.
+// The dots run in FP32 on hi, the updates in double-float on (hi, m16) with
+// error-free two-sums, and a few FP64 operations per entry and step remain.
 //
 // Layout: the kernels below work on n rounded up to a multiple of 4 rows with
 // zero padding, so they move 16-byte vectors (four rows per thread) and never
@@ -123,8 +124,8 @@ __device__ __forceinline__ float4 load_w4(const double2 *w, int64_t i4) {
 //   one sweep:  v_j and the next tentative w1' = A M v_j - V_{j+1} h_j.
 // Two sweeps over the basis per step instead of four; the Givens rotation of a
 // column is applied once it is final, so convergence is seen one step later.
-// Precision as in the two-pass kernels above: dots in FP32 on V_hi, updates in
-// double-float on (V_hi, V_lo).
+// Precision as above: dots in FP32 on the hi parts, updates in double-float on
+// the (hi, m16) pairs.
 constexpr int kDCH = 8;          // basis vectors per chunk of the dual dot sweep
 constexpr int kDotThreads = 1024; // dual dot sweep: one block of 1024 threads per SM
 constexpr int kUpdPre = 16;      // basis vectors an update thread prefetches before its wait
