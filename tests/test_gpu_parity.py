@@ -318,6 +318,12 @@ def test_spmv_sigma_sorted_sell(sg, ctx, oracle_lib):
     yo = oracle_lib.spmv(A, x)
     bound = oracle_lib.spmv(synth.CSR(A.n, A.rp, A.ci, np.abs(A.va)), np.abs(x))
     assert np.all(np.abs(y - yo) <= 1e-12 * bound)
+    # FP32 values with FP64-accurate sums through the same permuted slices: the
+    # rounded matrix, to FP64 tolerance
+    sg.sait_mat_set_store(ctx, M, "f32x64")
+    y32 = sg.sait_spmv(ctx, M, dev(x)).cpu().numpy()
+    Ar = synth.CSR(A.n, A.rp, A.ci, A.va.astype(np.float32).astype(np.float64))
+    assert np.all(np.abs(y32 - oracle_lib.spmv(Ar, x)) <= 1e-12 * bound)
     rep = sg.sait_mat_autotune(ctx, M).as_dict()
     assert any(c["format"] == "sell32" for c in rep["candidates"])
 
