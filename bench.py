@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", choices=["bicgstab", "pcg", "trisolve", "batched", "rhs", "eigen", "adjoint"],
                     help="run one extra workload once at --grid (for profiling) and print its record")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="with --case: replay the batched solvers' iteration graph from the host instead of "
+                         "looping inside a conditional graph node (kernel profilers skip the kernels of graphs "
+                         "with conditional nodes)")
     ap.add_argument("--summarize-launches", metavar="CSV",
                     help="print the per-kernel table of an ncu launch list (--metrics gpu__time_duration.sum --csv)")
     return ap.parse_args()
@@ -241,10 +245,13 @@ def batched_workloads(sg, ctx, torch, device, stream):
         del keep
         it = max(info.graph_replays, 1)
         bytes_it = batched_iter_bytes(A, nl, nu, store, 1, row_iters, it)
+        bnd = batched_iter_bound(A, nl, nu, store, 1, row_iters, it)
         res[store] = {"ms": round(ms, 3), "build_ms": round(b_ms, 3), "solve_ms": round(s_ms, 3),
                       "ms_per_iteration": round(s_ms / it, 4), "bytes_per_iteration": bytes_it,
                       "gbs_per_iteration": round(bytes_it / (s_ms / it) / 1e6, 1),
-                      "frac_per_iteration": round(bytes_it / (s_ms / it) / 1e6 / peaks()[0], 4), **info.as_dict()}
+                      "frac_per_iteration": round(bytes_it / (s_ms / it) / 1e6 / peaks()[0], 4),
+                      "bound_ms_per_iteration": round(bnd["bound_ms"], 4),
+                      "frac_of_bound": round(bnd["bound_ms"] / (s_ms / it), 4), **info.as_dict()}
     out["independent_systems"] = {"nsys": len(systems), "n": A.n, "nnz": A.nnz,
                                   "sides": [int(sides.min()), int(sides.max())], "solver": "bicgstab",
                                   "m_terms": 3, "tol": TOL, **res}
@@ -282,10 +289,13 @@ def batched_workloads(sg, ctx, torch, device, stream):
         del keep
         it = max(info.graph_replays, 1)
         bytes_it = batched_iter_bytes(A, nl, nu, store, k, row_iters, it)
+        bnd = batched_iter_bound(A, nl, nu, store, k, row_iters, it)
         res[store] = {"ms": round(ms, 3), "build_ms": round(b_ms, 3), "solve_ms": round(s_ms, 3),
                       "ms_per_iteration": round(s_ms / it, 4), "bytes_per_iteration": bytes_it,
                       "gbs_per_iteration": round(bytes_it / (s_ms / it) / 1e6, 1),
-                      "frac_per_iteration": round(bytes_it / (s_ms / it) / 1e6 / peaks()[0], 4), **info.as_dict()}
+                      "frac_per_iteration": round(bytes_it / (s_ms / it) / 1e6 / peaks()[0], 4),
+                      "bound_ms_per_iteration": round(bnd["bound_ms"], 4),
+                      "frac_of_bound": round(bnd["bound_ms"] / (s_ms / it), 4), **info.as_dict()}
     out["many_rhs"] = {"n": A.n, "k": k, "solver": "bicgstab", "m_terms": 3, "tol": TOL, **res}
     del d
     torch.cuda.empty_cache()
@@ -494,6 +504,44 @@ def batched_iter_bytes(A, nnz_ml, nnz_mu, store, k, row_iters=None, replays=1):
     spmv_b = A.nnz * 12 + 4 * (n + 1) + 16 * n * k
     vec_rows = n * k if row_iters is None else row_iters / replays
     return int(2 * apply_b + 2 * spmv_b + 22 * 8 * vec_rows)
+
+
+# FP64 fused multiply-adds per SM per clock on GB300 (152 SMs, 2070 MHz maximum
+# clock: 1.26 TFLOP/s, the nominal FP64 rate); the 64^3 x 64 block product with
+# A ran 115.9 M FMAs in 203.7 us at 92.3% FP64-pipe busy (ncu), 1.96 per SM clock.
+FP64_FMA_PER_SM_CLK = 2
+SM_COUNT, SM_MAX_MHZ = 152, 2070
+
+
+def fp64_fma_rate():
+    """FP64 multiply-adds per second at the maximum SM clock."""
+    return FP64_FMA_PER_SM_CLK * SM_COUNT * SM_MAX_MHZ * 1e6
+
+
+def batched_iter_bound(A, nnz_ml, nnz_mu, store, k, row_iters=None, replays=1):
+    """Lower bound (ms) on one batched BiCGSTAB iteration: each part of the
+    iteration takes at least the longer of its algorithmic bytes at the
+    measured copy bandwidth and its FP64 multiply-adds at the FP64 rate.  With
+    k columns every matrix entry feeds k FP64 multiply-adds, so for k = 64 the
+    products of A (and, in the FP64-arithmetic storage modes, the two SAIT
+    products) are bound by the FP64 pipe, not by HBM.  The FP32 storage mode
+    multiplies in FP32, whose rate is 64 times the FP64 one.  The vector passes
+    do 12 FP64 multiply-adds per iterating row and column (6 dot terms, 6 in the
+    updates) against 176 bytes."""
+    n = A.n
+    bw = peaks()[0] * 1e6       # bytes per ms
+    fma = fp64_fma_rate() / 1e3  # per ms
+    sv = {"f64": 8, "f32": 4, "bf16": 2, "f32x64": 4, "bf16x64": 2}[store]
+    vec = 32 if store in ("f64", "f32x64", "bf16x64") else 24
+    apply_b = (nnz_ml + nnz_mu) * (sv + 4) + 2 * 4 * (n + 1) + vec * n * k
+    apply_f = (nnz_ml + nnz_mu) * k if store in ("f64", "f32x64", "bf16x64") else 0
+    spmv_b = A.nnz * 12 + 4 * (n + 1) + 16 * n * k
+    spmv_f = A.nnz * k
+    vec_rows = n * k if row_iters is None else row_iters / replays
+    parts = [(apply_b, apply_f)] * 2 + [(spmv_b, spmv_f)] * 2 + [(22 * 8 * vec_rows, 12 * vec_rows)]
+    return {"bound_ms": sum(max(b / bw, f / fma) for b, f in parts),
+            "fp64_fma": int(sum(f for _, f in parts)),
+            "fp64_bound_parts": sum(1 for b, f in parts if f / fma > b / bw)}
 
 
 def apply_bytes(n, nnz_l, nnz_u, store):
@@ -836,10 +884,11 @@ def summarize_extras(d):
     if "batched" in d:
         b = d["batched"]
         for key, name in (("independent_systems", "batched_512"), ("many_rhs", "rhs_64")):
-            # per storage: [build ms, solve ms, max iterations, GB/s per iteration, fraction of peak]
+            # per storage: [build ms, solve ms, max iterations, GB/s per iteration, fraction of
+            # the HBM peak, fraction of the HBM + FP64 bound]
             s[name] = {st: [round(b[key][st]["build_ms"], 1), round(b[key][st]["solve_ms"], 1),
                             b[key][st]["max_iters"], round(b[key][st]["gbs_per_iteration"]),
-                            b[key][st]["frac_per_iteration"]]
+                            b[key][st]["frac_per_iteration"], b[key][st]["frac_of_bound"]]
                        for st in ("f64", "f32", "f32x64") if st in b[key]}
     if "adjoint" in d:
         s["adjoint_ms"] = d["adjoint"]["ms_forward_backward"]
@@ -876,6 +925,8 @@ def run_case(a):
     device = torch.device("cuda", 0)
     ctx = sg.Context()
     stream = ctx.stream
+    if a.host_loop:
+        sg.sait_ctx_set_device_loop(ctx, False)
     g = a.grid
     if a.case in ("bicgstab", "trisolve"):
         P = Problem(g, device)

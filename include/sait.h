@@ -163,6 +163,15 @@ sait_status sait_ctx_set_timing_groups(sait_ctx ctx, uint32_t groups, int32_t ev
  * at all return SAIT_ERR_TIMEOUT; the context stays usable.  Affects later
  * calls on this context only. */
 sait_status sait_ctx_set_wait_limit(sait_ctx ctx, int64_t polls);
+/* on != 0 (the default): sait_bicgstab_batched and sait_bicgstab_multi run
+ * their iterations inside a WHILE conditional graph node, one graph launch per
+ * restart round.  on = 0: the same 8-iteration graph is replayed from the host,
+ * with a status read after each replay -- the path taken anyway where
+ * conditional nodes are unavailable, and the one a kernel profiler can look
+ * into (profilers skip the kernels of graphs with conditional nodes).  Both
+ * run the same kernels in the same order, so the results are identical.
+ * Affects later calls on this context only. */
+sait_status sait_ctx_set_device_loop(sait_ctx ctx, int32_t on);
 /* Read the launch count and timer totals accumulated since the last reset
  * (launches made by this host thread).  reset = 1 clears them afterwards.
  * Synchronizes. */
@@ -349,8 +358,12 @@ typedef struct {
     int32_t nsys;           /* systems (or right-hand sides) */
     int32_t converged;      /* with true relative residual <= tol */
     int32_t max_iters;      /* largest per-system iteration count */
-    int32_t graph_replays;  /* CUDA-graph replays of one iteration */
+    int32_t graph_replays;  /* iterations run from the captured graph (a multiple of 8) */
     double max_rel_resid;   /* largest true ||b_s - A_s x_s|| / ||b_s|| */
+    int32_t device_loop;    /* 1: the iterations looped on the device inside a WHILE
+                               conditional graph node; 0: the 8-iteration graph was
+                               replayed from the host (conditional nodes unavailable) */
+    int32_t graph_launches; /* launches of an executable graph by the host */
 } sait_batch_info;
 
 /* BiCGSTAB on many independent systems at once.  A is block diagonal: system
@@ -359,9 +372,14 @@ typedef struct {
  * outside its block.  P: a SAIT pair built from A's ILU(0) factors (block
  * diagonal as well) or NULL.  Every system has its own scalars, stopping test
  * (true relative residual <= tol) and iteration count (<= maxit); converged
- * systems stop changing.  One iteration is captured in a CUDA graph and
- * replayed.  rel_resid (device, nsys doubles) and iters (device, nsys ints)
- * receive per-system results when not NULL.  Synchronizes. */
+ * systems stop changing.  Eight iterations and the count of the systems still
+ * active are captured once as the body of a WHILE conditional graph node, so
+ * one graph launch runs the iterations on the device until every system has
+ * stopped or maxit iterations (rounded up to a multiple of 8) have run; a
+ * restart from the true residual (a system whose recurrence residual met tol
+ * but whose true residual did not) starts another launch.  rel_resid (device,
+ * nsys doubles) and iters (device, nsys ints) receive per-system results when
+ * not NULL.  Synchronizes. */
 sait_status sait_bicgstab_batched(sait_ctx ctx, sait_mat A, sait_prec P, int32_t nsys, const int64_t *sys_ptr,
                                   const double *b, double *x, double tol, int32_t maxit, sait_batch_info *info,
                                   double *rel_resid, int32_t *iters);

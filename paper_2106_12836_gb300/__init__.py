@@ -29,7 +29,7 @@ __all__ = [
     "sait_outer_on_pattern", "sait_bicgstab_batched", "sait_bicgstab_multi", "BatchInfo", "Stats",
     "TIMERS", "lib_path", "EXPORTS", "sait_lobpcg", "sait_pcg", "sait_prec_create_jacobi", "sait_ilut",
     "sait_mat_autotune", "sait_batch_autotune", "sait_ctx_set_batch_tile", "sait_tune_params",
-    "sait_ctx_set_wait_limit", "sait_ctx_set_timing_groups", "SOLVER", "ParamReport",
+    "sait_ctx_set_wait_limit", "sait_ctx_set_timing_groups", "sait_ctx_set_device_loop", "SOLVER", "ParamReport",
 ]
 
 DROP = {"none": 0, "abs": 1, "rowrel": 2, "pattern": 3, "hybrid": 4}
@@ -46,7 +46,7 @@ EXPORTS = [
     "sait_apply_static", "sait_spmm", "sait_apply_multi", "sait_mat_transpose", "sait_outer_on_pattern",
     "sait_bicgstab_batched", "sait_bicgstab_multi", "sait_lobpcg", "sait_pcg", "sait_prec_create_jacobi", "sait_ilut",
     "sait_mat_autotune", "sait_batch_autotune", "sait_ctx_set_batch_tile", "sait_tune_params",
-    "sait_ctx_set_wait_limit", "sait_ctx_set_timing_groups",
+    "sait_ctx_set_wait_limit", "sait_ctx_set_timing_groups", "sait_ctx_set_device_loop",
 ]
 SOLVER = {"gmres": 0, "bicgstab": 1, "pcg": 2}
 PARAM_MAX = 16  # SAIT_PARAM_MAX in include/sait.h
@@ -74,7 +74,8 @@ class Stats(C.Structure):
 
 class BatchInfo(C.Structure):
     _fields_ = [("nsys", C.c_int32), ("converged", C.c_int32), ("max_iters", C.c_int32),
-                ("graph_replays", C.c_int32), ("max_rel_resid", C.c_double)]
+                ("graph_replays", C.c_int32), ("max_rel_resid", C.c_double), ("device_loop", C.c_int32),
+                ("graph_launches", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -168,6 +169,7 @@ def _L():
             "sait_bicgstab": [vp, vp, vp, vp, vp, d, i32, C.POINTER(Info)],
             "sait_ctx_set_timing": [vp, C.c_int],
             "sait_ctx_set_wait_limit": [vp, i64],
+            "sait_ctx_set_device_loop": [vp, i32],
             "sait_ctx_set_timing_groups": [vp, C.c_uint32, i32],
             "sait_ctx_stats": [vp, C.POINTER(Stats), C.c_int],
             "sait_apply_static": [vp, vp, vp, vp, vp],
@@ -337,6 +339,12 @@ def sait_ctx_set_timing_groups(ctx: Context, groups=None, every: int = 1):
 def sait_ctx_set_wait_limit(ctx: Context, polls: int = 0):
     """Polls a device-side dependency wait makes before giving up (0: the default)."""
     _check(ctx, _L().sait_ctx_set_wait_limit(ctx.h, int(polls)), "sait_ctx_set_wait_limit")
+
+
+def sait_ctx_set_device_loop(ctx: Context, on: bool = True):
+    """Batched solvers: iterate inside a WHILE graph node (True) or replay the
+    iteration graph from the host (False; what kernel profilers can see)."""
+    _check(ctx, _L().sait_ctx_set_device_loop(ctx.h, int(bool(on))), "sait_ctx_set_device_loop")
 
 
 def sait_ctx_stats(ctx: Context, reset: bool = False) -> Stats:

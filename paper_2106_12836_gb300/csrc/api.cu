@@ -76,6 +76,12 @@ extern "C" sait_status sait_ctx_set_wait_limit(sait_ctx ctx, int64_t polls) {
     return SAIT_OK;
 }
 
+extern "C" sait_status sait_ctx_set_device_loop(sait_ctx ctx, int32_t on) {
+    if (!ctx) return SAIT_ERR_INVALID_ARG;
+    ctx->device_loop = on ? 1 : 0;
+    return SAIT_OK;
+}
+
 extern "C" sait_status sait_ctx_stats(sait_ctx ctx, sait_stats *out, int reset) {
     if (!ctx || !out) return SAIT_ERR_INVALID_ARG;
     SAIT_CK(cudaStreamSynchronize(ctx->stream));

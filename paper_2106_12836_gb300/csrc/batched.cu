@@ -13,8 +13,11 @@
 //     so every matrix entry is read once per iteration for all k columns.
 //
 // kPollB iterations of either solver, with the count of the systems still
-// active, are captured once in a CUDA graph; the graph is replayed until the
-// count (read after each replay) is zero.
+// active, are captured once as the body of a WHILE conditional graph node:
+// one graph launch per restart round runs the iterations on the device until
+// the count is zero (or the iteration limit is reached).  Where conditional
+// nodes are unavailable the body is captured as a plain graph and replayed
+// from the host until the count, read after each replay, is zero.
 #include <algorithm>
 #include <cmath>
 
@@ -292,7 +295,28 @@ k_mc_dots(int64_t n, int k, int nd, const int *__restrict__ active, const double
     double s0 = 0.0, s1 = 0.0;
     const bool on = (int)threadIdx.x < rows_per_pass * k && (!active || active[c]);
     if (on) {
-        for (int64_t i = (int64_t)blockIdx.x * rows_per_pass + r0; i < n; i += (int64_t)gridDim.x * rows_per_pass) {
+        // four rows per trip, all loads issued before the multiply-adds
+        const int64_t step = (int64_t)gridDim.x * rows_per_pass;
+        int64_t i = (int64_t)blockIdx.x * rows_per_pass + r0;
+        for (; i + 3 * step < n; i += 4 * step) {
+            double a[4], b[4], u[4], v[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int64_t e = (i + q * step) * k + c;
+                a[q] = x0[e];
+                b[q] = y0[e];
+                if (nd > 1) {
+                    u[q] = x1[e];
+                    v[q] = y1[e];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                s0 = fma(a[q], b[q], s0);
+                if (nd > 1) s1 = fma(u[q], v[q], s1);
+            }
+        }
+        for (; i < n; i += step) {
             const int64_t e = i * k + c;
             s0 = fma(x0[e], y0[e], s0);
             if (nd > 1) s1 = fma(x1[e], y1[e], s1);
@@ -415,6 +439,97 @@ sait_status capture(sait_ctx ctx, cudaStream_t cs, F body, cudaGraphExec_t *exec
     return SAIT_OK;
 }
 
+// Ends one pass of the loop body: counts the pass and lets the loop go on
+// while some system is active and fewer than max_bodies passes have run, so
+// the device loop ends after at most max_bodies passes whatever the flags say.
+__global__ void k_b_continue(cudaGraphConditionalHandle h, const int *__restrict__ count, int *bodies,
+                             int max_bodies) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const int b = *bodies + 1;
+        *bodies = b;
+        cudaGraphSetConditional(h, (*count > 0 && b < max_bodies) ? 1u : 0u);
+    }
+}
+
+// The same body (kPollB iterations and the count of active systems) as the
+// inside of a WHILE conditional node, followed by k_b_continue: one launch of
+// the executable graph runs the iterations on the device until the systems
+// stop or max_bodies passes have run, with no host round trip per pass.  Any
+// failure (no conditional nodes) leaves *exec null so that the caller falls
+// back to replaying the body graph from the host.
+template <class F>
+sait_status capture_loop(sait_ctx ctx, cudaStream_t cs, F body, const int *count, int *bodies, int max_bodies,
+                         cudaGraphExec_t *exec, int64_t *kernels) {
+    *exec = nullptr;
+    const bool timing = ctx->timing;
+    ctx->timing = false;
+    const int64_t l0 = g_sait_launches;
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle h = 0;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {};
+    cudaGraphNode_t node = nullptr;
+    if (e == cudaSuccess) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    }
+    sait_status st = SAIT_OK;
+    if (e == cudaSuccess) {
+        cudaGraph_t inner = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(cs, inner, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            st = body(cs);
+            launch_k(k_b_continue, 1, 32, 0, cs, h, count, bodies, max_bodies);
+            cudaError_t e2 = cudaStreamEndCapture(cs, &inner);
+            if (e == cudaSuccess) e = e2;
+        }
+    }
+    ctx->timing = timing;
+    *kernels = g_sait_launches - l0;
+    g_sait_launches = l0;
+    if (e == cudaSuccess && st == SAIT_OK) e = cudaGraphInstantiate(exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (st != SAIT_OK) return st;
+    if (e != cudaSuccess) {
+        *exec = nullptr;
+        cudaGetLastError();  // fall back to host replays
+    }
+    return SAIT_OK;
+}
+
+// Runs the iterations of one restart round: the device loop when there is
+// one, else the body graph replayed from the host with a status read after
+// each replay.  *iterations grows by kPollB per pass of the body.
+sait_status run_iterations(sait_ctx ctx, cudaStream_t cs, cudaGraphExec_t loop, cudaGraphExec_t poll,
+                           int64_t loop_kernels, int64_t poll_kernels, int maxit, int *count, int *bodies,
+                           int *h, int *iterations, int *launches) {
+    if (maxit <= 0) return SAIT_OK;
+    if (loop) {
+        SAIT_CK(cudaMemsetAsync(bodies, 0, sizeof(int), cs));
+        SAIT_CK(cudaGraphLaunch(loop, cs));
+        ++*launches;
+        SAIT_CK(cudaMemcpyAsync(h, bodies, sizeof(int), cudaMemcpyDeviceToHost, cs));
+        SAIT_CK(cudaStreamSynchronize(cs));
+        g_sait_launches += loop_kernels * h[0];
+        *iterations += kPollB * h[0];
+        return SAIT_OK;
+    }
+    for (int it = 0; it < maxit; it += kPollB) {
+        SAIT_CK(cudaGraphLaunch(poll, cs));
+        ++*launches;
+        g_sait_launches += poll_kernels;
+        SAIT_CK(cudaMemcpyAsync(h, count, sizeof(int), cudaMemcpyDeviceToHost, cs));
+        SAIT_CK(cudaStreamSynchronize(cs));
+        *iterations += kPollB;
+        if (h[0] == 0) break;
+    }
+    return SAIT_OK;
+}
+
 sait_status sync_streams(sait_ctx ctx, cudaStream_t from, cudaStream_t to, cudaEvent_t ev) {
     SAIT_CK(cudaEventRecord(ev, from));
     SAIT_CK(cudaStreamWaitEvent(to, ev, 0));
@@ -440,10 +555,11 @@ extern "C" sait_status sait_bicgstab_batched(sait_ctx ctx, sait_mat A, sait_prec
     struct Cleanup {
         cudaStream_t cs;
         cudaEvent_t ev;
-        cudaGraphExec_t g = nullptr;
+        cudaGraphExec_t g = nullptr, loop = nullptr;
         ~Cleanup() {
             cudaStreamSynchronize(cs);
             if (g) cudaGraphExecDestroy(g);
+            if (loop) cudaGraphExecDestroy(loop);
             cudaEventDestroy(ev);
             cudaStreamDestroy(cs);
         }
@@ -555,20 +671,20 @@ extern "C" sait_status sait_bicgstab_batched(sait_ctx ctx, sait_mat A, sait_prec
         SAIT_CK(cudaGetLastError());
         return SAIT_OK;
     };
-    SAIT_TRY(capture(ctx, cs, poll_block, &cleanup.g, &graph_kernels));
+    DTemp<int> bodies;
+    SAIT_CK(bodies.alloc(1, s0));
+    int64_t loop_kernels = 0;
+    if (ctx->device_loop)
+        SAIT_TRY(capture_loop(ctx, cs, poll_block, ctx->d_word, bodies.p, (int)cdiv(maxit, kPollB), &cleanup.loop,
+                              &loop_kernels));
+    if (!cleanup.loop) SAIT_TRY(capture(ctx, cs, poll_block, &cleanup.g, &graph_kernels));
     SAIT_TRY(sync_streams(ctx, s0, cs, ev));
-    int total_iters = 0;
+    int total_iters = 0, graph_launches = 0;
     sait_status result = SAIT_OK;
     for (int round = 0;; round++) {
         // run until no system is active
-        for (int it = 0; it < maxit; it += kPollB) {
-            SAIT_CK(cudaGraphLaunch(cleanup.g, cs));
-            g_sait_launches += graph_kernels;
-            SAIT_CK(cudaMemcpyAsync(h, ctx->d_word, sizeof(int), cudaMemcpyDeviceToHost, cs));
-            SAIT_CK(cudaStreamSynchronize(cs));
-            total_iters += kPollB;
-            if (h[0] == 0) break;
-        }
+        SAIT_TRY(run_iterations(ctx, cs, cleanup.loop, cleanup.g, loop_kernels, graph_kernels, maxit, ctx->d_word,
+                                bodies.p, h, &total_iters, &graph_launches));
         // true residuals per system
         launch_k(k_b_residual, (unsigned)cdiv(n * 8, 256), 256, 0, cs, n, (const int32_t *)A->rp,
                  (const int32_t *)A->ci, (const double *)A->va, (const double *)x, b, B.r.p);
@@ -606,6 +722,8 @@ extern "C" sait_status sait_bicgstab_batched(sait_ctx ctx, sait_mat A, sait_prec
         else if (sts[q] == 2 && result == SAIT_OK && rr[q] > tol) result = SAIT_ERR_BREAKDOWN;
     }
     bi.graph_replays = total_iters;
+    bi.device_loop = cleanup.loop ? 1 : 0;
+    bi.graph_launches = graph_launches;
     if (info) *info = bi;
     if (result == SAIT_OK && bi.converged < nsys) result = SAIT_ERR_NOT_CONVERGED;
     SAIT_TRY(sync_streams(ctx, cs, s0, ev));
@@ -636,17 +754,18 @@ extern "C" sait_status sait_bicgstab_multi(sait_ctx ctx, sait_mat A, sait_prec P
     struct Cleanup {
         cudaStream_t cs;
         cudaEvent_t ev;
-        cudaGraphExec_t g = nullptr;
+        cudaGraphExec_t g = nullptr, loop = nullptr;
         ~Cleanup() {
             cudaStreamSynchronize(cs);
             if (g) cudaGraphExecDestroy(g);
+            if (loop) cudaGraphExecDestroy(loop);
             cudaEventDestroy(ev);
             cudaStreamDestroy(cs);
         }
     } cleanup{cs, ev};
     int *h = (int *)ctx->h_pinned;
     const int rows_per_pass = kT / k;
-    const int nb = (int)std::min<int64_t>(cdiv(n, rows_per_pass), 4LL * ctx->num_sms);
+    const int nb = (int)std::min<int64_t>(cdiv(n, rows_per_pass), 8LL * ctx->num_sms);
     Buffers Bf;
     for (DTemp<double> *d : {&Bf.r, &Bf.rh, &Bf.p, &Bf.v, &Bf.ph, &Bf.sv, &Bf.sh, &Bf.t}) SAIT_CK(d->alloc(nk, s0));
     DTemp<double> W;  // intermediate block of the SAIT apply
@@ -720,18 +839,18 @@ extern "C" sait_status sait_bicgstab_multi(sait_ctx ctx, sait_mat A, sait_prec P
         SAIT_CK(cudaGetLastError());
         return SAIT_OK;
     };
-    SAIT_TRY(capture(ctx, cs, poll_block, &cleanup.g, &graph_kernels));
+    DTemp<int> bodies;
+    SAIT_CK(bodies.alloc(1, s0));
+    int64_t loop_kernels = 0;
+    if (ctx->device_loop)
+        SAIT_TRY(capture_loop(ctx, cs, poll_block, ctx->d_word, bodies.p, (int)cdiv(maxit, kPollB), &cleanup.loop,
+                              &loop_kernels));
+    if (!cleanup.loop) SAIT_TRY(capture(ctx, cs, poll_block, &cleanup.g, &graph_kernels));
     SAIT_TRY(sync_streams(ctx, s0, cs, ev));
-    int total_iters = 0;
+    int total_iters = 0, graph_launches = 0;
     for (int round = 0;; round++) {
-        for (int it = 0; it < maxit; it += kPollB) {
-            SAIT_CK(cudaGraphLaunch(cleanup.g, cs));
-            g_sait_launches += graph_kernels;
-            SAIT_CK(cudaMemcpyAsync(h, ctx->d_word, sizeof(int), cudaMemcpyDeviceToHost, cs));
-            SAIT_CK(cudaStreamSynchronize(cs));
-            total_iters += kPollB;
-            if (h[0] == 0) break;
-        }
+        SAIT_TRY(run_iterations(ctx, cs, cleanup.loop, cleanup.g, loop_kernels, graph_kernels, maxit, ctx->d_word,
+                                bodies.p, h, &total_iters, &graph_launches));
         launch_k(k_mc_residual, ge, 256, 0, cs, n, (int)k, (const int32_t *)A->rp, (const int32_t *)A->ci,
                  (const double *)A->va, (const double *)X, B, Bf.r.p);
         dots(cs, nullptr, 1, Bf.r.p, Bf.r.p, nullptr, nullptr);
@@ -764,6 +883,8 @@ extern "C" sait_status sait_bicgstab_multi(sait_ctx ctx, sait_mat A, sait_prec P
         else if (sts[q] == 2 && result == SAIT_OK && rr[q] > tol) result = SAIT_ERR_BREAKDOWN;
     }
     bi.graph_replays = total_iters;
+    bi.device_loop = cleanup.loop ? 1 : 0;
+    bi.graph_launches = graph_launches;
     if (info) *info = bi;
     if (result == SAIT_OK && bi.converged < k) result = SAIT_ERR_NOT_CONVERGED;
     SAIT_TRY(sync_streams(ctx, cs, s0, ev));

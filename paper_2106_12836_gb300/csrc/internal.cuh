@@ -42,6 +42,7 @@ struct sait_ctx_s {
     int64_t launch_base = 0;
     int64_t batch_tile = 2048;  // rows per tile of the batched solver's schedule (sait_batch_autotune)
     int64_t wait_limit = 0;     // polls of a device-side dependency wait (0: the kernel's default)
+    int device_loop = 1;        // batched solvers: iterate inside a WHILE graph node (0: host replays)
 };
 
 // Kernel launches made by this host thread (graph kernel nodes included).

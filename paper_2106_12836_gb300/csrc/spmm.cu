@@ -9,6 +9,8 @@
 // k columns, the matrix traffic of one apply is shared by k vectors (the
 // block eigensolver and many-right-hand-side cases).
 #include <algorithm>
+#include <cstdint>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -55,6 +57,91 @@ k_spmm_csr(int64_t n, int k, int64_t ldx, int64_t ldy, const int32_t *__restrict
     }
 }
 
+__device__ __forceinline__ void put4(float *p, float a, float b, float c, float d) {
+    *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void put4(double *p, float a, float b, float c, float d) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(widen_exact(a), widen_exact(b));
+    reinterpret_cast<double2 *>(p)[1] = make_double2(widen_exact(c), widen_exact(d));
+}
+
+// FP32 arithmetic on an FP32 block X with k = 4 G columns: a group of G lanes
+// owns a row and each lane gathers four consecutive columns of X[c, :] with
+// one 16-byte load, so one warp serves 32 / G rows and each entry costs a
+// fraction of the instructions of k_spmm_csr's one-column-per-lane form
+// (which issued about 26 warp instructions per entry for k = 64 and was
+// issue- and latency-bound).  Two entries per trip, both gathers issued
+// first.  Every column sums the row's entries in entry order with fmaf, as
+// k_spmm_csr does, so the two kernels give the same bits.  Needs X, Y
+// 16-byte aligned and ldx, ldy multiples of 4.
+template <int G, typename TV, typename TY>
+__global__ void __launch_bounds__(256)
+k_spmm_f32x4(int64_t n, int64_t ldx, int64_t ldy, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+             const TV *__restrict__ va, const float *__restrict__ X, TY *__restrict__ Y, int *calls) {
+    if (calls && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(calls, 1);
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int gl = threadIdx.x & (G - 1);
+    const int gbase = (threadIdx.x & 31) & ~(G - 1);
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << gbase);
+    if (row >= n) return;  // whole groups leave together
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    const float4 *X4 = reinterpret_cast<const float4 *>(X) + gl;
+    const int64_t ld4 = ldx / 4;
+    const int b = rp[row], e = rp[row + 1];
+    for (int base = b; base < e; base += G) {
+        const int idx = base + gl;
+        const int c_l = idx < e ? __ldg(ci + idx) : 0;
+        const float v_l = idx < e ? Load<float, TV>::get(va[idx]) : 0.0f;
+        const int cnt = min(G, e - base);
+        int u = 0;
+        for (; u + 1 < cnt; u += 2) {
+            const int c0 = __shfl_sync(gmask, c_l, u, G), c1 = __shfl_sync(gmask, c_l, u + 1, G);
+            const float v0 = __shfl_sync(gmask, v_l, u, G), v1 = __shfl_sync(gmask, v_l, u + 1, G);
+            const float4 x0 = __ldg(X4 + c0 * ld4), x1 = __ldg(X4 + c1 * ld4);
+            a0 = fmaf(v0, x0.x, a0);
+            a1 = fmaf(v0, x0.y, a1);
+            a2 = fmaf(v0, x0.z, a2);
+            a3 = fmaf(v0, x0.w, a3);
+            a0 = fmaf(v1, x1.x, a0);
+            a1 = fmaf(v1, x1.y, a1);
+            a2 = fmaf(v1, x1.z, a2);
+            a3 = fmaf(v1, x1.w, a3);
+        }
+        if (u < cnt) {
+            const int c0 = __shfl_sync(gmask, c_l, u, G);
+            const float v0 = __shfl_sync(gmask, v_l, u, G);
+            const float4 x0 = __ldg(X4 + c0 * ld4);
+            a0 = fmaf(v0, x0.x, a0);
+            a1 = fmaf(v0, x0.y, a1);
+            a2 = fmaf(v0, x0.z, a2);
+            a3 = fmaf(v0, x0.w, a3);
+        }
+    }
+    put4(Y + row * ldy + 4 * gl, a0, a1, a2, a3);
+}
+
+template <int G, typename TV, typename TY>
+void launch_x4(const sait_mat_s *A, const TV *va, int64_t ldx, int64_t ldy, const float *X, TY *Y, cudaStream_t s,
+               int *calls) {
+    launch_k(k_spmm_f32x4<G, TV, TY>, (unsigned)cdiv(A->n * G, 256), 256, 0, s, A->n, ldx, ldy,
+             (const int32_t *)A->rp, (const int32_t *)A->ci, va, X, Y, calls);
+}
+
+// the four-column form for k in {8, 16, 32, 64, 128} with aligned blocks; false: not applicable
+template <typename TV, typename TY>
+bool launch_f32x4(const sait_mat_s *A, const TV *va, int k, int64_t ldx, int64_t ldy, const float *X, TY *Y,
+                  cudaStream_t s, int *calls) {
+    if (ldx % 4 || ldy % 4 || ((uintptr_t)X & 15) || ((uintptr_t)Y & 15)) return false;
+    switch (k) {
+        case 8: launch_x4<2>(A, va, ldx, ldy, X, Y, s, calls); return true;
+        case 16: launch_x4<4>(A, va, ldx, ldy, X, Y, s, calls); return true;
+        case 32: launch_x4<8>(A, va, ldx, ldy, X, Y, s, calls); return true;
+        case 64: launch_x4<16>(A, va, ldx, ldy, X, Y, s, calls); return true;
+        case 128: launch_x4<32>(A, va, ldx, ldy, X, Y, s, calls); return true;
+        default: return false;
+    }
+}
+
 template <int G, int CPL, typename TV, typename TA, typename TX, typename TY>
 void launch_gc(const sait_mat_s *A, const TV *va, int k, int64_t ldx, int64_t ldy, const TX *X, TY *Y,
                cudaStream_t s, int *calls) {
@@ -78,6 +165,13 @@ void launch_shape(const sait_mat_s *A, const TV *va, int k, int64_t ldx, int64_t
 template <typename TV, typename TA>
 cudaError_t spmm_xy(const sait_mat_s *A, const TV *va, int k, int64_t ldx, int64_t ldy, const void *X,
                     bool x_f32, void *Y, bool y_f32, cudaStream_t s, int *calls) {
+    if constexpr (std::is_same<TA, float>::value) {
+        if (x_f32) {
+            const bool done = y_f32 ? launch_f32x4(A, va, k, ldx, ldy, (const float *)X, (float *)Y, s, calls)
+                                    : launch_f32x4(A, va, k, ldx, ldy, (const float *)X, (double *)Y, s, calls);
+            if (done) return cudaGetLastError();
+        }
+    }
     if (x_f32) {
         if (y_f32) launch_shape<TV, TA>(A, va, k, ldx, ldy, (const float *)X, (float *)Y, s, calls);
         else launch_shape<TV, TA>(A, va, k, ldx, ldy, (const float *)X, (double *)Y, s, calls);

@@ -52,7 +52,8 @@ LAYOUTS = [
     ("sait_drop", "_Drop", ["kind", "p", "tau"]),
     ("sait_info", "Info", ["iters", "cycles", "reorth_steps", "pad", "rel_resid"]),
     ("sait_stats", "Stats", ["launches", "ms", "calls"]),
-    ("sait_batch_info", "BatchInfo", ["nsys", "converged", "max_iters", "graph_replays", "max_rel_resid"]),
+    ("sait_batch_info", "BatchInfo", ["nsys", "converged", "max_iters", "graph_replays", "max_rel_resid", "device_loop",
+                                       "graph_launches"]),
     ("sait_tune_report", "TuneReport", ["ncand", "chosen", "format", "lanes", "us"]),
     ("sait_batch_tune_report", "BatchTuneReport", ["ncand", "chosen", "tile_rows", "us"]),
     ("sait_param", "_Param", ["m_terms", "pad", "drop"]),

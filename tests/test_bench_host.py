@@ -79,3 +79,27 @@ def test_batched_iteration_bytes_by_hand():
     # converged systems skip the vector passes: 600 of the 1000 rows iterate 8 times over 8 replays
     part = one - 22 * 8 * 1000 + 22 * 8 * 600
     assert bench.batched_iter_bytes(A, nl, nu, "f32", 1, row_iters=600 * 8, replays=8) == part
+
+
+def test_batched_iteration_bound_by_hand(monkeypatch):
+    class A:
+        n, nnz = 1000, 4960
+    nl = nu = 5000
+    monkeypatch.setattr(bench, "peaks", lambda: (1000.0, "test"))  # 1000 GB/s = 1e9 bytes per ms
+    rate = 2 * 152 * 2070e6 / 1e3                                   # FP64 multiply-adds per ms
+    bw = 1e9
+    # FP64 storage, 64 columns: each SAIT product does (nl + nu) x 64 FMAs against its bytes
+    k = 64
+    apply_b, apply_f = (nl + nu) * 12 + 8 * 1001 + 32 * 1000 * k, (nl + nu) * k
+    spmv_b, spmv_f = 4960 * 12 + 4 * 1001 + 16 * 1000 * k, 4960 * k
+    vec_b, vec_f = 22 * 8 * 1000 * k, 12 * 1000 * k
+    want = 2 * max(apply_b / bw, apply_f / rate) + 2 * max(spmv_b / bw, spmv_f / rate) + max(vec_b / bw, vec_f / rate)
+    got = bench.batched_iter_bound(A, nl, nu, "f64", k)
+    assert abs(got["bound_ms"] - want) < 1e-12 * want
+    assert got["fp64_fma"] == 2 * apply_f + 2 * spmv_f + vec_f
+    # the FP32 mode multiplies the SAIT products in FP32: no FP64 term there
+    got32 = bench.batched_iter_bound(A, nl, nu, "f32", k)
+    assert got32["fp64_fma"] == 2 * spmv_f + vec_f
+    apply32_b = (nl + nu) * 8 + 8 * 1001 + 24 * 1000 * k
+    want32 = 2 * apply32_b / bw + 2 * max(spmv_b / bw, spmv_f / rate) + max(vec_b / bw, vec_f / rate)
+    assert abs(got32["bound_ms"] - want32) < 1e-12 * want32

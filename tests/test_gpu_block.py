@@ -43,7 +43,7 @@ def test_spmm_matches_columns(sg, oracle_lib, k):
 
 
 @pytest.mark.parametrize("store", ["f64", "f32", "bf16", "f32x64"])
-@pytest.mark.parametrize("k", [16, 64])
+@pytest.mark.parametrize("k", [8, 16, 40, 64, 128])
 def test_apply_multi_matches_columns(sg, oracle_lib, store, k):
     A = synth.varcoef3d(14, 1.0, 4)
     Lo, Uo = oracle_lib.ilu0(A)
@@ -62,3 +62,25 @@ def test_apply_multi_matches_columns(sg, oracle_lib, store, k):
         ref = oracle_lib.apply(MLo, MUo, R[:, t])
         bound = oracle_lib.apply(aL, aU, np.abs(R[:, t]))
         assert np.all(np.abs(Z[:, t] - ref) <= TOL[store] * bound), t
+
+
+@pytest.mark.parametrize("store", ["f32", "bf16"])
+@pytest.mark.parametrize("k", [8, 64, 128])
+def test_apply_multi_four_column_gather_same_bits(sg, store, k):
+    """FP32 block products gather four columns per lane when the blocks are
+    16-byte aligned with leading dimensions divisible by 4, and one column per
+    lane otherwise (here: Z with leading dimension k + 1).  Both sum each
+    column's entries in entry order, so Z is the same bit for bit."""
+    A = synth.varcoef3d(12, 1.0, 5)
+    R = synth.uniform(k + 2, (A.n, k))
+    with sg.Context() as ctx:
+        L, U = sg.sait_ilu0(ctx, A.n, dev(A.rp), dev(A.ci), dev(A.va))
+        ML = sg.sait_build(ctx, L, True, 3, "rowrel", 1e-3, store=store)
+        MU = sg.sait_build(ctx, U, False, 3, "rowrel", 1e-3, store=store)
+        Za = sg.sait_apply_multi(ctx, ML, MU, dev(R))
+        Zw = torch.full((A.n, k + 1), 7.0, dtype=torch.float64, device="cuda")
+        sg.sait_apply_multi(ctx, ML, MU, dev(R), Zw[:, :k])
+        torch.cuda.synchronize()
+    Za, Zw = Za.cpu().numpy(), Zw.cpu().numpy()
+    assert np.array_equal(Za, Zw[:, :k])
+    assert (Zw[:, k] == 7.0).all()
