@@ -65,17 +65,23 @@ __device__ __forceinline__ void put4(double *p, float a, float b, float c, float
     reinterpret_cast<double2 *>(p)[1] = make_double2(widen_exact(c), widen_exact(d));
 }
 
+// entries of a row gathered per trip in k_spmm_f32x4, and the resident blocks
+// per SM asked of the compiler (at most 40 registers): 128^3 x 64 FP32 apply
+// 1.52 ms with 2 entries, 1.44 ms with 4, 1.39 ms with 4 and 6 blocks per SM
+constexpr int kX4Entries = 4;
+constexpr int kX4MinBlocks = 6;
+
 // FP32 arithmetic on an FP32 block X with k = 4 G columns: a group of G lanes
 // owns a row and each lane gathers four consecutive columns of X[c, :] with
 // one 16-byte load, so one warp serves 32 / G rows and each entry costs a
 // fraction of the instructions of k_spmm_csr's one-column-per-lane form
 // (which issued about 26 warp instructions per entry for k = 64 and was
-// issue- and latency-bound).  Two entries per trip, both gathers issued
-// first.  Every column sums the row's entries in entry order with fmaf, as
+// issue- and latency-bound).  kX4Entries entries per trip, all gathers
+// issued first.  Every column sums the row's entries in entry order with fmaf, as
 // k_spmm_csr does, so the two kernels give the same bits.  Needs X, Y
 // 16-byte aligned and ldx, ldy multiples of 4.
-template <int G, typename TV, typename TY>
-__global__ void __launch_bounds__(256)
+template <int G, int U, typename TV, typename TY>
+__global__ void __launch_bounds__(256, kX4MinBlocks)
 k_spmm_f32x4(int64_t n, int64_t ldx, int64_t ldy, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
              const TV *__restrict__ va, const float *__restrict__ X, TY *__restrict__ Y, int *calls) {
     if (calls && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(calls, 1);
@@ -88,33 +94,34 @@ k_spmm_f32x4(int64_t n, int64_t ldx, int64_t ldy, const int32_t *__restrict__ rp
     const float4 *X4 = reinterpret_cast<const float4 *>(X) + gl;
     const int64_t ld4 = ldx / 4;
     const int b = rp[row], e = rp[row + 1];
+    auto add = [&](float v, const float4 &x) {
+        a0 = fmaf(v, x.x, a0);
+        a1 = fmaf(v, x.y, a1);
+        a2 = fmaf(v, x.z, a2);
+        a3 = fmaf(v, x.w, a3);
+    };
     for (int base = b; base < e; base += G) {
         const int idx = base + gl;
         const int c_l = idx < e ? __ldg(ci + idx) : 0;
         const float v_l = idx < e ? Load<float, TV>::get(va[idx]) : 0.0f;
         const int cnt = min(G, e - base);
         int u = 0;
-        for (; u + 1 < cnt; u += 2) {
-            const int c0 = __shfl_sync(gmask, c_l, u, G), c1 = __shfl_sync(gmask, c_l, u + 1, G);
-            const float v0 = __shfl_sync(gmask, v_l, u, G), v1 = __shfl_sync(gmask, v_l, u + 1, G);
-            const float4 x0 = __ldg(X4 + c0 * ld4), x1 = __ldg(X4 + c1 * ld4);
-            a0 = fmaf(v0, x0.x, a0);
-            a1 = fmaf(v0, x0.y, a1);
-            a2 = fmaf(v0, x0.z, a2);
-            a3 = fmaf(v0, x0.w, a3);
-            a0 = fmaf(v1, x1.x, a0);
-            a1 = fmaf(v1, x1.y, a1);
-            a2 = fmaf(v1, x1.z, a2);
-            a3 = fmaf(v1, x1.w, a3);
+        for (; u + U <= cnt; u += U) {  // U entries per trip, all gathers issued first
+            float4 xv[U];
+            float vv[U];
+#pragma unroll
+            for (int t = 0; t < U; t++) {
+                const int c = __shfl_sync(gmask, c_l, u + t, G);
+                vv[t] = __shfl_sync(gmask, v_l, u + t, G);
+                xv[t] = __ldg(X4 + c * ld4);
+            }
+#pragma unroll
+            for (int t = 0; t < U; t++) add(vv[t], xv[t]);
         }
-        if (u < cnt) {
-            const int c0 = __shfl_sync(gmask, c_l, u, G);
-            const float v0 = __shfl_sync(gmask, v_l, u, G);
-            const float4 x0 = __ldg(X4 + c0 * ld4);
-            a0 = fmaf(v0, x0.x, a0);
-            a1 = fmaf(v0, x0.y, a1);
-            a2 = fmaf(v0, x0.z, a2);
-            a3 = fmaf(v0, x0.w, a3);
+        for (; u < cnt; u++) {
+            const int c = __shfl_sync(gmask, c_l, u, G);
+            const float v = __shfl_sync(gmask, v_l, u, G);
+            add(v, __ldg(X4 + c * ld4));
         }
     }
     put4(Y + row * ldy + 4 * gl, a0, a1, a2, a3);
@@ -123,7 +130,8 @@ k_spmm_f32x4(int64_t n, int64_t ldx, int64_t ldy, const int32_t *__restrict__ rp
 template <int G, typename TV, typename TY>
 void launch_x4(const sait_mat_s *A, const TV *va, int64_t ldx, int64_t ldy, const float *X, TY *Y, cudaStream_t s,
                int *calls) {
-    launch_k(k_spmm_f32x4<G, TV, TY>, (unsigned)cdiv(A->n * G, 256), 256, 0, s, A->n, ldx, ldy,
+    constexpr int U = G < kX4Entries ? G : kX4Entries;
+    launch_k(k_spmm_f32x4<G, U, TV, TY>, (unsigned)cdiv(A->n * G, 256), 256, 0, s, A->n, ldx, ldy,
              (const int32_t *)A->rp, (const int32_t *)A->ci, va, X, Y, calls);
 }
 
