@@ -251,44 +251,66 @@ __global__ void k_res_finish(int k, int nb, const double *__restrict__ partial, 
 }
 
 // ---- small dense kernels (one block) ---------------------------------------------
-// In-place lower Cholesky of G (m x m, ld m) in shared memory; returns 1 on failure.
-__device__ int dev_chol(int m, double *G) {
+// In-place lower Cholesky of G (m x m, leading dimension ld) in shared memory,
+// right-looking: per column one reciprocal square root on one thread, then the
+// column scaled and the trailing block updated in parallel (a left-looking
+// form ran length-j FP64 dot chains on one thread, 64 cycles per operation).
+// Returns 1 when a pivot is not above 1e-14 of the largest diagonal entry.
+__device__ int dev_chol(int m, double *G, int ld) {
     __shared__ int fail;
-    __shared__ double mx;
+    __shared__ double mx, s_ir;
     if (threadIdx.x == 0) {
         fail = 0;
         mx = 0.0;
-        for (int i = 0; i < m; i++) mx = fmax(mx, G[i * m + i]);
+        for (int i = 0; i < m; i++) mx = fmax(mx, G[i * ld + i]);
     }
     __syncthreads();
     for (int j = 0; j < m; j++) {
         if (threadIdx.x == 0) {
-            double d = G[j * m + j];
-            for (int q = 0; q < j; q++) d -= G[j * m + q] * G[j * m + q];
+            const double d = G[j * ld + j];
             if (!(d > 1e-14 * mx)) fail = 1;
-            G[j * m + j] = d > 0.0 ? sqrt(d) : 1.0;
+            const double ir = d > 0.0 ? rsqrt(d) : 1.0;
+            G[j * ld + j] = d > 0.0 ? d * ir : 1.0;
+            s_ir = ir;
         }
         __syncthreads();
-        const double djj = G[j * m + j];
-        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
-            double s = G[i * m + j];
-            for (int q = 0; q < j; q++) s -= G[i * m + q] * G[j * m + q];
-            G[i * m + j] = s / djj;
+        const double ir = s_ir;
+        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) G[i * ld + j] *= ir;
+        __syncthreads();
+        const int r = m - j - 1;
+        for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+            const int i = j + 1 + e / r, l = j + 1 + e % r;
+            if (l <= i) G[i * ld + l] = fma(-G[i * ld + j], G[l * ld + j], G[i * ld + l]);
         }
-        for (int i = threadIdx.x; i < j; i += blockDim.x) G[i * m + j] = 0.0;
         __syncthreads();
     }
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x)
+        if (e % m > e / m) G[(e / m) * ld + e % m] = 0.0;
+    __syncthreads();
     return fail;
 }
 
-// R = L^{-1} (lower triangular), one column per thread
-__device__ void dev_tri_inv(int m, const double *L, double *R) {
+// R = L^{-1} (lower triangular; leading dimensions ldl, ldr), one column per
+// thread, with the reciprocals of the diagonal formed once and each row's sum
+// split in two chains
+__device__ void dev_tri_inv(int m, const double *L, int ldl, double *R, int ldr) {
+    __shared__ double dinv[kMaxM];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) dinv[i] = 1.0 / L[i * ldl + i];
+    __syncthreads();
     for (int j = threadIdx.x; j < m; j += blockDim.x)
         for (int i = 0; i < m; i++) {
-            if (i < j) { R[i * m + j] = 0.0; continue; }
-            double s = (i == j) ? 1.0 : 0.0;
-            for (int q = j; q < i; q++) s -= L[i * m + q] * R[q * m + j];
-            R[i * m + j] = s / L[i * m + i];
+            if (i < j) {
+                R[i * ldr + j] = 0.0;
+                continue;
+            }
+            double s0 = (i == j) ? 1.0 : 0.0, s1 = 0.0;
+            int q = j;
+            for (; q + 1 < i; q += 2) {
+                s0 = fma(-L[i * ldl + q], R[q * ldr + j], s0);
+                s1 = fma(-L[i * ldl + q + 1], R[(q + 1) * ldr + j], s1);
+            }
+            if (q < i) s0 = fma(-L[i * ldl + q], R[q * ldr + j], s0);
+            R[i * ldr + j] = (s0 + s1) * dinv[i];
         }
     __syncthreads();
 }
@@ -308,10 +330,10 @@ __global__ void k_cholqr_factor(int m, const double *__restrict__ G, double *out
     __syncthreads();
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) Gs[e] = G[e] * dsc[e / m] * dsc[e % m];
     __syncthreads();
-    int f = dev_chol(m, Gs);
+    int f = dev_chol(m, Gs, m);
     if (threadIdx.x == 0)
         for (int a = 0; a < m; a++) f |= dsc[a] == 0.0;
-    dev_tri_inv(m, Gs, Ri);
+    dev_tri_inv(m, Gs, m, Ri, m);
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         const int a = e / m, b = e % m;
         out[e] = dsc[a] * Ri[b * m + a];  // D L^{-T}
@@ -319,86 +341,35 @@ __global__ void k_cholqr_factor(int m, const double *__restrict__ G, double *out
     if (threadIdx.x == 0) *flag = f;
 }
 
-// Rayleigh-Ritz: generalized symmetric eigenproblem GA c = theta GB c (m x m);
-// theta[0:k] ascending and coefficients c (m x k) = L^{-T} Y(:, 0:k); flag = 1
-// if GB is not numerically positive definite.
-__global__ void __launch_bounds__(kT) k_rayleigh_ritz(int m, int k, const double *__restrict__ GA,
-                                                      const double *__restrict__ GB, double *theta, double *coef,
-                                                      int *flag) {
-    extern __shared__ double sm[];
-    const int me = m + (m & 1);  // even size for the round-robin ordering
-    double *L = sm;              // m x m
-    double *Li = L + m * m;      // m x m
-    double *C = Li + m * m;      // me x me
-    double *V = C + me * me;     // me x me
-    double *T = V + me * me;     // m x m scratch
-    double *rot = T + m * m;     // me/2 x 2 (c, s)
-    int *pr = (int *)(rot + me); // me/2 x 2 pair indices
-    __shared__ double offn, fro;
-    for (int e = threadIdx.x; e < m * m; e += kT) {
-        const int a = e / m, b = e % m;
-        L[e] = 0.5 * (GB[a * m + b] + GB[b * m + a]);
-        T[e] = 0.5 * (GA[a * m + b] + GA[b * m + a]);
-    }
-    __syncthreads();
-    const int f = dev_chol(m, L);
-    if (threadIdx.x == 0) *flag = f;
-    if (f) return;  // uniform: f is read from shared memory by every thread
-    dev_tri_inv(m, L, Li);
-    // C = Li T Li^T (padded to me with a decoupled large diagonal entry)
-    for (int e = threadIdx.x; e < m * m; e += kT) {
-        const int a = e / m, b = e % m;
-        double s = 0.0;
-        for (int q = 0; q <= a; q++) s += Li[a * m + q] * T[q * m + b];
-        V[a * me + b] = s;  // temporary: Li T
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < me * me; e += kT) {
-        const int a = e / me, b = e % me;
-        double s = 0.0;
-        if (a < m && b < m)
-            for (int q = 0; q <= b; q++) s += V[a * me + q] * Li[b * m + q];
-        C[e] = s;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < me * me; e += kT) {
-        const int a = e / me, b = e % me;
-        if (a < b) {
-            const double s = 0.5 * (C[a * me + b] + C[b * me + a]);
-            C[a * me + b] = s;
-            C[b * me + a] = s;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double mx = 0.0, f2 = 0.0;
-        for (int i = 0; i < m; i++) mx = fmax(mx, fabs(C[i * me + i]));
-        if (me > m) C[m * me + m] = 10.0 * mx + 1.0;  // sorted last
-        for (int i = 0; i < me * me; i++) f2 += C[i] * C[i];
-        fro = sqrt(f2);
-    }
-    for (int e = threadIdx.x; e < me * me; e += kT) V[e] = (e / me == e % me) ? 1.0 : 0.0;
-    __syncthreads();
+// Cyclic Jacobi on the symmetric me x me matrix C (me even; shared memory,
+// leading dimension ld), with the rotations accumulated into V: in round-robin
+// order, so every step rotates me/2 disjoint pairs at once.  A pair whose
+// off-diagonal entry is at most thr is not rotated.  Stops once the
+// off-diagonal norm is at most stop, or after max_sweeps sweeps.  rot holds me
+// values of type F, pr me ints.  ld = me + 1 keeps the column updates (lanes
+// on consecutive rows) on distinct shared-memory banks; with ld = 48 every
+// lane of a warp hit the same bank.
+template <typename F>
+__device__ void jacobi_sweeps(int me, int ld, F *C, F *V, F *rot, int *pr, F stop, F thr, int max_sweeps) {
+    __shared__ F offn;
+    __shared__ F opart[kT / 32];
     const int np = me / 2;
-    // a pair whose off-diagonal entry is already below thr cannot matter at the
-    // stopping level (offn <= 1e-15 fro) and is not rotated: in the later
-    // sweeps most pairs are skipped, which saves the FP64 rotation work
-    const double thr = 1e-17 * fro / me;
-    __shared__ double opart[kT / 32];
-    for (int sweep = 0; sweep < 40; sweep++) {
-        double o = 0.0;
-        for (int e = threadIdx.x; e < me * me; e += kT)
-            if (e / me != e % me) o += C[e] * C[e];
+    for (int sweep = 0; sweep < max_sweeps; sweep++) {
+        F o = F(0);
+        for (int e = threadIdx.x; e < me * me; e += kT) {
+            const int a = e / me, b = e % me;
+            if (a != b) o += C[a * ld + b] * C[a * ld + b];
+        }
         for (int d = 16; d > 0; d >>= 1) o += __shfl_xor_sync(0xffffffffu, o, d);
         if ((threadIdx.x & 31) == 0) opart[threadIdx.x >> 5] = o;
         __syncthreads();
         if (threadIdx.x == 0) {
-            double t = 0.0;
+            F t = F(0);
             for (int w = 0; w < kT / 32; w++) t += opart[w];
             offn = sqrt(t);
         }
         __syncthreads();
-        if (offn <= 1e-15 * fro || fro == 0.0) break;
+        if (offn <= stop) break;  // uniform: every thread reads the same shared value
         for (int step = 0; step < me - 1; step++) {
             // round-robin pairs: position 0 fixed, the others rotate
             for (int t = threadIdx.x; t < np; t += kT) {
@@ -408,63 +379,219 @@ __global__ void __launch_bounds__(kT) k_rayleigh_ritz(int m, int k, const double
                 const int lo = min(p, q), hi = max(p, q);
                 pr[2 * t] = lo;
                 pr[2 * t + 1] = hi;
-                const double apq = C[lo * me + hi];
-                double c = 1.0, s = 0.0;
-                if (fabs(apq) > thr) {  // symmetric 2x2 Schur decomposition
-                    const double tau = (C[hi * me + hi] - C[lo * me + lo]) / (2.0 * apq);
-                    const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                    c = 1.0 / sqrt(1.0 + tt * tt);
-                    s = tt * c;
+                const F apq = C[lo * ld + hi];
+                F c = F(1), sn = F(0);
+                if (fabs(apq) > thr) {
+                    // symmetric 2x2 Schur decomposition: t = tan of the angle,
+                    // sign(d) 2 a / (|d| + sqrt(d^2 + 4 a^2)) with d = a_hh - a_ll
+                    const F d = C[hi * ld + hi] - C[lo * ld + lo];
+                    const F tt = (d >= F(0) ? F(2) : F(-2)) * apq / (fabs(d) + sqrt(d * d + F(4) * apq * apq));
+                    c = rsqrt(F(1) + tt * tt);
+                    sn = tt * c;
                 }
                 rot[2 * t] = c;
-                rot[2 * t + 1] = s;
+                rot[2 * t + 1] = sn;
             }
             __syncthreads();
             for (int e = threadIdx.x; e < np * me; e += kT) {  // C <- C J, V <- V J (columns)
                 const int t = e / me, r = e % me;
                 const int p = pr[2 * t], q = pr[2 * t + 1];
-                const double c = rot[2 * t], s = rot[2 * t + 1];
-                if (s == 0.0) continue;
-                double a = C[r * me + p], b = C[r * me + q];
-                C[r * me + p] = c * a - s * b;
-                C[r * me + q] = s * a + c * b;
-                a = V[r * me + p];
-                b = V[r * me + q];
-                V[r * me + p] = c * a - s * b;
-                V[r * me + q] = s * a + c * b;
+                const F c = rot[2 * t], sn = rot[2 * t + 1];
+                if (sn == F(0)) continue;
+                F a = C[r * ld + p], b = C[r * ld + q];
+                C[r * ld + p] = c * a - sn * b;
+                C[r * ld + q] = sn * a + c * b;
+                a = V[r * ld + p];
+                b = V[r * ld + q];
+                V[r * ld + p] = c * a - sn * b;
+                V[r * ld + q] = sn * a + c * b;
             }
             __syncthreads();
             for (int e = threadIdx.x; e < np * me; e += kT) {  // C <- J^T C (rows)
                 const int t = e / me, r = e % me;
                 const int p = pr[2 * t], q = pr[2 * t + 1];
-                const double c = rot[2 * t], s = rot[2 * t + 1];
-                if (s == 0.0) continue;
-                const double a = C[p * me + r], b = C[q * me + r];
-                C[p * me + r] = c * a - s * b;
-                C[q * me + r] = s * a + c * b;
+                const F c = rot[2 * t], sn = rot[2 * t + 1];
+                if (sn == F(0)) continue;
+                const F a = C[p * ld + r], b = C[q * ld + r];
+                C[p * ld + r] = c * a - sn * b;
+                C[q * ld + r] = sn * a + c * b;
             }
             __syncthreads();
         }
     }
+}
+
+// Y = op(A) B for me x me matrices in shared memory (leading dimension ld;
+// op(A) = A^T when ta), one output entry per thread and pass, each sum split
+// in four chains (one FP64 operation every 64 cycles per chain otherwise)
+__device__ void smem_gemm(int me, int ld, const double *A, bool ta, const double *B, double *Y) {
+    for (int e = threadIdx.x; e < me * me; e += kT) {
+        const int a = e / me, b = e % me;
+        double s[4] = {0.0, 0.0, 0.0, 0.0};
+        int q = 0;
+        if (ta) {
+            for (; q + 3 < me; q += 4)
+#pragma unroll
+                for (int u = 0; u < 4; u++) s[u] = fma(A[(q + u) * ld + a], B[(q + u) * ld + b], s[u]);
+            for (; q < me; q++) s[0] = fma(A[q * ld + a], B[q * ld + b], s[0]);
+        } else {
+            for (; q + 3 < me; q += 4)
+#pragma unroll
+                for (int u = 0; u < 4; u++) s[u] = fma(A[a * ld + q + u], B[(q + u) * ld + b], s[u]);
+            for (; q < me; q++) s[0] = fma(A[a * ld + q], B[q * ld + b], s[0]);
+        }
+        Y[a * ld + b] = (s[0] + s[1]) + (s[2] + s[3]);
+    }
+    __syncthreads();
+}
+
+// Rayleigh-Ritz: generalized symmetric eigenproblem GA c = theta GB c (m x m);
+// theta[0:k] ascending and coefficients c (m x k) = L^{-T} Y(:, 0:k); flag = 1
+// if GB is not numerically positive definite.
+//
+// The reduced matrix C = L^{-1} GA L^{-T} is diagonalised by Jacobi rotations
+// in two phases.  One block runs this kernel, and one SM issues about two FP64
+// operations per clock on GB300, so FP64 sweeps from the start (each rotating
+// every entry of C and V me - 1 times) took about 3 ms at m = 48.  The first
+// sweeps therefore run in FP32 on a rounded copy, down to an off-diagonal norm
+// of 1e-6 ||C||_F; their rotations Q are made orthonormal in FP64 by two
+// Newton-Schulz steps Q <- Q (3 I - Q^T Q) / 2 (orthogonality error 1e-7, then
+// ~1e-14, then rounding level), C becomes Q^T C Q in FP64, and FP64 sweeps
+// finish the diagonalisation from there (two, by quadratic convergence), so
+// the result has the accuracy of an all-FP64 Jacobi run.  Every shared matrix
+// has a leading dimension one above its order (no bank conflicts in the
+// column-wise passes).
+__global__ void __launch_bounds__(kT) k_rayleigh_ritz(int m, int k, const double *__restrict__ GA,
+                                                      const double *__restrict__ GB, double *theta, double *coef,
+                                                      int *flag) {
+    extern __shared__ double sm[];
+    const int me = m + (m & 1);  // even size for the round-robin ordering
+    const int lm = m + 1, ld = me + 1;
+    double *L = sm;              // m x m (ld lm)
+    double *Li = L + m * lm;     // m x m (ld lm)
+    double *T = Li + m * lm;     // m x m (ld lm)
+    double *C = T + m * lm;      // me x me (ld ld)
+    double *V = C + me * ld;     // me x me
+    double *W = V + me * ld;     // me x me scratch
+    double *X = W + me * ld;     // me x me scratch (the FP32 copies of C and V during the FP32 sweeps)
+    double *rot = X + me * ld;   // me/2 x 2 (c, s)
+    int *pr = (int *)(rot + me); // me/2 x 2 pair indices
+    float *C32 = (float *)X, *V32 = C32 + me * ld;
+    __shared__ double fro;
+    for (int e = threadIdx.x; e < m * m; e += kT) {
+        const int a = e / m, b = e % m;
+        L[a * lm + b] = 0.5 * (GB[a * m + b] + GB[b * m + a]);
+        T[a * lm + b] = 0.5 * (GA[a * m + b] + GA[b * m + a]);
+    }
+    __syncthreads();
+    const int f = dev_chol(m, L, lm);
+    if (threadIdx.x == 0) *flag = f;
+    if (f) return;  // uniform: f is read from shared memory by every thread
+    dev_tri_inv(m, L, lm, Li, lm);
+    // C = Li T Li^T (padded to me with a decoupled large diagonal entry)
+    for (int e = threadIdx.x; e < m * m; e += kT) {
+        const int a = e / m, b = e % m;
+        double s0 = 0.0, s1 = 0.0;
+        int q = 0;
+        for (; q + 1 <= a; q += 2) {
+            s0 = fma(Li[a * lm + q], T[q * lm + b], s0);
+            s1 = fma(Li[a * lm + q + 1], T[(q + 1) * lm + b], s1);
+        }
+        if (q <= a) s0 = fma(Li[a * lm + q], T[q * lm + b], s0);
+        V[a * ld + b] = s0 + s1;  // temporary: Li T
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < me * me; e += kT) {
+        const int a = e / me, b = e % me;
+        double s0 = 0.0, s1 = 0.0;
+        if (a < m && b < m) {
+            int q = 0;
+            for (; q + 1 <= b; q += 2) {
+                s0 = fma(V[a * ld + q], Li[b * lm + q], s0);
+                s1 = fma(V[a * ld + q + 1], Li[b * lm + q + 1], s1);
+            }
+            if (q <= b) s0 = fma(V[a * ld + q], Li[b * lm + q], s0);
+        }
+        C[a * ld + b] = s0 + s1;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < me * me; e += kT) {
+        const int a = e / me, b = e % me;
+        if (a < b) {
+            const double sv = 0.5 * (C[a * ld + b] + C[b * ld + a]);
+            C[a * ld + b] = sv;
+            C[b * ld + a] = sv;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mx = 0.0, f2 = 0.0;
+        for (int i = 0; i < m; i++) mx = fmax(mx, fabs(C[i * ld + i]));
+        if (me > m) C[m * ld + m] = 10.0 * mx + 1.0;  // sorted last
+        for (int i = 0; i < me; i++)
+            for (int j = 0; j < me; j++) f2 += C[i * ld + j] * C[i * ld + j];
+        fro = sqrt(f2);
+    }
+    __syncthreads();
+    // FP32 sweeps on a rounded copy
+    for (int e = threadIdx.x; e < me * me; e += kT) {
+        const int a = e / me, b = e % me;
+        C32[a * ld + b] = (float)C[a * ld + b];
+        V32[a * ld + b] = a == b ? 1.0f : 0.0f;
+    }
+    __syncthreads();
+    const float fro32 = (float)fro;
+    jacobi_sweeps<float>(me, ld, C32, V32, (float *)rot, pr, 1e-6f * fro32, 1e-9f * fro32 / (float)me, 20);
+    // Q = their rotations, orthonormalised in FP64 (two Newton-Schulz steps)
+    for (int e = threadIdx.x; e < me * me; e += kT) {
+        const int a = e / me, b = e % me;
+        V[a * ld + b] = (double)V32[a * ld + b];
+    }
+    __syncthreads();
+    for (int it = 0; it < 2; it++) {
+        smem_gemm(me, ld, V, true, V, W);  // Q^T Q
+        for (int e = threadIdx.x; e < me * me; e += kT) {
+            const int a = e / me, b = e % me;
+            W[a * ld + b] = (a == b ? 1.5 : 0.0) - 0.5 * W[a * ld + b];
+        }
+        __syncthreads();
+        smem_gemm(me, ld, V, false, W, X);  // Q (3 I - Q^T Q) / 2
+        for (int e = threadIdx.x; e < me * me; e += kT) {
+            const int a = e / me, b = e % me;
+            V[a * ld + b] = X[a * ld + b];
+        }
+        __syncthreads();
+    }
+    // C <- Q^T C Q, symmetrised
+    smem_gemm(me, ld, C, false, V, W);
+    smem_gemm(me, ld, V, true, W, X);
+    for (int e = threadIdx.x; e < me * me; e += kT) {
+        const int a = e / me, b = e % me;
+        C[a * ld + b] = 0.5 * (X[a * ld + b] + X[b * ld + a]);
+    }
+    __syncthreads();
+    // FP64 sweeps to the stopping level: a pair whose off-diagonal entry is
+    // already below thr cannot matter at that level and is not rotated
+    jacobi_sweeps<double>(me, ld, C, V, rot, pr, 1e-15 * fro, 1e-17 * fro / me, 40);
     // sort: rank of each eigenvalue (ties by index), then pick the k smallest
     __shared__ int order[kMaxM + 2];
     for (int i = threadIdx.x; i < me; i += kT) {
-        const double wi = C[i * me + i];
+        const double wi = C[i * ld + i];
         int rank = 0;
         for (int j = 0; j < me; j++) {
-            const double wj = C[j * me + j];
+            const double wj = C[j * ld + j];
             rank += (wj < wi) || (wj == wi && j < i);
         }
         order[rank] = i;
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < k; j += kT) theta[j] = C[order[j] * me + order[j]];
+    for (int j = threadIdx.x; j < k; j += kT) theta[j] = C[order[j] * ld + order[j]];
     // coef = Li^T V(:, order[0:k])  (rows 0..m-1)
     for (int e = threadIdx.x; e < m * k; e += kT) {
         const int a = e / k, j = e % k;
         const int col = order[j];
         double s = 0.0;
-        for (int q = a; q < m; q++) s += Li[q * m + a] * V[q * me + col];
+        for (int q = a; q < m; q++) s += Li[q * lm + a] * V[q * ld + col];
         coef[a * k + j] = s;
     }
 }
@@ -551,7 +678,7 @@ extern "C" sait_status sait_lobpcg(sait_ctx ctx, sait_mat A, sait_prec P, int32_
     SAIT_CK(w.flag.alloc(1, s));
     SAIT_CK(w.active.alloc(kMaxK, s));
     SAIT_CK(w.nact.alloc(1, s));
-    const size_t rr_smem = (size_t)(2 * mmax * mmax + 3 * (mmax + 1) * (mmax + 1)) * sizeof(double) +
+    const size_t rr_smem = (size_t)(3 * mmax * (mmax + 1) + 4 * (mmax + 1) * (mmax + 2)) * sizeof(double) +
                            (size_t)(mmax + 2) * sizeof(double) + (size_t)(mmax + 2) * sizeof(int) + 64;
     SAIT_CK(cudaFuncSetAttribute(k_rayleigh_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rr_smem));
     SAIT_CK(cudaFuncSetAttribute(k_gram<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGramSmem));
